@@ -1,0 +1,374 @@
+"""FP64 CPU oracle of the refined template-matching EBSD indexer (arXiv 1807.11313).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The arithmetic
+lives in ``xcf_oracle.c`` (plain C, FP64, its own FFT); this module compiles it
+with gcc on first use and marshals numpy arrays through ctypes.  It shares no
+code with the CUDA library.
+
+Parity unpinned: window shape, band-pass shape and cut-offs, log-polar
+sampling constants (the paper gives none of them); everything else is pinned
+by the tests under ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "xcf_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/liboracle.so (gcc, -O2, OpenMP)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Opts(C.Structure):
+    _fields_ = [("window", C.c_int32), ("sigma_hp", C.c_double), ("sigma_lp", C.c_double),
+                ("lp_nr", C.c_int32), ("lp_neta", C.c_int32), ("lp_rmin", C.c_double),
+                ("lp_rmax", C.c_double)]
+
+
+def default_opts(n: int, **kw) -> Opts:
+    """Defaults: Hann window, sigma_hp = 2, sigma_lp = n/4 cycles per image,
+    log-polar n/2 radii x 2n angles over r in [4, n/2 - 1] px."""
+    d = dict(window=1, sigma_hp=2.0, sigma_lp=n / 4.0, lp_nr=n // 2, lp_neta=2 * n,
+             lp_rmin=4.0, lp_rmax=n / 2.0 - 1.0)
+    d.update(kw)
+    return Opts(**d)
+
+
+_D = C.POINTER(C.c_double)
+_F = C.POINTER(C.c_float)
+_I = C.POINTER(C.c_int32)
+
+
+def _lib_handle():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            sig = {
+                "orc_num_threads": ([], C.c_int),
+                "orc_dft1": ([_D, _D, C.c_int, C.c_int], None),
+                "orc_dft2_brute": ([_D, _D, C.c_int, C.c_int], None),
+                "orc_fft1": ([_D, C.c_int, C.c_int], None),
+                "orc_fft2": ([_D, C.c_int, C.c_int], None),
+                "orc_crop": ([C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                              _I, _I, _I, _D], C.c_int),
+                "orc_bandpass": ([C.c_int, C.c_int, C.c_int, C.c_double, C.c_double], C.c_double),
+                "orc_window": ([C.c_int, C.c_int, C.c_int], C.c_double),
+                "orc_prep": ([_D, C.c_int, C.POINTER(Opts), _D, _D], C.c_int),
+                "orc_prep_many": ([_D, C.c_int, C.c_int, C.POINTER(Opts), _D, _D, _I], None),
+                "orc_xcf_surface": ([_D, _D, C.c_int, _D], None),
+                "orc_xcf_spatial": ([_D, _D, C.c_int, _D], None),
+                "orc_parabola": ([C.c_double, C.c_double, C.c_double], C.c_double),
+                "orc_peak": ([_D, C.c_int, _D, _I, _I, _D, _D], None),
+                "orc_index": ([_D, C.c_int, _D, C.c_int, C.c_int, _I, _I, _D, _D, _D], None),
+                "orc_lambert_forward": ([_D, _D, _D], None),
+                "orc_lambert_inverse": ([C.c_double, C.c_double, _D], None),
+                "orc_master_lookup": ([_F, C.c_int, _D], C.c_double),
+                "orc_quat_to_matrix": ([_D, _D], None),
+                "orc_project": ([_F, C.c_int, _D, _D, C.c_double, C.c_double, C.c_int, _D], None),
+                "orc_project_many": ([_F, C.c_int, _D, _D, C.c_int, C.c_double, C.c_double,
+                                      C.c_int, _D], None),
+                "orc_qmul": ([_D, _D, _D], None),
+                "orc_cubic_ops": ([_D], None),
+                "orc_disorientation": ([_D, _D], C.c_double),
+                "orc_disorientation_many": ([_D, _D, C.c_int, _D], None),
+                "orc_logpolar": ([_D, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _D], None),
+                "orc_eta_xcf": ([_D, _D, C.c_int, C.c_int, _D, _D], C.c_double),
+                "orc_refine_one": ([_F, C.c_int, _D, C.c_double, C.c_double, C.POINTER(Opts), _F,
+                                    C.c_int, _D, C.c_int, C.c_double, _D, _D, _I, _D], C.c_int),
+                "orc_refine_many": ([_F, C.c_int, _D, C.c_double, C.c_double, C.POINTER(Opts), _F,
+                                     C.c_int, C.c_int, _D, C.c_int, C.c_double, _D, _D, _I], None),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = lib
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_D)
+
+
+def _f(a):
+    return a.ctypes.data_as(_F)
+
+
+def _i(a):
+    return a.ctypes.data_as(_I)
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def num_threads() -> int:
+    return _lib_handle().orc_num_threads()
+
+
+# ---------------------------------------------------------------- transforms
+def dft1(x, sign=-1):
+    x = _c128(x)
+    out = np.empty_like(x)
+    _lib_handle().orc_dft1(_d(x), _d(out), x.shape[0], sign)
+    return out
+
+
+def dft2_brute(x, sign=-1):
+    x = _c128(x)
+    out = np.empty_like(x)
+    _lib_handle().orc_dft2_brute(_d(x), _d(out), x.shape[0], sign)
+    return out
+
+
+def fft1(x, sign=-1):
+    x = _c128(x).copy()
+    _lib_handle().orc_fft1(_d(x), x.shape[0], sign)
+    return x
+
+
+def fft2(x, sign=-1):
+    x = _c128(x).copy()
+    _lib_handle().orc_fft2(_d(x), x.shape[0], sign)
+    return x
+
+
+# ------------------------------------------------------------ pre-processing
+def crop(W, H, pc, cap=256):
+    """Centred 2^k crop: returns (n, off_x, off_y, pc_cropped)."""
+    n, ox, oy = C.c_int32(), C.c_int32(), C.c_int32()
+    out = np.zeros(3)
+    rc = _lib_handle().orc_crop(W, H, cap, pc[0], pc[1], pc[2], C.byref(n), C.byref(ox),
+                                C.byref(oy), _d(out))
+    if rc != 0:
+        raise ValueError("detector too small")
+    return n.value, ox.value, oy.value, out
+
+
+def bandpass(u, v, n, sigma_hp, sigma_lp):
+    return _lib_handle().orc_bandpass(u, v, n, sigma_hp, sigma_lp)
+
+
+def window(k, n, kind=1):
+    return _lib_handle().orc_window(k, n, kind)
+
+
+def prep(img, opts=None):
+    """One n x n image -> (full spectrum S [n, n] complex, spatial y [n, n], degenerate)."""
+    img = _f64(img)
+    n = img.shape[0]
+    opts = opts or default_opts(n)
+    S = np.empty((n, n), np.complex128)
+    y = np.empty((n, n))
+    deg = _lib_handle().orc_prep(_d(img), n, C.byref(opts), _d(S), _d(y))
+    return S, y, bool(deg)
+
+
+def prep_many(imgs, opts=None, want_spatial=False):
+    imgs = _f64(imgs)
+    P, n = imgs.shape[0], imgs.shape[1]
+    opts = opts or default_opts(n)
+    S = np.empty((P, n, n), np.complex128)
+    y = np.empty((P, n, n)) if want_spatial else None
+    deg = np.zeros(P, np.int32)
+    _lib_handle().orc_prep_many(_d(imgs), P, n, C.byref(opts), _d(S),
+                                _d(y) if y is not None else None, _i(deg))
+    return S, y, deg
+
+
+# --------------------------------------------------------------- correlation
+def xcf_surface(St, Sp):
+    St, Sp = _c128(St), _c128(Sp)
+    n = St.shape[0]
+    r = np.empty((n, n))
+    _lib_handle().orc_xcf_surface(_d(St), _d(Sp), n, _d(r))
+    return r
+
+
+def xcf_spatial(a, b):
+    a, b = _f64(a), _f64(b)
+    n = a.shape[0]
+    r = np.empty((n, n))
+    _lib_handle().orc_xcf_spatial(_d(a), _d(b), n, _d(r))
+    return r
+
+
+def parabola(cm, c0, cp):
+    return _lib_handle().orc_parabola(cm, c0, cp)
+
+
+def peak(r):
+    """-> (peak, (sy, sx), (dx, dy))"""
+    r = _f64(r)
+    n = r.shape[0]
+    pk = C.c_double()
+    sy, sx = C.c_int32(), C.c_int32()
+    dx, dy = C.c_double(), C.c_double()
+    _lib_handle().orc_peak(_d(r), n, C.byref(pk), C.byref(sy), C.byref(sx), C.byref(dx),
+                           C.byref(dy))
+    return pk.value, (sy.value, sx.value), (dx.value, dy.value)
+
+
+def index(St, Sp, degenerate=None, want_all=False):
+    """Library search. St [T,n,n], Sp [P,n,n] full spectra.
+    -> best [P] int32, peak [P], shift [P,2] (dx, dy), peaks_all [P,T] or None."""
+    St, Sp = _c128(St), _c128(Sp)
+    T, n = St.shape[0], St.shape[1]
+    P = Sp.shape[0]
+    deg = np.zeros(P, np.int32) if degenerate is None else np.ascontiguousarray(degenerate, np.int32)
+    best = np.empty(P, np.int32)
+    pk = np.empty(P)
+    sh = np.empty((P, 2))
+    allp = np.empty((P, T)) if want_all else None
+    _lib_handle().orc_index(_d(St), T, _d(Sp), P, n, _i(deg), _i(best), _d(pk), _d(sh),
+                            _d(allp) if allp is not None else None)
+    return best, pk, sh, allp
+
+
+# ---------------------------------------------------------------- projection
+def lambert_forward(v):
+    v = _f64(v)
+    X, Y = C.c_double(), C.c_double()
+    _lib_handle().orc_lambert_forward(_d(v), C.byref(X), C.byref(Y))
+    return X.value, Y.value
+
+
+def lambert_inverse(X, Y):
+    v = np.empty(3)
+    _lib_handle().orc_lambert_inverse(X, Y, _d(v))
+    return v
+
+
+def master_lookup(master, v):
+    master, v = _f32(master), _f64(v)
+    return _lib_handle().orc_master_lookup(_f(master), master.shape[1], _d(v))
+
+
+def quat_to_matrix(q):
+    q = _f64(q)
+    R = np.empty(9)
+    _lib_handle().orc_quat_to_matrix(_d(q), _d(R))
+    return R.reshape(3, 3)
+
+
+def project(master, q, pc, n, sample_tilt=70.0, detector_tilt=0.0):
+    master, q, pc = _f32(master), _f64(q), _f64(pc)
+    out = np.empty((n, n))
+    _lib_handle().orc_project(_f(master), master.shape[1], _d(q), _d(pc), sample_tilt,
+                              detector_tilt, n, _d(out))
+    return out
+
+
+def project_many(master, quats, pcs, n, sample_tilt=70.0, detector_tilt=0.0):
+    master, quats = _f32(master), _f64(quats)
+    pcs = _f64(np.broadcast_to(np.asarray(pcs, np.float64), (quats.shape[0], 3)))
+    P = quats.shape[0]
+    out = np.empty((P, n, n))
+    _lib_handle().orc_project_many(_f(master), master.shape[1], _d(quats), _d(pcs), P,
+                                   sample_tilt, detector_tilt, n, _d(out))
+    return out
+
+
+# ---------------------------------------------------------------- symmetry
+def qmul(a, b):
+    a, b = _f64(a), _f64(b)
+    o = np.empty(4)
+    _lib_handle().orc_qmul(_d(a), _d(b), _d(o))
+    return o
+
+
+def cubic_ops():
+    o = np.empty((24, 4))
+    _lib_handle().orc_cubic_ops(_d(o))
+    return o
+
+
+def disorientation(qa, qb):
+    """Cubic disorientation in degrees; qa, qb [4] or [n, 4]."""
+    qa, qb = _f64(qa), _f64(qb)
+    if qa.ndim == 1:
+        return _lib_handle().orc_disorientation(_d(qa), _d(qb))
+    out = np.empty(qa.shape[0])
+    _lib_handle().orc_disorientation_many(_d(qa), _d(qb), qa.shape[0], _d(out))
+    return out
+
+
+# ---------------------------------------------------------------- refinement
+def logpolar(img, opts=None):
+    img = _f64(img)
+    n = img.shape[0]
+    o = opts or default_opts(n)
+    out = np.empty((o.lp_nr, o.lp_neta))
+    _lib_handle().orc_logpolar(_d(img), n, o.lp_nr, o.lp_neta, o.lp_rmin, o.lp_rmax, _d(out))
+    return out
+
+
+def eta_xcf(a, b):
+    """-> (shift along eta in samples, peak, c [neta])"""
+    a, b = _f64(a), _f64(b)
+    nr, ne = a.shape
+    pk = C.c_double()
+    c = np.empty(ne)
+    sh = _lib_handle().orc_eta_xcf(_d(a), _d(b), nr, ne, C.byref(pk), _d(c))
+    return sh, pk.value, c
+
+
+def refine_one(master, pattern, seed, pc, max_it=2, tol_deg=1e-3, opts=None,
+               sample_tilt=70.0, detector_tilt=0.0):
+    """-> (q [4], peak, iters, trace [iters, 4] = (dx, dy, deta, update_deg))"""
+    master, pattern = _f32(master), _f32(pattern)
+    n = pattern.shape[0]
+    o = opts or default_opts(n)
+    seed, pc = _f64(seed), _f64(pc)
+    q = np.empty(4)
+    pk = C.c_double()
+    it = C.c_int32()
+    trace = np.zeros((max(max_it, 1), 4))
+    _lib_handle().orc_refine_one(_f(master), master.shape[1], _d(pc), sample_tilt, detector_tilt,
+                                 C.byref(o), _f(pattern), n, _d(seed), max_it, tol_deg, _d(q),
+                                 C.byref(pk), C.byref(it), _d(trace))
+    return q, pk.value, it.value, trace[:it.value]
+
+
+def refine_many(master, patterns, seeds, pcs, max_it=2, tol_deg=1e-3, opts=None,
+                sample_tilt=70.0, detector_tilt=0.0):
+    """-> (quats [P,4], peaks [P], iters [P])"""
+    master, patterns = _f32(master), _f32(patterns)
+    P, n = patterns.shape[0], patterns.shape[1]
+    o = opts or default_opts(n)
+    seeds = _f64(seeds)
+    pcs = _f64(np.broadcast_to(np.asarray(pcs, np.float64), (P, 3)))
+    q = np.empty((P, 4))
+    pk = np.empty(P)
+    it = np.empty(P, np.int32)
+    _lib_handle().orc_refine_many(_f(master), master.shape[1], _d(pcs), sample_tilt,
+                                  detector_tilt, C.byref(o), _f(patterns), P, n, _d(seeds),
+                                  max_it, tol_deg, _d(q), _d(pk), _i(it))
+    return q, pk, it

@@ -1,0 +1,687 @@
+/*
+ * FP64 CPU oracle for the refined template-matching EBSD indexer
+ * (Foden, Collins, Wilkinson & Britton, arXiv 1807.11313).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * statement of what the CUDA path computes.  It is used by the tests, by
+ * __graft_entry__.smoke() and by the CPU-baseline leg of bench.py, and by
+ * nothing else.  It shares no code, header, table or constant with the CUDA
+ * library: it has its own DFT/FFT, its own Lambert map, its own projector.
+ *
+ * Every function cites the passage of the paper it follows.  Where the paper
+ * is silent or garbled the reading taken is stated in the comment.
+ * Parity unpinned: the window shape, the band-pass shape and its cut-offs, the
+ * log-polar sampling constants and the refinement's sign conventions are not
+ * fixed by the paper (it gives no values); they are pinned only against the
+ * paper's qualitative statements and internal invariants.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+#define ORC_PI 3.14159265358979323846264338327950288
+
+/* ---------------------------------------------------------------------- */
+/* options and geometry                                                    */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t window;      /* 0 = none, 1 = periodic Hann (separable)           */
+    double sigma_hp;     /* Gaussian high-pass sigma, cycles per image         */
+    double sigma_lp;     /* Gaussian low-pass sigma, cycles per image          */
+    int32_t lp_nr;       /* log-polar radial samples                           */
+    int32_t lp_neta;     /* log-polar angular samples                          */
+    double lp_rmin;      /* smallest radius, pixels                            */
+    double lp_rmax;      /* largest radius, pixels                             */
+} orc_opts;
+
+typedef struct {
+    int32_t width, height;       /* detector pixels                            */
+    double pcx, pcy, pcz;        /* Bruker-style pattern centre                */
+    double sample_tilt_deg;      /* sample tilt (70 deg in the paper)          */
+    double detector_tilt_deg;
+} orc_geom;
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ---------------------------------------------------------------------- */
+/* Fourier transforms (Eq. 4)                                              */
+/* ---------------------------------------------------------------------- */
+
+/* Direct O(n^2) 1-D DFT: out[k] = sum_x in[x] exp(sign 2 pi i k x / n).
+ * Unscaled.  The reference the FFT below is pinned against. */
+void orc_dft1(const cplx *in, cplx *out, int n, int sign) {
+    for (int k = 0; k < n; ++k) {
+        cplx s = 0;
+        for (int x = 0; x < n; ++x) {
+            double a = sign * 2.0 * ORC_PI * (double)(((long)k * x) % n) / n;
+            s += in[x] * (cos(a) + I * sin(a));
+        }
+        out[k] = s;
+    }
+}
+
+/* Direct O(n^4) 2-D DFT of an n x n array (row-major), unscaled. */
+void orc_dft2_brute(const cplx *in, cplx *out, int n, int sign) {
+    for (int u = 0; u < n; ++u)
+        for (int v = 0; v < n; ++v) {
+            cplx s = 0;
+            for (int x = 0; x < n; ++x)
+                for (int y = 0; y < n; ++y) {
+                    long p = ((long)u * x + (long)v * y) % n;
+                    double a = sign * 2.0 * ORC_PI * (double)p / n;
+                    s += in[x * n + y] * (cos(a) + I * sin(a));
+                }
+            out[u * n + v] = s;
+        }
+}
+
+/* In-place iterative radix-2 Cooley-Tukey FFT of length n (a power of two),
+ * stride `st` between elements.  Unscaled; sign -1 forward, +1 inverse. */
+static void fft1_strided(cplx *x, int n, int st, int sign) {
+    /* bit-reversal permutation */
+    for (int i = 1, j = 0; i < n; ++i) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            cplx t = x[i * st];
+            x[i * st] = x[j * st];
+            x[j * st] = t;
+        }
+    }
+    for (int len = 2; len <= n; len <<= 1) {
+        for (int i = 0; i < n; i += len) {
+            for (int k = 0; k < len / 2; ++k) {
+                double a = sign * 2.0 * ORC_PI * k / len;
+                cplx w = cos(a) + I * sin(a);
+                cplx u = x[(i + k) * st];
+                cplx v = x[(i + k + len / 2) * st] * w;
+                x[(i + k) * st] = u + v;
+                x[(i + k + len / 2) * st] = u - v;
+            }
+        }
+    }
+}
+
+void orc_fft1(cplx *x, int n, int sign) { fft1_strided(x, n, 1, sign); }
+
+/* 2-D FFT of an n x n row-major array: rows, then columns.  Unscaled. */
+void orc_fft2(cplx *x, int n, int sign) {
+    for (int r = 0; r < n; ++r) fft1_strided(x + (long)r * n, n, 1, sign);
+    for (int c = 0; c < n; ++c) fft1_strided(x + c, n, n, sign);
+}
+
+/* ---------------------------------------------------------------------- */
+/* pre-processing (Eq. 4 and the filtering / windowing of the FFT method)  */
+/* ---------------------------------------------------------------------- */
+
+/* Centred crop of a W x H detector to the largest 2^k square side (<= cap):
+ * the paper crops to a 2^n x 2^n field of view and updates the PC so that it
+ * keeps pointing at the same pixel (footnotes 1-2 of the FFT section; the
+ * worked example 200 -> 128 px moves PCx 0.4 -> 0.34).  Outputs the square
+ * side n, the crop offsets and the updated PC.  Returns 0, or -1 if the side
+ * would be below 16. */
+int orc_crop(int W, int H, int cap, double pcx, double pcy, double pcz,
+             int *n_out, int *off_x, int *off_y, double pc_out[3]) {
+    int m = W < H ? W : H;
+    int n = 1;
+    while (n * 2 <= m && n * 2 <= cap) n *= 2;
+    if (n < 16) return -1;
+    int ox = (W - n) / 2, oy = (H - n) / 2;
+    *n_out = n; *off_x = ox; *off_y = oy;
+    pc_out[0] = (pcx * W - ox) / n;
+    pc_out[1] = (pcy * H - oy) / n;
+    pc_out[2] = pcz * W / n;      /* detector distance in pixels is unchanged */
+    return 0;
+}
+
+/* Band-pass filter H(u,v) at integer frequency (u, v) of an n x n transform:
+ * the paper uses a high-pass (background) and a low-pass (noise) filter in
+ * Fourier space without giving their form; reading: Gaussian high-pass times
+ * Gaussian low-pass on the radial signed frequency rho. */
+double orc_bandpass(int u, int v, int n, double sigma_hp, double sigma_lp) {
+    double fu = (u < n / 2) ? u : u - n;
+    double fv = (v < n / 2) ? v : v - n;
+    double rho2 = fu * fu + fv * fv;
+    double hp = 1.0 - exp(-rho2 / (2.0 * sigma_hp * sigma_hp));
+    double lp = exp(-rho2 / (2.0 * sigma_lp * sigma_lp));
+    return hp * lp;
+}
+
+/* Window: the paper manages wrap-around artefacts with a window of unstated
+ * type; reading: separable periodic Hann, w(k) = (1 - cos(2 pi k / n)) / 2. */
+double orc_window(int k, int n, int kind) {
+    if (kind == 0) return 1.0;
+    return 0.5 * (1.0 - cos(2.0 * ORC_PI * k / n));
+}
+
+/* Pre-process one n x n image (already cropped):
+ *   1. contrast normalisation to zero mean, unit standard deviation (the
+ *      paper's simulations fix mean 0 and std 1 for both templates and
+ *      experimental patterns);
+ *   2. windowing;
+ *   3. unitary 2-D DFT (Eq. 4);
+ *   4. band-pass filter;
+ *   5. division by the norm of the filtered spectrum, so that the
+ *      correlation at zero shift of an image with itself is 1 and correlation
+ *      coefficients are comparable across templates (normalisation by the
+ *      autocorrelations of F and G, FFT section).
+ * S receives the full n x n spectrum; if y is non-NULL it receives the
+ * filtered spatial image y = unitary inverse DFT of S (real part), which has
+ * unit L2 norm.  Returns 0, or 1 if the image is degenerate (zero variance or
+ * zero filtered energy), in which case S (and y) are zero. */
+int orc_prep(const double *img, int n, const orc_opts *o, cplx *S, double *y) {
+    long nn = (long)n * n;
+    double mean = 0.0;
+    for (long i = 0; i < nn; ++i) mean += img[i];
+    mean /= nn;
+    double var = 0.0;
+    for (long i = 0; i < nn; ++i) var += (img[i] - mean) * (img[i] - mean);
+    var /= nn;
+    double sd = sqrt(var);
+    if (!(sd > 1e-12 * (1.0 + fabs(mean)))) {
+        memset(S, 0, sizeof(cplx) * nn);
+        if (y) memset(y, 0, sizeof(double) * nn);
+        return 1;
+    }
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c)
+            S[(long)r * n + c] = (img[(long)r * n + c] - mean) / sd *
+                                 orc_window(r, n, o->window) * orc_window(c, n, o->window);
+    orc_fft2(S, n, -1);
+    double energy = 0.0;
+    for (int u = 0; u < n; ++u)
+        for (int v = 0; v < n; ++v) {
+            long k = (long)u * n + v;
+            S[k] = S[k] / n * orc_bandpass(u, v, n, o->sigma_hp, o->sigma_lp);
+            energy += creal(S[k]) * creal(S[k]) + cimag(S[k]) * cimag(S[k]);
+        }
+    if (!(energy > 0.0)) {
+        memset(S, 0, sizeof(cplx) * nn);
+        if (y) memset(y, 0, sizeof(double) * nn);
+        return 1;
+    }
+    double inv = 1.0 / sqrt(energy);
+    for (long k = 0; k < nn; ++k) S[k] *= inv;
+    if (y) {
+        cplx *tmp = malloc(sizeof(cplx) * nn);
+        memcpy(tmp, S, sizeof(cplx) * nn);
+        orc_fft2(tmp, n, +1);
+        for (long k = 0; k < nn; ++k) y[k] = creal(tmp[k]) / n;
+        free(tmp);
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* cross-correlation (Eqs. 2, 3, 6)                                        */
+/* ---------------------------------------------------------------------- */
+
+/* Correlation surface r(s) = sum_k conj(St[k]) Sp[k] exp(+2 pi i k.s / n)
+ * (Eq. 6 with the conjugate on the template; Eq. 3 omits it).  With unit-norm
+ * spectra this is the normalised correlation coefficient, r(s) in [-1, 1];
+ * r is maximal at s = d when the pattern is the template translated by +d. */
+void orc_xcf_surface(const cplx *St, const cplx *Sp, int n, double *r) {
+    long nn = (long)n * n;
+    cplx *X = malloc(sizeof(cplx) * nn);
+    for (long k = 0; k < nn; ++k) X[k] = conj(St[k]) * Sp[k];
+    orc_fft2(X, n, +1);
+    for (long k = 0; k < nn; ++k) r[k] = creal(X[k]);
+    free(X);
+}
+
+/* Brute-force circular spatial cross-correlation (Eq. 2 with indices taken
+ * modulo n): r(m, l) = sum_{i,j} a[i, j] b[i + m, j + l]. */
+void orc_xcf_spatial(const double *a, const double *b, int n, double *r) {
+    for (int m = 0; m < n; ++m)
+        for (int l = 0; l < n; ++l) {
+            double s = 0.0;
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j)
+                    s += a[i * n + j] * b[((i + m) % n) * n + (j + l) % n];
+            r[m * n + l] = s;
+        }
+}
+
+/* 3-point parabolic vertex offset, clamped to [-0.5, 0.5]; 0 if not a maximum.
+ * The paper up-samples the peak for a sub-pixel shift without giving the
+ * method; reading: a parabola through the peak and its two neighbours. */
+double orc_parabola(double cm, double c0, double cp) {
+    double den = cm - 2.0 * c0 + cp;
+    if (!(den < 0.0)) return 0.0;
+    double d = (cm - cp) / (2.0 * den);
+    if (d > 0.5) d = 0.5;
+    if (d < -0.5) d = -0.5;
+    return d;
+}
+
+/* Peak of a correlation surface: integer argmax (ties -> lowest row-major
+ * index), value, and sub-pixel shift (dx, dy) = wrapped integer shift plus the
+ * parabolic offsets along columns and rows, wrapped into [-n/2, n/2). */
+void orc_peak(const double *r, int n, double *peak, int *sy, int *sx,
+              double *dx, double *dy) {
+    long nn = (long)n * n, best = 0;
+    for (long k = 1; k < nn; ++k)
+        if (r[k] > r[best]) best = k;
+    int y0 = (int)(best / n), x0 = (int)(best % n);
+    double c0 = r[best];
+    double cxm = r[(long)y0 * n + (x0 + n - 1) % n], cxp = r[(long)y0 * n + (x0 + 1) % n];
+    double cym = r[(long)((y0 + n - 1) % n) * n + x0], cyp = r[(long)((y0 + 1) % n) * n + x0];
+    *peak = c0;
+    *sy = y0;
+    *sx = x0;
+    *dx = (x0 < n / 2 ? x0 : x0 - n) + orc_parabola(cxm, c0, cxp);
+    *dy = (y0 < n / 2 ? y0 : y0 - n) + orc_parabola(cym, c0, cyp);
+}
+
+/* Library search (Fig. 1 A-C): for each pattern, the template whose
+ * correlation surface has the highest peak (ties -> lowest template index),
+ * that peak, and the sub-pixel shift at it.  St: [T, n, n] full spectra,
+ * Sp: [P, n, n].  degenerate[p] != 0 marks a pattern with no signal: best = -1,
+ * peak = 0, shift = 0.  peaks_all (nullable) receives the [P, T] matrix of
+ * per-template peaks.  Patterns run in parallel (one thread per pattern),
+ * each exactly as written above. */
+void orc_index(const cplx *St, int T, const cplx *Sp, int P, int n,
+               const int32_t *degenerate, int32_t *best, double *peak,
+               double *shift, double *peaks_all) {
+    long nn = (long)n * n;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int p = 0; p < P; ++p) {
+        double *r = malloc(sizeof(double) * nn);
+        if (degenerate && degenerate[p]) {
+            best[p] = -1; peak[p] = 0.0; shift[2 * p] = shift[2 * p + 1] = 0.0;
+            if (peaks_all) for (int t = 0; t < T; ++t) peaks_all[(long)p * T + t] = 0.0;
+            free(r);
+            continue;
+        }
+        int bt = -1;
+        double bv = 0.0;
+        for (int t = 0; t < T; ++t) {
+            orc_xcf_surface(St + (long)t * nn, Sp + (long)p * nn, n, r);
+            double m = r[0];
+            for (long k = 1; k < nn; ++k) if (r[k] > m) m = r[k];
+            if (peaks_all) peaks_all[(long)p * T + t] = m;
+            if (bt < 0 || m > bv) { bv = m; bt = t; }
+        }
+        orc_xcf_surface(St + (long)bt * nn, Sp + (long)p * nn, n, r);
+        int sy, sx;
+        orc_peak(r, n, &peak[p], &sy, &sx, &shift[2 * p], &shift[2 * p + 1]);
+        best[p] = bt;
+        free(r);
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* master pattern lookup and gnomonic projection (SO(3) Library Generation) */
+/* ---------------------------------------------------------------------- */
+
+/* Rosca (2010) equal-area map of the northern hemisphere onto the square
+ * [-sqrt(pi/2), sqrt(pi/2)]^2; the southern hemisphere uses (x, y, -z). */
+void orc_lambert_forward(const double v[3], double *X, double *Y) {
+    double x = v[0], y = v[1], z = fabs(v[2]);
+    double q = sqrt(2.0 * (1.0 - z));
+    double sp = sqrt(ORC_PI) / 2.0, ts = 2.0 / sqrt(ORC_PI);
+    if (x == 0.0 && y == 0.0) { *X = 0.0; *Y = 0.0; return; }
+    if (fabs(y) <= fabs(x)) {
+        double s = x >= 0 ? 1.0 : -1.0;
+        *X = s * q * sp;
+        *Y = s * q * ts * atan(y / x);
+    } else {
+        double s = y >= 0 ? 1.0 : -1.0;
+        *X = s * q * ts * atan(x / y);
+        *Y = s * q * sp;
+    }
+}
+
+/* Inverse of the above (northern hemisphere). */
+void orc_lambert_inverse(double X, double Y, double v[3]) {
+    if (X == 0.0 && Y == 0.0) { v[0] = 0; v[1] = 0; v[2] = 1; return; }
+    if (fabs(Y) <= fabs(X)) {
+        double f = (2.0 * X / ORC_PI) * sqrt(ORC_PI - X * X);
+        double a = ORC_PI * Y / (4.0 * X);
+        v[0] = f * cos(a); v[1] = f * sin(a); v[2] = 1.0 - 2.0 * X * X / ORC_PI;
+    } else {
+        double f = (2.0 * Y / ORC_PI) * sqrt(ORC_PI - Y * Y);
+        double a = ORC_PI * X / (4.0 * Y);
+        v[0] = f * sin(a); v[1] = f * cos(a); v[2] = 1.0 - 2.0 * Y * Y / ORC_PI;
+    }
+}
+
+/* Master intensity in direction v (unit): Lambert square coordinates, then
+ * bilinear interpolation between the four nearest cell centres of the
+ * hemisphere's M x M grid (cell (a, b) centred at X = L(2(b+.5)/M - 1),
+ * Y = L(2(a+.5)/M - 1)), clamped at the square's edge.  master: [2, M, M]. */
+double orc_master_lookup(const float *master, int M, const double v[3]) {
+    double X, Y;
+    orc_lambert_forward(v, &X, &Y);
+    double L = sqrt(ORC_PI / 2.0);
+    double fx = (X / L + 1.0) * M / 2.0 - 0.5;
+    double fy = (Y / L + 1.0) * M / 2.0 - 0.5;
+    if (fx < 0) fx = 0;
+    if (fx > M - 1) fx = M - 1;
+    if (fy < 0) fy = 0;
+    if (fy > M - 1) fy = M - 1;
+    int i0 = (int)floor(fx), j0 = (int)floor(fy);
+    if (i0 > M - 2) i0 = M - 2;
+    if (j0 > M - 2) j0 = M - 2;
+    double tx = fx - i0, ty = fy - j0;
+    const float *g = master + (v[2] >= 0.0 ? 0 : (long)M * M);
+    double a = g[(long)j0 * M + i0], b = g[(long)j0 * M + i0 + 1];
+    double c = g[(long)(j0 + 1) * M + i0], d = g[(long)(j0 + 1) * M + i0 + 1];
+    return (1 - ty) * ((1 - tx) * a + tx * b) + ty * ((1 - tx) * c + tx * d);
+}
+
+/* Rotation matrix of unit quaternion (w, x, y, z), row-major. */
+void orc_quat_to_matrix(const double q[4], double R[9]) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* Gnomonic projection of the master pattern onto an n x n detector for
+ * orientation q (reprojection of the master pattern, SO(3) Library Generation
+ * section).  Pixel (i, j) (row from the top, column from the left, centres at
+ * +0.5) looks along d = (j + .5 - pcx n, pcy n - (i + .5), pcz n) in the
+ * detector frame (x right, y up); the sample frame is reached by a rotation
+ * about x by 90 - sample_tilt + detector_tilt degrees, and the crystal frame
+ * by R(q).  The paper interpolates bicubically on a stereographic master;
+ * reading: bilinear on the equal-area master grid.  pc is the (cropped)
+ * pattern centre. */
+void orc_project(const float *master, int M, const double q[4], const double pc[3],
+                 double sample_tilt_deg, double detector_tilt_deg, int n, double *out) {
+    double R[9];
+    orc_quat_to_matrix(q, R);
+    double al = (90.0 - sample_tilt_deg + detector_tilt_deg) * ORC_PI / 180.0;
+    double ca = cos(al), sa = sin(al);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double dx = (j + 0.5) - pc[0] * n;
+            double dy = pc[1] * n - (i + 0.5);
+            double dz = pc[2] * n;
+            double nrm = sqrt(dx * dx + dy * dy + dz * dz);
+            dx /= nrm; dy /= nrm; dz /= nrm;
+            double s[3] = {dx, ca * dy - sa * dz, sa * dy + ca * dz};
+            double c[3] = {R[0] * s[0] + R[1] * s[1] + R[2] * s[2],
+                           R[3] * s[0] + R[4] * s[1] + R[5] * s[2],
+                           R[6] * s[0] + R[7] * s[1] + R[8] * s[2]};
+            out[(long)i * n + j] = orc_master_lookup(master, M, c);
+        }
+}
+
+/* Many projections, one thread per image. quats [P,4], pcs [P,3]. */
+void orc_project_many(const float *master, int M, const double *quats, const double *pcs,
+                      int P, double sample_tilt_deg, double detector_tilt_deg, int n,
+                      double *out) {
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int p = 0; p < P; ++p)
+        orc_project(master, M, quats + 4L * p, pcs + 3L * p, sample_tilt_deg,
+                    detector_tilt_deg, n, out + (long)p * n * n);
+}
+
+/* Many pre-processings, one thread per image. imgs [P, n, n]. */
+void orc_prep_many(const double *imgs, int P, int n, const orc_opts *o, cplx *S,
+                   double *y, int32_t *degenerate) {
+    long nn = (long)n * n;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int p = 0; p < P; ++p)
+        degenerate[p] = orc_prep(imgs + p * nn, n, o, S + p * nn, y ? y + p * nn : NULL);
+}
+
+/* ---------------------------------------------------------------------- */
+/* quaternions, symmetry, disorientation (second "Equation 6")             */
+/* ---------------------------------------------------------------------- */
+static void qmul(const double a[4], const double b[4], double o[4]) {
+    double r[4];
+    r[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    r[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    r[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    r[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+    memcpy(o, r, sizeof r);
+}
+
+static void qnormalise(double q[4]) {
+    double s = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    if (q[0] < 0) s = -s;
+    for (int i = 0; i < 4; ++i) q[i] /= s;
+}
+
+void orc_qmul(const double a[4], const double b[4], double o[4]) { qmul(a, b, o); }
+
+/* The 24 proper rotations of the cubic point group 432 as quaternions. */
+void orc_cubic_ops(double ops[24][4]) {
+    const double h = 0.5, r = sqrt(0.5);
+    int k = 0;
+    double id[4] = {1, 0, 0, 0};
+    memcpy(ops[k++], id, sizeof id);
+    for (int ax = 1; ax <= 3; ++ax) {          /* 180 deg about x, y, z */
+        double q[4] = {0, 0, 0, 0}; q[ax] = 1; memcpy(ops[k++], q, sizeof q);
+    }
+    for (int ax = 1; ax <= 3; ++ax)            /* +-90 deg about x, y, z */
+        for (int s = -1; s <= 1; s += 2) {
+            double q[4] = {r, 0, 0, 0}; q[ax] = s * r; memcpy(ops[k++], q, sizeof q);
+        }
+    for (int sx = -1; sx <= 1; sx += 2)        /* +-120 deg about <111> */
+        for (int sy = -1; sy <= 1; sy += 2)
+            for (int sz = -1; sz <= 1; sz += 2) {
+                double q[4] = {h, sx * h, sy * h, sz * h}; memcpy(ops[k++], q, sizeof q);
+            }
+    const int pairs[3][2] = {{1, 2}, {1, 3}, {2, 3}};  /* 180 deg about <110> */
+    for (int p = 0; p < 3; ++p)
+        for (int s = -1; s <= 1; s += 2) {
+            double q[4] = {0, 0, 0, 0};
+            q[pairs[p][0]] = r; q[pairs[p][1]] = s * r;
+            memcpy(ops[k++], q, sizeof q);
+        }
+}
+
+/* Disorientation angle (degrees) between orientations qa and qb of a cubic
+ * crystal: the smallest rotation angle of S (qa qb^-1) over the 24 operators
+ * S (the paper's minimum over pairs of symmetry operators reduces to one
+ * operator because the angle is invariant under conjugation). */
+double orc_disorientation(const double qa[4], const double qb[4]) {
+    double ops[24][4];
+    orc_cubic_ops(ops);
+    double binv[4] = {qb[0], -qb[1], -qb[2], -qb[3]};
+    double m[4];
+    qmul(qa, binv, m);
+    double best = 0.0;
+    for (int i = 0; i < 24; ++i) {
+        double t[4];
+        qmul(ops[i], m, t);
+        double w = fabs(t[0]) / sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + t[3] * t[3]);
+        if (w > best) best = w;
+    }
+    if (best > 1.0) best = 1.0;
+    return 2.0 * acos(best) * 180.0 / ORC_PI;
+}
+
+void orc_disorientation_many(const double *qa, const double *qb, int n, double *out) {
+    for (int i = 0; i < n; ++i) out[i] = orc_disorientation(qa + 4L * i, qb + 4L * i);
+}
+
+/* ---------------------------------------------------------------------- */
+/* refinement (Orientation and Pattern Centre Refinement; Eq. 7, Fig. 6)   */
+/* ---------------------------------------------------------------------- */
+
+/* Log-polar resampling of an n x n image about the screen centre
+ * c = (n/2 - 0.5, n/2 - 0.5): radii r_m = rmin (rmax/rmin)^(m/(nr-1)),
+ * angles eta_l = 2 pi l / neta counter-clockwise from +x (y up), sample at
+ * column c + r cos(eta), row c - r sin(eta), bilinear.  The paper centres the
+ * transform at the screen centre; the sampling constants are a reading. */
+void orc_logpolar(const double *img, int n, int nr, int neta, double rmin, double rmax,
+                  double *out) {
+    double c = n / 2.0 - 0.5;
+    for (int m = 0; m < nr; ++m) {
+        double r = rmin * pow(rmax / rmin, nr > 1 ? (double)m / (nr - 1) : 0.0);
+        for (int l = 0; l < neta; ++l) {
+            double eta = 2.0 * ORC_PI * l / neta;
+            double fx = c + r * cos(eta), fy = c - r * sin(eta);
+            int x0 = (int)floor(fx), y0 = (int)floor(fy);
+            if (x0 < 0) x0 = 0;
+            if (y0 < 0) y0 = 0;
+            if (x0 > n - 2) x0 = n - 2;
+            if (y0 > n - 2) y0 = n - 2;
+            double tx = fx - x0, ty = fy - y0;
+            double a = img[(long)y0 * n + x0], b = img[(long)y0 * n + x0 + 1];
+            double cc = img[(long)(y0 + 1) * n + x0], d = img[(long)(y0 + 1) * n + x0 + 1];
+            out[(long)m * neta + l] = (1 - ty) * ((1 - tx) * a + tx * b) + ty * ((1 - tx) * cc + tx * d);
+        }
+    }
+}
+
+/* Correlation along eta of two log-polar images (rotation about the screen
+ * centre becomes a shift along eta): both are made zero-mean, then
+ * c(D) = sum_m sum_l a[m][l] b[m][(l + D) mod neta] / (|a| |b|), computed by
+ * its definition.  Returns the shift D (argmax, ties -> lowest, wrapped into
+ * [-neta/2, neta/2), plus the parabolic offset) and the peak value.  b equal
+ * to a rotated counter-clockwise by theta peaks at D = theta neta / 2 pi. */
+double orc_eta_xcf(const double *a_in, const double *b_in, int nr, int neta, double *peak,
+                   double *c_out) {
+    long tot = (long)nr * neta;
+    double *a = malloc(sizeof(double) * tot), *b = malloc(sizeof(double) * tot);
+    double *c = c_out ? c_out : malloc(sizeof(double) * neta);
+    double ma = 0, mb = 0;
+    for (long k = 0; k < tot; ++k) { ma += a_in[k]; mb += b_in[k]; }
+    ma /= tot; mb /= tot;
+    double na = 0, nb = 0;
+    for (long k = 0; k < tot; ++k) {
+        a[k] = a_in[k] - ma; b[k] = b_in[k] - mb;
+        na += a[k] * a[k]; nb += b[k] * b[k];
+    }
+    double nrm = sqrt(na * nb);
+    if (!(nrm > 0)) nrm = 1.0;
+    for (int D = 0; D < neta; ++D) {
+        double s = 0.0;
+        for (int m = 0; m < nr; ++m)
+            for (int l = 0; l < neta; ++l)
+                s += a[(long)m * neta + l] * b[(long)m * neta + (l + D) % neta];
+        c[D] = s / nrm;
+    }
+    int best = 0;
+    for (int D = 1; D < neta; ++D) if (c[D] > c[best]) best = D;
+    double off = orc_parabola(c[(best + neta - 1) % neta], c[best], c[(best + 1) % neta]);
+    *peak = c[best];
+    double sh = (best < neta / 2 ? best : best - neta) + off;
+    free(a); free(b);
+    if (!c_out) free(c);
+    return sh;
+}
+
+/* q_new = q (x) q_s (x) conj(qQ) (x) conj(q_s): the orientation whose template
+ * equals the template of q rotated by the detector-frame rotation Q (q_s is
+ * the detector -> sample rotation about x). */
+static void apply_detector_rotation(const double q[4], const double qQ[4], double al,
+                                    double out[4]) {
+    double qs[4] = {cos(al / 2), sin(al / 2), 0, 0};
+    double qsi[4] = {qs[0], -qs[1], 0, 0};
+    double qQi[4] = {qQ[0], -qQ[1], -qQ[2], -qQ[3]};
+    double t1[4], t2[4];
+    qmul(q, qs, t1);
+    qmul(t1, qQi, t2);
+    qmul(t2, qsi, out);
+    qnormalise(out);
+}
+
+/* Refine one pattern from a seed orientation (the refinement section):
+ * for each iteration
+ *   X/Y: project the template at the current orientation with the pattern's
+ *        PC, pre-process, cross-correlate with the pattern -> sub-pixel shift
+ *        (dx, dy); a rotation about the detector y (x) axis is a horizontal
+ *        (vertical) shift, theta = atan(shift / L), L = pcz n (Eq. 7, with
+ *        atan in place of the small-angle ratio); compose;
+ *   Z:   re-project at the updated orientation, pre-process, log-polar
+ *        transform the filtered spatial images of template and pattern about
+ *        the screen centre, correlate along eta -> rotation about the
+ *        detector z axis; compose;
+ * and stop when the total update of the iteration is below tol_deg or after
+ * max_it iterations (the paper finds about two iterations suffice).
+ * Returns 0; q_out receives the refined orientation, *peak_out the XCF peak of
+ * the last X/Y step, *iters_out the iterations performed, and (nullable)
+ * trace[it*4 + 0..3] = (dx, dy, deta, update_deg) of each iteration. */
+int orc_refine_one(const float *master, int M, const double pc[3], double sample_tilt_deg,
+                   double detector_tilt_deg, const orc_opts *o, const float *pattern, int n,
+                   const double q_seed[4], int max_it, double tol_deg, double q_out[4],
+                   double *peak_out, int32_t *iters_out, double *trace) {
+    long nn = (long)n * n;
+    double *img = malloc(sizeof(double) * nn), *yP = malloc(sizeof(double) * nn);
+    double *yT = malloc(sizeof(double) * nn), *r = malloc(sizeof(double) * nn);
+    cplx *SP = malloc(sizeof(cplx) * nn), *ST = malloc(sizeof(cplx) * nn);
+    int nr = o->lp_nr, ne = o->lp_neta;
+    double *lpP = malloc(sizeof(double) * nr * ne), *lpT = malloc(sizeof(double) * nr * ne);
+    for (long k = 0; k < nn; ++k) img[k] = pattern[k];
+    orc_prep(img, n, o, SP, yP);
+    orc_logpolar(yP, n, nr, ne, o->lp_rmin, o->lp_rmax, lpP);
+    double al = (90.0 - sample_tilt_deg + detector_tilt_deg) * ORC_PI / 180.0;
+    double L = pc[2] * n;
+    double q[4] = {q_seed[0], q_seed[1], q_seed[2], q_seed[3]};
+    qnormalise(q);
+    double peak = 0.0;
+    int it = 0;
+    while (it < max_it) {
+        /* X/Y step */
+        orc_project(master, M, q, pc, sample_tilt_deg, detector_tilt_deg, n, img);
+        orc_prep(img, n, o, ST, NULL);
+        orc_xcf_surface(ST, SP, n, r);
+        int sy, sx;
+        double dx, dy;
+        orc_peak(r, n, &peak, &sy, &sx, &dx, &dy);
+        double tx = atan(dy / L), ty = atan(dx / L);
+        double qx[4] = {cos(tx / 2), sin(tx / 2), 0, 0};
+        double qy[4] = {cos(ty / 2), 0, sin(ty / 2), 0};
+        double qQ[4], q1[4];
+        qmul(qx, qy, qQ);
+        apply_detector_rotation(q, qQ, al, q1);
+        /* Z step */
+        orc_project(master, M, q1, pc, sample_tilt_deg, detector_tilt_deg, n, img);
+        orc_prep(img, n, o, ST, yT);
+        orc_logpolar(yT, n, nr, ne, o->lp_rmin, o->lp_rmax, lpT);
+        double zpk;
+        double deta = orc_eta_xcf(lpT, lpP, nr, ne, &zpk, NULL);
+        double tz = 2.0 * ORC_PI * deta / ne;
+        double qz[4] = {cos(tz / 2), 0, 0, sin(tz / 2)};
+        double q2[4];
+        apply_detector_rotation(q1, qz, al, q2);
+        double dot = fabs(q2[0] * q[0] + q2[1] * q[1] + q2[2] * q[2] + q2[3] * q[3]);
+        if (dot > 1.0) dot = 1.0;
+        double upd = 2.0 * acos(dot) * 180.0 / ORC_PI;
+        if (trace) {
+            trace[4 * it + 0] = dx; trace[4 * it + 1] = dy;
+            trace[4 * it + 2] = deta; trace[4 * it + 3] = upd;
+        }
+        memcpy(q, q2, sizeof q);
+        ++it;
+        if (upd < tol_deg) break;
+    }
+    memcpy(q_out, q, sizeof q);
+    *peak_out = peak;
+    *iters_out = it;
+    free(img); free(yP); free(yT); free(r); free(SP); free(ST); free(lpP); free(lpT);
+    return 0;
+}
+
+/* Refine many patterns, one thread per pattern. patterns [P, n, n] (cropped),
+ * pcs [P, 3] (cropped PCs), seeds [P, 4]. */
+void orc_refine_many(const float *master, int M, const double *pcs, double sample_tilt_deg,
+                     double detector_tilt_deg, const orc_opts *o, const float *patterns,
+                     int P, int n, const double *seeds, int max_it, double tol_deg,
+                     double *quats, double *peaks, int32_t *iters) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int p = 0; p < P; ++p)
+        orc_refine_one(master, M, pcs + 3L * p, sample_tilt_deg, detector_tilt_deg, o,
+                       patterns + (long)p * n * n, n, seeds + 4L * p, max_it, tol_deg,
+                       quats + 4L * p, peaks + p, iters + p, NULL);
+}
