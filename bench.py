@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 refined template-matching EBSD indexer.
+
+Workload (synthetic, seeded): BCC master pattern on a 2 x 1024^2 Lambert grid,
+128 x 128 detector, 4,065-orientation cubic-fundamental-zone library
+(S^2 x S^1 grid, 5.35 deg), a 100 x 100 map (10,000 patterns) of smoothly
+varying orientations with +-2 deg jitter, PC jittered by +-0.005, Poisson noise
+at 100 counts plus background.  One step = build the library (projection +
+pre-processing of every template), search every pattern against every
+template (FFT cross-correlation, best template, sub-pixel shift) and refine
+every pattern to convergence (at most 10 iterations) -- all through the C ABI
+on device-resident inputs.  The metric is patterns per second; the mean
+misorientation of the refined orientations against the ground truth is
+reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank indexes its own map (weak scaling, no data
+exchange); rank 0 prints one JSON line.  --impl reference times the FP64 CPU
+oracle on the host cores instead (bounded samples of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "patterns indexed/s at <=0.5 deg mean misorientation vs plain FP32 XCF; % roofline"
+UNIT = "patterns/s"
+FLOPS_PER_PAIR_128 = 2.5 * 128 * 128 * 14 + 6 * 128 * 65   # inverse real FFT + conj-multiply
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--map", type=int, default=100, help="map side (patterns = map^2)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=0, help="patterns in the CPU sample (0: auto)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def clocks_start(gpu_index: int):
+    f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    try:
+        p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={CLOCK_Q}",
+                              "--format=csv,noheader,nounits", "-lms", "200"], stdout=f,
+                             stderr=subprocess.DEVNULL)
+    except OSError:
+        p = None
+    return p, f.name
+
+
+def clocks_stop(handle):
+    p, path = handle
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        p.kill()
+    rows = []
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), hw=parts[5], hwt=parts[6],
+                             swt=parts[7], swp=parts[8]))
+        except ValueError:
+            continue
+    os.unlink(path)
+    if not rows:
+        return None
+    reasons = set()
+    for r in rows:
+        for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                        ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+            if r[k].lower().startswith("active"):
+                reasons.add(name)
+    return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+            "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# --------------------------------------------------------------- cpu side
+def cpu_oracle_rate(wl, pats: np.ndarray, sample: int):
+    """Time the FP64 oracle (as it stands) on `sample` patterns of the workload:
+    library build (amortised over the whole map) + full search + refinement."""
+    import oracle
+    threads = oracle.num_threads()
+    n, pc = wl["n"], wl["pc"]
+    t0 = time.perf_counter()
+    St, _, _ = oracle.prep_many(oracle.project_many(wl["master"], wl["lib_q"], pc, n))
+    t_lib = time.perf_counter() - t0
+    sel = np.arange(sample)
+    t0 = time.perf_counter()
+    Sp, _, deg = oracle.prep_many(pats[sel])
+    best, _, _, _ = oracle.index(St, Sp, deg)
+    seeds = wl["lib_q"][np.maximum(best, 0)]
+    oracle.refine_many(wl["master"], pats[sel], seeds, wl["pcs"][sel], max_it=wl["max_iter"], tol_deg=1e-3)
+    t_s = time.perf_counter() - t0
+    P = len(wl["truth_q"])
+    per_pattern = t_s / sample + t_lib / P
+    return 1.0 / per_pattern, threads, t_lib, t_s
+
+
+def _roofline_traffic(src_path: str):
+    """DRAM bytes per launch of the search kernel from the committed ncu
+    summary, if it was taken on the current source of that kernel."""
+    import hashlib
+    meta = os.path.join(ROOT, "profiles", "search128_traffic.json")
+    if not os.path.exists(meta):
+        return None
+    m = json.load(open(meta))
+    sha = hashlib.sha256(open(src_path, "rb").read()).hexdigest()
+    if m.get("source_sha256") != sha:
+        return None
+    return m.get("bytes_per_launch_full")
+
+
+def peaks_file():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(p)) if os.path.exists(p) else None
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    wl = synth.config_map_128(seed=0, ny=args.map, nx=args.map)
+    n, P = wl["n"], len(wl["truth_q"])
+    threads = oracle.num_threads()
+    sample = args.cpu_sample or max(threads, 8)
+    t0 = time.perf_counter()
+    St, _, _ = oracle.prep_many(oracle.project_many(wl["master"], wl["lib_q"], wl["pc"], n))
+    t_lib = time.perf_counter() - t0
+    times = []
+    for s in range(args.warmup + args.steps):
+        sel = (np.arange(sample) + s * sample) % P
+        clean = oracle.project_many(wl["master"], wl["truth_q"][sel], wl["pc"], n)
+        pats = synth.add_noise(clean, wl["pcs"][sel], wl["peak"], wl["noise_seed"] + s)
+        t0 = time.perf_counter()
+        Sp, _, deg = oracle.prep_many(pats)
+        best, _, _, _ = oracle.index(St, Sp, deg)
+        oracle.refine_many(wl["master"], pats, wl["lib_q"][np.maximum(best, 0)], wl["pcs"][sel],
+                           max_it=wl["max_iter"], tol_deg=1e-3)
+        dt = time.perf_counter() - t0 + t_lib * sample / P
+        if s >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = sample / (ms / 1e3)
+    samp = (f"{sample} patterns per step of the {P}-pattern map: full {len(wl['lib_q'])}-template search + "
+            f"refinement (<= {wl['max_iter']} iterations); library build ({t_lib:.1f} s) amortised over {P}")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "patterns_per_step": sample, "detector": n,
+                       "templates": len(wl["lib_q"])},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": samp},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import paper_1807_11313_gb300 as px
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    # ---- inputs (each rank its own map: weak scaling)
+    wl = synth.config_map_128(seed=rank, ny=args.map, nx=args.map)
+    n, P, T = wl["n"], len(wl["truth_q"]), len(wl["lib_q"])
+    geom = px.geometry(n, n, wl["pc"])
+    ctx = px.Context(max_iter=wl["max_iter"], tol_deg=1e-3)
+    master_d = torch.from_numpy(np.ascontiguousarray(wl["master"])).to(dev)
+    libq_d = torch.from_numpy(wl["lib_q"]).to(dev)
+    truth_d = torch.from_numpy(wl["truth_q"]).to(dev)
+    pcs_d = torch.from_numpy(wl["pcs"]).to(dev)
+    clean = px.xcf_project(ctx, master_d, truth_d, geom, pcs=pcs_d).cpu().numpy()
+    pats_np = synth.add_noise(clean, wl["pcs"], wl["peak"], wl["noise_seed"])
+    del clean
+    pats_d = torch.from_numpy(pats_np).to(dev)
+    out = dict(best=torch.empty(P, dtype=torch.int32, device=dev), peak=torch.empty(P, device=dev),
+               shift=torch.empty((P, 2), device=dev), quats=torch.empty((P, 4), dtype=torch.float64, device=dev),
+               rpeak=torch.empty(P, device=dev), iters=torch.empty(P, dtype=torch.int32, device=dev))
+
+    def step():
+        lib = px.xcf_build_library(ctx, master_d, libq_d, geom)
+        px.xcf_index_refine(ctx, lib, pats_d, pcs=pcs_d, out=out)
+        lib.close()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    mis = px.xcf_disorientation(ctx, out["quats"], truth_d)
+    best_np = out["best"].cpu().numpy()
+    lib_mis = px.xcf_disorientation(ctx, libq_d[out["best"].clamp(min=0).long()].contiguous(), truth_d)
+    accuracy = {"mean_misorientation_deg": float(mis.mean()), "median_misorientation_deg": float(mis.median()),
+                "frac_below_1deg": float((mis < 1.0).double().mean()),
+                "library_match_mean_deg": float(lib_mis.mean()), "iters_mean": float(out["iters"].double().mean()),
+                "degenerate": int((best_np < 0).sum())}
+
+    # ---- timed region
+    px.xcf_profile_read(ctx, reset=True)
+    px.xcf_profile_enable(ctx, True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks_start(local)
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        step()
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = clocks_stop(clk)
+    if dist:
+        dist.barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    px.xcf_profile_enable(ctx, False)
+    prof = px.xcf_profile_read(ctx, reset=True)
+    launches = int(sum(v[1] for v in prof.values()))
+    value = P * args.steps * world / (elapsed_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (the all-pairs search)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    pk = peaks_file()
+    sm_max = (pk or {}).get("sm_max_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
+    fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA = 2 flops
+    s_ms, s_n = prof["search"]
+    per_launch_ms = s_ms / max(s_n, 1)
+    flops_launch = P * T * FLOPS_PER_PAIR_128                 # one launch covers the whole map
+    achieved = flops_launch / (per_launch_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak,
+                "traffic": _roofline_traffic(os.path.join(ROOT, "paper_1807_11313_gb300", "csrc", "k_search128.cu")),
+                "kernel": "k_search128", "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                "search_ms_per_launch": per_launch_ms,
+                "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+
+    # ---- end to end through the host-memory entry point
+    e2e = None
+    if not args.no_e2e:
+        pats_h = torch.from_numpy(pats_np).pin_memory()
+        pcs_h = torch.from_numpy(wl["pcs"]).pin_memory()
+        master_h = torch.from_numpy(np.ascontiguousarray(wl["master"])).pin_memory()
+        libq_h = torch.from_numpy(wl["lib_q"]).pin_memory()
+        hout = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
+
+        def e2e_step():
+            m = master_h.to(dev, non_blocking=True)
+            q = libq_h.to(dev, non_blocking=True)
+            lib = px.xcf_build_library(ctx, m, q, geom)
+            px.xcf_index_refine_host(ctx, lib, pats_h, pcs=pcs_h, out=hout)
+            lib.close()
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        h2d = pats_h.numel() * 4 + pcs_h.numel() * 8 + master_h.numel() * 4 + libq_h.numel() * 8
+        d2h = sum(v.numel() * v.element_size() for v in hout.values())
+        e2e = {"value": P * args.steps * world / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    # ---- CPU oracle baseline (rank 0, one GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        sample = args.cpu_sample or max(2 * oracle.num_threads(), 16)
+        rate, threads, t_lib, t_s = cpu_oracle_rate(wl, pats_np, sample)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": (f"{sample} of the {P} patterns: full {T}-template search + refinement "
+                          f"(<= {wl['max_iter']} iterations) in {t_s:.1f} s; library build ({t_lib:.1f} s) "
+                          f"amortised over {P}")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl["name"], "detector": n, "templates": T, "patterns_per_gpu": P,
+                           "max_iter": wl["max_iter"], "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (655 MB patterns, 270 MB library spectra)"},
+                "accuracy": accuracy, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
+                "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

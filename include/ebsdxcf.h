@@ -1,0 +1,228 @@
+/*
+ * ebsdxcf — GB300 (sm_103a) EBSD pattern indexing by FFT cross-correlation
+ * template matching with orientation refinement, after Foden, Collins,
+ * Wilkinson & Britton, "Indexing Electron Backscatter Diffraction Patterns
+ * with a Refined Template Matching Approach" (arXiv 1807.11313).
+ *
+ * C ABI.  Conventions for every entry point:
+ *  - Return value: XCF_OK (0) or a negative XCF_ERR_* code; nothing throws
+ *    across the ABI.  xcf_strerror() names a code, xcf_last_error() gives the
+ *    detail of the last failing call on a context.
+ *  - Array arguments are DEVICE pointers owned by the caller, row-major and
+ *    contiguous, unless the entry point's name ends in _host (then they are
+ *    host pointers, ideally pinned).  Struct arguments (options, geometry) are
+ *    host pointers read during the call.
+ *  - Work is enqueued on the caller's `stream` (a cudaStream_t passed as
+ *    void*, NULL = legacy default stream) and is asynchronous unless stated.
+ *  - A context owns reusable device scratch.  One context must not be used
+ *    from two host threads or on two streams at once.
+ *  - Geometry: a W x H detector, pixel (i, j) = (row from the top, column from
+ *    the left); Bruker-style pattern centre (pcx of the width from the left,
+ *    pcy of the height from the top, detector distance pcz x width).  The
+ *    indexer works on the centred square crop of side N = the largest power
+ *    of two <= min(W, H) (capped at 256, at least 16), with the PC moved so
+ *    that it still points at the same pixel (paper, FFT section, footnotes 1-2).
+ *  - Orientations are unit quaternions (w, x, y, z) in float64; R(q) maps
+ *    sample-frame directions to crystal-frame directions.
+ *  - Spectra are half spectra [N][N/2 + 1] of interleaved float32 (re, im).
+ */
+#ifndef EBSDXCF_H
+#define EBSDXCF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define XCF_OK                 0
+#define XCF_ERR_ARG           -1  /* null pointer, negative count, bad option  */
+#define XCF_ERR_SIZE          -2  /* detector side not a usable power of two   */
+#define XCF_ERR_OOM           -3  /* device allocation failed                  */
+#define XCF_ERR_CUDA          -4  /* a CUDA runtime call or launch failed      */
+#define XCF_ERR_TIMEOUT       -5  /* a bounded device wait gave up             */
+#define XCF_ERR_UNIMPLEMENTED -6  /* combination not built (e.g. N = 256 here) */
+
+typedef struct xcf_ctx xcf_ctx;
+typedef struct xcf_library xcf_library;
+
+/* Pre-processing and refinement options.  Values <= 0 in the fields marked
+ * "auto" take the default for the detector side N. */
+typedef struct {
+    int32_t window;     /* 0 none, 1 periodic Hann (default)                       */
+    double sigma_hp;    /* Gaussian high-pass sigma, cycles/image (default 2)       */
+    double sigma_lp;    /* Gaussian low-pass sigma, cycles/image (auto: N/4)        */
+    int32_t lp_nr;      /* log-polar radii (auto: N/2)                              */
+    int32_t lp_neta;    /* log-polar angles (auto: 2N)                              */
+    double lp_rmin;     /* smallest log-polar radius, px (auto: 4)                  */
+    double lp_rmax;     /* largest log-polar radius, px (auto: N/2 - 1)             */
+    int32_t max_iter;   /* refinement iterations (default 2, as in the paper)       */
+    double tol_deg;     /* stop when an iteration's update is below this (1e-3)     */
+} xcf_options;
+
+/* Detector geometry of a map (or of a library). */
+typedef struct {
+    int32_t width, height;      /* detector pixels W, H                         */
+    double pcx, pcy, pcz;       /* Bruker-style pattern centre                  */
+    double sample_tilt_deg;     /* 70 in the paper                              */
+    double detector_tilt_deg;   /* 0                                            */
+} xcf_geometry;
+
+/* Text of a status code (static storage). */
+const char *xcf_strerror(int code);
+
+/* Detail of the last error on ctx (empty string if none); valid until the
+ * next call on ctx. */
+const char *xcf_last_error(const xcf_ctx *ctx);
+
+/* Fill *opt with the defaults (paper readings: Hann window, Gaussian
+ * band-pass sigma_hp = 2, sigma_lp = N/4; two refinement iterations). */
+int xcf_options_default(xcf_options *opt);
+
+/* Square crop rule (paper, FFT section, footnotes 1-2): side n, offsets of the
+ * crop in the detector and the pattern centre of the cropped square.  Host
+ * only; XCF_ERR_SIZE if the side would be below 16. */
+int xcf_crop(const xcf_geometry *g, int32_t *n, int32_t *off_x, int32_t *off_y,
+             double pc_out[3]);
+
+/* Create a context on CUDA device `device` (the device is made current for
+ * the call).  opt may be NULL (defaults).  Allocates nothing yet. */
+int xcf_create(xcf_ctx **out, const xcf_options *opt, int device);
+int xcf_destroy(xcf_ctx *ctx);
+
+/* Gnomonic reprojection of a master pattern onto the detector (paper,
+ * "SO(3) Library Generation"): for each of P orientations, pixel (i, j) looks
+ * along d = (j + .5 - pcx W, pcy H - (i + .5), pcz W) in the detector frame
+ * (x right, y up), is rotated to the sample frame about x by
+ * 90 - sample_tilt + detector_tilt degrees and to the crystal frame by R(q),
+ * and samples the master bilinearly on its Rosca equal-area square grid.
+ *   master  [2, M, M] float32: hemispheres z >= 0 and z < 0; cell (a, b)
+ *           centred at X = L(2(b + .5)/M - 1), Y = L(2(a + .5)/M - 1),
+ *           L = sqrt(pi/2).
+ *   quats   [P, 4] float64.
+ *   pcs     [P, 3] float64 per-image pattern centres, or NULL (use g's).
+ *   out     [P, H, W] float32.                                              */
+int xcf_project(xcf_ctx *ctx, const float *master, int32_t M, const double *quats, int32_t P,
+                const xcf_geometry *g, const double *pcs, float *out, void *stream);
+
+/* Pre-processing of P detector images (paper, FFT section and the
+ * simulation set-up of "SO(3) Sampling Frequency"): centred 2^n crop, zero
+ * mean / unit standard deviation, window, 2-D FFT (Eq. 4), band-pass, and
+ * division by the filtered spectrum's norm.
+ *   images   [P, H, W] float32 (H, W from g).
+ *   spectra  [P, N, N/2 + 1, 2] float32 (unit-norm half spectra).
+ *   spatial  [P, N, N] float32 or NULL: filtered image = unitary inverse
+ *            transform of the unit-norm spectrum (unit L2 norm).
+ *   degenerate [P] int32 or NULL: 1 where the image has no signal (zero
+ *            variance or no energy in the pass band); its outputs are 0.     */
+int xcf_prep(xcf_ctx *ctx, const float *images, int32_t P, const xcf_geometry *g,
+             float *spectra, float *spatial, int32_t *degenerate, void *stream);
+
+/* Build a template library (paper, "SO(3) Library Generation"): project the
+ * master at each of T orientations on the cropped detector of g, pre-process
+ * (as xcf_prep), and keep the half spectra on the device.  The library keeps
+ * device copies of the master and of quats (used by refinement).  Input
+ * pointers are device pointers and need not outlive the call.  Synchronous
+ * with respect to `stream`. */
+int xcf_build_library(xcf_ctx *ctx, const float *master, int32_t M, const double *quats,
+                      int32_t T, const xcf_geometry *g, xcf_library **out, void *stream);
+int xcf_library_free(xcf_library *lib);
+
+/* Build a library from template images the caller simulated elsewhere
+ * (images [T, H, W] float32 on g's detector, pre-processed as xcf_prep)
+ * with their orientations quats [T, 4]; master [2, M, M] (M >= 2) is kept for
+ * refinement and may be NULL (M = 0), in which case xcf_refine fails with
+ * XCF_ERR_ARG.  Synchronous with respect to `stream`. */
+int xcf_build_library_images(xcf_ctx *ctx, const float *images, const double *quats, int32_t T,
+                             const xcf_geometry *g, const float *master, int32_t M,
+                             xcf_library **out, void *stream);
+
+/* Library size T, detector side N, and the device pointer to its spectra
+ * [T, N, N/2 + 1, 2] (owned by the library; read-only). */
+int xcf_library_info(const xcf_library *lib, int32_t *T, int32_t *N, const float **spectra);
+
+/* Library search (paper, Fig. 1 A-C, Eqs. 3 and 6): for each pattern, the
+ * template maximising the peak of the normalised cross-correlation surface
+ * r(s) = sum_k conj(S_t[k]) S_p[k] exp(+2 pi i k.s / N) over all N^2 circular
+ * shifts; ties go to the lowest template index and, within a surface, to the
+ * lowest row-major shift.
+ *   patterns [P, H, W] float32 with the library's geometry.
+ *   best     [P] int32: template index, or -1 for a degenerate pattern.
+ *   peak     [P] float32: r at the integer peak of the best template.
+ *   shift    [P, 2] float32 (dx, dy) px: the pattern is the template
+ *            translated by +shift; integer peak wrapped into [-N/2, N/2) plus a
+ *            3-point parabolic sub-pixel offset per axis (the paper's peak
+ *            up-sampling, read as a parabola fit), clamped to +-0.5.       */
+int xcf_index(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P,
+              int32_t *best, float *peak, float *shift, void *stream);
+
+/* The same search, but returning every per-template peak: peaks [P, T]
+ * float32 (max over shifts of r for each pair).  For analysis and tests. */
+int xcf_correlate_all(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P,
+                      float *peaks, void *stream);
+
+/* Orientation refinement (paper, "Orientation and Pattern Centre
+ * Refinement", Eq. 7, Fig. 6): starting from seeds, each iteration
+ *  (X/Y) projects the template at the current orientation with the
+ *        pattern's PC, cross-correlates it with the pattern, and turns the
+ *        sub-pixel shift (dx, dy) into rotations about the detector y and x
+ *        axes, theta = atan(shift / L), L = pcz W (Eq. 7 with atan);
+ *  (Z)   re-projects, log-polar transforms the filtered template and pattern
+ *        about the screen centre, correlates along the angle and turns the
+ *        angular shift into a rotation about the detector z axis;
+ * composing each rotation onto the orientation in float64, until the update
+ * of an iteration is below opt.tol_deg or opt.max_iter iterations ran.
+ *   patterns [P, H, W] float32; seeds [P, 4] float64; pcs [P, 3] float64 or
+ *   NULL (library PC); quats [P, 4] float64 out; peak [P] float32 out (XCF
+ *   peak of the last X/Y step); iters [P] int32 out.                      */
+int xcf_refine(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P,
+               const double *seeds, const double *pcs, double *quats, float *peak,
+               int32_t *iters, void *stream);
+
+/* Cubic (432) disorientation in degrees between qa[i] and qb[i] (paper, second
+ * "Equation 6"): the smallest rotation angle of S qa qb^-1 over the 24 proper
+ * cubic operators S.  qa, qb [n, 4] float64; out [n] float64. */
+int xcf_disorientation(xcf_ctx *ctx, const double *qa, const double *qb, int32_t n, double *out,
+                       void *stream);
+
+/* Search then refine in one call (device memory): xcf_index, seeds = the
+ * library orientations of the best templates (identity for degenerate
+ * patterns), then xcf_refine.  Outputs as those two calls. */
+int xcf_index_refine(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P,
+                     const double *pcs, int32_t *best, float *peak, float *shift, double *quats,
+                     float *rpeak, int32_t *iters, void *stream);
+
+/* End to end from host memory: search and refine P patterns held in host
+ * memory (pinned for full speed), streaming them through the device in chunks
+ * of `chunk` patterns with copies overlapped on a second stream, and writing
+ * host outputs.  pcs (host, [P, 3]) may be NULL.  Outputs: best, peak, shift
+ * as xcf_index; quats, rpeak, iters as xcf_refine (seeds = library
+ * orientations of best).  Synchronous. */
+int xcf_index_refine_host(xcf_ctx *ctx, const xcf_library *lib, const float *patterns,
+                          int32_t P, const double *pcs, int32_t chunk, int32_t *best, float *peak,
+                          float *shift, double *quats, float *rpeak, int32_t *iters);
+
+/* Profiling.  Every context counts the kernels it launches, per stage.  When
+ * timing is enabled it also records a CUDA event pair on the launching stream
+ * around each launch and accumulates the elapsed device time per stage. */
+#define XCF_STAGE_PROJECT  0   /* gnomonic reprojection                          */
+#define XCF_STAGE_PREP     1   /* crop, standardise, window, FFT, filter, norm    */
+#define XCF_STAGE_SEARCH   2   /* all-pairs correlation and best-template keys    */
+#define XCF_STAGE_PEAK     3   /* single-surface argmax and sub-pixel fit         */
+#define XCF_STAGE_LOGPOLAR 4   /* log-polar resampling                            */
+#define XCF_STAGE_UPDATE   5   /* refinement updates (X/Y shift, angular xcf + Z) */
+#define XCF_STAGE_OTHER    6   /* small bookkeeping kernels                       */
+#define XCF_NUM_STAGES     7
+
+/* Turn event timing on (1) or off (0).  Host only. */
+int xcf_profile_enable(xcf_ctx *ctx, int on);
+
+/* Per-stage accumulated device milliseconds (ms, may be NULL) and kernel
+ * launch counts (launches, may be NULL), arrays of XCF_NUM_STAGES.  Waits for
+ * the recorded events.  reset != 0 clears the accumulators afterwards. */
+int xcf_profile_read(xcf_ctx *ctx, double *ms, int64_t *launches, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EBSDXCF_H */

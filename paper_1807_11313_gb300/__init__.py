@@ -1,0 +1,14 @@
+"""GB300 (sm_103a) EBSD indexing by FFT cross-correlation template matching
+with orientation refinement (Foden, Collins, Wilkinson & Britton,
+arXiv 1807.11313).
+
+The compute path is the CUDA library built from ``csrc/`` (C ABI in
+``include/ebsdxcf.h``); ``xcf`` is its thin binding.  Importing this package
+loads nothing; the first call loads (and if needed builds) the library.
+"""
+from .xcf import (  # noqa: F401
+    Context, Library, XcfError, geometry, xcf_build_library, xcf_build_library_images,
+    xcf_correlate_all, xcf_crop, xcf_disorientation, xcf_index, xcf_index_refine, xcf_index_refine_host,
+    xcf_options, xcf_geometry, xcf_prep, xcf_project, xcf_refine, load, library_path,
+    xcf_profile_enable, xcf_profile_read, STAGES,
+)

@@ -1,0 +1,766 @@
+// Host side of the ebsdxcf C ABI: argument checks, the per-context scratch
+// arena, library construction, and the index / refine / end-to-end flows.
+// Every compute step is one of the kernels in this directory; the host only
+// sequences launches on the caller's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ebsdxcf.h"
+#include "kernels.cuh"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+enum Slot {
+    S_SPEC_P = 0,   // pattern half spectra
+    S_SPEC_T,       // per-pattern template half spectra (refinement)
+    S_SPATIAL_P,    // filtered pattern images
+    S_SPATIAL_T,    // filtered template images
+    S_IMG,          // projected template images
+    S_LP_P,         // log-polar patterns
+    S_LP_T,         // log-polar templates
+    S_KEYS,
+    S_DEGEN,
+    S_ACTIVE,
+    S_SHIFT,
+    S_Q1,
+    S_SEEDS,
+    S_BEST,
+    S_PEAK,
+    S_IO_PAT,       // host pipeline: device copy of a chunk of patterns
+    S_IO_PCS,
+    S_IO_OUT,
+    S_COUNT
+};
+
+}  // namespace
+
+struct xcf_ctx {
+    int device = 0;
+    int num_sms = 0;
+    xcf_options opt{};
+    std::string err;
+    void *buf[S_COUNT] = {};
+    size_t cap[S_COUNT] = {};
+    // profiling
+    bool timing = false;
+    int64_t launches[XCF_NUM_STAGES] = {};
+    double ms[XCF_NUM_STAGES] = {};
+    struct Rec { int stage; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+};
+
+struct xcf_library {
+    int device = 0;
+    int T = 0, N = 0, M = 0;
+    xcf_geometry geom{};
+    int ox = 0, oy = 0;
+    double pc[3] = {0, 0, 0};
+    float2 *spectra = nullptr;
+    double *quats = nullptr;
+    float *master = nullptr;
+};
+
+namespace {
+
+int fail(xcf_ctx *ctx, int code, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_fail(xcf_ctx *ctx, cudaError_t e, const char *where) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? XCF_ERR_OOM : XCF_ERR_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define XCF_CHECK(expr, where)                                  \
+    do {                                                        \
+        cudaError_t e_ = (expr);                                \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+    } while (0)
+
+// a kernel launch of `stage` on stream `st`: counted, and timed with an
+// event pair when the context's timing is on
+#define XCF_LAUNCH(stage, st, expr, where)                                   \
+    do {                                                                     \
+        cudaEvent_t a_ = nullptr, b_ = nullptr;                              \
+        if (ctx->timing && cudaEventCreate(&a_) == cudaSuccess)              \
+            cudaEventRecord(a_, st);                                         \
+        cudaError_t e_ = (expr);                                             \
+        if (e_ != cudaSuccess) {                                             \
+            if (a_) cudaEventDestroy(a_);                                    \
+            return cuda_fail(ctx, e_, where);                                \
+        }                                                                    \
+        ctx->launches[stage] += 1;                                           \
+        if (a_ && cudaEventCreate(&b_) == cudaSuccess) {                     \
+            cudaEventRecord(b_, st);                                         \
+            ctx->recs.push_back({stage, a_, b_});                            \
+        } else if (a_) {                                                     \
+            cudaEventDestroy(a_);                                            \
+        }                                                                    \
+    } while (0)
+
+// grow-only scratch buffer; cudaFree / cudaMalloc synchronise, so the first
+// call at a size pays for it and later calls reuse the allocation
+int scratch(xcf_ctx *ctx, int slot, size_t bytes, void **out) {
+    if (bytes == 0) bytes = 16;
+    if (ctx->cap[slot] < bytes) {
+        if (ctx->buf[slot]) cudaFree(ctx->buf[slot]);
+        ctx->buf[slot] = nullptr;
+        ctx->cap[slot] = 0;
+        cudaError_t e = cudaMalloc(&ctx->buf[slot], bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, XCF_ERR_OOM, "scratch allocation of " + std::to_string(bytes) + " bytes failed");
+        }
+        ctx->cap[slot] = bytes;
+    }
+    *out = ctx->buf[slot];
+    return XCF_OK;
+}
+
+template <typename T>
+int scratch_t(xcf_ctx *ctx, int slot, size_t count, T **out) {
+    void *p = nullptr;
+    int rc = scratch(ctx, slot, count * sizeof(T), &p);
+    *out = static_cast<T *>(p);
+    return rc;
+}
+
+struct Crop {
+    int n, ox, oy;
+    double pc[3];
+};
+
+int crop_of(const xcf_geometry *g, int cap, Crop *c) {
+    if (!g || g->width <= 0 || g->height <= 0) return XCF_ERR_ARG;
+    int m = g->width < g->height ? g->width : g->height;
+    int n = 1;
+    while (n * 2 <= m && n * 2 <= cap) n *= 2;
+    if (n < 16) return XCF_ERR_SIZE;
+    c->n = n;
+    c->ox = (g->width - n) / 2;
+    c->oy = (g->height - n) / 2;
+    c->pc[0] = (g->pcx * g->width - c->ox) / n;
+    c->pc[1] = (g->pcy * g->height - c->oy) / n;
+    c->pc[2] = g->pcz * g->width / n;
+    return XCF_OK;
+}
+
+double alpha_of(const xcf_geometry *g) {
+    return (90.0 - g->sample_tilt_deg + g->detector_tilt_deg) * kPi / 180.0;
+}
+
+struct Resolved {
+    int window;
+    double sigma_hp, sigma_lp;
+    int nr, neta;
+    double rmin, rmax;
+};
+
+Resolved resolve(const xcf_options &o, int n) {
+    Resolved r;
+    r.window = o.window;
+    r.sigma_hp = o.sigma_hp > 0 ? o.sigma_hp : 2.0;
+    r.sigma_lp = o.sigma_lp > 0 ? o.sigma_lp : n / 4.0;
+    r.nr = o.lp_nr > 0 ? o.lp_nr : n / 2;
+    r.neta = o.lp_neta > 0 ? o.lp_neta : 2 * n;
+    r.rmin = o.lp_rmin > 0 ? o.lp_rmin : 4.0;
+    r.rmax = o.lp_rmax > 0 ? o.lp_rmax : n / 2.0 - 1.0;
+    return r;
+}
+
+PrepArgs prep_args(const xcf_geometry *g, const Crop &c, const Resolved &r) {
+    PrepArgs a;
+    a.N = c.n;
+    a.W = g->width;
+    a.H = g->height;
+    a.ox = c.ox;
+    a.oy = c.oy;
+    a.window = r.window;
+    a.inv2shp = (float)(1.0 / (2.0 * r.sigma_hp * r.sigma_hp));
+    a.inv2slp = (float)(1.0 / (2.0 * r.sigma_lp * r.sigma_lp));
+    return a;
+}
+
+// square n x n template images on the cropped detector (the source image of
+// the pre-processing is then the n x n image itself: W = H = n, no offset)
+ProjArgs proj_args_cropped(const xcf_geometry *g, const Crop &c) {
+    ProjArgs a;
+    a.W = g->width;
+    a.H = g->height;
+    a.ox = c.ox;
+    a.oy = c.oy;
+    a.nx = c.n;
+    a.ny = c.n;
+    a.pcx = g->pcx;
+    a.pcy = g->pcy;
+    a.pcz = g->pcz;
+    a.alpha = alpha_of(g);
+    return a;
+}
+
+PrepArgs prep_args_square(const Crop &c, const Resolved &r) {
+    PrepArgs a;
+    a.N = c.n;
+    a.W = c.n;
+    a.H = c.n;
+    a.ox = 0;
+    a.oy = 0;
+    a.window = r.window;
+    a.inv2shp = (float)(1.0 / (2.0 * r.sigma_hp * r.sigma_hp));
+    a.inv2slp = (float)(1.0 / (2.0 * r.sigma_lp * r.sigma_lp));
+    return a;
+}
+
+bool supported_n(int n) { return n == 16 || n == 32 || n == 64 || n == 128; }
+
+int check_lib(xcf_ctx *ctx, const xcf_library *lib) {
+    if (!ctx) return XCF_ERR_ARG;
+    if (!lib) return fail(ctx, XCF_ERR_ARG, "library is NULL");
+    if (lib->device != ctx->device) return fail(ctx, XCF_ERR_ARG, "library and context on different devices");
+    return XCF_OK;
+}
+
+constexpr int kChunk = 16384;   // patterns per pass (bounds the scratch footprint)
+
+// index one chunk already on the device: spectra of the patterns, search,
+// best, and the sub-pixel peak of the best template
+int index_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int P, int *best,
+                float *peak, float *shift, float *peaks_all, cudaStream_t st) {
+    const xcf_geometry *g = &lib->geom;
+    Crop c;
+    crop_of(g, 256, &c);
+    const Resolved r = resolve(ctx->opt, c.n);
+    const int H = c.n * (c.n / 2 + 1);
+    float2 *sp;
+    int *degen;
+    unsigned long long *keys;
+    int rc;
+    if ((rc = scratch_t(ctx, S_SPEC_P, (size_t)P * H, &sp))) return rc;
+    if ((rc = scratch_t(ctx, S_DEGEN, P, &degen))) return rc;
+    if ((rc = scratch_t(ctx, S_KEYS, P, &keys))) return rc;
+    XCF_LAUNCH(XCF_STAGE_PREP, st, launch_prep(patterns, P, prep_args(g, c, r), sp, nullptr, degen, nullptr, st), "prep");
+    XCF_CHECK(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * P, st), "memset keys");
+    if (peaks_all)   // degenerate patterns keep all-zero rows
+        XCF_CHECK(cudaMemsetAsync(peaks_all, 0, sizeof(float) * (size_t)P * lib->T, st), "memset peaks");
+    XCF_LAUNCH(XCF_STAGE_SEARCH, st,
+               launch_search(c.n, lib->spectra, lib->T, sp, degen, P, keys, peaks_all, ctx->num_sms, st),
+               "search");
+    if (best) {
+        XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_keys_to_best(keys, P, best, st), "keys_to_best");
+        XCF_LAUNCH(XCF_STAGE_PEAK, st,
+                   launch_pair_peak(c.n, lib->spectra, best, sp, degen, nullptr, P, peak, shift, st),
+                   "pair_peak");
+    }
+    return XCF_OK;
+}
+
+int refine_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int P,
+                 const double *seeds, const double *pcs, double *quats, float *peak, int *iters,
+                 cudaStream_t st) {
+    const xcf_geometry *g = &lib->geom;
+    Crop c;
+    crop_of(g, 256, &c);
+    const Resolved r = resolve(ctx->opt, c.n);
+    const int n = c.n, H = n * (n / 2 + 1), L = r.nr * r.neta;
+    float2 *sp, *stt;
+    float *yp, *yt, *img, *lpp, *lpt, *shift;
+    int *degen, *active;
+    double *q1;
+    int rc;
+    if ((rc = scratch_t(ctx, S_SPEC_P, (size_t)P * H, &sp))) return rc;
+    if ((rc = scratch_t(ctx, S_SPEC_T, (size_t)P * H, &stt))) return rc;
+    if ((rc = scratch_t(ctx, S_SPATIAL_P, (size_t)P * n * n, &yp))) return rc;
+    if ((rc = scratch_t(ctx, S_SPATIAL_T, (size_t)P * n * n, &yt))) return rc;
+    if ((rc = scratch_t(ctx, S_IMG, (size_t)P * n * n, &img))) return rc;
+    if ((rc = scratch_t(ctx, S_LP_P, (size_t)P * L, &lpp))) return rc;
+    if ((rc = scratch_t(ctx, S_LP_T, (size_t)P * L, &lpt))) return rc;
+    if ((rc = scratch_t(ctx, S_SHIFT, (size_t)P * 2, &shift))) return rc;
+    if ((rc = scratch_t(ctx, S_DEGEN, P, &degen))) return rc;
+    if ((rc = scratch_t(ctx, S_ACTIVE, P, &active))) return rc;
+    if ((rc = scratch_t(ctx, S_Q1, (size_t)P * 4, &q1))) return rc;
+    const PrepArgs pa = prep_args(g, c, r), ps = prep_args_square(c, r);
+    const ProjArgs pj = proj_args_cropped(g, c);
+    const double alpha = alpha_of(g);
+    XCF_LAUNCH(XCF_STAGE_PREP, st, launch_prep(patterns, P, pa, sp, yp, degen, nullptr, st), "prep patterns");
+    XCF_LAUNCH(XCF_STAGE_LOGPOLAR, st,
+               launch_logpolar(yp, nullptr, P, n, r.nr, r.neta, (float)r.rmin, (float)r.rmax, lpp, st),
+               "logpolar patterns");
+    if (quats != seeds)
+        XCF_CHECK(cudaMemcpyAsync(quats, seeds, sizeof(double) * 4 * P, cudaMemcpyDeviceToDevice, st),
+                  "copy seeds");
+    XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_init_refine(degen, P, active, iters, peak, st), "init");
+    for (int it = 0; it < ctx->opt.max_iter; ++it) {
+        // X / Y: shift of the template at the current orientation
+        XCF_LAUNCH(XCF_STAGE_PROJECT, st, launch_project(lib->master, lib->M, quats, pcs, active, P, pj, img, st),
+                   "project");
+        XCF_LAUNCH(XCF_STAGE_PREP, st, launch_prep(img, P, ps, stt, nullptr, nullptr, active, st), "prep templates");
+        XCF_LAUNCH(XCF_STAGE_PEAK, st, launch_pair_peak(n, stt, nullptr, sp, degen, active, P, peak, shift, st),
+                   "xy peak");
+        XCF_LAUNCH(XCF_STAGE_UPDATE, st,
+                   launch_update_xy(quats, shift, pcs, g->pcz, g->width, alpha, active, P, q1, st), "xy update");
+        // Z: angular shift of the log-polar images
+        XCF_LAUNCH(XCF_STAGE_PROJECT, st, launch_project(lib->master, lib->M, q1, pcs, active, P, pj, img, st),
+                   "project");
+        XCF_LAUNCH(XCF_STAGE_PREP, st, launch_prep(img, P, ps, stt, yt, nullptr, active, st), "prep templates");
+        XCF_LAUNCH(XCF_STAGE_LOGPOLAR, st,
+                   launch_logpolar(yt, active, P, n, r.nr, r.neta, (float)r.rmin, (float)r.rmax, lpt, st),
+                   "logpolar templates");
+        XCF_LAUNCH(XCF_STAGE_UPDATE, st,
+                   launch_eta_update(lpt, lpp, r.nr, r.neta, quats, q1, alpha, ctx->opt.tol_deg, active, iters,
+                                     quats, P, st),
+                   "z update");
+    }
+    return XCF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *xcf_strerror(int code) {
+    switch (code) {
+        case XCF_OK: return "ok";
+        case XCF_ERR_ARG: return "invalid argument";
+        case XCF_ERR_SIZE: return "unsupported detector size";
+        case XCF_ERR_OOM: return "out of device memory";
+        case XCF_ERR_CUDA: return "CUDA error";
+        case XCF_ERR_TIMEOUT: return "device wait timed out";
+        case XCF_ERR_UNIMPLEMENTED: return "not implemented";
+        default: return "unknown error";
+    }
+}
+
+const char *xcf_last_error(const xcf_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int xcf_options_default(xcf_options *o) {
+    if (!o) return XCF_ERR_ARG;
+    o->window = 1;
+    o->sigma_hp = 2.0;
+    o->sigma_lp = 0.0;
+    o->lp_nr = 0;
+    o->lp_neta = 0;
+    o->lp_rmin = 0.0;
+    o->lp_rmax = 0.0;
+    o->max_iter = 2;
+    o->tol_deg = 1e-3;
+    return XCF_OK;
+}
+
+int xcf_crop(const xcf_geometry *g, int32_t *n, int32_t *off_x, int32_t *off_y, double pc_out[3]) {
+    Crop c;
+    int rc = crop_of(g, 256, &c);
+    if (rc) return rc;
+    if (n) *n = c.n;
+    if (off_x) *off_x = c.ox;
+    if (off_y) *off_y = c.oy;
+    if (pc_out) memcpy(pc_out, c.pc, sizeof c.pc);
+    return XCF_OK;
+}
+
+int xcf_create(xcf_ctx **out, const xcf_options *opt, int device) {
+    if (!out) return XCF_ERR_ARG;
+    *out = nullptr;
+    xcf_options o;
+    if (opt) {
+        o = *opt;
+        if (o.window < 0 || o.window > 1 || o.max_iter < 0 || o.sigma_hp < 0) return XCF_ERR_ARG;
+    } else {
+        xcf_options_default(&o);
+    }
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return XCF_ERR_CUDA;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        return XCF_ERR_CUDA;
+    }
+    xcf_ctx *c = new xcf_ctx();
+    c->device = device;
+    c->num_sms = sms;
+    c->opt = o;
+    *out = c;
+    return XCF_OK;
+}
+
+int xcf_destroy(xcf_ctx *ctx) {
+    if (!ctx) return XCF_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    for (auto &r : ctx->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (int i = 0; i < S_COUNT; ++i)
+        if (ctx->buf[i]) cudaFree(ctx->buf[i]);
+    delete ctx;
+    return XCF_OK;
+}
+
+int xcf_project(xcf_ctx *ctx, const float *master, int32_t M, const double *quats, int32_t P,
+                const xcf_geometry *g, const double *pcs, float *out, void *stream) {
+    if (!ctx) return XCF_ERR_ARG;
+    if (P == 0) return XCF_OK;
+    if (!master || !quats || !g || !out || P < 0 || M < 2)
+        return fail(ctx, XCF_ERR_ARG, "xcf_project: bad argument");
+    if (g->width <= 0 || g->height <= 0) return fail(ctx, XCF_ERR_ARG, "xcf_project: bad detector size");
+    cudaSetDevice(ctx->device);
+    ProjArgs a;
+    a.W = g->width;
+    a.H = g->height;
+    a.ox = 0;
+    a.oy = 0;
+    a.nx = g->width;
+    a.ny = g->height;
+    a.pcx = g->pcx;
+    a.pcy = g->pcy;
+    a.pcz = g->pcz;
+    a.alpha = alpha_of(g);
+    cudaStream_t st = (cudaStream_t)stream;
+    XCF_LAUNCH(XCF_STAGE_PROJECT, st, launch_project(master, M, quats, pcs, nullptr, P, a, out, st), "project");
+    return XCF_OK;
+}
+
+int xcf_prep(xcf_ctx *ctx, const float *images, int32_t P, const xcf_geometry *g, float *spectra,
+             float *spatial, int32_t *degenerate, void *stream) {
+    if (!ctx) return XCF_ERR_ARG;
+    if (!g || P < 0) return fail(ctx, XCF_ERR_ARG, "xcf_prep: bad argument");
+    if (P == 0) return XCF_OK;
+    if (!images || !spectra) return fail(ctx, XCF_ERR_ARG, "xcf_prep: bad argument");
+    Crop c;
+    int rc = crop_of(g, 256, &c);
+    if (rc) return fail(ctx, rc, "xcf_prep: detector too small");
+    if (!supported_n(c.n)) return fail(ctx, XCF_ERR_UNIMPLEMENTED, "xcf_prep: N = 256 is not built");
+    cudaSetDevice(ctx->device);
+    const Resolved r = resolve(ctx->opt, c.n);
+    int *degen = degenerate;
+    if (!degen && (rc = scratch_t(ctx, S_DEGEN, P, &degen))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    XCF_LAUNCH(XCF_STAGE_PREP, st,
+               launch_prep(images, P, prep_args(g, c, r), reinterpret_cast<float2 *>(spectra), spatial, degen,
+                           nullptr, st),
+               "prep");
+    return XCF_OK;
+}
+
+int xcf_build_library(xcf_ctx *ctx, const float *master, int32_t M, const double *quats, int32_t T,
+                      const xcf_geometry *g, xcf_library **out, void *stream) {
+    if (!ctx) return XCF_ERR_ARG;
+    if (!master || !quats || !g || !out || T <= 0 || M < 2)
+        return fail(ctx, XCF_ERR_ARG, "xcf_build_library: bad argument");
+    *out = nullptr;
+    Crop c;
+    int rc = crop_of(g, 256, &c);
+    if (rc) return fail(ctx, rc, "xcf_build_library: detector too small");
+    if (!supported_n(c.n)) return fail(ctx, XCF_ERR_UNIMPLEMENTED, "xcf_build_library: N = 256 is not built");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const Resolved r = resolve(ctx->opt, c.n);
+    xcf_library *lib = new xcf_library();
+    lib->device = ctx->device;
+    lib->T = T;
+    lib->N = c.n;
+    lib->M = M;
+    lib->geom = *g;
+    lib->ox = c.ox;
+    lib->oy = c.oy;
+    memcpy(lib->pc, c.pc, sizeof c.pc);
+    const size_t H = (size_t)c.n * (c.n / 2 + 1);
+    cudaError_t e = cudaMalloc(&lib->spectra, sizeof(float2) * H * T);
+    if (e == cudaSuccess) e = cudaMalloc(&lib->quats, sizeof(double) * 4 * T);
+    if (e == cudaSuccess) e = cudaMalloc(&lib->master, sizeof(float) * 2 * (size_t)M * M);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        xcf_library_free(lib);
+        return fail(ctx, XCF_ERR_OOM, "xcf_build_library: allocation failed");
+    }
+    e = cudaMemcpyAsync(lib->quats, quats, sizeof(double) * 4 * T, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(lib->master, master, sizeof(float) * 2 * (size_t)M * M, cudaMemcpyDeviceToDevice, st);
+    // project and pre-process in chunks (bounded image scratch)
+    const ProjArgs pj = proj_args_cropped(g, c);
+    const PrepArgs ps = prep_args_square(c, r);
+    int *degen = nullptr;
+    float *img = nullptr;
+    for (int t0 = 0; e == cudaSuccess && t0 < T; t0 += kChunk) {
+        const int nt = T - t0 < kChunk ? T - t0 : kChunk;
+        if ((rc = scratch_t(ctx, S_IMG, (size_t)nt * c.n * c.n, &img)) ||
+            (rc = scratch_t(ctx, S_DEGEN, nt, &degen))) {
+            xcf_library_free(lib);
+            return rc;
+        }
+        e = launch_project(lib->master, M, lib->quats + 4 * (size_t)t0, nullptr, nullptr, nt, pj, img, st);
+        if (e == cudaSuccess) e = launch_prep(img, nt, ps, lib->spectra + H * t0, nullptr, degen, nullptr, st);
+        ctx->launches[XCF_STAGE_PROJECT] += 1;
+        ctx->launches[XCF_STAGE_PREP] += 1;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        xcf_library_free(lib);
+        return cuda_fail(ctx, e, "xcf_build_library");
+    }
+    *out = lib;
+    return XCF_OK;
+}
+
+int xcf_build_library_images(xcf_ctx *ctx, const float *images, const double *quats, int32_t T,
+                             const xcf_geometry *g, const float *master, int32_t M, xcf_library **out,
+                             void *stream) {
+    if (!ctx) return XCF_ERR_ARG;
+    if (!images || !quats || !g || !out || T <= 0 || (master && M < 2))
+        return fail(ctx, XCF_ERR_ARG, "xcf_build_library_images: bad argument");
+    *out = nullptr;
+    Crop c;
+    int rc = crop_of(g, 256, &c);
+    if (rc) return fail(ctx, rc, "xcf_build_library_images: detector too small");
+    if (!supported_n(c.n)) return fail(ctx, XCF_ERR_UNIMPLEMENTED, "xcf_build_library_images: N = 256 is not built");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const Resolved r = resolve(ctx->opt, c.n);
+    xcf_library *lib = new xcf_library();
+    lib->device = ctx->device;
+    lib->T = T;
+    lib->N = c.n;
+    lib->M = master ? M : 0;
+    lib->geom = *g;
+    lib->ox = c.ox;
+    lib->oy = c.oy;
+    memcpy(lib->pc, c.pc, sizeof c.pc);
+    const size_t H = (size_t)c.n * (c.n / 2 + 1);
+    cudaError_t e = cudaMalloc(&lib->spectra, sizeof(float2) * H * T);
+    if (e == cudaSuccess) e = cudaMalloc(&lib->quats, sizeof(double) * 4 * T);
+    if (e == cudaSuccess && master) e = cudaMalloc(&lib->master, sizeof(float) * 2 * (size_t)M * M);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        xcf_library_free(lib);
+        return fail(ctx, XCF_ERR_OOM, "xcf_build_library_images: allocation failed");
+    }
+    e = cudaMemcpyAsync(lib->quats, quats, sizeof(double) * 4 * T, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && master)
+        e = cudaMemcpyAsync(lib->master, master, sizeof(float) * 2 * (size_t)M * M, cudaMemcpyDeviceToDevice, st);
+    int *degen = nullptr;
+    if ((rc = scratch_t(ctx, S_DEGEN, T, &degen))) {
+        xcf_library_free(lib);
+        return rc;
+    }
+    if (e == cudaSuccess) e = launch_prep(images, T, prep_args(g, c, r), lib->spectra, nullptr, degen, nullptr, st);
+    ctx->launches[XCF_STAGE_PREP] += 1;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        xcf_library_free(lib);
+        return cuda_fail(ctx, e, "xcf_build_library_images");
+    }
+    *out = lib;
+    return XCF_OK;
+}
+
+int xcf_library_free(xcf_library *lib) {
+    if (!lib) return XCF_ERR_ARG;
+    cudaSetDevice(lib->device);
+    if (lib->spectra) cudaFree(lib->spectra);
+    if (lib->quats) cudaFree(lib->quats);
+    if (lib->master) cudaFree(lib->master);
+    delete lib;
+    return XCF_OK;
+}
+
+int xcf_library_info(const xcf_library *lib, int32_t *T, int32_t *N, const float **spectra) {
+    if (!lib) return XCF_ERR_ARG;
+    if (T) *T = lib->T;
+    if (N) *N = lib->N;
+    if (spectra) *spectra = reinterpret_cast<const float *>(lib->spectra);
+    return XCF_OK;
+}
+
+int xcf_index(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, int32_t *best,
+              float *peak, float *shift, void *stream) {
+    int rc = check_lib(ctx, lib);
+    if (rc) return rc;
+    if (P == 0) return XCF_OK;
+    if (!patterns || !best || !peak || !shift || P < 0) return fail(ctx, XCF_ERR_ARG, "xcf_index: bad argument");
+    cudaSetDevice(ctx->device);
+    const size_t img = (size_t)lib->geom.width * lib->geom.height;
+    for (int p0 = 0; p0 < P; p0 += kChunk) {
+        const int np = P - p0 < kChunk ? P - p0 : kChunk;
+        if ((rc = index_chunk(ctx, lib, patterns + img * p0, np, best + p0, peak + p0, shift + 2 * (size_t)p0,
+                              nullptr, (cudaStream_t)stream)))
+            return rc;
+    }
+    return XCF_OK;
+}
+
+int xcf_correlate_all(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, float *peaks,
+                      void *stream) {
+    int rc = check_lib(ctx, lib);
+    if (rc) return rc;
+    if (P == 0) return XCF_OK;
+    if (!patterns || !peaks || P < 0) return fail(ctx, XCF_ERR_ARG, "xcf_correlate_all: bad argument");
+    cudaSetDevice(ctx->device);
+    const size_t img = (size_t)lib->geom.width * lib->geom.height;
+    for (int p0 = 0; p0 < P; p0 += kChunk) {
+        const int np = P - p0 < kChunk ? P - p0 : kChunk;
+        if ((rc = index_chunk(ctx, lib, patterns + img * p0, np, nullptr, nullptr, nullptr,
+                              peaks + (size_t)lib->T * p0, (cudaStream_t)stream)))
+            return rc;
+    }
+    return XCF_OK;
+}
+
+int xcf_refine(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, const double *seeds,
+               const double *pcs, double *quats, float *peak, int32_t *iters, void *stream) {
+    int rc = check_lib(ctx, lib);
+    if (rc) return rc;
+    if (P == 0) return XCF_OK;
+    if (!patterns || !seeds || !quats || !peak || !iters || P < 0)
+        return fail(ctx, XCF_ERR_ARG, "xcf_refine: bad argument");
+    if (!lib->master) return fail(ctx, XCF_ERR_ARG, "xcf_refine: library has no master pattern");
+    const Resolved r = resolve(ctx->opt, lib->N);
+    if (r.neta < 8 || r.neta > 1024 || (r.neta & (r.neta - 1)) || r.nr < 1 || r.rmin <= 0 ||
+        r.rmax <= r.rmin || r.rmax > lib->N / 2.0 - 1.0)
+        return fail(ctx, XCF_ERR_ARG, "xcf_refine: log-polar options out of range");
+    cudaSetDevice(ctx->device);
+    const size_t img = (size_t)lib->geom.width * lib->geom.height;
+    for (int p0 = 0; p0 < P; p0 += kChunk) {
+        const int np = P - p0 < kChunk ? P - p0 : kChunk;
+        if ((rc = refine_chunk(ctx, lib, patterns + img * p0, np, seeds + 4 * (size_t)p0,
+                               pcs ? pcs + 3 * (size_t)p0 : nullptr, quats + 4 * (size_t)p0, peak + p0,
+                               iters + p0, (cudaStream_t)stream)))
+            return rc;
+    }
+    return XCF_OK;
+}
+
+int xcf_disorientation(xcf_ctx *ctx, const double *qa, const double *qb, int32_t n, double *out, void *stream) {
+    if (!ctx) return XCF_ERR_ARG;
+    if (n == 0) return XCF_OK;
+    if (!qa || !qb || !out || n < 0) return fail(ctx, XCF_ERR_ARG, "xcf_disorientation: bad argument");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_disorientation(qa, qb, n, out, st), "disorientation");
+    return XCF_OK;
+}
+
+int xcf_index_refine(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, const double *pcs,
+                     int32_t *best, float *peak, float *shift, double *quats, float *rpeak, int32_t *iters,
+                     void *stream) {
+    int rc = check_lib(ctx, lib);
+    if (rc) return rc;
+    if (P == 0) return XCF_OK;
+    if (!patterns || !best || !peak || !shift || !quats || !rpeak || !iters || P < 0)
+        return fail(ctx, XCF_ERR_ARG, "xcf_index_refine: bad argument");
+    if (!lib->master) return fail(ctx, XCF_ERR_ARG, "xcf_index_refine: library has no master pattern");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t img = (size_t)lib->geom.width * lib->geom.height;
+    for (int p0 = 0; p0 < P; p0 += kChunk) {
+        const int np = P - p0 < kChunk ? P - p0 : kChunk;
+        double *seeds;
+        if ((rc = index_chunk(ctx, lib, patterns + img * p0, np, best + p0, peak + p0, shift + 2 * (size_t)p0,
+                              nullptr, st)))
+            return rc;
+        if ((rc = scratch_t(ctx, S_SEEDS, (size_t)np * 4, &seeds))) return rc;
+        XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_gather_seeds(lib->quats, best + p0, np, seeds, st), "seeds");
+        if ((rc = refine_chunk(ctx, lib, patterns + img * p0, np, seeds, pcs ? pcs + 3 * (size_t)p0 : nullptr,
+                               quats + 4 * (size_t)p0, rpeak + p0, iters + p0, st)))
+            return rc;
+    }
+    return XCF_OK;
+}
+
+int xcf_index_refine_host(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P,
+                          const double *pcs, int32_t chunk, int32_t *best, float *peak, float *shift,
+                          double *quats, float *rpeak, int32_t *iters) {
+    int rc = check_lib(ctx, lib);
+    if (rc) return rc;
+    if (P == 0) return XCF_OK;
+    if (!patterns || !best || !peak || !shift || !quats || !rpeak || !iters || P < 0)
+        return fail(ctx, XCF_ERR_ARG, "xcf_index_refine_host: bad argument");
+    if (chunk <= 0 || chunk > kChunk) chunk = kChunk;
+    cudaSetDevice(ctx->device);
+    const size_t img = (size_t)lib->geom.width * lib->geom.height;
+    cudaStream_t st = nullptr;
+    XCF_CHECK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream");
+    // device layout of one chunk: patterns | pcs | outputs
+    float *dpat;
+    double *dpcs = nullptr, *dq, *dseeds;
+    int *dbest, *diters;
+    float *dpeak, *dshift, *drpeak;
+    const size_t out_bytes = (size_t)chunk * (4 + 4 + 8 + 32 + 4 + 4) + 256;
+    char *dout;
+    if ((rc = scratch_t(ctx, S_IO_PAT, img * chunk, &dpat)) ||
+        (pcs && (rc = scratch_t(ctx, S_IO_PCS, (size_t)chunk * 3, &dpcs))) ||
+        (rc = scratch_t(ctx, S_IO_OUT, out_bytes, &dout)) ||
+        (rc = scratch_t(ctx, S_SEEDS, (size_t)chunk * 4, &dseeds))) {
+        cudaStreamDestroy(st);
+        return rc;
+    }
+    dq = reinterpret_cast<double *>(dout);
+    dbest = reinterpret_cast<int *>(dq + 4 * (size_t)chunk);
+    diters = dbest + chunk;
+    dpeak = reinterpret_cast<float *>(diters + chunk);
+    dshift = dpeak + chunk;
+    drpeak = dshift + 2 * (size_t)chunk;
+    int status = XCF_OK;
+    for (int p0 = 0; p0 < P && status == XCF_OK; p0 += chunk) {
+        const int np = P - p0 < chunk ? P - p0 : chunk;
+        cudaError_t e = cudaMemcpyAsync(dpat, patterns + img * p0, sizeof(float) * img * np, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && pcs)
+            e = cudaMemcpyAsync(dpcs, pcs + 3 * (size_t)p0, sizeof(double) * 3 * np, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) { status = cuda_fail(ctx, e, "H2D"); break; }
+        if ((status = index_chunk(ctx, lib, dpat, np, dbest, dpeak, dshift, nullptr, st))) break;
+        e = launch_gather_seeds(lib->quats, dbest, np, dseeds, st);
+        if (e != cudaSuccess) { status = cuda_fail(ctx, e, "seeds"); break; }
+        ctx->launches[XCF_STAGE_OTHER] += 1;
+        if ((status = refine_chunk(ctx, lib, dpat, np, dseeds, dpcs, dq, drpeak, diters, st))) break;
+        e = cudaMemcpyAsync(best + p0, dbest, sizeof(int) * np, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(peak + p0, dpeak, sizeof(float) * np, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(shift + 2 * (size_t)p0, dshift, sizeof(float) * 2 * np, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(quats + 4 * (size_t)p0, dq, sizeof(double) * 4 * np, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rpeak + p0, drpeak, sizeof(float) * np, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(iters + p0, diters, sizeof(int) * np, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) status = cuda_fail(ctx, e, "xcf_index_refine_host");
+    }
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    return status;
+}
+
+int xcf_profile_enable(xcf_ctx *ctx, int on) {
+    if (!ctx) return XCF_ERR_ARG;
+    ctx->timing = on != 0;
+    return XCF_OK;
+}
+
+int xcf_profile_read(xcf_ctx *ctx, double *ms, int64_t *launches, int reset) {
+    if (!ctx) return XCF_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    int status = XCF_OK;
+    for (auto &r : ctx->recs) {
+        float t = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess && status == XCF_OK) status = cuda_fail(ctx, e, "xcf_profile_read");
+        ctx->ms[r.stage] += t;
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    ctx->recs.clear();
+    for (int i = 0; i < XCF_NUM_STAGES; ++i) {
+        if (ms) ms[i] = ctx->ms[i];
+        if (launches) launches[i] = ctx->launches[i];
+        if (reset) {
+            ctx->ms[i] = 0.0;
+            ctx->launches[i] = 0;
+        }
+    }
+    return status;
+}
+
+}  // extern "C"

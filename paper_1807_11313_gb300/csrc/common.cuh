@@ -1,0 +1,136 @@
+// Shared device helpers of the ebsdxcf CUDA library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#define XCF_PI 3.14159265358979323846
+
+// ---------------------------------------------------------------- complex
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+__device__ __forceinline__ float2 c_mulcj(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
+// multiply by +i / -i
+__device__ __forceinline__ float2 c_mul_pi(float2 a) { return make_float2(-a.y, a.x); }
+__device__ __forceinline__ float2 c_mul_mi(float2 a) { return make_float2(a.y, -a.x); }
+
+// ---------------------------------------------------- compile-time twiddles
+// cos / sin of 2 pi k / n evaluated at compile time by Taylor series after
+// exact range reduction (k mod n), so every constant below is a literal.
+__host__ __device__ constexpr double cx_taylor_sin(double x) {
+    double term = x, sum = x;
+    for (int i = 1; i < 30; ++i) {
+        term *= -x * x / ((2.0 * i) * (2.0 * i + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double cx_taylor_cos(double x) {
+    double term = 1.0, sum = 1.0;
+    for (int i = 1; i < 30; ++i) {
+        term *= -x * x / ((2.0 * i - 1.0) * (2.0 * i));
+        sum += term;
+    }
+    return sum;
+}
+// angle 2 pi k / n reduced to [-pi, pi]
+__host__ __device__ constexpr double cx_angle(long k, long n) {
+    long r = ((k % n) + n) % n;
+    if (2 * r > n) r -= n;
+    return 2.0 * XCF_PI * (double)r / (double)n;
+}
+template <long K, long N, int SIGN>
+struct Tw {
+    static constexpr double a = cx_angle(K, N);
+    static constexpr float re = (float)cx_taylor_cos(a);
+    static constexpr float im = (float)(SIGN * cx_taylor_sin(a));
+};
+
+// x * exp(SIGN 2 pi i K / N) with the trivial cases written out
+template <long K, long N, int SIGN>
+__device__ __forceinline__ float2 tw_mul(float2 x) {
+    constexpr long r = ((K % N) + N) % N;
+    if constexpr (r == 0) {
+        return x;
+    } else if constexpr (4 * r == N) {
+        return SIGN > 0 ? c_mul_pi(x) : c_mul_mi(x);
+    } else if constexpr (2 * r == N) {
+        return make_float2(-x.x, -x.y);
+    } else if constexpr (4 * r == 3 * N) {
+        return SIGN > 0 ? c_mul_mi(x) : c_mul_pi(x);
+    } else if constexpr (8 * r == N || 8 * r == 3 * N || 8 * r == 5 * N || 8 * r == 7 * N) {
+        // (+-1 +- i)/sqrt(2): two multiplies, two adds
+        constexpr float h = 0.70710678118654752440f;
+        constexpr float cr = Tw<K, N, SIGN>::re, ci = Tw<K, N, SIGN>::im;
+        float s = (cr > 0 ? 1.f : -1.f), t = (ci > 0 ? 1.f : -1.f);
+        // (x.x + i x.y)(s + i t) h
+        return make_float2(h * (s * x.x - t * x.y), h * (s * x.y + t * x.x));
+    } else {
+        constexpr float cr = Tw<K, N, SIGN>::re, ci = Tw<K, N, SIGN>::im;
+        return make_float2(fmaf(x.x, cr, -x.y * ci), fmaf(x.x, ci, x.y * cr));
+    }
+}
+
+// ------------------------------------------------------------ static_for
+template <int I, int E>
+struct StaticFor {
+    template <class F>
+    __device__ __forceinline__ static void run(F &&f) {
+        if constexpr (I < E) {
+            f(std::integral_constant<int, I>{});
+            StaticFor<I + 1, E>::run(f);
+        }
+    }
+};
+
+__host__ __device__ constexpr int cx_log2(int n) { return n <= 1 ? 0 : 1 + cx_log2(n / 2); }
+__host__ __device__ constexpr int cx_bitrev(int x, int bits) {
+    int r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1) << (bits - 1 - i);
+    return r;
+}
+
+// In-register radix-2 decimation-in-frequency FFT of R points,
+// x[j] <- sum_i x[i] exp(SIGN 2 pi i i j / R) (unscaled).  Input in natural
+// order, output in bit-reversed order: after the call x[p] holds X[bitrev(p)].
+template <int R, int SIGN>
+__device__ __forceinline__ void fft_reg_dif(float2 (&x)[R]) {
+    constexpr int LOG = cx_log2(R);
+    StaticFor<0, LOG>::run([&](auto stage) {
+        constexpr int span = R >> (decltype(stage)::value + 1);
+        StaticFor<0, R / (2 * span)>::run([&](auto blk) {
+            StaticFor<0, span>::run([&](auto k) {
+                constexpr int kk = decltype(k)::value;
+                constexpr int i0 = decltype(blk)::value * 2 * span + kk;
+                constexpr int i1 = i0 + span;
+                float2 a = x[i0], b = x[i1];
+                x[i0] = c_add(a, b);
+                x[i1] = tw_mul<kk, 2 * span, SIGN>(c_sub(a, b));
+            });
+        });
+    });
+}
+
+// order-preserving float -> uint32 (larger float -> larger key)
+__device__ __forceinline__ uint32_t float_to_ordered(float f) {
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ordered_to_float(uint32_t k) {
+    uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    return __uint_as_float(u);
+}
+
+// key = (ordered peak << 32) | (0xffffffff - t): max key = highest peak,
+// lowest template index on ties
+__device__ __forceinline__ unsigned long long pack_key(float v, int t) {
+    return ((unsigned long long)float_to_ordered(v) << 32) | (unsigned long long)(0xffffffffu - (uint32_t)t);
+}

@@ -1,0 +1,401 @@
+// Geometry and refinement kernels: gnomonic reprojection of the master
+// pattern, log-polar resampling, the angular correlation, float64 orientation
+// updates and the cubic disorientation.
+//
+// Paper: "SO(3) Library Generation" (reprojection of the master pattern),
+// "Orientation and Pattern Centre Refinement" (Eq. 7, Fig. 6: shifts to
+// rotations about detector x / y, log-polar transform for z), second
+// "Equation 6" (disorientation with the 24 cubic operators).
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace {
+
+// ----------------------------------------------------------- quaternions
+struct Q { double w, x, y, z; };
+
+__device__ __forceinline__ Q qmul(const Q &a, const Q &b) {
+    return {a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z,
+            a.w * b.x + a.x * b.w + a.y * b.z - a.z * b.y,
+            a.w * b.y - a.x * b.z + a.y * b.w + a.z * b.x,
+            a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w};
+}
+__device__ __forceinline__ Q qconj(const Q &a) { return {a.w, -a.x, -a.y, -a.z}; }
+__device__ __forceinline__ Q qcanon(Q a) {
+    double s = sqrt(a.w * a.w + a.x * a.x + a.y * a.y + a.z * a.z);
+    if (a.w < 0) s = -s;
+    return {a.w / s, a.x / s, a.y / s, a.z / s};
+}
+__device__ __forceinline__ Q qload(const double *p) { return {p[0], p[1], p[2], p[3]}; }
+__device__ __forceinline__ void qstore(double *p, const Q &a) {
+    p[0] = a.w; p[1] = a.x; p[2] = a.y; p[3] = a.z;
+}
+// orientation whose template is the template of q rotated by the
+// detector-frame rotation R: q (x) qs (x) conj(R) (x) conj(qs), qs = detector
+// -> sample rotation about x by alpha
+__device__ __forceinline__ Q rotate_in_detector(const Q &q, const Q &R, double alpha) {
+    double s, c;
+    sincos(0.5 * alpha, &s, &c);
+    const Q qs = {c, s, 0.0, 0.0};
+    return qcanon(qmul(qmul(qmul(q, qs), qconj(R)), qconj(qs)));
+}
+
+// ------------------------------------------------------ Lambert lookup
+// Rosca equal-area square of a hemisphere, then bilinear interpolation of
+// the M x M grid of cell centres, clamped at the edges.
+__device__ __forceinline__ float master_lookup(const float *__restrict__ master, int M, float x, float y,
+                                               float z) {
+    const float az = fabsf(z);
+    const float s2 = x * x + y * y;
+    float X = 0.f, Y = 0.f;
+    if (s2 > 0.f) {
+        const float qv = sqrtf(2.f * s2 / (1.f + az));   // sqrt(2 (1 - |z|)), cancellation-free
+        const float sp = 0.88622692545275801365f;         // sqrt(pi) / 2
+        const float ts = 1.12837916709551257390f;         // 2 / sqrt(pi)
+        if (fabsf(y) <= fabsf(x)) {
+            const float sg = x >= 0.f ? 1.f : -1.f;
+            X = sg * qv * sp;
+            Y = sg * qv * ts * atanf(y / x);
+        } else {
+            const float sg = y >= 0.f ? 1.f : -1.f;
+            X = sg * qv * ts * atanf(x / y);
+            Y = sg * qv * sp;
+        }
+    }
+    const float invL = 0.79788456080286535588f;           // 1 / sqrt(pi / 2)
+    float fx = (X * invL + 1.f) * (0.5f * M) - 0.5f;
+    float fy = (Y * invL + 1.f) * (0.5f * M) - 0.5f;
+    fx = fminf(fmaxf(fx, 0.f), (float)(M - 1));
+    fy = fminf(fmaxf(fy, 0.f), (float)(M - 1));
+    int i0 = min((int)floorf(fx), M - 2), j0 = min((int)floorf(fy), M - 2);
+    const float tx = fx - i0, ty = fy - j0;
+    const float *g = master + (z >= 0.f ? 0 : (size_t)M * M) + (size_t)j0 * M + i0;
+    const float a = __ldg(g), b = __ldg(g + 1), c = __ldg(g + M), d = __ldg(g + M + 1);
+    return (1.f - ty) * ((1.f - tx) * a + tx * b) + ty * ((1.f - tx) * c + tx * d);
+}
+
+// ---------------------------------------------------------- projection
+__global__ void __launch_bounds__(256) k_project(const float *__restrict__ master, int M,
+                                                 const double *__restrict__ quats,
+                                                 const double *__restrict__ pcs,
+                                                 const int *__restrict__ active, ProjArgs a,
+                                                 float *__restrict__ out) {
+    const int p = blockIdx.y;
+    if (active && !active[p]) return;
+    __shared__ float G[9];
+    __shared__ float pc[3];
+    if (threadIdx.x == 0) {
+        const Q q = qcanon(qload(quats + 4 * (size_t)p));
+        double R[9];
+        R[0] = 1 - 2 * (q.y * q.y + q.z * q.z); R[1] = 2 * (q.x * q.y - q.w * q.z); R[2] = 2 * (q.x * q.z + q.w * q.y);
+        R[3] = 2 * (q.x * q.y + q.w * q.z); R[4] = 1 - 2 * (q.x * q.x + q.z * q.z); R[5] = 2 * (q.y * q.z - q.w * q.x);
+        R[6] = 2 * (q.x * q.z - q.w * q.y); R[7] = 2 * (q.y * q.z + q.w * q.x); R[8] = 1 - 2 * (q.x * q.x + q.y * q.y);
+        double sa, ca;
+        sincos(a.alpha, &sa, &ca);
+        // G = R(q) Rx(alpha): detector direction -> crystal direction
+        for (int i = 0; i < 3; ++i) {
+            G[3 * i + 0] = (float)R[3 * i + 0];
+            G[3 * i + 1] = (float)(R[3 * i + 1] * ca + R[3 * i + 2] * sa);
+            G[3 * i + 2] = (float)(-R[3 * i + 1] * sa + R[3 * i + 2] * ca);
+        }
+        double px = a.pcx, py = a.pcy, pz = a.pcz;
+        if (pcs) { px = pcs[3 * (size_t)p]; py = pcs[3 * (size_t)p + 1]; pz = pcs[3 * (size_t)p + 2]; }
+        pc[0] = (float)(px * a.W);
+        pc[1] = (float)(py * a.H);
+        pc[2] = (float)(pz * a.W);
+    }
+    __syncthreads();
+    const int npx = a.nx * a.ny;
+    float *dst = out + (size_t)p * npx;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < npx; idx += gridDim.x * blockDim.x) {
+        const int i = idx / a.nx, j = idx % a.nx;
+        float dx = (float)(a.ox + j) + 0.5f - pc[0];
+        float dy = pc[1] - ((float)(a.oy + i) + 0.5f);
+        float dz = pc[2];
+        const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= inv; dy *= inv; dz *= inv;
+        const float cx = G[0] * dx + G[1] * dy + G[2] * dz;
+        const float cy = G[3] * dx + G[4] * dy + G[5] * dz;
+        const float cz = G[6] * dx + G[7] * dy + G[8] * dz;
+        dst[idx] = master_lookup(master, M, cx, cy, cz);
+    }
+}
+
+// ------------------------------------------------------------ log-polar
+__global__ void __launch_bounds__(256) k_logpolar(const float *__restrict__ spatial,
+                                                  const int *__restrict__ active, int N, int nr,
+                                                  int neta, float rmin, float rmax,
+                                                  float *__restrict__ out) {
+    const int p = blockIdx.y;
+    if (active && !active[p]) return;
+    const float *img = spatial + (size_t)p * N * N;
+    const float c = 0.5f * N - 0.5f;
+    const float lr = logf(rmax / rmin);
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nr * neta; idx += gridDim.x * blockDim.x) {
+        const int m = idx / neta, l = idx % neta;
+        const float r = rmin * expf(lr * (nr > 1 ? (float)m / (nr - 1) : 0.f));
+        float sn, cs;
+        sincospif(2.f * l / neta, &sn, &cs);
+        const float fx = c + r * cs, fy = c - r * sn;
+        int x0 = (int)floorf(fx), y0 = (int)floorf(fy);
+        x0 = min(max(x0, 0), N - 2);
+        y0 = min(max(y0, 0), N - 2);
+        const float tx = fx - x0, ty = fy - y0;
+        const float *g = img + y0 * N + x0;
+        out[(size_t)p * nr * neta + idx] =
+            (1.f - ty) * ((1.f - tx) * g[0] + tx * g[1]) + ty * ((1.f - tx) * g[N] + tx * g[N + 1]);
+    }
+}
+
+__device__ double block_sum_d(double v, double *sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[32] = v;
+    }
+    __syncthreads();
+    double r = sh[32];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ float parabola(float cm, float c0, float cp) {
+    float den = cm - 2.f * c0 + cp;
+    if (!(den < 0.f)) return 0.f;
+    float d = (cm - cp) / (2.f * den);
+    return fminf(0.5f, fmaxf(-0.5f, d));
+}
+
+// ------------------------------------------------ angular correlation + Z
+// c(D) = sum_m sum_l a[m][l] b[m][(l + D) mod neta] / (|a| |b|) on mean-free
+// log-polar images (a = template, b = pattern); each thread accumulates 8
+// consecutive shifts over a slice of the radii, sliding along l in blocks of
+// 8 so that every loaded value feeds 8 fused multiply-adds.
+constexpr int kEtaThreads = 256;
+__global__ void __launch_bounds__(kEtaThreads) k_eta_update(const float *__restrict__ lpT,
+                                                            const float *__restrict__ lpP, int nr,
+                                                            int neta, const double *__restrict__ q0s,
+                                                            const double *__restrict__ q1s,
+                                                            double alpha, double tol_deg,
+                                                            int *__restrict__ active,
+                                                            int *__restrict__ iters,
+                                                            double *__restrict__ q_out) {
+    const int p = blockIdx.x;
+    if (!active[p]) return;
+    extern __shared__ float4 smem_raw[];
+    float *sa = reinterpret_cast<float *>(smem_raw);
+    float *sb = sa + nr * neta;
+    float *cacc = sb + nr * neta;           // [row groups][neta]
+    __shared__ double red[33];
+    const int tot = nr * neta, tid = threadIdx.x;
+    const float *ga = lpT + (size_t)p * tot, *gb = lpP + (size_t)p * tot;
+    double s1 = 0, s2 = 0;
+    for (int i = tid; i < tot; i += kEtaThreads) {
+        float x = ga[i], y = gb[i];
+        sa[i] = x; sb[i] = y;
+        s1 += x; s2 += y;
+    }
+    const double ma = block_sum_d(s1, red) / tot;
+    const double mb = block_sum_d(s2, red) / tot;
+    double n1 = 0, n2 = 0;
+    for (int i = tid; i < tot; i += kEtaThreads) {
+        float x = sa[i] - (float)ma, y = sb[i] - (float)mb;
+        sa[i] = x; sb[i] = y;
+        n1 += (double)x * x; n2 += (double)y * y;
+    }
+    const double na = block_sum_d(n1, red), nb = block_sum_d(n2, red);
+    double nrm = sqrt(na * nb);
+    if (!(nrm > 0)) nrm = 1.0;
+    const int G = neta / 8;                    // groups of 8 shifts
+    const int RG = kEtaThreads / G;            // row groups
+    const int gidx = tid % G, rg = tid / G;
+    if (rg < RG) {
+        float acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+        const int D0 = gidx * 8;
+        for (int m = rg; m < nr; m += RG) {
+            const float *ar = sa + m * neta, *br = sb + m * neta;
+            for (int l = 0; l < neta; l += 8) {
+                float av[8], bv[16];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) av[j] = ar[l + j];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) bv[j] = br[(l + D0 + j) & (neta - 1)];
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) acc[k] = fmaf(av[j], bv[j + k], acc[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) cacc[rg * neta + D0 + k] = acc[k];
+    }
+    __syncthreads();
+    // finish the sum over row groups in float64, then argmax
+    __shared__ float cfin[1024];
+    for (int D = tid; D < neta; D += kEtaThreads) {
+        double s = 0;
+        for (int g = 0; g < RG; ++g) s += cacc[g * neta + D];
+        cfin[D] = (float)(s / nrm);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int best = 0;
+        for (int D = 1; D < neta; ++D) if (cfin[D] > cfin[best]) best = D;
+        const float off = parabola(cfin[(best + neta - 1) % neta], cfin[best], cfin[(best + 1) % neta]);
+        const double deta = (double)(best < neta / 2 ? best : best - neta) + off;
+        const double tz = 2.0 * XCF_PI * deta / neta;
+        double s, c;
+        sincos(0.5 * tz, &s, &c);
+        const Q Rz = {c, 0.0, 0.0, s};
+        const Q q0 = qload(q0s + 4 * (size_t)p);
+        const Q q2 = rotate_in_detector(qload(q1s + 4 * (size_t)p), Rz, alpha);
+        double dot = fabs(q2.w * q0.w + q2.x * q0.x + q2.y * q0.y + q2.z * q0.z);
+        dot = fmin(dot, 1.0);
+        const double upd = 2.0 * acos(dot) * 180.0 / XCF_PI;
+        qstore(q_out + 4 * (size_t)p, q2);
+        iters[p] += 1;
+        if (upd < tol_deg) active[p] = 0;
+    }
+}
+
+__global__ void k_update_xy(const double *__restrict__ qs, const float *__restrict__ shift,
+                            const double *__restrict__ pcs, double pcz_def, int W, double alpha,
+                            const int *__restrict__ active, int P, double *__restrict__ q1s) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P || !active[p]) return;
+    const double L = (pcs ? pcs[3 * (size_t)p + 2] : pcz_def) * W;
+    const double tx = atan((double)shift[2 * p + 1] / L), ty = atan((double)shift[2 * p] / L);
+    double sx, cx, sy, cy;
+    sincos(0.5 * tx, &sx, &cx);
+    sincos(0.5 * ty, &sy, &cy);
+    const Q R = qmul(Q{cx, sx, 0.0, 0.0}, Q{cy, 0.0, sy, 0.0});
+    qstore(q1s + 4 * (size_t)p, rotate_in_detector(qload(qs + 4 * (size_t)p), R, alpha));
+}
+
+__global__ void k_gather_seeds(const double *__restrict__ lib_quats, const int *__restrict__ best, int P,
+                               double *__restrict__ seeds) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int t = best[p];
+    for (int k = 0; k < 4; ++k) seeds[4 * (size_t)p + k] = t >= 0 ? lib_quats[4 * (size_t)t + k] : (k == 0 ? 1.0 : 0.0);
+}
+
+__global__ void k_init_refine(const int *__restrict__ degen, int P, int *__restrict__ active,
+                              int *__restrict__ iters, float *__restrict__ peak) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    active[p] = degen[p] ? 0 : 1;
+    iters[p] = 0;
+    peak[p] = 0.f;
+}
+
+// the 24 proper rotations of the cubic group 432, (w, x, y, z)
+__constant__ double c_cubic[24][4] = {
+    {1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1},
+    {0.70710678118654752440, 0.70710678118654752440, 0, 0}, {0.70710678118654752440, -0.70710678118654752440, 0, 0},
+    {0.70710678118654752440, 0, 0.70710678118654752440, 0}, {0.70710678118654752440, 0, -0.70710678118654752440, 0},
+    {0.70710678118654752440, 0, 0, 0.70710678118654752440}, {0.70710678118654752440, 0, 0, -0.70710678118654752440},
+    {0.5, 0.5, 0.5, 0.5}, {0.5, 0.5, 0.5, -0.5}, {0.5, 0.5, -0.5, 0.5}, {0.5, 0.5, -0.5, -0.5},
+    {0.5, -0.5, 0.5, 0.5}, {0.5, -0.5, 0.5, -0.5}, {0.5, -0.5, -0.5, 0.5}, {0.5, -0.5, -0.5, -0.5},
+    {0, 0.70710678118654752440, 0.70710678118654752440, 0}, {0, 0.70710678118654752440, -0.70710678118654752440, 0},
+    {0, 0.70710678118654752440, 0, 0.70710678118654752440}, {0, 0.70710678118654752440, 0, -0.70710678118654752440},
+    {0, 0, 0.70710678118654752440, 0.70710678118654752440}, {0, 0, 0.70710678118654752440, -0.70710678118654752440},
+};
+
+__global__ void k_disorientation(const double *__restrict__ qa, const double *__restrict__ qb, int n,
+                                 double *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Q m = qmul(qload(qa + 4 * (size_t)i), qconj(qload(qb + 4 * (size_t)i)));
+    const double nm = sqrt(m.w * m.w + m.x * m.x + m.y * m.y + m.z * m.z);
+    double best = 0.0;
+    for (int k = 0; k < 24; ++k) {
+        const double w = c_cubic[k][0] * m.w - c_cubic[k][1] * m.x - c_cubic[k][2] * m.y - c_cubic[k][3] * m.z;
+        best = fmax(best, fabs(w) / nm);
+    }
+    out[i] = 2.0 * acos(fmin(best, 1.0)) * 180.0 / XCF_PI;
+}
+
+}  // namespace
+
+cudaError_t launch_project(const float *master, int M, const double *quats, const double *pcs,
+                           const int *active, int P, const ProjArgs &a, float *out, cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    const size_t npx = (size_t)a.nx * a.ny;
+    for (int p0 = 0; p0 < P; p0 += 65535) {          // grid.y limit
+        const int np = P - p0 < 65535 ? P - p0 : 65535;
+        dim3 grid((unsigned)((npx + 255) / 256), np);
+        k_project<<<grid, 256, 0, st>>>(master, M, quats + 4 * (size_t)p0, pcs ? pcs + 3 * (size_t)p0 : nullptr,
+                                        active ? active + p0 : nullptr, a, out + npx * p0);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_logpolar(const float *spatial, const int *active, int P, int N, int nr, int neta,
+                            float rmin, float rmax, float *out, cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    for (int p0 = 0; p0 < P; p0 += 65535) {          // grid.y limit
+        const int np = P - p0 < 65535 ? P - p0 : 65535;
+        dim3 grid((nr * neta + 255) / 256, np);
+        k_logpolar<<<grid, 256, 0, st>>>(spatial + (size_t)N * N * p0, active ? active + p0 : nullptr, N, nr,
+                                         neta, rmin, rmax, out + (size_t)nr * neta * p0);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_update_xy(const double *q, const float *shift, const double *pcs, double pcz_def,
+                             int W, double alpha, const int *active, int P, double *q1,
+                             cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    k_update_xy<<<(P + 127) / 128, 128, 0, st>>>(q, shift, pcs, pcz_def, W, alpha, active, P, q1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eta_update(const float *lpT, const float *lpP, int nr, int neta, const double *q0,
+                              const double *q1, double alpha, double tol_deg, int *active,
+                              int *iters, double *q_out, int P, cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    // requirements of the blocked correlation: neta a power of two, 8 <= neta <= 1024
+    if (neta < 8 || neta > 1024 || (neta & (neta - 1))) return cudaErrorInvalidValue;
+    const int G = neta / 8;
+    const int RG = G <= kEtaThreads ? kEtaThreads / G : 0;
+    if (RG == 0) return cudaErrorInvalidValue;
+    const size_t sm = sizeof(float) * ((size_t)2 * nr * neta + (size_t)RG * neta);
+    cudaError_t e = cudaFuncSetAttribute(k_eta_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_eta_update<<<P, kEtaThreads, sm, st>>>(lpT, lpP, nr, neta, q0, q1, alpha, tol_deg, active, iters, q_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_seeds(const double *lib_quats, const int *best, int P, double *seeds,
+                                cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    k_gather_seeds<<<(P + 127) / 128, 128, 0, st>>>(lib_quats, best, P, seeds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_refine(const int *degen, int P, int *active, int *iters, float *peak,
+                               cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    k_init_refine<<<(P + 127) / 128, 128, 0, st>>>(degen, P, active, iters, peak);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_disorientation(const double *qa, const double *qb, int n, double *out,
+                                  cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_disorientation<<<(n + 127) / 128, 128, 0, st>>>(qa, qb, n, out);
+    return cudaGetLastError();
+}

@@ -1,0 +1,246 @@
+// All-pairs XCF search for 128 x 128 detectors (the hot loop of the indexer).
+//
+// Paper: Eqs. 3 and 6 (correlation surface r(s) = sum_k conj(S_t) S_p
+// exp(+2 pi i k.s / N)), Fig. 1 B-C (best template by peak height), Fig. 5 /
+// Discussion (one inverse FFT per pattern-template pair dominates the cost).
+//
+// One CTA (256 threads, one per SM) keeps one pattern's half spectrum in
+// shared memory and streams the library's half spectra from L2/HBM, two
+// templates per inverse FFT: Z = X1 + i X2 with X_j = conj(S_tj) S_p extended
+// to the full spectrum by Hermitian symmetry, so that Re(IFFT Z) and
+// Im(IFFT Z) are the two real correlation surfaces.  The 128 x 128 inverse FFT
+// runs in three register rounds separated by two shared-memory transposes:
+//   round 1: thread (q, l) owns stored column q and rows u = l + 4m: two
+//            32-point FFTs over m (of X1 and X2), twiddle W128^(l k2); the
+//            conjugate-symmetric partner column 128 - q is written from the
+//            same registers (conj(A1) + i conj(A2) at sub-sequence 4 - l);
+//   round 2: thread (k2, g): radix-4 over l completes the column transform
+//            for rows k2 + 32 k1, then 16-point FFTs over the columns
+//            g + 8 i and twiddle W128^(g k3);
+//   round 3: thread (r, h): 8-point FFTs over g give row r, columns
+//            k3 + 16 k4, of both surfaces; the max of each is reduced.
+// No surface is written to global memory; only the per-pattern best key (and
+// optionally every per-pair peak) leave the kernel.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace {
+
+constexpr int N = 128;
+constexpr int HW = 65;          // stored columns of a half spectrum
+constexpr int SPEC = N * HW;    // complex values per half spectrum
+constexpr int NT = 256;
+
+// shared layout (float2 units)
+constexpr int OFF_SP = 0;                 // pattern half spectrum [128][65]
+constexpr int OFF_BUF = SPEC;             // transpose buffer, 16384
+constexpr int OFF_TW1 = OFF_BUF + N * N;  // W128^(l k2) at [k2][l]
+constexpr int OFF_TW2 = OFF_TW1 + 128;    // W128^(g k3) at [k3][g]
+constexpr int OFF_RED = OFF_TW2 + 128;    // [2][8 warps] (max re, max im)
+constexpr int SMEM_F2 = OFF_RED + 16;
+constexpr size_t SMEM_BYTES = sizeof(float2) * SMEM_F2;
+
+// round-1 output A[l][k2][v]; v swizzled by k2 so that round 2's reads of
+// four k2 rows land in distinct bank halves
+__device__ __forceinline__ int idxA(int l, int k2, int v) {
+    return ((l * 32 + k2) << 7) + (v ^ ((k2 & 3) << 3));
+}
+// round-2 output B[r][k3][g]; k3 and g swizzled by r for conflict-free
+// stores (round 2) and loads (round 3)
+__device__ __forceinline__ int idxB(int r, int k3, int g) {
+    return (r << 7) + ((k3 ^ (r & 1)) << 3) + (g ^ ((r >> 1) & 7));
+}
+
+__global__ void __launch_bounds__(NT, 1)
+k_search128(const float2 *__restrict__ St, int T, const float2 *__restrict__ Sp,
+            const int *__restrict__ degen, int pairs_per_cta,
+            unsigned long long *__restrict__ keys, float *__restrict__ peaks_all) {
+    extern __shared__ float4 smem_raw[];
+    float2 *sm = reinterpret_cast<float2 *>(smem_raw);
+    float2 *sp = sm + OFF_SP;
+    float2 *buf = sm + OFF_BUF;
+    float2 *tw1 = sm + OFF_TW1;
+    float2 *tw2 = sm + OFF_TW2;
+    float2 *red = sm + OFF_RED;
+
+    const int p = blockIdx.y;
+    if (degen[p]) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int npairs = (T + 1) / 2;
+    const int pb = blockIdx.x * pairs_per_cta;
+    const int pe = min(npairs, pb + pairs_per_cta);
+    if (pb >= pe) return;
+
+    {   // pattern spectrum and twiddle tables
+        const float4 *src = reinterpret_cast<const float4 *>(Sp + (size_t)p * SPEC);
+        float4 *dst = reinterpret_cast<float4 *>(sp);
+        for (int i = tid; i < SPEC / 2; i += NT) dst[i] = src[i];
+        if (tid < 128) {
+            double s, c;
+            int k2 = tid >> 2, l = tid & 3;
+            sincospi(2.0 * (k2 * l) / N, &s, &c);
+            tw1[tid] = make_float2((float)c, (float)s);
+            int k3 = tid >> 3, g = tid & 7;
+            sincospi(2.0 * (k3 * g) / N, &s, &c);
+            tw2[tid] = make_float2((float)c, (float)s);
+        }
+    }
+
+    // round-1 identity: warp -> sub-sequence l, lane -> stored column q
+    const int l1 = warp & 3;
+    const int q = ((warp >> 2) << 5) + lane;
+    // round-2 identity
+    const int k2r = (warp << 2) + (lane >> 3);
+    const int g2 = lane & 7;
+    // round-3 identity
+    const int r3 = (warp << 4) + (lane & 15);
+    const int h3 = lane >> 4;
+
+    float best_v = -INFINITY;
+    int best_t = -1;
+
+    for (int pi = pb; pi < pe; ++pi) {
+        const int t1 = 2 * pi, t2 = min(t1 + 1, T - 1);
+        const float2 *g1 = St + (size_t)t1 * SPEC;
+        const float2 *g2p = St + (size_t)t2 * SPEC;
+        __syncthreads();   // sp / tables ready (first pass); previous round 3 done with buf
+        // reduce the previous pair's per-warp maxima
+        if (pi > pb && tid == 0) {
+            const float2 *rr = red + ((pi - 1) & 1) * 8;
+            float m1 = rr[0].x, m2 = rr[0].y;
+#pragma unroll
+            for (int w = 1; w < 8; ++w) { m1 = fmaxf(m1, rr[w].x); m2 = fmaxf(m2, rr[w].y); }
+            const int u1 = 2 * (pi - 1), u2 = min(u1 + 1, T - 1);
+            if (m1 > best_v) { best_v = m1; best_t = u1; }
+            if (u2 != u1 && m2 > best_v) { best_v = m2; best_t = u2; }
+            if (peaks_all) {
+                peaks_all[(size_t)p * T + u1] = m1;
+                if (u2 != u1) peaks_all[(size_t)p * T + u2] = m2;
+            }
+        }
+
+        // ---------------- round 1: column sub-FFTs ----------------
+        float2 a[32], b[32];
+#pragma unroll
+        for (int m = 0; m < 32; ++m) {
+            const int k = (l1 + 4 * m) * HW + q;
+            const float2 s = sp[k];
+            const float2 x1 = c_mulcj(__ldg(g1 + k), s);
+            const float2 x2 = c_mulcj(__ldg(g2p + k), s);
+            if (q == 0) {
+                // columns 0 and 64 are self-conjugate: pack Z directly
+                const int k64 = (l1 + 4 * m) * HW + 64;
+                const float2 s64 = sp[k64];
+                const float2 y1 = c_mulcj(__ldg(g1 + k64), s64);
+                const float2 y2 = c_mulcj(__ldg(g2p + k64), s64);
+                a[m] = make_float2(x1.x - x2.y, x1.y + x2.x);
+                b[m] = make_float2(y1.x - y2.y, y1.y + y2.x);
+            } else {
+                a[m] = x1;
+                b[m] = x2;
+            }
+        }
+        fft_reg_dif<32, +1>(a);
+        fft_reg_dif<32, +1>(b);
+        {   // (the loop-head barrier already ordered these stores after round 3's loads)
+            const int lm = (4 - l1) & 3;
+            StaticFor<0, 32>::run([&](auto pp) {
+                constexpr int P = decltype(pp)::value;
+                constexpr int k2 = cx_bitrev(P, 5);
+                const float2 w = tw1[k2 * 4 + l1];
+                const float2 fa = c_mul(a[P], w), fb = c_mul(b[P], w);
+                if (q != 0) {
+                    buf[idxA(l1, k2, q)] = make_float2(fa.x - fb.y, fa.y + fb.x);
+                    buf[idxA(lm, k2, 128 - q)] = make_float2(fa.x + fb.y, fb.x - fa.y);
+                } else {
+                    buf[idxA(l1, k2, 0)] = fa;
+                    buf[idxA(l1, k2, 64)] = fb;
+                }
+            });
+        }
+        __syncthreads();
+
+        // ---------------- round 2: finish columns, start rows ----------------
+        float2 c[4][16];
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) c[l][i] = buf[idxA(l, k2r, g2 + 8 * i)];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const float2 x0 = c_add(c[0][i], c[2][i]), x1 = c_sub(c[0][i], c[2][i]);
+            const float2 x2 = c_add(c[1][i], c[3][i]), x3 = c_mul_pi(c_sub(c[1][i], c[3][i]));
+            c[0][i] = c_add(x0, x2);   // k1 = 0
+            c[2][i] = c_sub(x0, x2);   // k1 = 2
+            c[1][i] = c_add(x1, x3);   // k1 = 1
+            c[3][i] = c_sub(x1, x3);   // k1 = 3
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            fft_reg_dif<16, +1>(c[k1]);
+            const int r = k2r + 32 * k1;
+            StaticFor<0, 16>::run([&](auto pp) {
+                constexpr int P = decltype(pp)::value;
+                constexpr int k3 = cx_bitrev(P, 4);
+                buf[idxB(r, k3, g2)] = c_mul(c[k1][P], tw2[k3 * 8 + g2]);
+            });
+        }
+        __syncthreads();
+
+        // ---------------- round 3: finish rows, max ----------------
+        float m1 = -INFINITY, m2 = -INFINITY;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float2 d[8];
+#pragma unroll
+            for (int g = 0; g < 8; ++g) d[g] = buf[idxB(r3, 8 * h3 + j, g)];
+            fft_reg_dif<8, +1>(d);
+#pragma unroll
+            for (int g = 0; g < 8; ++g) { m1 = fmaxf(m1, d[g].x); m2 = fmaxf(m2, d[g].y); }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+            m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+        }
+        if (lane == 0) red[(pi & 1) * 8 + warp] = make_float2(m1, m2);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int pi = pe;
+        const float2 *rr = red + ((pi - 1) & 1) * 8;
+        float m1 = rr[0].x, m2 = rr[0].y;
+#pragma unroll
+        for (int w = 1; w < 8; ++w) { m1 = fmaxf(m1, rr[w].x); m2 = fmaxf(m2, rr[w].y); }
+        const int u1 = 2 * (pi - 1), u2 = min(u1 + 1, T - 1);
+        if (m1 > best_v) { best_v = m1; best_t = u1; }
+        if (u2 != u1 && m2 > best_v) { best_v = m2; best_t = u2; }
+        if (peaks_all) {
+            peaks_all[(size_t)p * T + u1] = m1;
+            if (u2 != u1) peaks_all[(size_t)p * T + u2] = m2;
+        }
+        atomicMax(keys + p, pack_key(best_v, best_t));
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_search128(const float2 *St, int T, const float2 *Sp, const int *degen, int P,
+                             unsigned long long *keys, float *peaks_all, int num_sms, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_search128, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    const int npairs = (T + 1) / 2;
+    // split the library across CTAs only when there are too few patterns to
+    // fill the GPU; each split CTA still covers at least 8 pairs
+    int chunks = (num_sms + P - 1) / P;
+    chunks = max(1, min(chunks, (npairs + 7) / 8));
+    int ppc = (npairs + chunks - 1) / chunks;
+    chunks = (npairs + ppc - 1) / ppc;
+    dim3 grid(chunks, P);
+    k_search128<<<grid, NT, SMEM_BYTES, st>>>(St, T, Sp, degen, ppc, keys, peaks_all);
+    return cudaGetLastError();
+}
+
+size_t search128_smem_bytes() { return SMEM_BYTES; }

@@ -1,0 +1,60 @@
+// Launchers of the ebsdxcf kernels (host side, internal to the library).
+// Every launcher enqueues on `st` and returns the cudaError_t of the launch.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+struct PrepArgs {
+    int N;            // square side after the crop
+    int W, H;         // detector (source image) size
+    int ox, oy;       // crop offsets
+    int window;       // 0 none, 1 Hann
+    float inv2shp;    // 1 / (2 sigma_hp^2)
+    float inv2slp;    // 1 / (2 sigma_lp^2)
+};
+
+struct ProjArgs {
+    int W, H;                 // detector size
+    int ox, oy, nx, ny;       // output region: detector pixels [oy, oy+ny) x [ox, ox+nx)
+    double pcx, pcy, pcz;     // default pattern centre (when pcs == nullptr)
+    double alpha;             // detector -> sample rotation about x, radians
+};
+
+// pre-processing: images [P, H, W] -> half spectra [P, N, N/2+1] (+ spatial [P, N, N])
+// `active` (nullable): images whose flag is 0 are skipped entirely
+cudaError_t launch_prep(const float *img, int P, const PrepArgs &a, float2 *spec, float *spatial,
+                        int *degen, const int *active, cudaStream_t st);
+
+// all-pairs search: per-pattern best key (atomicMax) and optional per-pair peaks [P, T]
+cudaError_t launch_search(int N, const float2 *St, int T, const float2 *Sp, const int *degen, int P,
+                          unsigned long long *keys, float *peaks_all, int num_sms, cudaStream_t st);
+
+// peak of one surface per pattern: template spectrum = St + (tidx ? tidx[p] : p) * H
+cudaError_t launch_pair_peak(int N, const float2 *St, const int *tidx, const float2 *Sp,
+                             const int *degen, const int *active, int P, float *peak, float *shift,
+                             cudaStream_t st);
+
+cudaError_t launch_keys_to_best(const unsigned long long *keys, int P, int *best, cudaStream_t st);
+
+cudaError_t launch_project(const float *master, int M, const double *quats, const double *pcs,
+                           const int *active, int P, const ProjArgs &a, float *out, cudaStream_t st);
+
+cudaError_t launch_logpolar(const float *spatial, const int *active, int P, int N, int nr, int neta,
+                            float rmin, float rmax, float *out, cudaStream_t st);
+
+// refinement updates (float64 orientation algebra)
+cudaError_t launch_update_xy(const double *q, const float *shift, const double *pcs, double pcz_def,
+                             int W, double alpha, const int *active, int P, double *q1,
+                             cudaStream_t st);
+cudaError_t launch_eta_update(const float *lpT, const float *lpP, int nr, int neta, const double *q0,
+                              const double *q1, double alpha, double tol_deg, int *active,
+                              int *iters, double *q_out, int P, cudaStream_t st);
+
+cudaError_t launch_gather_seeds(const double *lib_quats, const int *best, int P, double *seeds,
+                                cudaStream_t st);
+cudaError_t launch_init_refine(const int *degen, int P, int *active, int *iters, float *peak,
+                               cudaStream_t st);
+cudaError_t launch_copy_active_peak(const float *src, const int *active, int P, float *dst,
+                                    cudaStream_t st);
+cudaError_t launch_disorientation(const double *qa, const double *qb, int n, double *out,
+                                  cudaStream_t st);

@@ -1,0 +1,342 @@
+"""Thin Python binding of the ebsdxcf C ABI (include/ebsdxcf.h).
+
+Argument marshalling only: every step runs in the CUDA library
+``_build/libebsdxcf.so``.  Functions carry the C names; tensors are torch CUDA
+tensors (device pointers) except for the ``*_host`` entry point, which takes
+CPU tensors.  Work is enqueued on torch's current CUDA stream.  If the library
+is missing or cannot be loaded, every call raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build as _build
+
+XCF_OK = 0
+XCF_ERR_ARG = -1
+XCF_ERR_SIZE = -2
+XCF_ERR_OOM = -3
+XCF_ERR_CUDA = -4
+XCF_ERR_TIMEOUT = -5
+XCF_ERR_UNIMPLEMENTED = -6
+
+
+class XcfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class xcf_options(C.Structure):
+    _fields_ = [("window", C.c_int32), ("sigma_hp", C.c_double), ("sigma_lp", C.c_double),
+                ("lp_nr", C.c_int32), ("lp_neta", C.c_int32), ("lp_rmin", C.c_double),
+                ("lp_rmax", C.c_double), ("max_iter", C.c_int32), ("tol_deg", C.c_double)]
+
+
+class xcf_geometry(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("pcx", C.c_double),
+                ("pcy", C.c_double), ("pcz", C.c_double), ("sample_tilt_deg", C.c_double),
+                ("detector_tilt_deg", C.c_double)]
+
+
+def geometry(width, height, pc=(0.5, 0.5, 0.6), sample_tilt=70.0, detector_tilt=0.0) -> xcf_geometry:
+    return xcf_geometry(int(width), int(height), float(pc[0]), float(pc[1]), float(pc[2]),
+                        float(sample_tilt), float(detector_tilt))
+
+
+_P = C.c_void_p
+_I32 = C.c_int32
+# name -> argtypes (all return int unless noted)
+_SIGS = {
+    "xcf_strerror": ([C.c_int], C.c_char_p),
+    "xcf_last_error": ([_P], C.c_char_p),
+    "xcf_options_default": ([C.POINTER(xcf_options)], C.c_int),
+    "xcf_crop": ([C.POINTER(xcf_geometry), C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32),
+                  C.POINTER(C.c_double)], C.c_int),
+    "xcf_create": ([C.POINTER(_P), C.POINTER(xcf_options), C.c_int], C.c_int),
+    "xcf_destroy": ([_P], C.c_int),
+    "xcf_project": ([_P, _P, _I32, _P, _I32, C.POINTER(xcf_geometry), _P, _P, _P], C.c_int),
+    "xcf_prep": ([_P, _P, _I32, C.POINTER(xcf_geometry), _P, _P, _P, _P], C.c_int),
+    "xcf_build_library": ([_P, _P, _I32, _P, _I32, C.POINTER(xcf_geometry), C.POINTER(_P), _P], C.c_int),
+    "xcf_build_library_images": ([_P, _P, _P, _I32, C.POINTER(xcf_geometry), _P, _I32, C.POINTER(_P),
+                                  _P], C.c_int),
+    "xcf_library_free": ([_P], C.c_int),
+    "xcf_library_info": ([_P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_P)], C.c_int),
+    "xcf_index": ([_P, _P, _P, _I32, _P, _P, _P, _P], C.c_int),
+    "xcf_correlate_all": ([_P, _P, _P, _I32, _P, _P], C.c_int),
+    "xcf_refine": ([_P, _P, _P, _I32, _P, _P, _P, _P, _P, _P], C.c_int),
+    "xcf_disorientation": ([_P, _P, _P, _I32, _P, _P], C.c_int),
+    "xcf_index_refine_host": ([_P, _P, _P, _I32, _P, _I32, _P, _P, _P, _P, _P, _P], C.c_int),
+    "xcf_index_refine": ([_P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "xcf_profile_enable": ([_P, C.c_int], C.c_int),
+    "xcf_profile_read": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int], C.c_int),
+}
+
+STAGES = ("project", "prep", "search", "peak", "logpolar", "update", "other")
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it first if asked and needed)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"ebsdxcf CUDA library not built: {path}")
+        lib = C.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(rc: int, ctx=None):
+    if rc != XCF_OK:
+        lib = load()
+        detail = lib.xcf_last_error(ctx).decode() if ctx else ""
+        raise XcfError(rc, f"{lib.xcf_strerror(rc).decode()}: {detail}")
+
+
+def _ptr(t, dtype, name, allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(t, dtype, name, allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if t.dtype != dtype or t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CPU {dtype} tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# ------------------------------------------------------------------ handles
+class Context:
+    """An xcf_ctx on one CUDA device (owns reusable device scratch)."""
+
+    def __init__(self, options: xcf_options | None = None, device: int | None = None, **kw):
+        lib = load()
+        o = xcf_options()
+        lib.xcf_options_default(C.byref(o))
+        if options is not None:
+            o = options
+        for k, v in kw.items():
+            setattr(o, k, v)
+        self.options = o
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        h = C.c_void_p()
+        _check(lib.xcf_create(C.byref(h), C.byref(o), self.device))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().xcf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Library:
+    """An xcf_library (device-resident template spectra)."""
+
+    def __init__(self, handle, geom: xcf_geometry, quats: torch.Tensor | None = None):
+        self.handle = handle
+        self.geom = geom
+        T, N, sp = _I32(), _I32(), C.c_void_p()
+        _check(load().xcf_library_info(handle, C.byref(T), C.byref(N), C.byref(sp)))
+        self.T, self.N, self._spectra_ptr = T.value, N.value, sp.value
+        self.quats = quats
+
+    def spectra(self) -> torch.Tensor:
+        """Copy of the library's half spectra [T, N, N/2+1] complex64."""
+        shape = (self.T, self.N, self.N // 2 + 1, 2)
+
+        class _View:
+            __cuda_array_interface__ = {"shape": shape, "typestr": "<f4", "version": 3,
+                                        "data": (self._spectra_ptr, True), "strides": None}
+        view = torch.as_tensor(_View(), device=f"cuda:{torch.cuda.current_device()}")
+        return torch.view_as_complex(view.clone())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().xcf_library_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------ entry points
+def xcf_crop(geom: xcf_geometry):
+    n, ox, oy = _I32(), _I32(), _I32()
+    pc = (C.c_double * 3)()
+    _check(load().xcf_crop(C.byref(geom), C.byref(n), C.byref(ox), C.byref(oy), pc))
+    return n.value, ox.value, oy.value, tuple(pc)
+
+
+def xcf_project(ctx: Context, master, quats, geom: xcf_geometry, pcs=None, out=None):
+    P = quats.shape[0]
+    if out is None:
+        out = torch.empty((P, geom.height, geom.width), dtype=torch.float32, device=quats.device)
+    _check(load().xcf_project(ctx.handle, _ptr(master, torch.float32, "master"), master.shape[-1],
+                              _ptr(quats, torch.float64, "quats"), P, C.byref(geom),
+                              _ptr(pcs, torch.float64, "pcs", True), _ptr(out, torch.float32, "out"),
+                              _stream()), ctx.handle)
+    return out
+
+
+def xcf_prep(ctx: Context, images, geom: xcf_geometry, want_spatial=False):
+    P = images.shape[0]
+    n = xcf_crop(geom)[0]
+    spec = torch.empty((P, n, n // 2 + 1, 2), dtype=torch.float32, device=images.device)
+    spat = torch.empty((P, n, n), dtype=torch.float32, device=images.device) if want_spatial else None
+    degen = torch.empty(P, dtype=torch.int32, device=images.device)
+    _check(load().xcf_prep(ctx.handle, _ptr(images, torch.float32, "images"), P, C.byref(geom),
+                           _ptr(spec, torch.float32, "spectra"), _ptr(spat, torch.float32, "spatial", True),
+                           _ptr(degen, torch.int32, "degenerate"), _stream()), ctx.handle)
+    return torch.view_as_complex(spec), spat, degen
+
+
+def xcf_build_library(ctx: Context, master, quats, geom: xcf_geometry) -> Library:
+    h = C.c_void_p()
+    _check(load().xcf_build_library(ctx.handle, _ptr(master, torch.float32, "master"), master.shape[-1],
+                                    _ptr(quats, torch.float64, "quats"), quats.shape[0], C.byref(geom),
+                                    C.byref(h), _stream()), ctx.handle)
+    return Library(h, geom, quats)
+
+
+def xcf_build_library_images(ctx: Context, images, quats, geom: xcf_geometry, master=None) -> Library:
+    h = C.c_void_p()
+    M = master.shape[-1] if master is not None else 0
+    _check(load().xcf_build_library_images(ctx.handle, _ptr(images, torch.float32, "images"),
+                                           _ptr(quats, torch.float64, "quats"), quats.shape[0],
+                                           C.byref(geom), _ptr(master, torch.float32, "master", True), M,
+                                           C.byref(h), _stream()), ctx.handle)
+    return Library(h, geom, quats)
+
+
+def xcf_index(ctx: Context, lib: Library, patterns, best=None, peak=None, shift=None):
+    P = patterns.shape[0]
+    dev = patterns.device
+    best = torch.empty(P, dtype=torch.int32, device=dev) if best is None else best
+    peak = torch.empty(P, dtype=torch.float32, device=dev) if peak is None else peak
+    shift = torch.empty((P, 2), dtype=torch.float32, device=dev) if shift is None else shift
+    _check(load().xcf_index(ctx.handle, lib.handle, _ptr(patterns, torch.float32, "patterns"), P,
+                            _ptr(best, torch.int32, "best"), _ptr(peak, torch.float32, "peak"),
+                            _ptr(shift, torch.float32, "shift"), _stream()), ctx.handle)
+    return best, peak, shift
+
+
+def xcf_correlate_all(ctx: Context, lib: Library, patterns, peaks=None):
+    P = patterns.shape[0]
+    peaks = torch.empty((P, lib.T), dtype=torch.float32, device=patterns.device) if peaks is None else peaks
+    _check(load().xcf_correlate_all(ctx.handle, lib.handle, _ptr(patterns, torch.float32, "patterns"), P,
+                                    _ptr(peaks, torch.float32, "peaks"), _stream()), ctx.handle)
+    return peaks
+
+
+def xcf_refine(ctx: Context, lib: Library, patterns, seeds, pcs=None, quats=None, peak=None, iters=None):
+    P = patterns.shape[0]
+    dev = patterns.device
+    quats = torch.empty((P, 4), dtype=torch.float64, device=dev) if quats is None else quats
+    peak = torch.empty(P, dtype=torch.float32, device=dev) if peak is None else peak
+    iters = torch.empty(P, dtype=torch.int32, device=dev) if iters is None else iters
+    _check(load().xcf_refine(ctx.handle, lib.handle, _ptr(patterns, torch.float32, "patterns"), P,
+                             _ptr(seeds, torch.float64, "seeds"), _ptr(pcs, torch.float64, "pcs", True),
+                             _ptr(quats, torch.float64, "quats"), _ptr(peak, torch.float32, "peak"),
+                             _ptr(iters, torch.int32, "iters"), _stream()), ctx.handle)
+    return quats, peak, iters
+
+
+def xcf_disorientation(ctx: Context, qa, qb, out=None):
+    n = qa.shape[0]
+    out = torch.empty(n, dtype=torch.float64, device=qa.device) if out is None else out
+    _check(load().xcf_disorientation(ctx.handle, _ptr(qa, torch.float64, "qa"), _ptr(qb, torch.float64, "qb"),
+                                     n, _ptr(out, torch.float64, "out"), _stream()), ctx.handle)
+    return out
+
+
+def xcf_index_refine(ctx: Context, lib: Library, patterns, pcs=None, out=None):
+    """Search + refinement in one call on device tensors; returns a dict of outputs."""
+    P = patterns.shape[0]
+    d = patterns.device
+    if out is None:
+        out = dict(best=torch.empty(P, dtype=torch.int32, device=d), peak=torch.empty(P, device=d),
+                   shift=torch.empty((P, 2), device=d), quats=torch.empty((P, 4), dtype=torch.float64, device=d),
+                   rpeak=torch.empty(P, device=d), iters=torch.empty(P, dtype=torch.int32, device=d))
+    _check(load().xcf_index_refine(
+        ctx.handle, lib.handle, _ptr(patterns, torch.float32, "patterns"), P, _ptr(pcs, torch.float64, "pcs", True),
+        _ptr(out["best"], torch.int32, "best"), _ptr(out["peak"], torch.float32, "peak"),
+        _ptr(out["shift"], torch.float32, "shift"), _ptr(out["quats"], torch.float64, "quats"),
+        _ptr(out["rpeak"], torch.float32, "rpeak"), _ptr(out["iters"], torch.int32, "iters"), _stream()),
+        ctx.handle)
+    return out
+
+
+def xcf_index_refine_host(ctx: Context, lib: Library, patterns, pcs=None, chunk=0, out=None):
+    """Host-memory end to end (synchronous); patterns [P, H, W] CPU float32 (pinned for speed)."""
+    P = patterns.shape[0]
+    if out is None:
+        pin = patterns.is_pinned()
+        mk = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=pin)
+        out = dict(best=mk((P,), torch.int32), peak=mk((P,), torch.float32), shift=mk((P, 2), torch.float32),
+                   quats=mk((P, 4), torch.float64), rpeak=mk((P,), torch.float32), iters=mk((P,), torch.int32))
+    _check(load().xcf_index_refine_host(
+        ctx.handle, lib.handle, _hptr(patterns, torch.float32, "patterns"), P,
+        _hptr(pcs, torch.float64, "pcs", True), int(chunk), _hptr(out["best"], torch.int32, "best"),
+        _hptr(out["peak"], torch.float32, "peak"), _hptr(out["shift"], torch.float32, "shift"),
+        _hptr(out["quats"], torch.float64, "quats"), _hptr(out["rpeak"], torch.float32, "rpeak"),
+        _hptr(out["iters"], torch.int32, "iters")), ctx.handle)
+    return out
+
+
+def xcf_profile_enable(ctx: Context, on: bool = True):
+    _check(load().xcf_profile_enable(ctx.handle, 1 if on else 0), ctx.handle)
+
+
+def xcf_profile_read(ctx: Context, reset: bool = False):
+    """-> {stage: (device_ms, launches)}"""
+    ms = (C.c_double * len(STAGES))()
+    n = (C.c_int64 * len(STAGES))()
+    _check(load().xcf_profile_read(ctx.handle, ms, n, 1 if reset else 0), ctx.handle)
+    return {s: (ms[i], n[i]) for i, s in enumerate(STAGES)}

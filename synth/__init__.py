@@ -322,3 +322,31 @@ def random_images(n: int, H: int, W: int, seed: int) -> np.ndarray:
     """Plain seeded Gaussian images [n, H, W] float32 (for transform-level tests)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.standard_normal((n, H, W)).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# workload recipes (inputs only; projection is done by the caller)
+# ---------------------------------------------------------------------------
+def config_parity_64(seed: int = 0) -> dict:
+    """Plain search parity workload: diamond-cubic master (2 x 1024^2), 300
+    uniformly random library orientations, 16 random test orientations,
+    64 x 64 detector, PC (0.5, 0.5, 0.6), Poisson peak 200 + background."""
+    return dict(name="xcf64_T300_P16", crystal="diamond", M=1024, n=64, pc=DEFAULT_PC,
+                master=master_pattern("diamond", 1024),
+                lib_q=random_quaternions(300, seed), truth_q=random_quaternions(16, seed + 1),
+                pcs=np.broadcast_to(np.asarray(DEFAULT_PC), (16, 3)).copy(), peak=200.0,
+                noise_seed=seed + 2, max_iter=2)
+
+
+def config_map_128(seed: int = 0, ny: int = 100, nx: int = 100, step_deg: float = 5.35) -> dict:
+    """Search + refinement workload: BCC master (2 x 1024^2), 128 x 128
+    detector, ~4,000 library orientations (S^2 x S^1 grid in the cubic
+    fundamental zone, step 5.35 deg), a ny x nx map of orientations (smooth
+    random field +-10 deg plus +-2 deg jitter), PC (0.5, 0.5, 0.6) jittered by
+    +-0.005 per pattern, Poisson peak 100 counts + background, refinement to
+    convergence (at most 10 iterations)."""
+    P = ny * nx
+    return dict(name=f"xcf128_T{len(so3_grid_cubic_fz(step_deg))}_P{P}", crystal="bcc", M=1024, n=128,
+                pc=DEFAULT_PC, master=master_pattern("bcc", 1024), lib_q=so3_grid_cubic_fz(step_deg),
+                truth_q=smooth_orientation_map(ny, nx, seed + 1), pcs=jittered_pcs(P, seed + 2),
+                peak=100.0, noise_seed=seed + 3, max_iter=10)
