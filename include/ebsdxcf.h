@@ -52,9 +52,9 @@ typedef struct {
     int32_t window;     /* 0 none, 1 periodic Hann (default)                       */
     double sigma_hp;    /* Gaussian high-pass sigma, cycles/image (default 2)       */
     double sigma_lp;    /* Gaussian low-pass sigma, cycles/image (auto: N/4)        */
-    int32_t lp_nr;      /* log-polar radii (auto: N/2)                              */
+    int32_t lp_nr;      /* log-polar radii (auto: N/4)                              */
     int32_t lp_neta;    /* log-polar angles (auto: 2N)                              */
-    double lp_rmin;     /* smallest log-polar radius, px (auto: 4)                  */
+    double lp_rmin;     /* smallest log-polar radius, px (auto: N/4)                */
     double lp_rmax;     /* largest log-polar radius, px (auto: N/2 - 1)             */
     int32_t max_iter;   /* refinement iterations (default 2, as in the paper)       */
     double tol_deg;     /* stop when an iteration's update is below this (1e-3)     */

@@ -45,9 +45,9 @@ class Opts(C.Structure):
 
 def default_opts(n: int, **kw) -> Opts:
     """Defaults: Hann window, sigma_hp = 2, sigma_lp = n/4 cycles per image,
-    log-polar n/2 radii x 2n angles over r in [4, n/2 - 1] px."""
-    d = dict(window=1, sigma_hp=2.0, sigma_lp=n / 4.0, lp_nr=n // 2, lp_neta=2 * n,
-             lp_rmin=4.0, lp_rmax=n / 2.0 - 1.0)
+    log-polar n/4 radii x 2n angles over r in [n/4, n/2 - 1] px."""
+    d = dict(window=1, sigma_hp=2.0, sigma_lp=n / 4.0, lp_nr=max(n // 4, 2), lp_neta=2 * n,
+             lp_rmin=n / 4.0, lp_rmax=n / 2.0 - 1.0)
     d.update(kw)
     return Opts(**d)
 

@@ -167,9 +167,9 @@ Resolved resolve(const xcf_options &o, int n) {
     r.window = o.window;
     r.sigma_hp = o.sigma_hp > 0 ? o.sigma_hp : 2.0;
     r.sigma_lp = o.sigma_lp > 0 ? o.sigma_lp : n / 4.0;
-    r.nr = o.lp_nr > 0 ? o.lp_nr : n / 2;
+    r.nr = o.lp_nr > 0 ? o.lp_nr : (n / 4 > 2 ? n / 4 : 2);
     r.neta = o.lp_neta > 0 ? o.lp_neta : 2 * n;
-    r.rmin = o.lp_rmin > 0 ? o.lp_rmin : 4.0;
+    r.rmin = o.lp_rmin > 0 ? o.lp_rmin : n / 4.0;
     r.rmax = o.lp_rmax > 0 ? o.lp_rmax : n / 2.0 - 1.0;
     return r;
 }

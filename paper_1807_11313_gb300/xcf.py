@@ -190,7 +190,7 @@ class Library:
 
         class _View:
             __cuda_array_interface__ = {"shape": shape, "typestr": "<f4", "version": 3,
-                                        "data": (self._spectra_ptr, True), "strides": None}
+                                        "data": (self._spectra_ptr, False), "strides": None}
         view = torch.as_tensor(_View(), device=f"cuda:{torch.cuda.current_device()}")
         return torch.view_as_complex(view.clone())
 
