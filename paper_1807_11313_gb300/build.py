@@ -29,7 +29,8 @@ def _sources():
 
 
 def _deps():
-    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [
+    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(
+        glob.glob(os.path.join(CSRC, "*.h"))) + [
         os.path.join(ROOT, "include", "ebsdxcf.h"), os.path.abspath(__file__)]
 
 

@@ -9,61 +9,10 @@
 #include <vector>
 
 #include "../../include/ebsdxcf.h"
+#include "internal.h"
 #include "kernels.cuh"
 
-namespace {
-
-constexpr double kPi = 3.14159265358979323846;
-
-enum Slot {
-    S_SPEC_P = 0,   // pattern half spectra
-    S_SPEC_T,       // per-pattern template half spectra (refinement)
-    S_SPATIAL_P,    // filtered pattern images
-    S_SPATIAL_T,    // filtered template images
-    S_IMG,          // projected template images
-    S_LP_P,         // log-polar patterns
-    S_LP_T,         // log-polar templates
-    S_KEYS,
-    S_DEGEN,
-    S_ACTIVE,
-    S_SHIFT,
-    S_Q1,
-    S_SEEDS,
-    S_BEST,
-    S_PEAK,
-    S_IO_PAT,       // host pipeline: device copy of a chunk of patterns
-    S_IO_PCS,
-    S_IO_OUT,
-    S_COUNT
-};
-
-}  // namespace
-
-struct xcf_ctx {
-    int device = 0;
-    int num_sms = 0;
-    xcf_options opt{};
-    std::string err;
-    void *buf[S_COUNT] = {};
-    size_t cap[S_COUNT] = {};
-    // profiling
-    bool timing = false;
-    int64_t launches[XCF_NUM_STAGES] = {};
-    double ms[XCF_NUM_STAGES] = {};
-    struct Rec { int stage; cudaEvent_t a, b; };
-    std::vector<Rec> recs;
-};
-
-struct xcf_library {
-    int device = 0;
-    int T = 0, N = 0, M = 0;
-    xcf_geometry geom{};
-    int ox = 0, oy = 0;
-    double pc[3] = {0, 0, 0};
-    float2 *spectra = nullptr;
-    double *quats = nullptr;
-    float *master = nullptr;
-};
+using namespace xcf_internal;
 
 namespace {
 
