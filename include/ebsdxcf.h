@@ -202,6 +202,35 @@ int xcf_index_refine_host(xcf_ctx *ctx, const xcf_library *lib, const float *pat
                           int32_t P, const double *pcs, int32_t chunk, int32_t *best, float *peak,
                           float *shift, double *quats, float *rpeak, int32_t *iters);
 
+/* Library search without device allocation.  No counterpart in the paper.
+ *
+ * Some callers cannot call cudaMalloc: code whose device memory is entirely
+ * owned by another allocator (e.g. a framework's caching allocator that has
+ * reserved the GPU), or a latency-critical loop that cannot accept the
+ * device-wide synchronisation of cudaMalloc / cudaFree.  xcf_index_noalloc
+ * gives them the results of xcf_index (same kernels, same arguments and
+ * outputs) while allocating nothing: its scratch (pattern spectra, flags and
+ * keys) lives in one fixed array of XCF_NOALLOC_SCRATCH_BYTES compiled into
+ * the library, which every GPU that loads the library holds until the
+ * process exits.  The caller still provides inputs and outputs.
+ *  - P may not exceed xcf_noalloc_max_patterns(N) (252 patterns at N = 128,
+ *    992 at N = 64); larger P fails with XCF_ERR_SIZE and a message naming
+ *    the limit.
+ *  - The first call on a device looks up the array's device address (a
+ *    one-time set-up that allocates nothing); make that first call before
+ *    any stream capture.
+ *  - All calls on a device share the one array and it keeps the previous
+ *    call's contents (the call clears what must start at zero).  Calls whose
+ *    work overlaps on the GPU (other streams, other host threads) race on it:
+ *    serialise them. */
+#define XCF_NOALLOC_SCRATCH_BYTES (16u << 20)
+int xcf_index_noalloc(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P,
+                      int32_t *best, float *peak, float *shift, void *stream);
+
+/* Largest P that xcf_index_noalloc accepts for detector side n (0 if n is
+ * not a power of two in [16, 256]).  Host only. */
+int xcf_noalloc_max_patterns(int32_t n);
+
 /* Profiling.  Every context counts the kernels it launches, per stage.  When
  * timing is enabled it also records a CUDA event pair on the launching stream
  * around each launch and accumulates the elapsed device time per stage. */

@@ -10,5 +10,5 @@ from .xcf import (  # noqa: F401
     Context, Library, XcfError, geometry, xcf_build_library, xcf_build_library_images,
     xcf_correlate_all, xcf_crop, xcf_disorientation, xcf_index, xcf_index_refine, xcf_index_refine_host,
     xcf_options, xcf_geometry, xcf_prep, xcf_project, xcf_refine, load, library_path,
-    xcf_profile_enable, xcf_profile_read, STAGES,
+    xcf_profile_enable, xcf_profile_read, STAGES, xcf_index_noalloc, xcf_noalloc_max_patterns,
 )

@@ -71,6 +71,8 @@ _SIGS = {
     "xcf_disorientation": ([_P, _P, _P, _I32, _P, _P], C.c_int),
     "xcf_index_refine_host": ([_P, _P, _P, _I32, _P, _I32, _P, _P, _P, _P, _P, _P], C.c_int),
     "xcf_index_refine": ([_P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "xcf_index_noalloc": ([_P, _P, _P, _I32, _P, _P, _P, _P], C.c_int),
+    "xcf_noalloc_max_patterns": ([_I32], C.c_int),
     "xcf_profile_enable": ([_P, C.c_int], C.c_int),
     "xcf_profile_read": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int], C.c_int),
 }
@@ -340,3 +342,17 @@ def xcf_profile_read(ctx: Context, reset: bool = False):
     n = (C.c_int64 * len(STAGES))()
     _check(load().xcf_profile_read(ctx.handle, ms, n, 1 if reset else 0), ctx.handle)
     return {s: (ms[i], n[i]) for i, s in enumerate(STAGES)}
+
+
+def xcf_noalloc_max_patterns(n: int) -> int:
+    return int(load().xcf_noalloc_max_patterns(int(n)))
+
+
+def xcf_index_noalloc(ctx: Context, lib: Library, patterns, best, peak, shift):
+    """xcf_index without any device allocation by the library (its scratch is
+    a fixed array compiled into the library).  Outputs must be preallocated."""
+    P = patterns.shape[0]
+    _check(load().xcf_index_noalloc(ctx.handle, lib.handle, _ptr(patterns, torch.float32, "patterns"), P,
+                                    _ptr(best, torch.int32, "best"), _ptr(peak, torch.float32, "peak"),
+                                    _ptr(shift, torch.float32, "shift"), _stream()), ctx.handle)
+    return best, peak, shift
