@@ -198,7 +198,7 @@ int index_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int
     if (peaks_all)   // degenerate patterns keep all-zero rows
         XCF_CHECK(cudaMemsetAsync(peaks_all, 0, sizeof(float) * (size_t)P * lib->T, st), "memset peaks");
     XCF_LAUNCH(XCF_STAGE_SEARCH, st,
-               launch_search(c.n, lib->spectra, lib->T, sp, degen, P, keys, peaks_all, ctx->num_sms, st),
+               launch_search(c.n, search_spectra(lib), lib->T, sp, degen, P, keys, peaks_all, ctx->num_sms, st),
                "search");
     if (best) {
         XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_keys_to_best(keys, P, best, st), "keys_to_best");
@@ -449,6 +449,11 @@ int xcf_build_library(xcf_ctx *ctx, const float *master, int32_t M, const double
         ctx->launches[XCF_STAGE_PROJECT] += 1;
         ctx->launches[XCF_STAGE_PREP] += 1;
     }
+    if (e == cudaSuccess && c.n == 128) {
+        e = cudaMalloc(&lib->spectra_pk, sizeof(float2) * H * T);
+        if (e == cudaSuccess) e = launch_pack_search_layout(lib->spectra, T, c.n, lib->spectra_pk, st);
+        ctx->launches[XCF_STAGE_OTHER] += 1;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         xcf_library_free(lib);
@@ -500,6 +505,11 @@ int xcf_build_library_images(xcf_ctx *ctx, const float *images, const double *qu
     }
     if (e == cudaSuccess) e = launch_prep(images, T, prep_args(g, c, r), lib->spectra, nullptr, degen, nullptr, st);
     ctx->launches[XCF_STAGE_PREP] += 1;
+    if (e == cudaSuccess && c.n == 128) {
+        e = cudaMalloc(&lib->spectra_pk, sizeof(float2) * H * T);
+        if (e == cudaSuccess) e = launch_pack_search_layout(lib->spectra, T, c.n, lib->spectra_pk, st);
+        ctx->launches[XCF_STAGE_OTHER] += 1;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         xcf_library_free(lib);
@@ -513,6 +523,7 @@ int xcf_library_free(xcf_library *lib) {
     if (!lib) return XCF_ERR_ARG;
     cudaSetDevice(lib->device);
     if (lib->spectra) cudaFree(lib->spectra);
+    if (lib->spectra_pk) cudaFree(lib->spectra_pk);
     if (lib->quats) cudaFree(lib->quats);
     if (lib->master) cudaFree(lib->master);
     delete lib;

@@ -60,6 +60,12 @@ struct xcf_library {
     int ox = 0, oy = 0;
     double pc[3] = {0, 0, 0};
     float2 *spectra = nullptr;
+    float2 *spectra_pk = nullptr;   // N = 128 only: the search kernel's packed layout
     double *quats = nullptr;
     float *master = nullptr;
 };
+
+// spectra as the all-pairs search kernel of the library's size reads them
+inline const float2 *search_spectra(const xcf_library *lib) {
+    return lib->spectra_pk ? lib->spectra_pk : lib->spectra;
+}

@@ -29,6 +29,9 @@ cudaError_t launch_prep(const float *img, int P, const PrepArgs &a, float2 *spec
 cudaError_t launch_search(int N, const float2 *St, int T, const float2 *Sp, const int *degen, int P,
                           unsigned long long *keys, float *peaks_all, int num_sms, cudaStream_t st);
 
+// N = 128: library half spectra -> the search kernel's packed layout
+cudaError_t launch_pack_search_layout(const float2 *spectra, int T, int N, float2 *packed, cudaStream_t st);
+
 // peak of one surface per pattern: template spectrum = St + (tidx ? tidx[p] : p) * H
 cudaError_t launch_pair_peak(int N, const float2 *St, const int *tidx, const float2 *Sp,
                              const int *degen, const int *active, int P, float *peak, float *shift,

@@ -124,7 +124,7 @@ extern "C" int xcf_index_noalloc(xcf_ctx *ctx, const xcf_library *lib, const flo
     // the array keeps the previous call's contents: the keys must start at 0
     e = cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * P, st);
     if (e != cudaSuccess) return cuda_error(ctx, e, "clear keys");
-    e = launch_search(n, lib->spectra, lib->T, sp, degen, P, keys, nullptr, ctx->num_sms, st);
+    e = launch_search(n, search_spectra(lib), lib->T, sp, degen, P, keys, nullptr, ctx->num_sms, st);
     if (e != cudaSuccess) return cuda_error(ctx, e, "search");
     e = launch_keys_to_best(keys, P, best, st);
     if (e != cudaSuccess) return cuda_error(ctx, e, "keys_to_best");
