@@ -178,18 +178,20 @@ k_search128(const float2 *__restrict__ Spk, int T, const float2 *__restrict__ Sp
                     const float2 s = e ? make_float2(s4.z, s4.w) : make_float2(s4.x, s4.y);
                     const float2 v1 = e ? make_float2(t1.z, t1.w) : make_float2(t1.x, t1.y);
                     const float2 v2 = e ? make_float2(t2.z, t2.w) : make_float2(t2.x, t2.y);
-                    const float2 x1 = c_mulcj(v1, s), x2 = c_mulcj(v2, s);
-                    if (q == 0) {
-                        // columns 0 and 64 are self-conjugate: pack Z directly
-                        const int u = l1 + 4 * m;
-                        const float2 s64 = sp[COL64 + u];
-                        const float2 y1 = c_mulcj(c64[u], s64), y2 = c_mulcj(c64[128 + u], s64);
-                        a[m] = make_float2(x1.x - x2.y, x1.y + x2.x);
-                        b[m] = make_float2(y1.x - y2.y, y1.y + y2.x);
-                    } else {
-                        a[m] = x1;
-                        b[m] = x2;
-                    }
+                    a[m] = c_mulcj(v1, s);
+                    b[m] = c_mulcj(v2, s);
+                }
+            }
+            if (q == 0) {
+                // columns 0 and 64 are self-conjugate: pack Z = X1 + i X2 directly
+                // (column 0 from the products above, column 64 from c64)
+#pragma unroll
+                for (int m = 0; m < 32; ++m) {
+                    const int u = l1 + 4 * m;
+                    const float2 s64 = sp[COL64 + u];
+                    const float2 y1 = c_mulcj(c64[u], s64), y2 = c_mulcj(c64[128 + u], s64);
+                    a[m] = make_float2(a[m].x - b[m].y, a[m].y + b[m].x);
+                    b[m] = make_float2(y1.x - y2.y, y1.y + y2.x);
                 }
             }
         }
