@@ -199,7 +199,11 @@ k_search128(const float2 *__restrict__ Spk, int T, const float2 *__restrict__ Sp
         fft_reg_dif<32, +1>(a);
         fft_reg_dif<32, +1>(b);
         {
-            const int lm = (4 - l1) & 3;
+            // second store: the conjugate-symmetric partner column (q > 0), or
+            // column 64 (q = 0, whose b holds the column-64 transform)
+            const bool q0 = q == 0;
+            const int l_2 = q0 ? l1 : (4 - l1) & 3;
+            const int v_2 = q0 ? 64 : 128 - q;
             const float4 *tw = reinterpret_cast<const float4 *>(tw1 + l1 * 32);
             StaticFor<0, 16>::run([&](auto kk) {
                 constexpr int k2a = 2 * decltype(kk)::value;
@@ -209,13 +213,10 @@ k_search128(const float2 *__restrict__ Spk, int T, const float2 *__restrict__ Sp
                     constexpr int P = cx_bitrev(k2, 5);
                     const float2 w = decltype(ee)::value ? make_float2(w2.z, w2.w) : make_float2(w2.x, w2.y);
                     const float2 fa = c_mul(a[P], w), fb = c_mul(b[P], w);
-                    if (q != 0) {
-                        buf[idxA(l1, k2, q)] = make_float2(fa.x - fb.y, fa.y + fb.x);
-                        buf[idxA(lm, k2, 128 - q)] = make_float2(fa.x + fb.y, fb.x - fa.y);
-                    } else {
-                        buf[idxA(l1, k2, 0)] = fa;
-                        buf[idxA(l1, k2, 64)] = fb;
-                    }
+                    const float2 d1 = make_float2(fa.x - fb.y, fa.y + fb.x);   // F1 + i F2
+                    const float2 d2 = make_float2(fa.x + fb.y, fb.x - fa.y);   // conj(F1) + i conj(F2)
+                    buf[idxA(l1, k2, q)] = q0 ? fa : d1;
+                    buf[idxA(l_2, k2, v_2)] = q0 ? fb : d2;
                 });
             });
         }
