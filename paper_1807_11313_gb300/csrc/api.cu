@@ -166,7 +166,43 @@ PrepArgs prep_args_square(const Crop &c, const Resolved &r) {
     return a;
 }
 
-bool supported_n(int n) { return n == 16 || n == 32 || n == 64 || n == 128; }
+bool supported_n(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
+
+// N = 256 kernels: persistent grid and its per-CTA work arrays (context scratch)
+cudaError_t big_work(xcf_ctx *ctx, int n, long items, float2 **work, int *grid) {
+    *grid = big_grid(ctx->num_sms, items);
+    return scratch_t(ctx, S_WORK, big_work_bytes(n, *grid) / sizeof(float2), work) ? cudaErrorMemoryAllocation
+                                                                                   : cudaSuccess;
+}
+
+// pre-processing, search and peak: shared-memory kernels up to N = 128, the
+// global work-array kernels for N = 256
+cudaError_t run_prep(xcf_ctx *ctx, const float *img, int P, const PrepArgs &a, float2 *spec, float *spatial,
+                     int *degen, const int *active, cudaStream_t st) {
+    if (a.N <= 128) return launch_prep(img, P, a, spec, spatial, degen, active, st);
+    float2 *w;
+    int grid;
+    cudaError_t e = big_work(ctx, a.N, P, &w, &grid);
+    return e != cudaSuccess ? e : launch_prep_big(img, P, a, spec, spatial, degen, active, w, grid, st);
+}
+
+cudaError_t run_search(xcf_ctx *ctx, int n, const float2 *St, int T, const float2 *Sp, const int *degen, int P,
+                       unsigned long long *keys, float *peaks_all, int num_sms, cudaStream_t st) {
+    if (n <= 128) return launch_search(n, St, T, Sp, degen, P, keys, peaks_all, num_sms, st);
+    float2 *w;
+    int grid;
+    cudaError_t e = big_work(ctx, n, (long)P * ((T + 1) / 2), &w, &grid);
+    return e != cudaSuccess ? e : launch_search_big(n, St, T, Sp, degen, P, keys, peaks_all, w, grid, st);
+}
+
+cudaError_t run_pair_peak(xcf_ctx *ctx, int n, const float2 *St, const int *tidx, const float2 *Sp,
+                          const int *degen, const int *active, int P, float *peak, float *shift, cudaStream_t st) {
+    if (n <= 128) return launch_pair_peak(n, St, tidx, Sp, degen, active, P, peak, shift, st);
+    float2 *w;
+    int grid;
+    cudaError_t e = big_work(ctx, n, P, &w, &grid);
+    return e != cudaSuccess ? e : launch_pair_peak_big(n, St, tidx, Sp, degen, active, P, peak, shift, w, grid, st);
+}
 
 int check_lib(xcf_ctx *ctx, const xcf_library *lib) {
     if (!ctx) return XCF_ERR_ARG;
@@ -193,17 +229,17 @@ int index_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int
     if ((rc = scratch_t(ctx, S_SPEC_P, (size_t)P * H, &sp))) return rc;
     if ((rc = scratch_t(ctx, S_DEGEN, P, &degen))) return rc;
     if ((rc = scratch_t(ctx, S_KEYS, P, &keys))) return rc;
-    XCF_LAUNCH(XCF_STAGE_PREP, st, launch_prep(patterns, P, prep_args(g, c, r), sp, nullptr, degen, nullptr, st), "prep");
+    XCF_LAUNCH(XCF_STAGE_PREP, st, run_prep(ctx,patterns, P, prep_args(g, c, r), sp, nullptr, degen, nullptr, st), "prep");
     XCF_CHECK(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * P, st), "memset keys");
     if (peaks_all)   // degenerate patterns keep all-zero rows
         XCF_CHECK(cudaMemsetAsync(peaks_all, 0, sizeof(float) * (size_t)P * lib->T, st), "memset peaks");
     XCF_LAUNCH(XCF_STAGE_SEARCH, st,
-               launch_search(c.n, search_spectra(lib), lib->T, sp, degen, P, keys, peaks_all, ctx->num_sms, st),
+               run_search(ctx,c.n, search_spectra(lib), lib->T, sp, degen, P, keys, peaks_all, ctx->num_sms, st),
                "search");
     if (best) {
         XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_keys_to_best(keys, P, best, st), "keys_to_best");
         XCF_LAUNCH(XCF_STAGE_PEAK, st,
-                   launch_pair_peak(c.n, lib->spectra, best, sp, degen, nullptr, P, peak, shift, st),
+                   run_pair_peak(ctx,c.n, lib->spectra, best, sp, degen, nullptr, P, peak, shift, st),
                    "pair_peak");
     }
     return XCF_OK;
@@ -236,7 +272,7 @@ int refine_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, in
     const PrepArgs pa = prep_args(g, c, r), ps = prep_args_square(c, r);
     const ProjArgs pj = proj_args_cropped(g, c);
     const double alpha = alpha_of(g);
-    XCF_LAUNCH(XCF_STAGE_PREP, st, launch_prep(patterns, P, pa, sp, yp, degen, nullptr, st), "prep patterns");
+    XCF_LAUNCH(XCF_STAGE_PREP, st, run_prep(ctx,patterns, P, pa, sp, yp, degen, nullptr, st), "prep patterns");
     XCF_LAUNCH(XCF_STAGE_LOGPOLAR, st,
                launch_logpolar(yp, nullptr, P, n, r.nr, r.neta, (float)r.rmin, (float)r.rmax, lpp, st),
                "logpolar patterns");
@@ -248,15 +284,15 @@ int refine_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, in
         // X / Y: shift of the template at the current orientation
         XCF_LAUNCH(XCF_STAGE_PROJECT, st, launch_project(lib->master, lib->M, quats, pcs, active, P, pj, img, st),
                    "project");
-        XCF_LAUNCH(XCF_STAGE_PREP, st, launch_prep(img, P, ps, stt, nullptr, nullptr, active, st), "prep templates");
-        XCF_LAUNCH(XCF_STAGE_PEAK, st, launch_pair_peak(n, stt, nullptr, sp, degen, active, P, peak, shift, st),
+        XCF_LAUNCH(XCF_STAGE_PREP, st, run_prep(ctx,img, P, ps, stt, nullptr, nullptr, active, st), "prep templates");
+        XCF_LAUNCH(XCF_STAGE_PEAK, st, run_pair_peak(ctx,n, stt, nullptr, sp, degen, active, P, peak, shift, st),
                    "xy peak");
         XCF_LAUNCH(XCF_STAGE_UPDATE, st,
                    launch_update_xy(quats, shift, pcs, g->pcz, g->width, alpha, active, P, q1, st), "xy update");
         // Z: angular shift of the log-polar images
         XCF_LAUNCH(XCF_STAGE_PROJECT, st, launch_project(lib->master, lib->M, q1, pcs, active, P, pj, img, st),
                    "project");
-        XCF_LAUNCH(XCF_STAGE_PREP, st, launch_prep(img, P, ps, stt, yt, nullptr, active, st), "prep templates");
+        XCF_LAUNCH(XCF_STAGE_PREP, st, run_prep(ctx,img, P, ps, stt, yt, nullptr, active, st), "prep templates");
         XCF_LAUNCH(XCF_STAGE_LOGPOLAR, st,
                    launch_logpolar(yt, active, P, n, r.nr, r.neta, (float)r.rmin, (float)r.rmax, lpt, st),
                    "logpolar templates");
@@ -385,14 +421,14 @@ int xcf_prep(xcf_ctx *ctx, const float *images, int32_t P, const xcf_geometry *g
     Crop c;
     int rc = crop_of(g, 256, &c);
     if (rc) return fail(ctx, rc, "xcf_prep: detector too small");
-    if (!supported_n(c.n)) return fail(ctx, XCF_ERR_UNIMPLEMENTED, "xcf_prep: N = 256 is not built");
+    if (!supported_n(c.n)) return fail(ctx, XCF_ERR_UNIMPLEMENTED, "xcf_prep: detector side not supported");
     cudaSetDevice(ctx->device);
     const Resolved r = resolve(ctx->opt, c.n);
     int *degen = degenerate;
     if (!degen && (rc = scratch_t(ctx, S_DEGEN, P, &degen))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     XCF_LAUNCH(XCF_STAGE_PREP, st,
-               launch_prep(images, P, prep_args(g, c, r), reinterpret_cast<float2 *>(spectra), spatial, degen,
+               run_prep(ctx,images, P, prep_args(g, c, r), reinterpret_cast<float2 *>(spectra), spatial, degen,
                            nullptr, st),
                "prep");
     return XCF_OK;
@@ -407,7 +443,7 @@ int xcf_build_library(xcf_ctx *ctx, const float *master, int32_t M, const double
     Crop c;
     int rc = crop_of(g, 256, &c);
     if (rc) return fail(ctx, rc, "xcf_build_library: detector too small");
-    if (!supported_n(c.n)) return fail(ctx, XCF_ERR_UNIMPLEMENTED, "xcf_build_library: N = 256 is not built");
+    if (!supported_n(c.n)) return fail(ctx, XCF_ERR_UNIMPLEMENTED, "xcf_build_library: detector side not supported");
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const Resolved r = resolve(ctx->opt, c.n);
@@ -445,7 +481,7 @@ int xcf_build_library(xcf_ctx *ctx, const float *master, int32_t M, const double
             return rc;
         }
         e = launch_project(lib->master, M, lib->quats + 4 * (size_t)t0, nullptr, nullptr, nt, pj, img, st);
-        if (e == cudaSuccess) e = launch_prep(img, nt, ps, lib->spectra + H * t0, nullptr, degen, nullptr, st);
+        if (e == cudaSuccess) e = run_prep(ctx,img, nt, ps, lib->spectra + H * t0, nullptr, degen, nullptr, st);
         ctx->launches[XCF_STAGE_PROJECT] += 1;
         ctx->launches[XCF_STAGE_PREP] += 1;
     }
@@ -473,7 +509,7 @@ int xcf_build_library_images(xcf_ctx *ctx, const float *images, const double *qu
     Crop c;
     int rc = crop_of(g, 256, &c);
     if (rc) return fail(ctx, rc, "xcf_build_library_images: detector too small");
-    if (!supported_n(c.n)) return fail(ctx, XCF_ERR_UNIMPLEMENTED, "xcf_build_library_images: N = 256 is not built");
+    if (!supported_n(c.n)) return fail(ctx, XCF_ERR_UNIMPLEMENTED, "xcf_build_library_images: detector side not supported");
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const Resolved r = resolve(ctx->opt, c.n);
@@ -503,7 +539,7 @@ int xcf_build_library_images(xcf_ctx *ctx, const float *images, const double *qu
         xcf_library_free(lib);
         return rc;
     }
-    if (e == cudaSuccess) e = launch_prep(images, T, prep_args(g, c, r), lib->spectra, nullptr, degen, nullptr, st);
+    if (e == cudaSuccess) e = run_prep(ctx,images, T, prep_args(g, c, r), lib->spectra, nullptr, degen, nullptr, st);
     ctx->launches[XCF_STAGE_PREP] += 1;
     if (e == cudaSuccess && c.n == 128) {
         e = cudaMalloc(&lib->spectra_pk, sizeof(float2) * H * T);

@@ -33,6 +33,7 @@ enum Slot {
     S_IO_PAT,       // host pipeline: device copy of a chunk of patterns
     S_IO_PCS,
     S_IO_OUT,
+    S_WORK,         // per-CTA N x N work arrays of the N = 256 kernels
     S_COUNT
 };
 

@@ -178,6 +178,11 @@ __device__ __forceinline__ float parabola(float cm, float c0, float cp) {
 // consecutive shifts over a slice of the radii, sliding along l in blocks of
 // 8 so that every loaded value feeds 8 fused multiply-adds.
 constexpr int kEtaThreads = 256;
+// radii held in shared memory at a time (two images: 2 R neta floats <= 96 KB)
+__host__ __device__ __forceinline__ int eta_chunk_rows(int nr, int neta) {
+    const int r = 12288 / neta;
+    return r < nr ? (r > 0 ? r : 1) : nr;
+}
 __global__ void __launch_bounds__(kEtaThreads) k_eta_update(const float *__restrict__ lpT,
                                                             const float *__restrict__ lpP, int nr,
                                                             int neta, const double *__restrict__ q0s,
@@ -189,24 +194,20 @@ __global__ void __launch_bounds__(kEtaThreads) k_eta_update(const float *__restr
     const int p = blockIdx.x;
     if (!active[p]) return;
     extern __shared__ float4 smem_raw[];
+    const int R = eta_chunk_rows(nr, neta);  // radii per shared-memory chunk
     float *sa = reinterpret_cast<float *>(smem_raw);
-    float *sb = sa + nr * neta;
-    float *cacc = sb + nr * neta;           // [row groups][neta]
+    float *sb = sa + R * neta;
+    float *cacc = sb + R * neta;            // [row groups][neta]
     __shared__ double red[33];
     const int tot = nr * neta, tid = threadIdx.x;
     const float *ga = lpT + (size_t)p * tot, *gb = lpP + (size_t)p * tot;
     double s1 = 0, s2 = 0;
-    for (int i = tid; i < tot; i += kEtaThreads) {
-        float x = ga[i], y = gb[i];
-        sa[i] = x; sb[i] = y;
-        s1 += x; s2 += y;
-    }
-    const double ma = block_sum_d(s1, red) / tot;
-    const double mb = block_sum_d(s2, red) / tot;
+    for (int i = tid; i < tot; i += kEtaThreads) { s1 += ga[i]; s2 += gb[i]; }
+    const float ma = (float)(block_sum_d(s1, red) / tot);
+    const float mb = (float)(block_sum_d(s2, red) / tot);
     double n1 = 0, n2 = 0;
     for (int i = tid; i < tot; i += kEtaThreads) {
-        float x = sa[i] - (float)ma, y = sb[i] - (float)mb;
-        sa[i] = x; sb[i] = y;
+        const float x = ga[i] - ma, y = gb[i] - mb;
         n1 += (double)x * x; n2 += (double)y * y;
     }
     const double na = block_sum_d(n1, red), nb = block_sum_d(n2, red);
@@ -215,25 +216,36 @@ __global__ void __launch_bounds__(kEtaThreads) k_eta_update(const float *__restr
     const int G = neta / 8;                    // groups of 8 shifts
     const int RG = kEtaThreads / G;            // row groups
     const int gidx = tid % G, rg = tid / G;
-    if (rg < RG) {
-        float acc[8];
+    float acc[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = 0.f;
-        const int D0 = gidx * 8;
-        for (int m = rg; m < nr; m += RG) {
-            const float *ar = sa + m * neta, *br = sb + m * neta;
-            for (int l = 0; l < neta; l += 8) {
-                float av[8], bv[16];
+    for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+    const int D0 = gidx * 8;
+    for (int m0 = 0; m0 < nr; m0 += R) {       // chunks of R radii (mean-free) through shared memory
+        const int rows = min(R, nr - m0);
+        for (int i = tid; i < rows * neta; i += kEtaThreads) {
+            sa[i] = ga[(size_t)m0 * neta + i] - ma;
+            sb[i] = gb[(size_t)m0 * neta + i] - mb;
+        }
+        __syncthreads();
+        if (rg < RG) {
+            for (int m = rg; m < rows; m += RG) {
+                const float *ar = sa + m * neta, *br = sb + m * neta;
+                for (int l = 0; l < neta; l += 8) {
+                    float av[8], bv[16];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) av[j] = ar[l + j];
+                    for (int j = 0; j < 8; ++j) av[j] = ar[l + j];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) bv[j] = br[(l + D0 + j) & (neta - 1)];
+                    for (int j = 0; j < 16; ++j) bv[j] = br[(l + D0 + j) & (neta - 1)];
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
+                    for (int j = 0; j < 8; ++j)
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) acc[k] = fmaf(av[j], bv[j + k], acc[k]);
+                        for (int k = 0; k < 8; ++k) acc[k] = fmaf(av[j], bv[j + k], acc[k]);
+                }
             }
         }
+        __syncthreads();
+    }
+    if (rg < RG) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) cacc[rg * neta + D0 + k] = acc[k];
     }
@@ -372,7 +384,7 @@ cudaError_t launch_eta_update(const float *lpT, const float *lpP, int nr, int ne
     const int G = neta / 8;
     const int RG = G <= kEtaThreads ? kEtaThreads / G : 0;
     if (RG == 0) return cudaErrorInvalidValue;
-    const size_t sm = sizeof(float) * ((size_t)2 * nr * neta + (size_t)RG * neta);
+    const size_t sm = sizeof(float) * ((size_t)2 * eta_chunk_rows(nr, neta) * neta + (size_t)RG * neta);
     cudaError_t e = cudaFuncSetAttribute(k_eta_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_eta_update<<<P, kEtaThreads, sm, st>>>(lpT, lpP, nr, neta, q0, q1, alpha, tol_deg, active, iters, q_out);

@@ -29,6 +29,19 @@ cudaError_t launch_prep(const float *img, int P, const PrepArgs &a, float2 *spec
 cudaError_t launch_search(int N, const float2 *St, int T, const float2 *Sp, const int *degen, int P,
                           unsigned long long *keys, float *peaks_all, int num_sms, cudaStream_t st);
 
+// N = 256: the same three steps on a per-CTA N x N work array in global
+// memory (`work` holds grid * N * N complex values; big_grid gives the grid)
+int big_grid(int num_sms, long items);
+size_t big_work_bytes(int N, int grid);
+cudaError_t launch_prep_big(const float *img, int P, const PrepArgs &a, float2 *spec, float *spatial, int *degen,
+                            const int *active, float2 *work, int grid, cudaStream_t st);
+cudaError_t launch_search_big(int N, const float2 *St, int T, const float2 *Sp, const int *degen, int P,
+                              unsigned long long *keys, float *peaks_all, float2 *work, int grid,
+                              cudaStream_t st);
+cudaError_t launch_pair_peak_big(int N, const float2 *St, const int *tidx, const float2 *Sp, const int *degen,
+                                 const int *active, int P, float *peak, float *shift, float2 *work, int grid,
+                                 cudaStream_t st);
+
 // N = 128: library half spectra -> the search kernel's packed layout
 cudaError_t launch_pack_search_layout(const float2 *spectra, int T, int N, float2 *packed, cudaStream_t st);
 

@@ -63,7 +63,8 @@ int cuda_error(xcf_ctx *ctx, cudaError_t e, const char *where) {
 }  // namespace
 
 extern "C" int xcf_noalloc_max_patterns(int32_t n) {
-    if (n < 16 || n > 256 || (n & (n - 1))) return 0;
+    // N = 256 runs on per-CTA work arrays that this entry point does not hold
+    if (n < 16 || n > 128 || (n & (n - 1))) return 0;
     long lo = 0, hi = 1L << 24;
     while (lo < hi) {       // largest P whose scratch fits
         long mid = (lo + hi + 1) / 2;
@@ -83,6 +84,10 @@ extern "C" int xcf_index_noalloc(xcf_ctx *ctx, const xcf_library *lib, const flo
         return XCF_ERR_ARG;
     }
     const int n = lib->N;
+    if (n > 128) {
+        ctx->err = "xcf_index_noalloc: detectors of side 256 are searched with work arrays; use xcf_index";
+        return XCF_ERR_UNIMPLEMENTED;
+    }
     const int pmax = xcf_noalloc_max_patterns(n);
     if (P > pmax) {
         ctx->err = "xcf_index_noalloc: " + std::to_string(P) + " patterns exceed the fixed scratch (" +

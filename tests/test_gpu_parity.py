@@ -50,7 +50,7 @@ def _check_index(orc_best, orc_peak, orc_all, best, peak, rel_tie=2e-5):
 
 
 # ---------------------------------------------------------------- prep
-@pytest.mark.parametrize("n", [16, 32, 64, 128])
+@pytest.mark.parametrize("n", [16, 32, 64, 128, 256])
 def test_prep_matches_oracle(px, ctx, orc, n):
     rng = np.random.default_rng(n)
     imgs = (rng.standard_normal((5, n, n)) * 3 + 7).astype(np.float32)
@@ -124,7 +124,7 @@ def _patterns(orc, master, lib_q, idx, n, seed, pc=PC0, peak=300.0, perturb_deg=
 
 
 @pytest.mark.parametrize("n,T,P", [(16, 5, 3), (32, 9, 2), (64, 37, 5), (128, 41, 4), (128, 3, 1),
-                                   (128, 1, 2), (128, 200, 3)])
+                                   (128, 1, 2), (128, 200, 3), (256, 7, 2)])
 def test_correlate_all_matches_oracle(px, ctx, orc, n, T, P):
     master = synth.master_pattern("bcc", 512)
     lq = synth.random_quaternions(T, 10 + T)
@@ -142,7 +142,7 @@ def test_correlate_all_matches_oracle(px, ctx, orc, n, T, P):
     lib.close()
 
 
-@pytest.mark.parametrize("n,T,P", [(64, 50, 9), (128, 60, 12)])
+@pytest.mark.parametrize("n,T,P", [(64, 50, 9), (128, 60, 12), (256, 12, 3)])
 def test_index_matches_oracle(px, ctx, orc, n, T, P):
     master = synth.master_pattern("bcc", 1024)
     lq = synth.random_quaternions(T, 40 + n)
@@ -223,9 +223,8 @@ def test_config1_parity(px, ctx, orc):
 
 
 # ------------------------------------------------------------ refinement
-@pytest.mark.parametrize("noise", [None, 150.0])
-def test_refine_matches_oracle(px, orc, noise):
-    n, P = 128, 8
+@pytest.mark.parametrize("noise,n,P", [(None, 128, 8), (150.0, 128, 8), (150.0, 256, 4)])
+def test_refine_matches_oracle(px, orc, noise, n, P):
     master = synth.master_pattern("bcc", 1024)
     seeds = synth.random_quaternions(P, 90)
     truth = synth.perturb(seeds, 4.0, 91)
@@ -295,9 +294,15 @@ def test_host_pipeline_matches_device_path(px, orc):
 
 
 def test_errors_are_reported(px, ctx):
-    g = px.geometry(300, 300)                         # crops to 256: not built in this path
-    with pytest.raises(px.XcfError) as e:
-        px.xcf_prep(ctx, torch.zeros((1, 300, 300), device="cuda"), g)
-    assert e.value.code == -6
+    with pytest.raises(px.XcfError) as e:               # below the smallest 2^n crop
+        px.xcf_prep(ctx, torch.zeros((1, 12, 40), device="cuda"), px.geometry(40, 12))
+    assert e.value.code == px.xcf.XCF_ERR_SIZE
+    lib = px.xcf_build_library_images(ctx, torch.rand((2, 64, 64), device="cuda"),
+                                      torch.from_numpy(synth.random_quaternions(2, 0)).cuda(), px.geometry(64, 64))
+    with pytest.raises(px.XcfError) as e:               # no master pattern: nothing to re-project
+        px.xcf_refine(ctx, lib, torch.rand((1, 64, 64), device="cuda"),
+                      torch.from_numpy(synth.random_quaternions(1, 1)).cuda())
+    assert e.value.code == px.xcf.XCF_ERR_ARG
+    lib.close()
     with pytest.raises(TypeError):
         px.xcf_prep(ctx, torch.zeros((1, 64, 64), dtype=torch.float64, device="cuda"), px.geometry(64, 64))
