@@ -185,6 +185,35 @@ int xcf_refine(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int3
 int xcf_disorientation(xcf_ctx *ctx, const double *qa, const double *qb, int32_t n, double *out,
                        void *stream);
 
+/* Library builder with options.  Templates are projected from the master
+ * (images == NULL) or pre-processed from the caller's images [T, H, W]
+ * (master may then be NULL); flags:
+ *   XCF_LIB_SCREEN  also keep each template's unit-norm filtered spatial image
+ *                   in BF16 [T, N*N], needed by xcf_screen_topk.
+ * Synchronous with respect to `stream`. */
+#define XCF_LIB_SCREEN 1
+int xcf_build_library_ex(xcf_ctx *ctx, const float *master, int32_t M, const double *quats, int32_t T,
+                         const xcf_geometry *g, const float *images, int32_t flags, xcf_library **out,
+                         void *stream);
+
+/* Zero-shift correlation screen (paper, Eq. 1: the normalised dot product is
+ * the correlation at zero shift of the unit-norm filtered images; Eq. 3 is its
+ * generalisation to all shifts): score[p, t] = <y_p, y_t> computed on the
+ * tensor cores with BF16 operands and FP32 accumulation, and for each pattern
+ * the k best templates (1 <= k <= 64) by (score desc, index asc).
+ *   cand [P, k] int32 template indices (-1 where T < k); score [P, k] float32.
+ * The library must be built with XCF_LIB_SCREEN and hold at most 51,200
+ * templates.  Synchronous (it checks the kernel's status word);
+ * XCF_ERR_TIMEOUT if a bounded device wait gave up. */
+int xcf_screen_topk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, int32_t k,
+                    int32_t *cand, float *score, void *stream);
+
+/* FP32 FFT cross-correlation of each pattern against its own candidate list
+ * cand [P, k] (library indices; entries < 0 are skipped) -- the rescore of the
+ * precision form.  Outputs as xcf_index (best is a library index). */
+int xcf_rescore(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, const int32_t *cand,
+                int32_t k, int32_t *best, float *peak, float *shift, void *stream);
+
 /* Search then refine in one call (device memory): xcf_index, seeds = the
  * library orientations of the best templates (identity for degenerate
  * patterns), then xcf_refine.  Outputs as those two calls. */

@@ -96,6 +96,8 @@ def _lib_handle():
                                     C.c_int, _D, C.c_int, C.c_double, _D, _D, _I, _D], C.c_int),
                 "orc_refine_many": ([_F, C.c_int, _D, C.c_double, C.c_double, C.POINTER(Opts), _F,
                                      C.c_int, C.c_int, _D, C.c_int, C.c_double, _D, _D, _I], None),
+                "orc_bf16_round": ([C.c_double], C.c_double),
+                "orc_screen": ([_D, C.c_int, _D, C.c_int, C.c_long, C.c_int, _D], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -318,6 +320,21 @@ def disorientation(qa, qb):
     out = np.empty(qa.shape[0])
     _lib_handle().orc_disorientation_many(_d(qa), _d(qb), qa.shape[0], _d(out))
     return out
+
+
+# ------------------------------------------------------------- screen (Eq. 1)
+def bf16_round(x):
+    return _lib_handle().orc_bf16_round(float(x))
+
+
+def screen(yp, yt, bf16=True):
+    """Zero-shift scores S [P, T] = yp . yt^T in FP64 of the unit-norm filtered
+    images (flattened); bf16 rounds every input to BF16 first."""
+    yp = _f64(np.asarray(yp).reshape(len(yp), -1))
+    yt = _f64(np.asarray(yt).reshape(len(yt), -1))
+    S = np.empty((yp.shape[0], yt.shape[0]))
+    _lib_handle().orc_screen(_d(yp), yp.shape[0], _d(yt), yt.shape[0], yp.shape[1], 1 if bf16 else 0, _d(S))
+    return S
 
 
 # ---------------------------------------------------------------- refinement

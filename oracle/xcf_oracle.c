@@ -685,3 +685,36 @@ void orc_refine_many(const float *master, int M, const double *pcs, double sampl
                        patterns + (long)p * n * n, n, seeds + 4L * p, max_it, tol_deg,
                        quats + 4L * p, peaks + p, iters + p, NULL);
 }
+
+/* ---------------------------------------------------------------------- */
+/* zero-shift screen (Eq. 1: the normalised dot product is the correlation  */
+/* at zero shift of the unit-norm filtered images)                         */
+/* ---------------------------------------------------------------------- */
+
+/* Round to the nearest BF16 value (ties to even) through float32, the
+ * rounding the tensor-core operands receive. */
+double orc_bf16_round(double x) {
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+/* S[p][t] = sum_k yp[p][k] yt[t][k] in FP64; with bf16 != 0 every input is
+ * first rounded to BF16 (so that only the accumulation differs from the
+ * tensor cores).  yp [P][K], yt [T][K]. */
+void orc_screen(const double *yp, int P, const double *yt, int T, long K, int bf16, double *S) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int p = 0; p < P; ++p)
+        for (int t = 0; t < T; ++t) {
+            double s = 0.0;
+            for (long k = 0; k < K; ++k) {
+                double a = yp[(long)p * K + k], b = yt[(long)t * K + k];
+                if (bf16) { a = orc_bf16_round(a); b = orc_bf16_round(b); }
+                s += a * b;
+            }
+            S[(long)p * T + t] = s;
+        }
+}

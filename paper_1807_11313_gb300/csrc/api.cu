@@ -560,6 +560,7 @@ int xcf_library_free(xcf_library *lib) {
     cudaSetDevice(lib->device);
     if (lib->spectra) cudaFree(lib->spectra);
     if (lib->spectra_pk) cudaFree(lib->spectra_pk);
+    if (lib->bf16) cudaFree(lib->bf16);
     if (lib->quats) cudaFree(lib->quats);
     if (lib->master) cudaFree(lib->master);
     delete lib;
@@ -757,6 +758,176 @@ int xcf_profile_read(xcf_ctx *ctx, double *ms, int64_t *launches, int reset) {
         }
     }
     return status;
+}
+
+// ---------------------------------------------------------------- screen
+namespace {
+
+// chunk of patterns/templates whose f32 images and scores stay within ~1 GB
+int screen_chunk(int n, int T) {
+    const size_t lim = (size_t)1 << 30;
+    size_t c = lim / ((size_t)n * n * 4);
+    const size_t c2 = lim / ((size_t)(T > 0 ? T : 1) * 4);
+    if (c2 < c) c = c2;
+    if (c > (size_t)kChunk) c = kChunk;
+    return c < 1 ? 1 : (int)c;
+}
+
+// BF16 unit-norm filtered images of the library's templates: from the
+// caller's template images, or re-projected from the master
+int make_screen_images(xcf_ctx *ctx, xcf_library *lib, const float *images, cudaStream_t st) {
+    const xcf_geometry *g = &lib->geom;
+    Crop c;
+    crop_of(g, 256, &c);
+    const Resolved r = resolve(ctx->opt, c.n);
+    const size_t nn = (size_t)c.n * c.n, H = (size_t)c.n * (c.n / 2 + 1);
+    if (cudaMalloc(&lib->bf16, 2 * nn * lib->T) != cudaSuccess) {
+        cudaGetLastError();
+        lib->bf16 = nullptr;
+        return fail(ctx, XCF_ERR_OOM, "screen images: allocation failed");
+    }
+    const int chunk = screen_chunk(c.n, 1);
+    int rc;
+    for (int t0 = 0; t0 < lib->T; t0 += chunk) {
+        const int nt = lib->T - t0 < chunk ? lib->T - t0 : chunk;
+        float2 *spec;
+        float *spat, *img;
+        int *degen;
+        if ((rc = scratch_t(ctx, S_SPEC_T, H * nt, &spec)) || (rc = scratch_t(ctx, S_SPATIAL_T, nn * nt, &spat)) ||
+            (rc = scratch_t(ctx, S_DEGEN, nt, &degen)))
+            return rc;
+        if (images) {
+            XCF_LAUNCH(XCF_STAGE_PREP, st,
+                       run_prep(ctx, images + (size_t)g->width * g->height * t0, nt, prep_args(g, c, r), spec, spat,
+                                degen, nullptr, st),
+                       "screen prep");
+        } else {
+            if ((rc = scratch_t(ctx, S_IMG, nn * nt, &img))) return rc;
+            XCF_LAUNCH(XCF_STAGE_PROJECT, st,
+                       launch_project(lib->master, lib->M, lib->quats + 4 * (size_t)t0, nullptr, nullptr, nt,
+                                      proj_args_cropped(g, c), img, st),
+                       "screen project");
+            XCF_LAUNCH(XCF_STAGE_PREP, st,
+                       run_prep(ctx, img, nt, prep_args_square(c, r), spec, spat, degen, nullptr, st), "screen prep");
+        }
+        XCF_LAUNCH(XCF_STAGE_OTHER, st,
+                   launch_to_bf16(spat, nn * nt, static_cast<char *>(lib->bf16) + 2 * nn * t0, st), "bf16");
+    }
+    return XCF_OK;
+}
+
+}  // namespace
+
+int xcf_build_library_ex(xcf_ctx *ctx, const float *master, int32_t M, const double *quats, int32_t T,
+                         const xcf_geometry *g, const float *images, int32_t flags, xcf_library **out,
+                         void *stream) {
+    if (!ctx) return XCF_ERR_ARG;
+    if (!out) return fail(ctx, XCF_ERR_ARG, "xcf_build_library_ex: out is NULL");
+    if (flags & ~XCF_LIB_SCREEN) return fail(ctx, XCF_ERR_ARG, "xcf_build_library_ex: unknown flags");
+    int rc = images ? xcf_build_library_images(ctx, images, quats, T, g, master, M, out, stream)
+                    : xcf_build_library(ctx, master, M, quats, T, g, out, stream);
+    if (rc || !(flags & XCF_LIB_SCREEN)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = make_screen_images(ctx, *out, images, st);
+    if (rc == XCF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = cuda_fail(ctx, cudaGetLastError(), "screen images");
+    if (rc) {
+        xcf_library_free(*out);
+        *out = nullptr;
+    }
+    return rc;
+}
+
+int xcf_screen_topk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, int32_t k,
+                    int32_t *cand, float *score, void *stream) {
+    int rc = check_lib(ctx, lib);
+    if (rc) return rc;
+    if (P == 0) return XCF_OK;
+    if (!patterns || !cand || !score || P < 0 || k < 1 || k > 64)
+        return fail(ctx, XCF_ERR_ARG, "xcf_screen_topk: bad argument (1 <= k <= 64)");
+    if (!lib->bf16) return fail(ctx, XCF_ERR_ARG, "xcf_screen_topk: library built without XCF_LIB_SCREEN");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const xcf_geometry *g = &lib->geom;
+    Crop c;
+    crop_of(g, 256, &c);
+    const Resolved r = resolve(ctx->opt, c.n);
+    const size_t nn = (size_t)c.n * c.n, H = (size_t)c.n * (c.n / 2 + 1), img = (size_t)g->width * g->height;
+    if ((size_t)lib->T * 4 > 200 * 1024) return fail(ctx, XCF_ERR_SIZE, "xcf_screen_topk: more than 51,200 templates");
+    const int chunk = screen_chunk(c.n, lib->T);
+    int *err;
+    if ((rc = scratch_t(ctx, S_ERR, 1, &err))) return rc;
+    XCF_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st), "clear status");
+    for (int p0 = 0; p0 < P; p0 += chunk) {
+        const int np = P - p0 < chunk ? P - p0 : chunk;
+        float2 *spec;
+        float *spat, *S;
+        int *degen;
+        void *a;
+        if ((rc = scratch_t(ctx, S_SPEC_P, H * np, &spec)) || (rc = scratch_t(ctx, S_SPATIAL_P, nn * np, &spat)) ||
+            (rc = scratch_t(ctx, S_DEGEN, np, &degen)) || (rc = scratch(ctx, S_BF16_P, 2 * nn * np, &a)) ||
+            (rc = scratch_t(ctx, S_SCORE, (size_t)np * lib->T, &S)))
+            return rc;
+        XCF_LAUNCH(XCF_STAGE_PREP, st,
+                   run_prep(ctx, patterns + img * p0, np, prep_args(g, c, r), spec, spat, degen, nullptr, st),
+                   "screen prep");
+        XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_to_bf16(spat, nn * np, a, st), "bf16");
+        XCF_LAUNCH(XCF_STAGE_SEARCH, st, launch_screen_tc(a, np, lib->bf16, lib->T, (int)nn, S, err, st), "screen");
+        XCF_LAUNCH(XCF_STAGE_OTHER, st,
+                   launch_topk_rows(S, np, lib->T, k, cand + (size_t)k * p0, score + (size_t)k * p0, st), "topk");
+    }
+    int h_err = 0;
+    XCF_CHECK(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+    XCF_CHECK(cudaStreamSynchronize(st), "xcf_screen_topk");
+    if (h_err) return fail(ctx, XCF_ERR_TIMEOUT, "xcf_screen_topk: a tensor-core pipeline wait timed out");
+    return XCF_OK;
+}
+
+int xcf_rescore(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, const int32_t *cand,
+                int32_t k, int32_t *best, float *peak, float *shift, void *stream) {
+    int rc = check_lib(ctx, lib);
+    if (rc) return rc;
+    if (P == 0) return XCF_OK;
+    if (!patterns || !cand || !best || !peak || !shift || P < 0 || k < 1)
+        return fail(ctx, XCF_ERR_ARG, "xcf_rescore: bad argument");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const xcf_geometry *g = &lib->geom;
+    Crop c;
+    crop_of(g, 256, &c);
+    const Resolved r = resolve(ctx->opt, c.n);
+    const size_t H = (size_t)c.n * (c.n / 2 + 1), img = (size_t)g->width * g->height;
+    for (int p0 = 0; p0 < P; p0 += kChunk) {
+        const int np = P - p0 < kChunk ? P - p0 : kChunk;
+        float2 *sp;
+        int *degen;
+        unsigned long long *keys;
+        if ((rc = scratch_t(ctx, S_SPEC_P, H * np, &sp)) || (rc = scratch_t(ctx, S_DEGEN, np, &degen)) ||
+            (rc = scratch_t(ctx, S_KEYS, np, &keys)))
+            return rc;
+        const int *cp = cand + (size_t)k * p0;
+        XCF_LAUNCH(XCF_STAGE_PREP, st,
+                   run_prep(ctx, patterns + img * p0, np, prep_args(g, c, r), sp, nullptr, degen, nullptr, st),
+                   "prep");
+        XCF_CHECK(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * np, st), "memset keys");
+        if (c.n <= 128) {
+            XCF_LAUNCH(XCF_STAGE_SEARCH, st,
+                       launch_search_list(c.n, lib->spectra, cp, k, sp, degen, np, keys, nullptr, ctx->num_sms, st),
+                       "rescore");
+        } else {
+            float2 *w;
+            int grid;
+            XCF_CHECK(big_work(ctx, c.n, (long)np * ((k + 1) / 2), &w, &grid), "work arrays");
+            XCF_LAUNCH(XCF_STAGE_SEARCH, st,
+                       launch_search_big(c.n, lib->spectra, 0, sp, degen, np, keys, nullptr, w, grid, st, cp, k),
+                       "rescore");
+        }
+        XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_keys_to_best(keys, np, best + p0, st), "keys_to_best");
+        XCF_LAUNCH(XCF_STAGE_PEAK, st,
+                   run_pair_peak(ctx, c.n, lib->spectra, best + p0, sp, degen, nullptr, np, peak + p0,
+                                 shift + 2 * (size_t)p0, st),
+                   "pair_peak");
+    }
+    return XCF_OK;
 }
 
 }  // extern "C"

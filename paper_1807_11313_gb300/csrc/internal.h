@@ -34,6 +34,9 @@ enum Slot {
     S_IO_PCS,
     S_IO_OUT,
     S_WORK,         // per-CTA N x N work arrays of the N = 256 kernels
+    S_BF16_P,       // screen: pattern images in BF16
+    S_SCORE,        // screen: zero-shift scores of a chunk
+    S_ERR,          // device status word of kernels with bounded waits
     S_COUNT
 };
 
@@ -62,6 +65,7 @@ struct xcf_library {
     double pc[3] = {0, 0, 0};
     float2 *spectra = nullptr;
     float2 *spectra_pk = nullptr;   // N = 128 only: the search kernel's packed layout
+    void *bf16 = nullptr;           // screen: unit-norm filtered images [T][N*N] in BF16
     double *quats = nullptr;
     float *master = nullptr;
 };

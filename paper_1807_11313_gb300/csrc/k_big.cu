@@ -231,7 +231,8 @@ __global__ void __launch_bounds__(kThreads) k_search_big(const float2 *__restric
                                                          const int *__restrict__ degen, int P, int ppc,
                                                          unsigned long long *__restrict__ keys,
                                                          float *__restrict__ peaks_all,
-                                                         float2 *__restrict__ work) {
+                                                         float2 *__restrict__ work,
+                                                         const int *__restrict__ cand, int kc) {
     constexpr int HW = N / 2 + 1;
     extern __shared__ float4 smem_raw[];
     float2 *sm = reinterpret_cast<float2 *>(smem_raw);
@@ -240,7 +241,9 @@ __global__ void __launch_bounds__(kThreads) k_search_big(const float2 *__restric
     float2 *Z = work + (size_t)blockIdx.x * N * N;
     make_tw<N>(tw, +1);
     __syncthreads();
-    const int npairs = (T + 1) / 2, nchunks = (npairs + ppc - 1) / ppc;
+    // slots: every template, or each pattern's candidate list (entries < 0 are empty)
+    const int n = cand ? kc : T;
+    const int npairs = (n + 1) / 2, nchunks = (npairs + ppc - 1) / ppc;
     for (long item = blockIdx.x; item < (long)P * nchunks; item += gridDim.x) {
         const int p = (int)(item / nchunks), ch = (int)(item % nchunks);
         if (degen[p]) continue;
@@ -248,8 +251,10 @@ __global__ void __launch_bounds__(kThreads) k_search_big(const float2 *__restric
         float best_v = -INFINITY;
         int best_t = -1;
         for (int pi = ch * ppc; pi < min(npairs, (ch + 1) * ppc); ++pi) {
-            const int t1 = 2 * pi, t2 = min(t1 + 1, T - 1);
-            build_pair_big<N>(Z, St + (size_t)t1 * N * HW, St + (size_t)t2 * N * HW, sp);
+            const int j1 = 2 * pi, j2 = min(j1 + 1, n - 1);
+            const int t1 = cand ? cand[(size_t)p * kc + j1] : j1;
+            const int t2 = cand ? cand[(size_t)p * kc + j2] : j2;
+            build_pair_big<N>(Z, St + (size_t)max(t1, 0) * N * HW, St + (size_t)max(t2, 0) * N * HW, sp);
             __syncthreads();
             fft2_global<N>(Z, sm, tw);
             float m1 = -INFINITY, m2 = -INFINITY;
@@ -260,11 +265,13 @@ __global__ void __launch_bounds__(kThreads) k_search_big(const float2 *__restric
             }
             m1 = block_max_b(m1, redf);
             m2 = block_max_b(m2, redf);
-            if (m1 > best_v) { best_v = m1; best_t = t1; }
-            if (t2 != t1 && m2 > best_v) { best_v = m2; best_t = t2; }
+            if (t1 < 0) m1 = -INFINITY;
+            if (t2 < 0) m2 = -INFINITY;
+            if (t1 >= 0 && (m1 > best_v || (m1 == best_v && t1 < best_t))) { best_v = m1; best_t = t1; }
+            if (j2 != j1 && t2 >= 0 && (m2 > best_v || (m2 == best_v && t2 < best_t))) { best_v = m2; best_t = t2; }
             if (peaks_all && threadIdx.x == 0) {
-                peaks_all[(size_t)p * T + t1] = m1;
-                if (t2 != t1) peaks_all[(size_t)p * T + t2] = m2;
+                peaks_all[(size_t)p * n + j1] = m1;
+                if (j2 != j1) peaks_all[(size_t)p * n + j2] = m2;
             }
         }
         if (threadIdx.x == 0 && best_t >= 0) atomicMax(keys + p, pack_key(best_v, best_t));
@@ -364,18 +371,19 @@ cudaError_t launch_prep_big(const float *img, int P, const PrepArgs &a, float2 *
 
 cudaError_t launch_search_big(int N, const float2 *St, int T, const float2 *Sp, const int *degen, int P,
                               unsigned long long *keys, float *peaks_all, float2 *work, int grid,
-                              cudaStream_t st) {
-    if (P <= 0 || T <= 0) return cudaSuccess;
+                              cudaStream_t st, const int *cand, int kc) {
+    if (P <= 0 || (cand ? kc : T) <= 0) return cudaSuccess;
     if (N != 256) return cudaErrorInvalidValue;
     cudaError_t e = set_smem_b(k_search_big<256>, smem_big(256));
     if (e != cudaSuccess) return e;
-    const int npairs = (T + 1) / 2;
+    const int npairs = ((cand ? kc : T) + 1) / 2;
     // chunks of pairs so that there are at least ~4 work items per CTA
     long want = 4L * grid;
     int nchunks = (int)((want + P - 1) / P);
     nchunks = nchunks < 1 ? 1 : (nchunks > npairs ? npairs : nchunks);
     const int ppc = (npairs + nchunks - 1) / nchunks;
-    k_search_big<256><<<grid, kThreads, smem_big(256), st>>>(St, T, Sp, degen, P, ppc, keys, peaks_all, work);
+    k_search_big<256><<<grid, kThreads, smem_big(256), st>>>(St, T, Sp, degen, P, ppc, keys, peaks_all, work,
+                                                             cand, kc);
     return cudaGetLastError();
 }
 

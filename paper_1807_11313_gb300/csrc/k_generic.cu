@@ -225,7 +225,8 @@ __global__ void __launch_bounds__(kThreads) k_search_generic(const float2 *__res
                                                              const int *__restrict__ degen,
                                                              int pairs_per_cta,
                                                              unsigned long long *__restrict__ keys,
-                                                             float *__restrict__ peaks_all) {
+                                                             float *__restrict__ peaks_all,
+                                                             const int *__restrict__ cand, int kc) {
     constexpr int LD = N + 1, HW = N / 2 + 1;
     extern __shared__ float4 smem_raw[];
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
@@ -235,14 +236,18 @@ __global__ void __launch_bounds__(kThreads) k_search_generic(const float2 *__res
     if (degen[p]) return;
     make_twiddles<N>(twi, +1);
     const float2 *sp = Sp + (size_t)p * N * HW;
-    const int npairs = (T + 1) / 2;
+    // slots: every template, or this pattern's candidate list (entries < 0 are empty)
+    const int n = cand ? kc : T;
+    const int npairs = (n + 1) / 2;
     const int pb = blockIdx.x * pairs_per_cta, pe = min(npairs, pb + pairs_per_cta);
     float best_v = -INFINITY;
     int best_t = -1;
     for (int pi = pb; pi < pe; ++pi) {
-        const int t1 = 2 * pi, t2 = min(t1 + 1, T - 1);
+        const int j1 = 2 * pi, j2 = min(j1 + 1, n - 1);
+        const int t1 = cand ? cand[(size_t)p * kc + j1] : j1;
+        const int t2 = cand ? cand[(size_t)p * kc + j2] : j2;
         __syncthreads();
-        build_pair_spectrum<N>(buf, St + (size_t)t1 * N * HW, St + (size_t)t2 * N * HW, sp);
+        build_pair_spectrum<N>(buf, St + (size_t)max(t1, 0) * N * HW, St + (size_t)max(t2, 0) * N * HW, sp);
         __syncthreads();
         fft2_smem<N>(buf, twi);
         float m1 = -INFINITY, m2 = -INFINITY;
@@ -253,11 +258,13 @@ __global__ void __launch_bounds__(kThreads) k_search_generic(const float2 *__res
         }
         m1 = block_max(m1, redf);
         m2 = block_max(m2, redf);
-        if (m1 > best_v) { best_v = m1; best_t = t1; }
-        if (t2 != t1 && m2 > best_v) { best_v = m2; best_t = t2; }
+        if (t1 < 0) m1 = -INFINITY;
+        if (t2 < 0) m2 = -INFINITY;
+        if (t1 >= 0 && (m1 > best_v || (m1 == best_v && t1 < best_t))) { best_v = m1; best_t = t1; }
+        if (j2 != j1 && t2 >= 0 && (m2 > best_v || (m2 == best_v && t2 < best_t))) { best_v = m2; best_t = t2; }
         if (peaks_all && threadIdx.x == 0) {
-            peaks_all[(size_t)p * T + t1] = m1;
-            if (t2 != t1) peaks_all[(size_t)p * T + t2] = m2;
+            peaks_all[(size_t)p * n + j1] = m1;
+            if (j2 != j1) peaks_all[(size_t)p * n + j2] = m2;
         }
     }
     if (threadIdx.x == 0 && best_t >= 0) atomicMax(keys + p, pack_key(best_v, best_t));
@@ -364,11 +371,12 @@ cudaError_t prep_n(const float *img, int P, const PrepArgs &a, float2 *spec, flo
 
 template <int N>
 cudaError_t search_n(const float2 *St, int T, const float2 *Sp, const int *degen, int P,
-                     unsigned long long *keys, float *peaks_all, int num_sms, cudaStream_t st) {
+                     unsigned long long *keys, float *peaks_all, int num_sms, cudaStream_t st,
+                     const int *cand = nullptr, int kc = 0) {
     size_t sm = smem_bytes_generic<N>();
     cudaError_t e = set_smem(k_search_generic<N>, sm);
     if (e != cudaSuccess) return e;
-    const int npairs = (T + 1) / 2;
+    const int npairs = ((cand ? kc : T) + 1) / 2;
     // enough CTAs to fill the GPU a few times over, at least 4 pairs each
     long want = (long)num_sms * 8;
     int chunks = (int)((want + P - 1) / P);
@@ -376,7 +384,7 @@ cudaError_t search_n(const float2 *St, int T, const float2 *Sp, const int *degen
     int ppc = (npairs + chunks - 1) / chunks;
     chunks = (npairs + ppc - 1) / ppc;
     dim3 grid(chunks, P);
-    k_search_generic<N><<<grid, kThreads, sm, st>>>(St, T, Sp, degen, ppc, keys, peaks_all);
+    k_search_generic<N><<<grid, kThreads, sm, st>>>(St, T, Sp, degen, ppc, keys, peaks_all, cand, kc);
     return cudaGetLastError();
 }
 
@@ -423,6 +431,19 @@ cudaError_t launch_search_generic128(const float2 *St, int T, const float2 *Sp, 
                                      unsigned long long *keys, float *peaks_all, int num_sms,
                                      cudaStream_t st) {
     return search_n<128>(St, T, Sp, degen, P, keys, peaks_all, num_sms, st);
+}
+
+cudaError_t launch_search_list(int N, const float2 *St, const int *cand, int kc, const float2 *Sp,
+                               const int *degen, int P, unsigned long long *keys, float *peaks, int num_sms,
+                               cudaStream_t st) {
+    if (P <= 0 || kc <= 0) return cudaSuccess;
+    switch (N) {
+        case 16: return search_n<16>(St, 0, Sp, degen, P, keys, peaks, num_sms, st, cand, kc);
+        case 32: return search_n<32>(St, 0, Sp, degen, P, keys, peaks, num_sms, st, cand, kc);
+        case 64: return search_n<64>(St, 0, Sp, degen, P, keys, peaks, num_sms, st, cand, kc);
+        case 128: return search_n<128>(St, 0, Sp, degen, P, keys, peaks, num_sms, st, cand, kc);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_pair_peak(int N, const float2 *St, const int *tidx, const float2 *Sp,

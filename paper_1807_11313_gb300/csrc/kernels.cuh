@@ -37,7 +37,19 @@ cudaError_t launch_prep_big(const float *img, int P, const PrepArgs &a, float2 *
                             const int *active, float2 *work, int grid, cudaStream_t st);
 cudaError_t launch_search_big(int N, const float2 *St, int T, const float2 *Sp, const int *degen, int P,
                               unsigned long long *keys, float *peaks_all, float2 *work, int grid,
-                              cudaStream_t st);
+                              cudaStream_t st, const int *cand = nullptr, int kc = 0);
+
+// search over each pattern's candidate list cand [P][kc] (library indices, < 0 empty)
+cudaError_t launch_search_list(int N, const float2 *St, const int *cand, int kc, const float2 *Sp,
+                               const int *degen, int P, unsigned long long *keys, float *peaks, int num_sms,
+                               cudaStream_t st);
+
+// BF16 zero-shift screen S[P][T] = A[P][K] . B[T][K]^T on tcgen05; err set on a timed-out wait
+cudaError_t launch_screen_tc(const void *A, int P, const void *B, int T, int K, float *S, int *err,
+                             cudaStream_t st);
+// top-k (k <= 64) of each row of S [P][T]: candidates by (score desc, index asc)
+cudaError_t launch_topk_rows(const float *S, int P, int T, int k, int *cand, float *score, cudaStream_t st);
+cudaError_t launch_to_bf16(const float *x, size_t n, void *y, cudaStream_t st);
 cudaError_t launch_pair_peak_big(int N, const float2 *St, const int *tidx, const float2 *Sp, const int *degen,
                                  const int *active, int P, float *peak, float *shift, float2 *work, int grid,
                                  cudaStream_t st);

@@ -71,6 +71,10 @@ _SIGS = {
     "xcf_disorientation": ([_P, _P, _P, _I32, _P, _P], C.c_int),
     "xcf_index_refine_host": ([_P, _P, _P, _I32, _P, _I32, _P, _P, _P, _P, _P, _P], C.c_int),
     "xcf_index_refine": ([_P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "xcf_build_library_ex": ([_P, _P, _I32, _P, _I32, C.POINTER(xcf_geometry), _P, _I32, C.POINTER(_P), _P],
+                             C.c_int),
+    "xcf_screen_topk": ([_P, _P, _P, _I32, _I32, _P, _P, _P], C.c_int),
+    "xcf_rescore": ([_P, _P, _P, _I32, _P, _I32, _P, _P, _P, _P], C.c_int),
     "xcf_index_noalloc": ([_P, _P, _P, _I32, _P, _P, _P, _P], C.c_int),
     "xcf_noalloc_max_patterns": ([_I32], C.c_int),
     "xcf_profile_enable": ([_P, C.c_int], C.c_int),
@@ -355,4 +359,44 @@ def xcf_index_noalloc(ctx: Context, lib: Library, patterns, best, peak, shift):
     _check(load().xcf_index_noalloc(ctx.handle, lib.handle, _ptr(patterns, torch.float32, "patterns"), P,
                                     _ptr(best, torch.int32, "best"), _ptr(peak, torch.float32, "peak"),
                                     _ptr(shift, torch.float32, "shift"), _stream()), ctx.handle)
+    return best, peak, shift
+
+
+XCF_LIB_SCREEN = 1
+
+
+def xcf_build_library_ex(ctx: Context, quats, geom: xcf_geometry, master=None, images=None, flags: int = 0) -> Library:
+    """Library from the master (images None) or from template images; flags
+    XCF_LIB_SCREEN keeps BF16 filtered images for xcf_screen_topk."""
+    h = C.c_void_p()
+    M = master.shape[-1] if master is not None else 0
+    _check(load().xcf_build_library_ex(ctx.handle, _ptr(master, torch.float32, "master", True), M,
+                                       _ptr(quats, torch.float64, "quats"), quats.shape[0], C.byref(geom),
+                                       _ptr(images, torch.float32, "images", True), int(flags), C.byref(h),
+                                       _stream()), ctx.handle)
+    return Library(h, geom, quats)
+
+
+def xcf_screen_topk(ctx: Context, lib: Library, patterns, k: int = 32):
+    """-> (cand [P, k] int32, score [P, k] float32): BF16 zero-shift screen on the tensor cores."""
+    P = patterns.shape[0]
+    cand = torch.empty((P, k), dtype=torch.int32, device=patterns.device)
+    score = torch.empty((P, k), dtype=torch.float32, device=patterns.device)
+    _check(load().xcf_screen_topk(ctx.handle, lib.handle, _ptr(patterns, torch.float32, "patterns"), P, int(k),
+                                  _ptr(cand, torch.int32, "cand"), _ptr(score, torch.float32, "score"), _stream()),
+           ctx.handle)
+    return cand, score
+
+
+def xcf_rescore(ctx: Context, lib: Library, patterns, cand):
+    """FP32 FFT cross-correlation against each pattern's candidates -> (best, peak, shift)."""
+    P, k = cand.shape
+    d = patterns.device
+    best = torch.empty(P, dtype=torch.int32, device=d)
+    peak = torch.empty(P, dtype=torch.float32, device=d)
+    shift = torch.empty((P, 2), dtype=torch.float32, device=d)
+    _check(load().xcf_rescore(ctx.handle, lib.handle, _ptr(patterns, torch.float32, "patterns"), P,
+                              _ptr(cand, torch.int32, "cand"), int(k), _ptr(best, torch.int32, "best"),
+                              _ptr(peak, torch.float32, "peak"), _ptr(shift, torch.float32, "shift"), _stream()),
+           ctx.handle)
     return best, peak, shift
