@@ -214,6 +214,11 @@ int xcf_screen_topk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns,
 int xcf_rescore(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, const int32_t *cand,
                 int32_t k, int32_t *best, float *peak, float *shift, void *stream);
 
+/* Refinement seeded by library templates: seeds = library orientations of
+ * best [P] (identity where best < 0), then xcf_refine. */
+int xcf_refine_best(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, const int32_t *best,
+                    const double *pcs, double *quats, float *peak, int32_t *iters, void *stream);
+
 /* Search then refine in one call (device memory): xcf_index, seeds = the
  * library orientations of the best templates (identity for degenerate
  * patterns), then xcf_refine.  Outputs as those two calls. */
@@ -270,7 +275,8 @@ int xcf_noalloc_max_patterns(int32_t n);
 #define XCF_STAGE_LOGPOLAR 4   /* log-polar resampling                            */
 #define XCF_STAGE_UPDATE   5   /* refinement updates (X/Y shift, angular xcf + Z) */
 #define XCF_STAGE_OTHER    6   /* small bookkeeping kernels                       */
-#define XCF_NUM_STAGES     7
+#define XCF_STAGE_SCREEN   7   /* tensor-core zero-shift screen (GEMM)            */
+#define XCF_NUM_STAGES     8
 
 /* Turn event timing on (1) or off (0).  Host only. */
 int xcf_profile_enable(xcf_ctx *ctx, int on);

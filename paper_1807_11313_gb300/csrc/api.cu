@@ -670,6 +670,29 @@ int xcf_index_refine(xcf_ctx *ctx, const xcf_library *lib, const float *patterns
     return XCF_OK;
 }
 
+int xcf_refine_best(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, const int32_t *best,
+                    const double *pcs, double *quats, float *peak, int32_t *iters, void *stream) {
+    int rc = check_lib(ctx, lib);
+    if (rc) return rc;
+    if (P == 0) return XCF_OK;
+    if (!patterns || !best || !quats || !peak || !iters || P < 0)
+        return fail(ctx, XCF_ERR_ARG, "xcf_refine_best: bad argument");
+    if (!lib->master) return fail(ctx, XCF_ERR_ARG, "xcf_refine_best: library has no master pattern");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t img = (size_t)lib->geom.width * lib->geom.height;
+    for (int p0 = 0; p0 < P; p0 += kChunk) {
+        const int np = P - p0 < kChunk ? P - p0 : kChunk;
+        double *seeds;
+        if ((rc = scratch_t(ctx, S_SEEDS, (size_t)np * 4, &seeds))) return rc;
+        XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_gather_seeds(lib->quats, best + p0, np, seeds, st), "seeds");
+        if ((rc = refine_chunk(ctx, lib, patterns + img * p0, np, seeds, pcs ? pcs + 3 * (size_t)p0 : nullptr,
+                               quats + 4 * (size_t)p0, peak + p0, iters + p0, st)))
+            return rc;
+    }
+    return XCF_OK;
+}
+
 int xcf_index_refine_host(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P,
                           const double *pcs, int32_t chunk, int32_t *best, float *peak, float *shift,
                           double *quats, float *rpeak, int32_t *iters) {
@@ -871,7 +894,7 @@ int xcf_screen_topk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns,
                    run_prep(ctx, patterns + img * p0, np, prep_args(g, c, r), spec, spat, degen, nullptr, st),
                    "screen prep");
         XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_to_bf16(spat, nn * np, a, st), "bf16");
-        XCF_LAUNCH(XCF_STAGE_SEARCH, st, launch_screen_tc(a, np, lib->bf16, lib->T, (int)nn, S, err, st), "screen");
+        XCF_LAUNCH(XCF_STAGE_SCREEN, st, launch_screen_tc(a, np, lib->bf16, lib->T, (int)nn, S, err, st), "screen");
         XCF_LAUNCH(XCF_STAGE_OTHER, st,
                    launch_topk_rows(S, np, lib->T, k, cand + (size_t)k * p0, score + (size_t)k * p0, st), "topk");
     }

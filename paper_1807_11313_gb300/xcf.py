@@ -75,13 +75,14 @@ _SIGS = {
                              C.c_int),
     "xcf_screen_topk": ([_P, _P, _P, _I32, _I32, _P, _P, _P], C.c_int),
     "xcf_rescore": ([_P, _P, _P, _I32, _P, _I32, _P, _P, _P, _P], C.c_int),
+    "xcf_refine_best": ([_P, _P, _P, _I32, _P, _P, _P, _P, _P, _P], C.c_int),
     "xcf_index_noalloc": ([_P, _P, _P, _I32, _P, _P, _P, _P], C.c_int),
     "xcf_noalloc_max_patterns": ([_I32], C.c_int),
     "xcf_profile_enable": ([_P, C.c_int], C.c_int),
     "xcf_profile_read": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int], C.c_int),
 }
 
-STAGES = ("project", "prep", "search", "peak", "logpolar", "update", "other")
+STAGES = ("project", "prep", "search", "peak", "logpolar", "update", "other", "screen")
 
 _lib = None
 
@@ -386,6 +387,21 @@ def xcf_screen_topk(ctx: Context, lib: Library, patterns, k: int = 32):
                                   _ptr(cand, torch.int32, "cand"), _ptr(score, torch.float32, "score"), _stream()),
            ctx.handle)
     return cand, score
+
+
+def xcf_refine_best(ctx: Context, lib: Library, patterns, best, pcs=None, out=None):
+    """Refinement seeded by the library orientations of best -> (quats, peak, iters)."""
+    P = patterns.shape[0]
+    d = patterns.device
+    if out is None:
+        out = (torch.empty((P, 4), dtype=torch.float64, device=d), torch.empty(P, device=d),
+               torch.empty(P, dtype=torch.int32, device=d))
+    q, pk, it = out
+    _check(load().xcf_refine_best(ctx.handle, lib.handle, _ptr(patterns, torch.float32, "patterns"), P,
+                                  _ptr(best, torch.int32, "best"), _ptr(pcs, torch.float64, "pcs", True),
+                                  _ptr(q, torch.float64, "quats"), _ptr(pk, torch.float32, "peak"),
+                                  _ptr(it, torch.int32, "iters"), _stream()), ctx.handle)
+    return q, pk, it
 
 
 def xcf_rescore(ctx: Context, lib: Library, patterns, cand):

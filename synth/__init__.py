@@ -350,3 +350,17 @@ def config_map_128(seed: int = 0, ny: int = 100, nx: int = 100, step_deg: float 
                 pc=DEFAULT_PC, master=master_pattern("bcc", 1024), lib_q=so3_grid_cubic_fz(step_deg),
                 truth_q=smooth_orientation_map(ny, nx, seed + 1), pcs=jittered_pcs(P, seed + 2),
                 peak=100.0, noise_seed=seed + 3, max_iter=10)
+
+
+def config_precision_256(seed: int = 0, P: int = 50000, step_deg: float = 3.14) -> dict:
+    """Precision-form workload: BCC master (2 x 1024^2), 256 x 256 detector,
+    ~20,000 library orientations (S^2 x S^1 FZ grid, 3.14 deg), P patterns at
+    uniformly random orientations, PC (0.5, 0.5, 0.6) jittered by +-0.005,
+    Poisson peak drawn per pattern from U[50, 500]; screen top-32, FP32
+    rescore, two refinement iterations."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7))
+    lib_q = so3_grid_cubic_fz(step_deg)
+    return dict(name=f"xcf256_T{len(lib_q)}_P{P}", crystal="bcc", M=1024, n=256, pc=DEFAULT_PC,
+                master=master_pattern("bcc", 1024), lib_q=lib_q, truth_q=random_quaternions(P, seed + 1),
+                pcs=jittered_pcs(P, seed + 2), peak=rng.uniform(50.0, 500.0, size=P), noise_seed=seed + 3,
+                max_iter=2, k=32)
