@@ -53,10 +53,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="patterns in the CPU sample (0: auto)")
-    ap.add_argument("--form", default="plain", choices=["plain", "precision"],
+    ap.add_argument("--form", default="plain", choices=["plain", "precision", "batched"],
                     help="plain: full FP32 XCF search + refinement of the 128^2 map; precision: BF16 "
-                         "tensor-core screen top-32 + FP32 rescore + refinement at 256^2")
+                         "tensor-core screen top-32 + FP32 rescore + refinement at 256^2; batched: eight maps "
+                         "with different detectors in one persistent graph-captured search")
     ap.add_argument("--patterns", type=int, default=0, help="precision form: patterns per GPU (0: 50,000)")
+    ap.add_argument("--scale", type=float, default=1.0, help="batched form: scale of every map's pattern count")
     return ap.parse_args()
 
 
@@ -131,18 +133,32 @@ def cpu_oracle_rate(wl, pats: np.ndarray, sample: int):
     return 1.0 / per_pattern, threads, t_lib, t_s
 
 
-def _roofline_traffic(src_path: str):
-    """DRAM bytes per launch of the search kernel from the committed ncu
-    summary, if it was taken on the current source of that kernel."""
+def _roofline_traffic(meta_name: str, sources):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, if it
+    was taken on the current source of that kernel (sha256 over `sources`)."""
     import hashlib
-    meta = os.path.join(ROOT, "profiles", "search128_traffic.json")
+    meta = os.path.join(ROOT, "profiles", meta_name)
     if not os.path.exists(meta):
         return None
     m = json.load(open(meta))
-    sha = hashlib.sha256(open(src_path, "rb").read()).hexdigest()
-    if m.get("source_sha256") != sha:
+    h = hashlib.sha256()
+    for f in sources:
+        h.update(open(os.path.join(ROOT, "paper_1807_11313_gb300", "csrc", f), "rb").read())
+    if m.get("source_sha256") != h.hexdigest():
         return None
     return m.get("bytes_per_launch_full")
+
+
+SEARCH128_SOURCES = ("search128.cuh", "k_search128.cu")
+
+
+def _l2_note(pattern_bytes, lib_bytes, what):
+    big = pattern_bytes > L2_BYTES or lib_bytes > L2_BYTES
+    return (f"{'inputs larger than L2' if big else 'inputs NOT larger than L2'} "
+            f"({pattern_bytes / 1e6:.0f} MB patterns, {lib_bytes / 1e6:.0f} MB {what}; L2 129 MB)")
+
+
+L2_BYTES = 129e6
 
 
 def peaks_file():
@@ -194,14 +210,15 @@ def run_reference(args, rank, world):
 def _noisy_on_device(torch, clean, pcs, peak, gen):
     """Poisson(peak (0.6 hump + 0.4 clean scaled to [0, 1])) on the device
     (input generation only, outside the timed region)."""
-    P, n, _ = clean.shape
+    P, H, W = clean.shape
     lo = clean.amin(dim=(1, 2), keepdim=True)
     hi = clean.amax(dim=(1, 2), keepdim=True)
     ih = (clean - lo) / (hi - lo).clamp_min(1e-30)
-    r = torch.arange(n, device=clean.device, dtype=torch.float32) + 0.5
-    cy = (pcs[:, 1] * n).float().view(P, 1, 1)
-    cx = (pcs[:, 0] * n).float().view(P, 1, 1)
-    hump = torch.exp(-((r.view(1, n, 1) - cy) ** 2 + (r.view(1, 1, n) - cx) ** 2) / (2 * (0.35 * n) ** 2))
+    ry = torch.arange(H, device=clean.device, dtype=torch.float32) + 0.5
+    rx = torch.arange(W, device=clean.device, dtype=torch.float32) + 0.5
+    cy = (pcs[:, 1] * H).float().view(P, 1, 1)
+    cx = (pcs[:, 0] * W).float().view(P, 1, 1)
+    hump = torch.exp(-((ry.view(1, H, 1) - cy) ** 2 + (rx.view(1, 1, W) - cx) ** 2) / (2 * (0.35 * W) ** 2))
     lam = peak.float().view(P, 1, 1) * (0.6 * hump + 0.4 * ih)
     return torch.poisson(lam, generator=gen)
 
@@ -284,10 +301,148 @@ def run_precision(args, px, torch, dev, rank, world, local, dist):
                 "config": {"workload": wl["name"], "form": "precision", "detector": n, "templates": T,
                            "patterns_per_gpu": P, "top_k": k, "max_iter": wl["max_iter"],
                            "parallelism": f"replicas x{world}",
-                           "l2": "inputs larger than L2 (13 GB patterns, 2.6 GB BF16 templates)"},
+                           "l2": _l2_note(pats_d.numel() * 4, T * n * n * 2, "BF16 templates")},
                 "accuracy": accuracy, "gpu_launches": int(sum(v[1] for v in prof.values())), "clocks": clocks,
                 "roofline": roofline, "e2e": None, "cpu_baseline": None}
         print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------- batched form
+def flops_per_pair(n: int) -> float:
+    """Inverse real FFT of one n x n surface + conj-multiply of a half spectrum."""
+    import math
+    return 2.5 * n * n * math.log2(n * n) + 6 * n * (n // 2 + 1)
+
+
+def run_batched(args, px, torch, dev, rank, world, local, dist):
+    wl = synth.config_batched(seed=rank, scale=args.scale)
+    ctx = px.Context()
+    master_d = torch.from_numpy(np.ascontiguousarray(wl["master"])).to(dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(wl["noise_seed"])
+    batch, truths, libqs, hosts, ns, flops = [], [], [], [], [], 0.0
+    for m in wl["maps"]:
+        g = px.geometry(m["W"], m["H"], wl["pc"])
+        libq = torch.from_numpy(m["lib_q"]).to(dev)
+        lib = px.xcf_build_library(ctx, master_d, libq, g)
+        truth = torch.from_numpy(m["truth_q"]).to(dev)
+        pcs = torch.from_numpy(m["pcs"]).to(dev)
+        peak = torch.from_numpy(m["peak"]).to(dev)
+        P = truth.shape[0]
+        pats = torch.empty((P, m["H"], m["W"]), device=dev)
+        for c0 in range(0, P, 2048):
+            c1 = min(P, c0 + 2048)
+            clean = px.xcf_project(ctx, master_d, truth[c0:c1].contiguous(), g, pcs=pcs[c0:c1].contiguous())
+            pats[c0:c1] = _noisy_on_device(torch, clean, pcs[c0:c1], peak[c0:c1], gen)
+        batch.append((lib, pats))
+        truths.append(truth)
+        libqs.append(libq)
+        n = px.xcf_crop(g)[0]
+        ns.append(n)
+        flops += P * lib.T * flops_per_pair(n)   # every (pattern, template) pair
+    P_all = sum(p.shape[0] for _, p in batch)
+    outs = px.xcf_index_maps(ctx, batch, graph=True)          # first call: tune + capture
+    for _ in range(args.warmup):
+        px.xcf_index_maps(ctx, batch, outs=outs, graph=True)
+    torch.cuda.synchronize()
+    lib_mis = torch.cat([px.xcf_disorientation(ctx, libq[o[0].clamp(min=0).long()].contiguous(), t)
+                         for libq, o, t in zip(libqs, outs, truths)])
+    accuracy = {"library_match_mean_deg": float(lib_mis.mean()),
+                "library_match_median_deg": float(lib_mis.median()),
+                "frac_below_library_step": float(sum(
+                    (px.xcf_disorientation(ctx, libq[o[0].clamp(min=0).long()].contiguous(), t) < m["step"])
+                    .double().sum() for libq, o, t, m in zip(libqs, outs, truths, wl["maps"])) / P_all)}
+
+    def timed(fn):
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    px.xcf_profile_read(ctx, reset=True)
+    px.xcf_profile_enable(ctx, True)
+    clk = clocks_start(local)
+    time.sleep(0.3)
+    elapsed_ms = timed(lambda: px.xcf_index_maps(ctx, batch, outs=outs, graph=True))
+    clocks = clocks_stop(clk)
+    prof = px.xcf_profile_read(ctx, reset=True)
+    launches = int(sum(v[1] for v in prof.values()))
+    # the same maps one after another through the per-map entry point, for comparison
+    seq_ms = timed(lambda: [px.xcf_index(ctx, lib, pats) for lib, pats in batch])
+    px.xcf_profile_read(ctx, reset=True)
+    # the search kernel alone (uncaptured calls time each stage)
+    for _ in range(2):
+        px.xcf_index_maps(ctx, batch, outs=outs)
+    torch.cuda.synchronize()
+    prof2 = px.xcf_profile_read(ctx, reset=True)
+    px.xcf_profile_enable(ctx, False)
+    s_ms, s_n = prof2["search"]
+    per_launch_ms = s_ms / max(s_n, 1)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    pk = peaks_file()
+    sm_max = (pk or {}).get("sm_max_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
+    fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (per_launch_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None, "kernel": "k_search_maps",
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                "search_ms_per_launch": per_launch_ms,
+                "stage_ms_per_step_uncaptured": {k: v[0] / 2 for k, v in prof2.items()}}
+    e2e = None
+    if not args.no_e2e:
+        hp = [p.cpu().pin_memory() for _, p in batch]
+        ho = [tuple(torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in o) for o in outs]
+
+        def e2e_step():
+            for (lib, pats), h in zip(batch, hp):
+                pats.copy_(h, non_blocking=True)
+            px.xcf_index_maps(ctx, batch, outs=outs, graph=True)
+            for o, h in zip(outs, ho):
+                for a, b in zip(h, o):
+                    a.copy_(b, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": P_all * args.steps * world / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(h.numel() * 4 for h in hp)),
+               "d2h_bytes_per_step": int(sum(a.numel() * a.element_size() for h in ho for a in h))}
+    value = P_all * args.steps * world / (elapsed_ms / 1e3)
+    if rank == 0:
+        line = {"metric": "patterns indexed/s (batched maps: prep + search + peak per map)", "value": value,
+                "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl["name"], "form": "batched", "maps": len(batch),
+                           "detectors": [[m["W"], m["H"]] for m in wl["maps"]], "crop": ns,
+                           "templates": [lib.T for lib, _ in batch], "patterns": [p.shape[0] for _, p in batch],
+                           "graph": True, "libraries": "resident (built before the timed region)",
+                           "parallelism": f"replicas x{world}",
+                           "l2": _l2_note(sum(p.numel() * 4 for _, p in batch),
+                                          sum(lib.T * n * (n // 2 + 1) * 8 for (lib, _), n in zip(batch, ns)),
+                                          "library spectra")},
+                "sequential_ms_per_step": seq_ms / args.steps,
+                "accuracy": accuracy, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
+                "e2e": e2e, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+    for lib, _ in batch:
+        lib.close()
+    ctx.close()
 
 
 # ------------------------------------------------------------------ our arm
@@ -307,8 +462,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    if args.form == "precision":
-        run_precision(args, px, torch, dev, rank, world, local, dist)
+    if args.form in ("precision", "batched"):
+        (run_precision if args.form == "precision" else run_batched)(args, px, torch, dev, rank, world, local, dist)
         if dist:
             dist.destroy_process_group()
         return
@@ -384,7 +539,7 @@ def main():
     achieved = flops_launch / (per_launch_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak,
-                "traffic": _roofline_traffic(os.path.join(ROOT, "paper_1807_11313_gb300", "csrc", "k_search128.cu")),
+                "traffic": _roofline_traffic("search128_traffic.json", SEARCH128_SOURCES),
                 "kernel": "k_search128", "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
                 "search_ms_per_launch": per_launch_ms,
                 "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
@@ -441,7 +596,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": wl["name"], "detector": n, "templates": T, "patterns_per_gpu": P,
                            "max_iter": wl["max_iter"], "parallelism": f"replicas x{world}",
-                           "l2": "inputs larger than L2 (655 MB patterns, 270 MB library spectra)"},
+                           "l2": _l2_note(pats_d.numel() * 4, T * n * (n // 2 + 1) * 8, "library spectra")},
                 "accuracy": accuracy, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
                 "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

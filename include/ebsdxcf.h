@@ -219,6 +219,29 @@ int xcf_rescore(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int
 int xcf_refine_best(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, const int32_t *best,
                     const double *pcs, double *quats, float *peak, int32_t *iters, void *stream);
 
+/* Several maps in one search (paper, Fig. 1 B-C, for every map of a batch;
+ * the maps may have different detectors, pattern centres and libraries --
+ * each map's detector is cropped to its 2^n square, e.g. 96 -> 64,
+ * 160 / 200 -> 128 px).  Patterns are pre-processed per map, then all maps
+ * are searched in ONE persistent launch that takes (map, pattern, template
+ * range) work items from a queue; the work granularity per detector side and
+ * library size is chosen by timing candidates on the first call (cached in
+ * the context).  With XCF_MAPS_GRAPH the whole sequence is captured in a CUDA
+ * graph the first time a batch configuration (pointers and sizes) is seen and
+ * replayed afterwards: the patterns may change between calls, the pointers may
+ * not.  Outputs per map as xcf_index.  Asynchronous with respect to `stream`
+ * except for the first call of a configuration. */
+typedef struct {
+    const xcf_library *lib;   /* the map's library (its detector geometry)        */
+    const float *patterns;    /* [P, H, W] float32 on the library's detector      */
+    int32_t P;
+    int32_t *best;            /* [P]                                              */
+    float *peak;              /* [P]                                              */
+    float *shift;             /* [P, 2]                                           */
+} xcf_map_desc;
+#define XCF_MAPS_GRAPH 1
+int xcf_index_maps(xcf_ctx *ctx, const xcf_map_desc *maps, int32_t n_maps, int32_t flags, void *stream);
+
 /* Search then refine in one call (device memory): xcf_index, seeds = the
  * library orientations of the best templates (identity for degenerate
  * patterns), then xcf_refine.  Outputs as those two calls. */

@@ -20,7 +20,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "xcf_oracle.c")
+_SRCS = (os.path.join(_HERE, "xcf_oracle.c"), os.path.join(_HERE, "cnn_oracle.c"))
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -29,9 +29,9 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/_build/liboracle.so (gcc, -O2, OpenMP)."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(map(os.path.getmtime, _SRCS)):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, *_SRCS, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -98,6 +98,19 @@ def _lib_handle():
                                      C.c_int, C.c_int, _D, C.c_int, C.c_double, _D, _D, _I], None),
                 "orc_bf16_round": ([C.c_double], C.c_double),
                 "orc_screen": ([_D, C.c_int, _D, C.c_int, C.c_long, C.c_int, _D], None),
+                "orc_cnn_num_params": ([C.c_int], C.c_long),
+                "orc_cnn_standardise": ([_D, C.c_int, _D], None),
+                "orc_conv3x3s2": ([_D, C.c_int, C.c_int, _D, _D, C.c_int, _D], None),
+                "orc_gram_schmidt": ([_D, _D], None),
+                "orc_gram_schmidt_backward": ([_D, _D, _D], None),
+                "orc_cubic_matrices": ([_D], None),
+                "orc_cnn_head_loss": ([_D, C.c_int, _D, _D, _I, _I], C.c_double),
+                "orc_cnn_forward": ([_F, _D, C.c_int, C.c_int, _D], None),
+                "orc_cnn_loss_grad": ([_F, _D, C.c_int, C.c_int, _D, _D, _I], C.c_double),
+                "orc_adam": ([_D, _D, _D, _D, C.c_long, C.c_int, C.c_double, C.c_double, C.c_double,
+                              C.c_double], None),
+                "orc_matrix_to_quat": ([_D, _D], None),
+                "orc_cnn_proposals": ([_D, C.c_int, C.c_int, _D], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -389,3 +402,96 @@ def refine_many(master, patterns, seeds, pcs, max_it=2, tol_deg=1e-3, opts=None,
                                   detector_tilt, C.byref(o), _f(patterns), P, n, _d(seeds),
                                   max_it, tol_deg, _d(q), _d(pk), _i(it))
     return q, pk, it
+
+
+# ------------------------------------------------------- learned proposal
+CNN_SIDE = 128
+
+
+def cnn_num_params(k: int = 8) -> int:
+    return int(_lib_handle().orc_cnn_num_params(k))
+
+
+def cnn_standardise(x):
+    x = _f64(x)
+    y = np.empty_like(x)
+    _lib_handle().orc_cnn_standardise(_d(x), x.size, _d(y))
+    return y
+
+
+def conv3x3s2(x, w, b=None):
+    """x [Ci, s, s], w [Co, Ci, 3, 3], b [Co] -> [Co, s/2, s/2] (no activation)."""
+    x, w = _f64(x), _f64(w)
+    ci, s = x.shape[0], x.shape[1]
+    co = w.shape[0]
+    y = np.empty((co, s // 2, s // 2))
+    _lib_handle().orc_conv3x3s2(_d(x), ci, s, _d(w), _d(_f64(b)) if b is not None else None, co, _d(y))
+    return y
+
+
+def gram_schmidt(a):
+    a = _f64(a)
+    R = np.empty((3, 3))
+    _lib_handle().orc_gram_schmidt(_d(a), _d(R))
+    return R
+
+
+def gram_schmidt_backward(a, G):
+    ga = np.empty(6)
+    _lib_handle().orc_gram_schmidt_backward(_d(_f64(a)), _d(_f64(G)), _d(ga))
+    return ga
+
+
+def cubic_matrices():
+    S = np.empty((24, 3, 3))
+    _lib_handle().orc_cubic_matrices(_d(S))
+    return S
+
+
+def cnn_head_loss(out6, k, q_gt, want_grad=True):
+    """-> (loss, dL/dout6 [6k] or None, head, operator)"""
+    out6 = _f64(out6)
+    g = np.empty(6 * k) if want_grad else None
+    h, s = C.c_int32(), C.c_int32()
+    loss = _lib_handle().orc_cnn_head_loss(_d(out6), k, _d(_f64(q_gt)), _d(g) if g is not None else None,
+                                           C.byref(h), C.byref(s))
+    return loss, g, h.value, s.value
+
+
+def cnn_forward(params, x, k=8):
+    """params float32 [n], x [B, 128, 128] -> out [B, 6k] (FP64)."""
+    x = _f64(x)
+    B = x.shape[0]
+    out = np.empty((B, 6 * k))
+    _lib_handle().orc_cnn_forward(_f(_f32(params)), _d(x), B, k, _d(out))
+    return out
+
+
+def cnn_loss_grad(params, x, q_gt, k=8, want_grad=True):
+    """-> (mean loss, grad [n] FP64 or None, winners [B, 2])"""
+    x = _f64(x)
+    B = x.shape[0]
+    grad = np.empty(cnn_num_params(k)) if want_grad else None
+    win = np.empty((B, 2), np.int32)
+    loss = _lib_handle().orc_cnn_loss_grad(_f(_f32(params)), _d(x), B, k, _d(_f64(q_gt)),
+                                           _d(grad) if grad is not None else None, _i(win))
+    return loss, grad, win
+
+
+def adam(params, grad, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In place on FP64 arrays params, m, v."""
+    _lib_handle().orc_adam(_d(params), _d(_f64(grad)), _d(m), _d(v), params.size, t, lr, b1, b2, eps)
+
+
+def matrix_to_quat(R):
+    q = np.empty(4)
+    _lib_handle().orc_matrix_to_quat(_d(_f64(R)), _d(q))
+    return q
+
+
+def cnn_proposals(out, k=8):
+    out = _f64(out)
+    B = out.shape[0]
+    q = np.empty((B, k, 4))
+    _lib_handle().orc_cnn_proposals(_d(out), B, k, _d(q))
+    return q

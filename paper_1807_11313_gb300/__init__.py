@@ -11,4 +11,6 @@ from .xcf import (  # noqa: F401
     xcf_correlate_all, xcf_crop, xcf_disorientation, xcf_index, xcf_index_refine, xcf_index_refine_host,
     xcf_options, xcf_geometry, xcf_prep, xcf_project, xcf_refine, load, library_path,
     xcf_profile_enable, xcf_profile_read, STAGES, xcf_index_noalloc, xcf_noalloc_max_patterns,
+    xcf_build_library_ex, xcf_screen_topk, xcf_rescore, xcf_refine_best, xcf_index_maps, XCF_LIB_SCREEN,
+    XCF_MAPS_GRAPH,
 )

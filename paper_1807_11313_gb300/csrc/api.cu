@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/ebsdxcf.h"
@@ -53,11 +54,21 @@ int cuda_fail(xcf_ctx *ctx, cudaError_t e, const char *where) {
         }                                                                    \
     } while (0)
 
+// a captured multi-map graph holds scratch pointers: it dies with them
+void drop_graph(xcf_ctx *ctx) {
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->graph_exec = nullptr;
+    ctx->graph = nullptr;
+    ctx->graph_key.clear();
+}
+
 // grow-only scratch buffer; cudaFree / cudaMalloc synchronise, so the first
 // call at a size pays for it and later calls reuse the allocation
 int scratch(xcf_ctx *ctx, int slot, size_t bytes, void **out) {
     if (bytes == 0) bytes = 16;
     if (ctx->cap[slot] < bytes) {
+        drop_graph(ctx);
         if (ctx->buf[slot]) cudaFree(ctx->buf[slot]);
         ctx->buf[slot] = nullptr;
         ctx->cap[slot] = 0;
@@ -382,6 +393,11 @@ int xcf_destroy(xcf_ctx *ctx) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+    for (auto &e : ctx->gev)
+        if (e) cudaEventDestroy(e);
     for (int i = 0; i < S_COUNT; ++i)
         if (ctx->buf[i]) cudaFree(ctx->buf[i]);
     delete ctx;
@@ -950,6 +966,257 @@ int xcf_rescore(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int
                                  shift + 2 * (size_t)p0, st),
                    "pair_peak");
     }
+    return XCF_OK;
+}
+
+// ------------------------------------------------------------- multi-map
+namespace {
+
+struct MapLayout {
+    std::vector<size_t> spec, idx;   // offsets (complex values / patterns) of each map's slices
+    size_t spec_total = 0, idx_total = 0;
+    bool big = false;
+};
+
+MapLayout maps_layout(const xcf_map_desc *maps, int n) {
+    MapLayout L;
+    for (int m = 0; m < n; ++m) {
+        const int N = maps[m].lib->N;
+        L.spec.push_back(L.spec_total);
+        L.idx.push_back(L.idx_total);
+        L.spec_total += (size_t)maps[m].P * N * (N / 2 + 1);
+        L.idx_total += (size_t)maps[m].P;
+        if (N > 128) L.big = true;
+    }
+    return L;
+}
+
+long long tune_key(int N, int T) { return ((long long)N << 32) | (unsigned)T; }
+
+int tuned_pairs(xcf_ctx *ctx, int N, int T) {
+    for (auto &kv : ctx->tune)
+        if (kv.first == tune_key(N, T)) return kv.second;
+    return 0;
+}
+
+// work items, most expensive (largest detector) first so that the tail of
+// the persistent launch is made of short items
+std::vector<WorkItem> maps_items(xcf_ctx *ctx, const xcf_map_desc *maps, int n, int p_limit = -1,
+                                 int only_map = -1, int pairs = 0) {
+    std::vector<int> order(n);
+    for (int m = 0; m < n; ++m) order[m] = m;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return maps[a].lib->N > maps[b].lib->N; });
+    std::vector<WorkItem> items;
+    for (int m : order) {
+        if (only_map >= 0 && m != only_map) continue;
+        const int T = maps[m].lib->T, npairs = (T + 1) / 2;
+        int c = pairs > 0 ? pairs : tuned_pairs(ctx, maps[m].lib->N, T);
+        if (c <= 0) c = npairs;
+        const int P = p_limit >= 0 && p_limit < maps[m].P ? p_limit : maps[m].P;
+        for (int p = 0; p < P; ++p)
+            for (int pb = 0; pb < npairs; pb += c) items.push_back({m, p, pb, pb + c < npairs ? pb + c : npairs});
+    }
+    return items;
+}
+
+struct MapsDev {
+    MapDev *maps;
+    WorkItem *items;
+    int *counter;
+    float2 *spec;
+    int *degen;
+    unsigned long long *keys;
+    float2 *work;
+    int grid;
+};
+
+// scratch for the batch (allocations happen here, never inside a capture)
+int maps_scratch(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout &L, size_t n_items, MapsDev *d) {
+    int rc;
+    void *mp;
+    const size_t table = ((sizeof(MapDev) * n + 255) & ~(size_t)255) + ((sizeof(WorkItem) * n_items + 255) & ~(size_t)255);
+    if ((rc = scratch(ctx, S_MAPS, table + 256, &mp)) || (rc = scratch_t(ctx, S_SPEC_P, L.spec_total, &d->spec)) ||
+        (rc = scratch_t(ctx, S_DEGEN, L.idx_total, &d->degen)) || (rc = scratch_t(ctx, S_KEYS, L.idx_total, &d->keys)))
+        return rc;
+    d->maps = static_cast<MapDev *>(mp);
+    d->items = reinterpret_cast<WorkItem *>(static_cast<char *>(mp) + ((sizeof(MapDev) * n + 255) & ~(size_t)255));
+    d->counter = reinterpret_cast<int *>(static_cast<char *>(mp) + table);
+    d->grid = ctx->num_sms;
+    d->work = nullptr;
+    if (L.big) {   // megakernel and the N = 256 peak kernel both draw on the work arrays
+        const int g2 = big_grid(ctx->num_sms, 1L << 30);
+        if ((rc = scratch_t(ctx, S_WORK, big_work_bytes(256, g2 > d->grid ? g2 : d->grid) / sizeof(float2), &d->work)))
+            return rc;
+    }
+    return XCF_OK;
+}
+
+int maps_table_upload(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout &L, const MapsDev &d,
+                      const std::vector<WorkItem> &items, cudaStream_t st) {
+    std::vector<MapDev> h(n);
+    for (int m = 0; m < n; ++m) {
+        const xcf_library *lib = maps[m].lib;
+        h[m] = {lib->N, lib->T, search_spectra(lib), d.spec + L.spec[m], d.degen + L.idx[m], d.keys + L.idx[m]};
+    }
+    XCF_CHECK(cudaMemcpyAsync(d.maps, h.data(), sizeof(MapDev) * n, cudaMemcpyHostToDevice, st), "map table");
+    if (!items.empty())
+        XCF_CHECK(cudaMemcpyAsync(d.items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, st),
+                  "work items");
+    XCF_CHECK(cudaStreamSynchronize(st), "map table");
+    return XCF_OK;
+}
+
+int maps_prep(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout &L, const MapsDev &d, cudaStream_t st) {
+    for (int m = 0; m < n; ++m) {
+        const xcf_library *lib = maps[m].lib;
+        Crop c;
+        crop_of(&lib->geom, 256, &c);
+        XCF_LAUNCH(XCF_STAGE_PREP, st,
+                   run_prep(ctx, maps[m].patterns, maps[m].P, prep_args(&lib->geom, c, resolve(ctx->opt, c.n)),
+                            d.spec + L.spec[m], nullptr, d.degen + L.idx[m], nullptr, st),
+                   "prep");
+    }
+    return XCF_OK;
+}
+
+// the capturable part: search of all maps in one launch, then each map's peak
+int maps_search_finish(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout &L, const MapsDev &d,
+                       int n_items, cudaStream_t st) {
+    XCF_CHECK(cudaMemsetAsync(d.keys, 0, sizeof(unsigned long long) * L.idx_total, st), "clear keys");
+    XCF_CHECK(cudaMemsetAsync(d.counter, 0, sizeof(int), st), "clear queue");
+    XCF_LAUNCH(XCF_STAGE_SEARCH, st, launch_search_maps(d.maps, d.items, n_items, d.counter, d.work, d.grid, st),
+               "multi-map search");
+    for (int m = 0; m < n; ++m) {
+        const xcf_library *lib = maps[m].lib;
+        XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_keys_to_best(d.keys + L.idx[m], maps[m].P, maps[m].best, st),
+                   "keys_to_best");
+        XCF_LAUNCH(XCF_STAGE_PEAK, st,
+                   run_pair_peak(ctx, lib->N, lib->spectra, maps[m].best, d.spec + L.spec[m], d.degen + L.idx[m],
+                                 nullptr, maps[m].P, maps[m].peak, maps[m].shift, st),
+                   "pair_peak");
+    }
+    return XCF_OK;
+}
+
+// time candidate work granularities on the first patterns of each untuned
+// (side, library size) and keep the fastest (patterns already pre-processed)
+int maps_autotune(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout &L, const MapsDev &d,
+                  cudaStream_t st) {
+    cudaEvent_t e0, e1;
+    XCF_CHECK(cudaEventCreate(&e0), "event");
+    XCF_CHECK(cudaEventCreate(&e1), "event");
+    int status = XCF_OK;
+    for (int m = 0; m < n && status == XCF_OK; ++m) {
+        const int N = maps[m].lib->N, T = maps[m].lib->T, npairs = (T + 1) / 2;
+        if (tuned_pairs(ctx, N, T) > 0) continue;
+        const int cands[3] = {npairs, npairs / 4 > 8 ? npairs / 4 : 8, npairs / 16 > 8 ? npairs / 16 : 8};
+        int best_c = npairs;
+        float best_t = 1e30f;
+        for (int ci = 0; ci < 3 && status == XCF_OK; ++ci) {
+            if (ci > 0 && cands[ci] >= cands[ci - 1]) continue;
+            std::vector<WorkItem> it = maps_items(ctx, maps, n, ctx->num_sms, m, cands[ci]);
+            if ((status = maps_table_upload(ctx, maps, n, L, d, it, st))) break;
+            cudaMemsetAsync(d.keys, 0, sizeof(unsigned long long) * L.idx_total, st);
+            cudaMemsetAsync(d.counter, 0, sizeof(int), st);
+            cudaEventRecord(e0, st);
+            cudaError_t e = launch_search_maps(d.maps, d.items, (int)it.size(), d.counter, d.work, d.grid, st);
+            cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) { status = cuda_fail(ctx, e, "autotune"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const int pats = ctx->num_sms < maps[m].P ? ctx->num_sms : maps[m].P;
+            const float per = ms / (pats > 0 ? pats : 1);
+            if (per < best_t) { best_t = per; best_c = cands[ci]; }
+        }
+        ctx->tune.push_back({tune_key(N, T), best_c});
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return status;
+}
+
+}  // namespace
+
+int xcf_index_maps(xcf_ctx *ctx, const xcf_map_desc *maps, int32_t n_maps, int32_t flags, void *stream) {
+    if (!ctx) return XCF_ERR_ARG;
+    if (n_maps < 0 || (n_maps > 0 && !maps) || (flags & ~XCF_MAPS_GRAPH))
+        return fail(ctx, XCF_ERR_ARG, "xcf_index_maps: bad argument");
+    if (n_maps == 0) return XCF_OK;
+    for (int m = 0; m < n_maps; ++m) {
+        int rc = check_lib(ctx, maps[m].lib);
+        if (rc) return rc;
+        if (maps[m].P < 0 || (maps[m].P > 0 && (!maps[m].patterns || !maps[m].best || !maps[m].peak || !maps[m].shift)))
+            return fail(ctx, XCF_ERR_ARG, "xcf_index_maps: bad map " + std::to_string(m));
+    }
+    cudaSetDevice(ctx->device);
+    cudaStream_t caller = (cudaStream_t)stream;
+    const MapLayout L = maps_layout(maps, n_maps);
+    MapsDev d;
+    int rc;
+
+    // the key of this batch configuration (graph replay needs the same pointers and sizes)
+    std::vector<char> key(reinterpret_cast<const char *>(maps), reinterpret_cast<const char *>(maps + n_maps));
+    for (int m = 0; m < n_maps; ++m) {   // a library freed and another made at its address differs in id
+        const uint64_t id = maps[m].lib->id;
+        key.insert(key.end(), reinterpret_cast<const char *>(&id), reinterpret_cast<const char *>(&id) + sizeof id);
+    }
+    const bool graph = (flags & XCF_MAPS_GRAPH) != 0;
+    if (graph && ctx->graph_exec && key == ctx->graph_key) {
+        XCF_CHECK(cudaEventRecord(ctx->gev[0], caller), "event");
+        XCF_CHECK(cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0), "event");
+        // a replay is timed as one search-stage interval; its kernels are counted per stage
+        XCF_LAUNCH(XCF_STAGE_SEARCH, ctx->gstream, cudaGraphLaunch(ctx->graph_exec, ctx->gstream), "graph launch");
+        ctx->launches[XCF_STAGE_SEARCH] -= 1;
+        for (int i = 0; i < XCF_NUM_STAGES; ++i) ctx->launches[i] += ctx->graph_launches[i];
+        XCF_CHECK(cudaEventRecord(ctx->gev[1], ctx->gstream), "event");
+        XCF_CHECK(cudaStreamWaitEvent(caller, ctx->gev[1], 0), "event");
+        return XCF_OK;
+    }
+
+    // first call of this configuration: scratch, pre-processing, autotuning, work items
+    std::vector<WorkItem> items = maps_items(ctx, maps, n_maps);
+    size_t max_items = items.size();
+    for (int m = 0; m < n_maps; ++m)   // the largest trial list of the autotuner
+        max_items = std::max(max_items, maps_items(ctx, maps, n_maps, ctx->num_sms, m, 8).size());
+    if ((rc = maps_scratch(ctx, maps, n_maps, L, max_items, &d))) return rc;
+    if ((rc = maps_prep(ctx, maps, n_maps, L, d, caller))) return rc;
+    if ((rc = maps_autotune(ctx, maps, n_maps, L, d, caller))) return rc;
+    items = maps_items(ctx, maps, n_maps);   // the tuned granularity may need a larger table
+    if (items.size() > max_items && (rc = maps_scratch(ctx, maps, n_maps, L, items.size(), &d))) return rc;
+    if ((rc = maps_table_upload(ctx, maps, n_maps, L, d, items, caller))) return rc;
+
+    if (!graph) return maps_search_finish(ctx, maps, n_maps, L, d, (int)items.size(), caller);
+
+    // capture prep + search + peaks on the context's own stream, then replay
+    if (!ctx->gstream) XCF_CHECK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking), "stream");
+    for (auto &e : ctx->gev)
+        if (!e) XCF_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    drop_graph(ctx);
+    XCF_CHECK(cudaStreamSynchronize(caller), "sync");
+    const bool timing = ctx->timing;
+    ctx->timing = false;   // no event pairs inside the capture
+    int64_t before[XCF_NUM_STAGES];
+    for (int i = 0; i < XCF_NUM_STAGES; ++i) before[i] = ctx->launches[i];
+    XCF_CHECK(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    rc = maps_prep(ctx, maps, n_maps, L, d, ctx->gstream);
+    if (rc == XCF_OK) rc = maps_search_finish(ctx, maps, n_maps, L, d, (int)items.size(), ctx->gstream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(ctx->gstream, &g);
+    ctx->timing = timing;
+    for (int i = 0; i < XCF_NUM_STAGES; ++i) ctx->graph_launches[i] = ctx->launches[i] - before[i];
+    if (rc != XCF_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (ec != cudaSuccess) return cuda_fail(ctx, ec, "end capture");
+    XCF_CHECK(cudaGraphInstantiate(&ctx->graph_exec, g, 0), "graph instantiate");
+    ctx->graph = g;
+    ctx->graph_key = key;
+    XCF_CHECK(cudaGraphLaunch(ctx->graph_exec, ctx->gstream), "graph launch");
+    XCF_CHECK(cudaEventRecord(ctx->gev[1], ctx->gstream), "event");
+    XCF_CHECK(cudaStreamWaitEvent(caller, ctx->gev[1], 0), "event");
     return XCF_OK;
 }
 

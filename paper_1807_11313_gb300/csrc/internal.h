@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -37,6 +38,7 @@ enum Slot {
     S_BF16_P,       // screen: pattern images in BF16
     S_SCORE,        // screen: zero-shift scores of a chunk
     S_ERR,          // device status word of kernels with bounded waits
+    S_MAPS,         // multi-map search: map table, work items, queue counter
     S_COUNT
 };
 
@@ -55,9 +57,24 @@ struct xcf_ctx {
     double ms[XCF_NUM_STAGES] = {};
     struct Rec { int stage; cudaEvent_t a, b; };
     std::vector<Rec> recs;
+    // multi-map search: autotuned template pairs per work item, keyed by (N, T)
+    std::vector<std::pair<long long, int>> tune;
+    // multi-map search: captured graph of the last batch configuration
+    std::vector<char> graph_key;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_launches[XCF_NUM_STAGES] = {};   // kernels of one replay, per stage
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev[2] = {nullptr, nullptr};
 };
 
+inline uint64_t next_library_id() {
+    static std::atomic<uint64_t> n{0};
+    return ++n;
+}
+
 struct xcf_library {
+    uint64_t id = next_library_id();   // unique per library made in this process
     int device = 0;
     int T = 0, N = 0, M = 0;
     xcf_geometry geom{};

@@ -6,98 +6,12 @@
 // Paper: FFT section (Eq. 4 transform, filtering, windowing, normalisation by
 // the autocorrelations), Eqs. 3 and 6 (correlation surface), peak up-sampling.
 #include "common.cuh"
+#include "generic.cuh"
 #include "kernels.cuh"
 
 namespace {
 
-constexpr int kThreads = 256;
-
-// FFT (unscaled) of `nlines` lines of N points held in shared memory: point i
-// of line l at buf[l * ls + i * es]; tw[k] = exp(SIGN 2 pi i k / N), k < N/2.
-template <int N>
-__device__ void smem_fft_lines(float2 *buf, int nlines, int ls, int es, const float2 *tw) {
-    constexpr int LOG = cx_log2(N);
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int l = threadIdx.x >> 5; l < nlines; l += nw) {
-        float2 *x = buf + l * ls;
-        for (int i = lane; i < N; i += 32) {
-            int j = __brev(i) >> (32 - LOG);
-            if (i < j) {
-                float2 t = x[i * es];
-                x[i * es] = x[j * es];
-                x[j * es] = t;
-            }
-        }
-        __syncwarp();
-#pragma unroll 1
-        for (int s = 0; s < LOG; ++s) {
-            const int half = 1 << s;
-            for (int b = lane; b < N / 2; b += 32) {
-                int k = b & (half - 1);
-                int i0 = ((b >> s) << (s + 1)) + k, i1 = i0 + half;
-                float2 w = tw[k << (LOG - 1 - s)];
-                float2 u = x[i0 * es], v = c_mul(x[i1 * es], w);
-                x[i0 * es] = c_add(u, v);
-                x[i1 * es] = c_sub(u, v);
-            }
-            __syncwarp();
-        }
-    }
-}
-
-template <int N>
-__device__ __forceinline__ void fft2_smem(float2 *buf, const float2 *tw) {
-    constexpr int LD = N + 1;
-    smem_fft_lines<N>(buf, N, LD, 1, tw);   // rows
-    __syncthreads();
-    smem_fft_lines<N>(buf, N, 1, LD, tw);   // columns
-    __syncthreads();
-}
-
-template <int N>
-__device__ void make_twiddles(float2 *tw, int sign) {
-    for (int k = threadIdx.x; k < N / 2; k += blockDim.x) {
-        double s, c;
-        sincospi(2.0 * k / N, &s, &c);
-        tw[k] = make_float2((float)c, (float)(sign * s));
-    }
-}
-
-__device__ double block_sum(double v, double *sh) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        v = lane < nw ? sh[lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[32] = v;
-    }
-    __syncthreads();
-    double r = sh[32];
-    __syncthreads();
-    return r;
-}
-
-__device__ float block_max(float v, float *sh) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        v = lane < nw ? sh[lane] : -INFINITY;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (lane == 0) sh[32] = v;
-    }
-    __syncthreads();
-    float r = sh[32];
-    __syncthreads();
-    return r;
-}
+using namespace gen;
 
 // --------------------------------------------------------------------------
 // pre-processing: crop, standardise, window, FFT, band-pass, unit norm
@@ -190,35 +104,6 @@ __global__ void __launch_bounds__(kThreads) k_prep(const float *__restrict__ img
     }
 }
 
-// Z = X1 + i X2 over the full N x N spectrum, X_j = conj(St_j) Sp extended
-// from the stored half (columns 0..N/2) by Hermitian symmetry.
-template <int N>
-__device__ __forceinline__ void build_pair_spectrum(float2 *buf, const float2 *__restrict__ t1,
-                                                    const float2 *__restrict__ t2,
-                                                    const float2 *__restrict__ sp) {
-    constexpr int LD = N + 1, HW = N / 2 + 1;
-    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-        int r = idx / N, c = idx % N;
-        float2 Z;
-        if (c <= N / 2) {
-            int k = r * HW + c;
-            float2 s = sp[k];
-            float2 x1 = c_mulcj(t1[k], s), x2 = c_mulcj(t2[k], s);
-            Z = make_float2(x1.x - x2.y, x1.y + x2.x);
-        } else {
-            int k = ((N - r) & (N - 1)) * HW + (N - c);
-            float2 s = sp[k];
-            float2 x1 = c_mulcj(t1[k], s), x2 = c_mulcj(t2[k], s);
-            Z = make_float2(x1.x + x2.y, -x1.y + x2.x);
-        }
-        buf[r * LD + c] = Z;
-    }
-}
-
-// --------------------------------------------------------------------------
-// all-pairs search, two templates per complex inverse FFT (real part = the
-// surface of the first, imaginary part = the second)
-// --------------------------------------------------------------------------
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_search_generic(const float2 *__restrict__ St, int T,
                                                              const float2 *__restrict__ Sp,
@@ -227,47 +112,11 @@ __global__ void __launch_bounds__(kThreads) k_search_generic(const float2 *__res
                                                              unsigned long long *__restrict__ keys,
                                                              float *__restrict__ peaks_all,
                                                              const int *__restrict__ cand, int kc) {
-    constexpr int LD = N + 1, HW = N / 2 + 1;
-    extern __shared__ float4 smem_raw[];
-    float2 *buf = reinterpret_cast<float2 *>(smem_raw);
-    float2 *twi = buf + N * LD;
-    __shared__ float redf[33];
     const int p = blockIdx.y;
     if (degen[p]) return;
-    make_twiddles<N>(twi, +1);
-    const float2 *sp = Sp + (size_t)p * N * HW;
-    // slots: every template, or this pattern's candidate list (entries < 0 are empty)
-    const int n = cand ? kc : T;
-    const int npairs = (n + 1) / 2;
+    const int npairs = ((cand ? kc : T) + 1) / 2;
     const int pb = blockIdx.x * pairs_per_cta, pe = min(npairs, pb + pairs_per_cta);
-    float best_v = -INFINITY;
-    int best_t = -1;
-    for (int pi = pb; pi < pe; ++pi) {
-        const int j1 = 2 * pi, j2 = min(j1 + 1, n - 1);
-        const int t1 = cand ? cand[(size_t)p * kc + j1] : j1;
-        const int t2 = cand ? cand[(size_t)p * kc + j2] : j2;
-        __syncthreads();
-        build_pair_spectrum<N>(buf, St + (size_t)max(t1, 0) * N * HW, St + (size_t)max(t2, 0) * N * HW, sp);
-        __syncthreads();
-        fft2_smem<N>(buf, twi);
-        float m1 = -INFINITY, m2 = -INFINITY;
-        for (int idx = threadIdx.x; idx < N * N; idx += kThreads) {
-            float2 z = buf[(idx / N) * LD + idx % N];
-            m1 = fmaxf(m1, z.x);
-            m2 = fmaxf(m2, z.y);
-        }
-        m1 = block_max(m1, redf);
-        m2 = block_max(m2, redf);
-        if (t1 < 0) m1 = -INFINITY;
-        if (t2 < 0) m2 = -INFINITY;
-        if (t1 >= 0 && (m1 > best_v || (m1 == best_v && t1 < best_t))) { best_v = m1; best_t = t1; }
-        if (j2 != j1 && t2 >= 0 && (m2 > best_v || (m2 == best_v && t2 < best_t))) { best_v = m2; best_t = t2; }
-        if (peaks_all && threadIdx.x == 0) {
-            peaks_all[(size_t)p * n + j1] = m1;
-            if (j2 != j1) peaks_all[(size_t)p * n + j2] = m2;
-        }
-    }
-    if (threadIdx.x == 0 && best_t >= 0) atomicMax(keys + p, pack_key(best_v, best_t));
+    search_body<N>(St, T, Sp, p, pb, pe, keys, peaks_all, cand, kc);
 }
 
 __device__ __forceinline__ float parabola(float cm, float c0, float cp) {

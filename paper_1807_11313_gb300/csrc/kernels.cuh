@@ -54,6 +54,21 @@ cudaError_t launch_pair_peak_big(int N, const float2 *St, const int *tidx, const
                                  const int *active, int P, float *peak, float *shift, float2 *work, int grid,
                                  cudaStream_t st);
 
+// multi-map search: one persistent launch over a queue of work items
+struct MapDev {
+    int N, T;                      // detector side, library size
+    const float2 *St;              // library spectra as the side's search body reads them
+    const float2 *Sp;              // the map's pattern spectra
+    const int *degen;              // the map's degeneracy flags
+    unsigned long long *keys;      // the map's best keys
+};
+struct WorkItem {
+    int map, p, pb, pe;            // pattern p of map `map` against template pairs [pb, pe)
+};
+size_t maps_smem_bytes();
+cudaError_t launch_search_maps(const MapDev *maps, const WorkItem *items, int n_items, int *counter, float2 *work,
+                               int grid, cudaStream_t st);
+
 // N = 128: library half spectra -> the search kernel's packed layout
 cudaError_t launch_pack_search_layout(const float2 *spectra, int T, int N, float2 *packed, cudaStream_t st);
 

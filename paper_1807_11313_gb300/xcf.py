@@ -49,7 +49,13 @@ def geometry(width, height, pc=(0.5, 0.5, 0.6), sample_tilt=70.0, detector_tilt=
 
 _P = C.c_void_p
 _I32 = C.c_int32
-# name -> argtypes (all return int unless noted)
+
+
+class xcf_map_desc(C.Structure):
+    _fields_ = [("lib", _P), ("patterns", _P), ("P", _I32), ("best", _P), ("peak", _P), ("shift", _P)]
+
+
+# name -> (argtypes, restype)
 _SIGS = {
     "xcf_strerror": ([C.c_int], C.c_char_p),
     "xcf_last_error": ([_P], C.c_char_p),
@@ -78,6 +84,7 @@ _SIGS = {
     "xcf_refine_best": ([_P, _P, _P, _I32, _P, _P, _P, _P, _P, _P], C.c_int),
     "xcf_index_noalloc": ([_P, _P, _P, _I32, _P, _P, _P, _P], C.c_int),
     "xcf_noalloc_max_patterns": ([_I32], C.c_int),
+    "xcf_index_maps": ([_P, _P, _I32, _I32, _P], C.c_int),
     "xcf_profile_enable": ([_P, C.c_int], C.c_int),
     "xcf_profile_read": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int], C.c_int),
 }
@@ -416,3 +423,29 @@ def xcf_rescore(ctx: Context, lib: Library, patterns, cand):
                               _ptr(peak, torch.float32, "peak"), _ptr(shift, torch.float32, "shift"), _stream()),
            ctx.handle)
     return best, peak, shift
+
+
+XCF_MAPS_GRAPH = 1
+
+
+def xcf_index_maps(ctx: Context, maps, outs=None, graph: bool = False):
+    """Index several maps (each a (Library, patterns [P, H, W]) pair, detectors
+    of any supported size) with one persistent search launch.  With graph=True
+    the batch is captured as a CUDA graph and replayed while the same tensors
+    (patterns and outputs, pass `outs` back in) are given.  -> outs, a list of
+    (best, peak, shift) per map."""
+    n = len(maps)
+    if outs is None:
+        outs = []
+        for lib, pats in maps:
+            P, d = pats.shape[0], pats.device
+            outs.append((torch.empty(P, dtype=torch.int32, device=d), torch.empty(P, dtype=torch.float32, device=d),
+                         torch.empty((P, 2), dtype=torch.float32, device=d)))
+    desc = (xcf_map_desc * max(n, 1))()
+    for i, ((lib, pats), (best, peak, shift)) in enumerate(zip(maps, outs)):
+        desc[i] = xcf_map_desc(lib.handle, _ptr(pats, torch.float32, "patterns"), pats.shape[0],
+                               _ptr(best, torch.int32, "best"), _ptr(peak, torch.float32, "peak"),
+                               _ptr(shift, torch.float32, "shift"))
+    _check(load().xcf_index_maps(ctx.handle, C.cast(desc, _P), n, XCF_MAPS_GRAPH if graph else 0, _stream()),
+           ctx.handle)
+    return outs

@@ -364,3 +364,60 @@ def config_precision_256(seed: int = 0, P: int = 50000, step_deg: float = 3.14) 
                 master=master_pattern("bcc", 1024), lib_q=lib_q, truth_q=random_quaternions(P, seed + 1),
                 pcs=jittered_pcs(P, seed + 2), peak=rng.uniform(50.0, 500.0, size=P), noise_seed=seed + 3,
                 max_iter=2, k=32)
+
+
+# detector (width, height), FZ grid step (deg), patterns per map for the batched form:
+# detectors {96, 128, 160, 200, 256}^2 (cropped to 64, 128, 128, 128, 256),
+# libraries ~1,000-20,000 orientations, 2,000-8,000 patterns per map
+BATCHED_MAPS = (
+    ((96, 96), 8.5, 2000),
+    ((128, 128), 5.35, 4000),
+    ((160, 160), 6.75, 3000),
+    ((200, 200), 8.5, 4000),
+    ((256, 256), 8.5, 2000),
+    ((96, 96), 3.14, 2000),
+    ((128, 128), 8.5, 8000),
+    ((160, 160), 5.35, 2000),
+)
+
+
+def config_batched(seed: int = 0, maps=BATCHED_MAPS, scale: float = 1.0) -> dict:
+    """Batched-form workload: several maps with different detectors and
+    libraries indexed together.  Per map: BCC master (shared, 2 x 1024^2), an
+    S^2 x S^1 FZ library at the map's step, patterns at uniformly random
+    orientations, PC (0.5, 0.5, 0.6) jittered by +-0.005, Poisson peak drawn
+    from U[50, 500].  ``scale`` multiplies every map's pattern count."""
+    out = []
+    for i, ((W, H), step, P) in enumerate(maps):
+        P = max(2, int(P * scale))
+        rng = np.random.Generator(np.random.PCG64(seed * 1000 + 17 * i + 5))
+        out.append(dict(W=W, H=H, step=step, lib_q=so3_grid_cubic_fz(step),
+                        truth_q=random_quaternions(P, seed * 1000 + 17 * i + 1),
+                        pcs=jittered_pcs(P, seed * 1000 + 17 * i + 2), peak=rng.uniform(50.0, 500.0, size=P)))
+    sizes = "_".join(f"{m['W']}T{len(m['lib_q'])}P{len(m['truth_q'])}" for m in out)
+    return dict(name=f"maps{len(out)}_{sizes}", master=master_pattern("bcc", 1024), pc=DEFAULT_PC, maps=out,
+                noise_seed=seed + 3)
+
+
+# channel widths of the proposal network's five stride-2 convolutions and its hidden layer
+CNN_CHANNELS = (1, 32, 64, 64, 128, 128)
+CNN_HIDDEN = 256
+
+
+def cnn_init_params(k: int = 8, seed: int = 0) -> np.ndarray:
+    """Initial parameters of the proposal network as one float32 array in the
+    order conv1 W, b, ..., conv5 W, b, fc1 W, b, fc2 W, b: weights uniform in
+    +-sqrt(6 / fan_in) (He et al. 2015), biases 0.01 for the ReLU layers and 0
+    for the output layer."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    ch = CNN_CHANNELS
+    for l in range(5):
+        fan = ch[l] * 9
+        parts.append(rng.uniform(-1, 1, ch[l + 1] * ch[l] * 9) * np.sqrt(6.0 / fan))
+        parts.append(np.full(ch[l + 1], 0.01))
+    parts.append(rng.uniform(-1, 1, CNN_HIDDEN * ch[5]) * np.sqrt(6.0 / ch[5]))
+    parts.append(np.full(CNN_HIDDEN, 0.01))
+    parts.append(rng.uniform(-1, 1, 6 * k * CNN_HIDDEN) * np.sqrt(6.0 / CNN_HIDDEN))
+    parts.append(np.zeros(6 * k))
+    return np.concatenate(parts).astype(np.float32)
