@@ -288,6 +288,68 @@ int xcf_index_noalloc(xcf_ctx *ctx, const xcf_library *lib, const float *pattern
  * not a power of two in [16, 256]).  Host only. */
 int xcf_noalloc_max_patterns(int32_t n);
 
+/* ---------------------------------------------------------------------
+ * Learned orientation proposal.  An extension of the paper's method: a small
+ * convolutional network proposes k orientations per pattern, each proposal is
+ * scored by the cross-correlation peak of its reprojected template (Fig. 1
+ * B-C), the best is refined (Fig. 6, Eq. 7), and patterns whose refined peak
+ * stays below a threshold fall back to the full library search.
+ *
+ * Network (input: the centred 128 x 128 crop of the detector, standardised
+ * per pattern): five 3 x 3 stride-2 convolutions with bias and ReLU, channels
+ * 1 -> 32 -> 64 -> 64 -> 128 -> 128; mean pool; fc 128 -> 256 + ReLU; fc
+ * 256 -> 6k.  Head h maps its six outputs (a1, a2) to the rotation with
+ * columns b1 = a1/|a1|, b2 = normalised a2 - (b1.a2) b1, b3 = b1 x b2.
+ * Training loss per pattern: min over heads and the 24 cubic operators S of
+ * |R_h - S R(q_gt)|_F^2; the batch loss is the mean.  Parameters: one float
+ * array, blocks conv1 W [32][1][3][3], b [32], ..., conv5 W, b, fc1 W [256][128],
+ * b [256], fc2 W [6k][256], b [6k].  FP32 throughout.
+ * --------------------------------------------------------------------- */
+typedef struct xcf_net xcf_net;
+#define XCF_NET_SIDE 128
+
+/* Parameter count for k heads (1 <= k <= 64), -1 otherwise.  Host only. */
+int64_t xcf_net_num_params(int32_t k);
+
+/* Network with k heads on the context's device.  params: device [n] copied in,
+ * or NULL for all zeros.  Adam state starts at zero.  Synchronous. */
+int xcf_net_create(xcf_ctx *ctx, int32_t k, const float *params, xcf_net **out);
+int xcf_net_free(xcf_net *net);
+
+/* Device pointer to the parameters (owned by the net, writable) and their count. */
+int xcf_net_params(xcf_net *net, float **params, int64_t *n);
+
+/* Raw outputs out [B][6k] for images [B][H][W] on detector g (the net reads the
+ * centred 128 x 128 crop; XCF_ERR_SIZE if the detector is smaller), or
+ * [B][128][128] when g is NULL. */
+int xcf_net_forward(xcf_ctx *ctx, xcf_net *net, const float *images, int32_t B, const xcf_geometry *g,
+                    float *out, void *stream);
+
+/* Mean loss of the batch (loss: device double [1], written) and its gradient
+ * kept in the net for xcf_net_adam (also copied to grad [n] when non-NULL);
+ * winners [B][2] (head, cubic operator index; may be NULL).  quats_gt [B][4]. */
+int xcf_net_loss_grad(xcf_ctx *ctx, xcf_net *net, const float *images, int32_t B, const xcf_geometry *g,
+                      const double *quats_gt, double *loss, float *grad, int32_t *winners, void *stream);
+
+/* One Adam step (Kingma & Ba 2015) with the gradient of the last
+ * xcf_net_loss_grad: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
+int xcf_net_adam(xcf_ctx *ctx, xcf_net *net, float lr, float beta1, float beta2, float eps, void *stream);
+
+/* k proposals per pattern: quats [P][k][4] (unit, w >= 0). */
+int xcf_propose(xcf_ctx *ctx, xcf_net *net, const float *patterns, int32_t P, const xcf_geometry *g,
+                double *quats, void *stream);
+
+/* Learned indexing: proposals, correlation score of each (the best by peak;
+ * ties to the lowest head), refinement of the best, then for every
+ * non-degenerate pattern whose refined peak is below tau the full search over
+ * lib and refinement from its best template.  Outputs as xcf_refine, plus
+ * fallback [P] (1 where the full search ran).  The library needs its master
+ * pattern.  Synchronises once per chunk of patterns (to size the fallback). */
+int xcf_index_learned(xcf_ctx *ctx, xcf_net *net, const xcf_library *lib, const float *patterns, int32_t P,
+                      const double *pcs, float tau, double *quats, float *peak, int32_t *iters, int32_t *fallback,
+                      void *stream);
+
 /* Profiling.  Every context counts the kernels it launches, per stage.  When
  * timing is enabled it also records a CUDA event pair on the launching stream
  * around each launch and accumulates the elapsed device time per stage. */
@@ -299,7 +361,8 @@ int xcf_noalloc_max_patterns(int32_t n);
 #define XCF_STAGE_UPDATE   5   /* refinement updates (X/Y shift, angular xcf + Z) */
 #define XCF_STAGE_OTHER    6   /* small bookkeeping kernels                       */
 #define XCF_STAGE_SCREEN   7   /* tensor-core zero-shift screen (GEMM)            */
-#define XCF_NUM_STAGES     8
+#define XCF_STAGE_NET      8   /* proposal network: forward, backward, optimiser  */
+#define XCF_NUM_STAGES     9
 
 /* Turn event timing on (1) or off (0).  Host only. */
 int xcf_profile_enable(xcf_ctx *ctx, int on);

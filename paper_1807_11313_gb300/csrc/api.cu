@@ -226,8 +226,9 @@ constexpr int kChunk = 16384;   // patterns per pass (bounds the scratch footpri
 
 // index one chunk already on the device: spectra of the patterns, search,
 // best, and the sub-pixel peak of the best template
+// only (nullable): patterns with only[p] == 0 are skipped like degenerate ones
 int index_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int P, int *best,
-                float *peak, float *shift, float *peaks_all, cudaStream_t st) {
+                float *peak, float *shift, float *peaks_all, cudaStream_t st, const int *only = nullptr) {
     const xcf_geometry *g = &lib->geom;
     Crop c;
     crop_of(g, 256, &c);
@@ -241,6 +242,12 @@ int index_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int
     if ((rc = scratch_t(ctx, S_DEGEN, P, &degen))) return rc;
     if ((rc = scratch_t(ctx, S_KEYS, P, &keys))) return rc;
     XCF_LAUNCH(XCF_STAGE_PREP, st, run_prep(ctx,patterns, P, prep_args(g, c, r), sp, nullptr, degen, nullptr, st), "prep");
+    if (only) {
+        int *mask;
+        if ((rc = scratch_t(ctx, S_MASK, P, &mask))) return rc;
+        XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_fallback_mask(degen, only, P, mask, st), "mask");
+        degen = mask;
+    }
     XCF_CHECK(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * P, st), "memset keys");
     if (peaks_all)   // degenerate patterns keep all-zero rows
         XCF_CHECK(cudaMemsetAsync(peaks_all, 0, sizeof(float) * (size_t)P * lib->T, st), "memset peaks");
@@ -258,7 +265,7 @@ int index_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int
 
 int refine_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int P,
                  const double *seeds, const double *pcs, double *quats, float *peak, int *iters,
-                 cudaStream_t st) {
+                 cudaStream_t st, const int *select = nullptr) {
     const xcf_geometry *g = &lib->geom;
     Crop c;
     crop_of(g, 256, &c);
@@ -290,7 +297,7 @@ int refine_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, in
     if (quats != seeds)
         XCF_CHECK(cudaMemcpyAsync(quats, seeds, sizeof(double) * 4 * P, cudaMemcpyDeviceToDevice, st),
                   "copy seeds");
-    XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_init_refine(degen, P, active, iters, peak, st), "init");
+    XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_init_refine(degen, select, P, active, iters, peak, st), "init");
     for (int it = 0; it < ctx->opt.max_iter; ++it) {
         // X / Y: shift of the template at the current orientation
         XCF_LAUNCH(XCF_STAGE_PROJECT, st, launch_project(lib->master, lib->M, quats, pcs, active, P, pj, img, st),
@@ -965,6 +972,280 @@ int xcf_rescore(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int
                    run_pair_peak(ctx, c.n, lib->spectra, best + p0, sp, degen, nullptr, np, peak + p0,
                                  shift + 2 * (size_t)p0, st),
                    "pair_peak");
+    }
+    return XCF_OK;
+}
+
+// ------------------------------------------------------ proposal network
+namespace {
+
+constexpr int kNetChunk = 1024;   // patterns per network pass (bounds the activations)
+
+int net_input(xcf_ctx *ctx, const float *images, const xcf_geometry *g, CnnInput *in) {
+    if (!g) {
+        *in = {images, (long)XCF_NET_SIDE * XCF_NET_SIDE, XCF_NET_SIDE, 0, 0};
+        return XCF_OK;
+    }
+    Crop c;
+    if (crop_of(g, XCF_NET_SIDE, &c) != XCF_OK || c.n != XCF_NET_SIDE)
+        return fail(ctx, XCF_ERR_SIZE, "proposal network: the detector must be at least 128 x 128");
+    *in = {images, (long)g->width * g->height, g->width, c.ox, c.oy};
+    return XCF_OK;
+}
+
+int net_reserve(xcf_ctx *ctx, xcf_net *net, int B, bool backward) {
+    const size_t a = cnn_act_floats(B, net->k);
+    if (net->act_cap < a) {
+        cudaFree(net->act);
+        net->act = nullptr;
+        net->act_cap = 0;
+        if (cudaMalloc(&net->act, sizeof(float) * a) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, XCF_ERR_OOM, "proposal network activations");
+        }
+        net->act_cap = a;
+    }
+    const size_t gb = cnn_grad_floats(B, net->k);
+    if (backward && net->gbuf_cap < gb) {
+        cudaFree(net->gbuf);
+        net->gbuf = nullptr;
+        net->gbuf_cap = 0;
+        if (cudaMalloc(&net->gbuf, sizeof(float) * gb) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, XCF_ERR_OOM, "proposal network gradient buffers");
+        }
+        net->gbuf_cap = gb;
+    }
+    return XCF_OK;
+}
+
+int check_net(xcf_ctx *ctx, const xcf_net *net) {
+    if (!ctx) return XCF_ERR_ARG;
+    if (!net) return fail(ctx, XCF_ERR_ARG, "network is NULL");
+    if (net->device != ctx->device) return fail(ctx, XCF_ERR_ARG, "network and context on different devices");
+    return XCF_OK;
+}
+
+// forward of B <= kNetChunk images; the outputs stay in net->act
+int net_forward_chunk(xcf_ctx *ctx, xcf_net *net, const CnnInput &in, int B, cudaStream_t st) {
+    int rc = net_reserve(ctx, net, B, false);
+    if (rc) return rc;
+    int nl = 0;
+    XCF_LAUNCH(XCF_STAGE_NET, st, launch_cnn_forward(net->params, net->k, in, B, net->act, &nl, st), "net forward");
+    ctx->launches[XCF_STAGE_NET] += nl - 1;
+    return XCF_OK;
+}
+
+CnnInput offset_input(const CnnInput &in, long b0) {
+    CnnInput o = in;
+    o.x = in.x + b0 * in.img_stride;
+    return o;
+}
+
+// proposals of P patterns -> quats [P][k][4]
+int propose_all(xcf_ctx *ctx, xcf_net *net, const CnnInput &in, int P, double *quats, cudaStream_t st) {
+    for (int b0 = 0; b0 < P; b0 += kNetChunk) {
+        const int nb = P - b0 < kNetChunk ? P - b0 : kNetChunk;
+        int rc = net_forward_chunk(ctx, net, offset_input(in, b0), nb, st);
+        if (rc) return rc;
+        XCF_LAUNCH(XCF_STAGE_NET, st,
+                   launch_cnn_proposals(cnn_output(net->act, nb, net->k), nb * net->k,
+                                        quats + (size_t)b0 * net->k * 4, st),
+                   "proposals");
+    }
+    return XCF_OK;
+}
+
+}  // namespace
+
+int64_t xcf_net_num_params(int32_t k) { return k >= 1 && k <= 64 ? (int64_t)cnn_num_params(k) : -1; }
+
+int xcf_net_create(xcf_ctx *ctx, int32_t k, const float *params, xcf_net **out) {
+    if (!ctx) return XCF_ERR_ARG;
+    if (!out || k < 1 || k > 64) return fail(ctx, XCF_ERR_ARG, "xcf_net_create: bad argument");
+    cudaSetDevice(ctx->device);
+    xcf_net *net = new xcf_net();
+    net->device = ctx->device;
+    net->k = k;
+    net->n = cnn_num_params(k);
+    float *base = nullptr;
+    cudaError_t e = cudaMalloc(&base, sizeof(float) * 4 * (size_t)net->n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete net;
+        return fail(ctx, XCF_ERR_OOM, "xcf_net_create: parameters");
+    }
+    net->params = base;
+    net->grad = base + net->n;
+    net->m = base + 2 * net->n;
+    net->v = base + 3 * net->n;
+    e = cudaMemset(base, 0, sizeof(float) * 4 * (size_t)net->n);
+    if (e == cudaSuccess && params)
+        e = cudaMemcpy(net->params, params, sizeof(float) * net->n, cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(base);
+        delete net;
+        return cuda_fail(ctx, e, "xcf_net_create");
+    }
+    *out = net;
+    return XCF_OK;
+}
+
+int xcf_net_free(xcf_net *net) {
+    if (!net) return XCF_ERR_ARG;
+    cudaSetDevice(net->device);
+    cudaFree(net->params);
+    cudaFree(net->act);
+    cudaFree(net->gbuf);
+    delete net;
+    return XCF_OK;
+}
+
+int xcf_net_params(xcf_net *net, float **params, int64_t *n) {
+    if (!net) return XCF_ERR_ARG;
+    if (params) *params = net->params;
+    if (n) *n = net->n;
+    return XCF_OK;
+}
+
+int xcf_net_forward(xcf_ctx *ctx, xcf_net *net, const float *images, int32_t B, const xcf_geometry *g, float *out,
+                    void *stream) {
+    int rc = check_net(ctx, net);
+    if (rc) return rc;
+    if (B == 0) return XCF_OK;
+    if (B < 0 || !images || !out) return fail(ctx, XCF_ERR_ARG, "xcf_net_forward: bad argument");
+    CnnInput in;
+    if ((rc = net_input(ctx, images, g, &in))) return rc;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int b0 = 0; b0 < B; b0 += kNetChunk) {
+        const int nb = B - b0 < kNetChunk ? B - b0 : kNetChunk;
+        if ((rc = net_forward_chunk(ctx, net, offset_input(in, b0), nb, st))) return rc;
+        XCF_CHECK(cudaMemcpyAsync(out + (size_t)b0 * 6 * net->k, cnn_output(net->act, nb, net->k),
+                                  sizeof(float) * 6 * net->k * nb, cudaMemcpyDeviceToDevice, st),
+                  "net outputs");
+    }
+    return XCF_OK;
+}
+
+int xcf_net_loss_grad(xcf_ctx *ctx, xcf_net *net, const float *images, int32_t B, const xcf_geometry *g,
+                      const double *quats_gt, double *loss, float *grad, int32_t *winners, void *stream) {
+    int rc = check_net(ctx, net);
+    if (rc) return rc;
+    if (B <= 0 || !images || !quats_gt || !loss) return fail(ctx, XCF_ERR_ARG, "xcf_net_loss_grad: bad argument");
+    CnnInput in;
+    if ((rc = net_input(ctx, images, g, &in))) return rc;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = net_reserve(ctx, net, B, true))) return rc;
+    XCF_CHECK(cudaMemsetAsync(loss, 0, sizeof(double), st), "loss");
+    int nl = 0;
+    XCF_LAUNCH(XCF_STAGE_NET, st, launch_cnn_forward(net->params, net->k, in, B, net->act, &nl, st), "net forward");
+    XCF_LAUNCH(XCF_STAGE_NET, st,
+               launch_cnn_backward(net->params, net->k, in, B, net->act, net->gbuf, quats_gt, loss, winners,
+                                   net->grad, ctx->num_sms, &nl, st),
+               "net backward");
+    ctx->launches[XCF_STAGE_NET] += nl - 2;
+    if (grad)
+        XCF_CHECK(cudaMemcpyAsync(grad, net->grad, sizeof(float) * net->n, cudaMemcpyDeviceToDevice, st),
+                  "gradient");
+    return XCF_OK;
+}
+
+int xcf_net_adam(xcf_ctx *ctx, xcf_net *net, float lr, float beta1, float beta2, float eps, void *stream) {
+    int rc = check_net(ctx, net);
+    if (rc) return rc;
+    if (!(lr >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+        return fail(ctx, XCF_ERR_ARG, "xcf_net_adam: bad hyper-parameter");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    net->t += 1;
+    XCF_LAUNCH(XCF_STAGE_NET, st,
+               launch_adam(net->params, net->grad, net->m, net->v, net->n, lr, beta1, beta2, eps, net->t, st),
+               "adam");
+    return XCF_OK;
+}
+
+int xcf_propose(xcf_ctx *ctx, xcf_net *net, const float *patterns, int32_t P, const xcf_geometry *g, double *quats,
+                void *stream) {
+    int rc = check_net(ctx, net);
+    if (rc) return rc;
+    if (P == 0) return XCF_OK;
+    if (P < 0 || !patterns || !quats) return fail(ctx, XCF_ERR_ARG, "xcf_propose: bad argument");
+    CnnInput in;
+    if ((rc = net_input(ctx, patterns, g, &in))) return rc;
+    cudaSetDevice(ctx->device);
+    return propose_all(ctx, net, in, P, quats, (cudaStream_t)stream);
+}
+
+int xcf_index_learned(xcf_ctx *ctx, xcf_net *net, const xcf_library *lib, const float *patterns, int32_t P,
+                      const double *pcs, float tau, double *quats, float *peak, int32_t *iters, int32_t *fallback,
+                      void *stream) {
+    int rc = check_net(ctx, net);
+    if (rc) return rc;
+    if ((rc = check_lib(ctx, lib))) return rc;
+    if (P == 0) return XCF_OK;
+    if (P < 0 || !patterns || !quats || !peak || !iters || !fallback)
+        return fail(ctx, XCF_ERR_ARG, "xcf_index_learned: bad argument");
+    if (!lib->master) return fail(ctx, XCF_ERR_ARG, "xcf_index_learned: library has no master pattern");
+    CnnInput in;
+    if ((rc = net_input(ctx, patterns, &lib->geom, &in))) return rc;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const xcf_geometry *g = &lib->geom;
+    Crop c;
+    crop_of(g, 256, &c);
+    const Resolved r = resolve(ctx->opt, c.n);
+    const int n = c.n, H = n * (n / 2 + 1), k = net->k;
+    const size_t img = (size_t)g->width * g->height;
+    const ProjArgs pj = proj_args_cropped(g, c);
+    const PrepArgs pa = prep_args(g, c, r), ps = prep_args_square(c, r);
+    for (int p0 = 0; p0 < P; p0 += kChunk) {
+        const int np = P - p0 < kChunk ? P - p0 : kChunk;
+        const float *pat = patterns + img * p0;
+        const double *pc = pcs ? pcs + 3 * (size_t)p0 : nullptr;
+        double *q = quats + 4 * (size_t)p0;
+        double *prop, *qh, *seeds;
+        float2 *sp, *stt;
+        float *img_t, *peak_h, *shift, *best_peak;
+        int *degen, *best, *count;
+        if ((rc = scratch_t(ctx, S_PROP, (size_t)np * k * 4, &prop)) || (rc = scratch_t(ctx, S_QH, (size_t)np * 4, &qh)) ||
+            (rc = scratch_t(ctx, S_SPEC_P, (size_t)np * H, &sp)) || (rc = scratch_t(ctx, S_SPEC_T, (size_t)np * H, &stt)) ||
+            (rc = scratch_t(ctx, S_IMG, (size_t)np * n * n, &img_t)) || (rc = scratch_t(ctx, S_PEAK, np, &peak_h)) ||
+            (rc = scratch_t(ctx, S_SHIFT, (size_t)np * 2, &shift)) || (rc = scratch_t(ctx, S_BESTPEAK, np, &best_peak)) ||
+            (rc = scratch_t(ctx, S_DEGEN, np, &degen)) || (rc = scratch_t(ctx, S_FBCOUNT, 1, &count)))
+            return rc;
+        // 1. proposals
+        if ((rc = propose_all(ctx, net, offset_input(in, p0), np, prop, st))) return rc;
+        // 2. correlation score of every proposal, the best kept as the seed
+        XCF_LAUNCH(XCF_STAGE_PREP, st, run_prep(ctx, pat, np, pa, sp, nullptr, degen, nullptr, st), "prep patterns");
+        for (int h = 0; h < k; ++h) {
+            XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_take_head(prop, np, k, h, qh, st), "take head");
+            XCF_LAUNCH(XCF_STAGE_PROJECT, st, launch_project(lib->master, lib->M, qh, pc, nullptr, np, pj, img_t, st),
+                       "project proposals");
+            XCF_LAUNCH(XCF_STAGE_PREP, st, run_prep(ctx, img_t, np, ps, stt, nullptr, nullptr, nullptr, st),
+                       "prep proposals");
+            XCF_LAUNCH(XCF_STAGE_PEAK, st, run_pair_peak(ctx, n, stt, nullptr, sp, degen, nullptr, np, peak_h, shift, st),
+                       "proposal peaks");
+            XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_keep_best(peak_h, qh, np, h, best_peak, q, nullptr, st), "keep best");
+        }
+        // 3. refinement of the best proposal
+        if ((rc = refine_chunk(ctx, lib, pat, np, q, pc, q, peak + p0, iters + p0, st))) return rc;
+        // 4. fallback where the refined peak stays below tau
+        if ((rc = scratch_t(ctx, S_DEGEN, np, &degen))) return rc;   // the refinement's pattern flags
+        XCF_CHECK(cudaMemsetAsync(count, 0, sizeof(int), st), "count");
+        XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_fallback_flags(peak + p0, degen, np, tau, fallback + p0, count, st),
+                   "fallback flags");
+        int n_fb = 0;
+        XCF_CHECK(cudaMemcpyAsync(&n_fb, count, sizeof(int), cudaMemcpyDeviceToHost, st), "count");
+        XCF_CHECK(cudaStreamSynchronize(st), "count");
+        if (n_fb == 0) continue;
+        if ((rc = scratch_t(ctx, S_BEST, np, &best)) || (rc = scratch_t(ctx, S_SEEDS, (size_t)np * 4, &seeds)))
+            return rc;
+        if ((rc = index_chunk(ctx, lib, pat, np, best, best_peak, shift, nullptr, st, fallback + p0))) return rc;
+        XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_fallback_seeds(fallback + p0, best, lib->quats, q, np, seeds, st),
+                   "fallback seeds");
+        if ((rc = refine_chunk(ctx, lib, pat, np, seeds, pc, q, peak + p0, iters + p0, st, fallback + p0))) return rc;
     }
     return XCF_OK;
 }

@@ -39,6 +39,11 @@ enum Slot {
     S_SCORE,        // screen: zero-shift scores of a chunk
     S_ERR,          // device status word of kernels with bounded waits
     S_MAPS,         // multi-map search: map table, work items, queue counter
+    S_PROP,         // learned proposals [P, k, 4]
+    S_QH,           // one proposal per pattern [P, 4]
+    S_BESTPEAK,     // best proposal peak [P]
+    S_MASK,         // search mask of the fallback pass
+    S_FBCOUNT,      // number of fallback patterns (device int)
     S_COUNT
 };
 
@@ -91,3 +96,16 @@ struct xcf_library {
 inline const float2 *search_spectra(const xcf_library *lib) {
     return lib->spectra_pk ? lib->spectra_pk : lib->spectra;
 }
+
+// the proposal network: parameters, Adam state and grow-only work buffers
+struct xcf_net {
+    int device = 0;
+    int k = 0;
+    long n = 0;                     // parameter count
+    float *params = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;   // [n] each, one allocation
+    int t = 0;                      // Adam steps taken
+    float *act = nullptr;           // activations of the last forward
+    size_t act_cap = 0;
+    float *gbuf = nullptr;          // gradient work buffers
+    size_t gbuf_cap = 0;
+};

@@ -300,10 +300,14 @@ __global__ void k_gather_seeds(const double *__restrict__ lib_quats, const int *
     for (int k = 0; k < 4; ++k) seeds[4 * (size_t)p + k] = t >= 0 ? lib_quats[4 * (size_t)t + k] : (k == 0 ? 1.0 : 0.0);
 }
 
-__global__ void k_init_refine(const int *__restrict__ degen, int P, int *__restrict__ active,
-                              int *__restrict__ iters, float *__restrict__ peak) {
+__global__ void k_init_refine(const int *__restrict__ degen, const int *__restrict__ select, int P,
+                              int *__restrict__ active, int *__restrict__ iters, float *__restrict__ peak) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
+    if (select && !select[p]) {   // not refined: outputs left as they are
+        active[p] = 0;
+        return;
+    }
     active[p] = degen[p] ? 0 : 1;
     iters[p] = 0;
     peak[p] = 0.f;
@@ -398,10 +402,10 @@ cudaError_t launch_gather_seeds(const double *lib_quats, const int *best, int P,
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_refine(const int *degen, int P, int *active, int *iters, float *peak,
+cudaError_t launch_init_refine(const int *degen, const int *select, int P, int *active, int *iters, float *peak,
                                cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
-    k_init_refine<<<(P + 127) / 128, 128, 0, st>>>(degen, P, active, iters, peak);
+    k_init_refine<<<(P + 127) / 128, 128, 0, st>>>(degen, select, P, active, iters, peak);
     return cudaGetLastError();
 }
 

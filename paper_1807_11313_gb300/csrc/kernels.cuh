@@ -95,9 +95,40 @@ cudaError_t launch_eta_update(const float *lpT, const float *lpP, int nr, int ne
 
 cudaError_t launch_gather_seeds(const double *lib_quats, const int *best, int P, double *seeds,
                                 cudaStream_t st);
-cudaError_t launch_init_refine(const int *degen, int P, int *active, int *iters, float *peak,
+// select (nullable): patterns with select[p] == 0 are not refined and their outputs are left untouched
+cudaError_t launch_init_refine(const int *degen, const int *select, int P, int *active, int *iters, float *peak,
                                cudaStream_t st);
 cudaError_t launch_copy_active_peak(const float *src, const int *active, int P, float *dst,
                                     cudaStream_t st);
 cudaError_t launch_disorientation(const double *qa, const double *qb, int n, double *out,
                                   cudaStream_t st);
+
+// ------------------------------------------------ learned proposal network
+// input images: the 128 x 128 crop at (ox, oy) of image b = x + b * img_stride
+struct CnnInput {
+    const float *x;
+    long img_stride, row_stride;
+    int ox, oy;
+};
+long cnn_num_params(int k);
+size_t cnn_act_floats(int B, int k);    // activations of a batch (forward, kept for backward)
+size_t cnn_grad_floats(int B, int k);   // gradient work buffers of a batch
+const float *cnn_output(float *act, int B, int k);   // [B][6k] inside the activations
+cudaError_t launch_cnn_forward(const float *params, int k, const CnnInput &in, int B, float *act, int *launches,
+                               cudaStream_t st);
+// after launch_cnn_forward on the same act: loss_sum += sum of per-pattern
+// losses, grad = d(mean loss)/d(params), winners [B][2] (nullable)
+cudaError_t launch_cnn_backward(const float *params, int k, const CnnInput &in, int B, float *act, float *gbuf,
+                                const double *qgt, double *loss_sum, int *winners, float *grad, int num_sms,
+                                int *launches, cudaStream_t st);
+cudaError_t launch_cnn_proposals(const float *out, int n_heads_total, double *quats, cudaStream_t st);
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, long n, float lr, float b1, float b2,
+                        float eps, int t, cudaStream_t st);
+cudaError_t launch_take_head(const double *prop, int P, int k, int h, double *q, cudaStream_t st);
+cudaError_t launch_keep_best(const float *peak_h, const double *q_h, int P, int h, float *best_peak, double *best_q,
+                             int *best_h, cudaStream_t st);
+cudaError_t launch_fallback_flags(const float *peak, const int *degen, int P, float tau, int *fb, int *count,
+                                  cudaStream_t st);
+cudaError_t launch_fallback_mask(const int *degen, const int *fb, int P, int *mask, cudaStream_t st);
+cudaError_t launch_fallback_seeds(const int *fb, const int *best, const double *lib_q, const double *cur, int P,
+                                  double *seeds, cudaStream_t st);

@@ -85,11 +85,20 @@ _SIGS = {
     "xcf_index_noalloc": ([_P, _P, _P, _I32, _P, _P, _P, _P], C.c_int),
     "xcf_noalloc_max_patterns": ([_I32], C.c_int),
     "xcf_index_maps": ([_P, _P, _I32, _I32, _P], C.c_int),
+    "xcf_net_num_params": ([_I32], C.c_int64),
+    "xcf_net_create": ([_P, _I32, _P, C.POINTER(_P)], C.c_int),
+    "xcf_net_free": ([_P], C.c_int),
+    "xcf_net_params": ([_P, C.POINTER(_P), C.POINTER(C.c_int64)], C.c_int),
+    "xcf_net_forward": ([_P, _P, _P, _I32, C.POINTER(xcf_geometry), _P, _P], C.c_int),
+    "xcf_net_loss_grad": ([_P, _P, _P, _I32, C.POINTER(xcf_geometry), _P, _P, _P, _P, _P], C.c_int),
+    "xcf_net_adam": ([_P, _P, C.c_float, C.c_float, C.c_float, C.c_float, _P], C.c_int),
+    "xcf_propose": ([_P, _P, _P, _I32, C.POINTER(xcf_geometry), _P, _P], C.c_int),
+    "xcf_index_learned": ([_P, _P, _P, _P, _I32, _P, C.c_float, _P, _P, _P, _P, _P], C.c_int),
     "xcf_profile_enable": ([_P, C.c_int], C.c_int),
     "xcf_profile_read": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int], C.c_int),
 }
 
-STAGES = ("project", "prep", "search", "peak", "logpolar", "update", "other", "screen")
+STAGES = ("project", "prep", "search", "peak", "logpolar", "update", "other", "screen", "net")
 
 _lib = None
 
@@ -449,3 +458,96 @@ def xcf_index_maps(ctx: Context, maps, outs=None, graph: bool = False):
     _check(load().xcf_index_maps(ctx.handle, C.cast(desc, _P), n, XCF_MAPS_GRAPH if graph else 0, _stream()),
            ctx.handle)
     return outs
+
+
+# ------------------------------------------------------- proposal network
+def xcf_net_num_params(k: int = 8) -> int:
+    return int(load().xcf_net_num_params(int(k)))
+
+
+class Net:
+    """Proposal network handle (parameters and Adam state on the device)."""
+
+    def __init__(self, handle, k: int):
+        self.handle, self.k = handle, k
+        p, n = C.c_void_p(), C.c_int64()
+        _check(load().xcf_net_params(handle, C.byref(p), C.byref(n)))
+        self.n, self._ptr = n.value, p.value
+
+    def params(self):
+        """Writable device view of the parameters (float32 [n])."""
+        class _View:
+            pass
+        v = _View()
+        v.__cuda_array_interface__ = {"shape": (self.n,), "typestr": "<f4", "data": (self._ptr, False),
+                                      "version": 3, "strides": None}
+        return torch.as_tensor(v, device="cuda")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().xcf_net_free(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+
+def _geom_ref(geom):
+    return C.byref(geom) if geom is not None else None
+
+
+def xcf_net_create(ctx: Context, k: int = 8, params=None) -> Net:
+    h = C.c_void_p()
+    _check(load().xcf_net_create(ctx.handle, int(k), _ptr(params, torch.float32, "params", True), C.byref(h)),
+           ctx.handle)
+    return Net(h, int(k))
+
+
+def xcf_net_forward(ctx: Context, net: Net, images, geom: xcf_geometry | None = None):
+    B = images.shape[0]
+    out = torch.empty((B, 6 * net.k), dtype=torch.float32, device=images.device)
+    _check(load().xcf_net_forward(ctx.handle, net.handle, _ptr(images, torch.float32, "images"), B, _geom_ref(geom),
+                                  _ptr(out, torch.float32, "out"), _stream()), ctx.handle)
+    return out
+
+
+def xcf_net_loss_grad(ctx: Context, net: Net, images, quats_gt, geom: xcf_geometry | None = None,
+                      want_grad: bool = False, want_winners: bool = False):
+    """-> (loss [1] float64 device tensor, grad [n] or None, winners [B, 2] or None)"""
+    B, d = images.shape[0], images.device
+    loss = torch.empty(1, dtype=torch.float64, device=d)
+    grad = torch.empty(net.n, dtype=torch.float32, device=d) if want_grad else None
+    win = torch.empty((B, 2), dtype=torch.int32, device=d) if want_winners else None
+    _check(load().xcf_net_loss_grad(ctx.handle, net.handle, _ptr(images, torch.float32, "images"), B,
+                                    _geom_ref(geom), _ptr(quats_gt, torch.float64, "quats_gt"),
+                                    _ptr(loss, torch.float64, "loss"), _ptr(grad, torch.float32, "grad", True),
+                                    _ptr(win, torch.int32, "winners", True), _stream()), ctx.handle)
+    return loss, grad, win
+
+
+def xcf_net_adam(ctx: Context, net: Net, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
+                 eps: float = 1e-8):
+    _check(load().xcf_net_adam(ctx.handle, net.handle, lr, beta1, beta2, eps, _stream()), ctx.handle)
+
+
+def xcf_propose(ctx: Context, net: Net, patterns, geom: xcf_geometry | None = None):
+    """-> quats [P, k, 4] float64"""
+    P = patterns.shape[0]
+    q = torch.empty((P, net.k, 4), dtype=torch.float64, device=patterns.device)
+    _check(load().xcf_propose(ctx.handle, net.handle, _ptr(patterns, torch.float32, "patterns"), P, _geom_ref(geom),
+                              _ptr(q, torch.float64, "quats"), _stream()), ctx.handle)
+    return q
+
+
+def xcf_index_learned(ctx: Context, net: Net, lib: Library, patterns, pcs=None, tau: float = 0.3, out=None):
+    """Proposals -> correlation score -> refinement, with the full search as
+    fallback below tau.  -> (quats [P, 4], peak [P], iters [P], fallback [P])"""
+    P, d = patterns.shape[0], patterns.device
+    if out is None:
+        out = (torch.empty((P, 4), dtype=torch.float64, device=d), torch.empty(P, dtype=torch.float32, device=d),
+               torch.empty(P, dtype=torch.int32, device=d), torch.empty(P, dtype=torch.int32, device=d))
+    q, pk, it, fb = out
+    _check(load().xcf_index_learned(ctx.handle, net.handle, lib.handle, _ptr(patterns, torch.float32, "patterns"), P,
+                                    _ptr(pcs, torch.float64, "pcs", True), float(tau), _ptr(q, torch.float64, "quats"),
+                                    _ptr(pk, torch.float32, "peak"), _ptr(it, torch.int32, "iters"),
+                                    _ptr(fb, torch.int32, "fallback"), _stream()), ctx.handle)
+    return out
