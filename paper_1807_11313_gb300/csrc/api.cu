@@ -200,10 +200,7 @@ cudaError_t run_prep(xcf_ctx *ctx, const float *img, int P, const PrepArgs &a, f
 cudaError_t run_search(xcf_ctx *ctx, int n, const float2 *St, int T, const float2 *Sp, const int *degen, int P,
                        unsigned long long *keys, float *peaks_all, int num_sms, cudaStream_t st) {
     if (n <= 128) return launch_search(n, St, T, Sp, degen, P, keys, peaks_all, num_sms, st);
-    float2 *w;
-    int grid;
-    cudaError_t e = big_work(ctx, n, (long)P * ((T + 1) / 2), &w, &grid);
-    return e != cudaSuccess ? e : launch_search_big(n, St, T, Sp, degen, P, keys, peaks_all, w, grid, st);
+    return launch_search_c256(St, T, Sp, degen, P, keys, peaks_all, nullptr, 0, st);
 }
 
 cudaError_t run_pair_peak(xcf_ctx *ctx, int n, const float2 *St, const int *tidx, const float2 *Sp,
@@ -960,12 +957,8 @@ int xcf_rescore(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int
                        launch_search_list(c.n, lib->spectra, cp, k, sp, degen, np, keys, nullptr, ctx->num_sms, st),
                        "rescore");
         } else {
-            float2 *w;
-            int grid;
-            XCF_CHECK(big_work(ctx, c.n, (long)np * ((k + 1) / 2), &w, &grid), "work arrays");
             XCF_LAUNCH(XCF_STAGE_SEARCH, st,
-                       launch_search_big(c.n, lib->spectra, 0, sp, degen, np, keys, nullptr, w, grid, st, cp, k),
-                       "rescore");
+                       launch_search_c256(lib->spectra, 0, sp, degen, np, keys, nullptr, cp, k, st), "rescore");
         }
         XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_keys_to_best(keys, np, best + p0, st), "keys_to_best");
         XCF_LAUNCH(XCF_STAGE_PEAK, st,

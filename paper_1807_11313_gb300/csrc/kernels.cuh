@@ -39,6 +39,13 @@ cudaError_t launch_search_big(int N, const float2 *St, int T, const float2 *Sp, 
                               unsigned long long *keys, float *peaks_all, float2 *work, int grid,
                               cudaStream_t st, const int *cand = nullptr, int kc = 0);
 
+// N = 256 search on clusters of four CTAs (the 256 x 256 array in distributed
+// shared memory); with cand: each pattern's candidate list cand [P][kc]
+cudaError_t launch_search_c256(const float2 *St, int T, const float2 *Sp, const int *degen, int P,
+                               unsigned long long *keys, float *peaks_all, const int *cand, int kc,
+                               cudaStream_t st);
+size_t c256_smem_bytes();
+
 // search over each pattern's candidate list cand [P][kc] (library indices, < 0 empty)
 cudaError_t launch_search_list(int N, const float2 *St, const int *cand, int kc, const float2 *Sp,
                                const int *degen, int P, unsigned long long *keys, float *peaks, int num_sms,
