@@ -191,10 +191,7 @@ cudaError_t big_work(xcf_ctx *ctx, int n, long items, float2 **work, int *grid) 
 cudaError_t run_prep(xcf_ctx *ctx, const float *img, int P, const PrepArgs &a, float2 *spec, float *spatial,
                      int *degen, const int *active, cudaStream_t st) {
     if (a.N <= 128) return launch_prep(img, P, a, spec, spatial, degen, active, st);
-    float2 *w;
-    int grid;
-    cudaError_t e = big_work(ctx, a.N, P, &w, &grid);
-    return e != cudaSuccess ? e : launch_prep_big(img, P, a, spec, spatial, degen, active, w, grid, st);
+    return launch_prep_c256(img, P, a, spec, spatial, degen, active, st);
 }
 
 cudaError_t run_search(xcf_ctx *ctx, int n, const float2 *St, int T, const float2 *Sp, const int *degen, int P,
@@ -206,10 +203,7 @@ cudaError_t run_search(xcf_ctx *ctx, int n, const float2 *St, int T, const float
 cudaError_t run_pair_peak(xcf_ctx *ctx, int n, const float2 *St, const int *tidx, const float2 *Sp,
                           const int *degen, const int *active, int P, float *peak, float *shift, cudaStream_t st) {
     if (n <= 128) return launch_pair_peak(n, St, tidx, Sp, degen, active, P, peak, shift, st);
-    float2 *w;
-    int grid;
-    cudaError_t e = big_work(ctx, n, P, &w, &grid);
-    return e != cudaSuccess ? e : launch_pair_peak_big(n, St, tidx, Sp, degen, active, P, peak, shift, w, grid, st);
+    return launch_pair_peak_c256(St, tidx, Sp, degen, active, P, peak, shift, st);
 }
 
 int check_lib(xcf_ctx *ctx, const xcf_library *lib) {

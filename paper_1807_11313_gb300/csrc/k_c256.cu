@@ -68,22 +68,59 @@ __device__ __forceinline__ void row_home(int u, int &owner, int &slot) {
 }
 __device__ __forceinline__ int zc_index(int slot, int x) { return slot * N + (x ^ ((slot >> 1) & 15)); }
 
-// 256-point inverse DFT (X[k] = sum_n x[n] e^{+2 pi i nk/256}) of a line held
-// by a 16-thread group: on entry a[n1] = x[16 n1 + t]; on exit a[p] =
+// 256-point DFT (X[k] = sum_n x[n] e^{SIGN 2 pi i nk/256}) of a line held by
+// a 16-thread group: on entry a[n1] = x[16 n1 + t]; on exit a[p] =
 // X[t + 16 bitrev4(p)].  tw[k] = e^{+2 pi i t k / 256}; scr = the group's buffer.
-__device__ __forceinline__ void line_ifft(float2 (&a)[16], const float2 (&tw)[16], float2 *scr, int t) {
-    fft_reg_dif<16, +1>(a);   // a[p] = A[bitrev(p)], A[k1] = sum_n1 x[16 n1 + t] e^{+2 pi i n1 k1 / 16}
+template <int SIGN>
+__device__ __forceinline__ void line_fft(float2 (&a)[16], const float2 (&tw)[16], float2 *scr, int t) {
+    fft_reg_dif<16, SIGN>(a);   // a[p] = A[bitrev(p)], A[k1] = sum_n1 x[16 n1 + t] e^{SIGN 2 pi i n1 k1 / 16}
     StaticFor<0, 16>::run([&](auto pp) {
         constexpr int p = decltype(pp)::value;
         constexpr int k1 = cx_bitrev(p, 4);
-        const float2 v = k1 == 0 ? a[p] : c_mul(a[p], tw[k1]);
+        float2 w = tw[k1];
+        if (SIGN < 0) w.y = -w.y;
+        const float2 v = k1 == 0 ? a[p] : c_mul(a[p], w);
         scr[t * 16 + (k1 ^ t)] = v;
     });
-    __syncwarp();
+    const unsigned gm = 0xffffu << (threadIdx.x & 16);   // the group's half of the warp
+    __syncwarp(gm);
 #pragma unroll
     for (int n2 = 0; n2 < 16; ++n2) a[n2] = scr[n2 * 16 + (t ^ n2)];
-    __syncwarp();
-    fft_reg_dif<16, +1>(a);   // a[p] = X[t + 16 bitrev(p)]
+    __syncwarp(gm);
+    fft_reg_dif<16, SIGN>(a);   // a[p] = X[t + 16 bitrev(p)]
+}
+__device__ __forceinline__ void line_ifft(float2 (&a)[16], const float2 (&tw)[16], float2 *scr, int t) {
+    line_fft<+1>(a, tw, scr, t);
+}
+
+// rows of Z = X1 + i X2 owned by CTA c, X_j = f_j conj(T_j) P_j (half spectra
+// T_j, P_j extended by Hermitian symmetry), transformed along v into Zc.
+// Group g builds and transforms the row pairs j = g and g + 16.
+__device__ __forceinline__ void rows_phase(float2 *Zc, const float2 *__restrict__ s1, const float2 *__restrict__ p1,
+                                           float f1, const float2 *__restrict__ s2, const float2 *__restrict__ p2,
+                                           float f2, const float2 (&tw)[16], float2 *scr, int c, int g, int t) {
+#pragma unroll 1
+    for (int r = 0; r < 4; ++r) {
+        const int j = g + 16 * (r >> 1), b = 32 * c + j;
+        const int u0 = b, u1 = b == 0 ? 128 : N - b;
+        const int u = (r & 1) ? u1 : u0;
+        const int pu = (N - u) & (N - 1);
+        float2 a[16];
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) {
+            const int v = 16 * n1 + t;
+            const bool direct = v <= 128;
+            const int k = direct ? u * HW + v : pu * HW + (N - v);   // Hermitian half: X(u, v) = conj(X(-u, 256 - v))
+            float2 x1 = c_mulcj(__ldg(s1 + k), __ldg(p1 + k)), x2 = c_mulcj(__ldg(s2 + k), __ldg(p2 + k));
+            x1 = make_float2(x1.x * f1, x1.y * f1);
+            x2 = make_float2(x2.x * f2, x2.y * f2);
+            a[n1] = direct ? make_float2(x1.x - x2.y, x1.y + x2.x) : make_float2(x1.x + x2.y, -x1.y + x2.x);
+        }
+        line_ifft(a, tw, scr, t);
+        const int slot = 2 * j + (r & 1);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) Zc[zc_index(slot, t + 16 * cx_bitrev(q, 4))] = a[q];
+    }
 }
 
 __device__ __forceinline__ float warp_max(float v) {
@@ -139,34 +176,7 @@ k_search_c256(const float2 *__restrict__ St, int T, const float2 *__restrict__ S
             const int t1 = cand ? cand[(size_t)p * kc + j1] : j1;
             const int t2 = cand ? cand[(size_t)p * kc + j2] : j2;
             const float2 *s1 = St + (size_t)max(t1, 0) * N * HW, *s2 = St + (size_t)max(t2, 0) * N * HW;
-            // ---- rows: group g builds and transforms the pairs j = g and g + 16
-#pragma unroll 1
-            for (int r = 0; r < 4; ++r) {
-                const int j = g + 16 * (r >> 1), b = 32 * c + j;
-                const int u0 = b, u1 = b == 0 ? 128 : N - b;
-                const int u = (r & 1) ? u1 : u0;
-                const int pu = (N - u) & (N - 1);
-                float2 a[16];
-#pragma unroll
-                for (int n1 = 0; n1 < 16; ++n1) {
-                    const int v = 16 * n1 + t;
-                    if (v <= 128) {
-                        const int k = u * HW + v;
-                        const float2 s = __ldg(sp + k);
-                        const float2 x1 = c_mulcj(__ldg(s1 + k), s), x2 = c_mulcj(__ldg(s2 + k), s);
-                        a[n1] = make_float2(x1.x - x2.y, x1.y + x2.x);
-                    } else {   // Hermitian half: X(u, v) = conj(X(-u, 256 - v))
-                        const int k = pu * HW + (N - v);
-                        const float2 s = __ldg(sp + k);
-                        const float2 x1 = c_mulcj(__ldg(s1 + k), s), x2 = c_mulcj(__ldg(s2 + k), s);
-                        a[n1] = make_float2(x1.x + x2.y, -x1.y + x2.x);
-                    }
-                }
-                line_ifft(a, tw, scr, t);
-                const int slot = 2 * j + (r & 1);
-#pragma unroll
-                for (int q = 0; q < 16; ++q) Zc[zc_index(slot, t + 16 * cx_bitrev(q, 4))] = a[q];
-            }
+            rows_phase(Zc, s1, sp, 1.f, s2, sp, 1.f, tw, scr, c, g, t);
             cluster_barrier();
             // ---- columns x = 64 c + 4 g + q: gather over the cluster, transform, maxima
             float m1 = -INFINITY, m2 = -INFINITY;
@@ -221,6 +231,405 @@ k_search_c256(const float2 *__restrict__ St, int T, const float2 *__restrict__ S
         if (tid == 0 && best_t >= 0) atomicMax(keys + p, pack_key(best_v, best_t));
     }
     cluster_barrier();   // no CTA leaves while another may still read its shared memory
+}
+
+// ------------------------------------------------------ single-surface peak
+// Two patterns per cluster pass, one surface each (real and imaginary parts
+// of one complex inverse transform): after the column phase every CTA posts
+// its best (value, row-major index) per surface; CTA 0 takes the cluster's
+// argmax (ties: lowest index), recomputes the three columns around each peak
+// from the distributed rows and fits the parabolas (the peak up-sampling
+// reading: 3 points per axis, clamped to +-0.5).
+constexpr size_t PEAK_SMEM = (ZC_F2 + SCR_F2) * sizeof(float2) + (6 * N + 64) * sizeof(float);
+
+__device__ __forceinline__ void better(float &bv, int &bi, float v, int i) {
+    if (v > bv || (v == bv && i < bi)) {
+        bv = v;
+        bi = i;
+    }
+}
+__device__ __forceinline__ float parabola_c(float cm, float c0, float cp) {
+    const float den = cm - 2.f * c0 + cp;
+    if (!(den < 0.f)) return 0.f;
+    const float d = (cm - cp) / (2.f * den);
+    return fminf(0.5f, fmaxf(-0.5f, d));
+}
+
+__global__ void __launch_bounds__(NT, 1)
+k_pair_peak_c256(const float2 *__restrict__ St, const int *__restrict__ tidx, const float2 *__restrict__ Sp,
+                 const int *__restrict__ degen, const int *__restrict__ active, int P, float *__restrict__ peak,
+                 float *__restrict__ shift) {
+    extern __shared__ float4 smem_raw[];
+    float2 *Zc = reinterpret_cast<float2 *>(smem_raw);
+    float2 *scr_all = Zc + ZC_F2;
+    float *colbuf = reinterpret_cast<float *>(scr_all + SCR_F2);   // [6][256] recomputed columns
+    float *cand = colbuf + 6 * N;                                   // [0..3] (value a, index a, value b, index b)
+    float *wred = cand + 8;                                         // [0..31] warp candidates
+    const int tid = threadIdx.x, t = tid & 15, g = tid >> 4, warp = tid >> 5, lane = tid & 31;
+    const int c = (int)cluster_rank();
+    const int cid = blockIdx.x / NC, ncl = gridDim.x / NC;
+    float2 *scr = scr_all + g * 256;
+
+    float2 tw[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        double sn, co;
+        sincospi(2.0 * t * k / N, &sn, &co);
+        tw[k] = make_float2((float)co, (float)sn);
+    }
+    const uint32_t zc_local = (uint32_t)__cvta_generic_to_shared(Zc);
+    const uint32_t cand_local = (uint32_t)__cvta_generic_to_shared(cand);
+    uint32_t rbase[16];
+    int rsw[16];
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) {
+        int owner, slot;
+        row_home(16 * n1 + t, owner, slot);
+        rbase[n1] = map_to_rank(zc_local, owner) + (uint32_t)(slot * N * sizeof(float2));
+        rsw[n1] = (slot >> 1) & 15;
+    }
+    const int npass = (P + 1) / 2;
+    for (int k2 = cid; k2 < npass; k2 += ncl) {
+        const int pa = 2 * k2, pb = 2 * k2 + 1;
+        // per surface: 0 skip (inactive / absent), 1 zero outputs, 2 compute
+        int mode[2];
+        int tt[2];
+        for (int s = 0; s < 2; ++s) {
+            const int p = s ? pb : pa;
+            if (p >= P || (active && !active[p])) {
+                mode[s] = 0;
+                tt[s] = 0;
+                continue;
+            }
+            tt[s] = tidx ? tidx[p] : p;
+            mode[s] = ((degen && degen[p]) || tt[s] < 0) ? 1 : 2;
+        }
+        if (tid == 0 && c == 0)
+            for (int s = 0; s < 2; ++s)
+                if (mode[s] == 1) {
+                    const int p = s ? pb : pa;
+                    peak[p] = 0.f;
+                    shift[2 * p] = 0.f;
+                    shift[2 * p + 1] = 0.f;
+                }
+        if (mode[0] != 2 && mode[1] != 2) continue;    // uniform over the cluster
+        const float2 *sa = St + (size_t)(mode[0] == 2 ? tt[0] : 0) * N * HW;
+        const float2 *sb = St + (size_t)(mode[1] == 2 ? tt[1] : 0) * N * HW;
+        const float2 *qa = Sp + (size_t)(mode[0] == 2 ? pa : 0) * N * HW;
+        const float2 *qb = Sp + (size_t)(mode[1] == 2 ? pb : 0) * N * HW;
+        rows_phase(Zc, sa, qa, mode[0] == 2 ? 1.f : 0.f, sb, qb, mode[1] == 2 ? 1.f : 0.f, tw, scr, c, g, t);
+        cluster_barrier();
+        float bva = -INFINITY, bvb = -INFINITY;
+        int bia = 0x7fffffff, bib = 0x7fffffff;
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+            const int x = ROWS * c + 4 * g + q;
+            float2 a[16];
+#pragma unroll
+            for (int n1 = 0; n1 < 16; ++n1)
+                a[n1] = ld_cluster(rbase[n1] + (uint32_t)((x ^ rsw[n1]) * sizeof(float2)));
+            line_ifft(a, tw, scr, t);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int i = (t + 16 * cx_bitrev(k, 4)) * N + x;
+                better(bva, bia, a[k].x, i);
+                better(bvb, bib, a[k].y, i);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            better(bva, bia, __shfl_xor_sync(0xffffffffu, bva, o), __shfl_xor_sync(0xffffffffu, bia, o));
+            better(bvb, bib, __shfl_xor_sync(0xffffffffu, bvb, o), __shfl_xor_sync(0xffffffffu, bib, o));
+        }
+        if (lane == 0) {
+            wred[4 * warp] = bva;
+            wred[4 * warp + 1] = __int_as_float(bia);
+            wred[4 * warp + 2] = bvb;
+            wred[4 * warp + 3] = __int_as_float(bib);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < NT / 32; ++w) {
+                better(bva, bia, wred[4 * w], __float_as_int(wred[4 * w + 1]));
+                better(bvb, bib, wred[4 * w + 2], __float_as_int(wred[4 * w + 3]));
+            }
+            cand[0] = bva;
+            cand[1] = __int_as_float(bia);
+            cand[2] = bvb;
+            cand[3] = __int_as_float(bib);
+        }
+        cluster_barrier();   // every CTA's candidates posted
+        if (c == 0) {
+            // the cluster's argmax, the same in every thread of CTA 0 (ranks in order)
+            float va = -INFINITY, vb = -INFINITY;
+            int ia = 0x7fffffff, ib = 0x7fffffff;
+            for (int r = 0; r < NC; ++r) {
+                const uint32_t ra = map_to_rank(cand_local, r);
+                better(va, ia, ld_cluster_f(ra), __float_as_int(ld_cluster_f(ra + 4)));
+                better(vb, ib, ld_cluster_f(ra + 8), __float_as_int(ld_cluster_f(ra + 12)));
+            }
+            // groups 0..5 recompute the columns x0 - 1, x0, x0 + 1 of each surface
+            if (g < 6) {
+                const int s = g / 3, d = g % 3 - 1;
+                const int i0 = s ? ib : ia;
+                const int x = ((i0 & (N - 1)) + d + N) & (N - 1);
+                float2 a[16];
+#pragma unroll
+                for (int n1 = 0; n1 < 16; ++n1)
+                    a[n1] = ld_cluster(rbase[n1] + (uint32_t)((x ^ rsw[n1]) * sizeof(float2)));
+                line_ifft(a, tw, scr, t);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) colbuf[g * N + t + 16 * cx_bitrev(k, 4)] = s ? a[k].y : a[k].x;
+            }
+            __syncthreads();
+            if (tid < 2 && mode[tid] == 2) {
+                const int s = tid, i0 = s ? ib : ia, p = s ? pb : pa;
+                const float *cb = colbuf + 3 * s * N;
+                const int y0 = i0 >> 8, x0 = i0 & (N - 1);
+                const float c0 = cb[N + y0];
+                const float cxm = cb[y0], cxp = cb[2 * N + y0];
+                const float cym = cb[N + ((y0 + N - 1) & (N - 1))], cyp = cb[N + ((y0 + 1) & (N - 1))];
+                peak[p] = c0;
+                shift[2 * p] = (float)(x0 < N / 2 ? x0 : x0 - N) + parabola_c(cxm, c0, cxp);
+                shift[2 * p + 1] = (float)(y0 < N / 2 ? y0 : y0 - N) + parabola_c(cym, c0, cyp);
+            }
+        }
+        cluster_barrier();   // CTA 0 done reading the distributed rows and candidates
+    }
+    cluster_barrier();
+}
+
+// ------------------------------------------------------ pre-processing
+// One cluster per image (Eq. 4 and the filtering / normalisation of the FFT
+// section): CTA c loads rows 64c..64c+63 of the crop, the cluster reduces the
+// mean and standard deviation, the rows are windowed and transformed two at a
+// time (one complex line, split by Hermitian symmetry) into R[y][0..128], and
+// CTA c then gathers and transforms columns 32c..32c+31 (CTA 3 also column
+// 128), filters them and reduces the filtered energy over the cluster.  With a
+// spatial output the filtered, normalised spectrum is transformed back:
+// columns in place, then rows two at a time (conjugate-symmetric extension).
+constexpr size_t RC_F2 = (size_t)ROWS * HW;                        // row spectra [64][129]
+constexpr size_t ST_F2 = (size_t)N * 32;                          // column staging [256][32]
+constexpr size_t PREP_SMEM = (RC_F2 + ST_F2 + N + SCR_F2) * sizeof(float2) + 16 * sizeof(double);
+
+__device__ __forceinline__ double ld_cluster_d(uint32_t addr) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ double block_sum_d(double v, double *sh) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += sh[w];
+    __syncthreads();
+    return s;
+}
+// sum of one partial per CTA, identical (same order) in every CTA of the cluster
+__device__ __forceinline__ double cluster_sum(double part, double *slot, uint32_t slot_addr) {
+    if (threadIdx.x == 0) *slot = part;
+    cluster_barrier();
+    double s = 0.0;
+    for (int r = 0; r < NC; ++r) s += ld_cluster_d(map_to_rank(slot_addr, r));
+    return s;
+}
+__device__ __forceinline__ int st_index(int u, int vl) { return u * 32 + (vl ^ (u & 31)); }
+
+__global__ void __launch_bounds__(NT, 1)
+k_prep_c256(const float *__restrict__ img, int P, PrepArgs a, float2 *__restrict__ spec, float *__restrict__ spatial,
+            int *__restrict__ degen, const int *__restrict__ active) {
+    extern __shared__ float4 smem_raw[];
+    float2 *Rc = reinterpret_cast<float2 *>(smem_raw);
+    float2 *Stage = Rc + RC_F2;                       // also the input rows [64][256] floats
+    float *Xr = reinterpret_cast<float *>(Stage);
+    float2 *Col128 = Stage + ST_F2;
+    float2 *scr_all = Col128 + N;
+    double *red = reinterpret_cast<double *>(scr_all + SCR_F2);   // [0..7] block partials, [8..10] cluster slots
+    const int tid = threadIdx.x, t = tid & 15, g = tid >> 4;
+    const int c = (int)cluster_rank();
+    const int cid = blockIdx.x / NC, ncl = gridDim.x / NC;
+    float2 *scr = scr_all + g * 256;
+
+    float2 tw[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        double sn, co;
+        sincospi(2.0 * t * k / N, &sn, &co);
+        tw[k] = make_float2((float)co, (float)sn);
+    }
+    const uint32_t rc_local = (uint32_t)__cvta_generic_to_shared(Rc);
+    const uint32_t st_local = (uint32_t)__cvta_generic_to_shared(Stage);
+    const uint32_t c128_local = (uint32_t)__cvta_generic_to_shared(Col128);
+    const uint32_t slot_local = (uint32_t)__cvta_generic_to_shared(red + 8);
+    uint32_t rrow[16];   // column phase: cluster address of row y = 16 n1 + t of R
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) {
+        const int y = 16 * n1 + t;
+        rrow[n1] = map_to_rank(rc_local, y >> 6) + (uint32_t)((y & 63) * HW * sizeof(float2));
+    }
+    const float inv_nn = 1.f / N;
+
+    for (int p = cid; p < P; p += ncl) {
+        if (active && !active[p]) continue;            // uniform over the cluster
+        const float *src = img + (size_t)p * a.W * a.H;
+        float2 *out = spec + (size_t)p * N * HW;
+        // ---- statistics of the crop
+        double s = 0.0;
+        for (int i = tid; i < ROWS * N; i += NT) {
+            const int r = i >> 8, x = i & (N - 1);
+            const float v = __ldg(src + (size_t)(a.oy + ROWS * c + r) * a.W + a.ox + x);
+            Xr[i] = v;
+            s += v;
+        }
+        const double mean = cluster_sum(block_sum_d(s, red), red + 8, slot_local) / ((double)N * N);
+        double ss = 0.0;
+        for (int i = tid; i < ROWS * N; i += NT) {
+            const double d = Xr[i] - mean;
+            ss += d * d;
+        }
+        const double sd =
+            sqrt(cluster_sum(block_sum_d(ss, red), red + 9, slot_local + sizeof(double)) / ((double)N * N));
+        bool bad = !(sd > 1e-12 * (1.0 + fabs(mean)));
+        if (!bad) {
+            // ---- rows (two per complex line), windowed and standardised
+            const float m = (float)mean, inv = (float)(1.0 / sd);
+#pragma unroll 1
+            for (int q = 0; q < 2; ++q) {
+                const int ra = 2 * (g + 16 * q), rb = ra + 1;
+                const int ya = ROWS * c + ra, yb = ya + 1;
+                const float wa = a.window ? 0.5f * (1.f - cospif(2.f * ya / N)) : 1.f;
+                const float wb = a.window ? 0.5f * (1.f - cospif(2.f * yb / N)) : 1.f;
+                float2 z[16];
+#pragma unroll
+                for (int n1 = 0; n1 < 16; ++n1) {
+                    const int x = 16 * n1 + t;
+                    const float wx = (a.window ? 0.5f * (1.f - cospif(2.f * x / N)) : 1.f) * inv;
+                    z[n1] = make_float2((Xr[ra * N + x] - m) * wx * wa, (Xr[rb * N + x] - m) * wx * wb);
+                }
+                line_fft<-1>(z, tw, scr, t);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) scr[t + 16 * cx_bitrev(k, 4)] = z[k];
+                __syncwarp(0xffffu << (tid & 16));
+#pragma unroll
+                for (int mm = 0; mm < 9; ++mm) {
+                    const int v = t + 16 * mm;
+                    if (v > 128) break;
+                    const float2 zv = scr[v], zn = scr[(N - v) & (N - 1)];
+                    Rc[ra * HW + v] = make_float2(0.5f * (zv.x + zn.x), 0.5f * (zv.y - zn.y));
+                    Rc[rb * HW + v] = make_float2(0.5f * (zv.y + zn.y), 0.5f * (zn.x - zv.x));
+                }
+                __syncwarp(0xffffu << (tid & 16));
+            }
+        }
+        cluster_barrier();   // R complete (every CTA takes the same branch: mean and sd are cluster-wide)
+        double e = 0.0;
+        if (!bad) {
+            // ---- columns: gather, transform, filter; keep in Stage / Col128
+            const int nq = (c == NC - 1 && g == 0) ? 3 : 2;
+#pragma unroll 1
+            for (int q = 0; q < nq; ++q) {
+                const int v = q < 2 ? 32 * c + 2 * g + q : 128;
+                float2 z[16];
+#pragma unroll
+                for (int n1 = 0; n1 < 16; ++n1) z[n1] = ld_cluster(rrow[n1] + (uint32_t)(v * sizeof(float2)));
+                line_fft<-1>(z, tw, scr, t);
+                const float fv = (float)(v < N / 2 ? v : v - N);
+                const double wv = (v == 0 || v == N / 2) ? 1.0 : 2.0;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int u = t + 16 * cx_bitrev(k, 4);
+                    const float fu = (float)(u < N / 2 ? u : u - N);
+                    const float rho2 = fu * fu + fv * fv;
+                    const float h = -expm1f(-rho2 * a.inv2shp) * expf(-rho2 * a.inv2slp);
+                    const float2 X = make_float2(z[k].x * h, z[k].y * h);
+                    e += wv * ((double)X.x * X.x + (double)X.y * X.y);
+                    if (q < 2) Stage[st_index(u, v - 32 * c)] = X;
+                    else Col128[u] = X;
+                }
+            }
+        }
+        const double energy = cluster_sum(block_sum_d(e, red), red + 10, slot_local + 2 * sizeof(double));
+        bad = bad || !(energy > 0.0);
+        if (tid == 0 && c == 0 && degen) degen[p] = bad ? 1 : 0;
+        if (bad) {
+            for (int i = tid; i < ROWS * HW; i += NT) out[(size_t)ROWS * c * HW + i] = make_float2(0.f, 0.f);
+            if (spatial)
+                for (int i = tid; i < ROWS * N; i += NT) spatial[(size_t)p * N * N + (size_t)ROWS * c * N + i] = 0.f;
+            continue;   // uniform: the decision used cluster-wide sums
+        }
+        const float sc = (float)(1.0 / sqrt(energy));
+        for (int i = tid; i < N * 32; i += NT) {
+            const int u = i >> 5, vl = i & 31;
+            const float2 X = Stage[st_index(u, vl)];
+            out[(size_t)u * HW + 32 * c + vl] = make_float2(X.x * sc, X.y * sc);
+        }
+        if (c == NC - 1)
+            for (int u = tid; u < N; u += NT) out[(size_t)u * HW + 128] = make_float2(Col128[u].x * sc, Col128[u].y * sc);
+        if (!spatial) {
+            __syncthreads();   // Stage is the next image's input buffer
+            continue;
+        }
+        __syncthreads();
+        // ---- spatial image: columns back in place, then rows two at a time
+        {
+            const int nq = (c == NC - 1 && g == 0) ? 3 : 2;
+#pragma unroll 1
+            for (int q = 0; q < nq; ++q) {
+                const int vl = 2 * g + q;
+                float2 z[16];
+#pragma unroll
+                for (int n1 = 0; n1 < 16; ++n1) {
+                    const int u = 16 * n1 + t;
+                    const float2 X = q < 2 ? Stage[st_index(u, vl)] : Col128[u];
+                    z[n1] = make_float2(X.x * sc, X.y * sc);
+                }
+                line_fft<+1>(z, tw, scr, t);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int y = t + 16 * cx_bitrev(k, 4);
+                    if (q < 2) Stage[st_index(y, vl)] = z[k];
+                    else Col128[y] = z[k];
+                }
+            }
+        }
+        cluster_barrier();   // T[y][v] of every column visible
+#pragma unroll 1
+        for (int q = 0; q < 2; ++q) {
+            const int ya = ROWS * c + 2 * (g + 16 * q), yb = ya + 1;
+            float2 z[16];
+#pragma unroll
+            for (int n1 = 0; n1 < 16; ++n1) {
+                const int v = 16 * n1 + t;
+                const int w = v <= 128 ? v : N - v;
+                float2 ta, tb;
+                if (w == 128) {
+                    const uint32_t base = map_to_rank(c128_local, NC - 1);
+                    ta = ld_cluster(base + (uint32_t)(ya * sizeof(float2)));
+                    tb = ld_cluster(base + (uint32_t)(yb * sizeof(float2)));
+                } else {
+                    const uint32_t base = map_to_rank(st_local, w >> 5);
+                    ta = ld_cluster(base + (uint32_t)(st_index(ya, w & 31) * sizeof(float2)));
+                    tb = ld_cluster(base + (uint32_t)(st_index(yb, w & 31) * sizeof(float2)));
+                }
+                if (v > 128) {   // conjugate-symmetric extension of a real image's row
+                    ta.y = -ta.y;
+                    tb.y = -tb.y;
+                }
+                z[n1] = make_float2(ta.x - tb.y, ta.y + tb.x);
+            }
+            line_fft<+1>(z, tw, scr, t);
+            float *oa = spatial + (size_t)p * N * N + (size_t)ya * N, *ob = oa + N;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int x = t + 16 * cx_bitrev(k, 4);
+                oa[x] = z[k].x * inv_nn;
+                ob[x] = z[k].y * inv_nn;
+            }
+        }
+        cluster_barrier();   // Stage / Col128 read by the other CTAs: free for the next image
+    }
+    cluster_barrier();
 }
 
 int max_active_clusters() {
@@ -282,4 +691,69 @@ cudaError_t launch_search_c256(const float2 *St, int T, const float2 *Sp, const 
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_search_c256, St, T, Sp, degen, nchunks, ppc, (int)n_items, keys, peaks_all,
                               cand, kc);
+}
+
+cudaError_t launch_prep_c256(const float *img, int P, const PrepArgs &a, float2 *spec, float *spatial, int *degen,
+                             const int *active, cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    if (a.N != N) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_prep_c256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PREP_SMEM);
+    if (e != cudaSuccess) return e;
+    static int ncl_max = -1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = PREP_SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = NC;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (ncl_max < 0) {
+        cfg.gridDim = dim3(NC * 64);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_prep_c256, &cfg) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 32;
+        }
+        ncl_max = n;
+    }
+    const int ncl = P < ncl_max ? P : ncl_max;
+    cfg.gridDim = dim3(NC * ncl);
+    return cudaLaunchKernelEx(&cfg, k_prep_c256, img, P, a, spec, spatial, degen, active);
+}
+
+cudaError_t launch_pair_peak_c256(const float2 *St, const int *tidx, const float2 *Sp, const int *degen,
+                                  const int *active, int P, float *peak, float *shift, cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_pair_peak_c256, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)PEAK_SMEM);
+    if (e != cudaSuccess) return e;
+    static int ncl_max = -1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = PEAK_SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = NC;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (ncl_max < 0) {
+        cfg.gridDim = dim3(NC * 64);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_pair_peak_c256, &cfg) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 32;
+        }
+        ncl_max = n;
+    }
+    const int npass = (P + 1) / 2;
+    const int ncl = npass < ncl_max ? npass : ncl_max;
+    cfg.gridDim = dim3(NC * ncl);
+    return cudaLaunchKernelEx(&cfg, k_pair_peak_c256, St, tidx, Sp, degen, active, P, peak, shift);
 }

@@ -45,6 +45,12 @@ cudaError_t launch_search_c256(const float2 *St, int T, const float2 *Sp, const 
                                unsigned long long *keys, float *peaks_all, const int *cand, int kc,
                                cudaStream_t st);
 size_t c256_smem_bytes();
+// N = 256 single-surface peak on clusters of four CTAs (two patterns per pass)
+cudaError_t launch_pair_peak_c256(const float2 *St, const int *tidx, const float2 *Sp, const int *degen,
+                                  const int *active, int P, float *peak, float *shift, cudaStream_t st);
+// N = 256 pre-processing on clusters of four CTAs (one image per cluster)
+cudaError_t launch_prep_c256(const float *img, int P, const PrepArgs &a, float2 *spec, float *spatial, int *degen,
+                             const int *active, cudaStream_t st);
 
 // search over each pattern's candidate list cand [P][kc] (library indices, < 0 empty)
 cudaError_t launch_search_list(int N, const float2 *St, const int *cand, int kc, const float2 *Sp,
