@@ -53,12 +53,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="patterns in the CPU sample (0: auto)")
-    ap.add_argument("--form", default="plain", choices=["plain", "precision", "batched"],
+    ap.add_argument("--form", default="plain", choices=["plain", "precision", "batched", "learned"],
                     help="plain: full FP32 XCF search + refinement of the 128^2 map; precision: BF16 "
                          "tensor-core screen top-32 + FP32 rescore + refinement at 256^2; batched: eight maps "
-                         "with different detectors in one persistent graph-captured search")
+                         "with different detectors in one persistent graph-captured search; learned: CNN proposals "
+                         "+ correlation score + refinement with full-search fallback")
     ap.add_argument("--patterns", type=int, default=0, help="precision form: patterns per GPU (0: 50,000)")
     ap.add_argument("--scale", type=float, default=1.0, help="batched form: scale of every map's pattern count")
+    ap.add_argument("--train", type=int, default=200000, help="learned form: training patterns")
+    ap.add_argument("--batch", type=int, default=256, help="learned form: training batch")
+    ap.add_argument("--lr", type=float, default=1e-3, help="learned form: peak learning rate")
     return ap.parse_args()
 
 
@@ -445,6 +449,141 @@ def run_batched(args, px, torch, dev, rank, world, local, dist):
     ctx.close()
 
 
+# ----------------------------------------------------------- learned form
+def _generate(px, torch, ctx, master_d, geom, q, pcs, peak, gen, chunk=4096):
+    """Noisy patterns [P, n, n] on the device from orientations / PCs / peaks (input generation)."""
+    P = q.shape[0]
+    out = torch.empty((P, geom.height, geom.width), device=q.device)
+    for c0 in range(0, P, chunk):
+        c1 = min(P, c0 + chunk)
+        clean = px.xcf_project(ctx, master_d, q[c0:c1].contiguous(), geom, pcs=pcs[c0:c1].contiguous())
+        out[c0:c1] = _noisy_on_device(torch, clean, pcs[c0:c1], peak[c0:c1], gen)
+    return out
+
+
+# forward multiply-adds of the proposal network per pattern x 2: five 3 x 3
+# stride-2 convolutions (1-32-64-64-128-128 channels, outputs 64^2 .. 4^2) and two fc layers
+CNN_FORWARD_FLOPS = 2.0 * (sum(co * ci * 9 * s * s for ci, co, s in
+                               ((1, 32, 64), (32, 64, 32), (64, 64, 16), (64, 128, 8), (128, 128, 4)))
+                           + 256 * 128 + 48 * 256)
+
+
+def run_learned(args, px, torch, dev, rank, world, local, dist):
+    n_test = args.patterns or 100000
+    wl = synth.config_learned_128(seed=rank, n_train=args.train, n_test=n_test)
+    n, k = wl["n"], wl["k"]
+    geom = px.geometry(n, n, wl["pc"])
+    ctx = px.Context(max_iter=wl["max_iter"], tol_deg=1e-3)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    master_d, libq_d = d(wl["master"]), d(wl["lib_q"])
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(wl["noise_seed"])
+    # ---- training (setup, outside the timed region): one pass over the generated training set
+    net = px.xcf_net_create(ctx, k, d(synth.cnn_init_params(k, rank)))
+    trq, trpc, trpk = d(wl["train_q"]), d(wl["train_pcs"]), d(wl["train_peak"])
+    B, n_train = args.batch, len(wl["train_q"])
+    steps = max(1, n_train // B)
+    t0 = time.perf_counter()
+    losses = []
+    for i in range(steps):
+        sl = slice(i * B, (i + 1) * B)
+        imgs = _generate(px, torch, ctx, master_d, geom, trq[sl], trpc[sl], trpk[sl], gen)
+        loss, _, _ = px.xcf_net_loss_grad(ctx, net, imgs, trq[sl].contiguous(), geom)
+        lr = args.lr * 0.5 * (1.0 + np.cos(np.pi * i / steps))          # cosine schedule
+        px.xcf_net_adam(ctx, net, lr=float(lr))
+        if i % 50 == 0 or i == steps - 1:
+            losses.append(float(loss))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    # ---- test set, resident on the device
+    teq, tepc, tepk = d(wl["test_q"]), d(wl["test_pcs"]), d(wl["test_peak"])
+    pats = _generate(px, torch, ctx, master_d, geom, teq, tepc, tepk, gen)
+    lib = px.xcf_build_library(ctx, master_d, libq_d, geom)
+    # ---- fallback threshold from a calibration slice: full search + refinement peaks
+    ncal = min(2000, n_test)
+    cal = px.xcf_index_refine(ctx, lib, pats[:ncal].contiguous(), pcs=tepc[:ncal].contiguous())
+    good = cal["rpeak"][cal["best"] >= 0].float()
+    tau = float(torch.quantile(good, 0.02)) * 0.8 if good.numel() else 0.0
+    outs = (torch.empty((n_test, 4), dtype=torch.float64, device=dev), torch.empty(n_test, device=dev),
+            torch.empty(n_test, dtype=torch.int32, device=dev), torch.empty(n_test, dtype=torch.int32, device=dev))
+
+    def step():
+        px.xcf_index_learned(ctx, net, lib, pats, pcs=tepc, tau=tau, out=outs)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    px.xcf_profile_read(ctx, reset=True)
+    px.xcf_profile_enable(ctx, True)
+    if dist:
+        dist.barrier()
+    clk = clocks_start(local)
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = clocks_stop(clk)
+    elapsed_ms = e0.elapsed_time(e1)
+    px.xcf_profile_enable(ctx, False)
+    prof = px.xcf_profile_read(ctx, reset=True)
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    mis = px.xcf_disorientation(ctx, outs[0], teq)
+    fb = outs[3].double()
+    # ---- ablation: the plain full search + refinement on the same test set, and the raw proposals
+    e0.record()
+    full = px.xcf_index_refine(ctx, lib, pats, pcs=tepc)
+    e1.record()
+    torch.cuda.synchronize()
+    full_ms = e0.elapsed_time(e1)
+    mis_full = px.xcf_disorientation(ctx, full["quats"], teq)
+    prop = px.xcf_propose(ctx, net, pats[:ncal].contiguous(), geom)
+    best_prop = torch.stack([px.xcf_disorientation(ctx, prop[:, h].contiguous(), teq[:ncal].contiguous())
+                             for h in range(k)]).min(dim=0).values
+    value = n_test * args.steps * world / (elapsed_ms / 1e3)
+    pk = peaks_file()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = (pk or {}).get("sm_max_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
+    fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    net_ms, net_n = prof["net"]
+    net_flops = CNN_FORWARD_FLOPS * n_test * args.steps
+    roofline = {"bound": "alu", "achieved": net_flops / (net_ms / 1e3) / 1e12 if net_ms else None, "peak": fp32_peak,
+                "unit": "TFLOP/s", "kernel": "proposal network forward (k_gemm)", "traffic": None,
+                "stage_ms_per_step": {kk: v[0] / args.steps for kk, v in prof.items()}}
+    roofline["frac"] = roofline["achieved"] / fp32_peak if roofline["achieved"] else None
+    if rank == 0:
+        line = {"metric": "patterns indexed/s (learned proposals + correlation score + refinement, full-search fallback)",
+                "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl["name"], "form": "learned", "detector": n, "templates": lib.T, "heads": k,
+                           "train_patterns": n_train, "batch": B, "test_patterns": n_test, "tau": tau,
+                           "parallelism": f"replicas x{world}",
+                           "l2": _l2_note(pats.numel() * 4, lib.T * n * (n // 2 + 1) * 8, "library spectra")},
+                "training": {"seconds": t_train, "steps": steps, "loss_trace": losses},
+                "accuracy": {"mean_misorientation_deg": float(mis.mean()),
+                             "median_misorientation_deg": float(mis.median()),
+                             "frac_below_1deg": float((mis < 1.0).double().mean()),
+                             "fallback_fraction": float(fb.mean())},
+                "ablation": {"full_search_patterns_per_s": n_test / (full_ms / 1e3),
+                             "full_search_mean_misorientation_deg": float(mis_full.mean()),
+                             "full_search_frac_below_1deg": float((mis_full < 1.0).double().mean()),
+                             "best_proposal_median_deg": float(best_prop.median()),
+                             "best_proposal_frac_below_5deg": float((best_prop < 5.0).double().mean()),
+                             "speedup_vs_full_search": value / (n_test / (full_ms / 1e3))},
+                "gpu_launches": int(sum(v[1] for v in prof.values())), "clocks": clocks, "roofline": roofline,
+                "e2e": None, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+    lib.close()
+    net.close()
+    ctx.close()
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -462,8 +601,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    if args.form in ("precision", "batched"):
-        (run_precision if args.form == "precision" else run_batched)(args, px, torch, dev, rank, world, local, dist)
+    if args.form in ("precision", "batched", "learned"):
+        fn = {"precision": run_precision, "batched": run_batched, "learned": run_learned}[args.form]
+        fn(args, px, torch, dev, rank, world, local, dist)
         if dist:
             dist.destroy_process_group()
         return

@@ -1243,7 +1243,6 @@ namespace {
 struct MapLayout {
     std::vector<size_t> spec, idx;   // offsets (complex values / patterns) of each map's slices
     size_t spec_total = 0, idx_total = 0;
-    bool big = false;
 };
 
 MapLayout maps_layout(const xcf_map_desc *maps, int n) {
@@ -1254,7 +1253,6 @@ MapLayout maps_layout(const xcf_map_desc *maps, int n) {
         L.idx.push_back(L.idx_total);
         L.spec_total += (size_t)maps[m].P * N * (N / 2 + 1);
         L.idx_total += (size_t)maps[m].P;
-        if (N > 128) L.big = true;
     }
     return L;
 }
@@ -1269,6 +1267,13 @@ int tuned_pairs(xcf_ctx *ctx, int N, int T) {
 
 // work items, most expensive (largest detector) first so that the tail of
 // the persistent launch is made of short items
+// sides served by the persistent queue.  The queue kernel is shaped for the
+// 128 x 128 body (one CTA of 255 registers and 200 KB per SM); measured on
+// the batched workload, smaller sides ran 1.4-1.6x slower in that shape than
+// in their own kernels (six CTAs per SM) and 256 x 256 needs a cluster, so
+// those maps get their own launches in the same stream (and graph).
+bool queued_side(int N) { return N == 128; }
+
 std::vector<WorkItem> maps_items(xcf_ctx *ctx, const xcf_map_desc *maps, int n, int p_limit = -1,
                                  int only_map = -1, int pairs = 0) {
     std::vector<int> order(n);
@@ -1277,7 +1282,7 @@ std::vector<WorkItem> maps_items(xcf_ctx *ctx, const xcf_map_desc *maps, int n, 
                      [&](int a, int b) { return maps[a].lib->N > maps[b].lib->N; });
     std::vector<WorkItem> items;
     for (int m : order) {
-        if (only_map >= 0 && m != only_map) continue;
+        if ((only_map >= 0 && m != only_map) || !queued_side(maps[m].lib->N)) continue;
         const int T = maps[m].lib->T, npairs = (T + 1) / 2;
         int c = pairs > 0 ? pairs : tuned_pairs(ctx, maps[m].lib->N, T);
         if (c <= 0) c = npairs;
@@ -1311,12 +1316,7 @@ int maps_scratch(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout 
     d->items = reinterpret_cast<WorkItem *>(static_cast<char *>(mp) + ((sizeof(MapDev) * n + 255) & ~(size_t)255));
     d->counter = reinterpret_cast<int *>(static_cast<char *>(mp) + table);
     d->grid = ctx->num_sms;
-    d->work = nullptr;
-    if (L.big) {   // megakernel and the N = 256 peak kernel both draw on the work arrays
-        const int g2 = big_grid(ctx->num_sms, 1L << 30);
-        if ((rc = scratch_t(ctx, S_WORK, big_work_bytes(256, g2 > d->grid ? g2 : d->grid) / sizeof(float2), &d->work)))
-            return rc;
-    }
+    d->work = nullptr;   // the queue serves 128 x 128 maps only: no global work arrays
     return XCF_OK;
 }
 
@@ -1353,8 +1353,17 @@ int maps_search_finish(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapL
                        int n_items, cudaStream_t st) {
     XCF_CHECK(cudaMemsetAsync(d.keys, 0, sizeof(unsigned long long) * L.idx_total, st), "clear keys");
     XCF_CHECK(cudaMemsetAsync(d.counter, 0, sizeof(int), st), "clear queue");
-    XCF_LAUNCH(XCF_STAGE_SEARCH, st, launch_search_maps(d.maps, d.items, n_items, d.counter, d.work, d.grid, st),
-               "multi-map search");
+    if (n_items > 0)
+        XCF_LAUNCH(XCF_STAGE_SEARCH, st, launch_search_maps(d.maps, d.items, n_items, d.counter, d.work, d.grid, st),
+                   "multi-map search");
+    for (int m = 0; m < n; ++m) {   // the other sides: their own kernels
+        const xcf_library *lib = maps[m].lib;
+        if (queued_side(lib->N)) continue;
+        XCF_LAUNCH(XCF_STAGE_SEARCH, st,
+                   run_search(ctx, lib->N, search_spectra(lib), lib->T, d.spec + L.spec[m], d.degen + L.idx[m],
+                              maps[m].P, d.keys + L.idx[m], nullptr, ctx->num_sms, st),
+                   "search");
+    }
     for (int m = 0; m < n; ++m) {
         const xcf_library *lib = maps[m].lib;
         XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_keys_to_best(d.keys + L.idx[m], maps[m].P, maps[m].best, st),
@@ -1377,7 +1386,7 @@ int maps_autotune(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout
     int status = XCF_OK;
     for (int m = 0; m < n && status == XCF_OK; ++m) {
         const int N = maps[m].lib->N, T = maps[m].lib->T, npairs = (T + 1) / 2;
-        if (tuned_pairs(ctx, N, T) > 0) continue;
+        if (!queued_side(N) || tuned_pairs(ctx, N, T) > 0) continue;
         const int cands[3] = {npairs, npairs / 4 > 8 ? npairs / 4 : 8, npairs / 16 > 8 ? npairs / 16 : 8};
         int best_c = npairs;
         float best_t = 1e30f;
