@@ -8,14 +8,20 @@
 // library cheaply before the FP32 FFT cross-correlation rescores the best k.
 //
 // k_screen_tc: one CTA (128 threads) computes a 128 (patterns) x 256
-// (templates) tile of S.  K-slices of 64 are staged by cp.async into shared
-// memory in the canonical no-swizzle K-major layout (8 x 16-byte core
-// matrices), three stages deep; one thread issues tcgen05.mma (M = 128,
-// N = 256, K = 16) with the accumulator in tensor memory and commits each
-// stage to an mbarrier that releases the stage for reuse.  The epilogue reads
-// the accumulator with tcgen05.ld (each warp its 32 lanes = rows) and writes
-// S.  Every wait is bounded: on time-out the kernel records an error flag,
-// drains its copies and frees its tensor memory.
+// (templates) tile of S.  Warp 0 is the loader: one thread issues TMA
+// (cp.async.bulk.tensor) copies of 64-wide K-slices of both operands into a
+// four-stage ring, 128-byte swizzled, each stage completing an mbarrier by
+// transaction count.  Warp 1 is the tensor-core issuer: one thread waits for
+// a stage, issues four tcgen05.mma (M = 128, N = 256, K = 16, BF16 in, FP32
+// accumulated in 256 TMEM columns) and commits them to the stage's "empty"
+// mbarrier, which hands the stage back to the loader.  After the last commit
+// all four warps read the accumulator with tcgen05.ld (each warp its 32 TMEM
+// lanes = tile rows) and write S.  Tiles are ordered in groups of eight
+// pattern tiles, so that the CTAs resident at one time share the template
+// tiles they stream.  Every wait is bounded: on time-out the kernel records an
+// error flag, waits (bounded) for its copies in flight and frees its tensor
+// memory.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -23,38 +29,27 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 3, NT = 128;
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4, NT = 128, GROUP_M = 8;
 constexpr int A_BYTES = BM * BK * 2;              // 16 KB
 constexpr int B_BYTES = BN * BK * 2;              // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;    // 48 KB
-constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 64;
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 128;
 constexpr unsigned kSpinLimit = 1u << 26;         // bounded waits
 
-// byte offset of element (row, k) of a tile in the canonical K-major layout:
-// core matrix (row / 8, k / 8) of 8 rows x 16 bytes at ((row/8) * 8 + k/8) * 128
-__device__ __forceinline__ int kmajor_off(int row, int k) {
-    return (((row >> 3) * (BK / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
-}
-
-// shared-memory matrix descriptor: start address, leading byte offset (between
-// core matrices adjacent in K) = 128, stride byte offset (between 8-row
-// groups) = 1024, version bits 46-48 = 1, no swizzle
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           (1ull << 46);
+// shared-memory matrix descriptor of a K-major operand tile written by TMA
+// with 128-byte swizzling: start address, leading byte offset 16 (unused for
+// this layout), stride byte offset 1024 (between 8-row groups), version 1,
+// swizzle mode 2 = 128 B.  Stage bases are 1024-byte aligned, so advancing
+// the start by 32 bytes per K = 16 step keeps the swizzle phase.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
 }
 
 // instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major,
 // N = 256, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                             ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void cp_async16_zfill(uint32_t saddr, const void *g, int bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(g), "r"(bytes));
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;"); }
-template <int N_>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N_) : "memory"); }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
     for (unsigned spin = 0; spin < kSpinLimit; ++spin) {
@@ -68,27 +63,53 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
     }
     return false;
 }
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// 2-D tiled TMA load: box at (x = K element, y = row), completes `bar` by transaction bytes
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
 
 __global__ void __launch_bounds__(NT, 1)
-k_screen_tc(const __nv_bfloat16 *__restrict__ A, int P, const __nv_bfloat16 *__restrict__ B, int T, int K,
+k_screen_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int P, int T, int K,
             float *__restrict__ S, int *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // 1024-aligned stage base
     const uint32_t sbase0 = (uint32_t)__cvta_generic_to_shared(smem_raw);
-    const uint32_t sbase = (sbase0 + 1023u) & ~1023u;
-    const uint32_t bar_base = sbase + STAGES * STAGE_BYTES;      // STAGES mbarriers (8 B each)
-    const uint32_t tmem_slot = bar_base + 8 * STAGES;            // tcgen05.alloc writes here
+    const uint32_t sbase = (sbase0 + 1023u) & ~1023u;            // 1024-aligned stages (swizzle atoms)
+    const uint32_t full_bar = sbase + STAGES * STAGE_BYTES;       // STAGES mbarriers: stage loaded
+    const uint32_t empty_bar = full_bar + 8 * STAGES;             // STAGES mbarriers: stage consumed
+    const uint32_t done_bar = empty_bar + 8 * STAGES;             // accumulator complete
+    const uint32_t tmem_slot = done_bar + 8;                      // tcgen05.alloc writes here
     unsigned char *gen_base = smem_raw + (sbase - sbase0);
-    volatile uint32_t *tmem_slot_ptr = reinterpret_cast<volatile uint32_t *>(gen_base + STAGES * STAGE_BYTES + 8 * STAGES);
+    volatile uint32_t *tmem_slot_ptr =
+        reinterpret_cast<volatile uint32_t *>(gen_base + STAGES * STAGE_BYTES + 16 * STAGES + 8);
+    volatile int *flag = reinterpret_cast<volatile int *>(gen_base + STAGES * STAGE_BYTES + 16 * STAGES + 16);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int t0 = blockIdx.x * BN, p0 = blockIdx.y * BM;
+    // grouped tile order: GROUP_M pattern tiles per template-tile sweep
+    const int num_m = (P + BM - 1) / BM, num_n = (T + BN - 1) / BN;
+    const int id = blockIdx.x, per_group = GROUP_M * num_n;
+    const int first_m = (id / per_group) * GROUP_M;
+    const int gsize = min(num_m - first_m, GROUP_M);
+    const int m_tile = first_m + (id % per_group) % gsize, n_tile = (id % per_group) / gsize;
+    const int p0 = m_tile * BM, t0 = n_tile * BN;
     const int nk = K / BK;
 
     if (tid == 0) {
-        for (int s = 0; s < STAGES; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_base + 8 * s));
+        for (int s = 0; s < STAGES; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full_bar + 8 * s));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty_bar + 8 * s));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(done_bar));
         asm volatile("fence.mbarrier_init.release.cluster;");
+        *flag = 0;
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tmem_slot), "r"(BN));
@@ -99,42 +120,34 @@ k_screen_tc(const __nv_bfloat16 *__restrict__ A, int P, const __nv_bfloat16 *__r
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot_ptr;
 
-    auto load_stage = [&](int kb, int s) {
-        const uint32_t sa = sbase + s * STAGE_BYTES, sb = sa + A_BYTES;
-        const int k0 = kb * BK;
-#pragma unroll
-        for (int i = 0; i < (BM * BK / 8) / NT; ++i) {            // A: 8 chunks per thread
-            const int idx = i * NT + tid, row = idx >> 3, kc = idx & 7;
-            const int p = p0 + row;
-            const __nv_bfloat16 *g = A + (size_t)(p < P ? p : 0) * K + k0 + kc * 8;
-            cp_async16_zfill(sa + kmajor_off(row, kc * 8), g, p < P ? 16 : 0);
+    int issued = 0;   // loader: stages issued (for the drain on a time-out)
+    if (warp == 0 && lane == 0) {
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES && !mbar_wait(empty_bar + 8 * s, (uint32_t)((kb / STAGES - 1) & 1))) {
+                *flag = 1;
+                break;
+            }
+            if (*flag) break;
+            const uint32_t sa = sbase + s * STAGE_BYTES, sb = sa + A_BYTES;
+            mbar_expect_tx(full_bar + 8 * s, STAGE_BYTES);
+            tma_load_2d(sa, &mapA, kb * BK, p0, full_bar + 8 * s);
+            tma_load_2d(sb, &mapB, kb * BK, t0, full_bar + 8 * s);
+            issued = kb + 1;
         }
-#pragma unroll
-        for (int i = 0; i < (BN * BK / 8) / NT; ++i) {            // B: 16 chunks per thread
-            const int idx = i * NT + tid, row = idx >> 3, kc = idx & 7;
-            const int t = t0 + row;
-            const __nv_bfloat16 *g = B + (size_t)(t < T ? t : 0) * K + k0 + kc * 8;
-            cp_async16_zfill(sb + kmajor_off(row, kc * 8), g, t < T ? 16 : 0);
-        }
-    };
-
-    bool ok = true;
-    load_stage(0, 0);
-    cp_commit();
-    if (nk > 1) load_stage(1, 1);
-    cp_commit();
-    for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % STAGES;
-        cp_wait<1>();                                             // this thread's copies of stage s landed
-        asm volatile("fence.proxy.async.shared::cta;");           // visible to the tensor core
-        ok = __syncthreads_and(ok ? 1 : 0) != 0;                  // block-uniform: every thread leaves together
-        if (!ok) break;
-        if (tid == 0) {
+    } else if (warp == 1 && lane == 0) {
+        int kb = 0;
+        for (; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            if (!mbar_wait(full_bar + 8 * s, (uint32_t)((kb / STAGES) & 1)) || *flag) {
+                *flag = 1;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t sa = sbase + s * STAGE_BYTES, sb = sa + A_BYTES;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint64_t ad = smem_desc(sa + kk * 256), bd = smem_desc(sb + kk * 256);
+                const uint64_t ad = smem_desc_sw128(sa + kk * 32), bd = smem_desc_sw128(sb + kk * 32);
                 const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -142,23 +155,26 @@ k_screen_tc(const __nv_bfloat16 *__restrict__ A, int P, const __nv_bfloat16 *__r
                     "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                bar_base + 8 * s));
+                empty_bar + 8 * s));
         }
-        // refill the stage read by the previous k-block once its MMAs are done
-        if (kb + 2 < nk) {
-            const int s2 = (kb + 2) % STAGES;
-            if (kb >= 1) ok = mbar_wait(bar_base + 8 * s2, (uint32_t)(((kb - 1) / STAGES) & 1));
-            if (ok) load_stage(kb + 2, s2);
-        }
-        cp_commit();
+        // the done barrier fires when every MMA issued above has completed
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done_bar));
     }
-    // all MMAs complete once the last k-block's commit has arrived
-    if (ok) ok = mbar_wait(bar_base + 8 * ((nk - 1) % STAGES), (uint32_t)(((nk - 1) / STAGES) & 1));
-    cp_wait<0>();
+    __syncwarp();
+    bool ok = mbar_wait(done_bar, 0u);
+    if (!ok) *flag = 1;
     __syncthreads();
+    const bool good = *flag == 0;
+    if (!good && warp == 0 && lane == 0) {
+        // drain: every issued stage's copies must land before the shared memory is released
+        for (int kb = 0; kb < issued; ++kb) {
+            const int s = kb % STAGES;
+            if (kb + STAGES >= issued) mbar_wait(full_bar + 8 * s, (uint32_t)((kb / STAGES) & 1));
+        }
+        atomicExch(err, 1);
+    }
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const int ok_all = __syncthreads_and(ok ? 1 : 0);
-    if (ok_all) {
+    if (good) {
         const int row = warp * 32 + lane, p = p0 + row;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -182,8 +198,6 @@ k_screen_tc(const __nv_bfloat16 *__restrict__ A, int P, const __nv_bfloat16 *__r
                     if (t0 + c0 + j < T) dst[j] = __uint_as_float(v[j]);
             }
         }
-    } else if (tid == 0) {
-        atomicExch(err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -295,15 +309,50 @@ __global__ void k_to_bf16(const float *__restrict__ x, size_t n, __nv_bfloat16 *
 
 }  // namespace
 
+namespace {
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda)
+typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_fn() {
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+// rows x K BF16 matrix (row-major), boxes of box_rows x 64 (128 bytes, the swizzle span)
+bool make_map(CUtensorMap *m, const void *base, int rows, int K, int box_rows) {
+    EncodeTiled f = encode_fn();
+    if (!f) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return f(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
 cudaError_t launch_screen_tc(const void *A, int P, const void *B, int T, int K, float *S, int *err,
                              cudaStream_t st) {
     if (P <= 0 || T <= 0) return cudaSuccess;
-    if (K % BK) return cudaErrorInvalidValue;
+    // TMA: 16-byte aligned bases and row strides; K a multiple of the 64-element slice
+    if (K % BK || (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15))
+        return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, P, K, BM) || !make_map(&mb, B, T, K, BN)) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_screen_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    dim3 grid((T + BN - 1) / BN, (P + BM - 1) / BM);
-    k_screen_tc<<<grid, NT, SMEM_BYTES, st>>>(static_cast<const __nv_bfloat16 *>(A), P,
-                                              static_cast<const __nv_bfloat16 *>(B), T, K, S, err);
+    const long tiles = (long)((P + BM - 1) / BM) * ((T + BN - 1) / BN);
+    if (tiles > 0x7fffffffL) return cudaErrorInvalidValue;
+    k_screen_tc<<<(unsigned)tiles, NT, SMEM_BYTES, st>>>(ma, mb, P, T, K, S, err);
     return cudaGetLastError();
 }
 

@@ -423,12 +423,14 @@ def cnn_init_params(k: int = 8, seed: int = 0) -> np.ndarray:
     return np.concatenate(parts).astype(np.float32)
 
 
-def config_learned_128(seed: int = 0, n_train: int = 200000, n_test: int = 100000, step_deg: float = 5.35) -> dict:
+def config_learned_128(seed: int = 0, n_train: int = 200000, n_test: int = 100000, step_deg: float = 5.35,
+                       n_cal: int = 4000) -> dict:
     """Learned-form workload: the 128 x 128 map generator (BCC master 2 x 1024^2,
     PC (0.5, 0.5, 0.6) jittered by +-0.005) with orientations uniform over
     SO(3), Poisson peak drawn per pattern from U[50, 500]; n_train training
     and n_test test patterns; the ~4,000-orientation FZ library for the
-    fallback search; refinement to convergence (at most 10 iterations)."""
+    fallback search; refinement to convergence (at most 10 iterations); n_cal
+    separate calibration patterns for the fallback threshold."""
     rng = np.random.Generator(np.random.PCG64(seed + 11))
     lib_q = so3_grid_cubic_fz(step_deg)
     return dict(name=f"learned128_T{len(lib_q)}_train{n_train}_test{n_test}", n=128, pc=DEFAULT_PC,
@@ -436,4 +438,6 @@ def config_learned_128(seed: int = 0, n_train: int = 200000, n_test: int = 10000
                 train_q=random_quaternions(n_train, seed + 12), train_pcs=jittered_pcs(n_train, seed + 13),
                 train_peak=rng.uniform(50.0, 500.0, size=n_train),
                 test_q=random_quaternions(n_test, seed + 14), test_pcs=jittered_pcs(n_test, seed + 15),
-                test_peak=rng.uniform(50.0, 500.0, size=n_test), noise_seed=seed + 16, max_iter=10, k=8)
+                test_peak=rng.uniform(50.0, 500.0, size=n_test),
+                cal_q=random_quaternions(n_cal, seed + 17), cal_pcs=jittered_pcs(n_cal, seed + 18),
+                cal_peak=rng.uniform(50.0, 500.0, size=n_cal), noise_seed=seed + 16, max_iter=10, k=8)
