@@ -6,6 +6,7 @@
 // "Orientation and Pattern Centre Refinement" (Eq. 7, Fig. 6: shifts to
 // rotations about detector x / y, log-polar transform for z), second
 // "Equation 6" (disorientation with the 24 cubic operators).
+#include "big.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -174,33 +175,34 @@ __device__ __forceinline__ float parabola(float cm, float c0, float cp) {
 
 // ------------------------------------------------ angular correlation + Z
 // c(D) = sum_m sum_l a[m][l] b[m][(l + D) mod neta] / (|a| |b|) on mean-free
-// log-polar images (a = template, b = pattern); each thread accumulates 8
-// consecutive shifts over a slice of the radii, sliding along l in blocks of
-// 8 so that every loaded value feeds 8 fused multiply-adds.
-constexpr int kEtaThreads = 256;
-// radii held in shared memory at a time (two images: 2 R neta floats <= 96 KB)
-__host__ __device__ __forceinline__ int eta_chunk_rows(int nr, int neta) {
-    const int r = 12288 / neta;
-    return r < nr ? (r > 0 ? r : 1) : nr;
-}
+// log-polar images (a = template, b = pattern), by the correlation theorem:
+// each warp transforms radii m = warp, warp + 8, ... as one complex line
+// z = a_m + i b_m, splits A_m and B_m by Hermitian symmetry and accumulates
+// C[k] = sum_m conj(A_m[k]) B_m[k] (k <= neta/2) in registers; the warps'
+// sums are added in float64 and one inverse transform of the Hermitian C
+// gives c(D) for every shift.  neta log neta work per radius instead of neta^2.
+constexpr int kEtaThreads = 256, kEtaWarps = kEtaThreads / 32;
+
+template <int NETA>
 __global__ void __launch_bounds__(kEtaThreads) k_eta_update(const float *__restrict__ lpT,
                                                             const float *__restrict__ lpP, int nr,
-                                                            int neta, const double *__restrict__ q0s,
+                                                            const double *__restrict__ q0s,
                                                             const double *__restrict__ q1s,
                                                             double alpha, double tol_deg,
                                                             int *__restrict__ active,
                                                             int *__restrict__ iters,
                                                             double *__restrict__ q_out) {
+    constexpr int H = NETA / 2 + 1, KPL = (H + 31) / 32;   // spectrum bins, bins per lane
     const int p = blockIdx.x;
     if (!active[p]) return;
-    extern __shared__ float4 smem_raw[];
-    const int R = eta_chunk_rows(nr, neta);  // radii per shared-memory chunk
-    float *sa = reinterpret_cast<float *>(smem_raw);
-    float *sb = sa + R * neta;
-    float *cacc = sb + R * neta;            // [row groups][neta]
+    __shared__ float2 line[kEtaWarps][NETA];   // per-warp lines, then per-warp sums C (k < H)
+    __shared__ float2 tw[NETA / 2];
+    __shared__ float2 zc[NETA];
+    __shared__ float cfin[NETA];
     __shared__ double red[33];
-    const int tot = nr * neta, tid = threadIdx.x;
+    const int tot = nr * NETA, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const float *ga = lpT + (size_t)p * tot, *gb = lpP + (size_t)p * tot;
+    bigk::make_tw<NETA>(tw, -1);
     double s1 = 0, s2 = 0;
     for (int i = tid; i < tot; i += kEtaThreads) { s1 += ga[i]; s2 += gb[i]; }
     const float ma = (float)(block_sum_d(s1, red) / tot);
@@ -213,57 +215,56 @@ __global__ void __launch_bounds__(kEtaThreads) k_eta_update(const float *__restr
     const double na = block_sum_d(n1, red), nb = block_sum_d(n2, red);
     double nrm = sqrt(na * nb);
     if (!(nrm > 0)) nrm = 1.0;
-    const int G = neta / 8;                    // groups of 8 shifts
-    const int RG = kEtaThreads / G;            // row groups
-    const int gidx = tid % G, rg = tid / G;
-    float acc[8];
+    float2 acc[KPL];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = 0.f;
-    const int D0 = gidx * 8;
-    for (int m0 = 0; m0 < nr; m0 += R) {       // chunks of R radii (mean-free) through shared memory
-        const int rows = min(R, nr - m0);
-        for (int i = tid; i < rows * neta; i += kEtaThreads) {
-            sa[i] = ga[(size_t)m0 * neta + i] - ma;
-            sb[i] = gb[(size_t)m0 * neta + i] - mb;
-        }
-        __syncthreads();
-        if (rg < RG) {
-            for (int m = rg; m < rows; m += RG) {
-                const float *ar = sa + m * neta, *br = sb + m * neta;
-                for (int l = 0; l < neta; l += 8) {
-                    float av[8], bv[16];
+    for (int j = 0; j < KPL; ++j) acc[j] = make_float2(0.f, 0.f);
+    float2 *z = line[w];
+    for (int m = w; m < nr; m += kEtaWarps) {
+        for (int l = lane; l < NETA; l += 32)
+            z[l] = make_float2(ga[(size_t)m * NETA + l] - ma, gb[(size_t)m * NETA + l] - mb);
+        __syncwarp();
+        bigk::warp_fft_line<NETA>(z, 1, tw);   // forward: Z[k] = sum_l z[l] e^{-2 pi i k l / NETA}
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) av[j] = ar[l + j];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) bv[j] = br[(l + D0 + j) & (neta - 1)];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j)
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) acc[k] = fmaf(av[j], bv[j + k], acc[k]);
-                }
+        for (int j = 0; j < KPL; ++j) {
+            const int k = lane + 32 * j;
+            if (k < H) {
+                const float2 zk = z[k], zn = z[(NETA - k) & (NETA - 1)];
+                // A = (Z[k] + conj Z[-k]) / 2, B = (Z[k] - conj Z[-k]) / (2i); acc += conj(A) B
+                const float2 A = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+                const float2 B = make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x));
+                acc[j].x += A.x * B.x + A.y * B.y;
+                acc[j].y += A.x * B.y - A.y * B.x;
             }
         }
-        __syncthreads();
+        __syncwarp();
     }
-    if (rg < RG) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) cacc[rg * neta + D0 + k] = acc[k];
+    for (int j = 0; j < KPL; ++j) {
+        const int k = lane + 32 * j;
+        if (k < H) z[k] = acc[j];
     }
     __syncthreads();
-    // finish the sum over row groups in float64, then argmax
-    __shared__ float cfin[1024];
-    for (int D = tid; D < neta; D += kEtaThreads) {
-        double s = 0;
-        for (int g = 0; g < RG; ++g) s += cacc[g * neta + D];
-        cfin[D] = (float)(s / nrm);
+    // C[k] over the warps in float64, extended by C[NETA - k] = conj C[k]; inverse transform by warp 0
+    if (w == 0) {
+        for (int k = lane; k < H; k += 32) {
+            double cr = 0, ci = 0;
+            for (int v = 0; v < kEtaWarps; ++v) { cr += line[v][k].x; ci += line[v][k].y; }
+            zc[k] = make_float2((float)cr, (float)ci);
+            if (k > 0 && k < NETA / 2) zc[NETA - k] = make_float2((float)cr, (float)-ci);
+        }
+        __syncwarp();
+        for (int k = lane; k < NETA / 2; k += 32) tw[k].y = -tw[k].y;   // inverse twiddles
+        __syncwarp();
+        bigk::warp_fft_line<NETA>(zc, 1, tw);
+        for (int d = lane; d < NETA; d += 32) cfin[d] = (float)((double)zc[d].x / (NETA * nrm));
     }
     __syncthreads();
     if (tid == 0) {
         int best = 0;
-        for (int D = 1; D < neta; ++D) if (cfin[D] > cfin[best]) best = D;
-        const float off = parabola(cfin[(best + neta - 1) % neta], cfin[best], cfin[(best + 1) % neta]);
-        const double deta = (double)(best < neta / 2 ? best : best - neta) + off;
-        const double tz = 2.0 * XCF_PI * deta / neta;
+        for (int D = 1; D < NETA; ++D) if (cfin[D] > cfin[best]) best = D;
+        const float off = parabola(cfin[(best + NETA - 1) % NETA], cfin[best], cfin[(best + 1) % NETA]);
+        const double deta = (double)(best < NETA / 2 ? best : best - NETA) + off;
+        const double tz = 2.0 * XCF_PI * deta / NETA;
         double s, c;
         sincos(0.5 * tz, &s, &c);
         const Q Rz = {c, 0.0, 0.0, s};
@@ -348,7 +349,8 @@ cudaError_t launch_project(const float *master, int M, const double *quats, cons
     const size_t npx = (size_t)a.nx * a.ny;
     for (int p0 = 0; p0 < P; p0 += 65535) {          // grid.y limit
         const int np = P - p0 < 65535 ? P - p0 : 65535;
-        dim3 grid((unsigned)((npx + 255) / 256), np);
+        // 16 pixels per thread: the per-block float64 frame set-up is amortised over 4096 pixels
+        dim3 grid((unsigned)((npx + 4095) / 4096), np);
         k_project<<<grid, 256, 0, st>>>(master, M, quats + 4 * (size_t)p0, pcs ? pcs + 3 * (size_t)p0 : nullptr,
                                         active ? active + p0 : nullptr, a, out + npx * p0);
         cudaError_t e = cudaGetLastError();
@@ -383,15 +385,19 @@ cudaError_t launch_eta_update(const float *lpT, const float *lpP, int nr, int ne
                               const double *q1, double alpha, double tol_deg, int *active,
                               int *iters, double *q_out, int P, cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
-    // requirements of the blocked correlation: neta a power of two, 8 <= neta <= 1024
-    if (neta < 8 || neta > 1024 || (neta & (neta - 1))) return cudaErrorInvalidValue;
-    const int G = neta / 8;
-    const int RG = G <= kEtaThreads ? kEtaThreads / G : 0;
-    if (RG == 0) return cudaErrorInvalidValue;
-    const size_t sm = sizeof(float) * ((size_t)2 * eta_chunk_rows(nr, neta) * neta + (size_t)RG * neta);
-    cudaError_t e = cudaFuncSetAttribute(k_eta_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_eta_update<<<P, kEtaThreads, sm, st>>>(lpT, lpP, nr, neta, q0, q1, alpha, tol_deg, active, iters, q_out);
+#define XCF_ETA_CASE(NE)                                                                                     \
+    case NE:                                                                                                 \
+        k_eta_update<NE><<<P, kEtaThreads, 0, st>>>(lpT, lpP, nr, q0, q1, alpha, tol_deg, active, iters, q_out); \
+        break;
+    switch (neta) {
+        XCF_ETA_CASE(32)
+        XCF_ETA_CASE(64)
+        XCF_ETA_CASE(128)
+        XCF_ETA_CASE(256)
+        XCF_ETA_CASE(512)
+        default: return cudaErrorInvalidValue;   // neta = 2N for N = 16 .. 256
+    }
+#undef XCF_ETA_CASE
     return cudaGetLastError();
 }
 
