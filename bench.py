@@ -251,12 +251,13 @@ def run_precision(args, px, torch, dev, rank, world, local, dist):
             torch.empty(P, dtype=torch.int32, device=dev))
     res = {}
 
+    best_d = torch.empty(P, dtype=torch.int32, device=dev)
+
     def step():
         lib = px.xcf.xcf_build_library_ex(ctx, libq_d, geom, master=master_d, flags=px.xcf.XCF_LIB_SCREEN)
-        cand, _ = px.xcf.xcf_screen_topk(ctx, lib, pats_d, k)
-        best, _, _ = px.xcf.xcf_rescore(ctx, lib, pats_d, cand)
-        px.xcf.xcf_refine_best(ctx, lib, pats_d, best, pcs=pcs_d, out=outq)
-        res["best"] = best
+        # screen top-k, FP32 rescore and refinement with one pre-processing of the patterns
+        px.xcf_index_precision(ctx, lib, pats_d, pcs=pcs_d, k=k, out=(best_d, outq[0], outq[1], outq[2]))
+        res["best"] = best_d
         lib.close()
 
     for _ in range(args.warmup):

@@ -214,6 +214,18 @@ int xcf_screen_topk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns,
 int xcf_rescore(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, const int32_t *cand,
                 int32_t k, int32_t *best, float *peak, float *shift, void *stream);
 
+/* Precision form in one call: per chunk of patterns ONE pre-processing (half
+ * spectra and filtered spatial images) serves the BF16 tensor-core screen
+ * (top-k by zero-shift score, as xcf_screen_topk), the FP32 XCF rescore of
+ * the k candidates (best [P], as xcf_rescore) and the refinement seeded by
+ * the best candidate's library orientation (quats [P, 4], peak [P], iters [P],
+ * as xcf_refine_best).  The outputs equal the three calls in sequence.  The
+ * library needs XCF_LIB_SCREEN and its master pattern; 1 <= k <= 64.  Waits
+ * for the device at the end (reports XCF_ERR_TIMEOUT from the screen). */
+int xcf_index_precision(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P,
+                        const double *pcs, int32_t k, int32_t *best, double *quats, float *peak, int32_t *iters,
+                        void *stream);
+
 /* Refinement seeded by library templates: seeds = library orientations of
  * best [P] (identity where best < 0), then xcf_refine. */
 int xcf_refine_best(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, const int32_t *best,

@@ -256,7 +256,7 @@ int index_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int
 
 int refine_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int P,
                  const double *seeds, const double *pcs, double *quats, float *peak, int *iters,
-                 cudaStream_t st, const int *select = nullptr) {
+                 cudaStream_t st, const int *select = nullptr, bool patterns_ready = false) {
     const xcf_geometry *g = &lib->geom;
     Crop c;
     crop_of(g, 256, &c);
@@ -281,7 +281,8 @@ int refine_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, in
     const PrepArgs pa = prep_args(g, c, r), ps = prep_args_square(c, r);
     const ProjArgs pj = proj_args_cropped(g, c);
     const double alpha = alpha_of(g);
-    XCF_LAUNCH(XCF_STAGE_PREP, st, run_prep(ctx,patterns, P, pa, sp, yp, degen, nullptr, st), "prep patterns");
+    if (!patterns_ready)   // else sp, yp, degen already hold this chunk's patterns
+        XCF_LAUNCH(XCF_STAGE_PREP, st, run_prep(ctx,patterns, P, pa, sp, yp, degen, nullptr, st), "prep patterns");
     XCF_LAUNCH(XCF_STAGE_LOGPOLAR, st,
                launch_logpolar(yp, nullptr, P, n, r.nr, r.neta, (float)r.rmin, (float)r.rmax, lpp, st),
                "logpolar patterns");
@@ -960,6 +961,74 @@ int xcf_rescore(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int
                                  shift + 2 * (size_t)p0, st),
                    "pair_peak");
     }
+    return XCF_OK;
+}
+
+int xcf_index_precision(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P,
+                        const double *pcs, int32_t k, int32_t *best, double *quats, float *peak, int32_t *iters,
+                        void *stream) {
+    int rc = check_lib(ctx, lib);
+    if (rc) return rc;
+    if (P == 0) return XCF_OK;
+    if (!patterns || !best || !quats || !peak || !iters || P < 0 || k < 1 || k > 64)
+        return fail(ctx, XCF_ERR_ARG, "xcf_index_precision: bad argument (1 <= k <= 64)");
+    if (!lib->bf16) return fail(ctx, XCF_ERR_ARG, "xcf_index_precision: library built without XCF_LIB_SCREEN");
+    if (!lib->master) return fail(ctx, XCF_ERR_ARG, "xcf_index_precision: library has no master pattern");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const xcf_geometry *g = &lib->geom;
+    Crop c;
+    crop_of(g, 256, &c);
+    const Resolved r = resolve(ctx->opt, c.n);
+    const size_t nn = (size_t)c.n * c.n, H = (size_t)c.n * (c.n / 2 + 1), img = (size_t)g->width * g->height;
+    if ((size_t)lib->T * 4 > 200 * 1024)
+        return fail(ctx, XCF_ERR_SIZE, "xcf_index_precision: more than 51,200 templates");
+    const int chunk = screen_chunk(c.n, lib->T);
+    int *err;
+    if ((rc = scratch_t(ctx, S_ERR, 1, &err))) return rc;
+    XCF_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st), "clear status");
+    for (int p0 = 0; p0 < P; p0 += chunk) {
+        const int np = P - p0 < chunk ? P - p0 : chunk;
+        const float *pat = patterns + img * p0;
+        float2 *spec;
+        float *spat, *S, *score;
+        int *degen, *cand;
+        unsigned long long *keys;
+        double *seeds;
+        void *a;
+        if ((rc = scratch_t(ctx, S_SPEC_P, H * np, &spec)) || (rc = scratch_t(ctx, S_SPATIAL_P, nn * np, &spat)) ||
+            (rc = scratch_t(ctx, S_DEGEN, np, &degen)) || (rc = scratch(ctx, S_BF16_P, 2 * nn * np, &a)) ||
+            (rc = scratch_t(ctx, S_SCORE, (size_t)np * lib->T, &S)) || (rc = scratch_t(ctx, S_KEYS, np, &keys)) ||
+            (rc = scratch_t(ctx, S_CAND, (size_t)np * k, &cand)) ||
+            (rc = scratch_t(ctx, S_CANDSC, (size_t)np * k, &score)) ||
+            (rc = scratch_t(ctx, S_SEEDS, (size_t)np * 4, &seeds)))
+            return rc;
+        // one pre-processing of the patterns serves the screen, the rescore and the refinement
+        XCF_LAUNCH(XCF_STAGE_PREP, st, run_prep(ctx, pat, np, prep_args(g, c, r), spec, spat, degen, nullptr, st),
+                   "prep");
+        XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_to_bf16(spat, nn * np, a, st), "bf16");
+        XCF_LAUNCH(XCF_STAGE_SCREEN, st, launch_screen_tc(a, np, lib->bf16, lib->T, (int)nn, S, err, st), "screen");
+        XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_topk_rows(S, np, lib->T, k, cand, score, st), "topk");
+        XCF_CHECK(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * np, st), "memset keys");
+        if (c.n <= 128) {
+            XCF_LAUNCH(XCF_STAGE_SEARCH, st,
+                       launch_search_list(c.n, lib->spectra, cand, k, spec, degen, np, keys, nullptr, ctx->num_sms,
+                                          st),
+                       "rescore");
+        } else {
+            XCF_LAUNCH(XCF_STAGE_SEARCH, st,
+                       launch_search_c256(lib->spectra, 0, spec, degen, np, keys, nullptr, cand, k, st), "rescore");
+        }
+        XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_keys_to_best(keys, np, best + p0, st), "keys_to_best");
+        XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_gather_seeds(lib->quats, best + p0, np, seeds, st), "seeds");
+        if ((rc = refine_chunk(ctx, lib, pat, np, seeds, pcs ? pcs + 3 * (size_t)p0 : nullptr, quats + 4 * (size_t)p0,
+                               peak + p0, iters + p0, st, nullptr, true)))
+            return rc;
+    }
+    int h_err = 0;
+    XCF_CHECK(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+    XCF_CHECK(cudaStreamSynchronize(st), "xcf_index_precision");
+    if (h_err) return fail(ctx, XCF_ERR_TIMEOUT, "xcf_index_precision: a tensor-core pipeline wait timed out");
     return XCF_OK;
 }
 

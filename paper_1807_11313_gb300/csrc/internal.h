@@ -44,6 +44,8 @@ enum Slot {
     S_BESTPEAK,     // best proposal peak [P]
     S_MASK,         // search mask of the fallback pass
     S_FBCOUNT,      // number of fallback patterns (device int)
+    S_CAND,         // screen candidates of a chunk [P, k]
+    S_CANDSC,       // their screen scores
     S_COUNT
 };
 

@@ -82,6 +82,7 @@ _SIGS = {
     "xcf_screen_topk": ([_P, _P, _P, _I32, _I32, _P, _P, _P], C.c_int),
     "xcf_rescore": ([_P, _P, _P, _I32, _P, _I32, _P, _P, _P, _P], C.c_int),
     "xcf_refine_best": ([_P, _P, _P, _I32, _P, _P, _P, _P, _P, _P], C.c_int),
+    "xcf_index_precision": ([_P, _P, _P, _I32, _P, _I32, _P, _P, _P, _P, _P], C.c_int),
     "xcf_index_noalloc": ([_P, _P, _P, _I32, _P, _P, _P, _P], C.c_int),
     "xcf_noalloc_max_patterns": ([_I32], C.c_int),
     "xcf_index_maps": ([_P, _P, _I32, _I32, _P], C.c_int),
@@ -550,4 +551,19 @@ def xcf_index_learned(ctx: Context, net: Net, lib: Library, patterns, pcs=None, 
                                     _ptr(pcs, torch.float64, "pcs", True), float(tau), _ptr(q, torch.float64, "quats"),
                                     _ptr(pk, torch.float32, "peak"), _ptr(it, torch.int32, "iters"),
                                     _ptr(fb, torch.int32, "fallback"), _stream()), ctx.handle)
+    return out
+
+
+def xcf_index_precision(ctx: Context, lib: Library, patterns, pcs=None, k: int = 32, out=None):
+    """Screen top-k + FP32 rescore + refinement with one pre-processing of the
+    patterns.  -> (best [P], quats [P, 4], peak [P], iters [P])"""
+    P, d = patterns.shape[0], patterns.device
+    if out is None:
+        out = (torch.empty(P, dtype=torch.int32, device=d), torch.empty((P, 4), dtype=torch.float64, device=d),
+               torch.empty(P, dtype=torch.float32, device=d), torch.empty(P, dtype=torch.int32, device=d))
+    b, q, pk, it = out
+    _check(load().xcf_index_precision(ctx.handle, lib.handle, _ptr(patterns, torch.float32, "patterns"), P,
+                                      _ptr(pcs, torch.float64, "pcs", True), int(k), _ptr(b, torch.int32, "best"),
+                                      _ptr(q, torch.float64, "quats"), _ptr(pk, torch.float32, "peak"),
+                                      _ptr(it, torch.int32, "iters"), _stream()), ctx.handle)
     return out

@@ -167,3 +167,28 @@ def test_precision_form_end_to_end(px, orc):
     assert mis.mean() <= 0.5, mis.mean()
     lib.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("n,P,k", [(128, 40, 16), (256, 9, 8)])
+def test_fused_precision_equals_the_three_calls(px, n, P, k):
+    """xcf_index_precision (one pre-processing per chunk) returns exactly what
+    screen_topk -> rescore -> refine_best return, including degenerate input."""
+    master = synth.master_pattern("bcc", 512)
+    lq = synth.so3_grid_cubic_fz(12.0)
+    truth = synth.random_quaternions(P, 31 + n)
+    pcs = synth.jittered_pcs(P, 32)
+    ctx = px.Context(max_iter=3)
+    g = px.geometry(n, n, PC0)
+    lib = px.xcf.xcf_build_library_ex(ctx, dev(lq), g, master=dev(master), flags=px.xcf.XCF_LIB_SCREEN)
+    pats = px.xcf_project(ctx, dev(master), dev(truth), g, pcs=dev(pcs)) * 90 + 15
+    pats[3] = 1.0                                            # degenerate
+    pats = pats.contiguous()
+    b, q, pk, it = px.xcf_index_precision(ctx, lib, pats, pcs=dev(pcs), k=k)
+    cand, _ = px.xcf.xcf_screen_topk(ctx, lib, pats, k)
+    best, _, _ = px.xcf.xcf_rescore(ctx, lib, pats, cand)
+    q2, pk2, it2 = px.xcf.xcf_refine_best(ctx, lib, pats, best, pcs=dev(pcs))
+    torch.cuda.synchronize()
+    assert torch.equal(b, best) and int(b[3]) == -1
+    assert torch.equal(q, q2) and torch.equal(pk, pk2) and torch.equal(it, it2)
+    lib.close()
+    ctx.close()
