@@ -30,7 +30,8 @@ constexpr int N = 256, HW = N / 2 + 1, NC = 4, NT = 256;
 constexpr int ROWS = N / NC;                      // rows (and columns) per CTA
 constexpr size_t ZC_F2 = (size_t)ROWS * N;        // 128 KB of row-transformed data
 constexpr size_t SCR_F2 = (NT / 16) * 256;        // one 16 x 16 transpose buffer per group
-constexpr size_t SMEM_BYTES = (ZC_F2 + SCR_F2) * sizeof(float2) + 64 * sizeof(float);
+constexpr size_t PSM_F2 = (size_t)ROWS * HW;                      // the pattern's rows of this CTA
+constexpr size_t SMEM_BYTES = (ZC_F2 + SCR_F2 + PSM_F2) * sizeof(float2) + 64 * sizeof(float);
 
 __device__ __forceinline__ uint32_t cluster_rank() {
     uint32_t r;
@@ -39,6 +40,12 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 }
 __device__ __forceinline__ void cluster_barrier() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_arrive() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 __device__ __forceinline__ uint32_t map_to_rank(uint32_t local, uint32_t rank) {
     uint32_t r;
@@ -123,6 +130,44 @@ __device__ __forceinline__ void rows_phase(float2 *Zc, const float2 *__restrict_
     }
 }
 
+// the search's row phase: as rows_phase with the pattern's rows in shared
+// memory (Psm[slot][129], the CTA's 64 rows) and the templates from global
+// memory; when `pending`, the previous pair's column-phase barrier is
+// completed just before the first store into Zc (its wait overlaps the first
+// row's loads and transform)
+__device__ __forceinline__ void rows_phase_sp(float2 *Zc, const float2 *__restrict__ s1,
+                                              const float2 *__restrict__ s2, const float2 *Psm,
+                                              const float2 (&tw)[16], float2 *scr, int c, int g, int t,
+                                              bool &pending) {
+#pragma unroll 1
+    for (int r = 0; r < 4; ++r) {
+        const int j = g + 16 * (r >> 1), b = 32 * c + j;
+        const int u0 = b, u1 = b == 0 ? 128 : N - b;
+        const int u = (r & 1) ? u1 : u0;
+        const int pu = (N - u) & (N - 1);
+        const int su = 2 * j + (r & 1), spu = b == 0 ? su : (su ^ 1);   // slots of u and of -u
+        float2 a[16];
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) {
+            const int v = 16 * n1 + t;
+            const bool direct = v <= 128;
+            const int col = direct ? v : N - v;
+            const int k = (direct ? u : pu) * HW + col;   // Hermitian half: X(u, v) = conj(X(-u, 256 - v))
+            const float2 ps = Psm[(direct ? su : spu) * HW + col];
+            const float2 x1 = c_mulcj(__ldg(s1 + k), ps), x2 = c_mulcj(__ldg(s2 + k), ps);
+            a[n1] = direct ? make_float2(x1.x - x2.y, x1.y + x2.x) : make_float2(x1.x + x2.y, -x1.y + x2.x);
+        }
+        line_ifft(a, tw, scr, t);
+        if (r == 0 && pending) {   // every CTA is done reading this CTA's Zc
+            cluster_wait();
+            pending = false;
+        }
+        const int slot = 2 * j + (r & 1);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) Zc[zc_index(slot, t + 16 * cx_bitrev(q, 4))] = a[q];
+    }
+}
+
 __device__ __forceinline__ float warp_max(float v) {
     for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
@@ -136,12 +181,14 @@ k_search_c256(const float2 *__restrict__ St, int T, const float2 *__restrict__ S
     extern __shared__ float4 smem_raw[];
     float2 *Zc = reinterpret_cast<float2 *>(smem_raw);
     float2 *scr_all = Zc + ZC_F2;
-    float *red = reinterpret_cast<float *>(scr_all + SCR_F2);   // [0..15] warp maxima, [32..33] CTA maxima
+    float2 *Psm = scr_all + SCR_F2;
+    float *red = reinterpret_cast<float *>(Psm + PSM_F2);   // [0..15] warp maxima, [32..33] CTA maxima
     const int tid = threadIdx.x, t = tid & 15, g = tid >> 4, warp = tid >> 5, lane = tid & 31;
     const int c = (int)cluster_rank();
     const int cid = blockIdx.x / NC, ncl = gridDim.x / NC;
     float2 *scr = scr_all + g * 256;
     const int n = cand ? kc : T;
+    bool pending = false;   // a column-phase barrier arrived on but not yet waited for
     const int npairs = (n + 1) / 2;
 
     float2 tw[16];
@@ -169,6 +216,13 @@ k_search_c256(const float2 *__restrict__ St, int T, const float2 *__restrict__ S
         const int pb = ch * ppc, pe = min(npairs, pb + ppc);
         if (degen[p]) continue;                       // uniform over the cluster
         const float2 *sp = Sp + (size_t)p * N * HW;
+        __syncthreads();                               // this CTA's reads of the previous pattern are done
+        for (int i = tid; i < ROWS * HW; i += NT) {    // the pattern's rows of this CTA, by slot
+            const int slot = i / HW, col = i - slot * HW, j = slot >> 1, b = 32 * c + j;
+            const int u = (slot & 1) ? (b == 0 ? 128 : N - b) : b;
+            Psm[i] = __ldg(sp + (size_t)u * HW + col);
+        }
+        __syncthreads();
         float best_v = -INFINITY;
         int best_t = -1;
         for (int pi = pb; pi < pe; ++pi) {
@@ -176,7 +230,7 @@ k_search_c256(const float2 *__restrict__ St, int T, const float2 *__restrict__ S
             const int t1 = cand ? cand[(size_t)p * kc + j1] : j1;
             const int t2 = cand ? cand[(size_t)p * kc + j2] : j2;
             const float2 *s1 = St + (size_t)max(t1, 0) * N * HW, *s2 = St + (size_t)max(t2, 0) * N * HW;
-            rows_phase(Zc, s1, sp, 1.f, s2, sp, 1.f, tw, scr, c, g, t);
+            rows_phase_sp(Zc, s1, s2, Psm, tw, scr, c, g, t, pending);
             cluster_barrier();
             // ---- columns x = 64 c + 4 g + q: gather over the cluster, transform, maxima
             float m1 = -INFINITY, m2 = -INFINITY;
@@ -216,7 +270,12 @@ k_search_c256(const float2 *__restrict__ St, int T, const float2 *__restrict__ S
             // per-CTA partial maxima: the key of the pattern is the max over CTAs
             if (t1 >= 0 && (m1 > best_v || (m1 == best_v && t1 < best_t))) { best_v = m1; best_t = t1; }
             if (j2 != j1 && t2 >= 0 && (m2 > best_v || (m2 == best_v && t2 < best_t))) { best_v = m2; best_t = t2; }
-            cluster_barrier();                        // every column read done; red[32..33] of all CTAs final
+            if (peaks_all) {
+                cluster_barrier();                    // every column read done; red[32..33] of all CTAs final
+            } else {
+                cluster_arrive();                     // completed before the next pair's first Zc store
+                pending = true;
+            }
             if (peaks_all && c == 0 && tid == 0) {   // the surfaces' maxima over the four CTAs
                 float a1 = m1, a2 = m2;
                 for (int o = 1; o < NC; ++o) {
@@ -230,6 +289,7 @@ k_search_c256(const float2 *__restrict__ St, int T, const float2 *__restrict__ S
         }
         if (tid == 0 && best_t >= 0) atomicMax(keys + p, pack_key(best_v, best_t));
     }
+    if (pending) cluster_wait();
     cluster_barrier();   // no CTA leaves while another may still read its shared memory
 }
 
