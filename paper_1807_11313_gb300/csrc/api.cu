@@ -1446,7 +1446,11 @@ int maps_search_finish(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapL
 }
 
 // time candidate work granularities on the first patterns of each untuned
-// (side, library size) and keep the fastest (patterns already pre-processed)
+// (side, library size) and keep the fastest (patterns already pre-processed).
+// The sample spans several waves of the persistent grid: finer items balance
+// a short tail but break the library-order L2 reuse of a full-length sweep,
+// and one wave alone overstates the first and hides the second.
+constexpr int kTuneWaves = 8;
 int maps_autotune(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout &L, const MapsDev &d,
                   cudaStream_t st) {
     cudaEvent_t e0, e1;
@@ -1461,7 +1465,7 @@ int maps_autotune(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout
         float best_t = 1e30f;
         for (int ci = 0; ci < 3 && status == XCF_OK; ++ci) {
             if (ci > 0 && cands[ci] >= cands[ci - 1]) continue;
-            std::vector<WorkItem> it = maps_items(ctx, maps, n, ctx->num_sms, m, cands[ci]);
+            std::vector<WorkItem> it = maps_items(ctx, maps, n, kTuneWaves * ctx->num_sms, m, cands[ci]);
             if ((status = maps_table_upload(ctx, maps, n, L, d, it, st))) break;
             cudaMemsetAsync(d.keys, 0, sizeof(unsigned long long) * L.idx_total, st);
             cudaMemsetAsync(d.counter, 0, sizeof(int), st);
@@ -1472,7 +1476,7 @@ int maps_autotune(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout
             if (e != cudaSuccess) { status = cuda_fail(ctx, e, "autotune"); break; }
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            const int pats = ctx->num_sms < maps[m].P ? ctx->num_sms : maps[m].P;
+            const int pats = kTuneWaves * ctx->num_sms < maps[m].P ? kTuneWaves * ctx->num_sms : maps[m].P;
             const float per = ms / (pats > 0 ? pats : 1);
             if (per < best_t) { best_t = per; best_c = cands[ci]; }
         }
@@ -1525,7 +1529,7 @@ int xcf_index_maps(xcf_ctx *ctx, const xcf_map_desc *maps, int32_t n_maps, int32
     std::vector<WorkItem> items = maps_items(ctx, maps, n_maps);
     size_t max_items = items.size();
     for (int m = 0; m < n_maps; ++m)   // the largest trial list of the autotuner
-        max_items = std::max(max_items, maps_items(ctx, maps, n_maps, ctx->num_sms, m, 8).size());
+        max_items = std::max(max_items, maps_items(ctx, maps, n_maps, kTuneWaves * ctx->num_sms, m, 8).size());
     if ((rc = maps_scratch(ctx, maps, n_maps, L, max_items, &d))) return rc;
     if ((rc = maps_prep(ctx, maps, n_maps, L, d, caller))) return rc;
     if ((rc = maps_autotune(ctx, maps, n_maps, L, d, caller))) return rc;

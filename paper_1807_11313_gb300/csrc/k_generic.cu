@@ -1,7 +1,8 @@
 // Pre-processing, the all-sides search kernel and the single-surface peak
-// kernel for N in {16, 32, 64, 128}: each CTA holds one N x N complex array in
-// shared memory (rows padded to N + 1) and transforms it with a radix-2 FFT
-// whose butterflies are spread over the lanes of a warp.
+// kernel for N in {16, 32, 64, 128}.  The search and peak kernels hold one
+// N x N complex array in shared memory (rows padded to N + 1) and transform it
+// with a radix-2 FFT whose butterflies are spread over the lanes of a warp;
+// the pre-processing transforms real images at half that work (below).
 //
 // Paper: FFT section (Eq. 4 transform, filtering, windowing, normalisation by
 // the autocorrelations), Eqs. 3 and 6 (correlation surface), peak up-sampling.
@@ -14,64 +15,149 @@ namespace {
 using namespace gen;
 
 // --------------------------------------------------------------------------
-// pre-processing: crop, standardise, window, FFT, band-pass, unit norm
+// pre-processing of real images with half the transform work: image rows
+// 2r and 2r+1 form one complex line (rows transformed as N/2 complex lines,
+// then split by Hermitian symmetry into R[y][0..N/2]); the columns of R are
+// transformed as their even- and odd-row halves (N/2-point transforms) joined
+// by one radix-2 stage.  Bins 0 and N/2 of every row are real, so they share
+// one complex slot per row pair.  The N/2 x (N+1) complex array (66 KB at
+// N = 128) lets three CTAs share an SM.  The spatial output runs the same
+// steps backwards.
+// layout of buf after the row split, row pr (image rows 2pr, 2pr+1):
+//   [0]        (Ra[0], Ra[N/2])   real bins of row 2pr
+//   [1, N/2)   Ra[v]
+//   [N/2]      (Rb[0], Rb[N/2])   real bins of row 2pr+1
+//   (N/2, N)   Rb[v - N/2]
+// after the column transforms, S[u][v] (1 <= v < N/2) is at buf[u][v] for
+// u < N/2 and at buf[u - N/2][N/2 + v] above; columns 0 and N/2 go to c0, cH.
 // --------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(kThreads) k_prep(const float *__restrict__ img, PrepArgs a,
-                                                   float2 *__restrict__ spec,
-                                                   float *__restrict__ spatial,
-                                                   int *__restrict__ degen,
-                                                   const int *__restrict__ active) {
-    constexpr int LD = N + 1, HW = N / 2 + 1;
+constexpr size_t smem_prep_real() {
+    return sizeof(float2) * ((size_t)(N / 2) * (N + 1) + N + N / 2 + 2 * N);
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_prep_real(const float *__restrict__ img, PrepArgs a,
+                                                        float2 *__restrict__ spec, float *__restrict__ spatial,
+                                                        int *__restrict__ degen, const int *__restrict__ active) {
+    constexpr int H = N / 2, LD = N + 1, HW = N / 2 + 1;
     if (active && !active[blockIdx.x]) return;
     extern __shared__ float4 smem_raw[];
-    float2 *buf = reinterpret_cast<float2 *>(smem_raw);
-    float2 *twf = buf + N * LD;
-    float2 *twi = twf + N / 2;
+    float2 *buf = reinterpret_cast<float2 *>(smem_raw);   // [H][LD]
+    float2 *twN = buf + H * LD;                            // e^{-2 pi i k / N},   k < N/2
+    float2 *twNi = twN + N / 2;                            // e^{+2 pi i k / N}
+    float2 *twH = twNi + N / 2;                            // e^{-2 pi i k / (N/2)}, k < N/4
+    float2 *twHi = twH + N / 4;
+    float2 *c0 = twHi + N / 4;                             // S[u][0],   u < N
+    float2 *cH = c0 + N;                                   // S[u][N/2], u < N
     __shared__ double red[33];
     const int p = blockIdx.x, tid = threadIdx.x;
     const float *src = img + (size_t)p * a.W * a.H;
     float2 *out = spec + (size_t)p * N * HW;
-
-    make_twiddles<N>(twf, -1);
-    make_twiddles<N>(twi, +1);
+    make_twiddles<N>(twN, -1);
+    make_twiddles<N>(twNi, +1);
+    make_twiddles<H>(twH, -1);
+    make_twiddles<H>(twHi, +1);
+    // ---- load (rows 2pr, 2pr+1 into the real and imaginary parts of buf row pr) and statistics
     double s = 0.0;
     for (int idx = tid; idx < N * N; idx += kThreads) {
-        int r = idx / N, c = idx % N;
-        float v = src[(size_t)(a.oy + r) * a.W + a.ox + c];
-        buf[r * LD + c] = make_float2(v, 0.f);
+        const int r = idx / N, c = idx % N;
+        const float v = src[(size_t)(a.oy + r) * a.W + a.ox + c];
+        reinterpret_cast<float *>(buf + (r >> 1) * LD + c)[r & 1] = v;
         s += v;
     }
     const double mean = block_sum(s, red) / (N * N);
     double ss = 0.0;
-    for (int idx = tid; idx < N * N; idx += kThreads) {
-        double d = buf[(idx / N) * LD + idx % N].x - mean;
-        ss += d * d;
+    for (int idx = tid; idx < H * N; idx += kThreads) {
+        const float2 z = buf[(idx / N) * LD + idx % N];
+        const double d0 = z.x - mean, d1 = z.y - mean;
+        ss += d0 * d0 + d1 * d1;
     }
     const double sd = sqrt(block_sum(ss, red) / (N * N));
     bool bad = !(sd > 1e-12 * (1.0 + fabs(mean)));
     double energy = 0.0;
     if (!bad) {
         const float m = (float)mean, inv = (float)(1.0 / sd);
-        for (int idx = tid; idx < N * N; idx += kThreads) {
-            int r = idx / N, c = idx % N;
-            float wr = a.window ? 0.5f * (1.f - cospif(2.f * r / N)) : 1.f;
-            float wc = a.window ? 0.5f * (1.f - cospif(2.f * c / N)) : 1.f;
-            float v = buf[r * LD + c].x;
-            buf[r * LD + c] = make_float2((v - m) * inv * wr * wc, 0.f);
+        for (int idx = tid; idx < H * N; idx += kThreads) {
+            const int pr = idx / N, c = idx % N;
+            const float wc = (a.window ? 0.5f * (1.f - cospif(2.f * c / N)) : 1.f) * inv;
+            const float w0 = a.window ? 0.5f * (1.f - cospif(2.f * (2 * pr) / N)) : 1.f;
+            const float w1 = a.window ? 0.5f * (1.f - cospif(2.f * (2 * pr + 1) / N)) : 1.f;
+            const float2 z = buf[pr * LD + c];
+            buf[pr * LD + c] = make_float2((z.x - m) * wc * w0, (z.y - m) * wc * w1);
         }
         __syncthreads();
-        fft2_smem<N>(buf, twf);
+        smem_fft_lines<N>(buf, H, LD, 1, twN);   // rows
+        __syncthreads();
+        {   // split every packed row into its two real rows' half spectra
+            constexpr int ITEMS = H * (N / 2), PER = (ITEMS + kThreads - 1) / kThreads;
+            float2 ra[PER], rb[PER];
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                const int it = tid + k * kThreads;
+                if (it < ITEMS) {
+                    const int pr = it / (N / 2), v = it % (N / 2);
+                    const float2 *row = buf + pr * LD;
+                    if (v == 0) {
+                        const float2 z0 = row[0], zh = row[N / 2];
+                        ra[k] = make_float2(z0.x, zh.x);
+                        rb[k] = make_float2(z0.y, zh.y);
+                    } else {
+                        const float2 zv = row[v], zn = row[N - v];
+                        ra[k] = make_float2(0.5f * (zv.x + zn.x), 0.5f * (zv.y - zn.y));
+                        rb[k] = make_float2(0.5f * (zv.y + zn.y), 0.5f * (zn.x - zv.x));
+                    }
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                const int it = tid + k * kThreads;
+                if (it < ITEMS) {
+                    const int pr = it / (N / 2), v = it % (N / 2);
+                    buf[pr * LD + v] = ra[k];
+                    buf[pr * LD + N / 2 + v] = rb[k];
+                }
+            }
+        }
+        __syncthreads();
+        smem_fft_lines<H>(buf, N, 1, LD, twH);   // even-row and odd-row halves of every column
+        __syncthreads();
+        // join the halves: X[u] = E[u] + w^u O[u], X[u + N/2] = E[u] - w^u O[u]
+        for (int it = tid; it < H * (N / 2); it += kThreads) {
+            const int u = it / (N / 2), v = it % (N / 2);
+            const float2 w = twN[u];
+            if (v == 0) {
+                // columns 0 and N/2: the packed real sequences, split first
+                const int un = (H - u) & (H - 1);
+                const float2 we = buf[u * LD], wen = buf[un * LD];
+                const float2 wo = buf[u * LD + N / 2], won = buf[un * LD + N / 2];
+                const float2 ae = make_float2(0.5f * (we.x + wen.x), 0.5f * (we.y - wen.y));
+                const float2 be = make_float2(0.5f * (we.y + wen.y), 0.5f * (wen.x - we.x));
+                const float2 ao = c_mul(make_float2(0.5f * (wo.x + won.x), 0.5f * (wo.y - won.y)), w);
+                const float2 bo = c_mul(make_float2(0.5f * (wo.y + won.y), 0.5f * (won.x - wo.x)), w);
+                c0[u] = c_add(ae, ao);
+                c0[u + H] = c_sub(ae, ao);
+                cH[u] = c_add(be, bo);
+                cH[u + H] = c_sub(be, bo);
+            } else {
+                const float2 e = buf[u * LD + v], o = c_mul(buf[u * LD + N / 2 + v], w);
+                buf[u * LD + v] = c_add(e, o);
+                buf[u * LD + N / 2 + v] = c_sub(e, o);
+            }
+        }
+        __syncthreads();
+        // band-pass and the filtered energy (bins 1..N/2-1 stand for their mirror images too)
         double e = 0.0;
-        for (int idx = tid; idx < N * N; idx += kThreads) {
-            int u = idx / N, v = idx % N;
-            float fu = (float)(u < N / 2 ? u : u - N), fv = (float)(v < N / 2 ? v : v - N);
-            float rho2 = fu * fu + fv * fv;
-            float h = -expm1f(-rho2 * a.inv2shp) * expf(-rho2 * a.inv2slp);
-            float2 X = buf[u * LD + v];
-            X = make_float2(X.x * h, X.y * h);
-            buf[u * LD + v] = X;
-            e += (double)X.x * X.x + (double)X.y * X.y;
+        for (int it = tid; it < N * HW; it += kThreads) {
+            const int u = it / HW, v = it % HW;
+            float2 *x = v == 0 ? c0 + u : (v == N / 2 ? cH + u : buf + (u & (H - 1)) * LD + (u >= H ? N / 2 : 0) + v);
+            const float fu = (float)(u < N / 2 ? u : u - N), fv = (float)(v < N / 2 ? v : v - N);
+            const float rho2 = fu * fu + fv * fv;
+            const float h = -expm1f(-rho2 * a.inv2shp) * expf(-rho2 * a.inv2slp);
+            const float2 X = make_float2(x->x * h, x->y * h);
+            *x = X;
+            e += (v == 0 || v == N / 2 ? 1.0 : 2.0) * ((double)X.x * X.x + (double)X.y * X.y);
         }
         energy = block_sum(e, red);
         bad = !(energy > 0.0);
@@ -84,23 +170,73 @@ __global__ void __launch_bounds__(kThreads) k_prep(const float *__restrict__ img
         return;
     }
     const float sc = (float)(1.0 / sqrt(energy));
-    for (int idx = tid; idx < N * HW; idx += kThreads) {
-        int u = idx / HW, v = idx % HW;
-        float2 X = buf[u * LD + v];
-        out[idx] = make_float2(X.x * sc, X.y * sc);
+    for (int it = tid; it < N * HW; it += kThreads) {
+        const int u = it / HW, v = it % HW;
+        const float2 X = v == 0 ? c0[u] : (v == N / 2 ? cH[u] : buf[(u & (H - 1)) * LD + (u >= H ? N / 2 : 0) + v]);
+        out[it] = make_float2(X.x * sc, X.y * sc);
     }
-    if (spatial) {
-        __syncthreads();
-        for (int idx = tid; idx < N * N; idx += kThreads) {
-            int u = idx / N, v = idx % N;
-            float2 X = buf[u * LD + v];
-            buf[u * LD + v] = make_float2(X.x * sc, X.y * sc);
+    if (!spatial) return;
+    __syncthreads();
+    // ---- spatial image: undo the join (E = X[u] + X[u + N/2], O = w^-u (X[u] - X[u + N/2]))
+    for (int it = tid; it < H * (N / 2); it += kThreads) {
+        const int u = it / (N / 2), v = it % (N / 2);
+        const float2 wi = twNi[u];
+        if (v == 0) {
+            const float2 e0 = c_add(c0[u], c0[u + H]), o0 = c_mul(c_sub(c0[u], c0[u + H]), wi);
+            const float2 eh = c_add(cH[u], cH[u + H]), oh = c_mul(c_sub(cH[u], cH[u + H]), wi);
+            // pack the two real-output columns: E0 + i EH, O0 + i OH (scaled)
+            buf[u * LD] = make_float2(sc * (e0.x - eh.y), sc * (e0.y + eh.x));
+            buf[u * LD + N / 2] = make_float2(sc * (o0.x - oh.y), sc * (o0.y + oh.x));
+        } else {
+            const float2 x0 = buf[u * LD + v], x1 = buf[u * LD + N / 2 + v];
+            const float2 e = c_add(x0, x1), o = c_mul(c_sub(x0, x1), wi);
+            buf[u * LD + v] = make_float2(e.x * sc, e.y * sc);
+            buf[u * LD + N / 2 + v] = make_float2(o.x * sc, o.y * sc);
+        }
+    }
+    __syncthreads();
+    smem_fft_lines<H>(buf, N, 1, LD, twHi);   // columns back: R'[y][v] in the split layout
+    __syncthreads();
+    {   // rows 2pr, 2pr+1 as one complex line: z[v] = Ra[v] + i Rb[v], conjugate-symmetric extension
+        constexpr int ITEMS = H * N, PER = (ITEMS + kThreads - 1) / kThreads;
+        float2 zz[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int it = tid + k * kThreads;
+            if (it < ITEMS) {
+                const int pr = it / N, v = it % N;
+                const float2 *row = buf + pr * LD;
+                const int w = v <= N / 2 ? v : N - v;
+                float2 ra, rb;
+                if (w == 0 || w == N / 2) {
+                    ra = make_float2(w == 0 ? row[0].x : row[0].y, 0.f);
+                    rb = make_float2(w == 0 ? row[N / 2].x : row[N / 2].y, 0.f);
+                } else {
+                    ra = row[w];
+                    rb = row[N / 2 + w];
+                    if (v > N / 2) {
+                        ra.y = -ra.y;
+                        rb.y = -rb.y;
+                    }
+                }
+                zz[k] = make_float2(ra.x - rb.y, ra.y + rb.x);
+            }
         }
         __syncthreads();
-        fft2_smem<N>(buf, twi);
-        const float invn = 1.f / N;
-        for (int idx = tid; idx < N * N; idx += kThreads)
-            spatial[(size_t)p * N * N + idx] = buf[(idx / N) * LD + idx % N].x * invn;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int it = tid + k * kThreads;
+            if (it < ITEMS) buf[(it / N) * LD + it % N] = zz[k];
+        }
+    }
+    __syncthreads();
+    smem_fft_lines<N>(buf, H, LD, 1, twNi);   // rows back
+    __syncthreads();
+    const float invn = 1.f / N;
+    for (int idx = tid; idx < N * N; idx += kThreads) {
+        const int r = idx / N, c = idx % N;
+        const float2 z = buf[(r >> 1) * LD + c];
+        spatial[(size_t)p * N * N + idx] = ((r & 1) ? z.y : z.x) * invn;
     }
 }
 
@@ -211,10 +347,10 @@ cudaError_t set_smem(K kern, size_t bytes) {
 template <int N>
 cudaError_t prep_n(const float *img, int P, const PrepArgs &a, float2 *spec, float *spatial, int *degen,
                    const int *active, cudaStream_t st) {
-    size_t sm = smem_bytes_generic<N>();
-    cudaError_t e = set_smem(k_prep<N>, sm);
+    const size_t sm = smem_prep_real<N>();
+    cudaError_t e = set_smem(k_prep_real<N>, sm);
     if (e != cudaSuccess) return e;
-    k_prep<N><<<P, kThreads, sm, st>>>(img, a, spec, spatial, degen, active);
+    k_prep_real<N><<<P, kThreads, sm, st>>>(img, a, spec, spatial, degen, active);
     return cudaGetLastError();
 }
 
