@@ -1487,6 +1487,53 @@ int maps_autotune(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout
     return status;
 }
 
+// launch shape of the queued items: persistent CTAs over the atomic queue
+// (grid = SMs) or one CTA per item (grid = 0).  Timed on the first waves of
+// the real item list and cached per batch configuration.
+int maps_shape(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout &L, const MapsDev &d,
+               const std::vector<WorkItem> &items, const std::vector<char> &key, cudaStream_t st, int *grid) {
+    for (auto &kv : ctx->shape_cache)
+        if (kv.first == key) {
+            *grid = kv.second;
+            return XCF_OK;
+        }
+    *grid = d.grid;
+    const size_t ns = std::min(items.size(), (size_t)kTuneWaves * ctx->num_sms);
+    if (ns > 0) {
+        std::vector<WorkItem> sample(items.begin(), items.begin() + ns);
+        int rc = maps_table_upload(ctx, maps, n, L, d, sample, st);
+        if (rc) return rc;
+        cudaEvent_t e0, e1;
+        XCF_CHECK(cudaEventCreate(&e0), "event");
+        XCF_CHECK(cudaEventCreate(&e1), "event");
+        float best = 1e30f;
+        const int shapes[2] = {d.grid, 0};
+        for (int g : shapes) {
+            cudaMemsetAsync(d.keys, 0, sizeof(unsigned long long) * L.idx_total, st);
+            cudaMemsetAsync(d.counter, 0, sizeof(int), st);
+            cudaEventRecord(e0, st);
+            cudaError_t e = launch_search_maps(d.maps, d.items, (int)ns, d.counter, d.work, g, st);
+            cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return cuda_fail(ctx, e, "launch-shape trial");
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                *grid = g;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    ctx->shape_cache.push_back({key, *grid});
+    return XCF_OK;
+}
+
 }  // namespace
 
 int xcf_index_maps(xcf_ctx *ctx, const xcf_map_desc *maps, int32_t n_maps, int32_t flags, void *stream) {
@@ -1535,6 +1582,7 @@ int xcf_index_maps(xcf_ctx *ctx, const xcf_map_desc *maps, int32_t n_maps, int32
     if ((rc = maps_autotune(ctx, maps, n_maps, L, d, caller))) return rc;
     items = maps_items(ctx, maps, n_maps);   // the tuned granularity may need a larger table
     if (items.size() > max_items && (rc = maps_scratch(ctx, maps, n_maps, L, items.size(), &d))) return rc;
+    if ((rc = maps_shape(ctx, maps, n_maps, L, d, items, key, caller, &d.grid))) return rc;
     if ((rc = maps_table_upload(ctx, maps, n_maps, L, d, items, caller))) return rc;
 
     if (!graph) return maps_search_finish(ctx, maps, n_maps, L, d, (int)items.size(), caller);

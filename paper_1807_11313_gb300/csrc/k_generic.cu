@@ -266,63 +266,93 @@ __device__ __forceinline__ float parabola(float cm, float c0, float cp) {
 // one surface per pattern: integer argmax (ties -> lowest row-major shift),
 // peak value and parabolic sub-pixel shift
 // --------------------------------------------------------------------------
+// Two patterns per CTA: Z = X_a + i X_b with X_s = conj(S_t(s)) S_p(s), so the
+// real and imaginary parts of one complex inverse transform are the two
+// surfaces.  A pattern that is skipped (inactive) or has no template
+// contributes X = 0.
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_pair_peak(const float2 *__restrict__ St,
                                                         const int *__restrict__ tidx,
                                                         const float2 *__restrict__ Sp,
                                                         const int *__restrict__ degen,
-                                                        const int *__restrict__ active,
+                                                        const int *__restrict__ active, int P,
                                                         float *__restrict__ peak,
                                                         float *__restrict__ shift) {
     constexpr int LD = N + 1, HW = N / 2 + 1;
     extern __shared__ float4 smem_raw[];
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
     float2 *twi = buf + N * LD;
-    __shared__ float rv[kThreads / 32];
-    __shared__ int ri[kThreads / 32];
-    __shared__ int s_best;
-    const int p = blockIdx.x;
-    if (active && !active[p]) return;
-    const int t = tidx ? tidx[p] : p;
-    if ((degen && degen[p]) || t < 0) {
-        if (threadIdx.x == 0) {
+    __shared__ float rv[2][kThreads / 32];
+    __shared__ int ri[2][kThreads / 32];
+    const int tid = threadIdx.x;
+    int pp[2], mode[2], tt[2];   // mode: 0 skip, 1 zero outputs, 2 compute
+    for (int s = 0; s < 2; ++s) {
+        pp[s] = 2 * blockIdx.x + s;
+        const int p = pp[s];
+        if (p >= P || (active && !active[p])) {
+            mode[s] = 0;
+            tt[s] = 0;
+            continue;
+        }
+        tt[s] = tidx ? tidx[p] : p;
+        mode[s] = ((degen && degen[p]) || tt[s] < 0) ? 1 : 2;
+        if (mode[s] == 1 && tid == 0) {
             peak[p] = 0.f;
             shift[2 * p] = 0.f;
             shift[2 * p + 1] = 0.f;
         }
-        return;
     }
+    if (mode[0] != 2 && mode[1] != 2) return;
     make_twiddles<N>(twi, +1);
-    const float2 *st = St + (size_t)t * N * HW;
-    build_pair_spectrum<N>(buf, st, st, Sp + (size_t)p * N * HW);
+    const float2 *ta = St + (size_t)(mode[0] == 2 ? tt[0] : 0) * N * HW;
+    const float2 *tb = St + (size_t)(mode[1] == 2 ? tt[1] : 0) * N * HW;
+    const float2 *qa = Sp + (size_t)(mode[0] == 2 ? pp[0] : 0) * N * HW;
+    const float2 *qb = Sp + (size_t)(mode[1] == 2 ? pp[1] : 0) * N * HW;
+    const float fa = mode[0] == 2 ? 1.f : 0.f, fb = mode[1] == 2 ? 1.f : 0.f;
+    for (int idx = tid; idx < N * N; idx += kThreads) {
+        const int r = idx / N, c = idx % N;
+        const bool direct = c <= N / 2;
+        const int k = direct ? r * HW + c : ((N - r) & (N - 1)) * HW + (N - c);   // conj(X(-u, -v)) above N/2
+        float2 x1 = c_mulcj(ta[k], qa[k]), x2 = c_mulcj(tb[k], qb[k]);
+        x1 = make_float2(x1.x * fa, x1.y * fa);
+        x2 = make_float2(x2.x * fb, x2.y * fb);
+        buf[r * LD + c] = direct ? make_float2(x1.x - x2.y, x1.y + x2.x) : make_float2(x1.x + x2.y, -x1.y + x2.x);
+    }
     __syncthreads();
     fft2_smem<N>(buf, twi);
-    // the imaginary part of Z = X + i X is a copy of the surface; use the real part
-    float bv = -INFINITY;
-    int bi = 0x7fffffff;
-    for (int idx = threadIdx.x; idx < N * N; idx += kThreads) {
-        float v = buf[(idx / N) * LD + idx % N].x;
-        if (v > bv) { bv = v; bi = idx; }
+    float bv[2] = {-INFINITY, -INFINITY};
+    int bi[2] = {0x7fffffff, 0x7fffffff};
+    for (int idx = tid; idx < N * N; idx += kThreads) {
+        const float2 v = buf[(idx / N) * LD + idx % N];
+        if (v.x > bv[0]) { bv[0] = v.x; bi[0] = idx; }
+        if (v.y > bv[1]) { bv[1] = v.y; bi[1] = idx; }
     }
+    const int lane = tid & 31, w = tid >> 5;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv[s], o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi[s], o);
+            if (ov > bv[s] || (ov == bv[s] && oi < bi[s])) { bv[s] = ov; bi[s] = oi; }
+        }
+        if (lane == 0) { rv[s][w] = bv[s]; ri[s][w] = bi[s]; }
     }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) { rv[w] = bv; ri[w] = bi; }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid < 2 && mode[tid] == 2) {
+        const int s = tid, p = pp[s];
+        float b = rv[s][0];
+        int i0 = ri[s][0];
         for (int k = 1; k < kThreads / 32; ++k)
-            if (rv[k] > bv || (rv[k] == bv && ri[k] < bi)) { bv = rv[k]; bi = ri[k]; }
-        s_best = bi;
-        const int y0 = bi / N, x0 = bi % N;
-        const float c0 = buf[y0 * LD + x0].x;
-        const float cxm = buf[y0 * LD + ((x0 + N - 1) & (N - 1))].x;
-        const float cxp = buf[y0 * LD + ((x0 + 1) & (N - 1))].x;
-        const float cym = buf[((y0 + N - 1) & (N - 1)) * LD + x0].x;
-        const float cyp = buf[((y0 + 1) & (N - 1)) * LD + x0].x;
+            if (rv[s][k] > b || (rv[s][k] == b && ri[s][k] < i0)) { b = rv[s][k]; i0 = ri[s][k]; }
+        const int y0 = i0 / N, x0 = i0 % N;
+        auto at = [&](int y, int x) {
+            const float2 z = buf[y * LD + x];
+            return s ? z.y : z.x;
+        };
+        const float c0 = at(y0, x0);
+        const float cxm = at(y0, (x0 + N - 1) & (N - 1)), cxp = at(y0, (x0 + 1) & (N - 1));
+        const float cym = at((y0 + N - 1) & (N - 1), x0), cyp = at((y0 + 1) & (N - 1), x0);
         peak[p] = c0;
         shift[2 * p] = (float)(x0 < N / 2 ? x0 : x0 - N) + parabola(cxm, c0, cxp);
         shift[2 * p + 1] = (float)(y0 < N / 2 ? y0 : y0 - N) + parabola(cym, c0, cyp);
@@ -379,7 +409,7 @@ cudaError_t pair_peak_n(const float2 *St, const int *tidx, const float2 *Sp, con
     size_t sm = smem_bytes_generic<N>();
     cudaError_t e = set_smem(k_pair_peak<N>, sm);
     if (e != cudaSuccess) return e;
-    k_pair_peak<N><<<P, kThreads, sm, st>>>(St, tidx, Sp, degen, active, peak, shift);
+    k_pair_peak<N><<<(P + 1) / 2, kThreads, sm, st>>>(St, tidx, Sp, degen, active, P, peak, shift);
     return cudaGetLastError();
 }
 

@@ -8,7 +8,8 @@
 // template pairs) of every 128 x 128 map of the batch, taken with an atomic
 // counter, and runs the tuned 128 x 128 body on each; the maps may have
 // different libraries, pattern centres and detectors.  A CTA never waits for
-// another: the queue only hands out indices.  (Maps of other sides run their
+// another: the queue only hands out indices.  The alternative launch shape
+// (one CTA per item, grid = items) is one of the autotuner's candidates.  (Maps of other sides run their
 // own kernels in the same stream: see queued_side in api.cu.)
 #include "common.cuh"
 #include "kernels.cuh"
@@ -17,6 +18,15 @@
 namespace {
 
 constexpr int kMapThreads = s128::NT;
+
+// one item per CTA (grid = items), the hardware block scheduler balancing
+__global__ void __launch_bounds__(kMapThreads, 1)
+k_search_items(const MapDev *__restrict__ maps, const WorkItem *__restrict__ items) {
+    const WorkItem w = items[blockIdx.x];
+    const MapDev m = maps[w.map];
+    if (m.degen[w.p] || m.N != 128) return;
+    s128::search_body(m.St, m.T, m.Sp, w.p, w.pb, w.pe, m.keys, nullptr);
+}
 
 __global__ void __launch_bounds__(kMapThreads, 1)
 k_search_maps(const MapDev *__restrict__ maps, const WorkItem *__restrict__ items, int n_items, int *counter,
@@ -43,6 +53,13 @@ size_t maps_smem_bytes() { return s128::SMEM_BYTES; }
 cudaError_t launch_search_maps(const MapDev *maps, const WorkItem *items, int n_items, int *counter, float2 *work,
                                int grid, cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
+    if (grid <= 0) {   // one CTA per item
+        cudaError_t e = cudaFuncSetAttribute(k_search_items, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)maps_smem_bytes());
+        if (e != cudaSuccess) return e;
+        k_search_items<<<n_items, kMapThreads, maps_smem_bytes(), st>>>(maps, items);
+        return cudaGetLastError();
+    }
     cudaError_t e = cudaFuncSetAttribute(k_search_maps, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)maps_smem_bytes());
     if (e != cudaSuccess) return e;

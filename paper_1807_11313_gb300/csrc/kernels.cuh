@@ -79,6 +79,7 @@ struct WorkItem {
     int map, p, pb, pe;            // pattern p of map `map` against template pairs [pb, pe)
 };
 size_t maps_smem_bytes();
+// grid > 0: persistent CTAs over an atomic queue (counter); grid <= 0: one CTA per item
 cudaError_t launch_search_maps(const MapDev *maps, const WorkItem *items, int n_items, int *counter, float2 *work,
                                int grid, cudaStream_t st);
 
