@@ -1,0 +1,166 @@
+"""The precision and batched forms at the sizes bench.py times.
+
+Precision form (256 x 256, 19,944 templates, 50,000 patterns, fused screen +
+rescore + refinement): on sampled patterns the oracle recomputes the screen
+scores of the returned candidates (BF16-rounded operands) and of random
+non-candidates (which must not beat the k-th candidate beyond the BF16
+tolerance), and the FP32 rescore over the candidate list (the returned best
+must be the oracle's argmax); everywhere, the refined orientations meet the
+accuracy bar.
+
+Batched form (eight maps, detectors 96 .. 256): the graph-captured multi-map
+search equals the per-map search bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+PC0 = (0.5, 0.5, 0.6)
+
+
+@pytest.fixture(scope="module")
+def px():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1807_11313_gb300 as px
+    px.load()
+    return px
+
+
+def _noisy(torch, clean, pcs, peak, gen):
+    P, H, W = clean.shape
+    lo = clean.amin(dim=(1, 2), keepdim=True)
+    hi = clean.amax(dim=(1, 2), keepdim=True)
+    ih = (clean - lo) / (hi - lo).clamp_min(1e-30)
+    ry = torch.arange(H, device=clean.device, dtype=torch.float32) + 0.5
+    rx = torch.arange(W, device=clean.device, dtype=torch.float32) + 0.5
+    cy = (pcs[:, 1] * H).float().view(P, 1, 1)
+    cx = (pcs[:, 0] * W).float().view(P, 1, 1)
+    hump = torch.exp(-((ry.view(1, H, 1) - cy) ** 2 + (rx.view(1, 1, W) - cx) ** 2) / (2 * (0.35 * W) ** 2))
+    return torch.poisson(peak.float().view(P, 1, 1) * (0.6 * hump + 0.4 * ih), generator=gen)
+
+
+@pytest.fixture(scope="module")
+def precision(px):
+    wl = synth.config_precision_256(seed=0)
+    n, k = wl["n"], wl["k"]
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    geom = px.geometry(n, n, wl["pc"])
+    ctx = px.Context(max_iter=wl["max_iter"], tol_deg=1e-3)
+    master, libq, truth, pcs, peak = d(wl["master"]), d(wl["lib_q"]), d(wl["truth_q"]), d(wl["pcs"]), d(wl["peak"])
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(wl["noise_seed"])
+    P = truth.shape[0]
+    pats = torch.empty((P, n, n), device="cuda")
+    for c0 in range(0, P, 4096):
+        c1 = min(P, c0 + 4096)
+        clean = px.xcf_project(ctx, master, truth[c0:c1].contiguous(), geom, pcs=pcs[c0:c1].contiguous())
+        pats[c0:c1] = _noisy(torch, clean, pcs[c0:c1], peak[c0:c1], gen)
+    lib = px.xcf.xcf_build_library_ex(ctx, libq, geom, master=master, flags=px.xcf.XCF_LIB_SCREEN)
+    best, q, pk, it = px.xcf_index_precision(ctx, lib, pats, pcs=pcs, k=k)
+    sel = torch.tensor([0, 17, 24999, 49999], device="cuda")
+    cand, score = px.xcf.xcf_screen_topk(ctx, lib, pats[sel].contiguous(), k)
+    mis = px.xcf_disorientation(ctx, q, truth)
+    torch.cuda.synchronize()
+    out = dict(wl=wl, lib=lib, ctx=ctx, geom=geom, master=master, libq=libq, sel=sel.cpu().numpy(),
+               pats_sel=pats[sel].cpu().numpy(), best=best.cpu().numpy(), iters=it.cpu().numpy(),
+               peak=pk.cpu().numpy(), mis=mis.cpu().numpy(), cand=cand.cpu().numpy(), score=score.cpu().numpy())
+    del pats
+    yield out
+    lib.close()
+    ctx.close()
+
+
+def _template_spatial(px, orc, run, tids):
+    """Oracle-filtered spatial images of library templates (GPU projection as the input)."""
+    n = run["wl"]["n"]
+    imgs = px.xcf_project(run["ctx"], run["master"], run["libq"][torch.as_tensor(tids).cuda()].contiguous(),
+                          run["geom"]).cpu().numpy()
+    _, y, _ = orc.prep_many(imgs, want_spatial=True)
+    return y
+
+
+def test_precision_fullsize_everywhere(precision):
+    r = precision
+    T = len(r["wl"]["lib_q"])
+    assert np.all((r["best"] >= 0) & (r["best"] < T))
+    assert np.all((r["iters"] >= 1) & (r["iters"] <= r["wl"]["max_iter"]))
+    assert np.all(r["peak"] > 0) and np.all(r["peak"] <= 1.0 + 1e-5)
+    assert r["mis"].mean() <= 0.5, r["mis"].mean()
+
+
+def test_precision_fullsize_sampled_screen_and_rescore(px, orc, precision):
+    r = precision
+    n, k = r["wl"]["n"], r["wl"]["k"]
+    _, yp, _ = orc.prep_many(r["pats_sel"], want_spatial=True)
+    rng = np.random.default_rng(3)
+    T = len(r["wl"]["lib_q"])
+    for i in range(len(r["sel"])):
+        cand = r["cand"][i]
+        # the returned scores are the oracle's zero-shift scores on BF16-rounded operands
+        yt = _template_spatial(px, orc, r, cand)
+        ref = orc.screen(yp[i:i + 1].reshape(1, -1), yt.reshape(len(cand), -1), bf16=True)[0]
+        tol = 1e-5 + 1e-8 * n * n
+        np.testing.assert_allclose(r["score"][i], ref, atol=tol)
+        # random non-candidates do not beat the k-th candidate
+        others = np.setdiff1d(rng.choice(T, 64, replace=False), cand)
+        yo = _template_spatial(px, orc, r, others)
+        so = orc.screen(yp[i:i + 1].reshape(1, -1), yo.reshape(len(others), -1), bf16=True)[0]
+        assert so.max() <= r["score"][i][-1] + tol
+        # the FP32 rescore picks the oracle's best correlation among the candidates
+        St, _, _ = orc.prep_many(px.xcf_project(r["ctx"], r["master"],
+                                                r["libq"][torch.as_tensor(cand).cuda()].contiguous(),
+                                                r["geom"]).cpu().numpy())
+        Sp, _, deg = orc.prep_many(r["pats_sel"][i:i + 1])
+        _, _, _, allp = orc.index(St, Sp, deg, want_all=True)
+        got = int(np.where(cand == r["best"][r["sel"][i]])[0][0])
+        ob = int(np.argmax(allp[0]))
+        assert got == ob or abs(allp[0, got] - allp[0, ob]) <= 2e-5 * abs(allp[0, ob]), (i, got, ob)
+
+
+def test_batched_fullsize_equals_per_map(px):
+    wl = synth.config_batched(seed=0)
+    ctx = px.Context()
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    master = d(wl["master"])
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(wl["noise_seed"])
+    batch = []
+    for m in wl["maps"]:
+        g = px.geometry(m["W"], m["H"], wl["pc"])
+        lib = px.xcf_build_library(ctx, master, d(m["lib_q"]), g)
+        clean = px.xcf_project(ctx, master, d(m["truth_q"]), g, pcs=d(m["pcs"]))
+        batch.append((lib, _noisy(torch, clean, d(m["pcs"]), d(m["peak"]), gen).contiguous()))
+    outs = px.xcf_index_maps(ctx, batch, graph=True)
+    outs = px.xcf_index_maps(ctx, batch, outs=outs, graph=True)   # a replay
+    for (lib, pats), o in zip(batch, outs):
+        ref = px.xcf_index(ctx, lib, pats)
+        torch.cuda.synchronize()
+        for a, b in zip(o, ref):
+            assert torch.equal(a, b)
+    for lib, _ in batch:
+        lib.close()
+    ctx.close()
+
+
+def test_empty_inputs(px):
+    """P = 0 everywhere is a no-op that succeeds."""
+    ctx = px.Context()
+    master = torch.from_numpy(np.ascontiguousarray(synth.master_pattern("bcc", 64))).cuda()
+    g = px.geometry(128, 128, PC0)
+    lq = torch.from_numpy(synth.random_quaternions(3, 1)).cuda()
+    lib = px.xcf.xcf_build_library_ex(ctx, lq, g, master=master, flags=px.xcf.XCF_LIB_SCREEN)
+    empty = torch.empty((0, 128, 128), device="cuda")
+    b, p, s = px.xcf_index(ctx, lib, empty)
+    assert b.numel() == 0
+    px.xcf_index_precision(ctx, lib, empty, k=2)
+    px.xcf_index_refine(ctx, lib, empty)
+    net = px.xcf_net_create(ctx, 8)
+    assert px.xcf_propose(ctx, net, empty, g).shape == (0, 8, 4)
+    px.xcf_index_learned(ctx, net, lib, empty)
+    assert px.xcf_index_maps(ctx, [(lib, empty)])[0][0].numel() == 0
+    net.close()
+    lib.close()
+    ctx.close()
