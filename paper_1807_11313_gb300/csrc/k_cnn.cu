@@ -21,76 +21,48 @@
 
 namespace {
 
-constexpr int BM = 64, BN = 128, BK = 16, GT = 256;
-constexpr int A_PER = BM * BK / GT, B_PER = BN * BK / GT;   // elements each thread stages per k-slice
+constexpr int BM = 64, BN = 64, BK = 16, GT = 256;
 
-// 64 x 128 tile per CTA, 4 x 8 outputs per thread (rows ty*4.., columns tx*4.. and 64 + tx*4..);
-// the next k-slice is gathered into registers while the current one is multiplied
 template <class LA, class LB, class EP>
 __global__ void __launch_bounds__(GT) k_gemm(int M, int N, int K, int kper, LA la, LB lb, EP ep) {
-    __shared__ __align__(16) float As[2][BK][BM + 4];
-    __shared__ __align__(16) float Bs[2][BK][BN + 4];
+    __shared__ float As[BK][BM + 4];
+    __shared__ float Bs[BK][BN + 4];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int kb = blockIdx.z * kper, ke = min(K, kb + kper);
-    float ra[A_PER], rb[B_PER];
-    auto gather = [&](int k0) {
-#pragma unroll
-        for (int i = 0; i < A_PER; ++i) {
-            const int e = tid + i * GT, am = e / BK, ak = e % BK;   // consecutive threads walk k
-            const int m = m0 + am, k = k0 + ak;
-            ra[i] = (m < M && k < ke) ? la(m, k) : 0.f;
-        }
-#pragma unroll
-        for (int i = 0; i < B_PER; ++i) {
-            const int e = tid + i * GT, bk = e / BN, bn = e % BN;   // consecutive threads walk n
-            const int n = n0 + bn, k = k0 + bk;
-            rb[i] = (n < N && k < ke) ? lb(k, n) : 0.f;
-        }
-    };
-    auto stash = [&](int buf) {
-#pragma unroll
-        for (int i = 0; i < A_PER; ++i) {
-            const int e = tid + i * GT;
-            As[buf][e % BK][e / BK] = ra[i];
-        }
-#pragma unroll
-        for (int i = 0; i < B_PER; ++i) {
-            const int e = tid + i * GT;
-            Bs[buf][e / BN][e % BN] = rb[i];
-        }
-    };
-    float acc[4][8] = {};
-    int buf = 0;
-    if (kb < ke) {
-        gather(kb);
-        stash(0);
-    }
-    __syncthreads();
+    float acc[4][4] = {};
     for (int k0 = kb; k0 < ke; k0 += BK) {
-        const bool more = k0 + BK < ke;
-        if (more) gather(k0 + BK);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int e = tid + i * GT;
+            const int am = e / BK, ak = e % BK;       // A: consecutive threads walk k
+            const int m = m0 + am, k = k0 + ak;
+            As[ak][am] = (m < M && k < ke) ? la(m, k) : 0.f;
+            const int bk = e / BN, bn = e % BN;       // B: consecutive threads walk n
+            const int n = n0 + bn, kk = k0 + bk;
+            Bs[bk][bn] = (n < N && kk < ke) ? lb(kk, n) : 0.f;
+        }
+        __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            const float4 a4 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
-            const float4 b4 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
-            const float4 c4 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
-            const float a[4] = {a4.x, a4.y, a4.z, a4.w};
-            const float b[8] = {b4.x, b4.y, b4.z, b4.w, c4.x, c4.y, c4.z, c4.w};
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                a[i] = As[kk][ty * 4 + i];
+                b[i] = Bs[kk][tx * 4 + i];
+            }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
-        if (more) stash(buf ^ 1);
         __syncthreads();
-        buf ^= 1;
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int m = m0 + ty * 4 + i, n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
             if (m < M && n < N) ep(m, n, acc[i][j]);
         }
 }

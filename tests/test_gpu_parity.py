@@ -306,3 +306,20 @@ def test_errors_are_reported(px, ctx):
     lib.close()
     with pytest.raises(TypeError):
         px.xcf_prep(ctx, torch.zeros((1, 64, 64), dtype=torch.float64, device="cuda"), px.geometry(64, 64))
+
+
+@pytest.mark.parametrize("n", [64, 128, 256])
+def test_pattern_at_library_orientation_returns_that_template(px, ctx, n):
+    """A noise-free pattern simulated at a library orientation (same geometry)
+    returns that template with a correlation peak of 1 at zero shift."""
+    master = dev(synth.master_pattern("bcc", 512))
+    lq = synth.so3_grid_cubic_fz(14.0 if n == 256 else 10.0)
+    g = px.geometry(n, n, PC0)
+    lib = px.xcf_build_library(ctx, master, dev(lq), g)
+    pick = np.array([0, 7, len(lq) // 2, len(lq) - 1])
+    pats = px.xcf_project(ctx, master, dev(lq[pick]), g)
+    best, peak, shift = (host(t) for t in px.xcf_index(ctx, lib, pats))
+    np.testing.assert_array_equal(best, pick)
+    np.testing.assert_allclose(peak, 1.0, atol=2e-5)
+    np.testing.assert_allclose(shift, 0.0, atol=1e-3)
+    lib.close()
