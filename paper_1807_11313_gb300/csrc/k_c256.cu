@@ -534,22 +534,25 @@ k_prep_c256(const float *__restrict__ img, int P, PrepArgs a, float2 *__restrict
         if (active && !active[p]) continue;            // uniform over the cluster
         const float *src = img + (size_t)p * a.W * a.H;
         float2 *out = spec + (size_t)p * N * HW;
-        // ---- statistics of the crop
-        double s = 0.0;
+        // ---- statistics of the crop: one pass, sum and sum of squares in float64
+        // (pixel values are counts: the cancellation in E[x^2] - E[x]^2 stays far
+        // below float precision), one cluster barrier for both
+        double s = 0.0, s2 = 0.0;
         for (int i = tid; i < ROWS * N; i += NT) {
             const int r = i >> 8, x = i & (N - 1);
             const float v = __ldg(src + (size_t)(a.oy + ROWS * c + r) * a.W + a.ox + x);
             Xr[i] = v;
             s += v;
+            s2 += (double)v * v;
         }
-        const double mean = cluster_sum(block_sum_d(s, red), red + 8, slot_local) / ((double)N * N);
-        double ss = 0.0;
-        for (int i = tid; i < ROWS * N; i += NT) {
-            const double d = Xr[i] - mean;
-            ss += d * d;
-        }
-        const double sd =
-            sqrt(cluster_sum(block_sum_d(ss, red), red + 9, slot_local + sizeof(double)) / ((double)N * N));
+        s = block_sum_d(s, red);
+        s2 = block_sum_d(s2, red);
+        if (tid == 0) red[9] = s2;
+        const double tot = cluster_sum(s, red + 8, slot_local);   // its barrier also publishes red[9]
+        double tot2 = 0.0;
+        for (int r = 0; r < NC; ++r) tot2 += ld_cluster_d(map_to_rank(slot_local + sizeof(double), r));
+        const double mean = tot / ((double)N * N);
+        const double sd = sqrt(fmax(tot2 / ((double)N * N) - mean * mean, 0.0));
         bool bad = !(sd > 1e-12 * (1.0 + fabs(mean)));
         if (!bad) {
             // ---- rows (two per complex line), windowed and standardised
