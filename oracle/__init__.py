@@ -40,14 +40,14 @@ def build(force: bool = False) -> str:
 class Opts(C.Structure):
     _fields_ = [("window", C.c_int32), ("sigma_hp", C.c_double), ("sigma_lp", C.c_double),
                 ("lp_nr", C.c_int32), ("lp_neta", C.c_int32), ("lp_rmin", C.c_double),
-                ("lp_rmax", C.c_double)]
+                ("lp_rmax", C.c_double), ("upsample", C.c_int32)]
 
 
 def default_opts(n: int, **kw) -> Opts:
     """Defaults: Hann window, sigma_hp = 2, sigma_lp = n/4 cycles per image,
     log-polar n/4 radii x 2n angles over r in [n/4, n/2 - 1] px."""
     d = dict(window=1, sigma_hp=2.0, sigma_lp=n / 4.0, lp_nr=max(n // 4, 2), lp_neta=2 * n,
-             lp_rmin=n / 4.0, lp_rmax=n / 2.0 - 1.0)
+             lp_rmin=n / 4.0, lp_rmax=n / 2.0 - 1.0, upsample=0)
     d.update(kw)
     return Opts(**d)
 
@@ -77,6 +77,9 @@ def _lib_handle():
                 "orc_xcf_surface": ([_D, _D, C.c_int, _D], None),
                 "orc_xcf_spatial": ([_D, _D, C.c_int, _D], None),
                 "orc_parabola": ([C.c_double, C.c_double, C.c_double], C.c_double),
+                "orc_peak_upsampled": ([_D, _D, C.c_int, C.c_int, _D, _D, _D], None),
+                "orc_pair_upsampled": ([_D, _D, C.c_int, C.c_int, _D, _D, _D], None),
+                "orc_upsampled_value": ([_D, _D, C.c_int, C.c_double, C.c_double], C.c_double),
                 "orc_peak": ([_D, C.c_int, _D, _I, _I, _D, _D], None),
                 "orc_index": ([_D, C.c_int, _D, C.c_int, C.c_int, _I, _I, _D, _D, _D], None),
                 "orc_lambert_forward": ([_D, _D, _D], None),
@@ -249,6 +252,20 @@ def peak(r):
     _lib_handle().orc_peak(_d(r), n, C.byref(pk), C.byref(sy), C.byref(sx), C.byref(dx),
                            C.byref(dy))
     return pk.value, (sy.value, sx.value), (dx.value, dy.value)
+
+
+def pair_upsampled(St, Sp, U):
+    """Up-sampled peak of one pair (full spectra [n, n]) -> (peak, (dx, dy))."""
+    St, Sp = _c128(St), _c128(Sp)
+    n = St.shape[0]
+    pk, dx, dy = C.c_double(), C.c_double(), C.c_double()
+    _lib_handle().orc_pair_upsampled(_d(St), _d(Sp), n, int(U), C.byref(pk), C.byref(dx), C.byref(dy))
+    return pk.value, (dx.value, dy.value)
+
+
+def upsampled_value(St, Sp, y, x):
+    St, Sp = _c128(St), _c128(Sp)
+    return _lib_handle().orc_upsampled_value(_d(St), _d(Sp), St.shape[0], float(y), float(x))
 
 
 def index(St, Sp, degenerate=None, want_all=False):

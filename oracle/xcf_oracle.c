@@ -39,6 +39,7 @@ typedef struct {
     int32_t lp_neta;     /* log-polar angular samples                          */
     double lp_rmin;      /* smallest radius, pixels                            */
     double lp_rmax;      /* largest radius, pixels                             */
+    int32_t upsample;    /* 0: 3-point parabola; U >= 2: up-sampled peak       */
 } orc_opts;
 
 typedef struct {
@@ -285,6 +286,80 @@ void orc_peak(const double *r, int n, double *peak, int *sy, int *sx,
     *sx = x0;
     *dx = (x0 < n / 2 ? x0 : x0 - n) + orc_parabola(cxm, c0, cxp);
     *dy = (y0 < n / 2 ? y0 : y0 - n) + orc_parabola(cym, c0, cyp);
+}
+
+/* Up-sampled peak (the paper's sub-pixel "up-sampling", its reference [17]
+ * absent; reading: the correlation evaluated off the integer grid by its
+ * Fourier series, as in matrix-multiply DFT up-sampling).  X = conj(St) Sp is
+ * the full n x n cross-power spectrum; the real surface off the grid is taken
+ * as r(y, x) = sum over stored columns v = 0..n/2 of w_v Re sum_u X[u][v]
+ * exp(+2 pi i (f(u) y + v x) / n), w_0 = w_{n/2} = 1, w_v = 2 otherwise, f(u)
+ * the signed frequency (u, or u - n above n/2); at integer (y, x) it is the
+ * FFT surface.  It is evaluated on the grid y0 + (m - U)/U, x0 + (l - U)/U,
+ * m, l = 0..2U (+-1 px around the integer argmax (y0, x0) of r), and the grid
+ * argmax (ties -> lowest (m, l) row-major) gives the peak and the shift
+ * (wrapped integer shift plus the grid offsets). */
+void orc_peak_upsampled(const cplx *X, const double *r, int n, int U, double *peak, double *dx, double *dy) {
+    long nn = (long)n * n, best = 0;
+    for (long k = 1; k < nn; ++k)
+        if (r[k] > r[best]) best = k;
+    int y0 = (int)(best / n), x0 = (int)(best % n), M = 2 * U + 1, H = n / 2 + 1;
+    cplx *T1 = malloc(sizeof(cplx) * M * H);
+    for (int m = 0; m < M; ++m) {
+        double y = y0 + (double)(m - U) / U;
+        for (int v = 0; v < H; ++v) {
+            cplx acc = 0;
+            for (int u = 0; u < n; ++u) {
+                double fu = u < n / 2 ? u : u - n;
+                double a = 2.0 * ORC_PI * fu * y / n;
+                acc += X[(long)u * n + v] * (cos(a) + I * sin(a));
+            }
+            T1[m * H + v] = acc;
+        }
+    }
+    double bv = -INFINITY;
+    int bm = 0, bl = 0;
+    for (int m = 0; m < M; ++m)
+        for (int l = 0; l < M; ++l) {
+            double x = x0 + (double)(l - U) / U, s = 0.0;
+            for (int v = 0; v < H; ++v) {
+                double a = 2.0 * ORC_PI * v * x / n, wv = (v == 0 || v == n / 2) ? 1.0 : 2.0;
+                s += wv * creal(T1[m * H + v] * (cos(a) + I * sin(a)));
+            }
+            if (s > bv) { bv = s; bm = m; bl = l; }
+        }
+    free(T1);
+    *peak = bv;
+    *dx = (x0 < n / 2 ? x0 : x0 - n) + (double)(bl - U) / U;
+    *dy = (y0 < n / 2 ? y0 : y0 - n) + (double)(bm - U) / U;
+}
+
+/* cross-power spectrum X = conj(St) Sp and its surface, then the up-sampled peak */
+void orc_pair_upsampled(const cplx *St, const cplx *Sp, int n, int U, double *peak, double *dx, double *dy) {
+    long nn = (long)n * n;
+    cplx *X = malloc(sizeof(cplx) * nn);
+    double *r = malloc(sizeof(double) * nn);
+    for (long k = 0; k < nn; ++k) X[k] = conj(St[k]) * Sp[k];
+    orc_xcf_surface(St, Sp, n, r);
+    orc_peak_upsampled(X, r, n, U, peak, dx, dy);
+    free(X);
+    free(r);
+}
+
+/* the up-sampled surface at one point (y, x) (the definition above), for the pins */
+double orc_upsampled_value(const cplx *St, const cplx *Sp, int n, double y, double x) {
+    int H = n / 2 + 1;
+    double s = 0.0;
+    for (int v = 0; v < H; ++v) {
+        cplx acc = 0;
+        for (int u = 0; u < n; ++u) {
+            double fu = u < n / 2 ? u : u - n;
+            double a = 2.0 * ORC_PI * (fu * y + v * x) / n;
+            acc += conj(St[(long)u * n + v]) * Sp[(long)u * n + v] * (cos(a) + I * sin(a));
+        }
+        s += ((v == 0 || v == n / 2) ? 1.0 : 2.0) * creal(acc);
+    }
+    return s;
 }
 
 /* Library search (Fig. 1 A-C): for each pattern, the template whose
@@ -638,7 +713,10 @@ int orc_refine_one(const float *master, int M, const double pc[3], double sample
         orc_xcf_surface(ST, SP, n, r);
         int sy, sx;
         double dx, dy;
-        orc_peak(r, n, &peak, &sy, &sx, &dx, &dy);
+        if (o->upsample >= 2)
+            orc_pair_upsampled(ST, SP, n, o->upsample, &peak, &dx, &dy);
+        else
+            orc_peak(r, n, &peak, &sy, &sx, &dx, &dy);
         double tx = atan(dy / L), ty = atan(dx / L);
         double qx[4] = {cos(tx / 2), sin(tx / 2), 0, 0};
         double qy[4] = {cos(ty / 2), 0, sin(ty / 2), 0};
