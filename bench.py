@@ -60,6 +60,8 @@ def parse():
                          "+ correlation score + refinement with full-search fallback")
     ap.add_argument("--patterns", type=int, default=0, help="precision form: patterns per GPU (0: 50,000)")
     ap.add_argument("--scale", type=float, default=1.0, help="batched form: scale of every map's pattern count")
+    ap.add_argument("--upsample", type=int, default=0,
+                    help="plain form: 0 = 3-point parabolic peak; U in [2, 20] = up-sampled peak (grid step 1/U px)")
     ap.add_argument("--train", type=int, default=200000, help="learned form: training patterns")
     ap.add_argument("--batch", type=int, default=256, help="learned form: training batch")
     ap.add_argument("--epochs", type=int, default=2, help="learned form: passes over the training set")
@@ -626,7 +628,7 @@ def main():
     wl = synth.config_map_128(seed=rank, ny=args.map, nx=args.map)
     n, P, T = wl["n"], len(wl["truth_q"]), len(wl["lib_q"])
     geom = px.geometry(n, n, wl["pc"])
-    ctx = px.Context(max_iter=wl["max_iter"], tol_deg=1e-3)
+    ctx = px.Context(max_iter=wl["max_iter"], tol_deg=1e-3, upsample=args.upsample)
     master_d = torch.from_numpy(np.ascontiguousarray(wl["master"])).to(dev)
     libq_d = torch.from_numpy(wl["lib_q"]).to(dev)
     truth_d = torch.from_numpy(wl["truth_q"]).to(dev)
@@ -750,6 +752,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": wl["name"], "detector": n, "templates": T, "patterns_per_gpu": P,
                            "max_iter": wl["max_iter"], "parallelism": f"replicas x{world}",
+                           "subpixel": f"up-sampled, step 1/{args.upsample} px" if args.upsample else "3-point parabola",
                            "l2": _l2_note(pats_d.numel() * 4, T * n * (n // 2 + 1) * 8, "library spectra")},
                 "accuracy": accuracy, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
                 "e2e": e2e, "cpu_baseline": cpu}

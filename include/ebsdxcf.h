@@ -58,6 +58,11 @@ typedef struct {
     double lp_rmax;     /* largest log-polar radius, px (auto: N/2 - 1)             */
     int32_t max_iter;   /* refinement iterations (default 2, as in the paper)       */
     double tol_deg;     /* stop when an iteration's update is below this (1e-3)     */
+    int32_t upsample;   /* sub-pixel peak: 0 = 3-point parabola per axis (default);
+                           U in [2, 20] = the correlation's Fourier series evaluated
+                           on a +-1 px grid of step 1/U around the integer peak (the
+                           paper's peak "up-sampling"); applies to every peak step
+                           (xcf_index shifts and the refinement's X/Y shifts)       */
 } xcf_options;
 
 /* Detector geometry of a map (or of a library). */

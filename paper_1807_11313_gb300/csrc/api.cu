@@ -200,10 +200,16 @@ cudaError_t run_search(xcf_ctx *ctx, int n, const float2 *St, int T, const float
     return launch_search_c256(St, T, Sp, degen, P, keys, peaks_all, nullptr, 0, st);
 }
 
+// integer peak and 3-point fit, then (with the up-sampling option) the up-sampled peak
 cudaError_t run_pair_peak(xcf_ctx *ctx, int n, const float2 *St, const int *tidx, const float2 *Sp,
                           const int *degen, const int *active, int P, float *peak, float *shift, cudaStream_t st) {
-    if (n <= 128) return launch_pair_peak(n, St, tidx, Sp, degen, active, P, peak, shift, st);
-    return launch_pair_peak_c256(St, tidx, Sp, degen, active, P, peak, shift, st);
+    const int U = ctx->opt.upsample;
+    int *argmax = nullptr;
+    if (U >= 2 && P > 0 && scratch_t(ctx, S_ARGMAX, P, &argmax)) return cudaErrorMemoryAllocation;
+    cudaError_t e = n <= 128 ? launch_pair_peak(n, St, tidx, Sp, degen, active, P, peak, shift, st, argmax)
+                             : launch_pair_peak_c256(St, tidx, Sp, degen, active, P, peak, shift, st, argmax);
+    if (e != cudaSuccess || U < 2) return e;
+    return launch_upsample_peak(n, St, tidx, Sp, degen, active, P, U, argmax, peak, shift, st);
 }
 
 int check_lib(xcf_ctx *ctx, const xcf_library *lib) {
@@ -344,6 +350,7 @@ int xcf_options_default(xcf_options *o) {
     o->lp_rmax = 0.0;
     o->max_iter = 2;
     o->tol_deg = 1e-3;
+    o->upsample = 0;
     return XCF_OK;
 }
 
@@ -365,6 +372,7 @@ int xcf_create(xcf_ctx **out, const xcf_options *opt, int device) {
     if (opt) {
         o = *opt;
         if (o.window < 0 || o.window > 1 || o.max_iter < 0 || o.sigma_hp < 0) return XCF_ERR_ARG;
+        if (o.upsample != 0 && (o.upsample < 2 || o.upsample > 20)) return XCF_ERR_ARG;
     } else {
         xcf_options_default(&o);
     }
@@ -1384,6 +1392,11 @@ int maps_scratch(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout 
     d->maps = static_cast<MapDev *>(mp);
     d->items = reinterpret_cast<WorkItem *>(static_cast<char *>(mp) + ((sizeof(MapDev) * n + 255) & ~(size_t)255));
     d->counter = reinterpret_cast<int *>(static_cast<char *>(mp) + table);
+    if (ctx->opt.upsample >= 2) {   // the peak step's argmax scratch, sized before any capture
+        int maxp = 1, *am;
+        for (int m = 0; m < n; ++m) maxp = maps[m].P > maxp ? maps[m].P : maxp;
+        if ((rc = scratch_t(ctx, S_ARGMAX, maxp, &am))) return rc;
+    }
     d->grid = ctx->num_sms;
     d->work = nullptr;   // the queue serves 128 x 128 maps only: no global work arrays
     return XCF_OK;

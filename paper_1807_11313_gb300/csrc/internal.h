@@ -46,6 +46,7 @@ enum Slot {
     S_FBCOUNT,      // number of fallback patterns (device int)
     S_CAND,         // screen candidates of a chunk [P, k]
     S_CANDSC,       // their screen scores
+    S_ARGMAX,       // integer peak positions for the up-sampled peak
     S_COUNT
 };
 

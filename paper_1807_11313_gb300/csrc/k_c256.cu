@@ -318,7 +318,7 @@ __device__ __forceinline__ float parabola_c(float cm, float c0, float cp) {
 __global__ void __launch_bounds__(NT, 1)
 k_pair_peak_c256(const float2 *__restrict__ St, const int *__restrict__ tidx, const float2 *__restrict__ Sp,
                  const int *__restrict__ degen, const int *__restrict__ active, int P, float *__restrict__ peak,
-                 float *__restrict__ shift) {
+                 float *__restrict__ shift, int *__restrict__ argmax) {
     extern __shared__ float4 smem_raw[];
     float2 *Zc = reinterpret_cast<float2 *>(smem_raw);
     float2 *scr_all = Zc + ZC_F2;
@@ -452,6 +452,7 @@ k_pair_peak_c256(const float2 *__restrict__ St, const int *__restrict__ tidx, co
                 peak[p] = c0;
                 shift[2 * p] = (float)(x0 < N / 2 ? x0 : x0 - N) + parabola_c(cxm, c0, cxp);
                 shift[2 * p + 1] = (float)(y0 < N / 2 ? y0 : y0 - N) + parabola_c(cym, c0, cyp);
+                if (argmax) argmax[p] = i0;
             }
         }
         cluster_barrier();   // CTA 0 done reading the distributed rows and candidates
@@ -789,7 +790,8 @@ cudaError_t launch_prep_c256(const float *img, int P, const PrepArgs &a, float2 
 }
 
 cudaError_t launch_pair_peak_c256(const float2 *St, const int *tidx, const float2 *Sp, const int *degen,
-                                  const int *active, int P, float *peak, float *shift, cudaStream_t st) {
+                                  const int *active, int P, float *peak, float *shift, cudaStream_t st,
+                                  int *argmax) {
     if (P <= 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_pair_peak_c256, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)PEAK_SMEM);
@@ -818,5 +820,5 @@ cudaError_t launch_pair_peak_c256(const float2 *St, const int *tidx, const float
     const int npass = (P + 1) / 2;
     const int ncl = npass < ncl_max ? npass : ncl_max;
     cfg.gridDim = dim3(NC * ncl);
-    return cudaLaunchKernelEx(&cfg, k_pair_peak_c256, St, tidx, Sp, degen, active, P, peak, shift);
+    return cudaLaunchKernelEx(&cfg, k_pair_peak_c256, St, tidx, Sp, degen, active, P, peak, shift, argmax);
 }

@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_peak(const float2 *__restrict
                                                         const int *__restrict__ degen,
                                                         const int *__restrict__ active, int P,
                                                         float *__restrict__ peak,
-                                                        float *__restrict__ shift) {
+                                                        float *__restrict__ shift, int *__restrict__ argmax) {
     constexpr int LD = N + 1, HW = N / 2 + 1;
     extern __shared__ float4 smem_raw[];
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
@@ -356,6 +356,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_peak(const float2 *__restrict
         peak[p] = c0;
         shift[2 * p] = (float)(x0 < N / 2 ? x0 : x0 - N) + parabola(cxm, c0, cxp);
         shift[2 * p + 1] = (float)(y0 < N / 2 ? y0 : y0 - N) + parabola(cym, c0, cyp);
+        if (argmax) argmax[p] = i0;
     }
 }
 
@@ -405,11 +406,11 @@ cudaError_t search_n(const float2 *St, int T, const float2 *Sp, const int *degen
 
 template <int N>
 cudaError_t pair_peak_n(const float2 *St, const int *tidx, const float2 *Sp, const int *degen,
-                        const int *active, int P, float *peak, float *shift, cudaStream_t st) {
+                        const int *active, int P, float *peak, float *shift, int *argmax, cudaStream_t st) {
     size_t sm = smem_bytes_generic<N>();
     cudaError_t e = set_smem(k_pair_peak<N>, sm);
     if (e != cudaSuccess) return e;
-    k_pair_peak<N><<<(P + 1) / 2, kThreads, sm, st>>>(St, tidx, Sp, degen, active, P, peak, shift);
+    k_pair_peak<N><<<(P + 1) / 2, kThreads, sm, st>>>(St, tidx, Sp, degen, active, P, peak, shift, argmax);
     return cudaGetLastError();
 }
 
@@ -463,13 +464,13 @@ cudaError_t launch_search_list(int N, const float2 *St, const int *cand, int kc,
 
 cudaError_t launch_pair_peak(int N, const float2 *St, const int *tidx, const float2 *Sp,
                              const int *degen, const int *active, int P, float *peak, float *shift,
-                             cudaStream_t st) {
+                             cudaStream_t st, int *argmax) {
     if (P <= 0) return cudaSuccess;
     switch (N) {
-        case 16: return pair_peak_n<16>(St, tidx, Sp, degen, active, P, peak, shift, st);
-        case 32: return pair_peak_n<32>(St, tidx, Sp, degen, active, P, peak, shift, st);
-        case 64: return pair_peak_n<64>(St, tidx, Sp, degen, active, P, peak, shift, st);
-        case 128: return pair_peak_n<128>(St, tidx, Sp, degen, active, P, peak, shift, st);
+        case 16: return pair_peak_n<16>(St, tidx, Sp, degen, active, P, peak, shift, argmax, st);
+        case 32: return pair_peak_n<32>(St, tidx, Sp, degen, active, P, peak, shift, argmax, st);
+        case 64: return pair_peak_n<64>(St, tidx, Sp, degen, active, P, peak, shift, argmax, st);
+        case 128: return pair_peak_n<128>(St, tidx, Sp, degen, active, P, peak, shift, argmax, st);
         default: return cudaErrorInvalidValue;
     }
 }

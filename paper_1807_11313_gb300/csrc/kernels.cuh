@@ -47,7 +47,8 @@ cudaError_t launch_search_c256(const float2 *St, int T, const float2 *Sp, const 
 size_t c256_smem_bytes();
 // N = 256 single-surface peak on clusters of four CTAs (two patterns per pass)
 cudaError_t launch_pair_peak_c256(const float2 *St, const int *tidx, const float2 *Sp, const int *degen,
-                                  const int *active, int P, float *peak, float *shift, cudaStream_t st);
+                                  const int *active, int P, float *peak, float *shift, cudaStream_t st,
+                                  int *argmax = nullptr);
 // N = 256 pre-processing on clusters of four CTAs (one image per cluster)
 cudaError_t launch_prep_c256(const float *img, int P, const PrepArgs &a, float2 *spec, float *spatial, int *degen,
                              const int *active, cudaStream_t st);
@@ -86,10 +87,16 @@ cudaError_t launch_search_maps(const MapDev *maps, const WorkItem *items, int n_
 // N = 128: library half spectra -> the search kernel's packed layout
 cudaError_t launch_pack_search_layout(const float2 *spectra, int T, int N, float2 *packed, cudaStream_t st);
 
-// peak of one surface per pattern: template spectrum = St + (tidx ? tidx[p] : p) * H
+// peak of one surface per pattern: template spectrum = St + (tidx ? tidx[p] : p) * H;
+// argmax (nullable) receives the integer peak's row-major index
 cudaError_t launch_pair_peak(int N, const float2 *St, const int *tidx, const float2 *Sp,
                              const int *degen, const int *active, int P, float *peak, float *shift,
-                             cudaStream_t st);
+                             cudaStream_t st, int *argmax = nullptr);
+// up-sampled peak (U >= 2): the correlation's Fourier series on a +-1 px grid of step 1/U
+// around argmax[p]; overwrites peak and shift of every computed pattern
+cudaError_t launch_upsample_peak(int N, const float2 *St, const int *tidx, const float2 *Sp, const int *degen,
+                                 const int *active, int P, int U, const int *argmax, float *peak, float *shift,
+                                 cudaStream_t st);
 
 cudaError_t launch_keys_to_best(const unsigned long long *keys, int P, int *best, cudaStream_t st);
 

@@ -85,7 +85,11 @@ extern "C" int xcf_index_noalloc(xcf_ctx *ctx, const xcf_library *lib, const flo
     }
     const int n = lib->N;
     if (n > 128) {
-        ctx->err = "xcf_index_noalloc: detectors of side 256 are searched with work arrays; use xcf_index";
+        ctx->err = "xcf_index_noalloc: detectors of side 256 are searched on thread-block clusters; use xcf_index";
+        return XCF_ERR_UNIMPLEMENTED;
+    }
+    if (ctx->opt.upsample >= 2) {
+        ctx->err = "xcf_index_noalloc: the up-sampled peak needs scratch; use xcf_index";
         return XCF_ERR_UNIMPLEMENTED;
     }
     const int pmax = xcf_noalloc_max_patterns(n);
