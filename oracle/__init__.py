@@ -40,14 +40,14 @@ def build(force: bool = False) -> str:
 class Opts(C.Structure):
     _fields_ = [("window", C.c_int32), ("sigma_hp", C.c_double), ("sigma_lp", C.c_double),
                 ("lp_nr", C.c_int32), ("lp_neta", C.c_int32), ("lp_rmin", C.c_double),
-                ("lp_rmax", C.c_double), ("upsample", C.c_int32)]
+                ("lp_rmax", C.c_double), ("upsample", C.c_int32), ("interp", C.c_int32)]
 
 
 def default_opts(n: int, **kw) -> Opts:
     """Defaults: Hann window, sigma_hp = 2, sigma_lp = n/4 cycles per image,
     log-polar n/4 radii x 2n angles over r in [n/4, n/2 - 1] px."""
     d = dict(window=1, sigma_hp=2.0, sigma_lp=n / 4.0, lp_nr=max(n // 4, 2), lp_neta=2 * n,
-             lp_rmin=n / 4.0, lp_rmax=n / 2.0 - 1.0, upsample=0)
+             lp_rmin=n / 4.0, lp_rmax=n / 2.0 - 1.0, upsample=0, interp=0)
     d.update(kw)
     return Opts(**d)
 
@@ -88,7 +88,8 @@ def _lib_handle():
                 "orc_quat_to_matrix": ([_D, _D], None),
                 "orc_project": ([_F, C.c_int, _D, _D, C.c_double, C.c_double, C.c_int, _D], None),
                 "orc_project_many": ([_F, C.c_int, _D, _D, C.c_int, C.c_double, C.c_double,
-                                      C.c_int, _D], None),
+                                      C.c_int, _D, C.c_int], None),
+                "orc_grid_interp": ([_F, C.c_int, C.c_double, C.c_double, C.c_int], C.c_double),
                 "orc_qmul": ([_D, _D, _D], None),
                 "orc_cubic_ops": ([_D], None),
                 "orc_disorientation": ([_D, _D], C.c_double),
@@ -318,14 +319,21 @@ def project(master, q, pc, n, sample_tilt=70.0, detector_tilt=0.0):
     return out
 
 
-def project_many(master, quats, pcs, n, sample_tilt=70.0, detector_tilt=0.0):
+def project_many(master, quats, pcs, n, sample_tilt=70.0, detector_tilt=0.0, interp=0):
+    """interp: master lookup, 0 bilinear, 1 bicubic (Keys, a = -1/2)."""
     master, quats = _f32(master), _f64(quats)
     pcs = _f64(np.broadcast_to(np.asarray(pcs, np.float64), (quats.shape[0], 3)))
     P = quats.shape[0]
     out = np.empty((P, n, n))
     _lib_handle().orc_project_many(_f(master), master.shape[1], _d(quats), _d(pcs), P,
-                                   sample_tilt, detector_tilt, n, _d(out))
+                                   sample_tilt, detector_tilt, n, _d(out), int(interp))
     return out
+
+
+def grid_interp(grid, fx, fy, interp):
+    """One hemisphere's grid [M, M] at grid coordinates (cell centres at integers)."""
+    g = _f32(grid)
+    return _lib_handle().orc_grid_interp(_f(g), g.shape[0], float(fx), float(fy), int(interp))
 
 
 # ---------------------------------------------------------------- symmetry

@@ -40,6 +40,7 @@ typedef struct {
     double lp_rmin;      /* smallest radius, pixels                            */
     double lp_rmax;      /* largest radius, pixels                             */
     int32_t upsample;    /* 0: 3-point parabola; U >= 2: up-sampled peak       */
+    int32_t interp;      /* master lookup: 0 bilinear, 1 bicubic (Keys)        */
 } orc_opts;
 
 typedef struct {
@@ -439,6 +440,58 @@ void orc_lambert_inverse(double X, double Y, double v[3]) {
  * bilinear interpolation between the four nearest cell centres of the
  * hemisphere's M x M grid (cell (a, b) centred at X = L(2(b+.5)/M - 1),
  * Y = L(2(a+.5)/M - 1)), clamped at the square's edge.  master: [2, M, M]. */
+/* Keys' cubic convolution weight (a = -1/2), the interpolation kernel of the
+ * paper's bicubic reprojection (its exact kernel is not given; reading). */
+static double keys_w(double t) {
+    t = fabs(t);
+    const double a = -0.5;
+    if (t <= 1.0) return (a + 2.0) * t * t * t - (a + 3.0) * t * t + 1.0;
+    if (t < 2.0) return a * t * t * t - 5.0 * a * t * t + 8.0 * a * t - 4.0 * a;
+    return 0.0;
+}
+
+/* value of one hemisphere's M x M grid at grid coordinates (fx, fy) (cell
+ * centres at integers), clamped to [0, M - 1]; interp 0 bilinear, 1 bicubic
+ * (4 x 4 cell centres, indices clamped at the edges) */
+double orc_grid_interp(const float *g, int M, double fx, double fy, int interp) {
+    if (fx < 0) fx = 0;
+    if (fx > M - 1) fx = M - 1;
+    if (fy < 0) fy = 0;
+    if (fy > M - 1) fy = M - 1;
+    if (interp == 1) {
+        const int i0 = (int)floor(fx), j0 = (int)floor(fy);
+        double s = 0.0;
+        for (int dj = -1; dj <= 2; ++dj) {
+            int j = j0 + dj;
+            j = j < 0 ? 0 : (j > M - 1 ? M - 1 : j);
+            const double wy = keys_w(fy - (j0 + dj));
+            for (int di = -1; di <= 2; ++di) {
+                int i = i0 + di;
+                i = i < 0 ? 0 : (i > M - 1 ? M - 1 : i);
+                s += wy * keys_w(fx - (i0 + di)) * g[(long)j * M + i];
+            }
+        }
+        return s;
+    }
+    int i0 = (int)floor(fx), j0 = (int)floor(fy);
+    if (i0 > M - 2) i0 = M - 2;
+    if (j0 > M - 2) j0 = M - 2;
+    double tx = fx - i0, ty = fy - j0;
+    double a = g[(long)j0 * M + i0], b = g[(long)j0 * M + i0 + 1];
+    double c = g[(long)(j0 + 1) * M + i0], d = g[(long)(j0 + 1) * M + i0 + 1];
+    return (1 - ty) * ((1 - tx) * a + tx * b) + ty * ((1 - tx) * c + tx * d);
+}
+
+/* master lookup with the chosen interpolation (0 bilinear, 1 bicubic) */
+double orc_master_lookup_interp(const float *master, int M, const double v[3], int interp) {
+    double X, Y;
+    orc_lambert_forward(v, &X, &Y);
+    double L = sqrt(ORC_PI / 2.0);
+    double fx = (X / L + 1.0) * M / 2.0 - 0.5;
+    double fy = (Y / L + 1.0) * M / 2.0 - 0.5;
+    return orc_grid_interp(master + (v[2] >= 0.0 ? 0 : (long)M * M), M, fx, fy, interp);
+}
+
 double orc_master_lookup(const float *master, int M, const double v[3]) {
     double X, Y;
     orc_lambert_forward(v, &X, &Y);
@@ -476,8 +529,16 @@ void orc_quat_to_matrix(const double q[4], double R[9]) {
  * by R(q).  The paper interpolates bicubically on a stereographic master;
  * reading: bilinear on the equal-area master grid.  pc is the (cropped)
  * pattern centre. */
+void orc_project_interp(const float *master, int M, const double q[4], const double pc[3],
+                        double sample_tilt_deg, double detector_tilt_deg, int n, double *out, int interp);
 void orc_project(const float *master, int M, const double q[4], const double pc[3],
                  double sample_tilt_deg, double detector_tilt_deg, int n, double *out) {
+    orc_project_interp(master, M, q, pc, sample_tilt_deg, detector_tilt_deg, n, out, 0);
+}
+
+/* the projection with the master interpolation of choice (0 bilinear, 1 bicubic) */
+void orc_project_interp(const float *master, int M, const double q[4], const double pc[3],
+                        double sample_tilt_deg, double detector_tilt_deg, int n, double *out, int interp) {
     double R[9];
     orc_quat_to_matrix(q, R);
     double al = (90.0 - sample_tilt_deg + detector_tilt_deg) * ORC_PI / 180.0;
@@ -493,18 +554,18 @@ void orc_project(const float *master, int M, const double q[4], const double pc[
             double c[3] = {R[0] * s[0] + R[1] * s[1] + R[2] * s[2],
                            R[3] * s[0] + R[4] * s[1] + R[5] * s[2],
                            R[6] * s[0] + R[7] * s[1] + R[8] * s[2]};
-            out[(long)i * n + j] = orc_master_lookup(master, M, c);
+            out[(long)i * n + j] = orc_master_lookup_interp(master, M, c, interp);
         }
 }
 
 /* Many projections, one thread per image. quats [P,4], pcs [P,3]. */
 void orc_project_many(const float *master, int M, const double *quats, const double *pcs,
                       int P, double sample_tilt_deg, double detector_tilt_deg, int n,
-                      double *out) {
+                      double *out, int interp) {
 #pragma omp parallel for schedule(dynamic, 4)
     for (int p = 0; p < P; ++p)
-        orc_project(master, M, quats + 4L * p, pcs + 3L * p, sample_tilt_deg,
-                    detector_tilt_deg, n, out + (long)p * n * n);
+        orc_project_interp(master, M, quats + 4L * p, pcs + 3L * p, sample_tilt_deg,
+                           detector_tilt_deg, n, out + (long)p * n * n, interp);
 }
 
 /* Many pre-processings, one thread per image. imgs [P, n, n]. */
@@ -708,7 +769,7 @@ int orc_refine_one(const float *master, int M, const double pc[3], double sample
     int it = 0;
     while (it < max_it) {
         /* X/Y step */
-        orc_project(master, M, q, pc, sample_tilt_deg, detector_tilt_deg, n, img);
+        orc_project_interp(master, M, q, pc, sample_tilt_deg, detector_tilt_deg, n, img, o->interp);
         orc_prep(img, n, o, ST, NULL);
         orc_xcf_surface(ST, SP, n, r);
         int sy, sx;
@@ -724,7 +785,7 @@ int orc_refine_one(const float *master, int M, const double pc[3], double sample
         qmul(qx, qy, qQ);
         apply_detector_rotation(q, qQ, al, q1);
         /* Z step */
-        orc_project(master, M, q1, pc, sample_tilt_deg, detector_tilt_deg, n, img);
+        orc_project_interp(master, M, q1, pc, sample_tilt_deg, detector_tilt_deg, n, img, o->interp);
         orc_prep(img, n, o, ST, yT);
         orc_logpolar(yT, n, nr, ne, o->lp_rmin, o->lp_rmax, lpT);
         double zpk;
