@@ -63,6 +63,10 @@ typedef struct {
                            on a +-1 px grid of step 1/U around the integer peak (the
                            paper's peak "up-sampling"); applies to every peak step
                            (xcf_index shifts and the refinement's X/Y shifts)       */
+    int32_t master_interp; /* master-pattern lookup of every projection: 0 = bilinear
+                              on the equal-area grid (default); 1 = bicubic (Keys'
+                              cubic convolution, a = -1/2), the paper's bicubic
+                              reprojection on the same grid                         */
 } xcf_options;
 
 /* Detector geometry of a map (or of a library). */

@@ -149,8 +149,9 @@ PrepArgs prep_args(const xcf_geometry *g, const Crop &c, const Resolved &r) {
 
 // square n x n template images on the cropped detector (the source image of
 // the pre-processing is then the n x n image itself: W = H = n, no offset)
-ProjArgs proj_args_cropped(const xcf_geometry *g, const Crop &c) {
+ProjArgs proj_args_cropped(const xcf_geometry *g, const Crop &c, int interp) {
     ProjArgs a;
+    a.interp = interp;
     a.W = g->width;
     a.H = g->height;
     a.ox = c.ox;
@@ -285,7 +286,7 @@ int refine_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, in
     if ((rc = scratch_t(ctx, S_ACTIVE, P, &active))) return rc;
     if ((rc = scratch_t(ctx, S_Q1, (size_t)P * 4, &q1))) return rc;
     const PrepArgs pa = prep_args(g, c, r), ps = prep_args_square(c, r);
-    const ProjArgs pj = proj_args_cropped(g, c);
+    const ProjArgs pj = proj_args_cropped(g, c, ctx->opt.master_interp);
     const double alpha = alpha_of(g);
     if (!patterns_ready)   // else sp, yp, degen already hold this chunk's patterns
         XCF_LAUNCH(XCF_STAGE_PREP, st, run_prep(ctx,patterns, P, pa, sp, yp, degen, nullptr, st), "prep patterns");
@@ -351,6 +352,7 @@ int xcf_options_default(xcf_options *o) {
     o->max_iter = 2;
     o->tol_deg = 1e-3;
     o->upsample = 0;
+    o->master_interp = 0;
     return XCF_OK;
 }
 
@@ -373,6 +375,7 @@ int xcf_create(xcf_ctx **out, const xcf_options *opt, int device) {
         o = *opt;
         if (o.window < 0 || o.window > 1 || o.max_iter < 0 || o.sigma_hp < 0) return XCF_ERR_ARG;
         if (o.upsample != 0 && (o.upsample < 2 || o.upsample > 20)) return XCF_ERR_ARG;
+        if (o.master_interp < 0 || o.master_interp > 1) return XCF_ERR_ARG;
     } else {
         xcf_options_default(&o);
     }
@@ -420,6 +423,7 @@ int xcf_project(xcf_ctx *ctx, const float *master, int32_t M, const double *quat
     if (g->width <= 0 || g->height <= 0) return fail(ctx, XCF_ERR_ARG, "xcf_project: bad detector size");
     cudaSetDevice(ctx->device);
     ProjArgs a;
+    a.interp = ctx->opt.master_interp;
     a.W = g->width;
     a.H = g->height;
     a.ox = 0;
@@ -492,7 +496,7 @@ int xcf_build_library(xcf_ctx *ctx, const float *master, int32_t M, const double
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(lib->master, master, sizeof(float) * 2 * (size_t)M * M, cudaMemcpyDeviceToDevice, st);
     // project and pre-process in chunks (bounded image scratch)
-    const ProjArgs pj = proj_args_cropped(g, c);
+    const ProjArgs pj = proj_args_cropped(g, c, ctx->opt.master_interp);
     const PrepArgs ps = prep_args_square(c, r);
     int *degen = nullptr;
     float *img = nullptr;
@@ -851,7 +855,7 @@ int make_screen_images(xcf_ctx *ctx, xcf_library *lib, const float *images, cuda
             if ((rc = scratch_t(ctx, S_IMG, nn * nt, &img))) return rc;
             XCF_LAUNCH(XCF_STAGE_PROJECT, st,
                        launch_project(lib->master, lib->M, lib->quats + 4 * (size_t)t0, nullptr, nullptr, nt,
-                                      proj_args_cropped(g, c), img, st),
+                                      proj_args_cropped(g, c, ctx->opt.master_interp), img, st),
                        "screen project");
             XCF_LAUNCH(XCF_STAGE_PREP, st,
                        run_prep(ctx, img, nt, prep_args_square(c, r), spec, spat, degen, nullptr, st), "screen prep");
@@ -1262,7 +1266,7 @@ int xcf_index_learned(xcf_ctx *ctx, xcf_net *net, const xcf_library *lib, const 
     const Resolved r = resolve(ctx->opt, c.n);
     const int n = c.n, H = n * (n / 2 + 1), k = net->k;
     const size_t img = (size_t)g->width * g->height;
-    const ProjArgs pj = proj_args_cropped(g, c);
+    const ProjArgs pj = proj_args_cropped(g, c, ctx->opt.master_interp);
     const PrepArgs pa = prep_args(g, c, r), ps = prep_args_square(c, r);
     for (int p0 = 0; p0 < P; p0 += kChunk) {
         const int np = P - p0 < kChunk ? P - p0 : kChunk;

@@ -42,10 +42,19 @@ __device__ __forceinline__ Q rotate_in_detector(const Q &q, const Q &R, double a
 }
 
 // ------------------------------------------------------ Lambert lookup
-// Rosca equal-area square of a hemisphere, then bilinear interpolation of
-// the M x M grid of cell centres, clamped at the edges.
+// Keys' cubic convolution weight, a = -1/2
+__device__ __forceinline__ float keys_weight(float t) {
+    t = fabsf(t);
+    if (t <= 1.f) return (1.5f * t - 2.5f) * t * t + 1.f;
+    if (t < 2.f) return ((-0.5f * t + 2.5f) * t - 4.f) * t + 2.f;
+    return 0.f;
+}
+
+// Rosca equal-area square of a hemisphere, then bilinear (interp 0) or
+// bicubic (interp 1, Keys) interpolation of the M x M grid of cell centres,
+// clamped at the edges.
 __device__ __forceinline__ float master_lookup(const float *__restrict__ master, int M, float x, float y,
-                                               float z) {
+                                               float z, int interp = 0) {
     const float az = fabsf(z);
     const float s2 = x * x + y * y;
     float X = 0.f, Y = 0.f;
@@ -68,6 +77,24 @@ __device__ __forceinline__ float master_lookup(const float *__restrict__ master,
     float fy = (Y * invL + 1.f) * (0.5f * M) - 0.5f;
     fx = fminf(fmaxf(fx, 0.f), (float)(M - 1));
     fy = fminf(fmaxf(fy, 0.f), (float)(M - 1));
+    if (interp == 1) {
+        const float *g = master + (z >= 0.f ? 0 : (size_t)M * M);
+        const int i0 = (int)floorf(fx), j0 = (int)floorf(fy);
+        float s = 0.f;
+#pragma unroll
+        for (int dj = -1; dj <= 2; ++dj) {
+            const int j = min(max(j0 + dj, 0), M - 1);
+            const float wy = keys_weight(fy - (float)(j0 + dj));
+            float row = 0.f;
+#pragma unroll
+            for (int di = -1; di <= 2; ++di) {
+                const int i = min(max(i0 + di, 0), M - 1);
+                row = fmaf(keys_weight(fx - (float)(i0 + di)), __ldg(g + (size_t)j * M + i), row);
+            }
+            s = fmaf(wy, row, s);
+        }
+        return s;
+    }
     int i0 = min((int)floorf(fx), M - 2), j0 = min((int)floorf(fy), M - 2);
     const float tx = fx - i0, ty = fy - j0;
     const float *g = master + (z >= 0.f ? 0 : (size_t)M * M) + (size_t)j0 * M + i0;
@@ -118,7 +145,7 @@ __global__ void __launch_bounds__(256) k_project(const float *__restrict__ maste
         const float cx = G[0] * dx + G[1] * dy + G[2] * dz;
         const float cy = G[3] * dx + G[4] * dy + G[5] * dz;
         const float cz = G[6] * dx + G[7] * dy + G[8] * dz;
-        dst[idx] = master_lookup(master, M, cx, cy, cz);
+        dst[idx] = master_lookup(master, M, cx, cy, cz, a.interp);
     }
 }
 

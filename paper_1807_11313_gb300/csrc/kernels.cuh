@@ -18,6 +18,7 @@ struct ProjArgs {
     int ox, oy, nx, ny;       // output region: detector pixels [oy, oy+ny) x [ox, ox+nx)
     double pcx, pcy, pcz;     // default pattern centre (when pcs == nullptr)
     double alpha;             // detector -> sample rotation about x, radians
+    int interp = 0;           // master lookup: 0 bilinear, 1 bicubic (Keys)
 };
 
 // pre-processing: images [P, H, W] -> half spectra [P, N, N/2+1] (+ spatial [P, N, N])

@@ -323,3 +323,18 @@ def test_pattern_at_library_orientation_returns_that_template(px, ctx, n):
     np.testing.assert_allclose(peak, 1.0, atol=2e-5)
     np.testing.assert_allclose(shift, 0.0, atol=1e-3)
     lib.close()
+
+
+def test_bicubic_projection_matches_oracle(px, orc):
+    """Projection with the bicubic master lookup (Keys, a = -1/2) against the oracle."""
+    n, P = 64, 5
+    master = synth.master_pattern("bcc", 256)
+    q = synth.random_quaternions(P, 81)
+    pcs = synth.jittered_pcs(P, 82)
+    ctx = px.Context(master_interp=1)
+    got = px.xcf_project(ctx, dev(master), dev(q), px.geometry(n, n, PC0), pcs=dev(pcs)).cpu().numpy()
+    ref = orc.project_many(master, q, pcs, n, interp=1)
+    lin = orc.project_many(master, q, pcs, n, interp=0)
+    _proj_check(got, ref, master)                         # FP32 ray and Lambert maths, as for bilinear
+    assert np.abs(got - lin).max() > 1e-3 * float(master.max() - master.min())   # the option is in effect
+    ctx.close()
