@@ -385,6 +385,17 @@ int xcf_index_learned(xcf_ctx *ctx, xcf_net *net, const xcf_library *lib, const 
 #define XCF_STAGE_NET      8   /* proposal network: forward, backward, optimiser  */
 #define XCF_NUM_STAGES     9
 
+/* Cap the context's device scratch (the sum of its grow-only buffers) at
+ * `bytes` (0 = no cap).  A call that would grow the scratch past the cap
+ * fails with XCF_ERR_OOM before allocating, and the context stays usable (for
+ * calls that fit, or after raising the cap).  Lets a caller share the device
+ * with other work, and lets tests exercise the out-of-memory path without
+ * exhausting the device.  Host only. */
+int xcf_set_scratch_limit(xcf_ctx *ctx, uint64_t bytes);
+
+/* Bytes of device scratch the context holds now.  Host only. */
+int xcf_scratch_bytes(const xcf_ctx *ctx, uint64_t *bytes);
+
 /* Turn event timing on (1) or off (0).  Host only. */
 int xcf_profile_enable(xcf_ctx *ctx, int on);
 

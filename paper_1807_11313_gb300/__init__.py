@@ -13,5 +13,5 @@ from .xcf import (  # noqa: F401
     xcf_profile_enable, xcf_profile_read, STAGES, xcf_index_noalloc, xcf_noalloc_max_patterns,
     xcf_build_library_ex, xcf_screen_topk, xcf_rescore, xcf_refine_best, xcf_index_maps, XCF_LIB_SCREEN,
     XCF_MAPS_GRAPH, Net, xcf_net_num_params, xcf_net_create, xcf_net_forward, xcf_net_loss_grad, xcf_net_adam,
-    xcf_propose, xcf_index_learned, xcf_index_precision,
+    xcf_propose, xcf_index_learned, xcf_index_precision, xcf_set_scratch_limit, xcf_scratch_bytes,
 )

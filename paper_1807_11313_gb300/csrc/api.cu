@@ -68,6 +68,14 @@ void drop_graph(xcf_ctx *ctx) {
 int scratch(xcf_ctx *ctx, int slot, size_t bytes, void **out) {
     if (bytes == 0) bytes = 16;
     if (ctx->cap[slot] < bytes) {
+        if (ctx->scratch_limit) {   // the caller's cap on the arena (0 = none)
+            size_t total = bytes;
+            for (int i = 0; i < S_COUNT; ++i)
+                if (i != slot) total += ctx->cap[i];
+            if (total > ctx->scratch_limit)
+                return fail(ctx, XCF_ERR_OOM, "scratch of " + std::to_string(bytes) +
+                                                  " bytes would exceed the context's limit");
+        }
         drop_graph(ctx);
         if (ctx->buf[slot]) cudaFree(ctx->buf[slot]);
         ctx->buf[slot] = nullptr;
@@ -777,6 +785,20 @@ int xcf_index_refine_host(xcf_ctx *ctx, const xcf_library *lib, const float *pat
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
     return status;
+}
+
+int xcf_set_scratch_limit(xcf_ctx *ctx, uint64_t bytes) {
+    if (!ctx) return XCF_ERR_ARG;
+    ctx->scratch_limit = (size_t)bytes;
+    return XCF_OK;
+}
+
+int xcf_scratch_bytes(const xcf_ctx *ctx, uint64_t *bytes) {
+    if (!ctx || !bytes) return XCF_ERR_ARG;
+    uint64_t t = 0;
+    for (int i = 0; i < S_COUNT; ++i) t += ctx->cap[i];
+    *bytes = t;
+    return XCF_OK;
 }
 
 int xcf_profile_enable(xcf_ctx *ctx, int on) {

@@ -59,6 +59,7 @@ struct xcf_ctx {
     std::string err;
     void *buf[xcf_internal::S_COUNT] = {};
     size_t cap[xcf_internal::S_COUNT] = {};
+    size_t scratch_limit = 0;   // 0: no cap on the sum of cap[]
     // profiling
     bool timing = false;
     int64_t launches[XCF_NUM_STAGES] = {};

@@ -96,6 +96,8 @@ _SIGS = {
     "xcf_net_adam": ([_P, _P, C.c_float, C.c_float, C.c_float, C.c_float, _P], C.c_int),
     "xcf_propose": ([_P, _P, _P, _I32, C.POINTER(xcf_geometry), _P, _P], C.c_int),
     "xcf_index_learned": ([_P, _P, _P, _P, _I32, _P, C.c_float, _P, _P, _P, _P, _P], C.c_int),
+    "xcf_set_scratch_limit": ([_P, C.c_uint64], C.c_int),
+    "xcf_scratch_bytes": ([_P, C.POINTER(C.c_uint64)], C.c_int),
     "xcf_profile_enable": ([_P, C.c_int], C.c_int),
     "xcf_profile_read": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int], C.c_int),
 }
@@ -353,6 +355,16 @@ def xcf_index_refine_host(ctx: Context, lib: Library, patterns, pcs=None, chunk=
         _hptr(out["quats"], torch.float64, "quats"), _hptr(out["rpeak"], torch.float32, "rpeak"),
         _hptr(out["iters"], torch.int32, "iters")), ctx.handle)
     return out
+
+
+def xcf_set_scratch_limit(ctx: Context, nbytes: int):
+    _check(load().xcf_set_scratch_limit(ctx.handle, int(nbytes)), ctx.handle)
+
+
+def xcf_scratch_bytes(ctx: Context) -> int:
+    b = C.c_uint64()
+    _check(load().xcf_scratch_bytes(ctx.handle, C.byref(b)), ctx.handle)
+    return int(b.value)
 
 
 def xcf_profile_enable(ctx: Context, on: bool = True):

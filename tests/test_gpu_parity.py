@@ -338,3 +338,28 @@ def test_bicubic_projection_matches_oracle(px, orc):
     _proj_check(got, ref, master)                         # FP32 ray and Lambert maths, as for bilinear
     assert np.abs(got - lin).max() > 1e-3 * float(master.max() - master.min())   # the option is in effect
     ctx.close()
+
+
+def test_scratch_limit_gives_oom_and_context_survives(px):
+    """A cap on the context's scratch turns a too-large call into XCF_ERR_OOM
+    before any allocation; the same context then serves calls that fit."""
+    n = 64
+    ctx = px.Context()
+    lq = synth.random_quaternions(4, 91)
+    master = dev(synth.master_pattern("bcc", 128))
+    lib = px.xcf_build_library(ctx, master, dev(lq), px.geometry(n, n, PC0))
+    pats = px.xcf_project(ctx, master, dev(lq), px.geometry(n, n, PC0))
+    best, _, _ = px.xcf_index(ctx, lib, pats)             # the small call's scratch is now held
+    used = px.xcf_scratch_bytes(ctx)
+    px.xcf_set_scratch_limit(ctx, used + 1024)
+    big = pats.repeat(2000, 1, 1).contiguous()           # needs far more scratch
+    with pytest.raises(px.XcfError) as e:
+        px.xcf_index(ctx, lib, big)
+    assert e.value.code == -3 and px.xcf_scratch_bytes(ctx) <= used + 1024
+    best, peak, _ = px.xcf_index(ctx, lib, pats)          # fits in what is held
+    assert torch.equal(best.cpu(), torch.arange(4, dtype=torch.int32))
+    px.xcf_set_scratch_limit(ctx, 0)                      # lifted: the large call now runs
+    best, _, _ = px.xcf_index(ctx, lib, big)
+    assert torch.equal(best[:4].cpu(), torch.arange(4, dtype=torch.int32))
+    lib.close()
+    ctx.close()
