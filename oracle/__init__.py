@@ -102,6 +102,13 @@ def _lib_handle():
                                      C.c_int, C.c_int, _D, C.c_int, C.c_double, _D, _D, _I], None),
                 "orc_bf16_round": ([C.c_double], C.c_double),
                 "orc_screen": ([_D, C.c_int, _D, C.c_int, C.c_long, C.c_int, _D], None),
+                "orc_ndp_normalise": ([_D, C.c_long, _D], C.c_int),
+                "orc_ndp": ([_D, _D, C.c_long], C.c_double),
+                "orc_ndp_index": ([_D, C.c_int, _D, C.c_int, C.c_long, _I, _D, _D], None),
+                "orc_scan_orientation": ([_D, C.c_int, C.c_double, C.c_double, C.c_double, _D], None),
+                "orc_rotation_scan": ([_F, C.c_int, C.c_int, _D, _D, C.c_double, C.c_double, C.POINTER(Opts),
+                                       _D, C.c_int, C.c_double, _D, _D], None),
+                "orc_fwhm": ([_D, C.c_int, C.c_double], C.c_double),
                 "orc_cnn_num_params": ([C.c_int], C.c_long),
                 "orc_cnn_standardise": ([_D, C.c_int, _D], None),
                 "orc_conv3x3s2": ([_D, C.c_int, C.c_int, _D, _D, C.c_int, _D], None),
@@ -373,6 +380,64 @@ def screen(yp, yt, bf16=True):
     S = np.empty((yp.shape[0], yt.shape[0]))
     _lib_handle().orc_screen(_d(yp), yp.shape[0], _d(yt), yt.shape[0], yp.shape[1], 1 if bf16 else 0, _d(S))
     return S
+
+
+# ------------------------------------------------- NDP and peak-width scans
+def ndp_normalise(img):
+    """Contrast normalisation (zero mean, unit population std) -> (out, degenerate)."""
+    img = _f64(img)
+    out = np.empty_like(img)
+    deg = _lib_handle().orc_ndp_normalise(_d(img), img.size, _d(out))
+    return out, bool(deg)
+
+
+def ndp(a, b):
+    """Eq. 1 between two images of the same size."""
+    a, b = _f64(a), _f64(b)
+    assert a.size == b.size
+    return _lib_handle().orc_ndp(_d(a), _d(b), a.size)
+
+
+def ndp_index(pats, tmpl, want_all=False):
+    """NDP dictionary indexing: pats [P, ...], tmpl [T, ...] images.
+    -> best [P] int32 (-1 for a constant pattern), score [P], scores [P, T] or None."""
+    pats = _f64(np.asarray(pats).reshape(len(pats), -1))
+    tmpl = _f64(np.asarray(tmpl).reshape(len(tmpl), -1))
+    P, T, d = pats.shape[0], tmpl.shape[0], pats.shape[1]
+    best = np.empty(P, np.int32)
+    score = np.empty(P)
+    scores = np.empty((P, T)) if want_all else None
+    _lib_handle().orc_ndp_index(_d(pats), P, _d(tmpl), T, d, _i(best), _d(score),
+                                _d(scores) if scores is not None else None)
+    return best, score, scores
+
+
+def scan_orientation(q, axis, theta_rad, sample_tilt=70.0, detector_tilt=0.0):
+    q = _f64(q)
+    out = np.empty(4)
+    _lib_handle().orc_scan_orientation(_d(q), int(axis), float(theta_rad), sample_tilt, detector_tilt, _d(out))
+    return out
+
+
+def rotation_scan(master, q, pc_ref, n, nh, step_deg, pc_test=None, opts=None, sample_tilt=70.0,
+                  detector_tilt=0.0):
+    """Fig. 3 / 4 rotation experiment on an n x n screen -> (ndp [3, L], xcf [3, L]), L = 2 nh + 1."""
+    master, q = _f32(master), _f64(q)
+    pc_ref = _f64(pc_ref)
+    pc_test = pc_ref if pc_test is None else _f64(pc_test)
+    o = opts or default_opts(n)
+    L = 2 * nh + 1
+    ndp_out, xcf_out = np.empty((3, L)), np.empty((3, L))
+    _lib_handle().orc_rotation_scan(_f(master), master.shape[1], n, _d(pc_ref), _d(pc_test), sample_tilt,
+                                    detector_tilt, C.byref(o), _d(q), int(nh), float(step_deg), _d(ndp_out),
+                                    _d(xcf_out))
+    return ndp_out, xcf_out
+
+
+def fwhm(curve, step):
+    """Full width at half maximum of a centred curve (units of step); -1 if unresolved."""
+    c = _f64(curve)
+    return _lib_handle().orc_fwhm(_d(c), c.size, float(step))
 
 
 # ---------------------------------------------------------------- refinement

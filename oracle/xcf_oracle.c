@@ -857,3 +857,159 @@ void orc_screen(const double *yp, int P, const double *yt, int T, long K, int bf
             S[(long)p * T + t] = s;
         }
 }
+
+/* ---------------------------------------------------------------------- */
+/* normalised dot product (Eq. 1) and the peak-width experiments of the     */
+/* sampling-frequency section (Figs. 3 and 4)                              */
+/* ---------------------------------------------------------------------- */
+
+/* Contrast normalisation of the NDP (NDP section; the simulation set-up of
+ * the sampling-frequency section): zero mean and unit population standard
+ * deviation over the d pixels.  Returns 1 and zeros for a constant image (the
+ * same degeneracy test as orc_prep). */
+int orc_ndp_normalise(const double *img, long d, double *out) {
+    double mean = 0.0;
+    for (long i = 0; i < d; ++i) mean += img[i];
+    mean /= d;
+    double var = 0.0;
+    for (long i = 0; i < d; ++i) var += (img[i] - mean) * (img[i] - mean);
+    var /= d;
+    double sd = sqrt(var);
+    if (!(sd > 1e-12 * (1.0 + fabs(mean)))) {
+        memset(out, 0, sizeof(double) * d);
+        return 1;
+    }
+    for (long i = 0; i < d; ++i) out[i] = (img[i] - mean) / sd;
+    return 0;
+}
+
+/* Eq. 1 for one pair: the mean over the d pixels of the products of the two
+ * contrast-normalised images.  Reading: the printed formula carries both a
+ * 1/d and the two vector norms, which would give 1/d for identical images,
+ * while the text fixes that value at 1; with unit-variance images the norms
+ * are sqrt(d) and one normalisation is kept, making the NDP the cosine of the
+ * angle between the mean-removed pixel vectors.  0 if either image is
+ * constant. */
+double orc_ndp(const double *a, const double *b, long d) {
+    double *na = malloc(sizeof(double) * d), *nb = malloc(sizeof(double) * d);
+    int da = orc_ndp_normalise(a, d, na), db = orc_ndp_normalise(b, d, nb);
+    double s = 0.0;
+    if (!da && !db)
+        for (long i = 0; i < d; ++i) s += na[i] * nb[i];
+    free(na); free(nb);
+    return s / d;
+}
+
+/* Dictionary indexing with Eq. 1 (the NDP section): for each pattern the
+ * template of largest NDP (ties -> lowest index) and that NDP; scores
+ * (nullable) receives all P x T values.  pats [P][d], tmpl [T][d]; a constant
+ * pattern gets best = -1 and score 0. */
+void orc_ndp_index(const double *pats, int P, const double *tmpl, int T, long d, int32_t *best,
+                   double *score, double *scores) {
+    double *nt = malloc(sizeof(double) * d * T);
+    for (int t = 0; t < T; ++t) orc_ndp_normalise(tmpl + (long)t * d, d, nt + (long)t * d);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int p = 0; p < P; ++p) {
+        double *np_ = malloc(sizeof(double) * d);
+        int deg = orc_ndp_normalise(pats + (long)p * d, d, np_);
+        int b = -1;
+        double bs = 0.0;
+        for (int t = 0; t < T; ++t) {
+            double s = 0.0;
+            for (long i = 0; i < d; ++i) s += np_[i] * nt[(long)t * d + i];
+            s /= d;
+            if (scores) scores[(long)p * T + t] = s;
+            if (!deg && (b < 0 || s > bs)) { b = t; bs = s; }
+        }
+        best[p] = b;
+        score[p] = deg ? 0.0 : bs;
+        free(np_);
+    }
+    free(nt);
+}
+
+/* Test orientation of the rotation experiment (sampling-frequency section):
+ * the crystal of q rotated by theta (radians) about axis `axis` (0 x, 1 y,
+ * 2 z) of the detector frame, i.e. the orientation whose pattern is the
+ * pattern of q rotated by that detector-frame rotation (the composition the
+ * refinement applies). */
+void orc_scan_orientation(const double q[4], int axis, double theta, double sample_tilt_deg,
+                          double detector_tilt_deg, double out[4]) {
+    double al = (90.0 - sample_tilt_deg + detector_tilt_deg) * ORC_PI / 180.0;
+    double qQ[4] = {cos(theta / 2), 0, 0, 0};
+    qQ[1 + axis] = sin(theta / 2);
+    apply_detector_rotation(q, qQ, al, out);
+}
+
+/* The rotation experiment of Fig. 3: a reference pattern of orientation q at
+ * pattern centre pc_ref against test patterns rotated about the detector x, y
+ * and z axes by theta_j = (j - nh) step_deg, j = 0..2 nh, projected at pc_test
+ * (the PC-error experiment of Fig. 4 A-C when pc_test differs).  For each
+ * axis a and step j:
+ *   ndp[a L + j] = Eq. 1 between reference and test (contrast-normalised);
+ *   xcf[a L + j] = peak of the FFT cross-correlation (Eqs. 4-6: window,
+ *                  band-pass, unit-norm spectra; integer peak, or the
+ *                  up-sampled peak when o->upsample >= 2), reference as the
+ *                  template, 0 if either image is degenerate;
+ * L = 2 nh + 1.  pcs are those of the n x n (cropped) screen. */
+void orc_rotation_scan(const float *master, int M, int n, const double pc_ref[3], const double pc_test[3],
+                       double sample_tilt_deg, double detector_tilt_deg, const orc_opts *o,
+                       const double q[4], int nh, double step_deg, double *ndp, double *xcf) {
+    long nn = (long)n * n;
+    int L = 2 * nh + 1;
+    double *ref = malloc(sizeof(double) * nn);
+    cplx *Sr = malloc(sizeof(cplx) * nn);
+    orc_project_interp(master, M, q, pc_ref, sample_tilt_deg, detector_tilt_deg, n, ref, o->interp);
+    int dref = orc_prep(ref, n, o, Sr, NULL);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int k = 0; k < 3 * L; ++k) {
+        int a = k / L, j = k % L;
+        double qt[4];
+        orc_scan_orientation(q, a, (j - nh) * step_deg * ORC_PI / 180.0, sample_tilt_deg,
+                             detector_tilt_deg, qt);
+        double *img = malloc(sizeof(double) * nn), *r = malloc(sizeof(double) * nn);
+        cplx *St = malloc(sizeof(cplx) * nn);
+        orc_project_interp(master, M, qt, pc_test, sample_tilt_deg, detector_tilt_deg, n, img, o->interp);
+        ndp[k] = orc_ndp(ref, img, nn);
+        int dt = orc_prep(img, n, o, St, NULL);
+        double pk = 0.0;
+        if (!dref && !dt) {
+            if (o->upsample >= 2) {
+                double dx, dy;
+                orc_pair_upsampled(Sr, St, n, o->upsample, &pk, &dx, &dy);
+            } else {
+                int sy, sx;
+                double dx, dy;
+                orc_xcf_surface(Sr, St, n, r);
+                orc_peak(r, n, &pk, &sy, &sx, &dx, &dy);
+            }
+        }
+        xcf[k] = pk;
+        free(img); free(r); free(St);
+    }
+    free(ref); free(Sr);
+}
+
+/* Full width at half maximum of a correlation-versus-angle curve (the
+ * sampling-frequency section measures the peak width of Fig. 3 this way):
+ * c[j] sampled at theta_j = (j - (L - 1) / 2) step, the maximum at the lowest
+ * index of the largest value, half = max / 2 (the maximum's half height over
+ * zero correlation); walking outwards from the maximum to the first sample
+ * below half on each side, each crossing is placed by linear interpolation
+ * between that sample and its inner neighbour.  Returns the width (units of
+ * step), or -1 when the curve does not fall below half on both sides within
+ * the scan or its maximum is not positive. */
+double orc_fwhm(const double *c, int L, double step) {
+    int m = 0;
+    for (int j = 1; j < L; ++j)
+        if (c[j] > c[m]) m = j;
+    if (!(c[m] > 0.0)) return -1.0;
+    double h = 0.5 * c[m];
+    int l = m, r = m;
+    while (l > 0 && c[l - 1] >= h) --l;
+    while (r < L - 1 && c[r + 1] >= h) ++r;
+    if (l == 0 || r == L - 1) return -1.0;
+    double tl = (l - 1) + (h - c[l - 1]) / (c[l] - c[l - 1]);
+    double tr = r + (c[r] - h) / (c[r] - c[r + 1]);
+    return (tr - tl) * step;
+}
