@@ -201,6 +201,16 @@ int xcf_disorientation(xcf_ctx *ctx, const double *qa, const double *qb, int32_t
  *                   in BF16 [T, N*N], needed by xcf_screen_topk.
  * Synchronous with respect to `stream`. */
 #define XCF_LIB_SCREEN 1
+/*   XCF_LIB_NDP     also keep each template's contrast-normalised image (zero
+ *                   mean, unit standard deviation over the N x N crop, scaled
+ *                   by 1/N so that a plain dot product is Eq. 1) in FP32 and in
+ *                   BF16 [T, N*N] each, needed by xcf_index_ndp.              */
+#define XCF_LIB_NDP 2
+/*   XCF_LIB_NO_SPECTRA  skip the FFT spectra: the library then serves only
+ *                   xcf_index_ndp, xcf_screen_topk (with XCF_LIB_SCREEN) and
+ *                   the refinement calls; the correlation searches reject it
+ *                   with XCF_ERR_ARG.                                         */
+#define XCF_LIB_NO_SPECTRA 4
 int xcf_build_library_ex(xcf_ctx *ctx, const float *master, int32_t M, const double *quats, int32_t T,
                          const xcf_geometry *g, const float *images, int32_t flags, xcf_library **out,
                          void *stream);
@@ -239,6 +249,43 @@ int xcf_index_precision(xcf_ctx *ctx, const xcf_library *lib, const float *patte
  * best [P] (identity where best < 0), then xcf_refine. */
 int xcf_refine_best(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, const int32_t *best,
                     const double *pcs, double *quats, float *peak, int32_t *iters, void *stream);
+
+/* Dictionary indexing with the normalised dot product (paper, Eq. 1 and the
+ * NDP section): each pattern's N x N crop is contrast-normalised (zero mean,
+ * unit population standard deviation; a constant crop is degenerate), the NDP
+ * against every template is computed on the tensor cores with BF16 operands
+ * and FP32 accumulation, the k best templates (1 <= k <= 64; score desc,
+ * index asc) are rescored in FP32, and the best of those is returned:
+ *   best [P] int32 out (-1 for a degenerate pattern), ndp [P] float32 out (its
+ *   FP32 NDP, 0 when degenerate); cand [P, k] int32 and cand_score [P, k]
+ *   float32 (nullable, together) receive the candidates and their BF16 scores.
+ * There is no translation freedom (the NDP compares fixed templates).  The
+ * library needs XCF_LIB_NDP and at most 51,200 templates.  Refinement from the
+ * result: xcf_refine_best.  Synchronous (XCF_ERR_TIMEOUT if a bounded device
+ * wait of the tensor-core pipeline gave up). */
+int xcf_index_ndp(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, int32_t k,
+                  int32_t *best, float *ndp, int32_t *cand, float *cand_score, void *stream);
+
+/* The peak-width experiment of the sampling-frequency section (Figs. 3 and
+ * 4): a reference pattern of orientation q [4] (float64, device) at the
+ * geometry's PC, against test patterns of the crystal rotated about the
+ * detector x, y and z axes by theta_j = (j - h) step_deg, j = 0 .. 2h,
+ * projected at pc_test [3] (detector-frame PC, device; NULL = the geometry's;
+ * a different PC is the PC-error experiment of Fig. 4 A-C).  All images are
+ * the N x N crop of the detector.  Per axis a and step j:
+ *   ndp [3, 2h+1] float32: Eq. 1 between reference and test pattern;
+ *   xcf [3, 2h+1] float32: peak of their FFT cross-correlation with the
+ *     context's pre-processing (Eqs. 4-6; up-sampled when the option is set),
+ *     the reference taken as the template; 0 if either image is degenerate;
+ *   fwhm [2, 3] float32 (nullable): full width at half maximum in degrees of
+ *     each curve (row 0 NDP, row 1 FFT; columns x, y, z): half = max / 2, the
+ *     crossings nearest the maximum (the lowest-index maximum) placed by linear
+ *     interpolation, -1 where the curve does not fall below half on both sides
+ *     within the scan.
+ * 1 <= h <= 2048, step_deg > 0; the master and its size as xcf_project. */
+int xcf_rotation_scan(xcf_ctx *ctx, const float *master, int32_t M, const xcf_geometry *g, const double *q,
+                      const double *pc_test, int32_t h, double step_deg, float *ndp, float *xcf, float *fwhm,
+                      void *stream);
 
 /* Several maps in one search (paper, Fig. 1 B-C, for every map of a batch;
  * the maps may have different detectors, pattern centres and libraries --

@@ -221,10 +221,12 @@ cudaError_t run_pair_peak(xcf_ctx *ctx, int n, const float2 *St, const int *tidx
     return launch_upsample_peak(n, St, tidx, Sp, degen, active, P, U, argmax, peak, shift, st);
 }
 
-int check_lib(xcf_ctx *ctx, const xcf_library *lib) {
+// spectra: the call correlates against the library's FFT spectra
+int check_lib(xcf_ctx *ctx, const xcf_library *lib, bool spectra = false) {
     if (!ctx) return XCF_ERR_ARG;
     if (!lib) return fail(ctx, XCF_ERR_ARG, "library is NULL");
     if (lib->device != ctx->device) return fail(ctx, XCF_ERR_ARG, "library and context on different devices");
+    if (spectra && !lib->spectra) return fail(ctx, XCF_ERR_ARG, "library built with XCF_LIB_NO_SPECTRA");
     return XCF_OK;
 }
 
@@ -469,8 +471,29 @@ int xcf_prep(xcf_ctx *ctx, const float *images, int32_t P, const xcf_geometry *g
     return XCF_OK;
 }
 
+namespace {
+int build_from_master(xcf_ctx *ctx, const float *master, int32_t M, const double *quats, int32_t T,
+                      const xcf_geometry *g, bool spectra, xcf_library **out, void *stream);
+int build_from_images(xcf_ctx *ctx, const float *images, const double *quats, int32_t T, const xcf_geometry *g,
+                      const float *master, int32_t M, bool spectra, xcf_library **out, void *stream);
+}  // namespace
+
 int xcf_build_library(xcf_ctx *ctx, const float *master, int32_t M, const double *quats, int32_t T,
                       const xcf_geometry *g, xcf_library **out, void *stream) {
+    return build_from_master(ctx, master, M, quats, T, g, true, out, stream);
+}
+
+int xcf_build_library_images(xcf_ctx *ctx, const float *images, const double *quats, int32_t T,
+                             const xcf_geometry *g, const float *master, int32_t M, xcf_library **out,
+                             void *stream) {
+    return build_from_images(ctx, images, quats, T, g, master, M, true, out, stream);
+}
+
+namespace {
+// spectra == false: the library keeps its orientations, master and geometry
+// but no FFT spectra (an NDP-only library)
+int build_from_master(xcf_ctx *ctx, const float *master, int32_t M, const double *quats, int32_t T,
+                      const xcf_geometry *g, bool spectra, xcf_library **out, void *stream) {
     if (!ctx) return XCF_ERR_ARG;
     if (!master || !quats || !g || !out || T <= 0 || M < 2)
         return fail(ctx, XCF_ERR_ARG, "xcf_build_library: bad argument");
@@ -492,7 +515,7 @@ int xcf_build_library(xcf_ctx *ctx, const float *master, int32_t M, const double
     lib->oy = c.oy;
     memcpy(lib->pc, c.pc, sizeof c.pc);
     const size_t H = (size_t)c.n * (c.n / 2 + 1);
-    cudaError_t e = cudaMalloc(&lib->spectra, sizeof(float2) * H * T);
+    cudaError_t e = spectra ? cudaMalloc(&lib->spectra, sizeof(float2) * H * T) : cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&lib->quats, sizeof(double) * 4 * T);
     if (e == cudaSuccess) e = cudaMalloc(&lib->master, sizeof(float) * 2 * (size_t)M * M);
     if (e != cudaSuccess) {
@@ -508,7 +531,7 @@ int xcf_build_library(xcf_ctx *ctx, const float *master, int32_t M, const double
     const PrepArgs ps = prep_args_square(c, r);
     int *degen = nullptr;
     float *img = nullptr;
-    for (int t0 = 0; e == cudaSuccess && t0 < T; t0 += kChunk) {
+    for (int t0 = 0; spectra && e == cudaSuccess && t0 < T; t0 += kChunk) {
         const int nt = T - t0 < kChunk ? T - t0 : kChunk;
         if ((rc = scratch_t(ctx, S_IMG, (size_t)nt * c.n * c.n, &img)) ||
             (rc = scratch_t(ctx, S_DEGEN, nt, &degen))) {
@@ -520,7 +543,7 @@ int xcf_build_library(xcf_ctx *ctx, const float *master, int32_t M, const double
         ctx->launches[XCF_STAGE_PROJECT] += 1;
         ctx->launches[XCF_STAGE_PREP] += 1;
     }
-    if (e == cudaSuccess && c.n == 128) {
+    if (spectra && e == cudaSuccess && c.n == 128) {
         e = cudaMalloc(&lib->spectra_pk, sizeof(float2) * H * T);
         if (e == cudaSuccess) e = launch_pack_search_layout(lib->spectra, T, c.n, lib->spectra_pk, st);
         ctx->launches[XCF_STAGE_OTHER] += 1;
@@ -534,9 +557,8 @@ int xcf_build_library(xcf_ctx *ctx, const float *master, int32_t M, const double
     return XCF_OK;
 }
 
-int xcf_build_library_images(xcf_ctx *ctx, const float *images, const double *quats, int32_t T,
-                             const xcf_geometry *g, const float *master, int32_t M, xcf_library **out,
-                             void *stream) {
+int build_from_images(xcf_ctx *ctx, const float *images, const double *quats, int32_t T, const xcf_geometry *g,
+                      const float *master, int32_t M, bool spectra, xcf_library **out, void *stream) {
     if (!ctx) return XCF_ERR_ARG;
     if (!images || !quats || !g || !out || T <= 0 || (master && M < 2))
         return fail(ctx, XCF_ERR_ARG, "xcf_build_library_images: bad argument");
@@ -558,7 +580,7 @@ int xcf_build_library_images(xcf_ctx *ctx, const float *images, const double *qu
     lib->oy = c.oy;
     memcpy(lib->pc, c.pc, sizeof c.pc);
     const size_t H = (size_t)c.n * (c.n / 2 + 1);
-    cudaError_t e = cudaMalloc(&lib->spectra, sizeof(float2) * H * T);
+    cudaError_t e = spectra ? cudaMalloc(&lib->spectra, sizeof(float2) * H * T) : cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&lib->quats, sizeof(double) * 4 * T);
     if (e == cudaSuccess && master) e = cudaMalloc(&lib->master, sizeof(float) * 2 * (size_t)M * M);
     if (e != cudaSuccess) {
@@ -574,9 +596,12 @@ int xcf_build_library_images(xcf_ctx *ctx, const float *images, const double *qu
         xcf_library_free(lib);
         return rc;
     }
-    if (e == cudaSuccess) e = run_prep(ctx,images, T, prep_args(g, c, r), lib->spectra, nullptr, degen, nullptr, st);
-    ctx->launches[XCF_STAGE_PREP] += 1;
-    if (e == cudaSuccess && c.n == 128) {
+    if (spectra) {
+        if (e == cudaSuccess)
+            e = run_prep(ctx, images, T, prep_args(g, c, r), lib->spectra, nullptr, degen, nullptr, st);
+        ctx->launches[XCF_STAGE_PREP] += 1;
+    }
+    if (spectra && e == cudaSuccess && c.n == 128) {
         e = cudaMalloc(&lib->spectra_pk, sizeof(float2) * H * T);
         if (e == cudaSuccess) e = launch_pack_search_layout(lib->spectra, T, c.n, lib->spectra_pk, st);
         ctx->launches[XCF_STAGE_OTHER] += 1;
@@ -589,6 +614,7 @@ int xcf_build_library_images(xcf_ctx *ctx, const float *images, const double *qu
     *out = lib;
     return XCF_OK;
 }
+}  // namespace
 
 int xcf_library_free(xcf_library *lib) {
     if (!lib) return XCF_ERR_ARG;
@@ -596,6 +622,7 @@ int xcf_library_free(xcf_library *lib) {
     if (lib->spectra) cudaFree(lib->spectra);
     if (lib->spectra_pk) cudaFree(lib->spectra_pk);
     if (lib->bf16) cudaFree(lib->bf16);
+    if (lib->ndp32) cudaFree(lib->ndp32);
     if (lib->quats) cudaFree(lib->quats);
     if (lib->master) cudaFree(lib->master);
     delete lib;
@@ -612,7 +639,7 @@ int xcf_library_info(const xcf_library *lib, int32_t *T, int32_t *N, const float
 
 int xcf_index(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, int32_t *best,
               float *peak, float *shift, void *stream) {
-    int rc = check_lib(ctx, lib);
+    int rc = check_lib(ctx, lib, true);
     if (rc) return rc;
     if (P == 0) return XCF_OK;
     if (!patterns || !best || !peak || !shift || P < 0) return fail(ctx, XCF_ERR_ARG, "xcf_index: bad argument");
@@ -629,7 +656,7 @@ int xcf_index(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32
 
 int xcf_correlate_all(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, float *peaks,
                       void *stream) {
-    int rc = check_lib(ctx, lib);
+    int rc = check_lib(ctx, lib, true);
     if (rc) return rc;
     if (P == 0) return XCF_OK;
     if (!patterns || !peaks || P < 0) return fail(ctx, XCF_ERR_ARG, "xcf_correlate_all: bad argument");
@@ -681,7 +708,7 @@ int xcf_disorientation(xcf_ctx *ctx, const double *qa, const double *qb, int32_t
 int xcf_index_refine(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, const double *pcs,
                      int32_t *best, float *peak, float *shift, double *quats, float *rpeak, int32_t *iters,
                      void *stream) {
-    int rc = check_lib(ctx, lib);
+    int rc = check_lib(ctx, lib, true);
     if (rc) return rc;
     if (P == 0) return XCF_OK;
     if (!patterns || !best || !peak || !shift || !quats || !rpeak || !iters || P < 0)
@@ -731,7 +758,7 @@ int xcf_refine_best(xcf_ctx *ctx, const xcf_library *lib, const float *patterns,
 int xcf_index_refine_host(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P,
                           const double *pcs, int32_t chunk, int32_t *best, float *peak, float *shift,
                           double *quats, float *rpeak, int32_t *iters) {
-    int rc = check_lib(ctx, lib);
+    int rc = check_lib(ctx, lib, true);
     if (rc) return rc;
     if (P == 0) return XCF_OK;
     if (!patterns || !best || !peak || !shift || !quats || !rpeak || !iters || P < 0)
@@ -888,6 +915,46 @@ int make_screen_images(xcf_ctx *ctx, xcf_library *lib, const float *images, cuda
     return XCF_OK;
 }
 
+// contrast-normalised FP32 and BF16 images of the library's templates (NDP,
+// Eq. 1): from the caller's template images, or re-projected from the master
+int make_ndp_images(xcf_ctx *ctx, xcf_library *lib, const float *images, cudaStream_t st) {
+    const xcf_geometry *g = &lib->geom;
+    Crop c;
+    crop_of(g, 256, &c);
+    const size_t nn = (size_t)c.n * c.n;
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, 6 * nn * lib->T) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, XCF_ERR_OOM, "NDP images: allocation failed");
+    }
+    lib->ndp32 = static_cast<float *>(mem);
+    lib->ndp16 = static_cast<char *>(mem) + 4 * nn * lib->T;
+    const int chunk = screen_chunk(c.n, 1);
+    int rc;
+    for (int t0 = 0; t0 < lib->T; t0 += chunk) {
+        const int nt = lib->T - t0 < chunk ? lib->T - t0 : chunk;
+        float *o32 = lib->ndp32 + nn * t0;
+        void *o16 = static_cast<char *>(lib->ndp16) + 2 * nn * t0;
+        if (images) {
+            XCF_LAUNCH(XCF_STAGE_PREP, st,
+                       launch_ndp_norm(images + (size_t)g->width * g->height * t0, nt,
+                                       (long)g->width * g->height, g->width, c.ox, c.oy, c.n, o32, o16, nullptr,
+                                       st),
+                       "ndp normalise");
+        } else {
+            float *img;
+            if ((rc = scratch_t(ctx, S_IMG, nn * nt, &img))) return rc;
+            XCF_LAUNCH(XCF_STAGE_PROJECT, st,
+                       launch_project(lib->master, lib->M, lib->quats + 4 * (size_t)t0, nullptr, nullptr, nt,
+                                      proj_args_cropped(g, c, ctx->opt.master_interp), img, st),
+                       "ndp project");
+            XCF_LAUNCH(XCF_STAGE_PREP, st,
+                       launch_ndp_norm(img, nt, (long)nn, c.n, 0, 0, c.n, o32, o16, nullptr, st), "ndp normalise");
+        }
+    }
+    return XCF_OK;
+}
+
 }  // namespace
 
 int xcf_build_library_ex(xcf_ctx *ctx, const float *master, int32_t M, const double *quats, int32_t T,
@@ -895,12 +962,15 @@ int xcf_build_library_ex(xcf_ctx *ctx, const float *master, int32_t M, const dou
                          void *stream) {
     if (!ctx) return XCF_ERR_ARG;
     if (!out) return fail(ctx, XCF_ERR_ARG, "xcf_build_library_ex: out is NULL");
-    if (flags & ~XCF_LIB_SCREEN) return fail(ctx, XCF_ERR_ARG, "xcf_build_library_ex: unknown flags");
-    int rc = images ? xcf_build_library_images(ctx, images, quats, T, g, master, M, out, stream)
-                    : xcf_build_library(ctx, master, M, quats, T, g, out, stream);
-    if (rc || !(flags & XCF_LIB_SCREEN)) return rc;
+    if (flags & ~(XCF_LIB_SCREEN | XCF_LIB_NDP | XCF_LIB_NO_SPECTRA))
+        return fail(ctx, XCF_ERR_ARG, "xcf_build_library_ex: unknown flags");
+    const bool spectra = !(flags & XCF_LIB_NO_SPECTRA);
+    int rc = images ? build_from_images(ctx, images, quats, T, g, master, M, spectra, out, stream)
+                    : build_from_master(ctx, master, M, quats, T, g, spectra, out, stream);
+    if (rc || !(flags & (XCF_LIB_SCREEN | XCF_LIB_NDP))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    rc = make_screen_images(ctx, *out, images, st);
+    if (flags & XCF_LIB_SCREEN) rc = make_screen_images(ctx, *out, images, st);
+    if (rc == XCF_OK && (flags & XCF_LIB_NDP)) rc = make_ndp_images(ctx, *out, images, st);
     if (rc == XCF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = cuda_fail(ctx, cudaGetLastError(), "screen images");
     if (rc) {
         xcf_library_free(*out);
@@ -956,7 +1026,7 @@ int xcf_screen_topk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns,
 
 int xcf_rescore(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, const int32_t *cand,
                 int32_t k, int32_t *best, float *peak, float *shift, void *stream) {
-    int rc = check_lib(ctx, lib);
+    int rc = check_lib(ctx, lib, true);
     if (rc) return rc;
     if (P == 0) return XCF_OK;
     if (!patterns || !cand || !best || !peak || !shift || P < 0 || k < 1)
@@ -1001,7 +1071,7 @@ int xcf_rescore(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int
 int xcf_index_precision(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P,
                         const double *pcs, int32_t k, int32_t *best, double *quats, float *peak, int32_t *iters,
                         void *stream) {
-    int rc = check_lib(ctx, lib);
+    int rc = check_lib(ctx, lib, true);
     if (rc) return rc;
     if (P == 0) return XCF_OK;
     if (!patterns || !best || !quats || !peak || !iters || P < 0 || k < 1 || k > 64)
@@ -1063,6 +1133,106 @@ int xcf_index_precision(xcf_ctx *ctx, const xcf_library *lib, const float *patte
     XCF_CHECK(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
     XCF_CHECK(cudaStreamSynchronize(st), "xcf_index_precision");
     if (h_err) return fail(ctx, XCF_ERR_TIMEOUT, "xcf_index_precision: a tensor-core pipeline wait timed out");
+    return XCF_OK;
+}
+
+// ------------------------------------------------------------------- NDP
+int xcf_index_ndp(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, int32_t k,
+                  int32_t *best, float *ndp, int32_t *cand, float *cand_score, void *stream) {
+    int rc = check_lib(ctx, lib);
+    if (rc) return rc;
+    if (P == 0) return XCF_OK;
+    if (!patterns || !best || !ndp || P < 0 || k < 1 || k > 64 || (!cand) != (!cand_score))
+        return fail(ctx, XCF_ERR_ARG, "xcf_index_ndp: bad argument (1 <= k <= 64; cand and cand_score together)");
+    if (!lib->ndp32) return fail(ctx, XCF_ERR_ARG, "xcf_index_ndp: library built without XCF_LIB_NDP");
+    if ((size_t)lib->T * 4 > 200 * 1024) return fail(ctx, XCF_ERR_SIZE, "xcf_index_ndp: more than 51,200 templates");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const xcf_geometry *g = &lib->geom;
+    Crop c;
+    crop_of(g, 256, &c);
+    const size_t nn = (size_t)c.n * c.n, img = (size_t)g->width * g->height;
+    const int chunk = screen_chunk(c.n, lib->T);
+    int *err;
+    if ((rc = scratch_t(ctx, S_ERR, 1, &err))) return rc;
+    XCF_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st), "clear status");
+    for (int p0 = 0; p0 < P; p0 += chunk) {
+        const int np = P - p0 < chunk ? P - p0 : chunk;
+        float *pn, *S, *csc;
+        int *degen, *cd;
+        void *a;
+        if ((rc = scratch_t(ctx, S_SPATIAL_P, nn * np, &pn)) || (rc = scratch_t(ctx, S_DEGEN, np, &degen)) ||
+            (rc = scratch(ctx, S_BF16_P, 2 * nn * np, &a)) ||
+            (rc = scratch_t(ctx, S_SCORE, (size_t)np * lib->T, &S)))
+            return rc;
+        if (cand) {
+            cd = cand + (size_t)k * p0;
+            csc = cand_score + (size_t)k * p0;
+        } else if ((rc = scratch_t(ctx, S_CAND, (size_t)np * k, &cd)) ||
+                   (rc = scratch_t(ctx, S_CANDSC, (size_t)np * k, &csc))) {
+            return rc;
+        }
+        XCF_LAUNCH(XCF_STAGE_PREP, st,
+                   launch_ndp_norm(patterns + img * p0, np, (long)img, g->width, c.ox, c.oy, c.n, pn, a, degen, st),
+                   "ndp normalise");
+        XCF_LAUNCH(XCF_STAGE_SCREEN, st, launch_screen_tc(a, np, lib->ndp16, lib->T, (int)nn, S, err, st), "ndp gemm");
+        XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_topk_rows(S, np, lib->T, k, cd, csc, st), "topk");
+        XCF_LAUNCH(XCF_STAGE_SEARCH, st,
+                   launch_ndp_rescore(pn, lib->ndp32, (long)nn, cd, k, degen, np, best + p0, ndp + p0, st),
+                   "ndp rescore");
+    }
+    int h_err = 0;
+    XCF_CHECK(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+    XCF_CHECK(cudaStreamSynchronize(st), "xcf_index_ndp");
+    if (h_err) return fail(ctx, XCF_ERR_TIMEOUT, "xcf_index_ndp: a tensor-core pipeline wait timed out");
+    return XCF_OK;
+}
+
+int xcf_rotation_scan(xcf_ctx *ctx, const float *master, int32_t M, const xcf_geometry *g, const double *q,
+                      const double *pc_test, int32_t h, double step_deg, float *ndp, float *xcf, float *fwhm,
+                      void *stream) {
+    if (!ctx) return XCF_ERR_ARG;
+    if (!master || !g || !q || !ndp || !xcf || M < 2 || h < 1 || h > 2048 || !(step_deg > 0.0))
+        return fail(ctx, XCF_ERR_ARG, "xcf_rotation_scan: bad argument (1 <= h <= 2048, step_deg > 0)");
+    Crop c;
+    int rc = crop_of(g, 256, &c);
+    if (rc) return fail(ctx, rc, "xcf_rotation_scan: detector too small");
+    if (!supported_n(c.n)) return fail(ctx, XCF_ERR_UNIMPLEMENTED, "xcf_rotation_scan: detector side not supported");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const Resolved r = resolve(ctx->opt, c.n);
+    const int L = 2 * h + 1, n_img = 1 + 3 * L, nt = 3 * L;
+    const size_t nn = (size_t)c.n * c.n, H = (size_t)c.n * (c.n / 2 + 1);
+    double *qs, *pcs;
+    float *imgs, *pn, *shift;
+    float2 *spec;
+    int *degen, *zeros, *junk_best;
+    if ((rc = scratch_t(ctx, S_SEEDS, (size_t)n_img * 4, &qs)) || (rc = scratch_t(ctx, S_Q1, (size_t)n_img * 3, &pcs)) ||
+        (rc = scratch_t(ctx, S_IMG, nn * n_img, &imgs)) || (rc = scratch_t(ctx, S_SPATIAL_P, nn * n_img, &pn)) ||
+        (rc = scratch_t(ctx, S_SPEC_P, H * n_img, &spec)) || (rc = scratch_t(ctx, S_DEGEN, n_img, &degen)) ||
+        (rc = scratch_t(ctx, S_CAND, nt, &zeros)) || (rc = scratch_t(ctx, S_BEST, nt, &junk_best)) ||
+        (rc = scratch_t(ctx, S_SHIFT, 2 * (size_t)nt, &shift)))
+        return rc;
+    XCF_CHECK(cudaMemsetAsync(zeros, 0, sizeof(int) * nt, st), "clear template indices");
+    XCF_LAUNCH(XCF_STAGE_OTHER, st,
+               launch_scan_setup(q, pc_test, g->pcx, g->pcy, g->pcz, h, step_deg * kPi / 180.0, alpha_of(g), qs, pcs,
+                                 st),
+               "scan setup");
+    XCF_LAUNCH(XCF_STAGE_PROJECT, st,
+               launch_project(master, M, qs, pcs, nullptr, n_img, proj_args_cropped(g, c, ctx->opt.master_interp),
+                              imgs, st),
+               "scan project");
+    // Eq. 1: every image normalised, then each test image against the reference (entry 0)
+    XCF_LAUNCH(XCF_STAGE_PREP, st,
+               launch_ndp_norm(imgs, n_img, (long)nn, c.n, 0, 0, c.n, pn, nullptr, degen, st), "ndp normalise");
+    XCF_LAUNCH(XCF_STAGE_SEARCH, st,
+               launch_ndp_rescore(pn + nn, pn, (long)nn, zeros, 1, degen + 1, nt, junk_best, ndp, st), "ndp pairs");
+    // FFT XCF: the reference's spectrum as the template of every test image
+    XCF_LAUNCH(XCF_STAGE_PREP, st,
+               run_prep(ctx, imgs, n_img, prep_args_square(c, r), spec, nullptr, degen, nullptr, st), "scan prep");
+    XCF_LAUNCH(XCF_STAGE_PEAK, st,
+               run_pair_peak(ctx, c.n, spec, zeros, spec + H, degen + 1, nullptr, nt, xcf, shift, st), "scan peak");
+    if (fwhm) XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_fwhm(ndp, xcf, 6, L, (float)step_deg, fwhm, st), "fwhm");
     return XCF_OK;
 }
 
@@ -1273,7 +1443,7 @@ int xcf_index_learned(xcf_ctx *ctx, xcf_net *net, const xcf_library *lib, const 
                       void *stream) {
     int rc = check_net(ctx, net);
     if (rc) return rc;
-    if ((rc = check_lib(ctx, lib))) return rc;
+    if ((rc = check_lib(ctx, lib, true))) return rc;
     if (P == 0) return XCF_OK;
     if (P < 0 || !patterns || !quats || !peak || !iters || !fallback)
         return fail(ctx, XCF_ERR_ARG, "xcf_index_learned: bad argument");
@@ -1581,7 +1751,7 @@ int xcf_index_maps(xcf_ctx *ctx, const xcf_map_desc *maps, int32_t n_maps, int32
         return fail(ctx, XCF_ERR_ARG, "xcf_index_maps: bad argument");
     if (n_maps == 0) return XCF_OK;
     for (int m = 0; m < n_maps; ++m) {
-        int rc = check_lib(ctx, maps[m].lib);
+        int rc = check_lib(ctx, maps[m].lib, true);
         if (rc) return rc;
         if (maps[m].P < 0 || (maps[m].P > 0 && (!maps[m].patterns || !maps[m].best || !maps[m].peak || !maps[m].shift)))
             return fail(ctx, XCF_ERR_ARG, "xcf_index_maps: bad map " + std::to_string(m));

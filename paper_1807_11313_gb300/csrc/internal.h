@@ -94,6 +94,8 @@ struct xcf_library {
     float2 *spectra = nullptr;
     float2 *spectra_pk = nullptr;   // N = 128 only: the search kernel's packed layout
     void *bf16 = nullptr;           // screen: unit-norm filtered images [T][N*N] in BF16
+    float *ndp32 = nullptr;         // NDP: contrast-normalised images / N [T][N*N] in FP32 ...
+    void *ndp16 = nullptr;          // ... and in BF16 (inside the same allocation)
     double *quats = nullptr;
     float *master = nullptr;
 };

@@ -368,6 +368,33 @@ __global__ void k_disorientation(const double *__restrict__ qa, const double *__
     out[i] = 2.0 * acos(fmin(best, 1.0)) * 180.0 / XCF_PI;
 }
 
+// orientations and PCs of the rotation experiment (sampling-frequency
+// section): entry 0 the reference (q, pc_ref), entry 1 + a L + j the crystal
+// rotated by theta_j = (j - h) step about detector axis a, at pc_test
+__global__ void k_scan_setup(const double *__restrict__ q, const double *__restrict__ pc_test, double pcx,
+                             double pcy, double pcz, int h, double step_rad, double alpha, double *__restrict__ qs,
+                             double *__restrict__ pcs) {
+    const int L = 2 * h + 1, i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > 3 * L) return;
+    const Q q0 = qload(q);
+    double *pc = pcs + 3 * (size_t)i;
+    if (i == 0) {
+        qstore(qs, qcanon(q0));
+        pc[0] = pcx; pc[1] = pcy; pc[2] = pcz;
+        return;
+    }
+    const int a = (i - 1) / L, j = (i - 1) % L;
+    double s, c;
+    sincos(0.5 * (j - h) * step_rad, &s, &c);
+    const Q R = {c, a == 0 ? s : 0.0, a == 1 ? s : 0.0, a == 2 ? s : 0.0};
+    qstore(qs + 4 * (size_t)i, rotate_in_detector(q0, R, alpha));
+    if (pc_test) {
+        pc[0] = pc_test[0]; pc[1] = pc_test[1]; pc[2] = pc_test[2];
+    } else {
+        pc[0] = pcx; pc[1] = pcy; pc[2] = pcz;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_project(const float *master, int M, const double *quats, const double *pcs,
@@ -446,5 +473,12 @@ cudaError_t launch_disorientation(const double *qa, const double *qb, int n, dou
                                   cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     k_disorientation<<<(n + 127) / 128, 128, 0, st>>>(qa, qb, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_setup(const double *q, const double *pc_test, double pcx, double pcy, double pcz, int h,
+                              double step_rad, double alpha, double *qs, double *pcs, cudaStream_t st) {
+    const int n = 3 * (2 * h + 1) + 1;
+    k_scan_setup<<<(n + 127) / 128, 128, 0, st>>>(q, pc_test, pcx, pcy, pcz, h, step_rad, alpha, qs, pcs);
     return cudaGetLastError();
 }

@@ -125,6 +125,21 @@ cudaError_t launch_copy_active_peak(const float *src, const int *active, int P, 
 cudaError_t launch_disorientation(const double *qa, const double *qb, int n, double *out,
                                   cudaStream_t st);
 
+// normalised dot product (Eq. 1): contrast-normalised crops / sqrt(d) of
+// images [P] (image p at img + p * img_stride, rows row_stride apart, crop at
+// (ox, oy), side n a power of two) -> out32 [P][n*n] and / or out16 (BF16), degen [P]
+cudaError_t launch_ndp_norm(const float *img, int P, long img_stride, int row_stride, int ox, int oy, int n,
+                            float *out32, void *out16, int *degen, cudaStream_t st);
+// FP32 NDP of pattern p (pn [P][d]) against its candidates cand [P][k] of
+// tn [T][d] (< 0 skipped): best [P] (-1 if degenerate), score [P]
+cudaError_t launch_ndp_rescore(const float *pn, const float *tn, long d, const int *cand, int k, const int *degen,
+                               int P, int *best, float *score, cudaStream_t st);
+// FWHM of nc curves of length L (the first nc/2 from a, the rest from b) -> out [nc]
+cudaError_t launch_fwhm(const float *a, const float *b, int nc, int L, float step, float *out, cudaStream_t st);
+// rotation experiment: qs [1 + 3L][4], pcs [1 + 3L][3] (detector-frame PCs), L = 2h + 1
+cudaError_t launch_scan_setup(const double *q, const double *pc_test, double pcx, double pcy, double pcz, int h,
+                              double step_rad, double alpha, double *qs, double *pcs, cudaStream_t st);
+
 // ------------------------------------------------ learned proposal network
 // input images: the 128 x 128 crop at (ox, oy) of image b = x + b * img_stride
 struct CnnInput {

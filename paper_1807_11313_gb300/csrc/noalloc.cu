@@ -78,6 +78,7 @@ extern "C" int xcf_index_noalloc(xcf_ctx *ctx, const xcf_library *lib, const flo
     if (!ctx) return XCF_ERR_ARG;
     if (!lib) { ctx->err = "xcf_index_noalloc: library is NULL"; return XCF_ERR_ARG; }
     if (lib->device != ctx->device) { ctx->err = "xcf_index_noalloc: library on another device"; return XCF_ERR_ARG; }
+    if (!lib->spectra) { ctx->err = "xcf_index_noalloc: library built with XCF_LIB_NO_SPECTRA"; return XCF_ERR_ARG; }
     if (P == 0) return XCF_OK;
     if (!patterns || !best || !peak || !shift || P < 0) {
         ctx->err = "xcf_index_noalloc: bad argument";

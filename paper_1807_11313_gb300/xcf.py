@@ -84,6 +84,8 @@ _SIGS = {
     "xcf_rescore": ([_P, _P, _P, _I32, _P, _I32, _P, _P, _P, _P], C.c_int),
     "xcf_refine_best": ([_P, _P, _P, _I32, _P, _P, _P, _P, _P, _P], C.c_int),
     "xcf_index_precision": ([_P, _P, _P, _I32, _P, _I32, _P, _P, _P, _P, _P], C.c_int),
+    "xcf_index_ndp": ([_P, _P, _P, _I32, _I32, _P, _P, _P, _P, _P], C.c_int),
+    "xcf_rotation_scan": ([_P, _P, _I32, _P, _P, _P, _I32, C.c_double, _P, _P, _P, _P], C.c_int),
     "xcf_index_noalloc": ([_P, _P, _P, _I32, _P, _P, _P, _P], C.c_int),
     "xcf_noalloc_max_patterns": ([_I32], C.c_int),
     "xcf_index_maps": ([_P, _P, _I32, _I32, _P], C.c_int),
@@ -394,11 +396,15 @@ def xcf_index_noalloc(ctx: Context, lib: Library, patterns, best, peak, shift):
 
 
 XCF_LIB_SCREEN = 1
+XCF_LIB_NDP = 2
+XCF_LIB_NO_SPECTRA = 4
 
 
 def xcf_build_library_ex(ctx: Context, quats, geom: xcf_geometry, master=None, images=None, flags: int = 0) -> Library:
     """Library from the master (images None) or from template images; flags
-    XCF_LIB_SCREEN keeps BF16 filtered images for xcf_screen_topk."""
+    XCF_LIB_SCREEN keeps BF16 filtered images for xcf_screen_topk, XCF_LIB_NDP
+    the contrast-normalised FP32 + BF16 images for xcf_index_ndp,
+    XCF_LIB_NO_SPECTRA skips the FFT spectra (no correlation search)."""
     h = C.c_void_p()
     M = master.shape[-1] if master is not None else 0
     _check(load().xcf_build_library_ex(ctx.handle, _ptr(master, torch.float32, "master", True), M,
@@ -417,6 +423,40 @@ def xcf_screen_topk(ctx: Context, lib: Library, patterns, k: int = 32):
                                   _ptr(cand, torch.int32, "cand"), _ptr(score, torch.float32, "score"), _stream()),
            ctx.handle)
     return cand, score
+
+
+def xcf_index_ndp(ctx: Context, lib: Library, patterns, k: int = 4, want_cand: bool = False):
+    """Dictionary indexing by the normalised dot product (Eq. 1): BF16
+    tensor-core NDP over the library, FP32 rescore of the k best.
+    -> (best [P] int32, ndp [P] float32) or, with want_cand, also
+    (cand [P, k] int32, cand_score [P, k] float32)."""
+    P, d = patterns.shape[0], patterns.device
+    best = torch.empty(P, dtype=torch.int32, device=d)
+    ndp = torch.empty(P, dtype=torch.float32, device=d)
+    cand = torch.empty((P, k), dtype=torch.int32, device=d) if want_cand else None
+    cs = torch.empty((P, k), dtype=torch.float32, device=d) if want_cand else None
+    _check(load().xcf_index_ndp(ctx.handle, lib.handle, _ptr(patterns, torch.float32, "patterns"), P, int(k),
+                                _ptr(best, torch.int32, "best"), _ptr(ndp, torch.float32, "ndp"),
+                                _ptr(cand, torch.int32, "cand", True), _ptr(cs, torch.float32, "cand_score", True),
+                                _stream()), ctx.handle)
+    return (best, ndp, cand, cs) if want_cand else (best, ndp)
+
+
+def xcf_rotation_scan(ctx: Context, master, geom: xcf_geometry, q, h: int, step_deg: float, pc_test=None):
+    """Peak-width experiment (Figs. 3, 4): reference of orientation q [4]
+    against the crystal rotated about detector x, y, z by (j - h) step_deg.
+    -> (ndp [3, 2h+1], xcf [3, 2h+1], fwhm [2, 3] degrees, -1 unresolved)."""
+    d = master.device
+    L = 2 * int(h) + 1
+    ndp = torch.empty((3, L), dtype=torch.float32, device=d)
+    xc = torch.empty((3, L), dtype=torch.float32, device=d)
+    fw = torch.empty((2, 3), dtype=torch.float32, device=d)
+    _check(load().xcf_rotation_scan(ctx.handle, _ptr(master, torch.float32, "master"), master.shape[-1],
+                                    C.byref(geom), _ptr(q, torch.float64, "q"),
+                                    _ptr(pc_test, torch.float64, "pc_test", True), int(h), float(step_deg),
+                                    _ptr(ndp, torch.float32, "ndp"), _ptr(xc, torch.float32, "xcf"),
+                                    _ptr(fw, torch.float32, "fwhm"), _stream()), ctx.handle)
+    return ndp, xc, fw
 
 
 def xcf_refine_best(ctx: Context, lib: Library, patterns, best, pcs=None, out=None):
