@@ -40,14 +40,16 @@ def build(force: bool = False) -> str:
 class Opts(C.Structure):
     _fields_ = [("window", C.c_int32), ("sigma_hp", C.c_double), ("sigma_lp", C.c_double),
                 ("lp_nr", C.c_int32), ("lp_neta", C.c_int32), ("lp_rmin", C.c_double),
-                ("lp_rmax", C.c_double), ("upsample", C.c_int32), ("interp", C.c_int32)]
+                ("lp_rmax", C.c_double), ("upsample", C.c_int32), ("interp", C.c_int32),
+                ("ndp_bg_sigma", C.c_double)]
 
 
 def default_opts(n: int, **kw) -> Opts:
     """Defaults: Hann window, sigma_hp = 2, sigma_lp = n/4 cycles per image,
-    log-polar n/4 radii x 2n angles over r in [n/4, n/2 - 1] px."""
+    log-polar n/4 radii x 2n angles over r in [n/4, n/2 - 1] px, NDP
+    background sigma n/8 px (0 selects it; < 0 turns the correction off)."""
     d = dict(window=1, sigma_hp=2.0, sigma_lp=n / 4.0, lp_nr=max(n // 4, 2), lp_neta=2 * n,
-             lp_rmin=n / 4.0, lp_rmax=n / 2.0 - 1.0, upsample=0, interp=0)
+             lp_rmin=n / 4.0, lp_rmax=n / 2.0 - 1.0, upsample=0, interp=0, ndp_bg_sigma=0.0)
     d.update(kw)
     return Opts(**d)
 
@@ -103,6 +105,7 @@ def _lib_handle():
                 "orc_bf16_round": ([C.c_double], C.c_double),
                 "orc_screen": ([_D, C.c_int, _D, C.c_int, C.c_long, C.c_int, _D], None),
                 "orc_ndp_normalise": ([_D, C.c_long, _D], C.c_int),
+                "orc_ndp_background": ([_D, C.c_int, C.c_double, _D], None),
                 "orc_ndp": ([_D, _D, C.c_long], C.c_double),
                 "orc_ndp_index": ([_D, C.c_int, _D, C.c_int, C.c_long, _I, _D, _D], None),
                 "orc_scan_orientation": ([_D, C.c_int, C.c_double, C.c_double, C.c_double, _D], None),
@@ -389,6 +392,15 @@ def ndp_normalise(img):
     out = np.empty_like(img)
     deg = _lib_handle().orc_ndp_normalise(_d(img), img.size, _d(out))
     return out, bool(deg)
+
+
+def ndp_background(img, sigma=0.0):
+    """Background correction before the NDP: img minus its Gaussian blur
+    (sigma px; 0 = n/8; < 0 = unchanged), edges repeated."""
+    img = _f64(img)
+    out = np.empty_like(img)
+    _lib_handle().orc_ndp_background(_d(img), img.shape[0], float(sigma), _d(out))
+    return out
 
 
 def ndp(a, b):

@@ -41,6 +41,7 @@ typedef struct {
     double lp_rmax;      /* largest radius, pixels                             */
     int32_t upsample;    /* 0: 3-point parabola; U >= 2: up-sampled peak       */
     int32_t interp;      /* master lookup: 0 bilinear, 1 bicubic (Keys)        */
+    double ndp_bg_sigma; /* NDP background: Gaussian sigma, px; 0 = n/8, < 0 off */
 } orc_opts;
 
 typedef struct {
@@ -883,6 +884,48 @@ int orc_ndp_normalise(const double *img, long d, double *out) {
     return 0;
 }
 
+/* Background correction before the NDP (the NDP section and the simulation
+ * set-up of the sampling-frequency section correct the background of every
+ * pattern and template first, drawing out the bands; the paper names the
+ * routine but not its form).  Reading: subtract the Gaussian-blurred image,
+ * blur = separable Gaussian of standard deviation sigma pixels with weights
+ * exp(-k^2 / (2 sigma^2)), k = -R..R, R = floor(3 sigma + 1/2), normalised to
+ * sum 1, and edge pixels repeated beyond the border.  sigma = 0 takes n / 8
+ * (the value that indexed the synthetic noisy maps best); sigma < 0 copies
+ * the image unchanged.  img, out [n][n]. */
+void orc_ndp_background(const double *img, int n, double sigma, double *out) {
+    long nn = (long)n * n;
+    if (sigma < 0) {
+        memcpy(out, img, sizeof(double) * nn);
+        return;
+    }
+    if (sigma == 0) sigma = n / 8.0;
+    int R = (int)(3.0 * sigma + 0.5);
+    double *w = malloc(sizeof(double) * (2 * R + 1)), sw = 0.0;
+    for (int k = -R; k <= R; ++k) sw += (w[k + R] = exp(-(double)k * k / (2.0 * sigma * sigma)));
+    for (int k = 0; k <= 2 * R; ++k) w[k] /= sw;
+    double *rows = malloc(sizeof(double) * nn);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int k = -R; k <= R; ++k) {
+                int c = j + k < 0 ? 0 : (j + k >= n ? n - 1 : j + k);
+                s += w[k + R] * img[(long)i * n + c];
+            }
+            rows[(long)i * n + j] = s;
+        }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int k = -R; k <= R; ++k) {
+                int r = i + k < 0 ? 0 : (i + k >= n ? n - 1 : i + k);
+                s += w[k + R] * rows[(long)r * n + j];
+            }
+            out[(long)i * n + j] = img[(long)i * n + j] - s;
+        }
+    free(w); free(rows);
+}
+
 /* Eq. 1 for one pair: the mean over the d pixels of the products of the two
  * contrast-normalised images.  Reading: the printed formula carries both a
  * 1/d and the two vector norms, which would give 1/d for identical images,
@@ -946,20 +989,24 @@ void orc_scan_orientation(const double q[4], int axis, double theta, double samp
  * and z axes by theta_j = (j - nh) step_deg, j = 0..2 nh, projected at pc_test
  * (the PC-error experiment of Fig. 4 A-C when pc_test differs).  For each
  * axis a and step j:
- *   ndp[a L + j] = Eq. 1 between reference and test (contrast-normalised);
+ *   ndp[a L + j] = Eq. 1 between reference and test (background-corrected,
+ *                  contrast-normalised);
  *   xcf[a L + j] = peak of the FFT cross-correlation (Eqs. 4-6: window,
  *                  band-pass, unit-norm spectra; integer peak, or the
  *                  up-sampled peak when o->upsample >= 2), reference as the
  *                  template, 0 if either image is degenerate;
- * L = 2 nh + 1.  pcs are those of the n x n (cropped) screen. */
+ * L = 2 nh + 1.  pcs are those of the n x n (cropped) screen.  The NDP
+ * compares the background-corrected images (orc_ndp_background with
+ * o->ndp_bg_sigma), the FFT the raw ones through its own filters. */
 void orc_rotation_scan(const float *master, int M, int n, const double pc_ref[3], const double pc_test[3],
                        double sample_tilt_deg, double detector_tilt_deg, const orc_opts *o,
                        const double q[4], int nh, double step_deg, double *ndp, double *xcf) {
     long nn = (long)n * n;
     int L = 2 * nh + 1;
-    double *ref = malloc(sizeof(double) * nn);
+    double *ref = malloc(sizeof(double) * nn), *refb = malloc(sizeof(double) * nn);
     cplx *Sr = malloc(sizeof(cplx) * nn);
     orc_project_interp(master, M, q, pc_ref, sample_tilt_deg, detector_tilt_deg, n, ref, o->interp);
+    orc_ndp_background(ref, n, o->ndp_bg_sigma, refb);
     int dref = orc_prep(ref, n, o, Sr, NULL);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int k = 0; k < 3 * L; ++k) {
@@ -970,7 +1017,8 @@ void orc_rotation_scan(const float *master, int M, int n, const double pc_ref[3]
         double *img = malloc(sizeof(double) * nn), *r = malloc(sizeof(double) * nn);
         cplx *St = malloc(sizeof(cplx) * nn);
         orc_project_interp(master, M, qt, pc_test, sample_tilt_deg, detector_tilt_deg, n, img, o->interp);
-        ndp[k] = orc_ndp(ref, img, nn);
+        orc_ndp_background(img, n, o->ndp_bg_sigma, r);
+        ndp[k] = orc_ndp(refb, r, nn);
         int dt = orc_prep(img, n, o, St, NULL);
         double pk = 0.0;
         if (!dref && !dt) {
@@ -987,7 +1035,7 @@ void orc_rotation_scan(const float *master, int M, int n, const double pc_ref[3]
         xcf[k] = pk;
         free(img); free(r); free(St);
     }
-    free(ref); free(Sr);
+    free(ref); free(refb); free(Sr);
 }
 
 /* Full width at half maximum of a correlation-versus-angle curve (the

@@ -171,7 +171,8 @@ def test_scan_self_match_at_zero(master):
 
 
 def test_scan_matches_its_definition(master):
-    """Each curve entry is Eq. 1 / the FFT peak of the two projections."""
+    """Each curve entry is Eq. 1 of the background-corrected projections / the
+    FFT peak of the two projections."""
     q = synth.random_quaternions(1, 6)[0]
     n, pc, pt = 64, (0.5, 0.3, 0.6), (0.51, 0.3, 0.6)
     nd, xc = orc.rotation_scan(master, q, pc, n, 3, 2.0, pc_test=pt)
@@ -180,7 +181,7 @@ def test_scan_matches_its_definition(master):
     for ax, j in ((0, 0), (1, 5), (2, 6)):
         qt = orc.scan_orientation(q, ax, math.radians((j - 3) * 2.0))
         t = orc.project_many(master, qt[None], pt, n)[0]
-        assert nd[ax, j] == pytest.approx(orc.ndp(ref, t), abs=1e-14)
+        assert nd[ax, j] == pytest.approx(orc.ndp(orc.ndp_background(ref), orc.ndp_background(t)), abs=1e-14)
         St, _, _ = orc.prep(t)
         assert xc[ax, j] == pytest.approx(orc.peak(orc.xcf_surface(Sr, St))[0], abs=1e-14)
 
@@ -207,3 +208,37 @@ def test_pc_error_costs_ndp_more_than_fft(master):
     for d in ((0.02, 0, 0), (0, 0.02, 0), (0, 0, 0.02)):
         nd, xc = orc.rotation_scan(master, q, pc, 128, 1, 0.5, pc_test=tuple(np.add(pc, d)))
         assert xc[0, 1] > 0.98 and nd[0, 1] < xc[0, 1] - 0.02, (d, nd[0, 1], xc[0, 1])
+
+
+# ------------------------------------------------- background correction
+def test_background_is_image_minus_scipy_gaussian():
+    from scipy import ndimage
+    rng = np.random.default_rng(8)
+    for n, sigma in ((16, 1.3), (32, 0.0), (64, 5.0), (64, 11.7)):
+        img = rng.random((n, n)) + np.linspace(0, 3, n)[None, :]
+        s = n / 8.0 if sigma == 0 else sigma
+        ref = img - ndimage.gaussian_filter(img, s, mode="nearest", truncate=3.0)
+        np.testing.assert_allclose(orc.ndp_background(img, sigma), ref, atol=1e-12)
+
+
+def test_background_off_constant_and_ramp():
+    rng = np.random.default_rng(9)
+    img = rng.random((32, 32))
+    np.testing.assert_array_equal(orc.ndp_background(img, -1.0), img)
+    assert np.abs(orc.ndp_background(np.full((32, 32), 4.2), 3.0)).max() < 1e-13
+    # a linear ramp is reproduced by a symmetric blur away from the edges
+    ramp = np.tile(np.arange(64, dtype=float), (64, 1))
+    out = orc.ndp_background(ramp, 4.0)
+    assert np.abs(out[:, 13:-13]).max() < 1e-12 and np.abs(out[:, :3]).max() > 0.1
+
+
+def test_scan_uses_background_corrected_ndp(master):
+    """The NDP curve of the scan is Eq. 1 of the background-corrected images."""
+    q = synth.random_quaternions(1, 12)[0]
+    n, pc = 64, (0.5, 0.3, 0.6)
+    nd, _ = orc.rotation_scan(master, q, pc, n, 2, 3.0)
+    nd_off, _ = orc.rotation_scan(master, q, pc, n, 2, 3.0, opts=orc.default_opts(n, ndp_bg_sigma=-1.0))
+    ref = orc.project_many(master, q[None], pc, n)[0]
+    t = orc.project_many(master, orc.scan_orientation(q, 1, math.radians(3.0))[None], pc, n)[0]
+    assert nd[1, 3] == pytest.approx(orc.ndp(orc.ndp_background(ref), orc.ndp_background(t)), abs=1e-14)
+    assert nd_off[1, 3] == pytest.approx(orc.ndp(ref, t), abs=1e-14)
