@@ -53,11 +53,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="patterns in the CPU sample (0: auto)")
-    ap.add_argument("--form", default="plain", choices=["plain", "precision", "batched", "learned"],
+    ap.add_argument("--form", default="plain", choices=["plain", "precision", "batched", "learned", "ndp"],
                     help="plain: full FP32 XCF search + refinement of the 128^2 map; precision: BF16 "
                          "tensor-core screen top-32 + FP32 rescore + refinement at 256^2; batched: eight maps "
                          "with different detectors in one persistent graph-captured search; learned: CNN proposals "
-                         "+ correlation score + refinement with full-search fallback")
+                         "+ correlation score + refinement with full-search fallback; ndp: normalised dot product "
+                         "(Eq. 1) over the 2.5 deg library on the tensor cores + FP32 rescore + refinement of the "
+                         "same 128^2 map")
     ap.add_argument("--patterns", type=int, default=0, help="precision form: patterns per GPU (0: 50,000)")
     ap.add_argument("--scale", type=float, default=1.0, help="batched form: scale of every map's pattern count")
     ap.add_argument("--upsample", type=int, default=0,
@@ -313,6 +315,89 @@ def run_precision(args, px, torch, dev, rank, world, local, dist):
                 "accuracy": accuracy, "gpu_launches": int(sum(v[1] for v in prof.values())), "clocks": clocks,
                 "roofline": roofline, "e2e": None, "cpu_baseline": None}
         print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- ndp form
+def run_ndp(args, px, torch, dev, rank, world, local, dist):
+    """NDP dictionary indexing (Eq. 1) of the plain form's map against the
+    2.5 deg library, then the same refinement."""
+    wl = synth.config_ndp_128(seed=rank, ny=args.map, nx=args.map)
+    n, P, T, k = wl["n"], len(wl["truth_q"]), len(wl["lib_q"]), wl["k"]
+    geom = px.geometry(n, n, wl["pc"])
+    ctx = px.Context(max_iter=wl["max_iter"], tol_deg=1e-3)
+    master_d = torch.from_numpy(np.ascontiguousarray(wl["master"])).to(dev)
+    libq_d = torch.from_numpy(wl["lib_q"]).to(dev)
+    truth_d = torch.from_numpy(wl["truth_q"]).to(dev)
+    pcs_d = torch.from_numpy(wl["pcs"]).to(dev)
+    clean = px.xcf_project(ctx, master_d, truth_d, geom, pcs=pcs_d).cpu().numpy()
+    pats_d = torch.from_numpy(synth.add_noise(clean, wl["pcs"], wl["peak"], wl["noise_seed"])).to(dev)
+    del clean
+    outq = (torch.empty((P, 4), dtype=torch.float64, device=dev), torch.empty(P, device=dev),
+            torch.empty(P, dtype=torch.int32, device=dev))
+    res = {}
+
+    def step():
+        lib = px.xcf.xcf_build_library_ex(ctx, libq_d, geom, master=master_d,
+                                          flags=px.XCF_LIB_NDP | px.XCF_LIB_NO_SPECTRA)
+        best, ndp = px.xcf_index_ndp(ctx, lib, pats_d, k=k)
+        px.xcf_refine_best(ctx, lib, pats_d, best, pcs=pcs_d, out=outq)
+        res["best"], res["ndp"] = best, ndp
+        lib.close()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    mis = px.xcf_disorientation(ctx, outq[0], truth_d)
+    lib_mis = px.xcf_disorientation(ctx, libq_d[res["best"].clamp(min=0).long()].contiguous(), truth_d)
+    accuracy = {"mean_misorientation_deg": float(mis.mean()), "median_misorientation_deg": float(mis.median()),
+                "frac_below_1deg": float((mis < 1.0).double().mean()),
+                "library_match_mean_deg": float(lib_mis.mean()), "iters_mean": float(outq[2].double().mean()),
+                "ndp_mean": float(res["ndp"].mean())}
+    px.xcf_profile_read(ctx, reset=True)
+    px.xcf_profile_enable(ctx, True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks_start(local)
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        step()
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = clocks_stop(clk)
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    px.xcf_profile_enable(ctx, False)
+    prof = px.xcf_profile_read(ctx, reset=True)
+    pk = peaks_file() or {}
+    tensor_peak = pk.get("bf16_tflops_sustained") or 1700.0
+    s_ms, s_n = prof["screen"]
+    flops_step = 2.0 * P * T * n * n
+    achieved = flops_step * args.steps / (s_ms / 1e3) / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": tensor_peak, "unit": "TFLOP/s",
+                "frac": achieved / tensor_peak, "traffic": None, "kernel": "k_screen_tc (NDP operands)",
+                "peak_basis": "measured sustained cuBLAS BF16 (MEASURED_PEAKS.json)" if pk else "fallback",
+                "screen_ms_per_launch": s_ms / max(s_n, 1), "launches_per_step": s_n / args.steps,
+                "stage_ms_per_step": {kk: v[0] / args.steps for kk, v in prof.items()}}
+    value = P * args.steps * world / (elapsed_ms / 1e3)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16 ndp + f32 rescore / refinement",
+                "data": "synthetic",
+                "config": {"workload": wl["name"], "form": "ndp", "detector": n, "templates": T,
+                           "patterns_per_gpu": P, "top_k": k, "max_iter": wl["max_iter"],
+                           "parallelism": f"replicas x{world}",
+                           "l2": _l2_note(pats_d.numel() * 4, T * n * n * 6, "FP32 + BF16 NDP templates")},
+                "accuracy": accuracy, "gpu_launches": int(sum(v[1] for v in prof.values())), "clocks": clocks,
+                "roofline": roofline, "e2e": None, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 # ----------------------------------------------------------- batched form
@@ -617,8 +702,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    if args.form in ("precision", "batched", "learned"):
-        fn = {"precision": run_precision, "batched": run_batched, "learned": run_learned}[args.form]
+    if args.form in ("precision", "batched", "learned", "ndp"):
+        fn = {"precision": run_precision, "batched": run_batched, "learned": run_learned, "ndp": run_ndp}[args.form]
         fn(args, px, torch, dev, rank, world, local, dist)
         if dist:
             dist.destroy_process_group()

@@ -67,6 +67,11 @@ typedef struct {
                               on the equal-area grid (default); 1 = bicubic (Keys'
                               cubic convolution, a = -1/2), the paper's bicubic
                               reprojection on the same grid                         */
+    double ndp_bg_sigma; /* background correction of the NDP (xcf_index_ndp, the NDP
+                            curves of xcf_rotation_scan): each crop minus its
+                            Gaussian blur of this sigma in px (truncated at
+                            round(3 sigma), edges repeated); 0 = N/8 (default),
+                            < 0 = no correction                                     */
 } xcf_options;
 
 /* Detector geometry of a map (or of a library). */

@@ -142,6 +142,36 @@ Resolved resolve(const xcf_options &o, int n) {
     return r;
 }
 
+// background sigma of the NDP for side n (0 = no correction)
+float ndp_sigma(const xcf_options &o, int n) {
+    if (o.ndp_bg_sigma < 0) return 0.f;
+    const double s = o.ndp_bg_sigma > 0 ? o.ndp_bg_sigma : n / 8.0;
+    return (float)(s < n ? s : n);
+}
+
+// contrast-normalised (and, with the background option, first background-
+// corrected) crops of P images -> out32 / out16 (NDP operands)
+int ndp_operands(xcf_ctx *ctx, const float *img, int P, long img_stride, int row_stride, int ox, int oy, int n,
+                 float *out32, void *out16, int *degen, cudaStream_t st) {
+    const float sg = ndp_sigma(ctx->opt, n);
+    if (sg > 0.f) {
+        float *tmp, *cor;
+        int rc;
+        if ((rc = scratch_t(ctx, S_BG_TMP, (size_t)n * n * P, &tmp)) ||
+            (rc = scratch_t(ctx, S_BG_OUT, (size_t)n * n * P, &cor)))
+            return rc;
+        XCF_LAUNCH(XCF_STAGE_PREP, st, launch_ndp_background(img, P, img_stride, row_stride, ox, oy, n, sg, tmp, cor, st),
+                   "ndp background");
+        img = cor;
+        img_stride = (long)n * n;
+        row_stride = n;
+        ox = oy = 0;
+    }
+    XCF_LAUNCH(XCF_STAGE_PREP, st, launch_ndp_norm(img, P, img_stride, row_stride, ox, oy, n, out32, out16, degen, st),
+               "ndp normalise");
+    return XCF_OK;
+}
+
 PrepArgs prep_args(const xcf_geometry *g, const Crop &c, const Resolved &r) {
     PrepArgs a;
     a.N = c.n;
@@ -363,6 +393,7 @@ int xcf_options_default(xcf_options *o) {
     o->tol_deg = 1e-3;
     o->upsample = 0;
     o->master_interp = 0;
+    o->ndp_bg_sigma = 0.0;
     return XCF_OK;
 }
 
@@ -386,6 +417,7 @@ int xcf_create(xcf_ctx **out, const xcf_options *opt, int device) {
         if (o.window < 0 || o.window > 1 || o.max_iter < 0 || o.sigma_hp < 0) return XCF_ERR_ARG;
         if (o.upsample != 0 && (o.upsample < 2 || o.upsample > 20)) return XCF_ERR_ARG;
         if (o.master_interp < 0 || o.master_interp > 1) return XCF_ERR_ARG;
+        if (!(o.ndp_bg_sigma == o.ndp_bg_sigma)) return XCF_ERR_ARG;   // NaN
     } else {
         xcf_options_default(&o);
     }
@@ -936,11 +968,9 @@ int make_ndp_images(xcf_ctx *ctx, xcf_library *lib, const float *images, cudaStr
         float *o32 = lib->ndp32 + nn * t0;
         void *o16 = static_cast<char *>(lib->ndp16) + 2 * nn * t0;
         if (images) {
-            XCF_LAUNCH(XCF_STAGE_PREP, st,
-                       launch_ndp_norm(images + (size_t)g->width * g->height * t0, nt,
-                                       (long)g->width * g->height, g->width, c.ox, c.oy, c.n, o32, o16, nullptr,
-                                       st),
-                       "ndp normalise");
+            if ((rc = ndp_operands(ctx, images + (size_t)g->width * g->height * t0, nt, (long)g->width * g->height,
+                                   g->width, c.ox, c.oy, c.n, o32, o16, nullptr, st)))
+                return rc;
         } else {
             float *img;
             if ((rc = scratch_t(ctx, S_IMG, nn * nt, &img))) return rc;
@@ -948,8 +978,7 @@ int make_ndp_images(xcf_ctx *ctx, xcf_library *lib, const float *images, cudaStr
                        launch_project(lib->master, lib->M, lib->quats + 4 * (size_t)t0, nullptr, nullptr, nt,
                                       proj_args_cropped(g, c, ctx->opt.master_interp), img, st),
                        "ndp project");
-            XCF_LAUNCH(XCF_STAGE_PREP, st,
-                       launch_ndp_norm(img, nt, (long)nn, c.n, 0, 0, c.n, o32, o16, nullptr, st), "ndp normalise");
+            if ((rc = ndp_operands(ctx, img, nt, (long)nn, c.n, 0, 0, c.n, o32, o16, nullptr, st))) return rc;
         }
     }
     return XCF_OK;
@@ -1172,9 +1201,8 @@ int xcf_index_ndp(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, i
                    (rc = scratch_t(ctx, S_CANDSC, (size_t)np * k, &csc))) {
             return rc;
         }
-        XCF_LAUNCH(XCF_STAGE_PREP, st,
-                   launch_ndp_norm(patterns + img * p0, np, (long)img, g->width, c.ox, c.oy, c.n, pn, a, degen, st),
-                   "ndp normalise");
+        if ((rc = ndp_operands(ctx, patterns + img * p0, np, (long)img, g->width, c.ox, c.oy, c.n, pn, a, degen, st)))
+            return rc;
         XCF_LAUNCH(XCF_STAGE_SCREEN, st, launch_screen_tc(a, np, lib->ndp16, lib->T, (int)nn, S, err, st), "ndp gemm");
         XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_topk_rows(S, np, lib->T, k, cd, csc, st), "topk");
         XCF_LAUNCH(XCF_STAGE_SEARCH, st,
@@ -1223,8 +1251,7 @@ int xcf_rotation_scan(xcf_ctx *ctx, const float *master, int32_t M, const xcf_ge
                               imgs, st),
                "scan project");
     // Eq. 1: every image normalised, then each test image against the reference (entry 0)
-    XCF_LAUNCH(XCF_STAGE_PREP, st,
-               launch_ndp_norm(imgs, n_img, (long)nn, c.n, 0, 0, c.n, pn, nullptr, degen, st), "ndp normalise");
+    if ((rc = ndp_operands(ctx, imgs, n_img, (long)nn, c.n, 0, 0, c.n, pn, nullptr, degen, st))) return rc;
     XCF_LAUNCH(XCF_STAGE_SEARCH, st,
                launch_ndp_rescore(pn + nn, pn, (long)nn, zeros, 1, degen + 1, nt, junk_best, ndp, st), "ndp pairs");
     // FFT XCF: the reference's spectrum as the template of every test image

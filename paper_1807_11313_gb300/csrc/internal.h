@@ -47,6 +47,8 @@ enum Slot {
     S_CAND,         // screen candidates of a chunk [P, k]
     S_CANDSC,       // their screen scores
     S_ARGMAX,       // integer peak positions for the up-sampled peak
+    S_BG_TMP,       // NDP background correction: row-blurred crops
+    S_BG_OUT,       // NDP background correction: corrected crops
     S_COUNT
 };
 

@@ -11,6 +11,9 @@
 //   per pixel (FP32 and BF16 outputs).
 // k_ndp_rescore: FP32 NDP of each pattern against its k candidates, the best
 //   by (score desc, template asc).  HBM: 4 B per pixel of each candidate.
+// k_bg_rows / k_bg_cols: background correction before the NDP, the crop minus
+//   its separable Gaussian blur (rows through shared memory into a work array,
+//   then 32-column strips of it).  HBM: about 20 B per pixel.
 // k_fwhm: full width at half maximum of correlation-versus-angle curves, one
 //   thread per curve.
 #include <cuda_bf16.h>
@@ -104,6 +107,77 @@ __global__ void __launch_bounds__(kRescoreThreads) k_ndp_rescore(const float *__
     if (tid == 0) { best[p] = bt; score[p] = bt < 0 ? 0.f : bs; }
 }
 
+// ---- background correction: crop minus its separable Gaussian blur (weights
+// exp(-k^2 / (2 sigma^2)), |k| <= R, normalised; edge pixels repeated)
+constexpr int kBgRows = 8, kBgThreads = 256;
+
+__device__ __forceinline__ void bg_weights(float *w, int R, float sigma) {
+    const float c = -0.5f / (sigma * sigma);
+    for (int k = threadIdx.x; k <= 2 * R; k += blockDim.x) w[k] = expf(c * (float)((k - R) * (k - R)));
+    __syncthreads();
+    // every thread sums the weights in the same order, so all hold the same total
+    float s = 0.f;
+    for (int k = 0; k <= 2 * R; ++k) s += w[k];
+    __syncthreads();
+    const float inv = 1.f / s;
+    for (int k = threadIdx.x; k <= 2 * R; k += blockDim.x) w[k] *= inv;
+    __syncthreads();
+}
+
+// rows: tmp [P][n][n] = horizontal blur of the crop; grid (n / kBgRows, P)
+__global__ void __launch_bounds__(kBgThreads) k_bg_rows(const float *__restrict__ img, long img_stride,
+                                                        int row_stride, int ox, int oy, int n, int R, float sigma,
+                                                        float *__restrict__ tmp) {
+    extern __shared__ float4 smem_raw[];
+    float *w = reinterpret_cast<float *>(smem_raw);   // [2R + 1]
+    float *rows = w + ((2 * R + 4) & ~3);              // [kBgRows][n]
+    const int p = blockIdx.y, r0 = blockIdx.x * kBgRows, lg = __ffs(n) - 1;
+    const float *src = img + (size_t)p * img_stride + (size_t)(oy + r0) * row_stride + ox;
+    for (int i = threadIdx.x; i < kBgRows * n; i += kBgThreads)
+        rows[i] = __ldg(src + (size_t)(i >> lg) * row_stride + (i & (n - 1)));
+    bg_weights(w, R, sigma);
+    float *dst = tmp + (size_t)p * n * n + (size_t)r0 * n;
+    for (int i = threadIdx.x; i < kBgRows * n; i += kBgThreads) {
+        const int r = i >> lg, c = i & (n - 1);
+        const float *row = rows + r * n;
+        float s = 0.f;
+        if (c - R >= 0 && c + R < n) {
+            for (int k = -R; k <= R; ++k) s = fmaf(w[k + R], row[c + k], s);
+        } else {
+            for (int k = -R; k <= R; ++k) s = fmaf(w[k + R], row[min(max(c + k, 0), n - 1)], s);
+        }
+        dst[i] = s;
+    }
+}
+
+// columns: out [P][n][n] = crop - vertical blur of tmp; grid (n / 32, P),
+// lane = column of a 32-wide strip, warp = row phase
+__global__ void __launch_bounds__(kBgThreads) k_bg_cols(const float *__restrict__ img, long img_stride,
+                                                        int row_stride, int ox, int oy, int n, int R, float sigma,
+                                                        const float *__restrict__ tmp, float *__restrict__ out) {
+    extern __shared__ float4 smem_raw[];
+    float *w = reinterpret_cast<float *>(smem_raw);
+    float *strip = w + ((2 * R + 4) & ~3);              // [n][32]
+    const int p = blockIdx.y, c0 = blockIdx.x * 32, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float *t = tmp + (size_t)p * n * n + c0;
+    const int wdt = n < 32 ? n : 32;   // strip width (n = 16: half the lanes idle)
+    for (int i = threadIdx.x; i < n * 32; i += kBgThreads)
+        strip[i] = (i & 31) < wdt ? __ldg(t + (size_t)(i >> 5) * n + (i & 31)) : 0.f;
+    bg_weights(w, R, sigma);
+    if (lane >= wdt) return;
+    const float *src = img + (size_t)p * img_stride + (size_t)oy * row_stride + ox + c0 + lane;
+    float *dst = out + (size_t)p * n * n + c0 + lane;
+    for (int r = warp; r < n; r += kBgThreads / 32) {
+        float s = 0.f;
+        if (r - R >= 0 && r + R < n) {
+            for (int k = -R; k <= R; ++k) s = fmaf(w[k + R], strip[(r + k) * 32 + lane], s);
+        } else {
+            for (int k = -R; k <= R; ++k) s = fmaf(w[k + R], strip[min(max(r + k, 0), n - 1) * 32 + lane], s);
+        }
+        dst[(size_t)r * n] = __ldg(src + (size_t)r * row_stride) - s;
+    }
+}
+
 // curves c < nc/2 read a, the others b; each [L] sampled at (j - (L-1)/2) step
 __global__ void k_fwhm(const float *__restrict__ a, const float *__restrict__ b, int nc, int L, float step,
                        float *__restrict__ out) {
@@ -146,5 +220,23 @@ cudaError_t launch_ndp_rescore(const float *pn, const float *tn, long d, const i
 cudaError_t launch_fwhm(const float *a, const float *b, int nc, int L, float step, float *out, cudaStream_t st) {
     if (nc <= 0) return cudaSuccess;
     k_fwhm<<<(nc + 63) / 64, 64, 0, st>>>(a, b, nc, L, step, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ndp_background(const float *img, int P, long img_stride, int row_stride, int ox, int oy, int n,
+                                  float sigma, float *tmp, float *out, cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    if (n < 16 || (n & (n - 1)) || !(sigma > 0.f) || sigma > (float)n) return cudaErrorInvalidValue;
+    const int R = (int)(3.0f * sigma + 0.5f);
+    const size_t wb = sizeof(float) * (size_t)((2 * R + 4) & ~3);
+    const size_t sm_rows = wb + sizeof(float) * kBgRows * n, sm_cols = wb + sizeof(float) * 32 * n;
+    cudaError_t e = cudaFuncSetAttribute(k_bg_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_rows);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_bg_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cols);
+    if (e != cudaSuccess) return e;
+    k_bg_rows<<<dim3(n / kBgRows, P), kBgThreads, sm_rows, st>>>(img, img_stride, row_stride, ox, oy, n, R, sigma,
+                                                                   tmp);
+    k_bg_cols<<<dim3((n + 31) / 32, P), kBgThreads, sm_cols, st>>>(img, img_stride, row_stride, ox, oy, n, R, sigma, tmp,
+                                                              out);
     return cudaGetLastError();
 }

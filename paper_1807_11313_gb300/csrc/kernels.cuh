@@ -130,6 +130,10 @@ cudaError_t launch_disorientation(const double *qa, const double *qb, int n, dou
 // (ox, oy), side n a power of two) -> out32 [P][n*n] and / or out16 (BF16), degen [P]
 cudaError_t launch_ndp_norm(const float *img, int P, long img_stride, int row_stride, int ox, int oy, int n,
                             float *out32, void *out16, int *degen, cudaStream_t st);
+// background correction of the same crops: out [P][n][n] = crop - Gaussian
+// blur (sigma px, 0 < sigma <= n), tmp [P][n][n] work array
+cudaError_t launch_ndp_background(const float *img, int P, long img_stride, int row_stride, int ox, int oy, int n,
+                                  float sigma, float *tmp, float *out, cudaStream_t st);
 // FP32 NDP of pattern p (pn [P][d]) against its candidates cand [P][k] of
 // tn [T][d] (< 0 skipped): best [P] (-1 if degenerate), score [P]
 cudaError_t launch_ndp_rescore(const float *pn, const float *tn, long d, const int *cand, int k, const int *degen,

@@ -352,6 +352,18 @@ def config_map_128(seed: int = 0, ny: int = 100, nx: int = 100, step_deg: float 
                 peak=100.0, noise_seed=seed + 3, max_iter=10)
 
 
+def config_ndp_128(seed: int = 0, ny: int = 100, nx: int = 100, step_deg: float = 2.5) -> dict:
+    """NDP dictionary-indexing workload: the 128 x 128 map of config_map_128
+    (same orientations, PCs and noise) against the library spacing the paper
+    gives the NDP (2.5 deg: 39,784 orientations in the cubic fundamental
+    zone), top-4 BF16 candidates rescored in FP32, then the same refinement."""
+    wl = config_map_128(seed=seed, ny=ny, nx=nx)
+    wl["lib_q"] = so3_grid_cubic_fz(step_deg)
+    wl["name"] = f"ndp128_T{len(wl['lib_q'])}_P{ny * nx}"
+    wl["k"] = 4
+    return wl
+
+
 def config_precision_256(seed: int = 0, P: int = 50000, step_deg: float = 3.14) -> dict:
     """Precision-form workload: BCC master (2 x 1024^2), 256 x 256 detector,
     ~20,000 library orientations (S^2 x S^1 FZ grid, 3.14 deg), P patterns at

@@ -41,6 +41,11 @@ def _tol(K):
     return 1e-5 + 1e-8 * K
 
 
+def _bg(orc, imgs, sigma):
+    """Oracle background correction of each image (sigma as the option)."""
+    return np.stack([orc.ndp_background(im, sigma) for im in imgs])
+
+
 def _ndp_vectors(orc, imgs, n):
     """Oracle contrast-normalised crops scaled by 1/n (unit vectors)."""
     return np.stack([orc.ndp_normalise(im)[0].ravel() / n for im in imgs])
@@ -58,16 +63,19 @@ def _case(orc, n, T, P, seed):
     return master, lq, timgs.astype(np.float32), pimgs.astype(np.float32)
 
 
-@pytest.mark.parametrize("n,T,P,k", [(64, 300, 37, 8), (128, 500, 21, 4)])
-def test_ndp_index_matches_oracle(px, orc, n, T, P, k):
+@pytest.mark.parametrize("n,T,P,k,sigma", [(64, 300, 37, 8, 0.0), (128, 500, 21, 4, 0.0), (64, 300, 37, 8, -1.0),
+                                           (16, 60, 9, 4, 0.0), (32, 80, 11, 3, 2.5)])
+def test_ndp_index_matches_oracle(px, orc, n, T, P, k, sigma):
     master, lq, timgs, pimgs = _case(orc, n, T, P, seed=n)
     pimgs[P - 1] = 3.0                                  # a constant (degenerate) pattern
-    ctx = px.Context()
+    ctx = px.Context(ndp_bg_sigma=sigma)
     g = px.geometry(n, n, PC0)
     lib = px.xcf.xcf_build_library_ex(ctx, dev(lq), g, images=dev(timgs),
                                       flags=px.XCF_LIB_NDP | px.XCF_LIB_NO_SPECTRA)
     best, ndp, cand, cs = px.xcf_index_ndp(ctx, lib, dev(pimgs), k=k, want_cand=True)
     best, ndp, cand, cs = host(best), host(ndp), host(cand), host(cs)
+    # background correction (or none with sigma < 0), then Eq. 1
+    timgs, pimgs = _bg(orc, timgs, sigma), _bg(orc, pimgs, sigma)
     vt, vp = _ndp_vectors(orc, timgs, n), _ndp_vectors(orc, pimgs, n)
     S_bf = orc.screen(vp, vt, bf16=True)
     S = vp @ vt.T                                        # Eq. 1, FP64
@@ -95,7 +103,7 @@ def test_ndp_index_matches_oracle(px, orc, n, T, P, k):
             assert best[p] == ob[p] or abs(S[p, best[p]] - osc[p]) <= 2e-6
     # an NDP-only library refuses the FFT search
     with pytest.raises(px.XcfError) as e:
-        px.xcf_index(ctx, lib, dev(pimgs))
+        px.xcf_index(ctx, lib, dev(pimgs.astype(np.float32)))
     assert e.value.code == -1
     lib.close()
     ctx.close()
@@ -104,7 +112,7 @@ def test_ndp_index_matches_oracle(px, orc, n, T, P, k):
 def test_ndp_cropped_detector_and_master_library(px, orc):
     """An 80 x 72 detector (crop 64 at offsets (8, 4)): the library projected
     from the master equals the one made from the detector images, and both
-    agree with the oracle on the crops."""
+    agree with the oracle on the background-corrected crops."""
     W, H, T, P = 80, 72, 120, 9
     master = synth.master_pattern("bcc", 512)
     lq = synth.random_quaternions(T, 3)
@@ -121,8 +129,8 @@ def test_ndp_cropped_detector_and_master_library(px, orc):
     bm, nm = px.xcf_index_ndp(ctx, lib_m, pats, k=4)
     bi, ni = px.xcf_index_ndp(ctx, lib_i, pats, k=4)
     assert torch.equal(bm, bi) and torch.equal(nm, ni)
-    crops_t = host(full_t)[:, oy:oy + n, ox:ox + n]
-    crops_p = host(pats)[:, oy:oy + n, ox:ox + n]
+    crops_t = _bg(orc, host(full_t)[:, oy:oy + n, ox:ox + n], 0.0)
+    crops_p = _bg(orc, host(pats)[:, oy:oy + n, ox:ox + n], 0.0)
     ob, osc, _ = orc.ndp_index(crops_p, crops_t)
     bm, nm = host(bm), host(nm)
     for p in range(P):
