@@ -178,6 +178,122 @@ __global__ void __launch_bounds__(kBgThreads) k_bg_cols(const float *__restrict_
     }
 }
 
+// ---- the same blur with the truncation radius R fixed at compile time (the
+// default sigma = N / 8 gives R = 3N / 8): the weights travel as a kernel
+// parameter (constant bank, read as FMA operands of the unrolled taps) and
+// every thread slides one window over J consecutive outputs, so a loaded
+// pixel feeds up to J FMAs.
+template <int R>
+struct BgW {
+    float w[2 * R + 1];
+};
+
+template <int N>
+struct BgShape {
+    static constexpr int J = N >= 64 ? 8 : N / 8;   // outputs per window
+    static constexpr int LANES = N < 32 ? N : 32;   // rows (row pass) / columns (column pass) per CTA
+    static constexpr int SPAN = N / 8;              // outputs of one warp along the blurred axis
+};
+
+// row pass: LANES rows per CTA, lane = row, the 8 warps split the columns;
+// padded rows (edges repeated R times) in shared memory with an odd stride
+template <int N, int R>
+__global__ void __launch_bounds__(kBgThreads) k_bg_rows_t(const float *__restrict__ img, long img_stride,
+                                                          int row_stride, int ox, int oy,
+                                                          const __grid_constant__ BgW<R> W, float *__restrict__ tmp) {
+    using S = BgShape<N>;
+    constexpr int PW = N + 2 * R, LD = PW + 1, OLD = N + 1;
+    extern __shared__ float4 smem_raw[];
+    float *rows = reinterpret_cast<float *>(smem_raw);   // [LANES][LD]
+    float *outs = rows + S::LANES * LD;                  // [LANES][OLD]
+    const int p = blockIdx.y, r0 = blockIdx.x * S::LANES;
+    const float *src = img + (size_t)p * img_stride + (size_t)(oy + r0) * row_stride + ox;
+    for (int i = threadIdx.x; i < S::LANES * PW; i += kBgThreads) {
+        const int r = i / PW, q = i % PW;
+        rows[r * LD + q] = __ldg(src + (size_t)r * row_stride + min(max(q - R, 0), N - 1));
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane < S::LANES) {
+        const float *row = rows + lane * LD;
+        for (int c0 = warp * S::SPAN; c0 < (warp + 1) * S::SPAN; c0 += S::J) {
+            float acc[S::J];
+#pragma unroll
+            for (int j = 0; j < S::J; ++j) acc[j] = 0.f;
+#pragma unroll
+            for (int m = 0; m < 2 * R + S::J; ++m) {
+                const float v = row[c0 + m];
+#pragma unroll
+                for (int j = 0; j < S::J; ++j)
+                    if (m - j >= 0 && m - j <= 2 * R) acc[j] = fmaf(W.w[m - j], v, acc[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < S::J; ++j) outs[lane * OLD + c0 + j] = acc[j];
+        }
+    }
+    __syncthreads();
+    float *dst = tmp + (size_t)p * N * N + (size_t)r0 * N;
+    for (int i = threadIdx.x; i < S::LANES * N; i += kBgThreads) dst[i] = outs[(i / N) * OLD + i % N];
+}
+
+// column pass: a strip of LANES columns per CTA, lane = column, the 8 warps
+// split the rows; padded strip (edge rows repeated R times) in shared memory
+template <int N, int R>
+__global__ void __launch_bounds__(kBgThreads) k_bg_cols_t(const float *__restrict__ img, long img_stride,
+                                                          int row_stride, int ox, int oy,
+                                                          const __grid_constant__ BgW<R> W,
+                                                          const float *__restrict__ tmp, float *__restrict__ out) {
+    using S = BgShape<N>;
+    constexpr int PH = N + 2 * R, L = S::LANES;
+    extern __shared__ float4 smem_raw[];
+    float *strip = reinterpret_cast<float *>(smem_raw);   // [PH][L]
+    const int p = blockIdx.y, c0 = blockIdx.x * L, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float *t = tmp + (size_t)p * N * N + c0;
+    for (int i = threadIdx.x; i < PH * L; i += kBgThreads) {
+        const int q = i / L, c = i % L;
+        strip[i] = __ldg(t + (size_t)min(max(q - R, 0), N - 1) * N + c);
+    }
+    __syncthreads();
+    if (lane >= L) return;
+    const float *src = img + (size_t)p * img_stride + (size_t)oy * row_stride + ox + c0 + lane;
+    float *dst = out + (size_t)p * N * N + c0 + lane;
+    for (int q0 = warp * S::SPAN; q0 < (warp + 1) * S::SPAN; q0 += S::J) {
+        float acc[S::J];
+#pragma unroll
+        for (int j = 0; j < S::J; ++j) acc[j] = 0.f;
+#pragma unroll
+        for (int m = 0; m < 2 * R + S::J; ++m) {
+            const float v = strip[(q0 + m) * L + lane];
+#pragma unroll
+            for (int j = 0; j < S::J; ++j)
+                if (m - j >= 0 && m - j <= 2 * R) acc[j] = fmaf(W.w[m - j], v, acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < S::J; ++j)
+            dst[(size_t)(q0 + j) * N] = __ldg(src + (size_t)(q0 + j) * row_stride) - acc[j];
+    }
+}
+
+template <int N, int R>
+cudaError_t bg_fixed(const float *img, int P, long img_stride, int row_stride, int ox, int oy, float sigma,
+                     float *tmp, float *out, cudaStream_t st) {
+    using S = BgShape<N>;
+    BgW<R> W;
+    double w[2 * R + 1], sw = 0.0;
+    for (int k = -R; k <= R; ++k) sw += (w[k + R] = exp(-(double)k * k / (2.0 * sigma * sigma)));
+    for (int k = 0; k <= 2 * R; ++k) W.w[k] = (float)(w[k] / sw);
+    const size_t sm_rows = sizeof(float) * S::LANES * ((N + 2 * R + 1) + (N + 1));
+    const size_t sm_cols = sizeof(float) * (N + 2 * R) * S::LANES;
+    cudaError_t e = cudaFuncSetAttribute(k_bg_rows_t<N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_rows);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_bg_cols_t<N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cols);
+    if (e != cudaSuccess) return e;
+    k_bg_rows_t<N, R><<<dim3(N / S::LANES, P), kBgThreads, sm_rows, st>>>(img, img_stride, row_stride, ox, oy, W, tmp);
+    k_bg_cols_t<N, R><<<dim3(N / S::LANES, P), kBgThreads, sm_cols, st>>>(img, img_stride, row_stride, ox, oy, W, tmp,
+                                                                          out);
+    return cudaGetLastError();
+}
+
 // curves c < nc/2 read a, the others b; each [L] sampled at (j - (L-1)/2) step
 __global__ void k_fwhm(const float *__restrict__ a, const float *__restrict__ b, int nc, int L, float step,
                        float *__restrict__ out) {
@@ -228,6 +344,12 @@ cudaError_t launch_ndp_background(const float *img, int P, long img_stride, int 
     if (P <= 0) return cudaSuccess;
     if (n < 16 || (n & (n - 1)) || !(sigma > 0.f) || sigma > (float)n) return cudaErrorInvalidValue;
     const int R = (int)(3.0f * sigma + 0.5f);
+    // the radii of the default sigma = n / 8 run the compile-time kernels
+    if (n == 16 && R == 6) return bg_fixed<16, 6>(img, P, img_stride, row_stride, ox, oy, sigma, tmp, out, st);
+    if (n == 32 && R == 12) return bg_fixed<32, 12>(img, P, img_stride, row_stride, ox, oy, sigma, tmp, out, st);
+    if (n == 64 && R == 24) return bg_fixed<64, 24>(img, P, img_stride, row_stride, ox, oy, sigma, tmp, out, st);
+    if (n == 128 && R == 48) return bg_fixed<128, 48>(img, P, img_stride, row_stride, ox, oy, sigma, tmp, out, st);
+    if (n == 256 && R == 96) return bg_fixed<256, 96>(img, P, img_stride, row_stride, ox, oy, sigma, tmp, out, st);
     const size_t wb = sizeof(float) * (size_t)((2 * R + 4) & ~3);
     const size_t sm_rows = wb + sizeof(float) * kBgRows * n, sm_cols = wb + sizeof(float) * 32 * n;
     cudaError_t e = cudaFuncSetAttribute(k_bg_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_rows);
