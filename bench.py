@@ -53,13 +53,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="patterns in the CPU sample (0: auto)")
-    ap.add_argument("--form", default="plain", choices=["plain", "precision", "batched", "learned", "ndp"],
+    ap.add_argument("--form", default="plain", choices=["plain", "precision", "batched", "learned", "ndp", "fwhm"],
                     help="plain: full FP32 XCF search + refinement of the 128^2 map; precision: BF16 "
                          "tensor-core screen top-32 + FP32 rescore + refinement at 256^2; batched: eight maps "
                          "with different detectors in one persistent graph-captured search; learned: CNN proposals "
                          "+ correlation score + refinement with full-search fallback; ndp: normalised dot product "
                          "(Eq. 1) over the 2.5 deg library on the tensor cores + FP32 rescore + refinement of the "
-                         "same 128^2 map")
+                         "same 128^2 map; fwhm: the peak-width experiments of Figs. 3-4 (rotation scans about the "
+                         "detector axes, NDP and FFT, against screen size and PC error)")
     ap.add_argument("--patterns", type=int, default=0, help="precision form: patterns per GPU (0: 50,000)")
     ap.add_argument("--scale", type=float, default=1.0, help="batched form: scale of every map's pattern count")
     ap.add_argument("--upsample", type=int, default=0,
@@ -68,6 +69,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=256, help="learned form: training batch")
     ap.add_argument("--epochs", type=int, default=2, help="learned form: passes over the training set")
     ap.add_argument("--lr", type=float, default=1e-3, help="learned form: peak learning rate")
+    ap.add_argument("--sigma-hp", type=float, default=0.0,
+                    help="fwhm form: high-pass sigma of the FFT path, cycles/image (0: the library default)")
     return ap.parse_args()
 
 
@@ -400,6 +403,85 @@ def run_ndp(args, px, torch, dev, rank, world, local, dist):
     ctx.close()
 
 
+# -------------------------------------------------------------- fwhm form
+FWHM_SIDES = (16, 32, 64, 128, 256)
+FWHM_DPC = (-0.04, -0.02, 0.0, 0.02, 0.04)
+
+
+def run_fwhm(args, px, torch, dev, rank, world, local, dist):
+    """Figs. 3-4: rotation scans (+-45 deg in 0.5 deg steps about detector x,
+    y, z) of a reference pattern at PC (0.5, 0.3, 0.6), NDP and FFT, for every
+    screen side, and at 128 x 128 for PC errors along x, y and z; FWHMs
+    averaged over four reference orientations.  One step = the whole sweep."""
+    pc0 = (0.5, 0.3, 0.6)
+    h, step_deg = 90, 0.5
+    master = torch.from_numpy(np.ascontiguousarray(synth.master_pattern("bcc", 1024))).to(dev)
+    qs = torch.from_numpy(synth.random_quaternions(4, 100 + rank)).to(dev)
+    ctx = px.Context(sigma_hp=args.sigma_hp) if args.sigma_hp > 0 else px.Context()
+    cases = [(n, None) for n in FWHM_SIDES]
+    cases += [(128, (ax, d)) for ax in range(3) for d in FWHM_DPC if d != 0.0]
+    pct = {}
+    for n, e in cases:
+        if e is not None:
+            pc = list(pc0)
+            pc[e[0]] += e[1]
+            pct[e] = torch.tensor(pc, dtype=torch.float64, device=dev)
+    out = {}
+
+    def step():
+        for n, e in cases:
+            g = px.geometry(n, n, pc0)
+            fws = []
+            for i in range(qs.shape[0]):
+                _, _, fw = px.xcf_rotation_scan(ctx, master, g, qs[i].contiguous(), h, step_deg,
+                                                pc_test=pct[e] if e is not None else None)
+                fws.append(fw)
+            out[(n, e)] = torch.stack(fws)
+
+    for _ in range(args.warmup):
+        step()
+    px.xcf_profile_read(ctx, reset=True)
+    px.xcf_profile_enable(ctx, True)
+    torch.cuda.synchronize()
+    clk = clocks_start(local)
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        step()
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = clocks_stop(clk)
+    elapsed_ms = ev0.elapsed_time(ev1)
+    px.xcf_profile_enable(ctx, False)
+    prof = px.xcf_profile_read(ctx, reset=True)
+
+    def summary(fw):
+        """FWHM per (method, axis) for each reference orientation (-1: wider than the scan)"""
+        f = fw.cpu().numpy()
+        return {f"{m}_{ax}": [round(float(v), 1) for v in f[:, r, a]]
+                for r, m in enumerate(("ndp", "fft")) for a, ax in enumerate("xyz")}
+
+    table = {"screen_side": {str(n): summary(out[(n, None)]) for n in FWHM_SIDES},
+             "pc_error_128": {f"d{'xyz'[a]}={d:+.2f}": summary(out[(128, (a, d))])
+                              for a in range(3) for d in FWHM_DPC if d != 0.0}}
+    images = sum((1 + 3 * (2 * h + 1)) * qs.shape[0] for _ in cases)
+    if rank == 0:
+        line = {"metric": "rotation-scan test patterns/s (FWHM experiments of Figs. 3-4)",
+                "value": images * args.steps / (elapsed_ms / 1e3), "unit": "patterns/s", "n_gpus": 1,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"fwhm_scan_h{h}_step{step_deg}_pc{pc0}", "form": "fwhm",
+                           "sigma_hp": ctx.options.sigma_hp,
+                           "scans_per_step": len(cases) * qs.shape[0], "patterns_per_scan": 1 + 3 * (2 * h + 1)},
+                "fwhm_deg": table, "gpu_launches": int(sum(v[1] for v in prof.values())), "clocks": clocks,
+                "stage_ms_per_step": {kk: v[0] / args.steps for kk, v in prof.items()},
+                "roofline": None, "e2e": None, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 # ----------------------------------------------------------- batched form
 def flops_per_pair(n: int) -> float:
     """Inverse real FFT of one n x n surface + conj-multiply of a half spectrum."""
@@ -702,8 +784,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    if args.form in ("precision", "batched", "learned", "ndp"):
-        fn = {"precision": run_precision, "batched": run_batched, "learned": run_learned, "ndp": run_ndp}[args.form]
+    if args.form in ("precision", "batched", "learned", "ndp", "fwhm"):
+        fn = {"precision": run_precision, "batched": run_batched, "learned": run_learned, "ndp": run_ndp,
+              "fwhm": run_fwhm}[args.form]
         fn(args, px, torch, dev, rank, world, local, dist)
         if dist:
             dist.destroy_process_group()
