@@ -112,6 +112,8 @@ def _lib_handle():
                 "orc_rotation_scan": ([_F, C.c_int, C.c_int, _D, _D, C.c_double, C.c_double, C.POINTER(Opts),
                                        _D, C.c_int, C.c_double, _D, _D], None),
                 "orc_fwhm": ([_D, C.c_int, C.c_double], C.c_double),
+                "orc_so3_grid": ([C.c_double, C.c_int, _D, C.c_long], C.c_long),
+                "orc_nearest_disorientation": ([_D, C.c_int, _D, C.c_int, C.c_int, _D, _I], None),
                 "orc_cnn_num_params": ([C.c_int], C.c_long),
                 "orc_cnn_standardise": ([_D, C.c_int, _D], None),
                 "orc_conv3x3s2": ([_D, C.c_int, C.c_int, _D, _D, C.c_int, _D], None),
@@ -450,6 +452,30 @@ def fwhm(curve, step):
     """Full width at half maximum of a centred curve (units of step); -1 if unresolved."""
     c = _f64(curve)
     return _lib_handle().orc_fwhm(_d(c), c.size, float(step))
+
+
+# ---------------------------------------------------------------- SO(3) sampling
+def so3_grid(step_deg, dedup=True):
+    """S^2 x S^1 library generator in the cubic fundamental zone -> [T, 4]."""
+    lib = _lib_handle()
+    n = lib.orc_so3_grid(float(step_deg), int(dedup), None, 0)
+    out = np.empty((n, 4))
+    lib.orc_so3_grid(float(step_deg), int(dedup), _d(out), n)
+    return out
+
+
+def nearest_disorientation(qa, qb=None, mode=None):
+    """Nearest qb (cubic disorientation) of every qa -> (angle_deg [na], index [na]).
+    qb None: qa against itself excluding self (mode 1); mode 2: earlier entries only."""
+    qa = _f64(qa)
+    same = qb is None
+    qb = qa if same else _f64(qb)
+    if mode is None:
+        mode = 1 if same else 0
+    ang = np.empty(len(qa))
+    idx = np.empty(len(qa), np.int32)
+    _lib_handle().orc_nearest_disorientation(_d(qa), len(qa), _d(qb), len(qb), int(mode), _d(ang), _i(idx))
+    return ang, idx
 
 
 # ---------------------------------------------------------------- refinement

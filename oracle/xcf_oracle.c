@@ -1061,3 +1061,95 @@ double orc_fwhm(const double *c, int L, double step) {
     double tr = r + (c[r] - h) / (c[r] - c[r + 1]);
     return (tr - tl) * step;
 }
+
+/* ---------------------------------------------------------------------- */
+/* SO(3) sampling: the library generator and the nearest-neighbour study   */
+/* (SO(3) Library Generation, Sampling Frequency; Eq. 6 (the second); Fig. 2) */
+/* ---------------------------------------------------------------------- */
+
+/* Bunge (phi1, Phi, phi2) -> q = qz(phi1) qx(Phi) qz(phi2), unit, w >= 0. */
+static void bunge_to_quat(double p1, double P, double p2, double q[4]) {
+    double a[4] = {cos(p1 / 2), 0, 0, sin(p1 / 2)}, b[4] = {cos(P / 2), sin(P / 2), 0, 0};
+    double c[4] = {cos(p2 / 2), 0, 0, sin(p2 / 2)}, t[4];
+    qmul(a, b, t);
+    qmul(t, c, q);
+    qnormalise(q);
+    if (q[0] < 0) for (int i = 0; i < 4; ++i) q[i] = -q[i];
+}
+
+/* Cubic (432) fundamental zone in Rodrigues space: |r_i| <= sqrt(2) - 1 and
+ * |r_1| + |r_2| + |r_3| <= 1, r = (x, y, z) / w; faces included (1e-12). */
+static int in_cubic_fz(const double q[4]) {
+    double w = q[0] > 1e-300 ? q[0] : 1e-300;
+    double r0 = fabs(q[1]) / w, r1 = fabs(q[2]) / w, r2 = fabs(q[3]) / w;
+    double m = r0 > r1 ? (r0 > r2 ? r0 : r2) : (r1 > r2 ? r1 : r2);
+    return m <= sqrt(2.0) - 1.0 + 1e-12 && r0 + r1 + r2 <= 1.0 + 1e-12;
+}
+
+/* The library generator (SO(3) Library Generation section: MTEX's S^2 x S^1
+ * scheme): the polar angle of S^2 split into n_p = round(pi / d) equal steps,
+ * ring i sampled at n_a = max(1, round(2 pi sin(Phi_i) / d)) azimuths (offset
+ * by half a step on odd rings), the rotation about each S^2 point (S^1) split
+ * into n_s = round(2 pi / d) equal steps; orientation = Bunge (azimuth, Phi,
+ * S^1 angle); kept where it falls in the cubic fundamental zone, in
+ * generation order (ring, azimuth, S^1).  Reading: points on the zone's faces
+ * are kept, and with dedup != 0 a point whose disorientation to an earlier
+ * kept point is below 1e-3 deg (a symmetry copy across a face) is dropped.
+ * Rounding: halves away from zero.  Writes at most cap orientations [cap][4]
+ * (out may be NULL) and returns the count. */
+long orc_so3_grid(double step_deg, int dedup, double *out, long cap) {
+    double d = step_deg * ORC_PI / 180.0;
+    long np_ = lround(ORC_PI / d), ns = lround(2 * ORC_PI / d);
+    if (np_ < 1) np_ = 1;
+    if (ns < 1) ns = 1;
+    long n = 0, kept_cap = 1024;
+    double *kept = malloc(sizeof(double) * 4 * kept_cap);
+    for (long i = 0; i <= np_; ++i) {
+        double Phi = ORC_PI * i / np_;
+        long na = lround(2 * ORC_PI * sin(Phi) / d);
+        if (na < 1) na = 1;
+        for (long j = 0; j < na; ++j) {
+            double p1 = 2 * ORC_PI * (j + 0.5 * (i % 2)) / na;
+            for (long k = 0; k < ns; ++k) {
+                double q[4];
+                bunge_to_quat(p1, Phi, 2 * ORC_PI * k / ns, q);
+                if (!in_cubic_fz(q)) continue;
+                int dup = 0;
+                for (long m = 0; dedup && m < n && !dup; ++m)
+                    dup = orc_disorientation(q, kept + 4 * m) < 1e-3;
+                if (dup) continue;
+                if (n == kept_cap) {
+                    kept_cap *= 2;
+                    kept = realloc(kept, sizeof(double) * 4 * kept_cap);
+                }
+                memcpy(kept + 4 * n, q, sizeof q);
+                if (out && n < cap) memcpy(out + 4 * n, q, sizeof q);
+                ++n;
+            }
+        }
+    }
+    free(kept);
+    return n;
+}
+
+/* Nearest neighbour under the cubic disorientation (the Fig. 2 study measures
+ * every library orientation's disorientation to its closest other member):
+ * for each qa[i], the qb[j] of smallest disorientation (ties -> lowest j) over
+ * j != i (mode 1: the two sets are one), j < i (mode 2), or every j (mode 0);
+ * angle in degrees, -1 and index -1 when there is no candidate. */
+void orc_nearest_disorientation(const double *qa, int na, const double *qb, int nb, int mode,
+                                double *angle, int32_t *index) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int i = 0; i < na; ++i) {
+        double best = -1.0;
+        int bj = -1;
+        int lim = mode == 2 ? (i < nb ? i : nb) : nb;
+        for (int j = 0; j < lim; ++j) {
+            if (mode == 1 && j == i) continue;
+            double a = orc_disorientation(qa + 4L * i, qb + 4L * j);
+            if (bj < 0 || a < best) { best = a; bj = j; }
+        }
+        angle[i] = best;
+        index[i] = bj;
+    }
+}
