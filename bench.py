@@ -53,14 +53,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="patterns in the CPU sample (0: auto)")
-    ap.add_argument("--form", default="plain", choices=["plain", "precision", "batched", "learned", "ndp", "fwhm"],
+    ap.add_argument("--form", default="plain",
+                    choices=["plain", "precision", "batched", "learned", "ndp", "fwhm", "so3"],
                     help="plain: full FP32 XCF search + refinement of the 128^2 map; precision: BF16 "
                          "tensor-core screen top-32 + FP32 rescore + refinement at 256^2; batched: eight maps "
                          "with different detectors in one persistent graph-captured search; learned: CNN proposals "
                          "+ correlation score + refinement with full-search fallback; ndp: normalised dot product "
                          "(Eq. 1) over the 2.5 deg library on the tensor cores + FP32 rescore + refinement of the "
                          "same 128^2 map; fwhm: the peak-width experiments of Figs. 3-4 (rotation scans about the "
-                         "detector axes, NDP and FFT, against screen size and PC error)")
+                         "detector axes, NDP and FFT, against screen size and PC error); so3: the SO(3) sampling "
+                         "study of Fig. 2 (library generation and nearest-neighbour disorientations)")
     ap.add_argument("--patterns", type=int, default=0, help="precision form: patterns per GPU (0: 50,000)")
     ap.add_argument("--scale", type=float, default=1.0, help="batched form: scale of every map's pattern count")
     ap.add_argument("--upsample", type=int, default=0,
@@ -482,6 +484,70 @@ def run_fwhm(args, px, torch, dev, rank, world, local, dist):
     ctx.close()
 
 
+# --------------------------------------------------------------- so3 form
+SO3_STEPS = (10.0, 7.5, 5.0, 3.5, 2.5)
+
+
+def run_so3(args, px, torch, dev, rank, world, local, dist):
+    """Fig. 2: for each sampling frequency, generate the library (S^2 x S^1
+    grid in the cubic zone, symmetry copies dropped), every member's
+    disorientation to its nearest other member (max / mean / median / mode
+    of the distribution) and the coverage of 100,000 random orientations.
+    One step = the whole sweep."""
+    ctx = px.Context()
+    rnd = torch.from_numpy(synth.random_quaternions(100000, 300 + rank)).to(dev)
+    res = {}
+
+    def step():
+        for sf in SO3_STEPS:
+            g = px.xcf_so3_grid(ctx, sf)
+            nn, _ = px.xcf_nearest_disorientation(ctx, g)
+            cov, _ = px.xcf_nearest_disorientation(ctx, rnd, g)
+            res[sf] = (g.shape[0], nn, cov)
+
+    for _ in range(args.warmup):
+        step()
+    px.xcf_profile_read(ctx, reset=True)
+    px.xcf_profile_enable(ctx, True)
+    torch.cuda.synchronize()
+    clk = clocks_start(local)
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        step()
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = clocks_stop(clk)
+    elapsed_ms = ev0.elapsed_time(ev1)
+    px.xcf_profile_enable(ctx, False)
+    prof = px.xcf_profile_read(ctx, reset=True)
+    table, pairs = {}, 0
+    for sf, (T, nn, cov) in res.items():
+        a = nn.cpu().numpy()
+        h, e = np.histogram(a, bins=np.arange(0.0, sf + 0.5, 0.1))
+        c = cov.cpu().numpy()
+        table[str(sf)] = {"orientations": int(T), "nn_max": round(float(a.max()), 3),
+                          "nn_mean": round(float(a.mean()), 3), "nn_median": round(float(np.median(a)), 3),
+                          "nn_mode_bin": round(float(e[h.argmax()]), 1),
+                          "nn_frac_below_0.9sf": round(float(np.mean(a < 0.9 * sf)), 3),
+                          "cover_max": round(float(c.max()), 3), "cover_mean": round(float(c.mean()), 3)}
+        pairs += T * T + rnd.shape[0] * T
+    if rank == 0:
+        line = {"metric": "orientation pairs compared/s (SO(3) sampling study of Fig. 2)",
+                "value": pairs * args.steps / (elapsed_ms / 1e3), "unit": "pairs/s", "n_gpus": 1,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 rank + f64 angle",
+                "data": "synthetic",
+                "config": {"workload": "so3_study_" + "_".join(str(x) for x in SO3_STEPS), "form": "so3",
+                           "random_orientations": int(rnd.shape[0])},
+                "so3": table, "gpu_launches": int(sum(v[1] for v in prof.values())), "clocks": clocks,
+                "stage_ms_per_step": {kk: v[0] / args.steps for kk, v in prof.items()},
+                "roofline": None, "e2e": None, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 # ----------------------------------------------------------- batched form
 def flops_per_pair(n: int) -> float:
     """Inverse real FFT of one n x n surface + conj-multiply of a half spectrum."""
@@ -784,9 +850,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    if args.form in ("precision", "batched", "learned", "ndp", "fwhm"):
+    if args.form in ("precision", "batched", "learned", "ndp", "fwhm", "so3"):
         fn = {"precision": run_precision, "batched": run_batched, "learned": run_learned, "ndp": run_ndp,
-              "fwhm": run_fwhm}[args.form]
+              "fwhm": run_fwhm, "so3": run_so3}[args.form]
         fn(args, px, torch, dev, rank, world, local, dist)
         if dist:
             dist.destroy_process_group()

@@ -292,6 +292,32 @@ int xcf_rotation_scan(xcf_ctx *ctx, const float *master, int32_t M, const xcf_ge
                       const double *pc_test, int32_t h, double step_deg, float *ndp, float *xcf, float *fwhm,
                       void *stream);
 
+/* SO(3) library generator (paper, "SO(3) Library Generation": the S^2 x S^1
+ * scheme of MTEX): the polar angle split into round(pi / d) equal steps, ring
+ * i sampled at max(1, round(2 pi sin(Phi_i) / d)) azimuths (half a step
+ * offset on odd rings), the rotation about each point split into round(2 pi /
+ * d) steps, d = step_deg; orientation = Bunge (azimuth, Phi, rotation) as a
+ * unit quaternion (w >= 0); kept where it lies in the cubic (432) fundamental
+ * zone (faces included), in generation order (ring, azimuth, rotation).
+ * With XCF_SO3_DEDUP a point within 1e-3 deg of an earlier in-zone point (a
+ * symmetry copy across a face) is dropped.  Rounding: halves away from zero.
+ *   *count (host) receives the number of orientations; quats [cap, 4] float64
+ *   (device, NULL to query the count) receives them; XCF_ERR_SIZE if cap is
+ *   smaller than the count.  0.5 <= step_deg <= 180.  Synchronous. */
+#define XCF_SO3_DEDUP 1
+int xcf_so3_grid(xcf_ctx *ctx, double step_deg, int32_t flags, double *quats, int64_t cap, int64_t *count,
+                 void *stream);
+
+/* Nearest neighbour under the cubic disorientation (the second Eq. 6; the
+ * Fig. 2 study of a library's spacing): for each qa[i] the qb[j] of smallest
+ * disorientation, over every j (mode 0), j != i (mode 1; the sets are one,
+ * qb may be NULL = qa) or j < i (mode 2).  Pairs are ranked in FP32 (ties ->
+ * lowest j); the chosen pair's angle is recomputed in FP64.
+ *   qa [na, 4], qb [nb, 4] float64 unit quaternions (device); angle_deg [na]
+ *   float64 and index [na] int32 out (-1 and -1 when there is no candidate). */
+int xcf_nearest_disorientation(xcf_ctx *ctx, const double *qa, int32_t na, const double *qb, int32_t nb,
+                               int32_t mode, double *angle_deg, int32_t *index, void *stream);
+
 /* Several maps in one search (paper, Fig. 1 B-C, for every map of a batch;
  * the maps may have different detectors, pattern centres and libraries --
  * each map's detector is cropped to its 2^n square, e.g. 96 -> 64,

@@ -1263,6 +1263,104 @@ int xcf_rotation_scan(xcf_ctx *ctx, const float *master, int32_t M, const xcf_ge
     return XCF_OK;
 }
 
+// --------------------------------------------------------- SO(3) sampling
+int xcf_nearest_disorientation(xcf_ctx *ctx, const double *qa, int32_t na, const double *qb, int32_t nb,
+                               int32_t mode, double *angle_deg, int32_t *index, void *stream) {
+    if (!ctx) return XCF_ERR_ARG;
+    if (na == 0) return XCF_OK;
+    if (!qb) {
+        qb = qa;
+        nb = na;
+    }
+    if (!qa || !angle_deg || !index || na < 0 || nb < 0 || mode < 0 || mode > 2 || (mode && qb != qa))
+        return fail(ctx, XCF_ERR_ARG, "xcf_nearest_disorientation: bad argument (modes 1, 2 need qb == qa or NULL)");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long *keys;
+    int rc;
+    if ((rc = scratch_t(ctx, S_NN_KEYS, na, &keys))) return rc;
+    XCF_LAUNCH(XCF_STAGE_OTHER, st,
+               launch_nearest_disorientation(qa, na, qb, nb, mode, keys, angle_deg, index, ctx->num_sms, st),
+               "nearest disorientation");
+    return XCF_OK;
+}
+
+int xcf_so3_grid(xcf_ctx *ctx, double step_deg, int32_t flags, double *quats, int64_t cap, int64_t *count,
+                 void *stream) {
+    if (!ctx) return XCF_ERR_ARG;
+    if (!count || !(step_deg >= 0.5 && step_deg <= 180.0) || (flags & ~XCF_SO3_DEDUP) || cap < 0)
+        return fail(ctx, XCF_ERR_ARG, "xcf_so3_grid: bad argument (0.5 <= step_deg <= 180)");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    // ring sizes: integer bookkeeping of the scheme (sizes of the launches below)
+    const double d = step_deg * kPi / 180.0;
+    const long n_polar = std::max(1L, lround(kPi / d)), n_s1 = std::max(1L, lround(2 * kPi / d));
+    const int n_rings = (int)n_polar + 1;
+    std::vector<long long> start(n_rings);
+    std::vector<int> az(n_rings);
+    long long G = 0;
+    for (int i = 0; i < n_rings; ++i) {
+        az[i] = (int)std::max(1L, lround(2 * kPi * sin(kPi * i / n_polar) / d));
+        start[i] = G;
+        G += (long long)az[i] * n_s1;
+    }
+    long long *ring_start, *total;
+    int *ring_az, *flag, *bc;
+    double *q_all, *q_fz;
+    int rc;
+    const int nb = compact_blocks(G);
+    if ((rc = scratch(ctx, S_SO3_RING, (sizeof(long long) + sizeof(int)) * n_rings, (void **)&ring_start)) ||
+        (rc = scratch_t(ctx, S_SO3_QALL, 4 * (size_t)G, &q_all)) || (rc = scratch_t(ctx, S_SO3_FLAG, (size_t)G, &flag)) ||
+        (rc = scratch(ctx, S_SO3_CNT, sizeof(long long) + sizeof(int) * (size_t)nb, (void **)&total)))
+        return rc;
+    ring_az = reinterpret_cast<int *>(ring_start + n_rings);
+    bc = reinterpret_cast<int *>(total + 1);
+    XCF_CHECK(cudaMemcpyAsync(ring_start, start.data(), sizeof(long long) * n_rings, cudaMemcpyHostToDevice, st),
+              "ring starts");
+    XCF_CHECK(cudaMemcpyAsync(ring_az, az.data(), sizeof(int) * n_rings, cudaMemcpyHostToDevice, st), "ring sizes");
+    XCF_LAUNCH(XCF_STAGE_OTHER, st,
+               launch_so3_points(ring_start, n_rings, (int)n_polar, (int)n_s1, ring_az, G, q_all, flag, st),
+               "so3 points");
+    long long n_fz = 0;
+    XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_compact(q_all, flag, G, bc, total, nullptr, st), "so3 count");
+    XCF_CHECK(cudaMemcpyAsync(&n_fz, total, sizeof n_fz, cudaMemcpyDeviceToHost, st), "so3 count");
+    XCF_CHECK(cudaStreamSynchronize(st), "xcf_so3_grid");
+    if (n_fz > INT32_MAX) return fail(ctx, XCF_ERR_SIZE, "xcf_so3_grid: more than 2^31 orientations");
+    if ((rc = scratch_t(ctx, S_SO3_QFZ, 4 * (size_t)n_fz, &q_fz))) return rc;
+    XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_compact(q_all, flag, G, bc, total, q_fz, st), "so3 zone");
+    long long n = n_fz;
+    const double *src = q_fz;
+    if (flags & XCF_SO3_DEDUP) {
+        double *ang;
+        int *idx;
+        unsigned long long *keys;
+        if ((rc = scratch_t(ctx, S_NN_ANG, (size_t)n_fz, &ang)) || (rc = scratch_t(ctx, S_NN_IDX, (size_t)n_fz, &idx)) ||
+            (rc = scratch_t(ctx, S_NN_KEYS, (size_t)n_fz, &keys)))
+            return rc;
+        XCF_LAUNCH(XCF_STAGE_OTHER, st,
+                   launch_nearest_disorientation(q_fz, (int)n_fz, q_fz, (int)n_fz, 2, keys, ang, idx, ctx->num_sms,
+                                                 st),
+                   "so3 copies");
+        XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_keep_flags(ang, n_fz, 1e-3, flag, st), "so3 keep");
+        XCF_LAUNCH(XCF_STAGE_OTHER, st,
+                   launch_compact(q_fz, flag, n_fz, bc, total, quats && cap >= n_fz ? quats : nullptr, st),
+                   "so3 dedup");
+        XCF_CHECK(cudaMemcpyAsync(&n, total, sizeof n, cudaMemcpyDeviceToHost, st), "so3 count");
+        XCF_CHECK(cudaStreamSynchronize(st), "xcf_so3_grid");
+        src = nullptr;   // written by the compaction (when it fitted)
+        if (quats && cap < n_fz && cap >= n) {
+            // the output could not hold the pre-duplicate set: compact again into it
+            XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_compact(q_fz, flag, n_fz, bc, total, quats, st), "so3 dedup");
+        }
+    }
+    *count = n;
+    if (!quats) return XCF_OK;
+    if (cap < n) return fail(ctx, XCF_ERR_SIZE, "xcf_so3_grid: cap smaller than the orientation count");
+    if (src) XCF_CHECK(cudaMemcpyAsync(quats, src, sizeof(double) * 4 * n, cudaMemcpyDeviceToDevice, st), "so3 out");
+    XCF_CHECK(cudaStreamSynchronize(st), "xcf_so3_grid");
+    return XCF_OK;
+}
+
 // ------------------------------------------------------ proposal network
 namespace {
 

@@ -49,6 +49,14 @@ enum Slot {
     S_ARGMAX,       // integer peak positions for the up-sampled peak
     S_BG_TMP,       // NDP background correction: row-blurred crops
     S_BG_OUT,       // NDP background correction: corrected crops
+    S_SO3_RING,     // SO(3) generator: ring starts and azimuth counts
+    S_SO3_QALL,     // SO(3) generator: every grid point [G][4]
+    S_SO3_QFZ,      // SO(3) generator: the points in the fundamental zone
+    S_SO3_FLAG,     // SO(3) generator: keep flags
+    S_SO3_CNT,      // SO(3) generator: compaction block counts + total
+    S_NN_KEYS,      // nearest neighbour: packed best keys
+    S_NN_ANG,       // nearest neighbour: angles (generator's duplicate pass)
+    S_NN_IDX,       // nearest neighbour: indices (generator's duplicate pass)
     S_COUNT
 };
 

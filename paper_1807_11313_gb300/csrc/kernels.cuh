@@ -144,6 +144,23 @@ cudaError_t launch_fwhm(const float *a, const float *b, int nc, int L, float ste
 cudaError_t launch_scan_setup(const double *q, const double *pc_test, double pcx, double pcy, double pcz, int h,
                               double step_rad, double alpha, double *qs, double *pcs, cudaStream_t st);
 
+// SO(3) library generator: grid point g of ring i (ring_start [n_rings], ring_az
+// [n_rings] azimuths) -> q_all [G][4] and its cubic-zone flag [G]
+cudaError_t launch_so3_points(const long long *ring_start, int n_rings, int n_polar, int n_s1, const int *ring_az,
+                              long long G, double *q_all, int *flag, cudaStream_t st);
+// order-preserving compaction of the flagged rows of q_in [G][4] -> q_out (nullable:
+// count only); block_counts [compact_blocks(G)], *total (device) = the count
+int compact_blocks(long long G);
+cudaError_t launch_compact(const double *q_in, const int *flag, long long G, int *block_counts, long long *total,
+                           double *q_out, cudaStream_t st);
+// flag[i] = 0 where 0 <= angle[i] < thr, else 1
+cudaError_t launch_keep_flags(const double *angle, long long n, double thr, int *flag, cudaStream_t st);
+// nearest qb of each qa under the cubic disorientation (mode 0 all, 1 j != i,
+// 2 j < i): angle [na] degrees (-1 none), index [na]; keys [na] work array
+cudaError_t launch_nearest_disorientation(const double *qa, int na, const double *qb, int nb, int mode,
+                                          unsigned long long *keys, double *angle, int *index, int num_sms,
+                                          cudaStream_t st);
+
 // ------------------------------------------------ learned proposal network
 // input images: the 128 x 128 crop at (ox, oy) of image b = x + b * img_stride
 struct CnnInput {

@@ -86,6 +86,8 @@ _SIGS = {
     "xcf_index_precision": ([_P, _P, _P, _I32, _P, _I32, _P, _P, _P, _P, _P], C.c_int),
     "xcf_index_ndp": ([_P, _P, _P, _I32, _I32, _P, _P, _P, _P, _P], C.c_int),
     "xcf_rotation_scan": ([_P, _P, _I32, _P, _P, _P, _I32, C.c_double, _P, _P, _P, _P], C.c_int),
+    "xcf_so3_grid": ([_P, C.c_double, _I32, _P, C.c_int64, _P, _P], C.c_int),
+    "xcf_nearest_disorientation": ([_P, _P, _I32, _P, _I32, _I32, _P, _P, _P], C.c_int),
     "xcf_index_noalloc": ([_P, _P, _P, _I32, _P, _P, _P, _P], C.c_int),
     "xcf_noalloc_max_patterns": ([_I32], C.c_int),
     "xcf_index_maps": ([_P, _P, _I32, _I32, _P], C.c_int),
@@ -457,6 +459,36 @@ def xcf_rotation_scan(ctx: Context, master, geom: xcf_geometry, q, h: int, step_
                                     _ptr(ndp, torch.float32, "ndp"), _ptr(xc, torch.float32, "xcf"),
                                     _ptr(fw, torch.float32, "fwhm"), _stream()), ctx.handle)
     return ndp, xc, fw
+
+
+XCF_SO3_DEDUP = 1
+
+
+def xcf_so3_grid(ctx: Context, step_deg: float, dedup: bool = True, device=None):
+    """S^2 x S^1 library orientations in the cubic fundamental zone -> [T, 4] float64 (device)."""
+    d = torch.device("cuda", ctx.device) if device is None else device
+    n = C.c_int64()
+    flags = XCF_SO3_DEDUP if dedup else 0
+    _check(load().xcf_so3_grid(ctx.handle, float(step_deg), flags, None, 0, C.byref(n), _stream()), ctx.handle)
+    q = torch.empty((n.value, 4), dtype=torch.float64, device=d)
+    _check(load().xcf_so3_grid(ctx.handle, float(step_deg), flags, _ptr(q, torch.float64, "quats"), n.value,
+                               C.byref(n), _stream()), ctx.handle)
+    return q
+
+
+def xcf_nearest_disorientation(ctx: Context, qa, qb=None, mode: int | None = None):
+    """Nearest qb of each qa under the cubic disorientation -> (angle_deg [na] float64, index [na] int32).
+    qb None: qa against itself without self (mode 1); mode 2: earlier entries only."""
+    na = qa.shape[0]
+    if mode is None:
+        mode = 1 if qb is None else 0
+    ang = torch.empty(na, dtype=torch.float64, device=qa.device)
+    idx = torch.empty(na, dtype=torch.int32, device=qa.device)
+    _check(load().xcf_nearest_disorientation(ctx.handle, _ptr(qa, torch.float64, "qa"), na,
+                                             _ptr(qb, torch.float64, "qb", True), qb.shape[0] if qb is not None else 0,
+                                             int(mode), _ptr(ang, torch.float64, "angle"),
+                                             _ptr(idx, torch.int32, "index"), _stream()), ctx.handle)
+    return ang, idx
 
 
 def xcf_refine_best(ctx: Context, lib: Library, patterns, best, pcs=None, out=None):
