@@ -41,15 +41,16 @@ class Opts(C.Structure):
     _fields_ = [("window", C.c_int32), ("sigma_hp", C.c_double), ("sigma_lp", C.c_double),
                 ("lp_nr", C.c_int32), ("lp_neta", C.c_int32), ("lp_rmin", C.c_double),
                 ("lp_rmax", C.c_double), ("upsample", C.c_int32), ("interp", C.c_int32),
-                ("ndp_bg_sigma", C.c_double)]
+                ("ndp_bg_sigma", C.c_double), ("lp_windows", C.c_int32)]
 
 
 def default_opts(n: int, **kw) -> Opts:
     """Defaults: Hann window, sigma_hp = 2, sigma_lp = n/4 cycles per image,
-    log-polar n/4 radii x 2n angles over r in [n/4, n/2 - 1] px, NDP
-    background sigma n/8 px (0 selects it; < 0 turns the correction off)."""
+    log-polar n/4 radii x 2n angles over r in [n/4, n/2 - 1] px in 4 radial
+    windows, NDP background sigma n/8 px (0 selects it; < 0 turns the
+    correction off)."""
     d = dict(window=1, sigma_hp=2.0, sigma_lp=n / 4.0, lp_nr=max(n // 4, 2), lp_neta=2 * n,
-             lp_rmin=n / 4.0, lp_rmax=n / 2.0 - 1.0, upsample=0, interp=0, ndp_bg_sigma=0.0)
+             lp_rmin=n / 4.0, lp_rmax=n / 2.0 - 1.0, upsample=0, interp=0, ndp_bg_sigma=0.0, lp_windows=4)
     d.update(kw)
     return Opts(**d)
 
@@ -112,6 +113,7 @@ def _lib_handle():
                 "orc_rotation_scan": ([_F, C.c_int, C.c_int, _D, _D, C.c_double, C.c_double, C.POINTER(Opts),
                                        _D, C.c_int, C.c_double, _D, _D], None),
                 "orc_fwhm": ([_D, C.c_int, C.c_double], C.c_double),
+                "orc_eta_windows": ([_D, _D, C.c_int, C.c_int, C.c_int, _D], C.c_double),
                 "orc_so3_grid": ([C.c_double, C.c_int, _D, C.c_long], C.c_long),
                 "orc_nearest_disorientation": ([_D, C.c_int, _D, C.c_int, C.c_int, _D, _I], None),
                 "orc_cnn_num_params": ([C.c_int], C.c_long),
@@ -496,6 +498,15 @@ def eta_xcf(a, b):
     c = np.empty(ne)
     sh = _lib_handle().orc_eta_xcf(_d(a), _d(b), nr, ne, C.byref(pk), _d(c))
     return sh, pk.value, c
+
+
+def eta_windows(a, b, windows):
+    """Multiple-window Z measurement -> (median band shift, largest band peak)"""
+    a, b = _f64(a), _f64(b)
+    nr, ne = a.shape
+    pk = C.c_double()
+    sh = _lib_handle().orc_eta_windows(_d(a), _d(b), nr, ne, int(windows), C.byref(pk))
+    return sh, pk.value
 
 
 def refine_one(master, pattern, seed, pc, max_it=2, tol_deg=1e-3, opts=None,

@@ -42,6 +42,7 @@ typedef struct {
     int32_t upsample;    /* 0: 3-point parabola; U >= 2: up-sampled peak       */
     int32_t interp;      /* master lookup: 0 bilinear, 1 bicubic (Keys)        */
     double ndp_bg_sigma; /* NDP background: Gaussian sigma, px; 0 = n/8, < 0 off */
+    int32_t lp_windows;  /* log-polar radial windows of the Z step (<= 1: one)  */
 } orc_opts;
 
 typedef struct {
@@ -718,6 +719,33 @@ double orc_eta_xcf(const double *a_in, const double *b_in, int nr, int neta, dou
     return sh;
 }
 
+/* The Z measurement with multiple windows (the refinement section correlates
+ * "multiple windows" of the log-polar images and keeps only the shift along
+ * eta; reading: W radial bands, band w holding radii [w nr / W, (w+1) nr / W)
+ * (integer division), each correlated along eta on its own as orc_eta_xcf
+ * does for the whole image, the shift the median of the W band shifts (the
+ * mean of the middle two for even W)).  W <= 1 is orc_eta_xcf.  *peak gets
+ * the largest band peak. */
+double orc_eta_windows(const double *a, const double *b, int nr, int neta, int W, double *peak) {
+    if (W <= 1) return orc_eta_xcf(a, b, nr, neta, peak, NULL);
+    if (W > nr) W = nr;
+    double *sh = malloc(sizeof(double) * W), best = -2.0;
+    for (int w = 0; w < W; ++w) {
+        int m0 = w * nr / W, m1 = (w + 1) * nr / W;
+        double pk;
+        sh[w] = orc_eta_xcf(a + (long)m0 * neta, b + (long)m0 * neta, m1 - m0, neta, &pk, NULL);
+        if (pk > best) best = pk;
+    }
+    for (int i = 1; i < W; ++i)   /* insertion sort */
+        for (int j = i; j > 0 && sh[j] < sh[j - 1]; --j) {
+            double t = sh[j]; sh[j] = sh[j - 1]; sh[j - 1] = t;
+        }
+    double med = W % 2 ? sh[W / 2] : 0.5 * (sh[W / 2 - 1] + sh[W / 2]);
+    free(sh);
+    *peak = best;
+    return med;
+}
+
 /* q_new = q (x) q_s (x) conj(qQ) (x) conj(q_s): the orientation whose template
  * equals the template of q rotated by the detector-frame rotation Q (q_s is
  * the detector -> sample rotation about x). */
@@ -790,7 +818,7 @@ int orc_refine_one(const float *master, int M, const double pc[3], double sample
         orc_prep(img, n, o, ST, yT);
         orc_logpolar(yT, n, nr, ne, o->lp_rmin, o->lp_rmax, lpT);
         double zpk;
-        double deta = orc_eta_xcf(lpT, lpP, nr, ne, &zpk, NULL);
+        double deta = orc_eta_windows(lpT, lpP, nr, ne, o->lp_windows, &zpk);
         double tz = 2.0 * ORC_PI * deta / ne;
         double qz[4] = {cos(tz / 2), 0, 0, sin(tz / 2)};
         double q2[4];
@@ -1094,7 +1122,8 @@ static int in_cubic_fz(const double q[4]) {
  * S^1 angle); kept where it falls in the cubic fundamental zone, in
  * generation order (ring, azimuth, S^1).  Reading: points on the zone's faces
  * are kept, and with dedup != 0 a point whose disorientation to an earlier
- * kept point is below 1e-3 deg (a symmetry copy across a face) is dropped.
+ * in-zone grid point is below 1e-3 deg (a symmetry copy across a face) is
+ * dropped.
  * Rounding: halves away from zero.  Writes at most cap orientations [cap][4]
  * (out may be NULL) and returns the count. */
 long orc_so3_grid(double step_deg, int dedup, double *out, long cap) {
@@ -1102,8 +1131,8 @@ long orc_so3_grid(double step_deg, int dedup, double *out, long cap) {
     long np_ = lround(ORC_PI / d), ns = lround(2 * ORC_PI / d);
     if (np_ < 1) np_ = 1;
     if (ns < 1) ns = 1;
-    long n = 0, kept_cap = 1024;
-    double *kept = malloc(sizeof(double) * 4 * kept_cap);
+    long n = 0, nc = 0, cand_cap = 1024;
+    double *cand = malloc(sizeof(double) * 4 * cand_cap);   /* every in-zone point so far */
     for (long i = 0; i <= np_; ++i) {
         double Phi = ORC_PI * i / np_;
         long na = lround(2 * ORC_PI * sin(Phi) / d);
@@ -1115,20 +1144,20 @@ long orc_so3_grid(double step_deg, int dedup, double *out, long cap) {
                 bunge_to_quat(p1, Phi, 2 * ORC_PI * k / ns, q);
                 if (!in_cubic_fz(q)) continue;
                 int dup = 0;
-                for (long m = 0; dedup && m < n && !dup; ++m)
-                    dup = orc_disorientation(q, kept + 4 * m) < 1e-3;
-                if (dup) continue;
-                if (n == kept_cap) {
-                    kept_cap *= 2;
-                    kept = realloc(kept, sizeof(double) * 4 * kept_cap);
+                for (long m = 0; dedup && m < nc && !dup; ++m)
+                    dup = orc_disorientation(q, cand + 4 * m) < 1e-3;
+                if (nc == cand_cap) {
+                    cand_cap *= 2;
+                    cand = realloc(cand, sizeof(double) * 4 * cand_cap);
                 }
-                memcpy(kept + 4 * n, q, sizeof q);
+                memcpy(cand + 4 * nc++, q, sizeof q);
+                if (dup) continue;
                 if (out && n < cap) memcpy(out + 4 * n, q, sizeof q);
                 ++n;
             }
         }
     }
-    free(kept);
+    free(cand);
     return n;
 }
 

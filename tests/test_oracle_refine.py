@@ -23,6 +23,30 @@ def test_eta_xcf_recovers_roll(orc):
         assert pk == pytest.approx(1.0) and sh == pytest.approx(D if D >= -32 else D + 64)
 
 
+def test_eta_windows_median_of_band_shifts(orc):
+    """Multiple windows: radial bands correlated on their own, the median
+    band shift (mean of the middle two for an even count)."""
+    rng = np.random.default_rng(1)
+    a = rng.standard_normal((16, 64))
+    # one window is the whole-image correlation
+    b = np.roll(a, 7, axis=1)
+    assert orc.eta_windows(a, b, 1)[0] == pytest.approx(orc.eta_xcf(a, b)[0])
+    # a common roll is recovered by every band
+    for W in (2, 3, 4, 16):
+        assert orc.eta_windows(a, b, W)[0] == pytest.approx(7.0)
+    # one corrupted band of three is outvoted
+    c = b.copy()
+    c[5:10] = rng.standard_normal((5, 64))
+    assert orc.eta_windows(a, c, 3)[0] == pytest.approx(7.0)
+    # bands rolled by 2, 4, 6, 8 (four radii each): median (4 + 6) / 2
+    d = np.concatenate([np.roll(a[4 * k:4 * k + 4], 2 * (k + 1), axis=1) for k in range(4)])
+    assert orc.eta_windows(a, d, 4)[0] == pytest.approx(5.0)
+    # three bands of 16 // 3 = 5, 5, 6 radii: rolls 1, 9, 3 -> median 3
+    bounds = [(0, 5), (5, 10), (10, 16)]
+    e = np.concatenate([np.roll(a[m0:m1], r, axis=1) for (m0, m1), r in zip(bounds, (1, 9, 3))])
+    assert orc.eta_windows(a, e, 3)[0] == pytest.approx(3.0)
+
+
 def test_logpolar_turns_rotation_into_eta_shift(orc):
     """Rotating an image counter-clockwise (y up) about the screen centre
     shifts its log-polar transform along eta by theta neta / 2 pi."""
