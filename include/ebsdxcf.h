@@ -72,6 +72,11 @@ typedef struct {
                             Gaussian blur of this sigma in px (truncated at
                             round(3 sigma), edges repeated); 0 = N/8 (default),
                             < 0 = no correction                                     */
+    int32_t lp_windows;  /* Z step: the log-polar radii split into this many radial
+                            windows (at most 16 and lp_nr), each correlated along eta
+                            on its own, the rotation the median window shift (the
+                            paper's "multiple windows"); 0 = 4 (default), 1 = the
+                            whole image as one window                               */
 } xcf_options;
 
 /* Detector geometry of a map (or of a library). */

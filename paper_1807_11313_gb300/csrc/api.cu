@@ -128,6 +128,7 @@ struct Resolved {
     double sigma_hp, sigma_lp;
     int nr, neta;
     double rmin, rmax;
+    int windows;   // radial log-polar windows of the Z step
 };
 
 Resolved resolve(const xcf_options &o, int n) {
@@ -139,6 +140,8 @@ Resolved resolve(const xcf_options &o, int n) {
     r.neta = o.lp_neta > 0 ? o.lp_neta : 2 * n;
     r.rmin = o.lp_rmin > 0 ? o.lp_rmin : n / 4.0;
     r.rmax = o.lp_rmax > 0 ? o.lp_rmax : n / 2.0 - 1.0;
+    r.windows = o.lp_windows > 0 ? o.lp_windows : 4;
+    if (r.windows > r.nr) r.windows = r.nr;
     return r;
 }
 
@@ -354,7 +357,7 @@ int refine_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, in
                    launch_logpolar(yt, active, P, n, r.nr, r.neta, (float)r.rmin, (float)r.rmax, lpt, st),
                    "logpolar templates");
         XCF_LAUNCH(XCF_STAGE_UPDATE, st,
-                   launch_eta_update(lpt, lpp, r.nr, r.neta, quats, q1, alpha, ctx->opt.tol_deg, active, iters,
+                   launch_eta_update(lpt, lpp, r.nr, r.neta, r.windows, quats, q1, alpha, ctx->opt.tol_deg, active, iters,
                                      quats, P, st),
                    "z update");
     }
@@ -394,6 +397,7 @@ int xcf_options_default(xcf_options *o) {
     o->upsample = 0;
     o->master_interp = 0;
     o->ndp_bg_sigma = 0.0;
+    o->lp_windows = 0;
     return XCF_OK;
 }
 
@@ -418,6 +422,7 @@ int xcf_create(xcf_ctx **out, const xcf_options *opt, int device) {
         if (o.upsample != 0 && (o.upsample < 2 || o.upsample > 20)) return XCF_ERR_ARG;
         if (o.master_interp < 0 || o.master_interp > 1) return XCF_ERR_ARG;
         if (!(o.ndp_bg_sigma == o.ndp_bg_sigma)) return XCF_ERR_ARG;   // NaN
+        if (o.lp_windows < 0 || o.lp_windows > 16) return XCF_ERR_ARG;
     } else {
         xcf_options_default(&o);
     }

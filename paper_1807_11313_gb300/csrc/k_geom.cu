@@ -208,11 +208,11 @@ __device__ __forceinline__ float parabola(float cm, float c0, float cp) {
 // C[k] = sum_m conj(A_m[k]) B_m[k] (k <= neta/2) in registers; the warps'
 // sums are added in float64 and one inverse transform of the Hermitian C
 // gives c(D) for every shift.  neta log neta work per radius instead of neta^2.
-constexpr int kEtaThreads = 256, kEtaWarps = kEtaThreads / 32;
+constexpr int kEtaThreads = 256, kEtaWarps = kEtaThreads / 32, kMaxLpWindows = 16;
 
 template <int NETA>
 __global__ void __launch_bounds__(kEtaThreads) k_eta_update(const float *__restrict__ lpT,
-                                                            const float *__restrict__ lpP, int nr,
+                                                            const float *__restrict__ lpP, int nr, int windows,
                                                             const double *__restrict__ q0s,
                                                             const double *__restrict__ q1s,
                                                             double alpha, double tol_deg,
@@ -223,74 +223,83 @@ __global__ void __launch_bounds__(kEtaThreads) k_eta_update(const float *__restr
     const int p = blockIdx.x;
     if (!active[p]) return;
     __shared__ float2 line[kEtaWarps][NETA];   // per-warp lines, then per-warp sums C (k < H)
-    __shared__ float2 tw[NETA / 2];
+    __shared__ float2 tw[NETA / 2], twi[NETA / 2];
     __shared__ float2 zc[NETA];
     __shared__ float cfin[NETA];
     __shared__ double red[33];
-    const int tot = nr * NETA, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const float *ga = lpT + (size_t)p * tot, *gb = lpP + (size_t)p * tot;
+    __shared__ double wshift[kMaxLpWindows];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const float *ga = lpT + (size_t)p * nr * NETA, *gb = lpP + (size_t)p * nr * NETA;
     bigk::make_tw<NETA>(tw, -1);
-    double s1 = 0, s2 = 0;
-    for (int i = tid; i < tot; i += kEtaThreads) { s1 += ga[i]; s2 += gb[i]; }
-    const float ma = (float)(block_sum_d(s1, red) / tot);
-    const float mb = (float)(block_sum_d(s2, red) / tot);
-    double n1 = 0, n2 = 0;
-    for (int i = tid; i < tot; i += kEtaThreads) {
-        const float x = ga[i] - ma, y = gb[i] - mb;
-        n1 += (double)x * x; n2 += (double)y * y;
-    }
-    const double na = block_sum_d(n1, red), nb = block_sum_d(n2, red);
-    double nrm = sqrt(na * nb);
-    if (!(nrm > 0)) nrm = 1.0;
-    float2 acc[KPL];
-#pragma unroll
-    for (int j = 0; j < KPL; ++j) acc[j] = make_float2(0.f, 0.f);
+    bigk::make_tw<NETA>(twi, +1);
     float2 *z = line[w];
-    for (int m = w; m < nr; m += kEtaWarps) {
-        for (int l = lane; l < NETA; l += 32)
-            z[l] = make_float2(ga[(size_t)m * NETA + l] - ma, gb[(size_t)m * NETA + l] - mb);
-        __syncwarp();
-        bigk::warp_fft_line<NETA>(z, 1, tw);   // forward: Z[k] = sum_l z[l] e^{-2 pi i k l / NETA}
+    // radial window b holds radii [b nr / W, (b + 1) nr / W); each is correlated along eta on its own
+    for (int b = 0; b < windows; ++b) {
+        const int m0 = b * nr / windows, m1 = (b + 1) * nr / windows;
+        const int i0 = m0 * NETA, i1 = m1 * NETA;
+        double s1 = 0, s2 = 0;
+        for (int i = i0 + tid; i < i1; i += kEtaThreads) { s1 += ga[i]; s2 += gb[i]; }
+        const float ma = (float)(block_sum_d(s1, red) / (i1 - i0));
+        const float mb = (float)(block_sum_d(s2, red) / (i1 - i0));
+        float2 acc[KPL];
+#pragma unroll
+        for (int j = 0; j < KPL; ++j) acc[j] = make_float2(0.f, 0.f);
+        for (int m = m0 + w; m < m1; m += kEtaWarps) {
+            for (int l = lane; l < NETA; l += 32)
+                z[l] = make_float2(ga[(size_t)m * NETA + l] - ma, gb[(size_t)m * NETA + l] - mb);
+            __syncwarp();
+            bigk::warp_fft_line<NETA>(z, 1, tw);   // forward: Z[k] = sum_l z[l] e^{-2 pi i k l / NETA}
+#pragma unroll
+            for (int j = 0; j < KPL; ++j) {
+                const int k = lane + 32 * j;
+                if (k < H) {
+                    const float2 zk = z[k], zn = z[(NETA - k) & (NETA - 1)];
+                    // A = (Z[k] + conj Z[-k]) / 2, B = (Z[k] - conj Z[-k]) / (2i); acc += conj(A) B
+                    const float2 A = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+                    const float2 B = make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x));
+                    acc[j].x += A.x * B.x + A.y * B.y;
+                    acc[j].y += A.x * B.y - A.y * B.x;
+                }
+            }
+            __syncwarp();
+        }
 #pragma unroll
         for (int j = 0; j < KPL; ++j) {
             const int k = lane + 32 * j;
-            if (k < H) {
-                const float2 zk = z[k], zn = z[(NETA - k) & (NETA - 1)];
-                // A = (Z[k] + conj Z[-k]) / 2, B = (Z[k] - conj Z[-k]) / (2i); acc += conj(A) B
-                const float2 A = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
-                const float2 B = make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x));
-                acc[j].x += A.x * B.x + A.y * B.y;
-                acc[j].y += A.x * B.y - A.y * B.x;
+            if (k < H) z[k] = acc[j];
+        }
+        __syncthreads();
+        // C[k] over the warps in float64, extended by C[NETA - k] = conj C[k]; inverse transform by warp 0.
+        // The correlation's scale does not move its argmax or parabolic offset, so it is not normalised.
+        if (w == 0) {
+            for (int k = lane; k < H; k += 32) {
+                double cr = 0, ci = 0;
+                for (int v = 0; v < kEtaWarps; ++v) { cr += line[v][k].x; ci += line[v][k].y; }
+                zc[k] = make_float2((float)cr, (float)ci);
+                if (k > 0 && k < NETA / 2) zc[NETA - k] = make_float2((float)cr, (float)-ci);
             }
+            __syncwarp();
+            bigk::warp_fft_line<NETA>(zc, 1, twi);
+            for (int d = lane; d < NETA; d += 32) cfin[d] = zc[d].x;
         }
-        __syncwarp();
-    }
-#pragma unroll
-    for (int j = 0; j < KPL; ++j) {
-        const int k = lane + 32 * j;
-        if (k < H) z[k] = acc[j];
-    }
-    __syncthreads();
-    // C[k] over the warps in float64, extended by C[NETA - k] = conj C[k]; inverse transform by warp 0
-    if (w == 0) {
-        for (int k = lane; k < H; k += 32) {
-            double cr = 0, ci = 0;
-            for (int v = 0; v < kEtaWarps; ++v) { cr += line[v][k].x; ci += line[v][k].y; }
-            zc[k] = make_float2((float)cr, (float)ci);
-            if (k > 0 && k < NETA / 2) zc[NETA - k] = make_float2((float)cr, (float)-ci);
+        __syncthreads();
+        if (tid == 0) {
+            int best = 0;
+            for (int D = 1; D < NETA; ++D) if (cfin[D] > cfin[best]) best = D;
+            const float off = parabola(cfin[(best + NETA - 1) % NETA], cfin[best], cfin[(best + 1) % NETA]);
+            wshift[b] = (double)(best < NETA / 2 ? best : best - NETA) + off;
         }
-        __syncwarp();
-        for (int k = lane; k < NETA / 2; k += 32) tw[k].y = -tw[k].y;   // inverse twiddles
-        __syncwarp();
-        bigk::warp_fft_line<NETA>(zc, 1, tw);
-        for (int d = lane; d < NETA; d += 32) cfin[d] = (float)((double)zc[d].x / (NETA * nrm));
+        __syncthreads();   // line, zc and cfin are reused by the next window
     }
-    __syncthreads();
     if (tid == 0) {
-        int best = 0;
-        for (int D = 1; D < NETA; ++D) if (cfin[D] > cfin[best]) best = D;
-        const float off = parabola(cfin[(best + NETA - 1) % NETA], cfin[best], cfin[(best + 1) % NETA]);
-        const double deta = (double)(best < NETA / 2 ? best : best - NETA) + off;
+        // median of the window shifts (mean of the middle two for an even count)
+        for (int i = 1; i < windows; ++i)
+            for (int j = i; j > 0 && wshift[j] < wshift[j - 1]; --j) {
+                const double t = wshift[j];
+                wshift[j] = wshift[j - 1];
+                wshift[j - 1] = t;
+            }
+        const double deta = windows % 2 ? wshift[windows / 2] : 0.5 * (wshift[windows / 2 - 1] + wshift[windows / 2]);
         const double tz = 2.0 * XCF_PI * deta / NETA;
         double s, c;
         sincos(0.5 * tz, &s, &c);
@@ -435,13 +444,15 @@ cudaError_t launch_update_xy(const double *q, const float *shift, const double *
     return cudaGetLastError();
 }
 
-cudaError_t launch_eta_update(const float *lpT, const float *lpP, int nr, int neta, const double *q0,
-                              const double *q1, double alpha, double tol_deg, int *active,
+cudaError_t launch_eta_update(const float *lpT, const float *lpP, int nr, int neta, int windows,
+                              const double *q0, const double *q1, double alpha, double tol_deg, int *active,
                               int *iters, double *q_out, int P, cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
-#define XCF_ETA_CASE(NE)                                                                                     \
-    case NE:                                                                                                 \
-        k_eta_update<NE><<<P, kEtaThreads, 0, st>>>(lpT, lpP, nr, q0, q1, alpha, tol_deg, active, iters, q_out); \
+    if (windows < 1 || windows > kMaxLpWindows || windows > nr) return cudaErrorInvalidValue;
+#define XCF_ETA_CASE(NE)                                                                                    \
+    case NE:                                                                                                \
+        k_eta_update<NE><<<P, kEtaThreads, 0, st>>>(lpT, lpP, nr, windows, q0, q1, alpha, tol_deg, active,   \
+                                                    iters, q_out);                                          \
         break;
     switch (neta) {
         XCF_ETA_CASE(32)

@@ -111,8 +111,10 @@ cudaError_t launch_logpolar(const float *spatial, const int *active, int P, int 
 cudaError_t launch_update_xy(const double *q, const float *shift, const double *pcs, double pcz_def,
                              int W, double alpha, const int *active, int P, double *q1,
                              cudaStream_t st);
-cudaError_t launch_eta_update(const float *lpT, const float *lpP, int nr, int neta, const double *q0,
-                              const double *q1, double alpha, double tol_deg, int *active,
+// windows: radial bands of the log-polar images (1 .. min(16, nr)), each
+// correlated along eta on its own; the update takes the median band shift
+cudaError_t launch_eta_update(const float *lpT, const float *lpP, int nr, int neta, int windows,
+                              const double *q0, const double *q1, double alpha, double tol_deg, int *active,
                               int *iters, double *q_out, int P, cudaStream_t st);
 
 cudaError_t launch_gather_seeds(const double *lib_quats, const int *best, int P, double *seeds,

@@ -34,7 +34,8 @@ class xcf_options(C.Structure):
     _fields_ = [("window", C.c_int32), ("sigma_hp", C.c_double), ("sigma_lp", C.c_double),
                 ("lp_nr", C.c_int32), ("lp_neta", C.c_int32), ("lp_rmin", C.c_double),
                 ("lp_rmax", C.c_double), ("max_iter", C.c_int32), ("tol_deg", C.c_double),
-                ("upsample", C.c_int32), ("master_interp", C.c_int32), ("ndp_bg_sigma", C.c_double)]
+                ("upsample", C.c_int32), ("master_interp", C.c_int32), ("ndp_bg_sigma", C.c_double),
+                ("lp_windows", C.c_int32)]
 
 
 class xcf_geometry(C.Structure):

@@ -223,18 +223,21 @@ def test_config1_parity(px, ctx, orc):
 
 
 # ------------------------------------------------------------ refinement
-@pytest.mark.parametrize("noise,n,P", [(None, 128, 8), (150.0, 128, 8), (150.0, 256, 4)])
-def test_refine_matches_oracle(px, orc, noise, n, P):
+@pytest.mark.parametrize("noise,n,P,windows", [(None, 128, 8, 0), (150.0, 128, 8, 0), (150.0, 256, 4, 0),
+                                               (150.0, 128, 8, 1), (150.0, 64, 8, 3), (150.0, 32, 6, 8)])
+def test_refine_matches_oracle(px, orc, noise, n, P, windows):
     master = synth.master_pattern("bcc", 1024)
     seeds = synth.random_quaternions(P, 90)
     truth = synth.perturb(seeds, 4.0, 91)
     pcs = synth.jittered_pcs(P, 92)
     clean = np.stack([orc.project(master, truth[i], pcs[i], n) for i in range(P)])
     pats = clean.astype(np.float32) if noise is None else synth.add_noise(clean, pcs, noise, 93)
-    c = px.Context(max_iter=4, tol_deg=0.0)
+    c = px.Context(max_iter=4, tol_deg=0.0, lp_windows=windows)
     lib = px.xcf_build_library(c, dev(master), dev(seeds[:2]), px.geometry(n, n, PC0))
     q, pk, it = (host(t) for t in px.xcf_refine(c, lib, dev(pats), dev(seeds), pcs=dev(pcs)))
-    oq, opk, oit = orc.refine_many(master, pats, seeds, pcs, max_it=4, tol_deg=0.0)
+    # log-polar windows: 0 selects four (at most the N/4 radii)
+    oq, opk, oit = orc.refine_many(master, pats, seeds, pcs, max_it=4, tol_deg=0.0,
+                                   opts=orc.default_opts(n, lp_windows=min(windows or 4, n // 4)))
     assert it.tolist() == oit.tolist() == [4] * P
     d = orc.disorientation(q, oq)
     assert d.max() < 0.01, d
