@@ -59,20 +59,21 @@ __device__ void make_twiddles(float2 *tw, int sign) {
     }
 }
 
-__device__ inline double block_sum(double v, double *sh) {
+// sum over the block of one FP32 partial per thread: warp sums in FP32, the
+// warps' sums added in FP64 (keeps the hot loops off the FP64 pipe)
+__device__ inline double block_sum_f(float v, double *sh) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[w] = v;
+    if (lane == 0) sh[w] = (double)v;
     __syncthreads();
-    if (w == 0) {
-        v = lane < nw ? sh[lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[32] = v;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < nw; ++i) s += sh[i];
+        sh[32] = s;
     }
     __syncthreads();
-    double r = sh[32];
+    const double r = sh[32];
     __syncthreads();
     return r;
 }

@@ -487,6 +487,16 @@ __device__ __forceinline__ double block_sum_d(double v, double *sh) {
     __syncthreads();
     return s;
 }
+// FP32 partial per thread: warp sums in FP32, the warps' sums in FP64
+__device__ __forceinline__ double block_sum_fd(float v, double *sh) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += sh[w];
+    __syncthreads();
+    return s;
+}
 // sum of one partial per CTA, identical (same order) in every CTA of the cluster
 __device__ __forceinline__ double cluster_sum(double part, double *slot, uint32_t slot_addr) {
     if (threadIdx.x == 0) *slot = part;
@@ -535,25 +545,28 @@ k_prep_c256(const float *__restrict__ img, int P, PrepArgs a, float2 *__restrict
         if (active && !active[p]) continue;            // uniform over the cluster
         const float *src = img + (size_t)p * a.W * a.H;
         float2 *out = spec + (size_t)p * N * HW;
-        // ---- statistics of the crop: one pass, sum and sum of squares in float64
-        // (pixel values are counts: the cancellation in E[x^2] - E[x]^2 stays far
-        // below float precision), one cluster barrier for both
-        double s = 0.0, s2 = 0.0;
+        // ---- statistics of the crop: one pass of FP32 sums of (x - x0), x0 the crop's
+        // first pixel (the same in every CTA; a constant crop has exactly zero variance),
+        // combined in FP64, one cluster barrier for both
+        const float x0 = __ldg(src + (size_t)a.oy * a.W + a.ox);
+        float sf = 0.f, sf2 = 0.f;
         for (int i = tid; i < ROWS * N; i += NT) {
             const int r = i >> 8, x = i & (N - 1);
             const float v = __ldg(src + (size_t)(a.oy + ROWS * c + r) * a.W + a.ox + x);
             Xr[i] = v;
-            s += v;
-            s2 += (double)v * v;
+            const float d = v - x0;
+            sf += d;
+            sf2 = fmaf(d, d, sf2);
         }
-        s = block_sum_d(s, red);
-        s2 = block_sum_d(s2, red);
+        const double s = block_sum_fd(sf, red);
+        const double s2 = block_sum_fd(sf2, red);
         if (tid == 0) red[9] = s2;
         const double tot = cluster_sum(s, red + 8, slot_local);   // its barrier also publishes red[9]
         double tot2 = 0.0;
         for (int r = 0; r < NC; ++r) tot2 += ld_cluster_d(map_to_rank(slot_local + sizeof(double), r));
-        const double mean = tot / ((double)N * N);
-        const double sd = sqrt(fmax(tot2 / ((double)N * N) - mean * mean, 0.0));
+        const double m1 = tot / ((double)N * N);
+        const double mean = x0 + m1;
+        const double sd = sqrt(fmax(tot2 / ((double)N * N) - m1 * m1, 0.0));
         bool bad = !(sd > 1e-12 * (1.0 + fabs(mean)));
         if (!bad) {
             // ---- rows (two per complex line), windowed and standardised
@@ -587,7 +600,7 @@ k_prep_c256(const float *__restrict__ img, int P, PrepArgs a, float2 *__restrict
             }
         }
         cluster_barrier();   // R complete (every CTA takes the same branch: mean and sd are cluster-wide)
-        double e = 0.0;
+        float e = 0.f;
         if (!bad) {
             // ---- columns: gather, transform, filter; keep in Stage / Col128
             const int nq = (c == NC - 1 && g == 0) ? 3 : 2;
@@ -599,7 +612,7 @@ k_prep_c256(const float *__restrict__ img, int P, PrepArgs a, float2 *__restrict
                 for (int n1 = 0; n1 < 16; ++n1) z[n1] = ld_cluster(rrow[n1] + (uint32_t)(v * sizeof(float2)));
                 line_fft<-1>(z, tw, scr, t);
                 const float fv = (float)(v < N / 2 ? v : v - N);
-                const double wv = (v == 0 || v == N / 2) ? 1.0 : 2.0;
+                const float wv = (v == 0 || v == N / 2) ? 1.f : 2.f;
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const int u = t + 16 * cx_bitrev(k, 4);
@@ -607,13 +620,13 @@ k_prep_c256(const float *__restrict__ img, int P, PrepArgs a, float2 *__restrict
                     const float rho2 = fu * fu + fv * fv;
                     const float h = -expm1f(-rho2 * a.inv2shp) * expf(-rho2 * a.inv2slp);
                     const float2 X = make_float2(z[k].x * h, z[k].y * h);
-                    e += wv * ((double)X.x * X.x + (double)X.y * X.y);
+                    e = fmaf(wv, X.x * X.x + X.y * X.y, e);
                     if (q < 2) Stage[st_index(u, v - 32 * c)] = X;
                     else Col128[u] = X;
                 }
             }
         }
-        const double energy = cluster_sum(block_sum_d(e, red), red + 10, slot_local + 2 * sizeof(double));
+        const double energy = cluster_sum(block_sum_fd(e, red), red + 10, slot_local + 2 * sizeof(double));
         bad = bad || !(energy > 0.0);
         if (tid == 0 && c == 0 && degen) degen[p] = bad ? 1 : 0;
         if (bad) {

@@ -58,22 +58,22 @@ __global__ void __launch_bounds__(kThreads) k_prep_real(const float *__restrict_
     make_twiddles<N>(twNi, +1);
     make_twiddles<H>(twH, -1);
     make_twiddles<H>(twHi, +1);
-    // ---- load (rows 2pr, 2pr+1 into the real and imaginary parts of buf row pr) and statistics
-    double s = 0.0;
+    // ---- load (rows 2pr, 2pr+1 into the real and imaginary parts of buf row pr) and statistics:
+    // one pass of FP32 sums of (x - x0), x0 the crop's first pixel (a constant crop has exactly
+    // zero variance; the shift keeps the per-thread sums well conditioned), combined in FP64
+    const float x0 = __ldg(src + (size_t)a.oy * a.W + a.ox);
+    float s1 = 0.f, s2 = 0.f;
     for (int idx = tid; idx < N * N; idx += kThreads) {
         const int r = idx / N, c = idx % N;
         const float v = src[(size_t)(a.oy + r) * a.W + a.ox + c];
         reinterpret_cast<float *>(buf + (r >> 1) * LD + c)[r & 1] = v;
-        s += v;
+        const float d = v - x0;
+        s1 += d;
+        s2 = fmaf(d, d, s2);
     }
-    const double mean = block_sum(s, red) / (N * N);
-    double ss = 0.0;
-    for (int idx = tid; idx < H * N; idx += kThreads) {
-        const float2 z = buf[(idx / N) * LD + idx % N];
-        const double d0 = z.x - mean, d1 = z.y - mean;
-        ss += d0 * d0 + d1 * d1;
-    }
-    const double sd = sqrt(block_sum(ss, red) / (N * N));
+    const double m1 = block_sum_f(s1, red) / (N * N), m2 = block_sum_f(s2, red) / (N * N);
+    const double mean = x0 + m1, var = m2 - m1 * m1;
+    const double sd = var > 0.0 ? sqrt(var) : 0.0;
     bool bad = !(sd > 1e-12 * (1.0 + fabs(mean)));
     double energy = 0.0;
     if (!bad) {
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kThreads) k_prep_real(const float *__restrict_
         }
         __syncthreads();
         // band-pass and the filtered energy (bins 1..N/2-1 stand for their mirror images too)
-        double e = 0.0;
+        float e = 0.f;
         for (int it = tid; it < N * HW; it += kThreads) {
             const int u = it / HW, v = it % HW;
             float2 *x = v == 0 ? c0 + u : (v == N / 2 ? cH + u : buf + (u & (H - 1)) * LD + (u >= H ? N / 2 : 0) + v);
@@ -157,9 +157,9 @@ __global__ void __launch_bounds__(kThreads) k_prep_real(const float *__restrict_
             const float h = -expm1f(-rho2 * a.inv2shp) * expf(-rho2 * a.inv2slp);
             const float2 X = make_float2(x->x * h, x->y * h);
             *x = X;
-            e += (v == 0 || v == N / 2 ? 1.0 : 2.0) * ((double)X.x * X.x + (double)X.y * X.y);
+            e = fmaf(v == 0 || v == N / 2 ? 1.f : 2.f, X.x * X.x + X.y * X.y, e);
         }
-        energy = block_sum(e, red);
+        energy = block_sum_f(e, red);
         bad = !(energy > 0.0);
     }
     if (tid == 0 && degen) degen[p] = bad ? 1 : 0;

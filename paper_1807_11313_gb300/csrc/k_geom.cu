@@ -175,20 +175,20 @@ __global__ void __launch_bounds__(256) k_logpolar(const float *__restrict__ spat
     }
 }
 
-__device__ double block_sum_d(double v, double *sh) {
+// FP32 partial per thread: warp sums in FP32, the warps' sums in FP64
+__device__ double block_sum_fd(float v, double *sh) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[w] = v;
+    if (lane == 0) sh[w] = (double)v;
     __syncthreads();
-    if (w == 0) {
-        v = lane < nw ? sh[lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[32] = v;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < nw; ++k) s += sh[k];
+        sh[32] = s;
     }
     __syncthreads();
-    double r = sh[32];
+    const double r = sh[32];
     __syncthreads();
     return r;
 }
@@ -237,10 +237,10 @@ __global__ void __launch_bounds__(kEtaThreads) k_eta_update(const float *__restr
     for (int b = 0; b < windows; ++b) {
         const int m0 = b * nr / windows, m1 = (b + 1) * nr / windows;
         const int i0 = m0 * NETA, i1 = m1 * NETA;
-        double s1 = 0, s2 = 0;
+        float s1 = 0.f, s2 = 0.f;
         for (int i = i0 + tid; i < i1; i += kEtaThreads) { s1 += ga[i]; s2 += gb[i]; }
-        const float ma = (float)(block_sum_d(s1, red) / (i1 - i0));
-        const float mb = (float)(block_sum_d(s2, red) / (i1 - i0));
+        const float ma = (float)(block_sum_fd(s1, red) / (i1 - i0));
+        const float mb = (float)(block_sum_fd(s2, red) / (i1 - i0));
         float2 acc[KPL];
 #pragma unroll
         for (int j = 0; j < KPL; ++j) acc[j] = make_float2(0.f, 0.f);
