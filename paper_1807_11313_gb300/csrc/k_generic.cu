@@ -36,8 +36,15 @@ constexpr size_t smem_prep_real() {
     return sizeof(float2) * ((size_t)(N / 2) * (N + 1) + N + N / 2 + 2 * N);
 }
 
+// threads per CTA: more warps for the larger sides hide the shared-memory and
+// global-load latency of the line transforms
 template <int N>
-__global__ void __launch_bounds__(kThreads) k_prep_real(const float *__restrict__ img, PrepArgs a,
+constexpr int prep_threads() { return N >= 128 ? 512 : kThreads; }
+template <int N>
+constexpr int peak_threads() { return N >= 128 ? 1024 : kThreads; }
+
+template <int N, int PT = prep_threads<N>()>
+__global__ void __launch_bounds__(PT) k_prep_real(const float *__restrict__ img, PrepArgs a,
                                                         float2 *__restrict__ spec, float *__restrict__ spatial,
                                                         int *__restrict__ degen, const int *__restrict__ active) {
     constexpr int H = N / 2, LD = N + 1, HW = N / 2 + 1;
@@ -63,7 +70,7 @@ __global__ void __launch_bounds__(kThreads) k_prep_real(const float *__restrict_
     // zero variance; the shift keeps the per-thread sums well conditioned), combined in FP64
     const float x0 = __ldg(src + (size_t)a.oy * a.W + a.ox);
     float s1 = 0.f, s2 = 0.f;
-    for (int idx = tid; idx < N * N; idx += kThreads) {
+    for (int idx = tid; idx < N * N; idx += PT) {
         const int r = idx / N, c = idx % N;
         const float v = src[(size_t)(a.oy + r) * a.W + a.ox + c];
         reinterpret_cast<float *>(buf + (r >> 1) * LD + c)[r & 1] = v;
@@ -78,7 +85,7 @@ __global__ void __launch_bounds__(kThreads) k_prep_real(const float *__restrict_
     double energy = 0.0;
     if (!bad) {
         const float m = (float)mean, inv = (float)(1.0 / sd);
-        for (int idx = tid; idx < H * N; idx += kThreads) {
+        for (int idx = tid; idx < H * N; idx += PT) {
             const int pr = idx / N, c = idx % N;
             const float wc = (a.window ? 0.5f * (1.f - cospif(2.f * c / N)) : 1.f) * inv;
             const float w0 = a.window ? 0.5f * (1.f - cospif(2.f * (2 * pr) / N)) : 1.f;
@@ -90,11 +97,11 @@ __global__ void __launch_bounds__(kThreads) k_prep_real(const float *__restrict_
         smem_fft_lines<N>(buf, H, LD, 1, twN);   // rows
         __syncthreads();
         {   // split every packed row into its two real rows' half spectra
-            constexpr int ITEMS = H * (N / 2), PER = (ITEMS + kThreads - 1) / kThreads;
+            constexpr int ITEMS = H * (N / 2), PER = (ITEMS + PT - 1) / PT;
             float2 ra[PER], rb[PER];
 #pragma unroll
             for (int k = 0; k < PER; ++k) {
-                const int it = tid + k * kThreads;
+                const int it = tid + k * PT;
                 if (it < ITEMS) {
                     const int pr = it / (N / 2), v = it % (N / 2);
                     const float2 *row = buf + pr * LD;
@@ -112,7 +119,7 @@ __global__ void __launch_bounds__(kThreads) k_prep_real(const float *__restrict_
             __syncthreads();
 #pragma unroll
             for (int k = 0; k < PER; ++k) {
-                const int it = tid + k * kThreads;
+                const int it = tid + k * PT;
                 if (it < ITEMS) {
                     const int pr = it / (N / 2), v = it % (N / 2);
                     buf[pr * LD + v] = ra[k];
@@ -124,7 +131,7 @@ __global__ void __launch_bounds__(kThreads) k_prep_real(const float *__restrict_
         smem_fft_lines<H>(buf, N, 1, LD, twH);   // even-row and odd-row halves of every column
         __syncthreads();
         // join the halves: X[u] = E[u] + w^u O[u], X[u + N/2] = E[u] - w^u O[u]
-        for (int it = tid; it < H * (N / 2); it += kThreads) {
+        for (int it = tid; it < H * (N / 2); it += PT) {
             const int u = it / (N / 2), v = it % (N / 2);
             const float2 w = twN[u];
             if (v == 0) {
@@ -149,7 +156,7 @@ __global__ void __launch_bounds__(kThreads) k_prep_real(const float *__restrict_
         __syncthreads();
         // band-pass and the filtered energy (bins 1..N/2-1 stand for their mirror images too)
         float e = 0.f;
-        for (int it = tid; it < N * HW; it += kThreads) {
+        for (int it = tid; it < N * HW; it += PT) {
             const int u = it / HW, v = it % HW;
             float2 *x = v == 0 ? c0 + u : (v == N / 2 ? cH + u : buf + (u & (H - 1)) * LD + (u >= H ? N / 2 : 0) + v);
             const float fu = (float)(u < N / 2 ? u : u - N), fv = (float)(v < N / 2 ? v : v - N);
@@ -164,13 +171,13 @@ __global__ void __launch_bounds__(kThreads) k_prep_real(const float *__restrict_
     }
     if (tid == 0 && degen) degen[p] = bad ? 1 : 0;
     if (bad) {
-        for (int idx = tid; idx < N * HW; idx += kThreads) out[idx] = make_float2(0.f, 0.f);
+        for (int idx = tid; idx < N * HW; idx += PT) out[idx] = make_float2(0.f, 0.f);
         if (spatial)
-            for (int idx = tid; idx < N * N; idx += kThreads) spatial[(size_t)p * N * N + idx] = 0.f;
+            for (int idx = tid; idx < N * N; idx += PT) spatial[(size_t)p * N * N + idx] = 0.f;
         return;
     }
     const float sc = (float)(1.0 / sqrt(energy));
-    for (int it = tid; it < N * HW; it += kThreads) {
+    for (int it = tid; it < N * HW; it += PT) {
         const int u = it / HW, v = it % HW;
         const float2 X = v == 0 ? c0[u] : (v == N / 2 ? cH[u] : buf[(u & (H - 1)) * LD + (u >= H ? N / 2 : 0) + v]);
         out[it] = make_float2(X.x * sc, X.y * sc);
@@ -178,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_prep_real(const float *__restrict_
     if (!spatial) return;
     __syncthreads();
     // ---- spatial image: undo the join (E = X[u] + X[u + N/2], O = w^-u (X[u] - X[u + N/2]))
-    for (int it = tid; it < H * (N / 2); it += kThreads) {
+    for (int it = tid; it < H * (N / 2); it += PT) {
         const int u = it / (N / 2), v = it % (N / 2);
         const float2 wi = twNi[u];
         if (v == 0) {
@@ -198,11 +205,11 @@ __global__ void __launch_bounds__(kThreads) k_prep_real(const float *__restrict_
     smem_fft_lines<H>(buf, N, 1, LD, twHi);   // columns back: R'[y][v] in the split layout
     __syncthreads();
     {   // rows 2pr, 2pr+1 as one complex line: z[v] = Ra[v] + i Rb[v], conjugate-symmetric extension
-        constexpr int ITEMS = H * N, PER = (ITEMS + kThreads - 1) / kThreads;
+        constexpr int ITEMS = H * N, PER = (ITEMS + PT - 1) / PT;
         float2 zz[PER];
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            const int it = tid + k * kThreads;
+            const int it = tid + k * PT;
             if (it < ITEMS) {
                 const int pr = it / N, v = it % N;
                 const float2 *row = buf + pr * LD;
@@ -225,7 +232,7 @@ __global__ void __launch_bounds__(kThreads) k_prep_real(const float *__restrict_
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            const int it = tid + k * kThreads;
+            const int it = tid + k * PT;
             if (it < ITEMS) buf[(it / N) * LD + it % N] = zz[k];
         }
     }
@@ -233,7 +240,7 @@ __global__ void __launch_bounds__(kThreads) k_prep_real(const float *__restrict_
     smem_fft_lines<N>(buf, H, LD, 1, twNi);   // rows back
     __syncthreads();
     const float invn = 1.f / N;
-    for (int idx = tid; idx < N * N; idx += kThreads) {
+    for (int idx = tid; idx < N * N; idx += PT) {
         const int r = idx / N, c = idx % N;
         const float2 z = buf[(r >> 1) * LD + c];
         spatial[(size_t)p * N * N + idx] = ((r & 1) ? z.y : z.x) * invn;
@@ -270,8 +277,8 @@ __device__ __forceinline__ float parabola(float cm, float c0, float cp) {
 // real and imaginary parts of one complex inverse transform are the two
 // surfaces.  A pattern that is skipped (inactive) or has no template
 // contributes X = 0.
-template <int N>
-__global__ void __launch_bounds__(kThreads) k_pair_peak(const float2 *__restrict__ St,
+template <int N, int QT = peak_threads<N>()>
+__global__ void __launch_bounds__(QT) k_pair_peak(const float2 *__restrict__ St,
                                                         const int *__restrict__ tidx,
                                                         const float2 *__restrict__ Sp,
                                                         const int *__restrict__ degen,
@@ -282,8 +289,8 @@ __global__ void __launch_bounds__(kThreads) k_pair_peak(const float2 *__restrict
     extern __shared__ float4 smem_raw[];
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
     float2 *twi = buf + N * LD;
-    __shared__ float rv[2][kThreads / 32];
-    __shared__ int ri[2][kThreads / 32];
+    __shared__ float rv[2][QT / 32];
+    __shared__ int ri[2][QT / 32];
     const int tid = threadIdx.x;
     int pp[2], mode[2], tt[2];   // mode: 0 skip, 1 zero outputs, 2 compute
     for (int s = 0; s < 2; ++s) {
@@ -309,7 +316,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_peak(const float2 *__restrict
     const float2 *qa = Sp + (size_t)(mode[0] == 2 ? pp[0] : 0) * N * HW;
     const float2 *qb = Sp + (size_t)(mode[1] == 2 ? pp[1] : 0) * N * HW;
     const float fa = mode[0] == 2 ? 1.f : 0.f, fb = mode[1] == 2 ? 1.f : 0.f;
-    for (int idx = tid; idx < N * N; idx += kThreads) {
+    for (int idx = tid; idx < N * N; idx += QT) {
         const int r = idx / N, c = idx % N;
         const bool direct = c <= N / 2;
         const int k = direct ? r * HW + c : ((N - r) & (N - 1)) * HW + (N - c);   // conj(X(-u, -v)) above N/2
@@ -322,7 +329,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_peak(const float2 *__restrict
     fft2_smem<N>(buf, twi);
     float bv[2] = {-INFINITY, -INFINITY};
     int bi[2] = {0x7fffffff, 0x7fffffff};
-    for (int idx = tid; idx < N * N; idx += kThreads) {
+    for (int idx = tid; idx < N * N; idx += QT) {
         const float2 v = buf[(idx / N) * LD + idx % N];
         if (v.x > bv[0]) { bv[0] = v.x; bi[0] = idx; }
         if (v.y > bv[1]) { bv[1] = v.y; bi[1] = idx; }
@@ -343,7 +350,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_peak(const float2 *__restrict
         const int s = tid, p = pp[s];
         float b = rv[s][0];
         int i0 = ri[s][0];
-        for (int k = 1; k < kThreads / 32; ++k)
+        for (int k = 1; k < QT / 32; ++k)
             if (rv[s][k] > b || (rv[s][k] == b && ri[s][k] < i0)) { b = rv[s][k]; i0 = ri[s][k]; }
         const int y0 = i0 / N, x0 = i0 % N;
         auto at = [&](int y, int x) {
@@ -381,7 +388,7 @@ cudaError_t prep_n(const float *img, int P, const PrepArgs &a, float2 *spec, flo
     const size_t sm = smem_prep_real<N>();
     cudaError_t e = set_smem(k_prep_real<N>, sm);
     if (e != cudaSuccess) return e;
-    k_prep_real<N><<<P, kThreads, sm, st>>>(img, a, spec, spatial, degen, active);
+    k_prep_real<N><<<P, prep_threads<N>(), sm, st>>>(img, a, spec, spatial, degen, active);
     return cudaGetLastError();
 }
 
@@ -410,7 +417,7 @@ cudaError_t pair_peak_n(const float2 *St, const int *tidx, const float2 *Sp, con
     size_t sm = smem_bytes_generic<N>();
     cudaError_t e = set_smem(k_pair_peak<N>, sm);
     if (e != cudaSuccess) return e;
-    k_pair_peak<N><<<(P + 1) / 2, kThreads, sm, st>>>(St, tidx, Sp, degen, active, P, peak, shift, argmax);
+    k_pair_peak<N><<<(P + 1) / 2, peak_threads<N>(), sm, st>>>(St, tidx, Sp, degen, active, P, peak, shift, argmax);
     return cudaGetLastError();
 }
 

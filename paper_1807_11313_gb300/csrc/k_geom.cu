@@ -118,8 +118,7 @@ __global__ void __launch_bounds__(256) k_project(const float *__restrict__ maste
         R[0] = 1 - 2 * (q.y * q.y + q.z * q.z); R[1] = 2 * (q.x * q.y - q.w * q.z); R[2] = 2 * (q.x * q.z + q.w * q.y);
         R[3] = 2 * (q.x * q.y + q.w * q.z); R[4] = 1 - 2 * (q.x * q.x + q.z * q.z); R[5] = 2 * (q.y * q.z - q.w * q.x);
         R[6] = 2 * (q.x * q.z - q.w * q.y); R[7] = 2 * (q.y * q.z + q.w * q.x); R[8] = 1 - 2 * (q.x * q.x + q.y * q.y);
-        double sa, ca;
-        sincos(a.alpha, &sa, &ca);
+        const double sa = a.sa, ca = a.ca;
         // G = R(q) Rx(alpha): detector direction -> crystal direction
         for (int i = 0; i < 3; ++i) {
             G[3 * i + 0] = (float)R[3 * i + 0];
@@ -408,6 +407,9 @@ __global__ void k_scan_setup(const double *__restrict__ q, const double *__restr
 
 cudaError_t launch_project(const float *master, int M, const double *quats, const double *pcs,
                            const int *active, int P, const ProjArgs &a, float *out, cudaStream_t st) {
+    ProjArgs b = a;   // the rotation's cosine and sine once, on the host
+    b.ca = cos(a.alpha);
+    b.sa = sin(a.alpha);
     if (P <= 0) return cudaSuccess;
     const size_t npx = (size_t)a.nx * a.ny;
     for (int p0 = 0; p0 < P; p0 += 65535) {          // grid.y limit
@@ -415,7 +417,7 @@ cudaError_t launch_project(const float *master, int M, const double *quats, cons
         // 16 pixels per thread: the per-block float64 frame set-up is amortised over 4096 pixels
         dim3 grid((unsigned)((npx + 4095) / 4096), np);
         k_project<<<grid, 256, 0, st>>>(master, M, quats + 4 * (size_t)p0, pcs ? pcs + 3 * (size_t)p0 : nullptr,
-                                        active ? active + p0 : nullptr, a, out + npx * p0);
+                                        active ? active + p0 : nullptr, b, out + npx * p0);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -19,6 +19,7 @@ struct ProjArgs {
     double pcx, pcy, pcz;     // default pattern centre (when pcs == nullptr)
     double alpha;             // detector -> sample rotation about x, radians
     int interp = 0;           // master lookup: 0 bilinear, 1 bicubic (Keys)
+    double ca = 1.0, sa = 0.0;   // cos / sin of alpha (set by launch_project)
 };
 
 // pre-processing: images [P, H, W] -> half spectra [P, N, N/2+1] (+ spatial [P, N, N])
