@@ -98,7 +98,8 @@ struct Src {   // layer input: activations [B][C][S][S], or the raw patterns (la
 // im2col element (k = ci*9 + ky*3 + kx, n = b*So*So + oy*So + ox)
 __device__ __forceinline__ float im2col(const Src &s, int So, int k, int n) {
     const int ci = k / 9, r = k - ci * 9, ky = r / 3, kx = r - ky * 3;
-    const int b = n / (So * So), p = n - b * So * So, oy = p / So, ox = p - oy * So;
+    const int lg = __ffs(So) - 1;   // output sides are powers of two: shifts, not divisions
+    const int b = n >> (2 * lg), p = n & (So * So - 1), oy = p >> lg, ox = p & (So - 1);
     const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
     if (iy < 0 || iy >= s.S || ix < 0 || ix >= s.S) return 0.f;
     const float v = s.x[b * s.img_stride + (long)ci * s.S * s.S + (long)(s.oy + iy) * s.row_stride + s.ox + ix];
@@ -139,7 +140,7 @@ struct LoadGradT {   // A(m = co, k = (b, p)) = g[b][co][p]
     const float *g;
     int C, Q;
     __device__ float operator()(int m, int k) const {
-        const int b = k / Q, p = k - b * Q;
+        const int b = k >> (__ffs(Q) - 1), p = k & (Q - 1);   // Q is a power of two
         return g[((long)b * C + m) * Q + p];
     }
 };
@@ -151,7 +152,8 @@ struct LoadGradScatter {
     __device__ float operator()(int k, int n) const {
         const int Si = 2 * So;
         const int co = k / 9, r = k - co * 9, ky = r / 3, kx = r - ky * 3;
-        const int b = n / (Si * Si), p = n - b * Si * Si, iy = p / Si, ix = p - iy * Si;
+        const int lg = __ffs(Si) - 1;   // a power of two
+        const int b = n >> (2 * lg), p = n & (Si * Si - 1), iy = p >> lg, ix = p & (Si - 1);
         const int ty = iy + 1 - ky, tx = ix + 1 - kx;
         if (ty < 0 || tx < 0 || (ty & 1) || (tx & 1)) return 0.f;
         const int oy = ty >> 1, ox = tx >> 1;
@@ -181,7 +183,7 @@ struct EpConv {   // y[b][co][p] = relu(acc + bias[co])
     const float *bias;
     int Co, Q;
     __device__ void operator()(int m, int n, float v) const {
-        const int b = n / Q, p = n - b * Q;
+        const int b = n >> (__ffs(Q) - 1), p = n & (Q - 1);   // Q is a power of two
         y[((long)b * Co + m) * Q + p] = fmaxf(v + bias[m], 0.f);
     }
 };
@@ -209,7 +211,7 @@ struct EpMaskedImg {   // gx[b][ci][p] = acc * (a[b][ci][p] > 0), n = b*Q + p
     const float *mask;
     int C, Q;
     __device__ void operator()(int m, int n, float v) const {
-        const int b = n / Q, p = n - b * Q;
+        const int b = n >> (__ffs(Q) - 1), p = n & (Q - 1);   // Q is a power of two
         const long i = ((long)b * C + m) * Q + p;
         y[i] = mask[i] > 0.f ? v : 0.f;
     }
