@@ -124,6 +124,7 @@ def _lib_handle():
                 "orc_cubic_matrices": ([_D], None),
                 "orc_cnn_head_loss": ([_D, C.c_int, _D, _D, _I, _I], C.c_double),
                 "orc_cnn_forward": ([_F, _D, C.c_int, C.c_int, _D], None),
+                "orc_cnn_forward_bf16": ([_F, _D, C.c_int, C.c_int, _D], None),
                 "orc_cnn_loss_grad": ([_F, _D, C.c_int, C.c_int, _D, _D, _I], C.c_double),
                 "orc_adam": ([_D, _D, _D, _D, C.c_long, C.c_int, C.c_double, C.c_double, C.c_double,
                               C.c_double], None),
@@ -603,6 +604,15 @@ def cnn_forward(params, x, k=8):
     B = x.shape[0]
     out = np.empty((B, 6 * k))
     _lib_handle().orc_cnn_forward(_f(_f32(params)), _d(x), B, k, _d(out))
+    return out
+
+
+def cnn_forward_bf16(params, x, k=8):
+    """The BF16 inference form: convolutions 2..5 on BF16-rounded inputs and weights."""
+    x = _f64(x)
+    B = x.shape[0]
+    out = np.empty((B, 6 * k))
+    _lib_handle().orc_cnn_forward_bf16(_f(_f32(params)), _d(x), B, k, _d(out))
     return out
 
 

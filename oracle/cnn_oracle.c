@@ -247,7 +247,13 @@ static void acts_free(acts_t *A) {
     for (int l = 0; l < CNN_LAYERS; ++l) free(A->a[l]);
 }
 
-static void forward_one(const float *params, const double *x, int k, acts_t *A, double *out) {
+double orc_bf16_round(double x);
+
+/* bf16 != 0: the inference form whose convolutions after the first take
+ * BF16 operands (the layer input rounded through FP32 to BF16, and the
+ * layer's weights likewise); accumulation, bias, ReLU, pool and the fully
+ * connected layers unchanged. */
+static void forward_one_p(const float *params, const double *x, int k, acts_t *A, double *out, int bf16) {
     long cw[CNN_LAYERS], cb[CNN_LAYERS], f1w, f1b, f2w, f2b;
     const long np = param_offsets(k, cw, cb, &f1w, &f1b, &f2w, &f2b);
     double *p = malloc(sizeof(double) * np);
@@ -256,6 +262,11 @@ static void forward_one(const float *params, const double *x, int k, acts_t *A, 
     const double *in = A->x0;
     int s = CNN_SIDE;
     for (int l = 0; l < CNN_LAYERS; ++l) {
+        if (bf16 && l > 0) {
+            const long nin = (long)kCh[l] * s * s;
+            for (long i = 0; i < nin; ++i) A->a[l - 1][i] = orc_bf16_round(A->a[l - 1][i]);
+            for (long i = 0; i < conv_w_count(l); ++i) p[cw[l] + i] = orc_bf16_round(p[cw[l] + i]);
+        }
         orc_conv3x3s2(in, kCh[l], s, p + cw[l], p + cb[l], kCh[l + 1], A->a[l]);
         s /= 2;
         const long cnt = (long)kCh[l + 1] * s * s;
@@ -281,6 +292,10 @@ static void forward_one(const float *params, const double *x, int k, acts_t *A, 
     free(p);
 }
 
+static void forward_one(const float *params, const double *x, int k, acts_t *A, double *out) {
+    forward_one_p(params, x, k, A, out, 0);
+}
+
 /* out [B][6k] for images x [B][128][128] */
 void orc_cnn_forward(const float *params, const double *x, int B, int k, double *out) {
 #pragma omp parallel for schedule(dynamic)
@@ -288,6 +303,17 @@ void orc_cnn_forward(const float *params, const double *x, int B, int k, double 
         acts_t A;
         acts_alloc(&A);
         forward_one(params, x + (long)b * CNN_SIDE * CNN_SIDE, k, &A, out + (long)b * 6 * k);
+        acts_free(&A);
+    }
+}
+
+/* the BF16 inference form of orc_cnn_forward (see forward_one_p) */
+void orc_cnn_forward_bf16(const float *params, const double *x, int B, int k, double *out) {
+#pragma omp parallel for schedule(dynamic)
+    for (int b = 0; b < B; ++b) {
+        acts_t A;
+        acts_alloc(&A);
+        forward_one_p(params, x + (long)b * CNN_SIDE * CNN_SIDE, k, &A, out + (long)b * 6 * k, 1);
         acts_free(&A);
     }
 }

@@ -216,3 +216,23 @@ def test_proposals_are_the_heads(orc):
             np.testing.assert_allclose(orc.quat_to_matrix(q[b, h]), orc.gram_schmidt(out[b, 6 * h:6 * h + 6]),
                                        atol=1e-12)
             assert q[b, h, 0] >= 0
+
+
+def test_bf16_form_rounds_only_the_later_convolutions():
+    """The BF16 inference form differs from the FP64 forward by the BF16
+    rounding of the inputs and weights of convolutions 2..5 only: close to it
+    (BF16 keeps 8 significant bits) but not equal; with those layers' weights
+    zeroed it equals the FP64 forward exactly (nothing else is rounded)."""
+    import oracle as orc
+    p = synth.cnn_init_params(8, 9).astype(np.float32)
+    x = np.random.default_rng(9).random((3, 128, 128))
+    a, b = orc.cnn_forward(p, x, 8), orc.cnn_forward_bf16(p, x, 8)
+    scale = np.abs(a).max()
+    assert 0 < np.abs(a - b).max() <= 2e-2 * scale
+    # zero the weights of convolutions 2..5: their outputs are their biases in both forms
+    q = p.copy()
+    o = 32 * 1 * 9 + 32
+    for ci, co in ((32, 64), (64, 64), (64, 128), (128, 128)):
+        q[o:o + co * ci * 9] = 0.0
+        o += co * ci * 9 + co
+    np.testing.assert_array_equal(orc.cnn_forward(q, x, 8), orc.cnn_forward_bf16(q, x, 8))
