@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=256, help="learned form: training batch")
     ap.add_argument("--epochs", type=int, default=2, help="learned form: passes over the training set")
     ap.add_argument("--lr", type=float, default=1e-3, help="learned form: peak learning rate")
+    ap.add_argument("--net-fp32", action="store_true",
+                    help="learned form: FP32 network inference (default: BF16 tensor-core convolutions 2..5)")
     ap.add_argument("--sigma-hp", type=float, default=0.0,
                     help="fwhm form: high-pass sigma of the FFT path, cycles/image (0: the library default)")
     return ap.parse_args()
@@ -735,6 +737,8 @@ def run_learned(args, px, torch, dev, rank, world, local, dist):
             losses.append(float(loss))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
+    # inference precision of the network (training above ran in FP32)
+    net.set_bf16(not args.net_fp32)
     # ---- test set, resident on the device
     teq, tepc, tepk = d(wl["test_q"]), d(wl["test_pcs"]), d(wl["test_peak"])
     pats = _generate(px, torch, ctx, master_d, geom, teq, tepc, tepk, gen)
@@ -799,17 +803,24 @@ def run_learned(args, px, torch, dev, rank, world, local, dist):
     fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
     net_ms, net_n = prof["net"]
     net_flops = CNN_FORWARD_FLOPS * n_test * args.steps
-    roofline = {"bound": "alu", "achieved": net_flops / (net_ms / 1e3) / 1e12 if net_ms else None, "peak": fp32_peak,
-                "unit": "TFLOP/s", "kernel": "proposal network forward (k_gemm)", "traffic": None,
+    if args.net_fp32:
+        net_peak, bound, kern, basis = fp32_peak, "alu", "proposal network forward (k_gemm, FP32)", "FP32 ALU"
+    else:
+        net_peak = (pk or {}).get("bf16_tflops_sustained") or 1700.0
+        bound, kern = "tensor", "proposal network forward (convolution 1 k_gemm FP32; 2-5 im2col + k_screen_tc BF16)"
+        basis = "measured sustained cuBLAS BF16 (MEASURED_PEAKS.json)" if pk else "fallback"
+    roofline = {"bound": bound, "achieved": net_flops / (net_ms / 1e3) / 1e12 if net_ms else None, "peak": net_peak,
+                "unit": "TFLOP/s", "kernel": kern, "peak_basis": basis, "traffic": None,
                 "stage_ms_per_step": {kk: v[0] / args.steps for kk, v in prof.items()}}
-    roofline["frac"] = roofline["achieved"] / fp32_peak if roofline["achieved"] else None
+    roofline["frac"] = roofline["achieved"] / net_peak if roofline["achieved"] else None
     if rank == 0:
         line = {"metric": "patterns indexed/s (learned proposals + correlation score + refinement, full-search fallback)",
                 "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f32" if args.net_fp32 else "bf16 network + f32 xcf",
+                "data": "synthetic",
                 "config": {"workload": wl["name"], "form": "learned", "detector": n, "templates": lib.T, "heads": k,
-                           "train_patterns": n_train, "epochs": args.epochs, "batch": B, "test_patterns": n_test,
+                           "network_inference": "fp32" if args.net_fp32 else "bf16", "train_patterns": n_train, "epochs": args.epochs, "batch": B, "test_patterns": n_test,
                            "tau": tau, "calibration_patterns": len(wl["cal_q"]),
                            "calibration_accepted_fraction": cal_accept,
                            "parallelism": f"replicas x{world}",

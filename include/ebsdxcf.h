@@ -440,6 +440,15 @@ int xcf_net_loss_grad(xcf_ctx *ctx, xcf_net *net, const float *images, int32_t B
  * p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
 int xcf_net_adam(xcf_ctx *ctx, xcf_net *net, float lr, float beta1, float beta2, float eps, void *stream);
 
+/* Inference precision of the network's forward pass in xcf_net_forward,
+ * xcf_propose and xcf_index_learned: on = 0 FP32 (default); on = 1 the
+ * convolutions after the first on the tensor cores with BF16 operands (layer
+ * inputs and weights rounded to BF16) and FP32 accumulation.  Training
+ * (xcf_net_loss_grad) always runs in FP32.  With BF16 on, those calls wait
+ * for the device at their end to read the tensor-core status word
+ * (XCF_ERR_TIMEOUT if a bounded wait gave up).  Host only. */
+int xcf_net_set_bf16(xcf_net *net, int32_t on);
+
 /* k proposals per pattern: quats [P][k][4] (unit, w >= 0). */
 int xcf_propose(xcf_ctx *ctx, xcf_net *net, const float *patterns, int32_t P, const xcf_geometry *g,
                 double *quats, void *stream);

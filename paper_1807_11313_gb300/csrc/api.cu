@@ -1416,13 +1416,43 @@ int check_net(xcf_ctx *ctx, const xcf_net *net) {
     return XCF_OK;
 }
 
-// forward of B <= kNetChunk images; the outputs stay in net->act
+// forward of B <= kNetChunk images (FP32, or the BF16 inference form); the
+// outputs stay in net->act
 int net_forward_chunk(xcf_ctx *ctx, xcf_net *net, const CnnInput &in, int B, cudaStream_t st) {
     int rc = net_reserve(ctx, net, B, false);
     if (rc) return rc;
     int nl = 0;
-    XCF_LAUNCH(XCF_STAGE_NET, st, launch_cnn_forward(net->params, net->k, in, B, net->act, &nl, st), "net forward");
+    if (net->bf16) {
+        void *work;
+        int *err;
+        if ((rc = scratch(ctx, S_NET_BF16, cnn_bf16_work_bytes(B), &work)) || (rc = scratch_t(ctx, S_ERR, 1, &err)))
+            return rc;
+        XCF_LAUNCH(XCF_STAGE_NET, st, launch_cnn_forward_bf16(net->params, net->k, in, B, net->act, work, err, &nl, st),
+                   "net forward (bf16)");
+    } else {
+        XCF_LAUNCH(XCF_STAGE_NET, st, launch_cnn_forward(net->params, net->k, in, B, net->act, &nl, st),
+                   "net forward");
+    }
     ctx->launches[XCF_STAGE_NET] += nl - 1;
+    return XCF_OK;
+}
+
+// the BF16 form's tensor-core status word: cleared before a call's forward
+// passes, read (waiting for the device) after them
+int net_status_begin(xcf_ctx *ctx, const xcf_net *net, cudaStream_t st) {
+    if (!net->bf16) return XCF_OK;
+    int *err, rc;
+    if ((rc = scratch_t(ctx, S_ERR, 1, &err))) return rc;
+    XCF_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st), "clear status");
+    return XCF_OK;
+}
+int net_status_end(xcf_ctx *ctx, const xcf_net *net, cudaStream_t st, const char *fn) {
+    if (!net->bf16) return XCF_OK;
+    int *err, rc, h = 0;
+    if ((rc = scratch_t(ctx, S_ERR, 1, &err))) return rc;
+    XCF_CHECK(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+    XCF_CHECK(cudaStreamSynchronize(st), fn);
+    if (h) return fail(ctx, XCF_ERR_TIMEOUT, std::string(fn) + ": a tensor-core pipeline wait timed out");
     return XCF_OK;
 }
 
@@ -1434,6 +1464,8 @@ CnnInput offset_input(const CnnInput &in, long b0) {
 
 // proposals of P patterns -> quats [P][k][4]
 int propose_all(xcf_ctx *ctx, xcf_net *net, const CnnInput &in, int P, double *quats, cudaStream_t st) {
+    int rc0 = net_status_begin(ctx, net, st);
+    if (rc0) return rc0;
     for (int b0 = 0; b0 < P; b0 += kNetChunk) {
         const int nb = P - b0 < kNetChunk ? P - b0 : kNetChunk;
         int rc = net_forward_chunk(ctx, net, offset_input(in, b0), nb, st);
@@ -1443,7 +1475,7 @@ int propose_all(xcf_ctx *ctx, xcf_net *net, const CnnInput &in, int P, double *q
                                         quats + (size_t)b0 * net->k * 4, st),
                    "proposals");
     }
-    return XCF_OK;
+    return net_status_end(ctx, net, st, "proposals");
 }
 
 }  // namespace
@@ -1508,6 +1540,7 @@ int xcf_net_forward(xcf_ctx *ctx, xcf_net *net, const float *images, int32_t B, 
     if ((rc = net_input(ctx, images, g, &in))) return rc;
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = net_status_begin(ctx, net, st))) return rc;
     for (int b0 = 0; b0 < B; b0 += kNetChunk) {
         const int nb = B - b0 < kNetChunk ? B - b0 : kNetChunk;
         if ((rc = net_forward_chunk(ctx, net, offset_input(in, b0), nb, st))) return rc;
@@ -1515,6 +1548,12 @@ int xcf_net_forward(xcf_ctx *ctx, xcf_net *net, const float *images, int32_t B, 
                                   sizeof(float) * 6 * net->k * nb, cudaMemcpyDeviceToDevice, st),
                   "net outputs");
     }
+    return net_status_end(ctx, net, st, "xcf_net_forward");
+}
+
+int xcf_net_set_bf16(xcf_net *net, int32_t on) {
+    if (!net || (on != 0 && on != 1)) return XCF_ERR_ARG;
+    net->bf16 = on;
     return XCF_OK;
 }
 

@@ -57,6 +57,7 @@ enum Slot {
     S_NN_KEYS,      // nearest neighbour: packed best keys
     S_NN_ANG,       // nearest neighbour: angles (generator's duplicate pass)
     S_NN_IDX,       // nearest neighbour: indices (generator's duplicate pass)
+    S_NET_BF16,     // proposal network, BF16 inference: weights and im2col matrix
     S_COUNT
 };
 
@@ -119,6 +120,7 @@ inline const float2 *search_spectra(const xcf_library *lib) {
 struct xcf_net {
     int device = 0;
     int k = 0;
+    int bf16 = 0;                   // inference forward: 0 FP32, 1 BF16 tensor-core convolutions
     long n = 0;                     // parameter count
     float *params = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;   // [n] each, one allocation
     int t = 0;                      // Adam steps taken

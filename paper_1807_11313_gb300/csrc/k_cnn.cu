@@ -16,6 +16,10 @@
 // written: C[m][n] = sum_k A(m, k) B(k, n) with the layer's loaders and
 // epilogue.  Weight gradients split the long reduction over gridDim.z and
 // accumulate with atomics.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -231,12 +235,16 @@ struct EpAtomic {   // grad[m][n] += acc
 // per-pattern (scale, shift) of the standardisation of the crop: (x - mean) / std
 __global__ void k_cnn_stats(const float *__restrict__ x, long img_stride, long row_stride, int ox, int oy,
                             int S, float2 *__restrict__ affine) {
+    // FP32 partial sums of (v - v0), v0 the first pixel (a constant image has exactly zero
+    // variance; the shift keeps the partial sums well conditioned), combined in FP64
     const float *img = x + blockIdx.x * img_stride + (long)oy * row_stride + ox;
-    double s = 0.0, s2 = 0.0;
+    const int lg = __ffs(S) - 1;   // S is a power of two
+    const float v0 = img[0];
+    float s = 0.f, s2 = 0.f;
     for (int i = threadIdx.x; i < S * S; i += blockDim.x) {
-        const double v = img[(long)(i / S) * row_stride + i % S];
-        s += v;
-        s2 += v * v;
+        const float d = img[(long)(i >> lg) * row_stride + (i & (S - 1))] - v0;
+        s += d;
+        s2 = fmaf(d, d, s2);
     }
     __shared__ double r1[32], r2[32];
     for (int o = 16; o; o >>= 1) {
@@ -254,8 +262,8 @@ __global__ void k_cnn_stats(const float *__restrict__ x, long img_stride, long r
             a += r1[w];
             b += r2[w];
         }
-        const double n = (double)S * S, mean = a / n;
-        const double var = fmax(b / n - mean * mean, 0.0), sd = sqrt(var);
+        const double n = (double)S * S, m1 = a / n, mean = v0 + m1;
+        const double var = fmax(b / n - m1 * m1, 0.0), sd = sqrt(var);
         const bool degenerate = !(sd > 1e-12 * (1.0 + fabs(mean)));
         affine[blockIdx.x] = degenerate ? make_float2(0.f, 0.f) : make_float2((float)(1.0 / sd), (float)(-mean / sd));
     }
@@ -267,6 +275,113 @@ __global__ void k_cnn_pool(const float *__restrict__ a, int BC, int Q, float *__
     if (i >= BC) return;
     float s = 0.f;
     for (int p = 0; p < Q; ++p) s += a[(long)i * Q + p];
+    pool[i] = s / Q;
+}
+
+// ---- BF16 inference form: convolutions 2..5 as tensor-core products of a
+// BF16 im2col matrix [rows = B So^2][Kp] and the layer's BF16 weights
+// [Co][Kp] (K = 9 Ci padded with zeros to Kp, a multiple of 64), FP32
+// accumulation into [rows][Co] (NHWC activations), then bias and ReLU.  The
+// first convolution (K = 9) stays an FP32 product and writes NHWC too.
+
+// im2col rows of NHWC input [B][S][S][Ci] (Ci a power of two, >= 8) in the
+// order k = (ky * 3 + kx) Ci + ci: each thread moves 8 consecutive channels
+// of one input pixel (two float4 loads, one 16-byte store of 8 BF16); zeros
+// for k >= 9 Ci.  Eight output positions per CTA.
+constexpr int kIm2colRows = 8;
+__global__ void __launch_bounds__(256) k_cnn_im2col_bf16(const float *__restrict__ x, int Ci, int S, int Kp,
+                                                         long rows, __nv_bfloat16 *__restrict__ out) {
+    const int So = S / 2, lg = __ffs(So) - 1, lc = __ffs(Ci) - 1, K = 9 * Ci, K8 = Kp / 8;
+    for (int rr = 0; rr < kIm2colRows; ++rr) {
+        const long row = (long)blockIdx.x * kIm2colRows + rr;
+        if (row >= rows) return;
+        const int b = (int)(row >> (2 * lg)), p = (int)(row & (So * So - 1)), oy = p >> lg, ox = p & (So - 1);
+        for (int k8 = threadIdx.x; k8 < K8; k8 += blockDim.x) {
+            const int k = 8 * k8;
+            float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+            if (k < K) {
+                const int r = k >> lc, ci = k & (Ci - 1), ky = r / 3, kx = r - 3 * ky;
+                const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
+                if (iy >= 0 && iy < S && ix >= 0 && ix < S) {
+                    const float4 *src = reinterpret_cast<const float4 *>(x + (((long)b * S + iy) * S + ix) * Ci + ci);
+                    lo = src[0];
+                    hi = src[1];
+                }
+            }
+            __nv_bfloat162 h[4] = {__floats2bfloat162_rn(lo.x, lo.y), __floats2bfloat162_rn(lo.z, lo.w),
+                                   __floats2bfloat162_rn(hi.x, hi.y), __floats2bfloat162_rn(hi.z, hi.w)};
+            *reinterpret_cast<uint4 *>(out + row * Kp + k) = *reinterpret_cast<const uint4 *>(h);
+        }
+    }
+}
+
+// the first convolution (one input channel, 32 outputs) directly: one thread
+// per output position, the standardised 3 x 3 input window against all 32
+// filters (weights and biases in shared memory), bias, ReLU, NHWC output
+__global__ void __launch_bounds__(256) k_cnn_conv1_nhwc(const float *__restrict__ x, long img_stride,
+                                                        long row_stride, int ox0, int oy0,
+                                                        const float2 *__restrict__ affine,
+                                                        const float *__restrict__ w, const float *__restrict__ bias,
+                                                        int B, float *__restrict__ y) {
+    constexpr int S = 128, So = 64, Co = 32;
+    __shared__ float ws[Co * 9], bs[Co];
+    for (int i = threadIdx.x; i < Co * 9; i += blockDim.x) ws[i] = w[i];
+    if (threadIdx.x < Co) bs[threadIdx.x] = bias[threadIdx.x];
+    __syncthreads();
+    const long n = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (long)B * So * So) return;
+    const int b = (int)(n >> 12), p = (int)(n & 4095), oy = p >> 6, ox = p & 63;
+    const float2 a = affine[b];
+    const float *img = x + b * img_stride + (long)oy0 * row_stride + ox0;
+    float v[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        const int iy = 2 * oy - 1 + r / 3, ix = 2 * ox - 1 + r % 3;
+        v[r] = (iy >= 0 && iy < S && ix >= 0 && ix < S) ? fmaf(img[(long)iy * row_stride + ix], a.x, a.y) : 0.f;
+    }
+    float4 *dst = reinterpret_cast<float4 *>(y + n * Co);
+#pragma unroll
+    for (int c4 = 0; c4 < Co / 4; ++c4) {
+        float o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = 4 * c4 + j;
+            float acc = bs[c];
+#pragma unroll
+            for (int r = 0; r < 9; ++r) acc = fmaf(ws[c * 9 + r], v[r], acc);
+            o[j] = fmaxf(acc, 0.f);
+        }
+        dst[c4] = make_float4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+// weights [Co][Ci][9] FP32 -> [Co][Kp] BF16 in the im2col order (r Ci + ci), zero padded
+__global__ void k_cnn_weights_bf16(const float *__restrict__ w, int Co, int Ci, int Kp,
+                                   __nv_bfloat16 *__restrict__ out) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long)Co * Kp) return;
+    const int co = (int)(i / Kp), k = (int)(i - (long)co * Kp);
+    float v = 0.f;
+    if (k < 9 * Ci) {
+        const int r = k / Ci, ci = k - r * Ci;
+        v = w[((long)co * Ci + ci) * 9 + r];
+    }
+    out[i] = __float2bfloat16_rn(v);
+}
+
+// y[row][c] = relu(y[row][c] + bias[c]), C a power of two
+__global__ void k_cnn_bias_relu_rows(float *__restrict__ y, const float *__restrict__ bias, long n, int C) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        y[i] = fmaxf(y[i] + bias[i & (C - 1)], 0.f);
+}
+
+// mean over the Q positions of NHWC activations [B][Q][C]: pool[b][c]
+__global__ void k_cnn_pool_nhwc(const float *__restrict__ a, int B, int C, int Q, float *__restrict__ pool) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * C) return;
+    const int b = i / C, c = i - b * C;
+    float s = 0.f;
+    for (int p = 0; p < Q; ++p) s += a[((long)b * Q + p) * C + c];
     pool[i] = s / Q;
 }
 
@@ -606,6 +721,75 @@ cudaError_t launch_cnn_forward(const float *params, int k, const CnnInput &in, i
         s = so;
     }
     k_cnn_pool<<<(B * kCh[5] + 255) / 256, 256, 0, st>>>(A.a[4], B * kCh[5], 16, A.pool);
+    CNN_TRY(cudaGetLastError());
+    CNN_TRY(gemm(kHidden, B, kCh[5], 1, LoadW{params + L.f1w, kCh[5]}, LoadRows{A.pool, kCh[5]},
+                 EpVec{A.h1, params + L.f1b, kHidden, true}, st));
+    CNN_TRY(gemm(6 * k, B, kHidden, 1, LoadW{params + L.f2w, kHidden}, LoadRows{A.h1, kHidden},
+                 EpVec{A.out, params + L.f2b, 6 * k, false}, st));
+    if (launches) *launches += n_launch + 3;
+    return cudaSuccess;
+}
+
+namespace {
+constexpr int kBf16Kp[5] = {0, 320, 576, 576, 1152};   // 9 Ci rounded up to a multiple of 64
+size_t bf16_weight_elems() {
+    size_t n = 0;
+    for (int l = 1; l < 5; ++l) n += (size_t)kCh[l + 1] * kBf16Kp[l];
+    return n;
+}
+}  // namespace
+
+size_t cnn_bf16_work_bytes(int B) {
+    size_t im = 0;
+    int s = 64;
+    for (int l = 1; l < 5; ++l) {
+        const size_t rows = (size_t)B * (s / 2) * (s / 2);
+        im = std::max(im, rows * kBf16Kp[l]);
+        s /= 2;
+    }
+    return 2 * (im + bf16_weight_elems()) + 256;
+}
+
+cudaError_t launch_cnn_forward_bf16(const float *params, int k, const CnnInput &in, int B, float *act, void *work,
+                                    int *err, int *launches, cudaStream_t st) {
+    if (B <= 0) return cudaSuccess;
+    const Layout L(k);
+    Acts A(act, B, k);
+    __nv_bfloat16 *wb = static_cast<__nv_bfloat16 *>(work);
+    __nv_bfloat16 *im = wb + ((bf16_weight_elems() + 127) & ~(size_t)127);   // 256-byte aligned
+    k_cnn_stats<<<B, 256, 0, st>>>(in.x, in.img_stride, in.row_stride, in.ox, in.oy, 128, A.affine);
+    CNN_TRY(cudaGetLastError());
+    int n_launch = 1;
+    // first convolution (K = 9) directly in FP32; every activation NHWC
+    {
+        const long np = (long)B * 64 * 64;
+        k_cnn_conv1_nhwc<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(in.x, in.img_stride, in.row_stride, in.ox,
+                                                                      in.oy, A.affine, params + L.cw[0],
+                                                                      params + L.cb[0], B, A.a[0]);
+        CNN_TRY(cudaGetLastError());
+        ++n_launch;
+    }
+    __nv_bfloat16 *wl = wb;
+    int s = 64;
+    for (int l = 1; l < 5; ++l) {
+        const int so = s / 2, Kp = kBf16Kp[l], Co = kCh[l + 1];
+        const long rows = (long)B * so * so;
+        const long nw = (long)Co * Kp;
+        k_cnn_weights_bf16<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(params + L.cw[l], Co, kCh[l], Kp, wl);
+        CNN_TRY(cudaGetLastError());
+        k_cnn_im2col_bf16<<<(unsigned)((rows + kIm2colRows - 1) / kIm2colRows), 256, 0, st>>>(A.a[l - 1], kCh[l], s,
+                                                                                            Kp, rows, im);
+        CNN_TRY(cudaGetLastError());
+        CNN_TRY(launch_screen_tc(im, (int)rows, wl, Co, Kp, A.a[l], err, st));
+        const long n = rows * Co;
+        k_cnn_bias_relu_rows<<<(unsigned)std::min<long>((n + 255) / 256, 65535), 256, 0, st>>>(A.a[l],
+                                                                                            params + L.cb[l], n, Co);
+        CNN_TRY(cudaGetLastError());
+        n_launch += 4;
+        wl += nw;
+        s = so;
+    }
+    k_cnn_pool_nhwc<<<(B * kCh[5] + 255) / 256, 256, 0, st>>>(A.a[4], B, kCh[5], 16, A.pool);
     CNN_TRY(cudaGetLastError());
     CNN_TRY(gemm(kHidden, B, kCh[5], 1, LoadW{params + L.f1w, kCh[5]}, LoadRows{A.pool, kCh[5]},
                  EpVec{A.h1, params + L.f1b, kHidden, true}, st));

@@ -175,6 +175,12 @@ long cnn_num_params(int k);
 size_t cnn_act_floats(int B, int k);    // activations of a batch (forward, kept for backward)
 size_t cnn_grad_floats(int B, int k);   // gradient work buffers of a batch
 const float *cnn_output(float *act, int B, int k);   // [B][6k] inside the activations
+// BF16 inference form: convolutions 2..5 on the tensor cores (BF16 operands,
+// FP32 accumulation); the same outputs location; work: cnn_bf16_work_bytes(B)
+// bytes (256-byte aligned); err: the tensor-core pipeline's status word
+size_t cnn_bf16_work_bytes(int B);
+cudaError_t launch_cnn_forward_bf16(const float *params, int k, const CnnInput &in, int B, float *act, void *work,
+                                    int *err, int *launches, cudaStream_t st);
 cudaError_t launch_cnn_forward(const float *params, int k, const CnnInput &in, int B, float *act, int *launches,
                                cudaStream_t st);
 // after launch_cnn_forward on the same act: loss_sum += sum of per-pattern

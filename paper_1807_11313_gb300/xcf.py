@@ -87,6 +87,7 @@ _SIGS = {
     "xcf_index_precision": ([_P, _P, _P, _I32, _P, _I32, _P, _P, _P, _P, _P], C.c_int),
     "xcf_index_ndp": ([_P, _P, _P, _I32, _I32, _P, _P, _P, _P, _P], C.c_int),
     "xcf_rotation_scan": ([_P, _P, _I32, _P, _P, _P, _I32, C.c_double, _P, _P, _P, _P], C.c_int),
+    "xcf_net_set_bf16": ([_P, _I32], C.c_int),
     "xcf_so3_grid": ([_P, C.c_double, _I32, _P, C.c_int64, _P, _P], C.c_int),
     "xcf_nearest_disorientation": ([_P, _P, _I32, _P, _I32, _I32, _P, _P, _P], C.c_int),
     "xcf_index_noalloc": ([_P, _P, _P, _I32, _P, _P, _P, _P], C.c_int),
@@ -569,6 +570,10 @@ class Net:
         v.__cuda_array_interface__ = {"shape": (self.n,), "typestr": "<f4", "data": (self._ptr, False),
                                       "version": 3, "strides": None}
         return torch.as_tensor(v, device="cuda")
+
+    def set_bf16(self, on: bool = True):
+        """Inference forward with BF16 tensor-core convolutions (True) or FP32 (False)."""
+        _check(load().xcf_net_set_bf16(self.handle, 1 if on else 0))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -76,6 +76,31 @@ def test_forward_matches_oracle(px, ctx, orc):
     net.close()
 
 
+def test_bf16_forward_matches_oracle_bf16_form(px, ctx, orc):
+    """BF16 inference: convolutions 2..5 on the tensor cores.  Against the
+    oracle's BF16 form (the same operands rounded to BF16, FP64 accumulation)
+    only the accumulation order differs, apart from rare operands that sit on
+    a BF16 rounding boundary after an FP32 (not FP64) previous layer: 2e-3 of
+    the output scale.  Against the FP32 forward: the BF16 rounding itself."""
+    p = synth.cnn_init_params(K, 5)
+    x = _images(37, 4)                           # ragged against the 128-row tiles
+    x[3] = 2.0                                   # constant image
+    net = px.xcf_net_create(ctx, K, dev(p))
+    net.set_bf16(True)
+    out = px.xcf_net_forward(ctx, net, dev(x)).cpu().numpy()
+    ref = orc.cnn_forward_bf16(p, x, K)
+    scale = np.abs(ref).max()
+    assert np.abs(out - ref).max() <= 2e-3 * scale, np.abs(out - ref).max() / scale
+    assert np.abs(out - orc.cnn_forward(p, x, K)).max() <= 3e-2 * scale
+    # the proposals follow the same forward; FP32 again when switched off
+    q = px.xcf_propose(ctx, net, dev(x[:4])).cpu().numpy()
+    np.testing.assert_allclose(np.linalg.norm(q, axis=-1), 1.0, atol=1e-9)
+    net.set_bf16(False)
+    out32 = px.xcf_net_forward(ctx, net, dev(x)).cpu().numpy()
+    assert np.abs(out32 - orc.cnn_forward(p, x, K)).max() <= 2e-4 * scale
+    net.close()
+
+
 def test_forward_reads_the_centred_crop(px, ctx, orc):
     W, H, pc = 160, 140, (0.5, 0.5, 0.6)
     p = synth.cnn_init_params(K, 4)
