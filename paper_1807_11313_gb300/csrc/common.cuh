@@ -119,6 +119,70 @@ __device__ __forceinline__ void fft_reg_dif(float2 (&x)[R]) {
     });
 }
 
+// ---------------------------------------------------- warp line FFT (N >= 64)
+// One line of N points in shared memory (point i at x[i * es]) transformed
+// by one warp in registers: lane l holds points l + 32 j (j < N/32);
+// decimation in frequency, the stages of span >= 32 pairing registers of a
+// lane and the five of span < 32 pairing lanes through shuffles; the results
+// go back in natural order (bit-reversed store addresses).  tw[k] = exp(SIGN
+// 2 pi i k / N), k < N/2; WarpFftTw holds the twiddles one lane needs, so that
+// a warp transforming several lines loads them once.
+template <int N>
+struct WarpFftTw {
+    static constexpr int R = N / 32, LR = cx_log2(R);
+    float2 wr[R > 1 ? R - 1 : 1];   // register stage st (span 32 h', h' = R >> (st+1)), pair (j, j + h')
+    float2 wc[5];                   // lane stage c (span 16 >> c)
+    __device__ __forceinline__ void load(const float2 *tw, int lane) {
+        int o = 0;
+#pragma unroll
+        for (int st = 0; st < LR; ++st) {
+            const int hp = R >> (st + 1);
+#pragma unroll
+            for (int jm = 0; jm < hp; ++jm) wr[o + jm] = tw[(lane + 32 * jm) << st];
+            o += hp;
+        }
+#pragma unroll
+        for (int c = 0; c < 5; ++c) wc[c] = tw[(lane & ((16 >> c) - 1)) << (LR + c)];
+    }
+};
+
+template <int N>
+__device__ __forceinline__ void warp_fft_reg(float2 *x, int es, const WarpFftTw<N> &t, int lane) {
+    constexpr int R = N / 32, LR = cx_log2(R), LOG = cx_log2(N);
+    static_assert(N >= 64, "register line FFT needs at least two points per lane");
+    float2 v[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) v[j] = x[(lane + 32 * j) * es];
+    int o = 0;
+#pragma unroll
+    for (int st = 0; st < LR; ++st) {
+        const int hp = R >> (st + 1);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            if (j & hp) continue;
+            const float2 a = v[j], b = v[j + hp];
+            v[j] = c_add(a, b);
+            v[j + hp] = c_mul(c_sub(a, b), t.wr[o + (j & (hp - 1))]);
+        }
+        o += hp;
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        const int h = 16 >> c;
+        const bool top = !(lane & h);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const float2 p = make_float2(__shfl_xor_sync(0xffffffffu, v[j].x, h),
+                                         __shfl_xor_sync(0xffffffffu, v[j].y, h));
+            v[j] = top ? c_add(v[j], p) : c_mul(c_sub(p, v[j]), t.wc[c]);
+        }
+    }
+    // every lane has read its points (the shuffles joined the warp): write back in place
+#pragma unroll
+    for (int j = 0; j < R; ++j) x[(__brev(lane + 32 * j) >> (32 - LOG)) * es] = v[j];
+    __syncwarp();
+}
+
 // order-preserving float -> uint32 (larger float -> larger key)
 __device__ __forceinline__ uint32_t float_to_ordered(float f) {
     uint32_t u = __float_as_uint(f);

@@ -10,68 +10,17 @@ constexpr int kThreads = 256;
 
 // FFT (unscaled) of `nlines` lines of N points held in shared memory: point i
 // of line l at buf[l * ls + i * es]; tw[k] = exp(SIGN 2 pi i k / N), k < N/2.
-// One warp per line.  N >= 64: the line is held in registers (lane l holds
-// points l + 32 j, j < N/32) and transformed by decimation in frequency: the
-// stages of span >= 32 pair registers of a lane, the five of span < 32 pair
-// lanes through shuffles; every twiddle a lane needs is loaded once per call;
-// the results go back in natural order (bit-reversed store addresses).
-// N < 64: radix-2 butterflies in shared memory.
+// One warp per line.  N >= 64: warp_fft_reg (registers and shuffles, each
+// lane's twiddles loaded once per call); N < 64: radix-2 butterflies in
+// shared memory.
 template <int N>
 __device__ void smem_fft_lines(float2 *buf, int nlines, int ls, int es, const float2 *tw) {
     constexpr int LOG = cx_log2(N);
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     if constexpr (N >= 64) {
-        constexpr int R = N / 32, LR = cx_log2(R);
-        // in-register stage s (span h = 32 h', h' = R >> (s+1)): the pair (j, j + h') of lane l takes
-        // tw[(l + 32 (j mod h')) << s]; cross-lane stage c (span 16 >> c) takes tw[(l mod span) << (LR + c)]
-        float2 wr[R > 1 ? R - 1 : 1];
-        {
-            int o = 0;
-#pragma unroll
-            for (int st = 0; st < LR; ++st) {
-                const int hp = R >> (st + 1);
-#pragma unroll
-                for (int jm = 0; jm < hp; ++jm) wr[o + jm] = tw[(lane + 32 * jm) << st];
-                o += hp;
-            }
-        }
-        float2 wc[5];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) wc[c] = tw[(lane & ((16 >> c) - 1)) << (LR + c)];
-        for (int l = threadIdx.x >> 5; l < nlines; l += nw) {
-            float2 *x = buf + l * ls;
-            float2 v[R];
-#pragma unroll
-            for (int j = 0; j < R; ++j) v[j] = x[(lane + 32 * j) * es];
-            int o = 0;
-#pragma unroll
-            for (int st = 0; st < LR; ++st) {
-                const int hp = R >> (st + 1);
-#pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    if (j & hp) continue;
-                    const float2 a = v[j], b = v[j + hp];
-                    v[j] = c_add(a, b);
-                    v[j + hp] = c_mul(c_sub(a, b), wr[o + (j & (hp - 1))]);
-                }
-                o += hp;
-            }
-#pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                const int h = 16 >> c;
-                const bool top = !(lane & h);
-#pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    const float2 p = make_float2(__shfl_xor_sync(0xffffffffu, v[j].x, h),
-                                                 __shfl_xor_sync(0xffffffffu, v[j].y, h));
-                    v[j] = top ? c_add(v[j], p) : c_mul(c_sub(p, v[j]), wc[c]);
-                }
-            }
-            // every lane has read its points (the shuffles above joined the warp): write back in place
-#pragma unroll
-            for (int j = 0; j < R; ++j) x[(__brev(lane + 32 * j) >> (32 - LOG)) * es] = v[j];
-            __syncwarp();
-        }
+        WarpFftTw<N> t;
+        t.load(tw, lane);
+        for (int l = threadIdx.x >> 5; l < nlines; l += nw) warp_fft_reg<N>(buf + l * ls, es, t, lane);
     } else {
         for (int l = threadIdx.x >> 5; l < nlines; l += nw) {
             float2 *x = buf + l * ls;
