@@ -104,11 +104,8 @@ __device__ void fft2_global(float2 *Z, float2 *sm, const float2 *tw) {
 
 template <int N>
 __device__ void make_tw(float2 *tw, int sign) {
-    for (int k = threadIdx.x; k < N / 2; k += blockDim.x) {
-        double s, c;
-        sincospi(2.0 * k / N, &s, &c);
-        tw[k] = make_float2((float)c, (float)(sign * s));
-    }
+    for (int k = threadIdx.x; k < N / 2; k += blockDim.x)
+        tw[k] = make_float2(kTwTable<N>.re[k], sign > 0 ? kTwTable<N>.im[k] : -kTwTable<N>.im[k]);
 }
 
 constexpr size_t smem_big(int N) { return sizeof(float2) * ((size_t)N * kColTile + N); }

@@ -54,6 +54,26 @@ struct Tw {
     static constexpr float im = (float)(SIGN * cx_taylor_sin(a));
 };
 
+// cos / sin of 2 pi k / N, k < N/2, as a table built at compile time (the
+// Taylor series above after exact range reduction: correctly rounded to
+// float), so that kernels fill their twiddle tables without FP64 work
+template <int N>
+struct TwTable {
+    float re[N / 2], im[N / 2];
+};
+template <int N>
+constexpr TwTable<N> make_tw_table() {
+    TwTable<N> t{};
+    for (int k = 0; k < N / 2; ++k) {
+        const double a = cx_angle(k, N);
+        t.re[k] = (float)cx_taylor_cos(a);
+        t.im[k] = (float)cx_taylor_sin(a);
+    }
+    return t;
+}
+template <int N>
+__device__ const TwTable<N> kTwTable = make_tw_table<N>();
+
 // x * exp(SIGN 2 pi i K / N) with the trivial cases written out
 template <long K, long N, int SIGN>
 __device__ __forceinline__ float2 tw_mul(float2 x) {

@@ -61,11 +61,8 @@ __device__ __forceinline__ void fft2_smem(float2 *buf, const float2 *tw) {
 
 template <int N>
 __device__ void make_twiddles(float2 *tw, int sign) {
-    for (int k = threadIdx.x; k < N / 2; k += blockDim.x) {
-        double s, c;
-        sincospi(2.0 * k / N, &s, &c);
-        tw[k] = make_float2((float)c, (float)(sign * s));
-    }
+    for (int k = threadIdx.x; k < N / 2; k += blockDim.x)
+        tw[k] = make_float2(kTwTable<N>.re[k], sign > 0 ? kTwTable<N>.im[k] : -kTwTable<N>.im[k]);
 }
 
 // sum over the block of one FP32 partial per thread: warp sums in FP32, the

@@ -113,23 +113,28 @@ __global__ void __launch_bounds__(256) k_project(const float *__restrict__ maste
     __shared__ float G[9];
     __shared__ float pc[3];
     if (threadIdx.x == 0) {
-        const Q q = qcanon(qload(quats + 4 * (size_t)p));
-        double R[9];
-        R[0] = 1 - 2 * (q.y * q.y + q.z * q.z); R[1] = 2 * (q.x * q.y - q.w * q.z); R[2] = 2 * (q.x * q.z + q.w * q.y);
-        R[3] = 2 * (q.x * q.y + q.w * q.z); R[4] = 1 - 2 * (q.x * q.x + q.z * q.z); R[5] = 2 * (q.y * q.z - q.w * q.x);
-        R[6] = 2 * (q.x * q.z - q.w * q.y); R[7] = 2 * (q.y * q.z + q.w * q.x); R[8] = 1 - 2 * (q.x * q.x + q.y * q.y);
-        const double sa = a.sa, ca = a.ca;
+        // the frame in FP32 (G is stored in FP32 anyway; FP64 here stalled the block on
+        // GB300's narrow FP64 pipe)
+        const double *qq = quats + 4 * (size_t)p;
+        float w = (float)qq[0], x = (float)qq[1], y = (float)qq[2], z = (float)qq[3];
+        const float inv = rsqrtf(w * w + x * x + y * y + z * z);
+        w *= inv; x *= inv; y *= inv; z *= inv;
+        float R[9];
+        R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+        R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+        R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+        const float sa = (float)a.sa, ca = (float)a.ca;
         // G = R(q) Rx(alpha): detector direction -> crystal direction
         for (int i = 0; i < 3; ++i) {
-            G[3 * i + 0] = (float)R[3 * i + 0];
-            G[3 * i + 1] = (float)(R[3 * i + 1] * ca + R[3 * i + 2] * sa);
-            G[3 * i + 2] = (float)(-R[3 * i + 1] * sa + R[3 * i + 2] * ca);
+            G[3 * i + 0] = R[3 * i + 0];
+            G[3 * i + 1] = R[3 * i + 1] * ca + R[3 * i + 2] * sa;
+            G[3 * i + 2] = -R[3 * i + 1] * sa + R[3 * i + 2] * ca;
         }
         double px = a.pcx, py = a.pcy, pz = a.pcz;
         if (pcs) { px = pcs[3 * (size_t)p]; py = pcs[3 * (size_t)p + 1]; pz = pcs[3 * (size_t)p + 2]; }
-        pc[0] = (float)(px * a.W);
-        pc[1] = (float)(py * a.H);
-        pc[2] = (float)(pz * a.W);
+        pc[0] = (float)px * (float)a.W;
+        pc[1] = (float)py * (float)a.H;
+        pc[2] = (float)pz * (float)a.W;
     }
     __syncthreads();
     const int npx = a.nx * a.ny;
