@@ -46,10 +46,14 @@ class Opts(C.Structure):
 
 def default_opts(n: int, **kw) -> Opts:
     """Defaults: Hann window, sigma_hp = 2, sigma_lp = n/4 cycles per image,
-    log-polar n/4 radii x 2n angles over r in [n/4, n/2 - 1] px in 4 radial
+    log-polar n/4 radii x (2n rounded up to a power of two) angles over
+    r in [n/4, n/2 - 1] px in 4 radial
     windows, NDP background sigma n/8 px (0 selects it; < 0 turns the
     correction off)."""
-    d = dict(window=1, sigma_hp=2.0, sigma_lp=n / 4.0, lp_nr=max(n // 4, 2), lp_neta=2 * n,
+    neta = 1
+    while neta < 2 * n:   # the angular sampling is a power of two (2n for 2^k sides)
+        neta *= 2
+    d = dict(window=1, sigma_hp=2.0, sigma_lp=n / 4.0, lp_nr=max(n // 4, 2), lp_neta=neta,
              lp_rmin=n / 4.0, lp_rmax=n / 2.0 - 1.0, upsample=0, interp=0, ndp_bg_sigma=0.0, lp_windows=4)
     d.update(kw)
     return Opts(**d)
@@ -73,6 +77,8 @@ def _lib_handle():
                 "orc_fft2": ([_D, C.c_int, C.c_int], None),
                 "orc_crop": ([C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                               _I, _I, _I, _D], C.c_int),
+                "orc_crop_ex": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                 _I, _I, _I, _D], C.c_int),
                 "orc_bandpass": ([C.c_int, C.c_int, C.c_int, C.c_double, C.c_double], C.c_double),
                 "orc_window": ([C.c_int, C.c_int, C.c_int], C.c_double),
                 "orc_prep": ([_D, C.c_int, C.POINTER(Opts), _D, _D], C.c_int),
@@ -195,12 +201,13 @@ def fft2(x, sign=-1):
 
 
 # ------------------------------------------------------------ pre-processing
-def crop(W, H, pc, cap=256):
-    """Centred 2^k crop: returns (n, off_x, off_y, pc_cropped)."""
+def crop(W, H, pc, cap=256, native=False):
+    """Centred crop (2^k sides, or with native=True also 96 and 160):
+    returns (n, off_x, off_y, pc_cropped)."""
     n, ox, oy = C.c_int32(), C.c_int32(), C.c_int32()
     out = np.zeros(3)
-    rc = _lib_handle().orc_crop(W, H, cap, pc[0], pc[1], pc[2], C.byref(n), C.byref(ox),
-                                C.byref(oy), _d(out))
+    rc = _lib_handle().orc_crop_ex(W, H, cap, int(native), pc[0], pc[1], pc[2], C.byref(n), C.byref(ox),
+                                   C.byref(oy), _d(out))
     if rc != 0:
         raise ValueError("detector too small")
     return n.value, ox.value, oy.value, out

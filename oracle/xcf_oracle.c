@@ -120,12 +120,26 @@ static void fft1_strided(cplx *x, int n, int st, int sign) {
     }
 }
 
-void orc_fft1(cplx *x, int n, int sign) { fft1_strided(x, n, 1, sign); }
+/* A line of any length: the radix-2 FFT for powers of two, the direct DFT
+ * (orc_dft1) otherwise (the 96- and 160-pixel native detectors). */
+static void line_transform(cplx *x, int n, int st, int sign) {
+    if ((n & (n - 1)) == 0) {
+        fft1_strided(x, n, st, sign);
+        return;
+    }
+    cplx *a = malloc(sizeof(cplx) * n), *b = malloc(sizeof(cplx) * n);
+    for (int i = 0; i < n; ++i) a[i] = x[(long)i * st];
+    orc_dft1(a, b, n, sign);
+    for (int i = 0; i < n; ++i) x[(long)i * st] = b[i];
+    free(a); free(b);
+}
 
-/* 2-D FFT of an n x n row-major array: rows, then columns.  Unscaled. */
+void orc_fft1(cplx *x, int n, int sign) { line_transform(x, n, 1, sign); }
+
+/* 2-D transform of an n x n row-major array: rows, then columns.  Unscaled. */
 void orc_fft2(cplx *x, int n, int sign) {
-    for (int r = 0; r < n; ++r) fft1_strided(x + (long)r * n, n, 1, sign);
-    for (int c = 0; c < n; ++c) fft1_strided(x + c, n, n, sign);
+    for (int r = 0; r < n; ++r) line_transform(x + (long)r * n, n, 1, sign);
+    for (int c = 0; c < n; ++c) line_transform(x + c, n, n, sign);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -138,11 +152,29 @@ void orc_fft2(cplx *x, int n, int sign) {
  * worked example 200 -> 128 px moves PCx 0.4 -> 0.34).  Outputs the square
  * side n, the crop offsets and the updated PC.  Returns 0, or -1 if the side
  * would be below 16. */
+int orc_crop_ex(int W, int H, int cap, int native, double pcx, double pcy, double pcz,
+                int *n_out, int *off_x, int *off_y, double pc_out[3]);
 int orc_crop(int W, int H, int cap, double pcx, double pcy, double pcz,
              int *n_out, int *off_x, int *off_y, double pc_out[3]) {
+    return orc_crop_ex(W, H, cap, 0, pcx, pcy, pcz, n_out, off_x, off_y, pc_out);
+}
+
+/* The crop with native sides (native != 0): the largest side of
+ * {16, 32, 64, 96, 128, 160, 256} that fits, so that 96- and 160-pixel
+ * detectors are used whole (the paper crops to 2^n only because its FFT and
+ * filters are easier there, footnote 1 of the FFT section). */
+int orc_crop_ex(int W, int H, int cap, int native, double pcx, double pcy, double pcz,
+                int *n_out, int *off_x, int *off_y, double pc_out[3]) {
+    static const int sides[7] = {16, 32, 64, 96, 128, 160, 256};
     int m = W < H ? W : H;
     int n = 1;
-    while (n * 2 <= m && n * 2 <= cap) n *= 2;
+    if (native) {
+        n = 0;
+        for (int i = 0; i < 7; ++i)
+            if (sides[i] <= m && sides[i] <= cap) n = sides[i];
+    } else {
+        while (n * 2 <= m && n * 2 <= cap) n *= 2;
+    }
     if (n < 16) return -1;
     int ox = (W - n) / 2, oy = (H - n) / 2;
     *n_out = n; *off_x = ox; *off_y = oy;
