@@ -53,7 +53,7 @@ typedef struct {
     double sigma_hp;    /* Gaussian high-pass sigma, cycles/image (default 2)       */
     double sigma_lp;    /* Gaussian low-pass sigma, cycles/image (auto: N/4)        */
     int32_t lp_nr;      /* log-polar radii (auto: N/4)                              */
-    int32_t lp_neta;    /* log-polar angles (auto: 2N)                              */
+    int32_t lp_neta;    /* log-polar angles, a power of two (auto: 2N rounded up)   */
     double lp_rmin;     /* smallest log-polar radius, px (auto: N/4)                */
     double lp_rmax;     /* largest log-polar radius, px (auto: N/2 - 1)             */
     int32_t max_iter;   /* refinement iterations (default 2, as in the paper)       */
@@ -77,6 +77,12 @@ typedef struct {
                             on its own, the rotation the median window shift (the
                             paper's "multiple windows"); 0 = 4 (default), 1 = the
                             whole image as one window                               */
+    int32_t native_sizes; /* crop rule: 0 = the largest 2^k square (default, the
+                             paper's practice); 1 = the largest of 16, 32, 64, 96,
+                             128, 160, 256 px, so that 96 and 160 px detectors are
+                             used whole (mixed-radix 3 x 32 and 5 x 32 transforms);
+                             a library keeps the rule of the context that built it.
+                             The NDP calls and the proposal network need 2^k sides */
 } xcf_options;
 
 /* Detector geometry of a map (or of a library). */
@@ -103,6 +109,13 @@ int xcf_options_default(xcf_options *opt);
  * only; XCF_ERR_SIZE if the side would be below 16. */
 int xcf_crop(const xcf_geometry *g, int32_t *n, int32_t *off_x, int32_t *off_y,
              double pc_out[3]);
+
+/* The same with the crop rule chosen: native = 0 is xcf_crop's 2^k rule, 1 the
+ * native rule of xcf_options.native_sizes (the largest of 16, 32, 64, 96, 128,
+ * 160, 256 px that fits).  A caller sizing xcf_prep's outputs on a context
+ * with native_sizes = 1 takes n from here.  XCF_ERR_ARG if native is not 0/1. */
+int xcf_crop_ex(const xcf_geometry *g, int32_t native, int32_t *n, int32_t *off_x,
+                int32_t *off_y, double pc_out[3]);
 
 /* Create a context on CUDA device `device` (the device is made current for
  * the call).  opt may be NULL (defaults).  Allocates nothing yet. */

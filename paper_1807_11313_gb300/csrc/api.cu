@@ -104,11 +104,20 @@ struct Crop {
     double pc[3];
 };
 
-int crop_of(const xcf_geometry *g, int cap, Crop *c) {
+// centred square crop: the largest 2^k side (native: the largest of 16, 32,
+// 64, 96, 128, 160, 256) that fits the detector and cap, PC updated
+int crop_of(const xcf_geometry *g, int cap, Crop *c, bool native = false) {
     if (!g || g->width <= 0 || g->height <= 0) return XCF_ERR_ARG;
     int m = g->width < g->height ? g->width : g->height;
     int n = 1;
-    while (n * 2 <= m && n * 2 <= cap) n *= 2;
+    if (native) {
+        static const int sides[7] = {16, 32, 64, 96, 128, 160, 256};
+        n = 0;
+        for (int i = 0; i < 7; ++i)
+            if (sides[i] <= m && sides[i] <= cap) n = sides[i];
+    } else {
+        while (n * 2 <= m && n * 2 <= cap) n *= 2;
+    }
     if (n < 16) return XCF_ERR_SIZE;
     c->n = n;
     c->ox = (g->width - n) / 2;
@@ -137,7 +146,10 @@ Resolved resolve(const xcf_options &o, int n) {
     r.sigma_hp = o.sigma_hp > 0 ? o.sigma_hp : 2.0;
     r.sigma_lp = o.sigma_lp > 0 ? o.sigma_lp : n / 4.0;
     r.nr = o.lp_nr > 0 ? o.lp_nr : (n / 4 > 2 ? n / 4 : 2);
-    r.neta = o.lp_neta > 0 ? o.lp_neta : 2 * n;
+    r.neta = o.lp_neta;
+    if (r.neta <= 0)   // 2N, rounded up to a power of two for the native 96 / 160 sides
+        for (r.neta = 1; r.neta < 2 * n; r.neta *= 2) {
+        }
     r.rmin = o.lp_rmin > 0 ? o.lp_rmin : n / 4.0;
     r.rmax = o.lp_rmax > 0 ? o.lp_rmax : n / 2.0 - 1.0;
     r.windows = o.lp_windows > 0 ? o.lp_windows : 4;
@@ -156,6 +168,7 @@ float ndp_sigma(const xcf_options &o, int n) {
 // corrected) crops of P images -> out32 / out16 (NDP operands)
 int ndp_operands(xcf_ctx *ctx, const float *img, int P, long img_stride, int row_stride, int ox, int oy, int n,
                  float *out32, void *out16, int *degen, cudaStream_t st) {
+    if (n & (n - 1)) return fail(ctx, XCF_ERR_UNIMPLEMENTED, "the NDP needs a 2^k detector side");
     const float sg = ndp_sigma(ctx->opt, n);
     if (sg > 0.f) {
         float *tmp, *cor;
@@ -219,7 +232,9 @@ PrepArgs prep_args_square(const Crop &c, const Resolved &r) {
     return a;
 }
 
-bool supported_n(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
+bool supported_n(int n) {
+    return n == 16 || n == 32 || n == 64 || n == 96 || n == 128 || n == 160 || n == 256;
+}
 
 // N = 256 kernels: persistent grid and its per-CTA work arrays (context scratch)
 cudaError_t big_work(xcf_ctx *ctx, int n, long items, float2 **work, int *grid) {
@@ -232,13 +247,13 @@ cudaError_t big_work(xcf_ctx *ctx, int n, long items, float2 **work, int *grid) 
 // global work-array kernels for N = 256
 cudaError_t run_prep(xcf_ctx *ctx, const float *img, int P, const PrepArgs &a, float2 *spec, float *spatial,
                      int *degen, const int *active, cudaStream_t st) {
-    if (a.N <= 128) return launch_prep(img, P, a, spec, spatial, degen, active, st);
+    if (a.N != 256) return launch_prep(img, P, a, spec, spatial, degen, active, st);
     return launch_prep_c256(img, P, a, spec, spatial, degen, active, st);
 }
 
 cudaError_t run_search(xcf_ctx *ctx, int n, const float2 *St, int T, const float2 *Sp, const int *degen, int P,
                        unsigned long long *keys, float *peaks_all, int num_sms, cudaStream_t st) {
-    if (n <= 128) return launch_search(n, St, T, Sp, degen, P, keys, peaks_all, num_sms, st);
+    if (n != 256) return launch_search(n, St, T, Sp, degen, P, keys, peaks_all, num_sms, st);
     return launch_search_c256(St, T, Sp, degen, P, keys, peaks_all, nullptr, 0, st);
 }
 
@@ -248,7 +263,7 @@ cudaError_t run_pair_peak(xcf_ctx *ctx, int n, const float2 *St, const int *tidx
     const int U = ctx->opt.upsample;
     int *argmax = nullptr;
     if (U >= 2 && P > 0 && scratch_t(ctx, S_ARGMAX, P, &argmax)) return cudaErrorMemoryAllocation;
-    cudaError_t e = n <= 128 ? launch_pair_peak(n, St, tidx, Sp, degen, active, P, peak, shift, st, argmax)
+    cudaError_t e = n != 256 ? launch_pair_peak(n, St, tidx, Sp, degen, active, P, peak, shift, st, argmax)
                              : launch_pair_peak_c256(St, tidx, Sp, degen, active, P, peak, shift, st, argmax);
     if (e != cudaSuccess || U < 2) return e;
     return launch_upsample_peak(n, St, tidx, Sp, degen, active, P, U, argmax, peak, shift, st);
@@ -272,7 +287,7 @@ int index_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int
                 float *peak, float *shift, float *peaks_all, cudaStream_t st, const int *only = nullptr) {
     const xcf_geometry *g = &lib->geom;
     Crop c;
-    crop_of(g, 256, &c);
+    crop_of(g, 256, &c, lib->native);
     const Resolved r = resolve(ctx->opt, c.n);
     const int H = c.n * (c.n / 2 + 1);
     float2 *sp;
@@ -309,7 +324,7 @@ int refine_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, in
                  cudaStream_t st, const int *select = nullptr, bool patterns_ready = false) {
     const xcf_geometry *g = &lib->geom;
     Crop c;
-    crop_of(g, 256, &c);
+    crop_of(g, 256, &c, lib->native);
     const Resolved r = resolve(ctx->opt, c.n);
     const int n = c.n, H = n * (n / 2 + 1), L = r.nr * r.neta;
     float2 *sp, *stt;
@@ -398,12 +413,19 @@ int xcf_options_default(xcf_options *o) {
     o->master_interp = 0;
     o->ndp_bg_sigma = 0.0;
     o->lp_windows = 0;
+    o->native_sizes = 0;
     return XCF_OK;
 }
 
 int xcf_crop(const xcf_geometry *g, int32_t *n, int32_t *off_x, int32_t *off_y, double pc_out[3]) {
+    return xcf_crop_ex(g, 0, n, off_x, off_y, pc_out);
+}
+
+int xcf_crop_ex(const xcf_geometry *g, int32_t native, int32_t *n, int32_t *off_x, int32_t *off_y,
+                double pc_out[3]) {
+    if (native != 0 && native != 1) return XCF_ERR_ARG;
     Crop c;
-    int rc = crop_of(g, 256, &c);
+    int rc = crop_of(g, 256, &c, native != 0);
     if (rc) return rc;
     if (n) *n = c.n;
     if (off_x) *off_x = c.ox;
@@ -423,6 +445,7 @@ int xcf_create(xcf_ctx **out, const xcf_options *opt, int device) {
         if (o.master_interp < 0 || o.master_interp > 1) return XCF_ERR_ARG;
         if (!(o.ndp_bg_sigma == o.ndp_bg_sigma)) return XCF_ERR_ARG;   // NaN
         if (o.lp_windows < 0 || o.lp_windows > 16) return XCF_ERR_ARG;
+        if (o.native_sizes < 0 || o.native_sizes > 1) return XCF_ERR_ARG;
     } else {
         xcf_options_default(&o);
     }
@@ -493,7 +516,7 @@ int xcf_prep(xcf_ctx *ctx, const float *images, int32_t P, const xcf_geometry *g
     if (P == 0) return XCF_OK;
     if (!images || !spectra) return fail(ctx, XCF_ERR_ARG, "xcf_prep: bad argument");
     Crop c;
-    int rc = crop_of(g, 256, &c);
+    int rc = crop_of(g, 256, &c, ctx->opt.native_sizes != 0);
     if (rc) return fail(ctx, rc, "xcf_prep: detector too small");
     if (!supported_n(c.n)) return fail(ctx, XCF_ERR_UNIMPLEMENTED, "xcf_prep: detector side not supported");
     cudaSetDevice(ctx->device);
@@ -536,7 +559,7 @@ int build_from_master(xcf_ctx *ctx, const float *master, int32_t M, const double
         return fail(ctx, XCF_ERR_ARG, "xcf_build_library: bad argument");
     *out = nullptr;
     Crop c;
-    int rc = crop_of(g, 256, &c);
+    int rc = crop_of(g, 256, &c, ctx->opt.native_sizes != 0);
     if (rc) return fail(ctx, rc, "xcf_build_library: detector too small");
     if (!supported_n(c.n)) return fail(ctx, XCF_ERR_UNIMPLEMENTED, "xcf_build_library: detector side not supported");
     cudaSetDevice(ctx->device);
@@ -546,6 +569,7 @@ int build_from_master(xcf_ctx *ctx, const float *master, int32_t M, const double
     lib->device = ctx->device;
     lib->T = T;
     lib->N = c.n;
+    lib->native = ctx->opt.native_sizes != 0;
     lib->M = M;
     lib->geom = *g;
     lib->ox = c.ox;
@@ -601,7 +625,7 @@ int build_from_images(xcf_ctx *ctx, const float *images, const double *quats, in
         return fail(ctx, XCF_ERR_ARG, "xcf_build_library_images: bad argument");
     *out = nullptr;
     Crop c;
-    int rc = crop_of(g, 256, &c);
+    int rc = crop_of(g, 256, &c, ctx->opt.native_sizes != 0);
     if (rc) return fail(ctx, rc, "xcf_build_library_images: detector too small");
     if (!supported_n(c.n)) return fail(ctx, XCF_ERR_UNIMPLEMENTED, "xcf_build_library_images: detector side not supported");
     cudaSetDevice(ctx->device);
@@ -611,6 +635,7 @@ int build_from_images(xcf_ctx *ctx, const float *images, const double *quats, in
     lib->device = ctx->device;
     lib->T = T;
     lib->N = c.n;
+    lib->native = ctx->opt.native_sizes != 0;
     lib->M = master ? M : 0;
     lib->geom = *g;
     lib->ox = c.ox;
@@ -914,7 +939,7 @@ int screen_chunk(int n, int T) {
 int make_screen_images(xcf_ctx *ctx, xcf_library *lib, const float *images, cudaStream_t st) {
     const xcf_geometry *g = &lib->geom;
     Crop c;
-    crop_of(g, 256, &c);
+    crop_of(g, 256, &c, lib->native);
     const Resolved r = resolve(ctx->opt, c.n);
     const size_t nn = (size_t)c.n * c.n, H = (size_t)c.n * (c.n / 2 + 1);
     if (cudaMalloc(&lib->bf16, 2 * nn * lib->T) != cudaSuccess) {
@@ -957,7 +982,7 @@ int make_screen_images(xcf_ctx *ctx, xcf_library *lib, const float *images, cuda
 int make_ndp_images(xcf_ctx *ctx, xcf_library *lib, const float *images, cudaStream_t st) {
     const xcf_geometry *g = &lib->geom;
     Crop c;
-    crop_of(g, 256, &c);
+    crop_of(g, 256, &c, lib->native);
     const size_t nn = (size_t)c.n * c.n;
     void *mem = nullptr;
     if (cudaMalloc(&mem, 6 * nn * lib->T) != cudaSuccess) {
@@ -1025,7 +1050,7 @@ int xcf_screen_topk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns,
     cudaStream_t st = (cudaStream_t)stream;
     const xcf_geometry *g = &lib->geom;
     Crop c;
-    crop_of(g, 256, &c);
+    crop_of(g, 256, &c, lib->native);
     const Resolved r = resolve(ctx->opt, c.n);
     const size_t nn = (size_t)c.n * c.n, H = (size_t)c.n * (c.n / 2 + 1), img = (size_t)g->width * g->height;
     if ((size_t)lib->T * 4 > 200 * 1024) return fail(ctx, XCF_ERR_SIZE, "xcf_screen_topk: more than 51,200 templates");
@@ -1069,7 +1094,7 @@ int xcf_rescore(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int
     cudaStream_t st = (cudaStream_t)stream;
     const xcf_geometry *g = &lib->geom;
     Crop c;
-    crop_of(g, 256, &c);
+    crop_of(g, 256, &c, lib->native);
     const Resolved r = resolve(ctx->opt, c.n);
     const size_t H = (size_t)c.n * (c.n / 2 + 1), img = (size_t)g->width * g->height;
     for (int p0 = 0; p0 < P; p0 += kChunk) {
@@ -1085,7 +1110,7 @@ int xcf_rescore(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int
                    run_prep(ctx, patterns + img * p0, np, prep_args(g, c, r), sp, nullptr, degen, nullptr, st),
                    "prep");
         XCF_CHECK(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * np, st), "memset keys");
-        if (c.n <= 128) {
+        if (c.n != 256) {
             XCF_LAUNCH(XCF_STAGE_SEARCH, st,
                        launch_search_list(c.n, lib->spectra, cp, k, sp, degen, np, keys, nullptr, ctx->num_sms, st),
                        "rescore");
@@ -1116,7 +1141,7 @@ int xcf_index_precision(xcf_ctx *ctx, const xcf_library *lib, const float *patte
     cudaStream_t st = (cudaStream_t)stream;
     const xcf_geometry *g = &lib->geom;
     Crop c;
-    crop_of(g, 256, &c);
+    crop_of(g, 256, &c, lib->native);
     const Resolved r = resolve(ctx->opt, c.n);
     const size_t nn = (size_t)c.n * c.n, H = (size_t)c.n * (c.n / 2 + 1), img = (size_t)g->width * g->height;
     if ((size_t)lib->T * 4 > 200 * 1024)
@@ -1148,7 +1173,7 @@ int xcf_index_precision(xcf_ctx *ctx, const xcf_library *lib, const float *patte
         XCF_LAUNCH(XCF_STAGE_SCREEN, st, launch_screen_tc(a, np, lib->bf16, lib->T, (int)nn, S, err, st), "screen");
         XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_topk_rows(S, np, lib->T, k, cand, score, st), "topk");
         XCF_CHECK(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * np, st), "memset keys");
-        if (c.n <= 128) {
+        if (c.n != 256) {
             XCF_LAUNCH(XCF_STAGE_SEARCH, st,
                        launch_search_list(c.n, lib->spectra, cand, k, spec, degen, np, keys, nullptr, ctx->num_sms,
                                           st),
@@ -1184,7 +1209,7 @@ int xcf_index_ndp(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, i
     cudaStream_t st = (cudaStream_t)stream;
     const xcf_geometry *g = &lib->geom;
     Crop c;
-    crop_of(g, 256, &c);
+    crop_of(g, 256, &c, lib->native);
     const size_t nn = (size_t)c.n * c.n, img = (size_t)g->width * g->height;
     const int chunk = screen_chunk(c.n, lib->T);
     int *err;
@@ -1228,7 +1253,7 @@ int xcf_rotation_scan(xcf_ctx *ctx, const float *master, int32_t M, const xcf_ge
     if (!master || !g || !q || !ndp || !xcf || M < 2 || h < 1 || h > 2048 || !(step_deg > 0.0))
         return fail(ctx, XCF_ERR_ARG, "xcf_rotation_scan: bad argument (1 <= h <= 2048, step_deg > 0)");
     Crop c;
-    int rc = crop_of(g, 256, &c);
+    int rc = crop_of(g, 256, &c, ctx->opt.native_sizes != 0);
     if (rc) return fail(ctx, rc, "xcf_rotation_scan: detector too small");
     if (!supported_n(c.n)) return fail(ctx, XCF_ERR_UNIMPLEMENTED, "xcf_rotation_scan: detector side not supported");
     cudaSetDevice(ctx->device);
@@ -1623,7 +1648,7 @@ int xcf_index_learned(xcf_ctx *ctx, xcf_net *net, const xcf_library *lib, const 
     cudaStream_t st = (cudaStream_t)stream;
     const xcf_geometry *g = &lib->geom;
     Crop c;
-    crop_of(g, 256, &c);
+    crop_of(g, 256, &c, lib->native);
     const Resolved r = resolve(ctx->opt, c.n);
     const int n = c.n, H = n * (n / 2 + 1), k = net->k;
     const size_t img = (size_t)g->width * g->height;
@@ -1786,7 +1811,7 @@ int maps_prep(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout &L,
     for (int m = 0; m < n; ++m) {
         const xcf_library *lib = maps[m].lib;
         Crop c;
-        crop_of(&lib->geom, 256, &c);
+        crop_of(&lib->geom, 256, &c, lib->native);
         XCF_LAUNCH(XCF_STAGE_PREP, st,
                    run_prep(ctx, maps[m].patterns, maps[m].P, prep_args(&lib->geom, c, resolve(ctx->opt, c.n)),
                             d.spec + L.spec[m], nullptr, d.degen + L.idx[m], nullptr, st),

@@ -140,51 +140,91 @@ __device__ __forceinline__ void fft_reg_dif(float2 (&x)[R]) {
 }
 
 // ---------------------------------------------------- warp line FFT (N >= 64)
-// One line of N points in shared memory (point i at x[i * es]) transformed
-// by one warp in registers: lane l holds points l + 32 j (j < N/32);
-// decimation in frequency, the stages of span >= 32 pairing registers of a
-// lane and the five of span < 32 pairing lanes through shuffles; the results
-// go back in natural order (bit-reversed store addresses).  tw[k] = exp(SIGN
-// 2 pi i k / N), k < N/2; WarpFftTw holds the twiddles one lane needs, so that
-// a warp transforming several lines loads them once.
+// One line of N = R x 32 points in shared memory (point i at x[i * es]),
+// transformed by one warp in registers: lane l holds points l + 32 j
+// (j < R).  R a power of two: decimation in frequency, the stages of span
+// >= 32 pairing registers of a lane, the five of span < 32 pairing lanes
+// through shuffles.  R = 3 or 5 (96- and 160-point lines): an R-point DFT
+// over a lane's registers, the twiddles W_N^(l k1), then the same five
+// shuffle stages for the 32-point DFT across lanes (Cooley-Tukey with N1 = R,
+// N2 = 32).  The results go back in natural order (reversed-digit store
+// addresses).  tw[k] = exp(SIGN 2 pi i k / N), k < N/2 (W^(k + N/2) = -W^k);
+// WarpFftTw holds the twiddles one lane needs, so that a warp transforming
+// several lines loads them once.
+template <int N>
+__device__ __forceinline__ float2 tw_any(const float2 *tw, int m) {   // W_N^m for 0 <= m < N
+    const float2 w = tw[m < N / 2 ? m : m - N / 2];
+    return m < N / 2 ? w : make_float2(-w.x, -w.y);
+}
+
 template <int N>
 struct WarpFftTw {
-    static constexpr int R = N / 32, LR = cx_log2(R);
-    float2 wr[R > 1 ? R - 1 : 1];   // register stage st (span 32 h', h' = R >> (st+1)), pair (j, j + h')
+    static constexpr int R = N / 32;
+    static constexpr bool P2 = (R & (R - 1)) == 0;
+    static constexpr int LR = P2 ? cx_log2(R) : 0;
+    float2 wr[R > 1 ? R - 1 : 1];   // 2^k: register stage st (span 32 h'), pair (j, j + h'); else W_N^(l k1)
+    float2 cr[P2 ? 1 : R - 1];      // R = 3, 5: W_R^m, m = 1 .. R-1
     float2 wc[5];                   // lane stage c (span 16 >> c)
     __device__ __forceinline__ void load(const float2 *tw, int lane) {
-        int o = 0;
+        if constexpr (P2) {
+            int o = 0;
 #pragma unroll
-        for (int st = 0; st < LR; ++st) {
-            const int hp = R >> (st + 1);
+            for (int st = 0; st < LR; ++st) {
+                const int hp = R >> (st + 1);
 #pragma unroll
-            for (int jm = 0; jm < hp; ++jm) wr[o + jm] = tw[(lane + 32 * jm) << st];
-            o += hp;
+                for (int jm = 0; jm < hp; ++jm) wr[o + jm] = tw[(lane + 32 * jm) << st];
+                o += hp;
+            }
+#pragma unroll
+            for (int c = 0; c < 5; ++c) wc[c] = tw[(lane & ((16 >> c) - 1)) << (LR + c)];
+        } else {
+#pragma unroll
+            for (int k1 = 1; k1 < R; ++k1) wr[k1 - 1] = tw_any<N>(tw, lane * k1);
+#pragma unroll
+            for (int m = 1; m < R; ++m) cr[m - 1] = tw_any<N>(tw, 32 * m);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) wc[c] = tw_any<N>(tw, R * ((lane & ((16 >> c) - 1)) << c));
         }
-#pragma unroll
-        for (int c = 0; c < 5; ++c) wc[c] = tw[(lane & ((16 >> c) - 1)) << (LR + c)];
     }
 };
 
 template <int N>
 __device__ __forceinline__ void warp_fft_reg(float2 *x, int es, const WarpFftTw<N> &t, int lane) {
-    constexpr int R = N / 32, LR = cx_log2(R), LOG = cx_log2(N);
-    static_assert(N >= 64, "register line FFT needs at least two points per lane");
+    constexpr int R = N / 32;
+    constexpr bool P2 = WarpFftTw<N>::P2;
+    static_assert(N >= 64 && N % 32 == 0 && (P2 || R == 3 || R == 5), "line length R x 32, R = 2^k, 3 or 5");
     float2 v[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) v[j] = x[(lane + 32 * j) * es];
-    int o = 0;
+    if constexpr (P2) {
+        constexpr int LR = cx_log2(R);
+        int o = 0;
 #pragma unroll
-    for (int st = 0; st < LR; ++st) {
-        const int hp = R >> (st + 1);
+        for (int st = 0; st < LR; ++st) {
+            const int hp = R >> (st + 1);
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
-            if (j & hp) continue;
-            const float2 a = v[j], b = v[j + hp];
-            v[j] = c_add(a, b);
-            v[j + hp] = c_mul(c_sub(a, b), t.wr[o + (j & (hp - 1))]);
+            for (int j = 0; j < R; ++j) {
+                if (j & hp) continue;
+                const float2 a = v[j], b = v[j + hp];
+                v[j] = c_add(a, b);
+                v[j + hp] = c_mul(c_sub(a, b), t.wr[o + (j & (hp - 1))]);
+            }
+            o += hp;
         }
-        o += hp;
+    } else {
+        float2 y[R];
+#pragma unroll
+        for (int k1 = 0; k1 < R; ++k1) {
+            y[k1] = v[0];
+#pragma unroll
+            for (int j = 1; j < R; ++j) {
+                const int m = (j * k1) % R;
+                y[k1] = c_add(y[k1], m == 0 ? v[j] : c_mul(v[j], t.cr[m - 1]));
+            }
+        }
+        v[0] = y[0];
+#pragma unroll
+        for (int k1 = 1; k1 < R; ++k1) v[k1] = c_mul(y[k1], t.wr[k1 - 1]);
     }
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
@@ -198,8 +238,15 @@ __device__ __forceinline__ void warp_fft_reg(float2 *x, int es, const WarpFftTw<
         }
     }
     // every lane has read its points (the shuffles joined the warp): write back in place
+    if constexpr (P2) {
+        constexpr int LOG = cx_log2(N);
 #pragma unroll
-    for (int j = 0; j < R; ++j) x[(__brev(lane + 32 * j) >> (32 - LOG)) * es] = v[j];
+        for (int j = 0; j < R; ++j) x[(__brev(lane + 32 * j) >> (32 - LOG)) * es] = v[j];
+    } else {
+        const int k2 = __brev(lane) >> 27;   // the 32-point transform leaves lane order bit-reversed
+#pragma unroll
+        for (int k1 = 0; k1 < R; ++k1) x[(k1 + R * k2) * es] = v[k1];
+    }
     __syncwarp();
 }
 

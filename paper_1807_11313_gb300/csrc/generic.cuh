@@ -10,14 +10,14 @@ constexpr int kThreads = 256;
 
 // FFT (unscaled) of `nlines` lines of N points held in shared memory: point i
 // of line l at buf[l * ls + i * es]; tw[k] = exp(SIGN 2 pi i k / N), k < N/2.
-// One warp per line.  N >= 64: warp_fft_reg (registers and shuffles, each
-// lane's twiddles loaded once per call); N < 64: radix-2 butterflies in
-// shared memory.
+// One warp per line.  N >= 64 (R x 32 with R = 2^k, 3 or 5): warp_fft_reg
+// (registers and shuffles, each lane's twiddles loaded once per call);
+// N < 64: radix-2 butterflies in shared memory.
 template <int N>
 __device__ void smem_fft_lines(float2 *buf, int nlines, int ls, int es, const float2 *tw) {
     constexpr int LOG = cx_log2(N);
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if constexpr (N >= 64) {
+    if constexpr (N >= 64) {   // N = R x 32 (R = 2^k, 3 or 5)
         WarpFftTw<N> t;
         t.load(tw, lane);
         for (int l = threadIdx.x >> 5; l < nlines; l += nw) warp_fft_reg<N>(buf + l * ls, es, t, lane);
@@ -118,7 +118,7 @@ __device__ __forceinline__ void build_pair_spectrum(float2 *buf, const float2 *_
             float2 x1 = c_mulcj(t1[k], s), x2 = c_mulcj(t2[k], s);
             Z = make_float2(x1.x - x2.y, x1.y + x2.x);
         } else {
-            int k = ((N - r) & (N - 1)) * HW + (N - c);
+            int k = ((N - r) % N) * HW + (N - c);
             float2 s = sp[k];
             float2 x1 = c_mulcj(t1[k], s), x2 = c_mulcj(t2[k], s);
             Z = make_float2(x1.x + x2.y, -x1.y + x2.x);

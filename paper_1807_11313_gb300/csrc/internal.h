@@ -99,6 +99,7 @@ struct xcf_library {
     uint64_t id = next_library_id();   // unique per library made in this process
     int device = 0;
     int T = 0, N = 0, M = 0;
+    bool native = false;               // crop rule of the context that built it (native 96 / 160 sides)
     xcf_geometry geom{};
     int ox = 0, oy = 0;
     double pc[3] = {0, 0, 0};

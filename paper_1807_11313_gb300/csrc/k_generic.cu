@@ -247,6 +247,156 @@ __global__ void __launch_bounds__(PT) k_prep_real(const float *__restrict__ img,
     }
 }
 
+// --------------------------------------------------------------------------
+// pre-processing of two images per CTA for the native 96 x 96 and 160 x 160
+// sides: image A in the real and image B in the imaginary part of one complex
+// N x N array in shared memory (rows padded to N + 1), one complex 2-D
+// transform (mixed-radix register line FFTs), then the two spectra split by
+// Hermitian symmetry, X_A = (Z(k) + conj Z(-k)) / 2, X_B = (Z(k) - conj
+// Z(-k)) / 2i.  In place, X_A(u, v) stays at (u, v) and X_B(u, v) moves to the
+// mirror (-u, -v) for 0 < v < N/2 (one thread owns both cells); columns 0 and
+// N/2 (their mirrors lie in the same column) go to four separate columns.  The
+// spatial outputs come back together from Z' = X_A' + i X_B'.
+// --------------------------------------------------------------------------
+constexpr int kPrepCplxThreads = 512;
+template <int N>
+constexpr size_t smem_prep_cplx() {
+    return sizeof(float2) * ((size_t)N * (N + 1) + N + 4 * N);
+}
+
+template <int N>
+__global__ void __launch_bounds__(kPrepCplxThreads) k_prep_cplx(const float *__restrict__ img, int P, PrepArgs a,
+                                                                float2 *__restrict__ spec,
+                                                                float *__restrict__ spatial,
+                                                                int *__restrict__ degen,
+                                                                const int *__restrict__ active) {
+    constexpr int LD = N + 1, HW = N / 2 + 1, NT = kPrepCplxThreads, H2 = N / 2;
+    extern __shared__ float4 smem_raw[];
+    float2 *buf = reinterpret_cast<float2 *>(smem_raw);
+    float2 *twf = buf + N * LD, *twi = twf + N / 2;
+    float2 *cA0 = twi + N / 2, *cAH = cA0 + N, *cB0 = cAH + N, *cBH = cB0 + N;
+    __shared__ double red[33];
+    const int tid = threadIdx.x;
+    const int pa = 2 * blockIdx.x, pb = pa + 1;
+    const bool ha = pa < P && (!active || active[pa]);
+    const bool hb = pb < P && (!active || active[pb]);
+    if (!ha && !hb) return;   // uniform over the CTA
+    make_twiddles<N>(twf, -1);
+    make_twiddles<N>(twi, +1);
+    const size_t isz = (size_t)a.W * a.H, off = (size_t)a.oy * a.W + a.ox;
+    const float *sa = img + (size_t)(ha ? pa : pb) * isz + off, *sb = img + (size_t)(hb ? pb : pa) * isz + off;
+    // ---- load both crops; FP32 statistics of (x - x0), x0 each crop's first pixel
+    const float xa0 = ha ? __ldg(sa) : 0.f, xb0 = hb ? __ldg(sb) : 0.f;
+    float a1 = 0.f, a2 = 0.f, b1 = 0.f, b2 = 0.f;
+    for (int idx = tid; idx < N * N; idx += NT) {
+        const int r = idx / N, c = idx - r * N;
+        const float va = ha ? __ldg(sa + (size_t)r * a.W + c) : 0.f;
+        const float vb = hb ? __ldg(sb + (size_t)r * a.W + c) : 0.f;
+        buf[r * LD + c] = make_float2(va, vb);
+        const float da = va - xa0, db = vb - xb0;
+        a1 += da;
+        a2 = fmaf(da, da, a2);
+        b1 += db;
+        b2 = fmaf(db, db, b2);
+    }
+    const double A1 = block_sum_f(a1, red) / (N * N), A2 = block_sum_f(a2, red) / (N * N);
+    const double B1 = block_sum_f(b1, red) / (N * N), B2 = block_sum_f(b2, red) / (N * N);
+    const double meanA = xa0 + A1, varA = A2 - A1 * A1, sdA = varA > 0.0 ? sqrt(varA) : 0.0;
+    const double meanB = xb0 + B1, varB = B2 - B1 * B1, sdB = varB > 0.0 ? sqrt(varB) : 0.0;
+    bool badA = !ha || !(sdA > 1e-12 * (1.0 + fabs(meanA)));
+    bool badB = !hb || !(sdB > 1e-12 * (1.0 + fabs(meanB)));
+    // ---- standardise and window (a degenerate crop becomes zeros)
+    {
+        const float mA = (float)meanA, iA = badA ? 0.f : (float)(1.0 / sdA);
+        const float mB = (float)meanB, iB = badB ? 0.f : (float)(1.0 / sdB);
+        for (int idx = tid; idx < N * N; idx += NT) {
+            const int r = idx / N, c = idx - r * N;
+            const float w = a.window ? 0.25f * (1.f - cospif(2.f * r / N)) * (1.f - cospif(2.f * c / N)) : 1.f;
+            const float2 z = buf[r * LD + c];
+            buf[r * LD + c] = make_float2((z.x - mA) * iA * w, (z.y - mB) * iB * w);
+        }
+    }
+    __syncthreads();
+    smem_fft_lines<N>(buf, N, LD, 1, twf);   // rows
+    __syncthreads();
+    smem_fft_lines<N>(buf, N, 1, LD, twf);   // columns
+    __syncthreads();
+    auto filt = [&](int u, int v) {
+        const float fu = (float)(u < N / 2 ? u : u - N), fv = (float)(v < N / 2 ? v : v - N);
+        const float rho2 = fu * fu + fv * fv;
+        return -expm1f(-rho2 * a.inv2shp) * expf(-rho2 * a.inv2slp);
+    };
+    // ---- split, filter, energies (bins 1..N/2-1 stand for their mirrors too)
+    float eA = 0.f, eB = 0.f;
+    for (int it = tid; it < N * (H2 - 1); it += NT) {
+        const int u = it / (H2 - 1), v = 1 + it % (H2 - 1), um = (N - u) % N, vm = N - v;
+        const float2 z = buf[u * LD + v], zm = buf[um * LD + vm];
+        const float h = filt(u, v);
+        const float2 XA = make_float2(0.5f * h * (z.x + zm.x), 0.5f * h * (z.y - zm.y));
+        const float2 XB = make_float2(0.5f * h * (z.y + zm.y), 0.5f * h * (zm.x - z.x));
+        eA = fmaf(2.f, XA.x * XA.x + XA.y * XA.y, eA);
+        eB = fmaf(2.f, XB.x * XB.x + XB.y * XB.y, eB);
+        buf[u * LD + v] = XA;
+        buf[um * LD + vm] = XB;
+    }
+    for (int it = tid; it < 2 * N; it += NT) {   // columns 0 and N/2 (not touched by the loop above)
+        const int u = it % N, v = it < N ? 0 : H2, um = (N - u) % N;
+        const float2 z = buf[u * LD + v], zm = buf[um * LD + v];
+        const float h = filt(u, v);
+        const float2 XA = make_float2(0.5f * h * (z.x + zm.x), 0.5f * h * (z.y - zm.y));
+        const float2 XB = make_float2(0.5f * h * (z.y + zm.y), 0.5f * h * (zm.x - z.x));
+        eA += XA.x * XA.x + XA.y * XA.y;
+        eB += XB.x * XB.x + XB.y * XB.y;
+        (v ? cAH : cA0)[u] = XA;
+        (v ? cBH : cB0)[u] = XB;
+    }
+    const double EA = block_sum_f(eA, red), EB = block_sum_f(eB, red);   // its barriers order the writes above
+    badA = badA || !(EA > 0.0);
+    badB = badB || !(EB > 0.0);
+    if (tid == 0 && degen) {
+        if (ha) degen[pa] = badA ? 1 : 0;
+        if (hb) degen[pb] = badB ? 1 : 0;
+    }
+    const float sA = badA ? 0.f : (float)(1.0 / sqrt(EA)), sB = badB ? 0.f : (float)(1.0 / sqrt(EB));
+    float2 *oa = spec + (size_t)pa * N * HW, *ob = spec + (size_t)pb * N * HW;
+    for (int it = tid; it < N * HW; it += NT) {
+        const int u = it / HW, v = it - u * HW;
+        float2 XA, XB;
+        if (v == 0) { XA = cA0[u]; XB = cB0[u]; }
+        else if (v == H2) { XA = cAH[u]; XB = cBH[u]; }
+        else { XA = buf[u * LD + v]; XB = buf[((N - u) % N) * LD + N - v]; }
+        if (ha) oa[it] = make_float2(XA.x * sA, XA.y * sA);
+        if (hb) ob[it] = make_float2(XB.x * sB, XB.y * sB);
+    }
+    if (!spatial) return;
+    __syncthreads();
+    // ---- spatial images: Z' = sA X_A + i sB X_B over the full spectrum, one inverse transform
+    for (int it = tid; it < N * (H2 - 1); it += NT) {
+        const int u = it / (H2 - 1), v = 1 + it % (H2 - 1), um = (N - u) % N, vm = N - v;
+        const float2 XA = buf[u * LD + v], XB = buf[um * LD + vm];
+        // Z'(u, v) = sA XA + i sB XB; Z'(-u, -v) = sA conj XA + i sB conj XB
+        buf[u * LD + v] = make_float2(sA * XA.x - sB * XB.y, sA * XA.y + sB * XB.x);
+        buf[um * LD + vm] = make_float2(sA * XA.x + sB * XB.y, -sA * XA.y + sB * XB.x);
+    }
+    for (int it = tid; it < 2 * N; it += NT) {
+        const int u = it % N, v = it < N ? 0 : H2;
+        const float2 XA = (v ? cAH : cA0)[u], XB = (v ? cBH : cB0)[u];
+        buf[u * LD + v] = make_float2(sA * XA.x - sB * XB.y, sA * XA.y + sB * XB.x);
+    }
+    __syncthreads();
+    smem_fft_lines<N>(buf, N, LD, 1, twi);   // rows back
+    __syncthreads();
+    smem_fft_lines<N>(buf, N, 1, LD, twi);   // columns back
+    __syncthreads();
+    const float invn = 1.f / N;
+    for (int idx = tid; idx < N * N; idx += NT) {
+        const int r = idx / N, c = idx - r * N;
+        const float2 z = buf[r * LD + c];
+        if (ha) spatial[(size_t)pa * N * N + idx] = z.x * invn;
+        if (hb) spatial[(size_t)pb * N * N + idx] = z.y * invn;
+    }
+}
+
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_search_generic(const float2 *__restrict__ St, int T,
                                                              const float2 *__restrict__ Sp,
@@ -319,7 +469,7 @@ __global__ void __launch_bounds__(QT) k_pair_peak(const float2 *__restrict__ St,
     for (int idx = tid; idx < N * N; idx += QT) {
         const int r = idx / N, c = idx % N;
         const bool direct = c <= N / 2;
-        const int k = direct ? r * HW + c : ((N - r) & (N - 1)) * HW + (N - c);   // conj(X(-u, -v)) above N/2
+        const int k = direct ? r * HW + c : ((N - r) % N) * HW + (N - c);   // conj(X(-u, -v)) above N/2
         float2 x1 = c_mulcj(ta[k], qa[k]), x2 = c_mulcj(tb[k], qb[k]);
         x1 = make_float2(x1.x * fa, x1.y * fa);
         x2 = make_float2(x2.x * fb, x2.y * fb);
@@ -358,8 +508,8 @@ __global__ void __launch_bounds__(QT) k_pair_peak(const float2 *__restrict__ St,
             return s ? z.y : z.x;
         };
         const float c0 = at(y0, x0);
-        const float cxm = at(y0, (x0 + N - 1) & (N - 1)), cxp = at(y0, (x0 + 1) & (N - 1));
-        const float cym = at((y0 + N - 1) & (N - 1), x0), cyp = at((y0 + 1) & (N - 1), x0);
+        const float cxm = at(y0, (x0 + N - 1) % N), cxp = at(y0, (x0 + 1) % N);
+        const float cym = at((y0 + N - 1) % N, x0), cyp = at((y0 + 1) % N, x0);
         peak[p] = c0;
         shift[2 * p] = (float)(x0 < N / 2 ? x0 : x0 - N) + parabola(cxm, c0, cxp);
         shift[2 * p + 1] = (float)(y0 < N / 2 ? y0 : y0 - N) + parabola(cym, c0, cyp);
@@ -389,6 +539,16 @@ cudaError_t prep_n(const float *img, int P, const PrepArgs &a, float2 *spec, flo
     cudaError_t e = set_smem(k_prep_real<N>, sm);
     if (e != cudaSuccess) return e;
     k_prep_real<N><<<P, prep_threads<N>(), sm, st>>>(img, a, spec, spatial, degen, active);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t prep_cplx_n(const float *img, int P, const PrepArgs &a, float2 *spec, float *spatial, int *degen,
+                        const int *active, cudaStream_t st) {
+    const size_t sm = smem_prep_cplx<N>();
+    cudaError_t e = set_smem(k_prep_cplx<N>, sm);
+    if (e != cudaSuccess) return e;
+    k_prep_cplx<N><<<(P + 1) / 2, kPrepCplxThreads, sm, st>>>(img, P, a, spec, spatial, degen, active);
     return cudaGetLastError();
 }
 
@@ -434,6 +594,8 @@ cudaError_t launch_prep(const float *img, int P, const PrepArgs &a, float2 *spec
         case 32: return prep_n<32>(img, P, a, spec, spatial, degen, active, st);
         case 64: return prep_n<64>(img, P, a, spec, spatial, degen, active, st);
         case 128: return prep_n<128>(img, P, a, spec, spatial, degen, active, st);
+        case 96: return prep_cplx_n<96>(img, P, a, spec, spatial, degen, active, st);
+        case 160: return prep_cplx_n<160>(img, P, a, spec, spatial, degen, active, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -446,6 +608,8 @@ cudaError_t launch_search(int N, const float2 *St, int T, const float2 *Sp, cons
         case 32: return search_n<32>(St, T, Sp, degen, P, keys, peaks_all, num_sms, st);
         case 64: return search_n<64>(St, T, Sp, degen, P, keys, peaks_all, num_sms, st);
         case 128: return launch_search128(St, T, Sp, degen, P, keys, peaks_all, num_sms, st);
+        case 96: return search_n<96>(St, T, Sp, degen, P, keys, peaks_all, num_sms, st);
+        case 160: return search_n<160>(St, T, Sp, degen, P, keys, peaks_all, num_sms, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -465,6 +629,8 @@ cudaError_t launch_search_list(int N, const float2 *St, const int *cand, int kc,
         case 32: return search_n<32>(St, 0, Sp, degen, P, keys, peaks, num_sms, st, cand, kc);
         case 64: return search_n<64>(St, 0, Sp, degen, P, keys, peaks, num_sms, st, cand, kc);
         case 128: return search_n<128>(St, 0, Sp, degen, P, keys, peaks, num_sms, st, cand, kc);
+        case 96: return search_n<96>(St, 0, Sp, degen, P, keys, peaks, num_sms, st, cand, kc);
+        case 160: return search_n<160>(St, 0, Sp, degen, P, keys, peaks, num_sms, st, cand, kc);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -478,6 +644,8 @@ cudaError_t launch_pair_peak(int N, const float2 *St, const int *tidx, const flo
         case 32: return pair_peak_n<32>(St, tidx, Sp, degen, active, P, peak, shift, argmax, st);
         case 64: return pair_peak_n<64>(St, tidx, Sp, degen, active, P, peak, shift, argmax, st);
         case 128: return pair_peak_n<128>(St, tidx, Sp, degen, active, P, peak, shift, argmax, st);
+        case 96: return pair_peak_n<96>(St, tidx, Sp, degen, active, P, peak, shift, argmax, st);
+        case 160: return pair_peak_n<160>(St, tidx, Sp, degen, active, P, peak, shift, argmax, st);
         default: return cudaErrorInvalidValue;
     }
 }

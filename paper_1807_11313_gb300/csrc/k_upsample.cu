@@ -22,7 +22,7 @@ constexpr int kUpThreads = 256, kMaxU = 20, kMaxM = 2 * kMaxU + 1;
 
 // e^{+2 pi i (k0 / N + num / den)} with k0 an integer and num / den a small rational
 __device__ __forceinline__ float2 phase(int k0, int N, int num, int den) {
-    const float a = 2.f * (float)(k0 & (N - 1)) / N + 2.f * (float)num / (float)den;   // in units of pi
+    const float a = 2.f * (float)(((k0 % N) + N) % N) / N + 2.f * (float)num / (float)den;   // in units of pi
     float s, c;
     sincospif(a, &s, &c);
     return make_float2(c, s);
@@ -132,6 +132,8 @@ cudaError_t launch_upsample_peak(int N, const float2 *St, const int *tidx, const
         case 32: return upsample_n<32>(St, tidx, Sp, degen, active, P, U, argmax, peak, shift, st);
         case 64: return upsample_n<64>(St, tidx, Sp, degen, active, P, U, argmax, peak, shift, st);
         case 128: return upsample_n<128>(St, tidx, Sp, degen, active, P, U, argmax, peak, shift, st);
+        case 96: return upsample_n<96>(St, tidx, Sp, degen, active, P, U, argmax, peak, shift, st);
+        case 160: return upsample_n<160>(St, tidx, Sp, degen, active, P, U, argmax, peak, shift, st);
         case 256: return upsample_n<256>(St, tidx, Sp, degen, active, P, U, argmax, peak, shift, st);
         default: return cudaErrorInvalidValue;
     }

@@ -35,7 +35,7 @@ class xcf_options(C.Structure):
                 ("lp_nr", C.c_int32), ("lp_neta", C.c_int32), ("lp_rmin", C.c_double),
                 ("lp_rmax", C.c_double), ("max_iter", C.c_int32), ("tol_deg", C.c_double),
                 ("upsample", C.c_int32), ("master_interp", C.c_int32), ("ndp_bg_sigma", C.c_double),
-                ("lp_windows", C.c_int32)]
+                ("lp_windows", C.c_int32), ("native_sizes", C.c_int32)]
 
 
 class xcf_geometry(C.Structure):
@@ -64,6 +64,8 @@ _SIGS = {
     "xcf_options_default": ([C.POINTER(xcf_options)], C.c_int),
     "xcf_crop": ([C.POINTER(xcf_geometry), C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32),
                   C.POINTER(C.c_double)], C.c_int),
+    "xcf_crop_ex": ([C.POINTER(xcf_geometry), _I32, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32),
+                     C.POINTER(C.c_double)], C.c_int),
     "xcf_create": ([C.POINTER(_P), C.POINTER(xcf_options), C.c_int], C.c_int),
     "xcf_destroy": ([_P], C.c_int),
     "xcf_project": ([_P, _P, _I32, _P, _I32, C.POINTER(xcf_geometry), _P, _P, _P], C.c_int),
@@ -240,10 +242,10 @@ class Library:
 
 
 # ------------------------------------------------------------ entry points
-def xcf_crop(geom: xcf_geometry):
+def xcf_crop(geom: xcf_geometry, native: bool = False):
     n, ox, oy = _I32(), _I32(), _I32()
     pc = (C.c_double * 3)()
-    _check(load().xcf_crop(C.byref(geom), C.byref(n), C.byref(ox), C.byref(oy), pc))
+    _check(load().xcf_crop_ex(C.byref(geom), int(bool(native)), C.byref(n), C.byref(ox), C.byref(oy), pc))
     return n.value, ox.value, oy.value, tuple(pc)
 
 
@@ -260,7 +262,7 @@ def xcf_project(ctx: Context, master, quats, geom: xcf_geometry, pcs=None, out=N
 
 def xcf_prep(ctx: Context, images, geom: xcf_geometry, want_spatial=False):
     P = images.shape[0]
-    n = xcf_crop(geom)[0]
+    n = xcf_crop(geom, ctx.options.native_sizes)[0]
     spec = torch.empty((P, n, n // 2 + 1, 2), dtype=torch.float32, device=images.device)
     spat = torch.empty((P, n, n), dtype=torch.float32, device=images.device) if want_spatial else None
     degen = torch.empty(P, dtype=torch.int32, device=images.device)
