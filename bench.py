@@ -65,6 +65,8 @@ def parse():
                          "study of Fig. 2 (library generation and nearest-neighbour disorientations)")
     ap.add_argument("--patterns", type=int, default=0, help="precision form: patterns per GPU (0: 50,000)")
     ap.add_argument("--scale", type=float, default=1.0, help="batched form: scale of every map's pattern count")
+    ap.add_argument("--native", action="store_true",
+                    help="batched form: native crop rule (96 and 160 px detectors used whole, 200 -> 160)")
     ap.add_argument("--upsample", type=int, default=0,
                     help="plain form: 0 = 3-point parabolic peak; U in [2, 20] = up-sampled peak (grid step 1/U px)")
     ap.add_argument("--train", type=int, default=200000, help="learned form: training patterns")
@@ -559,7 +561,7 @@ def flops_per_pair(n: int) -> float:
 
 def run_batched(args, px, torch, dev, rank, world, local, dist):
     wl = synth.config_batched(seed=rank, scale=args.scale)
-    ctx = px.Context()
+    ctx = px.Context(native_sizes=int(args.native))
     master_d = torch.from_numpy(np.ascontiguousarray(wl["master"])).to(dev)
     gen = torch.Generator(device=dev)
     gen.manual_seed(wl["noise_seed"])
@@ -580,7 +582,7 @@ def run_batched(args, px, torch, dev, rank, world, local, dist):
         batch.append((lib, pats))
         truths.append(truth)
         libqs.append(libq)
-        n = px.xcf_crop(g)[0]
+        n = px.xcf_crop(g, native=args.native)[0]
         ns.append(n)
         flops += P * lib.T * flops_per_pair(n)   # every (pattern, template) pair
     P_all = sum(p.shape[0] for _, p in batch)
@@ -630,17 +632,36 @@ def run_batched(args, px, torch, dev, rank, world, local, dist):
     torch.cuda.synchronize()
     prof2 = px.xcf_profile_read(ctx, reset=True)
     px.xcf_profile_enable(ctx, False)
-    s_ms, s_n = prof2["search"]
-    per_launch_ms = s_ms / max(s_n, 1)
+    # one call launches the queue kernel (128 x 128 maps) and one search kernel
+    # per map of another side: the stage time per call covers all of them
+    search_ms_call = prof2["search"][0] / 2
+    # per-map search time through the per-map entry point (its own kernel per side)
+    by_side = {}
+    for (lib, pats), n in zip(batch, ns):
+        px.xcf_profile_enable(ctx, True)
+        px.xcf_index(ctx, lib, pats)
+        torch.cuda.synchronize()
+        ms_map = px.xcf_profile_read(ctx, reset=True)["search"][0]
+        px.xcf_profile_enable(ctx, False)
+        d = by_side.setdefault(str(n), {"ms": 0.0, "tflop": 0.0})
+        d["ms"] += ms_map
+        d["tflop"] += pats.shape[0] * lib.T * flops_per_pair(n) / 1e12
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     pk = peaks_file()
     sm_max = (pk or {}).get("sm_max_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
     fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
-    achieved = flops / (per_launch_ms / 1e3) / 1e12
+    for d in by_side.values():
+        d["achieved_tflops"] = d["tflop"] / (d["ms"] / 1e3)
+        d["frac"] = d["achieved_tflops"] / fp32_peak
+    achieved = flops / (search_ms_call / 1e3) / 1e12
+    kernels = {16: "k_search_generic", 32: "k_search_generic", 64: "k_search_generic", 96: "k_search_generic",
+               128: "k_search_maps", 160: "k_search_generic", 256: "k_search_c256"}
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None, "kernel": "k_search_maps",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "kernel": "search stage of one call: " + " + ".join(sorted({kernels[n] for n in ns})),
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
-                "search_ms_per_launch": per_launch_ms,
+                "search_ms_per_call": search_ms_call,
+                "by_side_per_map_calls": by_side,
                 "stage_ms_per_step_uncaptured": {k: v[0] / 2 for k, v in prof2.items()}}
     e2e = None
     if not args.no_e2e:
@@ -671,7 +692,9 @@ def run_batched(args, px, torch, dev, rank, world, local, dist):
                 "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": wl["name"], "form": "batched", "maps": len(batch),
+                "config": {"workload": wl["name"] + ("_native" if args.native else ""), "form": "batched",
+                           "crop_rule": "native (16..256 incl. 96, 160)" if args.native else "2^k",
+                           "maps": len(batch),
                            "detectors": [[m["W"], m["H"]] for m in wl["maps"]], "crop": ns,
                            "templates": [lib.T for lib, _ in batch], "patterns": [p.shape[0] for _, p in batch],
                            "graph": True, "libraries": "resident (built before the timed region)",

@@ -188,14 +188,13 @@ struct WarpFftTw {
     }
 };
 
+// The transform of warp_fft_reg on values already in registers: on entry
+// v[j] = point lane + 32 j; on exit v[j] holds output warp_fft_out<N>(lane, j).
 template <int N>
-__device__ __forceinline__ void warp_fft_reg(float2 *x, int es, const WarpFftTw<N> &t, int lane) {
+__device__ __forceinline__ void warp_fft_core(float2 (&v)[N / 32], const WarpFftTw<N> &t, int lane) {
     constexpr int R = N / 32;
     constexpr bool P2 = WarpFftTw<N>::P2;
     static_assert(N >= 64 && N % 32 == 0 && (P2 || R == 3 || R == 5), "line length R x 32, R = 2^k, 3 or 5");
-    float2 v[R];
-#pragma unroll
-    for (int j = 0; j < R; ++j) v[j] = x[(lane + 32 * j) * es];
     if constexpr (P2) {
         constexpr int LR = cx_log2(R);
         int o = 0;
@@ -237,16 +236,29 @@ __device__ __forceinline__ void warp_fft_reg(float2 *x, int es, const WarpFftTw<
             v[j] = top ? c_add(v[j], p) : c_mul(c_sub(p, v[j]), t.wc[c]);
         }
     }
-    // every lane has read its points (the shuffles joined the warp): write back in place
-    if constexpr (P2) {
-        constexpr int LOG = cx_log2(N);
-#pragma unroll
-        for (int j = 0; j < R; ++j) x[(__brev(lane + 32 * j) >> (32 - LOG)) * es] = v[j];
+}
+
+// output index held in v[j] of `lane` after warp_fft_core
+template <int N>
+__device__ __forceinline__ int warp_fft_out(int lane, int j) {
+    constexpr int R = N / 32;
+    if constexpr (WarpFftTw<N>::P2) {
+        return __brev(lane + 32 * j) >> (32 - cx_log2(N));
     } else {
-        const int k2 = __brev(lane) >> 27;   // the 32-point transform leaves lane order bit-reversed
-#pragma unroll
-        for (int k1 = 0; k1 < R; ++k1) x[(k1 + R * k2) * es] = v[k1];
+        return j + R * (__brev(lane) >> 27);   // the 32-point transform leaves lane order bit-reversed
     }
+}
+
+template <int N>
+__device__ __forceinline__ void warp_fft_reg(float2 *x, int es, const WarpFftTw<N> &t, int lane) {
+    constexpr int R = N / 32;
+    float2 v[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) v[j] = x[(lane + 32 * j) * es];
+    warp_fft_core<N>(v, t, lane);
+    // every lane has read its points (the shuffles joined the warp): write back in place
+#pragma unroll
+    for (int j = 0; j < R; ++j) x[warp_fft_out<N>(lane, j) * es] = v[j];
     __syncwarp();
 }
 

@@ -127,13 +127,115 @@ __device__ __forceinline__ void build_pair_spectrum(float2 *buf, const float2 *_
     }
 }
 
+// Z = X1 + i X2 at the N/32 points c = lane + 32 j of row r (build_pair_spectrum
+// for one row, into registers).  The two halves of the row differ only in the
+// stored row they read and in signs, so both are loaded through one index.
+template <int N>
+__device__ __forceinline__ void pair_row(float2 (&v)[N / 32], int r, int lane, const float2 *__restrict__ t1,
+                                         const float2 *__restrict__ t2, const float2 *__restrict__ sp) {
+    constexpr int HW = N / 2 + 1;
+    const int rr = r == 0 ? 0 : N - r;
+#pragma unroll
+    for (int j = 0; j < N / 32; ++j) {
+        const int c = lane + 32 * j;
+        const bool lo = c <= N / 2;
+        const int k = lo ? r * HW + c : rr * HW + (N - c);
+        const float2 s = sp[k];
+        const float2 x1 = c_mulcj(t1[k], s), x2 = c_mulcj(t2[k], s);
+        v[j] = lo ? make_float2(x1.x - x2.y, x1.y + x2.x) : make_float2(x1.x + x2.y, x2.x - x1.y);
+    }
+}
+
+// search_body for N = R x 32 >= 64: per template pair, each warp builds its
+// rows of Z from the spectra straight into registers, transforms them
+// (warp_fft_core) and stores them once; after one barrier each warp loads its
+// columns, transforms them and keeps the running maxima of the real and
+// imaginary parts in registers (the surface is never written back); after a
+// second barrier thread 0 combines the warps' maxima.
+template <int N>
+__device__ void search_body_reg(const float2 *__restrict__ St, int T, const float2 *__restrict__ Sp, int p, int pb,
+                                int pe, unsigned long long *__restrict__ keys, float *__restrict__ peaks_all,
+                                const int *__restrict__ cand, int kc) {
+    constexpr int LD = N + 1, HW = N / 2 + 1, R = N / 32;
+    extern __shared__ float4 smem_raw[];
+    float2 *buf = reinterpret_cast<float2 *>(smem_raw);
+    float2 *twi = buf + N * LD;
+    __shared__ float2 red[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    make_twiddles<N>(twi, +1);
+    __syncthreads();
+    WarpFftTw<N> tw;
+    tw.load(twi, lane);
+    const float2 *sp = Sp + (size_t)p * N * HW;
+    const int n = cand ? kc : T;
+    float best_v = -INFINITY;
+    int best_t = -1;
+    for (int pi = pb; pi < pe; ++pi) {
+        const int j1 = 2 * pi, j2 = min(j1 + 1, n - 1);
+        const int t1 = cand ? cand[(size_t)p * kc + j1] : j1;
+        const int t2 = cand ? cand[(size_t)p * kc + j2] : j2;
+        const float2 *s1 = St + (size_t)max(t1, 0) * N * HW, *s2 = St + (size_t)max(t2, 0) * N * HW;
+        // rows (the previous pair's column reads ended at its second barrier)
+        for (int r = w; r < N; r += nw) {
+            float2 v[R];
+            pair_row<N>(v, r, lane, s1, s2, sp);
+            warp_fft_core<N>(v, tw, lane);
+#pragma unroll
+            for (int j = 0; j < R; ++j) buf[r * LD + warp_fft_out<N>(lane, j)] = v[j];
+        }
+        __syncthreads();
+        // columns: maxima only
+        float m1 = -INFINITY, m2 = -INFINITY;
+        for (int c = w; c < N; c += nw) {
+            float2 v[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j) v[j] = buf[(lane + 32 * j) * LD + c];
+            warp_fft_core<N>(v, tw, lane);
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                m1 = fmaxf(m1, v[j].x);
+                m2 = fmaxf(m2, v[j].y);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+            m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+        }
+        if (lane == 0) red[w] = make_float2(m1, m2);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            m1 = red[0].x;
+            m2 = red[0].y;
+            for (int i = 1; i < nw; ++i) {
+                m1 = fmaxf(m1, red[i].x);
+                m2 = fmaxf(m2, red[i].y);
+            }
+            if (t1 < 0) m1 = -INFINITY;
+            if (t2 < 0) m2 = -INFINITY;
+            if (t1 >= 0 && (m1 > best_v || (m1 == best_v && t1 < best_t))) { best_v = m1; best_t = t1; }
+            if (j2 != j1 && t2 >= 0 && (m2 > best_v || (m2 == best_v && t2 < best_t))) { best_v = m2; best_t = t2; }
+            if (peaks_all) {
+                peaks_all[(size_t)p * n + j1] = m1;
+                if (j2 != j1) peaks_all[(size_t)p * n + j2] = m2;
+            }
+        }
+    }
+    if (threadIdx.x == 0 && best_t >= 0) atomicMax(keys + p, pack_key(best_v, best_t));
+}
+
 // One work item: pattern p against slot pairs [pb, pe) (slots = all
 // templates, or the pattern's candidate list); kThreads threads and
 // smem_bytes<N>() of dynamic shared memory; folds the item's best into keys[p].
+// N >= 64 takes search_body_reg.
 template <int N>
 __device__ void search_body(const float2 *__restrict__ St, int T, const float2 *__restrict__ Sp, int p, int pb,
                             int pe, unsigned long long *__restrict__ keys, float *__restrict__ peaks_all,
                             const int *__restrict__ cand, int kc) {
+    if constexpr (N >= 64) {
+        search_body_reg<N>(St, T, Sp, p, pb, pe, keys, peaks_all, cand, kc);
+        return;
+    }
     constexpr int LD = N + 1, HW = N / 2 + 1;
     extern __shared__ float4 smem_raw[];
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);

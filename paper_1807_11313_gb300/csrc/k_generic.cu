@@ -42,6 +42,8 @@ template <int N>
 constexpr int prep_threads() { return N >= 128 ? 512 : kThreads; }
 template <int N>
 constexpr int peak_threads() { return N >= 128 ? 1024 : kThreads; }
+template <int N>
+constexpr int search_threads() { return N >= 128 ? 512 : kThreads; }
 
 template <int N, int PT = prep_threads<N>()>
 __global__ void __launch_bounds__(PT) k_prep_real(const float *__restrict__ img, PrepArgs a,
@@ -398,7 +400,7 @@ __global__ void __launch_bounds__(kPrepCplxThreads) k_prep_cplx(const float *__r
 }
 
 template <int N>
-__global__ void __launch_bounds__(kThreads) k_search_generic(const float2 *__restrict__ St, int T,
+__global__ void __launch_bounds__(search_threads<N>()) k_search_generic(const float2 *__restrict__ St, int T,
                                                              const float2 *__restrict__ Sp,
                                                              const int *__restrict__ degen,
                                                              int pairs_per_cta,
@@ -567,7 +569,7 @@ cudaError_t search_n(const float2 *St, int T, const float2 *Sp, const int *degen
     int ppc = (npairs + chunks - 1) / chunks;
     chunks = (npairs + ppc - 1) / ppc;
     dim3 grid(chunks, P);
-    k_search_generic<N><<<grid, kThreads, sm, st>>>(St, T, Sp, degen, ppc, keys, peaks_all, cand, kc);
+    k_search_generic<N><<<grid, search_threads<N>(), sm, st>>>(St, T, Sp, degen, ppc, keys, peaks_all, cand, kc);
     return cudaGetLastError();
 }
 

@@ -136,3 +136,38 @@ def test_native_refine_matches_oracle(px, orc, n, P):
                                     flags=px.XCF_LIB_NDP)
     lib.close()
     c.close()
+
+
+def test_native_maps_batch_matches_oracle(px, orc):
+    """One xcf_index_maps call over native 96 / 160 maps, a 2^k map and a 200 px
+    detector (native rule: 160) against the oracle's search of each map."""
+    master = synth.master_pattern("bcc", 512)
+    c = px.Context(native_sizes=1)
+    batch, oracle_in = [], []
+    for i, (W, T, P) in enumerate(((96, 11, 4), (160, 7, 3), (128, 9, 3), (200, 5, 2))):
+        n, ox, oy, pcc = orc.crop(W, W, PC0, native=True)
+        lq = synth.random_quaternions(T, 200 + i)
+        q = synth.perturb(lq[np.arange(P) % T], 2.0, 210 + i)
+        timgs = orc.project_many(master, lq, pcc, n).astype(np.float32)
+        pimgs = synth.add_noise(orc.project_many(master, q, pcc, n), np.broadcast_to(pcc, (P, 3)), 300.0, 220 + i)
+        tfull = np.zeros((T, W, W), np.float32)
+        pfull = np.zeros((P, W, W), np.float32)
+        tfull[:, oy:oy + n, ox:ox + n] = timgs
+        pfull[:, oy:oy + n, ox:ox + n] = pimgs
+        lib = px.xcf_build_library_images(c, dev(tfull), dev(lq), px.geometry(W, W, PC0))
+        batch.append((lib, dev(pfull)))
+        oracle_in.append((timgs, pimgs))
+    assert [lib.N for lib, _ in batch] == [96, 160, 128, 160]
+    outs = px.xcf_index_maps(c, batch)
+    for (best, peak, shift), (timgs, pimgs), (lib, _) in zip(outs, oracle_in, batch):
+        best, peak, shift = host(best), host(peak), host(shift)
+        St, _, _ = orc.prep_many(timgs)
+        Sp, _, deg = orc.prep_many(pimgs)
+        ob, opk, osh, allp = orc.index(St, Sp, deg, want_all=True)
+        for p in range(len(ob)):
+            assert best[p] == ob[p] or abs(allp[p, best[p]] - opk[p]) <= 2e-5 * abs(opk[p])
+        same = best == ob
+        np.testing.assert_allclose(peak[same], opk[same], rtol=1e-4, atol=1e-6)
+        np.testing.assert_allclose(shift[same], osh[same], atol=2e-3)
+        lib.close()
+    c.close()
