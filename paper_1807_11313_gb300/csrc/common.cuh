@@ -164,8 +164,14 @@ struct WarpFftTw {
     static constexpr int LR = P2 ? cx_log2(R) : 0;
     float2 wr[R > 1 ? R - 1 : 1];   // 2^k: register stage st (span 32 h'), pair (j, j + h'); else W_N^(l k1)
     float2 cr[P2 ? 1 : R - 1];      // R = 3, 5: W_R^m, m = 1 .. R-1
-    float2 wc[5];                   // lane stage c (span 16 >> c)
+    float2 wc[4];                   // lane stage c < 4 (span 16 >> c): 1 on the upper lane of a pair
     __device__ __forceinline__ void load(const float2 *tw, int lane) {
+        load_regs(tw, lane);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (!(lane & (16 >> c))) wc[c] = make_float2(1.f, 0.f);
+    }
+    __device__ __forceinline__ void load_regs(const float2 *tw, int lane) {
         if constexpr (P2) {
             int o = 0;
 #pragma unroll
@@ -176,14 +182,14 @@ struct WarpFftTw {
                 o += hp;
             }
 #pragma unroll
-            for (int c = 0; c < 5; ++c) wc[c] = tw[(lane & ((16 >> c) - 1)) << (LR + c)];
+            for (int c = 0; c < 4; ++c) wc[c] = tw[(lane & ((16 >> c) - 1)) << (LR + c)];
         } else {
 #pragma unroll
             for (int k1 = 1; k1 < R; ++k1) wr[k1 - 1] = tw_any<N>(tw, lane * k1);
 #pragma unroll
             for (int m = 1; m < R; ++m) cr[m - 1] = tw_any<N>(tw, 32 * m);
 #pragma unroll
-            for (int c = 0; c < 5; ++c) wc[c] = tw_any<N>(tw, R * ((lane & ((16 >> c) - 1)) << c));
+            for (int c = 0; c < 4; ++c) wc[c] = tw_any<N>(tw, R * ((lane & ((16 >> c) - 1)) << c));
         }
     }
 };
@@ -225,15 +231,19 @@ __device__ __forceinline__ void warp_fft_core(float2 (&v)[N / 32], const WarpFft
 #pragma unroll
         for (int k1 = 1; k1 < R; ++k1) v[k1] = c_mul(y[k1], t.wr[k1 - 1]);
     }
+    // lane stages: the upper lane of a pair keeps p + v, the lower (p - v) W;
+    // written as (p + sg v) wc with sg = +-1 and wc = 1 on the upper lane, so that no lane
+    // evaluates both branches; the last stage's twiddle is 1 on every lane
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
         const int h = 16 >> c;
-        const bool top = !(lane & h);
+        const float sg = (lane & h) ? -1.f : 1.f;
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             const float2 p = make_float2(__shfl_xor_sync(0xffffffffu, v[j].x, h),
                                          __shfl_xor_sync(0xffffffffu, v[j].y, h));
-            v[j] = top ? c_add(v[j], p) : c_mul(c_sub(p, v[j]), t.wc[c]);
+            const float2 d = make_float2(fmaf(sg, v[j].x, p.x), fmaf(sg, v[j].y, p.y));
+            v[j] = c < 4 ? c_mul(d, t.wc[c < 4 ? c : 0]) : d;
         }
     }
 }

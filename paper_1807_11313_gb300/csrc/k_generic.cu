@@ -43,7 +43,7 @@ constexpr int prep_threads() { return N >= 128 ? 512 : kThreads; }
 template <int N>
 constexpr int peak_threads() { return N >= 128 ? 1024 : kThreads; }
 template <int N>
-constexpr int search_threads() { return N >= 128 ? 512 : kThreads; }
+constexpr int search_threads() { return N >= 128 ? 1024 : kThreads; }
 
 template <int N, int PT = prep_threads<N>()>
 __global__ void __launch_bounds__(PT) k_prep_real(const float *__restrict__ img, PrepArgs a,
@@ -267,7 +267,7 @@ constexpr size_t smem_prep_cplx() {
 }
 
 template <int N>
-__global__ void __launch_bounds__(kPrepCplxThreads) k_prep_cplx(const float *__restrict__ img, int P, PrepArgs a,
+__global__ void __launch_bounds__(kPrepCplxThreads, 1) k_prep_cplx(const float *__restrict__ img, int P, PrepArgs a,
                                                                 float2 *__restrict__ spec,
                                                                 float *__restrict__ spatial,
                                                                 int *__restrict__ degen,
