@@ -236,15 +236,8 @@ bool supported_n(int n) {
     return n == 16 || n == 32 || n == 64 || n == 96 || n == 128 || n == 160 || n == 256;
 }
 
-// N = 256 kernels: persistent grid and its per-CTA work arrays (context scratch)
-cudaError_t big_work(xcf_ctx *ctx, int n, long items, float2 **work, int *grid) {
-    *grid = big_grid(ctx->num_sms, items);
-    return scratch_t(ctx, S_WORK, big_work_bytes(n, *grid) / sizeof(float2), work) ? cudaErrorMemoryAllocation
-                                                                                   : cudaSuccess;
-}
-
-// pre-processing, search and peak: shared-memory kernels up to N = 128, the
-// global work-array kernels for N = 256
+// pre-processing, search and peak: shared-memory kernels up to N = 160, the
+// four-CTA cluster kernels for N = 256
 cudaError_t run_prep(xcf_ctx *ctx, const float *img, int P, const PrepArgs &a, float2 *spec, float *spatial,
                      int *degen, const int *active, cudaStream_t st) {
     if (a.N != 256) return launch_prep(img, P, a, spec, spatial, degen, active, st);

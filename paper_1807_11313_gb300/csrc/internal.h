@@ -34,7 +34,6 @@ enum Slot {
     S_IO_PAT,       // host pipeline: device copy of a chunk of patterns
     S_IO_PCS,
     S_IO_OUT,
-    S_WORK,         // per-CTA N x N work arrays of the N = 256 kernels
     S_BF16_P,       // screen: pattern images in BF16
     S_SCORE,        // screen: zero-shift scores of a chunk
     S_ERR,          // device status word of kernels with bounded waits

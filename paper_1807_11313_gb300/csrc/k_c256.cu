@@ -478,15 +478,6 @@ __device__ __forceinline__ double ld_cluster_d(uint32_t addr) {
     asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
     return v;
 }
-__device__ __forceinline__ double block_sum_d(double v, double *sh) {
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double s = 0.0;
-    for (int w = 0; w < NT / 32; ++w) s += sh[w];
-    __syncthreads();
-    return s;
-}
 // FP32 partial per thread: warp sums in FP32, the warps' sums in FP64
 __device__ __forceinline__ double block_sum_fd(float v, double *sh) {
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -6,8 +6,8 @@
 // "Orientation and Pattern Centre Refinement" (Eq. 7, Fig. 6: shifts to
 // rotations about detector x / y, log-polar transform for z), second
 // "Equation 6" (disorientation with the 24 cubic operators).
-#include "big.cuh"
 #include "common.cuh"
+#include "line_fft.cuh"
 #include "kernels.cuh"
 
 namespace {
@@ -234,8 +234,8 @@ __global__ void __launch_bounds__(kEtaThreads) k_eta_update(const float *__restr
     __shared__ double wshift[kMaxLpWindows];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const float *ga = lpT + (size_t)p * nr * NETA, *gb = lpP + (size_t)p * nr * NETA;
-    bigk::make_tw<NETA>(tw, -1);
-    bigk::make_tw<NETA>(twi, +1);
+    linefft::make_tw<NETA>(tw, -1);
+    linefft::make_tw<NETA>(twi, +1);
     float2 *z = line[w];
     // radial window b holds radii [b nr / W, (b + 1) nr / W); each is correlated along eta on its own
     for (int b = 0; b < windows; ++b) {
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kEtaThreads) k_eta_update(const float *__restr
             for (int l = lane; l < NETA; l += 32)
                 z[l] = make_float2(ga[(size_t)m * NETA + l] - ma, gb[(size_t)m * NETA + l] - mb);
             __syncwarp();
-            bigk::warp_fft_line<NETA>(z, 1, tw);   // forward: Z[k] = sum_l z[l] e^{-2 pi i k l / NETA}
+            linefft::warp_fft_line<NETA>(z, 1, tw);   // forward: Z[k] = sum_l z[l] e^{-2 pi i k l / NETA}
 #pragma unroll
             for (int j = 0; j < KPL; ++j) {
                 const int k = lane + 32 * j;
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(kEtaThreads) k_eta_update(const float *__restr
                 if (k > 0 && k < NETA / 2) zc[NETA - k] = make_float2((float)cr, (float)-ci);
             }
             __syncwarp();
-            bigk::warp_fft_line<NETA>(zc, 1, twi);
+            linefft::warp_fft_line<NETA>(zc, 1, twi);
             for (int d = lane; d < NETA; d += 32) cfin[d] = zc[d].x;
         }
         __syncthreads();

@@ -21,12 +21,16 @@ namespace {
 
 constexpr int kNnThreads = 128, kNnTile = 1024;
 
-__device__ __forceinline__ double4 qmul_d(double4 a, double4 b) {
-    return make_double4(a.x * b.x - a.y * b.y - a.z * b.z - a.w * b.w, a.x * b.y + a.y * b.x + a.z * b.w - a.w * b.z,
-                        a.x * b.z - a.y * b.w + a.z * b.x + a.w * b.y, a.x * b.w + a.y * b.z - a.z * b.y + a.w * b.x);
+// a quaternion (w, x, y, z) held as members (x, y, z, w) = (w, x, y, z) in order
+struct Qd {
+    double x, y, z, w;
+};
+__device__ __forceinline__ Qd make_qd(double a, double b, double c, double d) { return Qd{a, b, c, d}; }
+__device__ __forceinline__ Qd qmul_d(Qd a, Qd b) {
+    return make_qd(a.x * b.x - a.y * b.y - a.z * b.z - a.w * b.w, a.x * b.y + a.y * b.x + a.z * b.w - a.w * b.z,
+                   a.x * b.z - a.y * b.w + a.z * b.x + a.w * b.y, a.x * b.w + a.y * b.z - a.z * b.y + a.w * b.x);
 }
 
-// (w, x, y, z) stored as double4 (x, y, z, w) = (w, x, y, z) in order
 __global__ void k_so3_points(const long long *__restrict__ ring_start, int n_rings, int n_polar, int n_s1,
                              const int *__restrict__ ring_az, long long G, double *__restrict__ q_all,
                              int *__restrict__ flag) {
@@ -46,10 +50,10 @@ __global__ void k_so3_points(const long long *__restrict__ ring_start, int n_rin
     sincos(0.5 * p1, &s1, &c1);
     sincos(0.5 * Phi, &s2, &c2);
     sincos(0.5 * p2, &s3, &c3);
-    double4 q = qmul_d(qmul_d(make_double4(c1, 0, 0, s1), make_double4(c2, s2, 0, 0)), make_double4(c3, 0, 0, s3));
+    Qd q = qmul_d(qmul_d(make_qd(c1, 0, 0, s1), make_qd(c2, s2, 0, 0)), make_qd(c3, 0, 0, s3));
     double nq = sqrt(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
     if (q.x < 0) nq = -nq;
-    q = make_double4(q.x / nq, q.y / nq, q.z / nq, q.w / nq);
+    q = make_qd(q.x / nq, q.y / nq, q.z / nq, q.w / nq);
     const double w = q.x > 1e-300 ? q.x : 1e-300;
     const double r0 = fabs(q.y) / w, r1 = fabs(q.z) / w, r2 = fabs(q.w) / w;
     const double mx = fmax(r0, fmax(r1, r2));
@@ -184,10 +188,9 @@ __global__ void k_nn_finish(const double *__restrict__ qa, int na, const double 
     const unsigned long long k = keys[i];
     if (k == 0) { angle[i] = -1.0; index[i] = -1; return; }
     const int j = (int)(0xffffffffu - (unsigned)(k & 0xffffffffu));
-    const double4 a = make_double4(qa[4 * i], qa[4 * i + 1], qa[4 * i + 2], qa[4 * i + 3]);
-    const double4 b = make_double4(qb[4 * (size_t)j], -qb[4 * (size_t)j + 1], -qb[4 * (size_t)j + 2],
-                                   -qb[4 * (size_t)j + 3]);
-    const double4 m = qmul_d(a, b);
+    const Qd a = make_qd(qa[4 * i], qa[4 * i + 1], qa[4 * i + 2], qa[4 * i + 3]);
+    const Qd b = make_qd(qb[4 * (size_t)j], -qb[4 * (size_t)j + 1], -qb[4 * (size_t)j + 2], -qb[4 * (size_t)j + 3]);
+    const Qd m = qmul_d(a, b);
     const double nm = sqrt(m.x * m.x + m.y * m.y + m.z * m.z + m.w * m.w);
     double t[4] = {fabs(m.x) / nm, fabs(m.y) / nm, fabs(m.z) / nm, fabs(m.w) / nm};
     for (int p = 0; p < 3; ++p)   // sort descending

@@ -31,16 +31,6 @@ cudaError_t launch_prep(const float *img, int P, const PrepArgs &a, float2 *spec
 cudaError_t launch_search(int N, const float2 *St, int T, const float2 *Sp, const int *degen, int P,
                           unsigned long long *keys, float *peaks_all, int num_sms, cudaStream_t st);
 
-// N = 256: the same three steps on a per-CTA N x N work array in global
-// memory (`work` holds grid * N * N complex values; big_grid gives the grid)
-int big_grid(int num_sms, long items);
-size_t big_work_bytes(int N, int grid);
-cudaError_t launch_prep_big(const float *img, int P, const PrepArgs &a, float2 *spec, float *spatial, int *degen,
-                            const int *active, float2 *work, int grid, cudaStream_t st);
-cudaError_t launch_search_big(int N, const float2 *St, int T, const float2 *Sp, const int *degen, int P,
-                              unsigned long long *keys, float *peaks_all, float2 *work, int grid,
-                              cudaStream_t st, const int *cand = nullptr, int kc = 0);
-
 // N = 256 search on clusters of four CTAs (the 256 x 256 array in distributed
 // shared memory); with cand: each pattern's candidate list cand [P][kc]
 cudaError_t launch_search_c256(const float2 *St, int T, const float2 *Sp, const int *degen, int P,
@@ -66,9 +56,6 @@ cudaError_t launch_screen_tc(const void *A, int P, const void *B, int T, int K, 
 // top-k (k <= 64) of each row of S [P][T]: candidates by (score desc, index asc)
 cudaError_t launch_topk_rows(const float *S, int P, int T, int k, int *cand, float *score, cudaStream_t st);
 cudaError_t launch_to_bf16(const float *x, size_t n, void *y, cudaStream_t st);
-cudaError_t launch_pair_peak_big(int N, const float2 *St, const int *tidx, const float2 *Sp, const int *degen,
-                                 const int *active, int P, float *peak, float *shift, float2 *work, int grid,
-                                 cudaStream_t st);
 
 // multi-map search: one persistent launch over a queue of work items
 struct MapDev {
