@@ -7,8 +7,9 @@ with gcc on first use and marshals numpy arrays through ctypes.  It shares no
 code with the CUDA library.
 
 Parity unpinned: window shape, band-pass shape and cut-offs, log-polar
-sampling constants (the paper gives none of them); everything else is pinned
-by the tests under ``tests/test_oracle_*.py``.
+sampling constants (the paper gives none of them); their implementation is
+pinned to library routines (``tests/test_oracle_filters.py``), and everything
+else by the tests under ``tests/test_oracle_*.py``.
 """
 from __future__ import annotations
 

@@ -13,7 +13,9 @@
  * Parity unpinned: the window shape, the band-pass shape and its cut-offs, the
  * log-polar sampling constants and the refinement's sign conventions are not
  * fixed by the paper (it gives no values); they are pinned only against the
- * paper's qualitative statements and internal invariants.
+ * paper's qualitative statements and internal invariants.  The implementation
+ * of those readings is pinned to library routines (scipy's periodic Hann,
+ * products of Fourier-domain Gaussians, bilinear resampling, numpy's FFT).
  */
 #include <complex.h>
 #include <math.h>
