@@ -387,9 +387,11 @@ int xcf_index_refine_host(xcf_ctx *ctx, const xcf_library *lib, const float *pat
  * keys) lives in one fixed array of XCF_NOALLOC_SCRATCH_BYTES compiled into
  * the library, which every GPU that loads the library holds until the
  * process exits.  The caller still provides inputs and outputs.
- *  - P may not exceed xcf_noalloc_max_patterns(N) (252 patterns at N = 128,
- *    992 at N = 64); larger P fails with XCF_ERR_SIZE and a message naming
- *    the limit.
+ *  - P may not exceed xcf_noalloc_max_patterns(N) (992 patterns at N = 64,
+ *    252 at N = 128, 63 at N = 256); larger P fails with XCF_ERR_SIZE and a
+ *    message naming the limit.  Every side the library builds is served
+ *    (native 96 and 160 included); the up-sampled peak option is not
+ *    (XCF_ERR_UNIMPLEMENTED: it needs scratch).
  *  - The first call on a device looks up the array's device address (a
  *    one-time set-up that allocates nothing); make that first call before
  *    any stream capture.
@@ -402,7 +404,7 @@ int xcf_index_noalloc(xcf_ctx *ctx, const xcf_library *lib, const float *pattern
                       int32_t *best, float *peak, float *shift, void *stream);
 
 /* Largest P that xcf_index_noalloc accepts for detector side n (0 if n is
- * not a power of two in [16, 256]).  Host only. */
+ * not a side the kernels take: 16, 32, 64, 96, 128, 160, 256).  Host only. */
 int xcf_noalloc_max_patterns(int32_t n);
 
 /* ---------------------------------------------------------------------

@@ -63,8 +63,8 @@ int cuda_error(xcf_ctx *ctx, cudaError_t e, const char *where) {
 }  // namespace
 
 extern "C" int xcf_noalloc_max_patterns(int32_t n) {
-    // N = 256 runs on per-CTA work arrays that this entry point does not hold
-    if (n < 16 || n > 128 || (n & (n - 1))) return 0;
+    // every side the kernels take: 2^k in [16, 256] and the native 96 and 160
+    if (!(n == 16 || n == 32 || n == 64 || n == 96 || n == 128 || n == 160 || n == 256)) return 0;
     long lo = 0, hi = 1L << 24;
     while (lo < hi) {       // largest P whose scratch fits
         long mid = (lo + hi + 1) / 2;
@@ -85,10 +85,6 @@ extern "C" int xcf_index_noalloc(xcf_ctx *ctx, const xcf_library *lib, const flo
         return XCF_ERR_ARG;
     }
     const int n = lib->N;
-    if (n > 128) {
-        ctx->err = "xcf_index_noalloc: detectors of side 256 are searched on thread-block clusters; use xcf_index";
-        return XCF_ERR_UNIMPLEMENTED;
-    }
     if (ctx->opt.upsample >= 2) {
         ctx->err = "xcf_index_noalloc: the up-sampled peak needs scratch; use xcf_index";
         return XCF_ERR_UNIMPLEMENTED;
@@ -129,16 +125,21 @@ extern "C" int xcf_index_noalloc(xcf_ctx *ctx, const xcf_library *lib, const flo
     a.inv2shp = (float)(1.0 / (2.0 * shp * shp));
     a.inv2slp = (float)(1.0 / (2.0 * slp * slp));
 
-    cudaError_t e = launch_prep(patterns, P, a, sp, nullptr, degen, nullptr, st);
+    // N = 256 runs on four-CTA clusters, which need no scratch beyond the spectra
+    const bool c256 = n == 256;
+    cudaError_t e = c256 ? launch_prep_c256(patterns, P, a, sp, nullptr, degen, nullptr, st)
+                         : launch_prep(patterns, P, a, sp, nullptr, degen, nullptr, st);
     if (e != cudaSuccess) return cuda_error(ctx, e, "prep");
     // the array keeps the previous call's contents: the keys must start at 0
     e = cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * P, st);
     if (e != cudaSuccess) return cuda_error(ctx, e, "clear keys");
-    e = launch_search(n, search_spectra(lib), lib->T, sp, degen, P, keys, nullptr, ctx->num_sms, st);
+    e = c256 ? launch_search_c256(search_spectra(lib), lib->T, sp, degen, P, keys, nullptr, nullptr, 0, st)
+             : launch_search(n, search_spectra(lib), lib->T, sp, degen, P, keys, nullptr, ctx->num_sms, st);
     if (e != cudaSuccess) return cuda_error(ctx, e, "search");
     e = launch_keys_to_best(keys, P, best, st);
     if (e != cudaSuccess) return cuda_error(ctx, e, "keys_to_best");
-    e = launch_pair_peak(n, lib->spectra, best, sp, degen, nullptr, P, peak, shift, st);
+    e = c256 ? launch_pair_peak_c256(lib->spectra, best, sp, degen, nullptr, P, peak, shift, st)
+             : launch_pair_peak(n, lib->spectra, best, sp, degen, nullptr, P, peak, shift, st);
     if (e != cudaSuccess) return cuda_error(ctx, e, "pair_peak");
     ctx->launches[XCF_STAGE_PREP] += 1;
     ctx->launches[XCF_STAGE_SEARCH] += 1;

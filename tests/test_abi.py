@@ -75,3 +75,20 @@ def test_native_crop_rule_matches_oracle(orc):
     assert xcf.xcf_crop(xcf.geometry(96, 96), native=True)[0] == 96
     assert xcf.xcf_crop(xcf.geometry(96, 96))[0] == 64
     assert xcf.load().xcf_crop_ex(ctypes.byref(xcf.geometry(96, 96)), 2, None, None, None, None) == xcf.XCF_ERR_ARG
+
+
+def test_noalloc_limits_cover_every_side():
+    """Host-only: the fixed no-alloc scratch holds this many patterns per side
+    (spectra + flags + keys in 16 MiB, each slice 256-byte aligned)."""
+    from paper_1807_11313_gb300 import xcf
+    def fits(n):
+        H = n * (n // 2 + 1)
+        r = lambda x: (x + 255) & ~255
+        P = 0
+        while r(8 * H * (P + 1)) + r(4 * (P + 1)) + r(8 * (P + 1)) <= 16 << 20:
+            P += 1
+        return P
+    for n in (16, 32, 64, 96, 128, 160, 256):
+        assert xcf.xcf_noalloc_max_patterns(n) == fits(n) > 0
+    for n in (0, 8, 100, 200, 512):
+        assert xcf.xcf_noalloc_max_patterns(n) == 0

@@ -38,14 +38,14 @@ def _compare(ref, got):
     np.testing.assert_allclose(gs, rs, atol=2e-3)
 
 
-@pytest.mark.parametrize("n", [128, 64])
+@pytest.mark.parametrize("n", [128, 64, 96, 160, 256])
 def test_noalloc_matches_index_on_consecutive_calls(px, n):
     T = 37
     timgs, pats1 = _inputs(n, T, 40, 1)
     _, pats2 = _inputs(n, T, 9, 2)
     pats2[3] = 1.5                                   # a pattern with no signal
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    ctx_ref = px.Context()
+    ctx_ref = px.Context(native_sizes=int(n in (96, 160)))
     g = px.geometry(n, n)
     lib = px.xcf_build_library_images(ctx_ref, dev(timgs), dev(synth.random_quaternions(T, 3)), g)
     ref1 = px.xcf_index(ctx_ref, lib, dev(pats1))
@@ -88,6 +88,9 @@ def test_noalloc_rejects_oversize(px):
     n = 128
     pmax = px.xcf.xcf_noalloc_max_patterns(n)
     assert pmax == 252
+    assert px.xcf.xcf_noalloc_max_patterns(256) == 63 and px.xcf.xcf_noalloc_max_patterns(64) == 992
+    assert px.xcf.xcf_noalloc_max_patterns(96) > 0 and px.xcf.xcf_noalloc_max_patterns(160) > 0
+    assert px.xcf.xcf_noalloc_max_patterns(100) == 0 and px.xcf.xcf_noalloc_max_patterns(512) == 0
     timgs, _ = _inputs(n, 3, 1, 4)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     ctx = px.Context()
