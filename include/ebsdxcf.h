@@ -37,11 +37,11 @@ extern "C" {
 
 #define XCF_OK                 0
 #define XCF_ERR_ARG           -1  /* null pointer, negative count, bad option  */
-#define XCF_ERR_SIZE          -2  /* detector side not a usable power of two   */
+#define XCF_ERR_SIZE          -2  /* detector below 16 px, or a count too large */
 #define XCF_ERR_OOM           -3  /* device allocation failed                  */
 #define XCF_ERR_CUDA          -4  /* a CUDA runtime call or launch failed      */
 #define XCF_ERR_TIMEOUT       -5  /* a bounded device wait gave up             */
-#define XCF_ERR_UNIMPLEMENTED -6  /* combination not built (e.g. N = 256 here) */
+#define XCF_ERR_UNIMPLEMENTED -6  /* combination not built (e.g. NDP at 96 px) */
 
 typedef struct xcf_ctx xcf_ctx;
 typedef struct xcf_library xcf_library;
