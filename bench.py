@@ -43,6 +43,24 @@ UNIT = "patterns/s"
 FLOPS_PER_PAIR_128 = 2.5 * 128 * 128 * 14 + 6 * 128 * 65   # inverse real FFT + conj-multiply
 
 
+# ------------------------------------------------------------ multi-rank timing
+def max_over_ranks(elapsed, dist, device):
+    """The job's time: every rank's elapsed time (any unit), all-reduced by
+    MAX (the slowest rank); unchanged on one rank."""
+    if not dist:
+        return elapsed
+    import torch
+    t = torch.tensor([float(elapsed)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step, steps, world, elapsed_ms):
+    """Whole-job throughput: the units every rank processed in `steps` steps
+    (weak scaling: the same count per rank), over the job's time."""
+    return units_per_rank_step * steps * world / (elapsed_ms / 1e3)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -296,10 +314,7 @@ def run_precision(args, px, torch, dev, rank, world, local, dist):
     torch.cuda.synchronize()
     clocks = clocks_stop(clk)
     elapsed_ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, dev)
     px.xcf_profile_enable(ctx, False)
     prof = px.xcf_profile_read(ctx, reset=True)
     pk = peaks_file() or {}
@@ -312,7 +327,7 @@ def run_precision(args, px, torch, dev, rank, world, local, dist):
                 "peak_basis": "measured sustained cuBLAS BF16 (MEASURED_PEAKS.json)" if pk else "fallback",
                 "screen_ms_per_launch": s_ms / max(s_n, 1), "launches_per_step": s_n / args.steps,
                 "stage_ms_per_step": {kk: v[0] / args.steps for kk, v in prof.items()}}
-    value = P * args.steps * world / (elapsed_ms / 1e3)
+    value = whole_job_rate(P, args.steps, world, elapsed_ms)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -377,10 +392,7 @@ def run_ndp(args, px, torch, dev, rank, world, local, dist):
     torch.cuda.synchronize()
     clocks = clocks_stop(clk)
     elapsed_ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, dev)
     px.xcf_profile_enable(ctx, False)
     prof = px.xcf_profile_read(ctx, reset=True)
     pk = peaks_file() or {}
@@ -393,7 +405,7 @@ def run_ndp(args, px, torch, dev, rank, world, local, dist):
                 "peak_basis": "measured sustained cuBLAS BF16 (MEASURED_PEAKS.json)" if pk else "fallback",
                 "screen_ms_per_launch": s_ms / max(s_n, 1), "launches_per_step": s_n / args.steps,
                 "stage_ms_per_step": {kk: v[0] / args.steps for kk, v in prof.items()}}
-    value = P * args.steps * world / (elapsed_ms / 1e3)
+    value = whole_job_rate(P, args.steps, world, elapsed_ms)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -609,10 +621,7 @@ def run_batched(args, px, torch, dev, rank, world, local, dist):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
         return ms
 
     px.xcf_profile_read(ctx, reset=True)
@@ -683,10 +692,10 @@ def run_batched(args, px, torch, dev, rank, world, local, dist):
             e2e_step()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        e2e = {"value": P_all * args.steps * world / dt, "unit": UNIT,
+        e2e = {"value": whole_job_rate(P_all, args.steps, world, dt * 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(sum(h.numel() * 4 for h in hp)),
                "d2h_bytes_per_step": int(sum(a.numel() * a.element_size() for h in ho for a in h))}
-    value = P_all * args.steps * world / (elapsed_ms / 1e3)
+    value = whole_job_rate(P_all, args.steps, world, elapsed_ms)
     if rank == 0:
         line = {"metric": "patterns indexed/s (batched maps: prep + search + peak per map)", "value": value,
                 "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -803,10 +812,7 @@ def run_learned(args, px, torch, dev, rank, world, local, dist):
     elapsed_ms = e0.elapsed_time(e1)
     px.xcf_profile_enable(ctx, False)
     prof = px.xcf_profile_read(ctx, reset=True)
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, dev)
     mis = px.xcf_disorientation(ctx, outs[0], teq)
     fb = outs[3].double()
     # ---- ablation: the plain full search + refinement on the same test set, and the raw proposals
@@ -819,7 +825,7 @@ def run_learned(args, px, torch, dev, rank, world, local, dist):
     prop = px.xcf_propose(ctx, net, pats[:ncal].contiguous(), geom)
     best_prop = torch.stack([px.xcf_disorientation(ctx, prop[:, h].contiguous(), teq[:ncal].contiguous())
                              for h in range(k)]).min(dim=0).values
-    value = n_test * args.steps * world / (elapsed_ms / 1e3)
+    value = whole_job_rate(n_test, args.steps, world, elapsed_ms)
     pk = peaks_file()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = (pk or {}).get("sm_max_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
@@ -943,14 +949,11 @@ def main():
     if dist:
         dist.barrier()
     elapsed_ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, dev)
     px.xcf_profile_enable(ctx, False)
     prof = px.xcf_profile_read(ctx, reset=True)
     launches = int(sum(v[1] for v in prof.values()))
-    value = P * args.steps * world / (elapsed_ms / 1e3)
+    value = whole_job_rate(P, args.steps, world, elapsed_ms)
 
     # ---- roofline of the dominant kernel (the all-pairs search)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -993,13 +996,10 @@ def main():
             e2e_step()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(dt, dist, dev)
         h2d = pats_h.numel() * 4 + pcs_h.numel() * 8 + master_h.numel() * 4 + libq_h.numel() * 8
         d2h = sum(v.numel() * v.element_size() for v in hout.values())
-        e2e = {"value": P * args.steps * world / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": whole_job_rate(P, args.steps, world, dt * 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
     # ---- CPU oracle baseline (rank 0, one GPU only)
