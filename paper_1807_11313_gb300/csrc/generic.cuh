@@ -1,6 +1,7 @@
-// Shared-memory 2-D FFT machinery and the all-pairs search body for
-// N <= 128 (generic radix-2 in shared memory), shared by the kernels of
-// k_generic.cu and the multi-map kernel.
+// Shared-memory 2-D FFT machinery and the all-pairs search body for the
+// sides other than the tuned 128 and 256 kernels (16 .. 160 px, native 96 and
+// 160 included): register line FFTs for N = R x 32 >= 64, radix-2 butterflies
+// in shared memory below; used by the kernels of k_generic.cu.
 #pragma once
 #include "common.cuh"
 

@@ -1,8 +1,10 @@
 // Pre-processing, the all-sides search kernel and the single-surface peak
-// kernel for N in {16, 32, 64, 128}.  The search and peak kernels hold one
-// N x N complex array in shared memory (rows padded to N + 1) and transform it
-// with a radix-2 FFT whose butterflies are spread over the lanes of a warp;
-// the pre-processing transforms real images at half that work (below).
+// kernel for N in {16, 32, 64, 96, 128, 160}.  The search and peak kernels
+// hold one N x N complex array in shared memory (rows padded to N + 1) and
+// transform its lines with the warp line FFT (registers and shuffles for
+// N = R x 32 >= 64, mixed radix at 96 and 160; radix-2 butterflies spread
+// over the lanes below 64); the pre-processing transforms two real images per
+// complex transform (rows paired for 2^k sides, whole images for 96 and 160).
 //
 // Paper: FFT section (Eq. 4 transform, filtering, windowing, normalisation by
 // the autocorrelations), Eqs. 3 and 6 (correlation surface), peak up-sampling.
