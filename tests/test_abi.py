@@ -92,3 +92,23 @@ def test_noalloc_limits_cover_every_side():
         assert xcf.xcf_noalloc_max_patterns(n) == fits(n) > 0
     for n in (0, 8, 100, 200, 512):
         assert xcf.xcf_noalloc_max_patterns(n) == 0
+
+
+def test_network_parameter_count_matches_oracle(orc):
+    """Host-only: the flat parameter count of the proposal network equals the
+    oracle's layer-by-layer count, for every valid head count."""
+    from paper_1807_11313_gb300 import xcf
+    L = xcf.load()
+    for k in (1, 2, 8, 17, 64):
+        assert L.xcf_net_num_params(k) == orc.cnn_num_params(k)
+    assert L.xcf_net_num_params(0) == -1 and L.xcf_net_num_params(65) == -1
+
+
+def test_option_defaults_are_the_documented_readings():
+    from paper_1807_11313_gb300 import xcf
+    o = xcf.xcf_options()
+    assert xcf.load().xcf_options_default(ctypes.byref(o)) == 0
+    assert (o.window, o.sigma_hp, o.max_iter, o.tol_deg) == (1, 2.0, 2, 1e-3)
+    assert o.sigma_lp == 0.0 and o.lp_nr == 0 and o.lp_neta == 0          # 0: N/4, N/4 radii, 2N angles
+    assert (o.upsample, o.master_interp, o.lp_windows, o.native_sizes) == (0, 0, 0, 0)
+    assert o.ndp_bg_sigma == 0.0                                          # 0: N/8 px
