@@ -125,11 +125,13 @@ static void fft1_strided(cplx *x, int n, int st, int sign) {
 /* A line of any length: the radix-2 FFT for powers of two, the direct DFT
  * (orc_dft1) otherwise (the 96- and 160-pixel native detectors). */
 static void line_transform(cplx *x, int n, int st, int sign) {
+    if (n <= 0) return;
     if ((n & (n - 1)) == 0) {
         fft1_strided(x, n, st, sign);
         return;
     }
     cplx *a = malloc(sizeof(cplx) * n), *b = malloc(sizeof(cplx) * n);
+    if (!a || !b) abort();   /* test infrastructure: no recovery from an exhausted host */
     for (int i = 0; i < n; ++i) a[i] = x[(long)i * st];
     orc_dft1(a, b, n, sign);
     for (int i = 0; i < n; ++i) x[(long)i * st] = b[i];
