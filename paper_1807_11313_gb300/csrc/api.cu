@@ -238,13 +238,13 @@ bool supported_n(int n) {
 
 // pre-processing, search and peak: shared-memory kernels up to N = 160, the
 // four-CTA cluster kernels for N = 256
-cudaError_t run_prep(xcf_ctx *ctx, const float *img, int P, const PrepArgs &a, float2 *spec, float *spatial,
+cudaError_t run_prep(xcf_ctx * /*ctx*/, const float *img, int P, const PrepArgs &a, float2 *spec, float *spatial,
                      int *degen, const int *active, cudaStream_t st) {
     if (a.N != 256) return launch_prep(img, P, a, spec, spatial, degen, active, st);
     return launch_prep_c256(img, P, a, spec, spatial, degen, active, st);
 }
 
-cudaError_t run_search(xcf_ctx *ctx, int n, const float2 *St, int T, const float2 *Sp, const int *degen, int P,
+cudaError_t run_search(xcf_ctx * /*ctx*/, int n, const float2 *St, int T, const float2 *Sp, const int *degen, int P,
                        unsigned long long *keys, float *peaks_all, int num_sms, cudaStream_t st) {
     if (n != 256) return launch_search(n, St, T, Sp, degen, P, keys, peaks_all, num_sms, st);
     return launch_search_c256(St, T, Sp, degen, P, keys, peaks_all, nullptr, 0, st);
