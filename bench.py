@@ -970,6 +970,9 @@ def main():
                 "kernel": "k_search128", "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
                 "search_ms_per_launch": per_launch_ms,
                 "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+    fma_tflops, _ = px.xcf_fp32_fma_rate(ctx)                 # measured FMA rate, beside the derived peak
+    roofline["fma_probe_tflops"] = fma_tflops
+    roofline["frac_of_fma_probe"] = achieved / fma_tflops
 
     # ---- end to end through the host-memory entry point
     e2e = None

@@ -178,15 +178,26 @@ int xcf_library_info(const xcf_library *lib, int32_t *T, int32_t *N, const float
  * r(s) = sum_k conj(S_t[k]) S_p[k] exp(+2 pi i k.s / N) over all N^2 circular
  * shifts; ties go to the lowest template index and, within a surface, to the
  * lowest row-major shift.
- *   patterns [P, H, W] float32 with the library's geometry.
+ *   patterns [P, H, W] float32 with the library's detector (W x H, tilts).
+ *   pcs      [P, 3] float64 per-pattern pattern centres (pcx, pcy, pcz), or
+ *            NULL (every pattern at the library's centre).  The per-pattern
+ *            geometry of a map whose pattern centre drifts across the scan
+ *            (paper, refinement section and the large Si map): the templates
+ *            stay at the library's centre (the correlation tolerates the
+ *            drift as a translation), and the shift is reported relative to
+ *            where the template would sit at the pattern's own centre.
  *   best     [P] int32: template index, or -1 for a degenerate pattern.
  *   peak     [P] float32: r at the integer peak of the best template.
  *   shift    [P, 2] float32 (dx, dy) px: the pattern is the template
  *            translated by +shift; integer peak wrapped into [-N/2, N/2) plus a
  *            3-point parabolic sub-pixel offset per axis (the paper's peak
- *            up-sampling, read as a parabola fit), clamped to +-0.5.       */
+ *            up-sampling, read as a parabola fit), clamped to +-0.5.  With
+ *            pcs, minus the translation (pcx_p - pcx_lib) W, (pcy_p - pcy_lib) H
+ *            that moving the pattern centre alone produces (a change of pcx
+ *            or pcy translates the gnomonic screen content exactly; pcz
+ *            scales it and is not corrected).                              */
 int xcf_index(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P,
-              int32_t *best, float *peak, float *shift, void *stream);
+              const double *pcs, int32_t *best, float *peak, float *shift, void *stream);
 
 /* The same search, but returning every per-template peak: peaks [P, T]
  * float32 (max over shifts of r for each pair).  For analysis and tests. */
@@ -203,13 +214,16 @@ int xcf_correlate_all(xcf_ctx *ctx, const xcf_library *lib, const float *pattern
  *        about the screen centre, correlates along the angle and turns the
  *        angular shift into a rotation about the detector z axis;
  * composing each rotation onto the orientation in float64, until the update
- * of an iteration is below opt.tol_deg or opt.max_iter iterations ran.
+ * of an iteration is below tol_deg or max_iter iterations ran.
  *   patterns [P, H, W] float32; seeds [P, 4] float64; pcs [P, 3] float64 or
- *   NULL (library PC); quats [P, 4] float64 out; peak [P] float32 out (XCF
- *   peak of the last X/Y step); iters [P] int32 out.                      */
+ *   NULL (library PC): the per-pattern geometry, used by every projection;
+ *   max_iter in [1, 1000], or <= 0 for the context's opt.max_iter; tol_deg
+ *   >= 0, or < 0 for opt.tol_deg; quats [P, 4] float64 out; peak [P] float32
+ *   out (XCF peak of the last X/Y step); iters [P] int32 out.
+ * XCF_ERR_ARG if max_iter > 1000.                                          */
 int xcf_refine(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P,
-               const double *seeds, const double *pcs, double *quats, float *peak,
-               int32_t *iters, void *stream);
+               const double *seeds, const double *pcs, int32_t max_iter, double tol_deg,
+               double *quats, float *peak, int32_t *iters, void *stream);
 
 /* Cubic (432) disorientation in degrees between qa[i] and qb[i] (paper, second
  * "Equation 6"): the smallest rotation angle of S qa qb^-1 over the 24 proper
@@ -359,9 +373,10 @@ typedef struct {
 #define XCF_MAPS_GRAPH 1
 int xcf_index_maps(xcf_ctx *ctx, const xcf_map_desc *maps, int32_t n_maps, int32_t flags, void *stream);
 
-/* Search then refine in one call (device memory): xcf_index, seeds = the
- * library orientations of the best templates (identity for degenerate
- * patterns), then xcf_refine.  Outputs as those two calls. */
+/* Search then refine in one call (device memory): xcf_index with pcs, seeds =
+ * the library orientations of the best templates (identity for degenerate
+ * patterns), then xcf_refine with pcs and the context's max_iter / tol_deg.
+ * Outputs as those two calls. */
 int xcf_index_refine(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P,
                      const double *pcs, int32_t *best, float *peak, float *shift, double *quats,
                      float *rpeak, int32_t *iters, void *stream);
@@ -392,9 +407,14 @@ int xcf_index_refine_host(xcf_ctx *ctx, const xcf_library *lib, const float *pat
  *    message naming the limit.  Every side the library builds is served
  *    (native 96 and 160 included); the up-sampled peak option is not
  *    (XCF_ERR_UNIMPLEMENTED: it needs scratch).
- *  - The first call on a device looks up the array's device address (a
- *    one-time set-up that allocates nothing); make that first call before
- *    any stream capture.
+ *  - The array is committed on a device by the first call there, not when
+ *    the library is loaded: CUDA loads the library's modules lazily by
+ *    default, and that first call loads the module holding the array (and
+ *    looks up its device address, once per device and CUDA context).  So
+ *    the first call on each device commits XCF_NOALLOC_SCRATCH_BYTES plus
+ *    the module's small code, and can fail with XCF_ERR_CUDA when the GPU is
+ *    full.  Make it before another allocator reserves the GPU, and before
+ *    any stream capture; later calls allocate nothing.
  *  - All calls on a device share the one array and it keeps the previous
  *    call's contents (the call clears what must start at zero).  Calls whose
  *    work overlaps on the GPU (other streams, other host threads) race on it:
@@ -402,6 +422,15 @@ int xcf_index_refine_host(xcf_ctx *ctx, const xcf_library *lib, const float *pat
 #define XCF_NOALLOC_SCRATCH_BYTES (16u << 20)
 int xcf_index_noalloc(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P,
                       int32_t *best, float *peak, float *shift, void *stream);
+
+/* Measured FP32 FMA throughput of the context's device (the paper has no
+ * counterpart: a measurement utility).  The all-pairs search is bound by FP32
+ * arithmetic, and its roofline takes SMs x 128 FMA lanes x 2 flops x clock as
+ * the peak; this launches 4 x SMs CTAs of 1,024 threads, each thread running
+ * eight independent FMA chains of 65,536 FMAs, and reports the best of three
+ * timed launches: tflops = flops / time in TFLOP/s, ms (nullable) the launch
+ * time.  Synchronous with respect to `stream`.                              */
+int xcf_fp32_fma_rate(xcf_ctx *ctx, double *tflops, double *ms, void *stream);
 
 /* Largest P that xcf_index_noalloc accepts for detector side n (0 if n is
  * not a side the kernels take: 16, 32, 64, 96, 128, 160, 256).  Host only. */

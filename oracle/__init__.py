@@ -92,6 +92,7 @@ def _lib_handle():
                 "orc_upsampled_value": ([_D, _D, C.c_int, C.c_double, C.c_double], C.c_double),
                 "orc_peak": ([_D, C.c_int, _D, _I, _I, _D, _D], None),
                 "orc_index": ([_D, C.c_int, _D, C.c_int, C.c_int, _I, _I, _D, _D, _D], None),
+                "orc_pc_shift": ([_D, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, _I, _D], None),
                 "orc_lambert_forward": ([_D, _D, _D], None),
                 "orc_lambert_inverse": ([C.c_double, C.c_double, _D], None),
                 "orc_master_lookup": ([_F, C.c_int, _D], C.c_double),
@@ -292,8 +293,11 @@ def upsampled_value(St, Sp, y, x):
     return _lib_handle().orc_upsampled_value(_d(St), _d(Sp), St.shape[0], float(y), float(x))
 
 
-def index(St, Sp, degenerate=None, want_all=False):
+def index(St, Sp, degenerate=None, want_all=False, pcs=None, geom=None):
     """Library search. St [T,n,n], Sp [P,n,n] full spectra.
+    pcs [P,3] with geom = (W, H, pcx_lib, pcy_lib): per-pattern pattern
+    centres; the shift is then taken relative to the template at the
+    pattern's own centre (orc_pc_shift).
     -> best [P] int32, peak [P], shift [P,2] (dx, dy), peaks_all [P,T] or None."""
     St, Sp = _c128(St), _c128(Sp)
     T, n = St.shape[0], St.shape[1]
@@ -305,6 +309,9 @@ def index(St, Sp, degenerate=None, want_all=False):
     allp = np.empty((P, T)) if want_all else None
     _lib_handle().orc_index(_d(St), T, _d(Sp), P, n, _i(deg), _i(best), _d(pk), _d(sh),
                             _d(allp) if allp is not None else None)
+    if pcs is not None:
+        W, H, pcx, pcy = geom
+        _lib_handle().orc_pc_shift(_d(_f64(pcs)), P, float(pcx), float(pcy), int(W), int(H), _i(best), _d(sh))
     return best, pk, sh, allp
 
 

@@ -438,6 +438,25 @@ void orc_index(const cplx *St, int T, const cplx *Sp, int P, int n,
     }
 }
 
+/* Per-pattern pattern centres in the search.  The gnomonic ray of pixel
+ * (i, j) is (j + .5 - pcx W, pcy H - (i + .5), pcz W) (projection below), so
+ * a pattern centre moved by (dx, dy) in (pcx, pcy) gives every ray to the
+ * pixel dx W columns right and dy H rows down: the screen content of the
+ * pattern is the library-centre projection translated by exactly
+ * (dx W, dy H) px.  The search keeps the library's templates, and this takes
+ * that translation out of the measured shift, so that what remains is the
+ * orientation's part (the refinement section's per-pattern centre).  pcz is
+ * a scale, not a translation, and is not corrected.  Degenerate patterns
+ * (best < 0) keep their zero shift. */
+void orc_pc_shift(const double *pcs, int P, double pcx, double pcy, int W, int H,
+                  const int32_t *best, double *shift) {
+    for (int p = 0; p < P; ++p) {
+        if (best[p] < 0) continue;
+        shift[2 * p] -= (pcs[3 * p] - pcx) * W;
+        shift[2 * p + 1] -= (pcs[3 * p + 1] - pcy) * H;
+    }
+}
+
 /* ---------------------------------------------------------------------- */
 /* master pattern lookup and gnomonic projection (SO(3) Library Generation) */
 /* ---------------------------------------------------------------------- */

@@ -276,8 +276,11 @@ constexpr int kChunk = 16384;   // patterns per pass (bounds the scratch footpri
 // index one chunk already on the device: spectra of the patterns, search,
 // best, and the sub-pixel peak of the best template
 // only (nullable): patterns with only[p] == 0 are skipped like degenerate ones
+// pcs (nullable, [P, 3]): per-pattern pattern centres; the shift is then taken
+// relative to the template as it would sit at the pattern's own centre
 int index_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int P, int *best,
-                float *peak, float *shift, float *peaks_all, cudaStream_t st, const int *only = nullptr) {
+                float *peak, float *shift, float *peaks_all, cudaStream_t st, const int *only = nullptr,
+                const double *pcs = nullptr) {
     const xcf_geometry *g = &lib->geom;
     Crop c;
     crop_of(g, 256, &c, lib->native);
@@ -308,13 +311,20 @@ int index_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int
         XCF_LAUNCH(XCF_STAGE_PEAK, st,
                    run_pair_peak(ctx,c.n, lib->spectra, best, sp, degen, nullptr, P, peak, shift, st),
                    "pair_peak");
+        if (pcs)
+            XCF_LAUNCH(XCF_STAGE_OTHER, st,
+                       launch_shift_pc(pcs, g->pcx, g->pcy, g->width, g->height, best, P, shift, st), "shift_pc");
     }
     return XCF_OK;
 }
 
+// max_iter <= 0 / tol_deg < 0: the context's options
 int refine_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int P,
                  const double *seeds, const double *pcs, double *quats, float *peak, int *iters,
-                 cudaStream_t st, const int *select = nullptr, bool patterns_ready = false) {
+                 cudaStream_t st, const int *select = nullptr, bool patterns_ready = false,
+                 int max_iter = 0, double tol_deg = -1.0) {
+    if (max_iter <= 0) max_iter = ctx->opt.max_iter;
+    if (tol_deg < 0.0) tol_deg = ctx->opt.tol_deg;
     const xcf_geometry *g = &lib->geom;
     Crop c;
     crop_of(g, 256, &c, lib->native);
@@ -348,7 +358,7 @@ int refine_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, in
         XCF_CHECK(cudaMemcpyAsync(quats, seeds, sizeof(double) * 4 * P, cudaMemcpyDeviceToDevice, st),
                   "copy seeds");
     XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_init_refine(degen, select, P, active, iters, peak, st), "init");
-    for (int it = 0; it < ctx->opt.max_iter; ++it) {
+    for (int it = 0; it < max_iter; ++it) {
         // X / Y: shift of the template at the current orientation
         XCF_LAUNCH(XCF_STAGE_PROJECT, st, launch_project(lib->master, lib->M, quats, pcs, active, P, pj, img, st),
                    "project");
@@ -365,7 +375,7 @@ int refine_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, in
                    launch_logpolar(yt, active, P, n, r.nr, r.neta, (float)r.rmin, (float)r.rmax, lpt, st),
                    "logpolar templates");
         XCF_LAUNCH(XCF_STAGE_UPDATE, st,
-                   launch_eta_update(lpt, lpp, r.nr, r.neta, r.windows, quats, q1, alpha, ctx->opt.tol_deg, active, iters,
+                   launch_eta_update(lpt, lpp, r.nr, r.neta, r.windows, quats, q1, alpha, tol_deg, active, iters,
                                      quats, P, st),
                    "z update");
     }
@@ -692,8 +702,8 @@ int xcf_library_info(const xcf_library *lib, int32_t *T, int32_t *N, const float
     return XCF_OK;
 }
 
-int xcf_index(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, int32_t *best,
-              float *peak, float *shift, void *stream) {
+int xcf_index(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, const double *pcs,
+              int32_t *best, float *peak, float *shift, void *stream) {
     int rc = check_lib(ctx, lib, true);
     if (rc) return rc;
     if (P == 0) return XCF_OK;
@@ -703,7 +713,7 @@ int xcf_index(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32
     for (int p0 = 0; p0 < P; p0 += kChunk) {
         const int np = P - p0 < kChunk ? P - p0 : kChunk;
         if ((rc = index_chunk(ctx, lib, patterns + img * p0, np, best + p0, peak + p0, shift + 2 * (size_t)p0,
-                              nullptr, (cudaStream_t)stream)))
+                              nullptr, (cudaStream_t)stream, nullptr, pcs ? pcs + 3 * (size_t)p0 : nullptr)))
             return rc;
     }
     return XCF_OK;
@@ -727,13 +737,15 @@ int xcf_correlate_all(xcf_ctx *ctx, const xcf_library *lib, const float *pattern
 }
 
 int xcf_refine(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int32_t P, const double *seeds,
-               const double *pcs, double *quats, float *peak, int32_t *iters, void *stream) {
+               const double *pcs, int32_t max_iter, double tol_deg, double *quats, float *peak, int32_t *iters,
+               void *stream) {
     int rc = check_lib(ctx, lib);
     if (rc) return rc;
     if (P == 0) return XCF_OK;
     if (!patterns || !seeds || !quats || !peak || !iters || P < 0)
         return fail(ctx, XCF_ERR_ARG, "xcf_refine: bad argument");
     if (!lib->master) return fail(ctx, XCF_ERR_ARG, "xcf_refine: library has no master pattern");
+    if (max_iter > 1000) return fail(ctx, XCF_ERR_ARG, "xcf_refine: max_iter above 1000");
     const Resolved r = resolve(ctx->opt, lib->N);
     if (r.neta < 8 || r.neta > 1024 || (r.neta & (r.neta - 1)) || r.nr < 1 || r.rmin <= 0 ||
         r.rmax <= r.rmin || r.rmax > lib->N / 2.0 - 1.0)
@@ -744,7 +756,7 @@ int xcf_refine(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int3
         const int np = P - p0 < kChunk ? P - p0 : kChunk;
         if ((rc = refine_chunk(ctx, lib, patterns + img * p0, np, seeds + 4 * (size_t)p0,
                                pcs ? pcs + 3 * (size_t)p0 : nullptr, quats + 4 * (size_t)p0, peak + p0,
-                               iters + p0, (cudaStream_t)stream)))
+                               iters + p0, (cudaStream_t)stream, nullptr, false, max_iter, tol_deg)))
             return rc;
     }
     return XCF_OK;
@@ -776,7 +788,7 @@ int xcf_index_refine(xcf_ctx *ctx, const xcf_library *lib, const float *patterns
         const int np = P - p0 < kChunk ? P - p0 : kChunk;
         double *seeds;
         if ((rc = index_chunk(ctx, lib, patterns + img * p0, np, best + p0, peak + p0, shift + 2 * (size_t)p0,
-                              nullptr, st)))
+                              nullptr, st, nullptr, pcs ? pcs + 3 * (size_t)p0 : nullptr)))
             return rc;
         if ((rc = scratch_t(ctx, S_SEEDS, (size_t)np * 4, &seeds))) return rc;
         XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_gather_seeds(lib->quats, best + p0, np, seeds, st), "seeds");
@@ -850,7 +862,7 @@ int xcf_index_refine_host(xcf_ctx *ctx, const xcf_library *lib, const float *pat
         if (e == cudaSuccess && pcs)
             e = cudaMemcpyAsync(dpcs, pcs + 3 * (size_t)p0, sizeof(double) * 3 * np, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) { status = cuda_fail(ctx, e, "H2D"); break; }
-        if ((status = index_chunk(ctx, lib, dpat, np, dbest, dpeak, dshift, nullptr, st))) break;
+        if ((status = index_chunk(ctx, lib, dpat, np, dbest, dpeak, dshift, nullptr, st, nullptr, dpcs))) break;
         e = launch_gather_seeds(lib->quats, dbest, np, dseeds, st);
         if (e != cudaSuccess) { status = cuda_fail(ctx, e, "seeds"); break; }
         ctx->launches[XCF_STAGE_OTHER] += 1;
@@ -867,6 +879,40 @@ int xcf_index_refine_host(xcf_ctx *ctx, const xcf_library *lib, const float *pat
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
     return status;
+}
+
+int xcf_fp32_fma_rate(xcf_ctx *ctx, double *tflops, double *ms, void *stream) {
+    if (!ctx || !tflops) return XCF_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    float *sink;
+    int rc;
+    if ((rc = scratch_t(ctx, S_PROBE, 1, &sink))) return rc;
+    const int threads = 1024, blocks = 4 * ctx->num_sms, iters = 4096;
+    cudaEvent_t a = nullptr, b = nullptr;
+    XCF_CHECK(cudaEventCreate(&a), "event");
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return fail(ctx, XCF_ERR_CUDA, "xcf_fp32_fma_rate: event");
+    }
+    cudaError_t e = launch_fma_rate(blocks, threads, iters / 8, sink, st);   // warm-up
+    float best = 0.f;
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+        float t = 0.f;
+        e = cudaEventRecord(a, st);
+        if (e == cudaSuccess) e = launch_fma_rate(blocks, threads, iters, sink, st);
+        if (e == cudaSuccess) e = cudaEventRecord(b, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+        if (e == cudaSuccess && (best == 0.f || t < best)) best = t;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "xcf_fp32_fma_rate");
+    ctx->launches[XCF_STAGE_OTHER] += 4;
+    *tflops = fma_rate_flops(blocks, threads, iters) / (best * 1e-3) / 1e12;
+    if (ms) *ms = best;
+    return XCF_OK;
 }
 
 int xcf_set_scratch_limit(xcf_ctx *ctx, uint64_t bytes) {

@@ -333,6 +333,17 @@ __global__ void k_update_xy(const double *__restrict__ qs, const float *__restri
     qstore(q1s + 4 * (size_t)p, rotate_in_detector(qload(qs + 4 * (size_t)p), R, alpha));
 }
 
+// per-pattern pattern centre: a change of (pcx, pcy) translates the gnomonic
+// screen content by (dpcx W, dpcy H) px, so that part of the measured shift is
+// the pattern centre's and the rest the orientation's
+__global__ void k_shift_pc(const double *__restrict__ pcs, double pcx, double pcy, int W, int H,
+                           const int *__restrict__ best, int P, float *__restrict__ shift) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P || best[p] < 0) return;
+    shift[2 * (size_t)p] = (float)((double)shift[2 * (size_t)p] - (pcs[3 * (size_t)p] - pcx) * W);
+    shift[2 * (size_t)p + 1] = (float)((double)shift[2 * (size_t)p + 1] - (pcs[3 * (size_t)p + 1] - pcy) * H);
+}
+
 __global__ void k_gather_seeds(const double *__restrict__ lib_quats, const int *__restrict__ best, int P,
                                double *__restrict__ seeds) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -477,6 +488,13 @@ cudaError_t launch_gather_seeds(const double *lib_quats, const int *best, int P,
                                 cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
     k_gather_seeds<<<(P + 127) / 128, 128, 0, st>>>(lib_quats, best, P, seeds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shift_pc(const double *pcs, double pcx, double pcy, int W, int H, const int *best, int P,
+                            float *shift, cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    k_shift_pc<<<(P + 127) / 128, 128, 0, st>>>(pcs, pcx, pcy, W, H, best, P, shift);
     return cudaGetLastError();
 }
 

@@ -108,6 +108,8 @@ cudaError_t launch_eta_update(const float *lpT, const float *lpP, int nr, int ne
 cudaError_t launch_gather_seeds(const double *lib_quats, const int *best, int P, double *seeds,
                                 cudaStream_t st);
 // select (nullable): patterns with select[p] == 0 are not refined and their outputs are left untouched
+cudaError_t launch_shift_pc(const double *pcs, double pcx, double pcy, int W, int H, const int *best, int P,
+                            float *shift, cudaStream_t st);
 cudaError_t launch_init_refine(const int *degen, const int *select, int P, int *active, int *iters, float *peak,
                                cudaStream_t st);
 cudaError_t launch_copy_active_peak(const float *src, const int *active, int P, float *dst,
@@ -186,3 +188,7 @@ cudaError_t launch_fallback_flags(const float *peak, const int *degen, int P, fl
 cudaError_t launch_fallback_mask(const int *degen, const int *fb, int P, int *mask, cudaStream_t st);
 cudaError_t launch_fallback_seeds(const int *fb, const int *best, const double *lib_q, const double *cur, int P,
                                   double *seeds, cudaStream_t st);
+
+// FP32 FMA rate probe (k_peak.cu): flops of one launch of the given shape
+cudaError_t launch_fma_rate(int blocks, int threads, int iters, float *sink, cudaStream_t st);
+double fma_rate_flops(int blocks, int threads, int iters);

@@ -7,7 +7,13 @@
 // xcf_index_noalloc runs exactly the kernels of xcf_index, but keeps its
 // scratch (pattern spectra, degeneracy flags, best-template keys) in the
 // fixed array below, compiled into the library.  Every GPU that loads the
-// library holds this array until the process exits.
+// library holds this array until the process exits.  CUDA loads a library's
+// modules lazily by default, so the array (with this file's small module) is
+// committed on a device by the first call there, not at library load: that
+// first call must come before another allocator reserves the GPU, and before
+// any stream capture.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "internal.h"
@@ -22,7 +28,37 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
-void *g_addr[kMaxDevices] = {};   // device address of g_noalloc_scratch, per device
+// device address of g_noalloc_scratch per device, and the CUDA context it was
+// looked up in (a device reset or a new primary context loads the module
+// again, possibly elsewhere: the address is then looked up anew)
+void *g_addr[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};
+
+// unique id of the current CUDA context (0 if it cannot be had)
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {   // under g_mutex
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<GetCurrent>(f1);
+            get_id = reinterpret_cast<GetId>(f2);
+        }
+        cudaGetLastError();
+        looked_up = true;
+    }
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 size_t round_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -33,15 +69,17 @@ size_t scratch_bytes(int n, long P) {
            round_up(sizeof(unsigned long long) * P);
 }
 
-// One-time set-up per device (the device is current): the host-side name of
-// the array is only a stand-in, so look up its device address.
+// One-time set-up per device and CUDA context (the device is current): the
+// host-side name of the array is only a stand-in, so look up its device
+// address (which loads this file's module on the first call).
 int device_scratch(xcf_ctx *ctx, void **out) {
     if (ctx->device < 0 || ctx->device >= kMaxDevices) {
         ctx->err = "xcf_index_noalloc: device ordinal out of range";
         return XCF_ERR_ARG;
     }
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_addr[ctx->device]) {
+    const unsigned long long id = current_context_id();
+    if (!g_addr[ctx->device] || id == 0 || id != g_ctx_id[ctx->device]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
@@ -50,6 +88,7 @@ int device_scratch(xcf_ctx *ctx, void **out) {
             return XCF_ERR_CUDA;
         }
         g_addr[ctx->device] = p;
+        g_ctx_id[ctx->device] = id;
     }
     *out = g_addr[ctx->device];
     return XCF_OK;
@@ -58,6 +97,27 @@ int device_scratch(xcf_ctx *ctx, void **out) {
 int cuda_error(xcf_ctx *ctx, cudaError_t e, const char *where) {
     ctx->err = std::string("xcf_index_noalloc: ") + where + ": " + cudaGetErrorString(e);
     return XCF_ERR_CUDA;
+}
+
+// one launch of `stage`: counted, and timed with an event pair when the
+// context's timing is on (as every other entry point's launches)
+template <class F>
+int launch(xcf_ctx *ctx, int stage, cudaStream_t st, F &&fn, const char *where) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (ctx->timing && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, st);
+    const cudaError_t e = fn();
+    if (e != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        return cuda_error(ctx, e, where);
+    }
+    ctx->launches[stage] += 1;
+    if (a && cudaEventCreate(&b) == cudaSuccess) {
+        cudaEventRecord(b, st);
+        ctx->recs.push_back({stage, a, b});
+    } else if (a) {
+        cudaEventDestroy(a);
+    }
+    return XCF_OK;
 }
 
 }  // namespace
@@ -127,23 +187,25 @@ extern "C" int xcf_index_noalloc(xcf_ctx *ctx, const xcf_library *lib, const flo
 
     // N = 256 runs on four-CTA clusters, which need no scratch beyond the spectra
     const bool c256 = n == 256;
-    cudaError_t e = c256 ? launch_prep_c256(patterns, P, a, sp, nullptr, degen, nullptr, st)
+    if ((rc = launch(ctx, XCF_STAGE_PREP, st, [&] {
+             return c256 ? launch_prep_c256(patterns, P, a, sp, nullptr, degen, nullptr, st)
                          : launch_prep(patterns, P, a, sp, nullptr, degen, nullptr, st);
-    if (e != cudaSuccess) return cuda_error(ctx, e, "prep");
+         }, "prep")))
+        return rc;
     // the array keeps the previous call's contents: the keys must start at 0
-    e = cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * P, st);
+    const cudaError_t e = cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * P, st);
     if (e != cudaSuccess) return cuda_error(ctx, e, "clear keys");
-    e = c256 ? launch_search_c256(search_spectra(lib), lib->T, sp, degen, P, keys, nullptr, nullptr, 0, st)
-             : launch_search(n, search_spectra(lib), lib->T, sp, degen, P, keys, nullptr, ctx->num_sms, st);
-    if (e != cudaSuccess) return cuda_error(ctx, e, "search");
-    e = launch_keys_to_best(keys, P, best, st);
-    if (e != cudaSuccess) return cuda_error(ctx, e, "keys_to_best");
-    e = c256 ? launch_pair_peak_c256(lib->spectra, best, sp, degen, nullptr, P, peak, shift, st)
-             : launch_pair_peak(n, lib->spectra, best, sp, degen, nullptr, P, peak, shift, st);
-    if (e != cudaSuccess) return cuda_error(ctx, e, "pair_peak");
-    ctx->launches[XCF_STAGE_PREP] += 1;
-    ctx->launches[XCF_STAGE_SEARCH] += 1;
-    ctx->launches[XCF_STAGE_OTHER] += 1;
-    ctx->launches[XCF_STAGE_PEAK] += 1;
-    return XCF_OK;
+    if ((rc = launch(ctx, XCF_STAGE_SEARCH, st, [&] {
+             return c256 ? launch_search_c256(search_spectra(lib), lib->T, sp, degen, P, keys, nullptr, nullptr, 0, st)
+                         : launch_search(n, search_spectra(lib), lib->T, sp, degen, P, keys, nullptr, ctx->num_sms,
+                                         st);
+         }, "search")))
+        return rc;
+    if ((rc = launch(ctx, XCF_STAGE_OTHER, st, [&] { return launch_keys_to_best(keys, P, best, st); },
+                     "keys_to_best")))
+        return rc;
+    return launch(ctx, XCF_STAGE_PEAK, st, [&] {
+        return c256 ? launch_pair_peak_c256(lib->spectra, best, sp, degen, nullptr, P, peak, shift, st)
+                    : launch_pair_peak(n, lib->spectra, best, sp, degen, nullptr, P, peak, shift, st);
+    }, "pair_peak");
 }

@@ -22,6 +22,7 @@ XCF_ERR_OOM = -3
 XCF_ERR_CUDA = -4
 XCF_ERR_TIMEOUT = -5
 XCF_ERR_UNIMPLEMENTED = -6
+XCF_NOALLOC_SCRATCH_BYTES = 16 << 20   # size of xcf_index_noalloc's fixed array
 
 
 class XcfError(RuntimeError):
@@ -75,9 +76,9 @@ _SIGS = {
                                   _P], C.c_int),
     "xcf_library_free": ([_P], C.c_int),
     "xcf_library_info": ([_P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_P)], C.c_int),
-    "xcf_index": ([_P, _P, _P, _I32, _P, _P, _P, _P], C.c_int),
+    "xcf_index": ([_P, _P, _P, _I32, _P, _P, _P, _P, _P], C.c_int),
     "xcf_correlate_all": ([_P, _P, _P, _I32, _P, _P], C.c_int),
-    "xcf_refine": ([_P, _P, _P, _I32, _P, _P, _P, _P, _P, _P], C.c_int),
+    "xcf_refine": ([_P, _P, _P, _I32, _P, _P, _I32, C.c_double, _P, _P, _P, _P], C.c_int),
     "xcf_disorientation": ([_P, _P, _P, _I32, _P, _P], C.c_int),
     "xcf_index_refine_host": ([_P, _P, _P, _I32, _P, _I32, _P, _P, _P, _P, _P, _P], C.c_int),
     "xcf_index_refine": ([_P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
@@ -104,6 +105,7 @@ _SIGS = {
     "xcf_net_adam": ([_P, _P, C.c_float, C.c_float, C.c_float, C.c_float, _P], C.c_int),
     "xcf_propose": ([_P, _P, _P, _I32, C.POINTER(xcf_geometry), _P, _P], C.c_int),
     "xcf_index_learned": ([_P, _P, _P, _P, _I32, _P, C.c_float, _P, _P, _P, _P, _P], C.c_int),
+    "xcf_fp32_fma_rate": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_double), _P], C.c_int),
     "xcf_set_scratch_limit": ([_P, C.c_uint64], C.c_int),
     "xcf_scratch_bytes": ([_P, C.POINTER(C.c_uint64)], C.c_int),
     "xcf_profile_enable": ([_P, C.c_int], C.c_int),
@@ -176,6 +178,31 @@ def _hptr(t, dtype, name, allow_none=False):
 
 def _stream():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+_PER_PATTERN = {"patterns": None, "best": 1, "peak": 1, "shift": 2, "pcs": 3, "seeds": 4, "quats": 4,
+                "iters": 1, "rpeak": 1, "peaks": 0}
+
+
+def _sizes(lib, P, **tensors):
+    """Element counts of a call's tensors against P and the library's
+    detector: patterns must hold exactly P x H x W values and every other
+    tensor at least P times its per-pattern count (an undersized output would
+    be written out of bounds on the device)."""
+    for name, t in tensors.items():
+        if t is None:
+            continue
+        per = _PER_PATTERN[name]
+        if per is None:
+            want = P * lib.geom.width * lib.geom.height
+            if t.numel() != want:
+                raise ValueError(f"{name} holds {t.numel()} values, expected {P} x {lib.geom.height} x "
+                                 f"{lib.geom.width} = {want}")
+        elif name == "peaks":
+            if t.numel() < P * lib.T:
+                raise ValueError(f"peaks holds {t.numel()} values, expected at least {P} x {lib.T}")
+        elif t.numel() < P * per:
+            raise ValueError(f"{name} holds {t.numel()} values, expected at least {P} x {per}")
 
 
 # ------------------------------------------------------------------ handles
@@ -290,13 +317,16 @@ def xcf_build_library_images(ctx: Context, images, quats, geom: xcf_geometry, ma
     return Library(h, geom, quats)
 
 
-def xcf_index(ctx: Context, lib: Library, patterns, best=None, peak=None, shift=None):
+def xcf_index(ctx: Context, lib: Library, patterns, best=None, peak=None, shift=None, pcs=None):
+    """pcs: per-pattern pattern centres [P, 3] float64 (None: the library's)."""
     P = patterns.shape[0]
     dev = patterns.device
     best = torch.empty(P, dtype=torch.int32, device=dev) if best is None else best
     peak = torch.empty(P, dtype=torch.float32, device=dev) if peak is None else peak
     shift = torch.empty((P, 2), dtype=torch.float32, device=dev) if shift is None else shift
+    _sizes(lib, P, patterns=patterns, best=best, peak=peak, shift=shift, pcs=pcs)
     _check(load().xcf_index(ctx.handle, lib.handle, _ptr(patterns, torch.float32, "patterns"), P,
+                            _ptr(pcs, torch.float64, "pcs", True),
                             _ptr(best, torch.int32, "best"), _ptr(peak, torch.float32, "peak"),
                             _ptr(shift, torch.float32, "shift"), _stream()), ctx.handle)
     return best, peak, shift
@@ -305,19 +335,24 @@ def xcf_index(ctx: Context, lib: Library, patterns, best=None, peak=None, shift=
 def xcf_correlate_all(ctx: Context, lib: Library, patterns, peaks=None):
     P = patterns.shape[0]
     peaks = torch.empty((P, lib.T), dtype=torch.float32, device=patterns.device) if peaks is None else peaks
+    _sizes(lib, P, patterns=patterns, peaks=peaks)
     _check(load().xcf_correlate_all(ctx.handle, lib.handle, _ptr(patterns, torch.float32, "patterns"), P,
                                     _ptr(peaks, torch.float32, "peaks"), _stream()), ctx.handle)
     return peaks
 
 
-def xcf_refine(ctx: Context, lib: Library, patterns, seeds, pcs=None, quats=None, peak=None, iters=None):
+def xcf_refine(ctx: Context, lib: Library, patterns, seeds, pcs=None, quats=None, peak=None, iters=None,
+               max_iter=0, tol_deg=-1.0):
+    """max_iter <= 0 / tol_deg < 0: the context's options."""
     P = patterns.shape[0]
     dev = patterns.device
     quats = torch.empty((P, 4), dtype=torch.float64, device=dev) if quats is None else quats
     peak = torch.empty(P, dtype=torch.float32, device=dev) if peak is None else peak
     iters = torch.empty(P, dtype=torch.int32, device=dev) if iters is None else iters
+    _sizes(lib, P, patterns=patterns, seeds=seeds, pcs=pcs, quats=quats, peak=peak, iters=iters)
     _check(load().xcf_refine(ctx.handle, lib.handle, _ptr(patterns, torch.float32, "patterns"), P,
                              _ptr(seeds, torch.float64, "seeds"), _ptr(pcs, torch.float64, "pcs", True),
+                             int(max_iter), float(tol_deg),
                              _ptr(quats, torch.float64, "quats"), _ptr(peak, torch.float32, "peak"),
                              _ptr(iters, torch.int32, "iters"), _stream()), ctx.handle)
     return quats, peak, iters
@@ -339,6 +374,7 @@ def xcf_index_refine(ctx: Context, lib: Library, patterns, pcs=None, out=None):
         out = dict(best=torch.empty(P, dtype=torch.int32, device=d), peak=torch.empty(P, device=d),
                    shift=torch.empty((P, 2), device=d), quats=torch.empty((P, 4), dtype=torch.float64, device=d),
                    rpeak=torch.empty(P, device=d), iters=torch.empty(P, dtype=torch.int32, device=d))
+    _sizes(lib, P, patterns=patterns, pcs=pcs, **out)
     _check(load().xcf_index_refine(
         ctx.handle, lib.handle, _ptr(patterns, torch.float32, "patterns"), P, _ptr(pcs, torch.float64, "pcs", True),
         _ptr(out["best"], torch.int32, "best"), _ptr(out["peak"], torch.float32, "peak"),
@@ -356,6 +392,7 @@ def xcf_index_refine_host(ctx: Context, lib: Library, patterns, pcs=None, chunk=
         mk = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=pin)
         out = dict(best=mk((P,), torch.int32), peak=mk((P,), torch.float32), shift=mk((P, 2), torch.float32),
                    quats=mk((P, 4), torch.float64), rpeak=mk((P,), torch.float32), iters=mk((P,), torch.int32))
+    _sizes(lib, P, patterns=patterns, pcs=pcs, **out)
     _check(load().xcf_index_refine_host(
         ctx.handle, lib.handle, _hptr(patterns, torch.float32, "patterns"), P,
         _hptr(pcs, torch.float64, "pcs", True), int(chunk), _hptr(out["best"], torch.int32, "best"),
@@ -363,6 +400,13 @@ def xcf_index_refine_host(ctx: Context, lib: Library, patterns, pcs=None, chunk=
         _hptr(out["quats"], torch.float64, "quats"), _hptr(out["rpeak"], torch.float32, "rpeak"),
         _hptr(out["iters"], torch.int32, "iters")), ctx.handle)
     return out
+
+
+def xcf_fp32_fma_rate(ctx: Context):
+    """Measured FP32 FMA throughput of the device -> (TFLOP/s, ms per launch)."""
+    t, ms = C.c_double(), C.c_double()
+    _check(load().xcf_fp32_fma_rate(ctx.handle, C.byref(t), C.byref(ms), _stream()), ctx.handle)
+    return t.value, ms.value
 
 
 def xcf_set_scratch_limit(ctx: Context, nbytes: int):
@@ -395,6 +439,7 @@ def xcf_index_noalloc(ctx: Context, lib: Library, patterns, best, peak, shift):
     """xcf_index without any device allocation by the library (its scratch is
     a fixed array compiled into the library).  Outputs must be preallocated."""
     P = patterns.shape[0]
+    _sizes(lib, P, patterns=patterns, best=best, peak=peak, shift=shift)
     _check(load().xcf_index_noalloc(ctx.handle, lib.handle, _ptr(patterns, torch.float32, "patterns"), P,
                                     _ptr(best, torch.int32, "best"), _ptr(peak, torch.float32, "peak"),
                                     _ptr(shift, torch.float32, "shift"), _stream()), ctx.handle)
@@ -503,6 +548,7 @@ def xcf_refine_best(ctx: Context, lib: Library, patterns, best, pcs=None, out=No
         out = (torch.empty((P, 4), dtype=torch.float64, device=d), torch.empty(P, device=d),
                torch.empty(P, dtype=torch.int32, device=d))
     q, pk, it = out
+    _sizes(lib, P, patterns=patterns, best=best, pcs=pcs, quats=q, peak=pk, iters=it)
     _check(load().xcf_refine_best(ctx.handle, lib.handle, _ptr(patterns, torch.float32, "patterns"), P,
                                   _ptr(best, torch.int32, "best"), _ptr(pcs, torch.float64, "pcs", True),
                                   _ptr(q, torch.float64, "quats"), _ptr(pk, torch.float32, "peak"),

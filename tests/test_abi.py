@@ -92,6 +92,26 @@ def test_noalloc_limits_cover_every_side():
         assert xcf.xcf_noalloc_max_patterns(n) == fits(n) > 0
     for n in (0, 8, 100, 200, 512):
         assert xcf.xcf_noalloc_max_patterns(n) == 0
+    m = re.search(r"#define XCF_NOALLOC_SCRATCH_BYTES \((\d+)u << (\d+)\)", open(HEADER).read())
+    assert xcf.XCF_NOALLOC_SCRATCH_BYTES == int(m.group(1)) << int(m.group(2)) == 16 << 20
+
+
+def test_binding_checks_sizes_before_calling_c():
+    """Host-only: a tensor whose element count does not match P and the
+    library's detector raises ValueError before any call into the library."""
+    import torch
+    from paper_1807_11313_gb300 import xcf
+
+    class _Lib:
+        geom = xcf.geometry(64, 48)
+        T = 7
+    lib = _Lib()
+    xcf._sizes(lib, 3, patterns=torch.empty(3, 48, 64), best=torch.empty(3), shift=torch.empty(3, 2),
+               pcs=torch.empty(3, 3), peaks=torch.empty(3, 7))
+    for bad in (dict(patterns=torch.empty(3, 64, 64)), dict(best=torch.empty(2)), dict(shift=torch.empty(3)),
+                dict(pcs=torch.empty(3, 2)), dict(quats=torch.empty(3, 3)), dict(peaks=torch.empty(3, 6))):
+        with pytest.raises(ValueError):
+            xcf._sizes(lib, 3, **bad)
 
 
 def test_network_parameter_count_matches_oracle(orc):

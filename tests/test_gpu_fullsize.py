@@ -50,7 +50,8 @@ def test_sampled_patterns_match_oracle(orc, run):
     sel = np.array([0, 1, 4321, 5000, 7777, 9999])
     St, _, _ = orc.prep_many(orc.project_many(wl["master"], wl["lib_q"], wl["pc"], n))
     Sp, _, deg = orc.prep_many(pats[sel])
-    ob, opk, osh, allp = orc.index(St, Sp, deg, want_all=True)
+    # the map's per-pattern centres: shifts relative to each pattern's own centre
+    ob, opk, osh, allp = orc.index(St, Sp, deg, want_all=True, pcs=wl["pcs"][sel], geom=(n, n, *wl["pc"][:2]))
     del St
     best = r["best"][sel]
     for i, p in enumerate(sel):

@@ -163,6 +163,44 @@ def test_index_matches_oracle(px, ctx, orc, n, T, P):
     lib.close()
 
 
+@pytest.mark.parametrize("n,W,H", [(64, 64, 64), (128, 150, 140)])
+def test_index_per_pattern_pcs_matches_oracle(px, ctx, orc, n, W, H):
+    """Per-pattern pattern centres (a map whose centre drifts): indices and
+    peaks are the library-centre search's, the shift is reported relative to
+    the template at the pattern's own centre; against the oracle at the
+    stated bounds, on a cropped rectangular detector too."""
+    P, T = 10, 40
+    master = synth.master_pattern("bcc", 1024)
+    lq = synth.random_quaternions(T, 300 + n)
+    g = px.geometry(W, H, PC0)
+    cn, ox, oy, pcc = orc.crop(W, H, PC0)
+    assert cn == n
+    timgs = np.zeros((T, H, W), np.float32)
+    timgs[:, oy:oy + n, ox:ox + n] = orc.project_many(master, lq, pcc, n)
+    pcs = synth.jittered_pcs(P, 301 + n, jitter=0.03)
+    q = synth.perturb(lq[np.arange(P) * 3 % T], 1.5, 302)
+    full = np.zeros((P, H, W), np.float32)
+    for i in range(P):
+        _, _, _, pci = orc.crop(W, H, pcs[i])
+        full[i, oy:oy + n, ox:ox + n] = orc.project(master, q[i], pci, n)
+    pimgs = synth.add_noise(full, pcs, 300.0, 303)
+    lib = px.xcf_build_library_images(ctx, dev(timgs), dev(lq), g)
+    best, peak, shift = (host(t) for t in px.xcf_index(ctx, lib, dev(pimgs), pcs=dev(pcs)))
+    b0, p0, s0 = (host(t) for t in px.xcf_index(ctx, lib, dev(pimgs)))
+    St, _, _ = orc.prep_many(timgs[:, oy:oy + n, ox:ox + n])
+    Sp, _, deg = orc.prep_many(pimgs[:, oy:oy + n, ox:ox + n])
+    ob, opk, osh, allp = orc.index(St, Sp, deg, want_all=True, pcs=pcs, geom=(W, H, PC0[0], PC0[1]))
+    _check_index(ob, opk, allp, best, peak)
+    same = best == ob
+    np.testing.assert_allclose(peak[same], opk[same], rtol=1e-4, atol=1e-6)
+    np.testing.assert_allclose(shift[same], osh[same], atol=2e-3)
+    # the centres change only the shift, by the translation they produce
+    assert np.array_equal(best, b0) and np.array_equal(peak, p0)
+    move = np.stack([(pcs[:, 0] - PC0[0]) * W, (pcs[:, 1] - PC0[1]) * H], axis=1)
+    np.testing.assert_allclose(s0 - shift, move, atol=1e-4)
+    lib.close()
+
+
 def test_build_library_matches_oracle_spectra(px, ctx, orc):
     n = 128
     master = synth.master_pattern("bcc", 1024)
@@ -200,10 +238,49 @@ def test_index_chunks_and_empty(px, orc):
     c.close()
 
 
+def _config1_inputs(orc):
+    """The 64 x 64 parity configuration: diamond-cubic master on a
+    2 x 1024^2 grid, 300 random templates, 16 random test patterns with
+    Poisson noise (peak 200) plus background, seed 0."""
+    n = 64
+    master = synth.master_pattern("diamond", 1024)
+    lq = synth.random_quaternions(300, 0)
+    tq = synth.random_quaternions(16, 1)
+    pcs = np.broadcast_to(np.asarray(PC0), (16, 3))
+    pimgs = synth.add_noise(orc.project_many(master, tq, PC0, n), pcs, 200.0, 2)
+    return n, master, lq, pimgs
+
+
+def test_config1_parity_same_templates(px, ctx, orc):
+    """The search itself at the parity configuration, at the stated bounds:
+    both sides correlate the same FP32 template images (the oracle's FP64
+    projection rounded to FP32), so only the FP32 transforms differ.  Indices
+    bit-exact outside ties (oracle peaks within 2e-5 relative), peaks 1e-4
+    relative, shifts 2e-3 px; every per-template peak 1e-4 relative."""
+    n, master, lq, pimgs = _config1_inputs(orc)
+    timgs = orc.project_many(master, lq, PC0, n).astype(np.float32)
+    g = px.geometry(n, n, PC0)
+    lib = px.xcf_build_library_images(ctx, dev(timgs), dev(lq), g, master=dev(master))
+    best, peak, shift = (host(t) for t in px.xcf_index(ctx, lib, dev(pimgs)))
+    allg = host(px.xcf_correlate_all(ctx, lib, dev(pimgs)))
+    St, _, _ = orc.prep_many(timgs)
+    Sp, _, deg = orc.prep_many(pimgs)
+    ob, opk, osh, allp = orc.index(St, Sp, deg, want_all=True)
+    _check_index(ob, opk, allp, best, peak, rel_tie=2e-5)
+    same = best == ob
+    assert same.sum() >= 15
+    np.testing.assert_allclose(peak[same], opk[same], rtol=1e-4)
+    np.testing.assert_allclose(shift[same], osh[same], atol=2e-3)
+    np.testing.assert_allclose(allg, allp, rtol=1e-4, atol=1e-6)
+    lib.close()
+
+
 def test_config1_parity(px, ctx, orc):
-    """Plain XCF search at the 64 x 64 parity configuration: diamond-cubic
-    master on a 2 x 1024^2 grid, 300 random templates, 16 random test
-    patterns with Poisson noise (peak 200) plus background, seed 0."""
+    """End to end at the parity configuration: the GPU library comes from the
+    GPU's own FP32 projection, the oracle's from its FP64 projection, so the
+    comparison carries the projection's FP32 error (up to ~1e-3 of the
+    master's range at single pixels near band edges) into the correlation.
+    Bounds: ties 1e-4 relative, peaks 2e-4 relative, shifts 5e-3 px."""
     n = 64
     master = synth.master_pattern("diamond", 1024)
     lq = synth.random_quaternions(300, 0)
@@ -284,7 +361,7 @@ def test_host_pipeline_matches_device_path(px, orc):
     lib = px.xcf_build_library(c, dev(master), dev(lq), px.geometry(n, n, PC0))
     out = px.xcf_index_refine_host(c, lib, torch.from_numpy(pimgs).pin_memory(),
                                    pcs=torch.from_numpy(pcs), chunk=16)
-    best, peak, shift = (host(t) for t in px.xcf_index(c, lib, dev(pimgs)))
+    best, peak, shift = (host(t) for t in px.xcf_index(c, lib, dev(pimgs), pcs=dev(pcs)))
     seeds = dev(lq[np.maximum(best, 0)])
     q, rpk, it = (host(t) for t in px.xcf_refine(c, lib, dev(pimgs), seeds, pcs=dev(pcs)))
     assert np.array_equal(out["best"].numpy(), best)

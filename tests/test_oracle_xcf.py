@@ -113,3 +113,39 @@ def test_index_search_and_ties(orc):
     # per-template peak is the maximum of the surface
     r = orc.xcf_surface(St0[1], Sp[0])
     assert allp[0, 1] == r.max()
+
+
+def test_per_pattern_pc_is_a_translation_and_is_taken_out(orc):
+    """A pattern whose pattern centre differs from the library's by
+    (dx, dy) in (pcx, pcy) is the library projection translated by
+    (dx W, dy H) px (the gnomonic ray of each pixel moves with the centre):
+    the raw search shift recovers that translation and the per-pattern
+    centre correction leaves only the orientation's part, here zero."""
+    import synth
+    n = 64
+    pc0 = np.array([0.5, 0.5, 0.6])
+    master = synth.master_pattern("bcc", 512)
+    lq = synth.random_quaternions(5, 71)
+    St, _, _ = orc.prep_many(orc.project_many(master, lq, pc0, n))
+    moves = np.array([[3, -2], [-5, 4], [0, 6]])
+    pcs = np.array([pc0 + [mx / n, my / n, 0.0] for mx, my in moves])
+    pats = np.stack([orc.project(master, lq[t], pcs[i], n) for i, t in enumerate([2, 4, 0])])
+    # the translation itself: interior pixels equal the library projection rolled by the move
+    ref = orc.project(master, lq[2], pc0, n)
+    np.testing.assert_allclose(pats[0][8:-8, 8:-8], np.roll(ref, (-2, 3), axis=(0, 1))[8:-8, 8:-8], atol=1e-12)
+    Sp, _, deg = orc.prep_many(pats)
+    b_raw, _, sh_raw, _ = orc.index(St, Sp, deg)
+    b, pk, sh, _ = orc.index(St, Sp, deg, pcs=pcs, geom=(n, n, pc0[0], pc0[1]))
+    assert b.tolist() == b_raw.tolist() == [2, 4, 0]
+    # the integer peak is the move exactly; the fixed window (the content moves
+    # under it) and the parabola leave a sub-pixel bias of ~0.02 px per px moved
+    assert np.array_equal(np.round(sh_raw), moves)
+    np.testing.assert_allclose(sh_raw, moves, atol=0.2)
+    np.testing.assert_allclose(sh, 0.0, atol=0.2)
+    np.testing.assert_allclose(sh_raw - sh, moves, atol=1e-12)
+    # the library's own centre changes nothing; degenerate patterns keep zero
+    b2, _, sh2, _ = orc.index(St, Sp, deg, pcs=np.tile(pc0, (3, 1)), geom=(n, n, pc0[0], pc0[1]))
+    np.testing.assert_array_equal(sh2, sh_raw)
+    Sz, _, dz = orc.prep_many(np.zeros((1, n, n)))
+    _, _, shz, _ = orc.index(St, Sz, dz, pcs=pcs[:1], geom=(n, n, pc0[0], pc0[1]))
+    assert np.all(shz == 0.0)

@@ -38,6 +38,31 @@ def _compare(ref, got):
     np.testing.assert_allclose(gs, rs, atol=2e-3)
 
 
+def test_first_call_commits_at_most_the_array(px):
+    """The first call on the device loads the module holding the fixed array
+    (CUDA loads modules lazily) and so commits the array there; it may take
+    no more than the array plus a small slack for the module itself.  Every
+    other kernel of the call is loaded beforehand by an ordinary xcf_index."""
+    n, T, P = 64, 5, 8
+    timgs, pats = _inputs(n, T, P, 7)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ctx = px.Context()
+    lib = px.xcf_build_library_images(ctx, dev(timgs), dev(synth.random_quaternions(T, 8)), px.geometry(n, n))
+    pd = dev(pats)
+    ref = px.xcf_index(ctx, lib, pd)
+    out = (torch.empty(P, dtype=torch.int32, device="cuda"), torch.empty(P, device="cuda"),
+           torch.empty((P, 2), device="cuda"))
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    px.xcf_index_noalloc(ctx, lib, pd, *out)
+    torch.cuda.synchronize()
+    taken = free0 - torch.cuda.mem_get_info()[0]
+    assert taken <= px.xcf.XCF_NOALLOC_SCRATCH_BYTES + (8 << 20), taken
+    _compare(ref, out)
+    lib.close()
+    ctx.close()
+
+
 @pytest.mark.parametrize("n", [128, 64, 96, 160, 256])
 def test_noalloc_matches_index_on_consecutive_calls(px, n):
     T = 37
