@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--map", type=int, default=100, help="map side (patterns = map^2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="plain form: skip the precision / learned / batched sub-records of the line")
+    ap.add_argument("--form-steps", type=int, default=3, help="timed steps of each sub-record form")
     ap.add_argument("--cpu-sample", type=int, default=0, help="patterns in the CPU sample (0: auto)")
     ap.add_argument("--form", default="plain",
                     choices=["plain", "precision", "batched", "learned", "ndp", "fwhm", "so3"],
@@ -259,7 +262,45 @@ def _noisy_on_device(torch, clean, pcs, peak, gen):
     return torch.poisson(lam, generator=gen)
 
 
-def run_precision(args, px, torch, dev, rank, world, local, dist):
+def cpu_precision_rate(wl, pats, pcs, P_total, t_sub=256):
+    """The FP64 oracle on a bounded sample of the precision workload: the
+    library build and the screen on t_sub evenly spaced templates (both
+    linear in the template count, scaled to the whole library), then for each
+    sample pattern its top-k candidates of that screen rescored by the XCF
+    (one pattern per call, timed on one core and divided by the core count:
+    patterns are independent) and the refinement (max_iter iterations)."""
+    import oracle
+    n, T, k = wl["n"], len(wl["lib_q"]), wl["k"]
+    threads = oracle.num_threads()
+    sub = np.linspace(0, T - 1, min(T, t_sub)).astype(np.int64)
+    t0 = time.perf_counter()
+    St, yt, _ = oracle.prep_many(oracle.project_many(wl["master"], wl["lib_q"][sub], wl["pc"], n), want_spatial=True)
+    t_lib = (time.perf_counter() - t0) * T / len(sub)
+    t0 = time.perf_counter()
+    Sp, yp, deg = oracle.prep_many(pats, want_spatial=True)
+    t_prep = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sc = oracle.screen(yp, yt, bf16=True)
+    t_screen = (time.perf_counter() - t0) * T / len(sub)
+    kk = min(k, len(sub))
+    cand = np.argsort(-sc, axis=1, kind="stable")[:, :kk]
+    t0 = time.perf_counter()
+    best = np.array([cand[p][max(0, int(oracle.index(St[cand[p]], Sp[p:p + 1], deg[p:p + 1])[0][0]))]
+                     for p in range(len(pats))])
+    t_rescore = (time.perf_counter() - t0) / threads
+    t0 = time.perf_counter()
+    oracle.refine_many(wl["master"], pats, wl["lib_q"][sub][best], pcs, max_it=wl["max_iter"], tol_deg=1e-3)
+    t_refine = time.perf_counter() - t0
+    S = len(pats)
+    per = t_lib / P_total + (t_prep + t_screen + t_rescore + t_refine) / S
+    sample = (f"{S} of the {P_total} patterns: pre-processing, BF16-rounded screen against {len(sub)} of the {T} "
+              f"templates scaled to {T} ({t_screen:.1f} s), top-{kk} XCF rescore ({t_rescore:.1f} s, one core / "
+              f"{threads}), refinement ({t_refine:.1f} s); library build of {len(sub)} templates scaled to {T} "
+              f"({t_lib:.0f} s) amortised over {P_total}")
+    return {"value": 1.0 / per, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+
+
+def run_precision(args, px, torch, dev, rank, world, local, dist, emit=True):
     P = args.patterns or 50000
     wl = synth.config_precision_256(seed=rank, P=P)
     n, T, k = wl["n"], len(wl["lib_q"]), wl["k"]
@@ -322,12 +363,56 @@ def run_precision(args, px, torch, dev, rank, world, local, dist):
     s_ms, s_n = prof["screen"]
     flops_step = 2.0 * P * T * n * n
     achieved = flops_step * args.steps / (s_ms / 1e3) / 1e12
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": tensor_peak, "unit": "TFLOP/s",
-                "frac": achieved / tensor_peak, "traffic": None, "kernel": "k_screen_tc",
-                "peak_basis": "measured sustained cuBLAS BF16 (MEASURED_PEAKS.json)" if pk else "fallback",
-                "screen_ms_per_launch": s_ms / max(s_n, 1), "launches_per_step": s_n / args.steps,
-                "stage_ms_per_step": {kk: v[0] / args.steps for kk, v in prof.items()}}
+    screen_roof = {"bound": "tensor", "achieved": achieved, "peak": tensor_peak, "unit": "TFLOP/s",
+                   "frac": achieved / tensor_peak, "traffic": None, "kernel": "k_screen_tc",
+                   "peak_basis": "measured sustained cuBLAS BF16 (MEASURED_PEAKS.json)" if pk else "fallback",
+                   "screen_ms_per_launch": s_ms / max(s_n, 1), "launches_per_step": s_n / args.steps}
+    # the dominant stage: the FP32 FFT rescore of the k candidates (k_search_c256, candidate-list mode)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = pk.get("sm_max_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
+    fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    r_ms = prof["search"][0] / args.steps
+    r_ach = P * k * flops_per_pair(n) / (r_ms / 1e3) / 1e12
+    stages = {kk: v[0] / args.steps for kk, v in prof.items()}
+    roofline = {"bound": "alu", "achieved": r_ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": r_ach / fp32_peak,
+                "traffic": None, "kernel": "k_search_c256 (rescore of the top-k candidates)",
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                "stage_share": r_ms / max(sum(stages.values()), 1e-9),
+                "stage_ms_per_step": stages, "secondary": {"screen": screen_roof}}
     value = whole_job_rate(P, args.steps, world, elapsed_ms)
+    e2e = None
+    if not args.no_e2e:
+        pats_h = pats_d.cpu().pin_memory()
+        pcs_h = pcs_d.cpu().pin_memory()
+        hout = (torch.empty(P, dtype=torch.int32, pin_memory=True), torch.empty((P, 4), dtype=torch.float64,
+                pin_memory=True), torch.empty(P, pin_memory=True), torch.empty(P, dtype=torch.int32, pin_memory=True))
+
+        def e2e_step():
+            pats_d.copy_(pats_h, non_blocking=True)
+            pcs_d.copy_(pcs_h, non_blocking=True)
+            step()
+            for h, o in zip(hout, (best_d, outq[0], outq[1], outq[2])):
+                h.copy_(o, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        e2e = {"value": whole_job_rate(P, args.steps, world, dt * 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(pats_h.numel() * 4 + pcs_h.numel() * 8),
+               "d2h_bytes_per_step": int(sum(h.numel() * h.element_size() for h in hout)),
+               "note": "patterns and PCs copied in from pinned host memory, outputs copied out, library built "
+                       "on the device from the resident master, every step"}
+        del pats_h
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        S = args.cpu_sample or oracle.num_threads()
+        cpu = cpu_precision_rate(wl, pats_d[:S].cpu().numpy(), wl["pcs"][:S], P)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -337,8 +422,13 @@ def run_precision(args, px, torch, dev, rank, world, local, dist):
                            "parallelism": f"replicas x{world}",
                            "l2": _l2_note(pats_d.numel() * 4, T * n * n * 2, "BF16 templates")},
                 "accuracy": accuracy, "gpu_launches": int(sum(v[1] for v in prof.values())), "clocks": clocks,
-                "roofline": roofline, "e2e": None, "cpu_baseline": None}
-        print(json.dumps(line), flush=True)
+                "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu}
+        if emit:
+            print(json.dumps(line), flush=True)
+    else:
+        line = None
+    ctx.close()
+    return line
 
 
 # --------------------------------------------------------------- ndp form
@@ -571,7 +661,37 @@ def flops_per_pair(n: int) -> float:
     return 2.5 * n * n * math.log2(n * n) + 6 * n * (n // 2 + 1)
 
 
-def run_batched(args, px, torch, dev, rank, world, local, dist):
+def cpu_batched_rate(wl, pats_list, crop_ns, native=False, t_sub=256):
+    """The FP64 oracle on a bounded sample of the batched workload: per map,
+    the library build and the search (pre-processing, every pair's surface,
+    best template, sub-pixel peak) against t_sub evenly spaced templates of its
+    library (both linear in the template count, scaled to the whole library),
+    on one sample pattern per core; the maps' times are added."""
+    import oracle
+    threads = oracle.num_threads()
+    total, P_all, parts = 0.0, 0, []
+    for m, pats, n in zip(wl["maps"], pats_list, crop_ns):
+        T, P = len(m["lib_q"]), len(m["truth_q"])
+        W, H = m["W"], m["H"]
+        _, ox, oy, pcc = oracle.crop(W, H, wl["pc"], native=native)
+        sub = np.linspace(0, T - 1, min(T, t_sub)).astype(np.int64)
+        t0 = time.perf_counter()
+        St, _, _ = oracle.prep_many(oracle.project_many(wl["master"], m["lib_q"][sub], pcc, n))
+        t_lib = (time.perf_counter() - t0) * T / len(sub)
+        S = min(threads, len(pats))
+        t0 = time.perf_counter()
+        Sp, _, deg = oracle.prep_many(pats[:S, oy:oy + n, ox:ox + n])
+        oracle.index(St, Sp, deg)
+        t_s = (time.perf_counter() - t0) * T / len(sub)
+        total += t_lib + P * t_s / S
+        P_all += P
+        parts.append(f"{W}px/{n} T{T} P{P}: lib {t_lib:.1f} s, {P * t_s / S:.1f} s search")
+    sample = (f"per map, {threads} sample patterns searched against {t_sub} evenly spaced templates and the "
+              f"library build of those templates, both scaled to the whole library: " + "; ".join(parts))
+    return {"value": P_all / total, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+
+
+def run_batched(args, px, torch, dev, rank, world, local, dist, emit=True):
     wl = synth.config_batched(seed=rank, scale=args.scale)
     ctx = px.Context(native_sizes=int(args.native))
     master_d = torch.from_numpy(np.ascontiguousarray(wl["master"])).to(dev)
@@ -714,10 +834,19 @@ def run_batched(args, px, torch, dev, rank, world, local, dist):
                 "sequential_ms_per_step": seq_ms / args.steps,
                 "accuracy": accuracy, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
                 "e2e": e2e, "cpu_baseline": None}
-        print(json.dumps(line), flush=True)
+        if world == 1 and not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            S = oracle.num_threads()
+            line["cpu_baseline"] = cpu_batched_rate(wl, [p[:S].cpu().numpy() for _, p in batch], ns, args.native)
+        if emit:
+            print(json.dumps(line), flush=True)
+    else:
+        line = None
     for lib, _ in batch:
         lib.close()
     ctx.close()
+    return line
 
 
 # ----------------------------------------------------------- learned form
@@ -739,7 +868,51 @@ CNN_FORWARD_FLOPS = 2.0 * (sum(co * ci * 9 * s * s for ci, co, s in
                            + 256 * 128 + 48 * 256)
 
 
-def run_learned(args, px, torch, dev, rank, world, local, dist):
+def cpu_learned_rate(wl, params, pats, pcs, fb_frac, P_total, tau):
+    """The FP64 oracle on a bounded sample of the learned workload: the
+    network's forward pass (BF16 form, the trained parameters) on the
+    standardised centred crops, the k proposals projected, pre-processed and
+    correlated with the pattern, refinement from the best proposal; patterns
+    whose refined peak stays below tau take the full search + refinement,
+    counted at the GPU run's fallback fraction and timed on two patterns
+    (library build amortised over the map)."""
+    import oracle
+    n, k = wl["n"], wl["k"]
+    threads = oracle.num_threads()
+    S = len(pats)
+    t0 = time.perf_counter()
+    x = np.stack([oracle.cnn_standardise(p) for p in pats])
+    props = oracle.cnn_proposals(oracle.cnn_forward_bf16(params, x, k), k)
+    t_net = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Sp, _, deg = oracle.prep_many(pats)
+    tm = oracle.project_many(wl["master"], props.reshape(-1, 4), np.repeat(pcs, k, axis=0), n)
+    St, _, _ = oracle.prep_many(tm)
+    seeds = np.empty((S, 4))
+    for p in range(S):
+        b = oracle.index(St[p * k:(p + 1) * k], Sp[p:p + 1], deg[p:p + 1])[0][0]
+        seeds[p] = props[p, max(0, int(b))]
+    t_score = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.refine_many(wl["master"], pats, seeds, pcs, max_it=wl["max_iter"], tol_deg=1e-3)
+    t_refine = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Sl, _, _ = oracle.prep_many(oracle.project_many(wl["master"], wl["lib_q"], wl["pc"], n))
+    t_lib = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b, _, _, _ = oracle.index(Sl, Sp[:2], deg[:2])
+    oracle.refine_many(wl["master"], pats[:2], wl["lib_q"][np.maximum(b, 0)], pcs[:2], max_it=wl["max_iter"],
+                       tol_deg=1e-3)
+    t_full = (time.perf_counter() - t0) / 2 * min(2, threads) / threads
+    per = (t_net + t_score + t_refine) / S + fb_frac * t_full + t_lib / P_total
+    sample = (f"{S} of the {P_total} test patterns: network forward ({t_net:.1f} s), {k} proposals projected, "
+              f"pre-processed and correlated ({t_score:.1f} s), refinement ({t_refine:.1f} s); the full-search "
+              f"fallback at the GPU run's fraction {fb_frac:.4f}, timed on 2 patterns; library build ({t_lib:.1f} s) "
+              f"amortised over {P_total}; training not included (set-up)")
+    return {"value": 1.0 / per, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+
+
+def run_learned(args, px, torch, dev, rank, world, local, dist, emit=True):
     n_test = args.patterns or 100000
     wl = synth.config_learned_128(seed=rank, n_train=args.train, n_test=n_test)
     n, k = wl["n"], wl["k"]
@@ -842,6 +1015,60 @@ def run_learned(args, px, torch, dev, rank, world, local, dist):
                 "unit": "TFLOP/s", "kernel": kern, "peak_basis": basis, "traffic": None,
                 "stage_ms_per_step": {kk: v[0] / args.steps for kk, v in prof.items()}}
     roofline["frac"] = roofline["achieved"] / net_peak if roofline["achieved"] else None
+    net_roof = roofline
+    # the dominant stage: pre-processing (k_prep_real).  Timed alone on the step's own test patterns (spectra
+    # and filtered images, as the learned path takes them); algorithmic bytes: the image in, the half spectrum
+    # and the filtered image out
+    stages = {kk: v[0] / args.steps for kk, v in prof.items()}
+    px.xcf_prep(ctx, pats, geom, want_spatial=True)            # warm-up (output buffers)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(3):
+        px.xcf_prep(ctx, pats, geom, want_spatial=True)
+    e1.record()
+    torch.cuda.synchronize()
+    prep_ms = e0.elapsed_time(e1) / 3
+    prep_bytes = n_test * (4 * n * n + 8 * n * (n // 2 + 1) + 4 * n * n)
+    hbm = (pk or {}).get("hbm_gbs") or 6800.0
+    roofline = {"bound": "hbm", "achieved": prep_bytes / (prep_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "traffic": None, "kernel": "k_prep_real (pre-processing: crop, statistics, window, FFT, band-pass, "
+                "norm, filtered image)", "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)" if pk else
+                "fallback", "timed": f"alone on the {n_test} test patterns, {prep_ms:.2f} ms per launch",
+                "stage_share": stages.get("prep", 0.0) / max(sum(stages.values()), 1e-9),
+                "stage_ms_per_step": stages, "secondary": {"network": net_roof}}
+    roofline["frac"] = roofline["achieved"] / hbm
+    e2e = None
+    if not args.no_e2e:
+        pats_h = pats.cpu().pin_memory()
+        pcs_h = tepc.cpu().pin_memory()
+        hout = tuple(torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs)
+
+        def e2e_step():
+            pats.copy_(pats_h, non_blocking=True)
+            tepc.copy_(pcs_h, non_blocking=True)
+            step()
+            for h, o in zip(hout, outs):
+                h.copy_(o, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        e2e = {"value": whole_job_rate(n_test, args.steps, world, dt * 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(pats_h.numel() * 4 + pcs_h.numel() * 8),
+               "d2h_bytes_per_step": int(sum(h.numel() * h.element_size() for h in hout)),
+               "note": "test patterns and PCs copied in from pinned host memory, outputs copied out, every step"}
+        del pats_h
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        S = args.cpu_sample or oracle.num_threads()
+        cpu = cpu_learned_rate(wl, net.params().cpu().numpy(), pats[:S].cpu().numpy(), wl["test_pcs"][:S],
+                               float(fb.mean()), n_test, tau)
     if rank == 0:
         line = {"metric": "patterns indexed/s (learned proposals + correlation score + refinement, full-search fallback)",
                 "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -866,11 +1093,15 @@ def run_learned(args, px, torch, dev, rank, world, local, dist):
                              "best_proposal_frac_below_5deg": float((best_prop < 5.0).double().mean()),
                              "speedup_vs_full_search": value / (n_test / (full_ms / 1e3))},
                 "gpu_launches": int(sum(v[1] for v in prof.values())), "clocks": clocks, "roofline": roofline,
-                "e2e": None, "cpu_baseline": None}
-        print(json.dumps(line), flush=True)
+                "e2e": e2e, "cpu_baseline": cpu}
+        if emit:
+            print(json.dumps(line), flush=True)
+    else:
+        line = None
     lib.close()
     net.close()
     ctx.close()
+    return line
 
 
 # ------------------------------------------------------------------ our arm
@@ -1027,9 +1258,41 @@ def main():
                            "l2": _l2_note(pats_d.numel() * 4, T * n * (n // 2 + 1) * 8, "library spectra")},
                 "accuracy": accuracy, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
                 "e2e": e2e, "cpu_baseline": cpu}
+    if world == 1 and not args.no_forms:
+        del pats_d, out
+        ctx.close()
+        torch.cuda.empty_cache()
+        line["forms"] = run_forms(args, px, torch, dev, rank, world, local, dist)
+    if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+FORM_KEYS = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "accuracy", "ablation",
+             "training", "sequential_ms_per_step", "gpu_launches", "clocks", "roofline", "e2e", "cpu_baseline")
+
+
+def run_forms(args, px, torch, dev, rank, world, local, dist):
+    """The other forms of the indexer, each on its own workload, measured in
+    the same run as the plain form (one GPU): each a sub-record with its
+    throughput, the roofline of the stage that dominates its step, an end to
+    end number (host buffers, copies in the timed region) and the oracle on
+    a bounded sample."""
+    forms = {}
+    for name, fn in (("precision", run_precision), ("batched", run_batched), ("learned", run_learned)):
+        sub = argparse.Namespace(**vars(args))
+        sub.form, sub.steps, sub.warmup = name, max(1, args.form_steps), max(3, min(args.warmup, 3))
+        sub.patterns, sub.scale, sub.native, sub.upsample, sub.cpu_sample = 0, 1.0, False, 0, 0
+        t0 = time.perf_counter()
+        rec = fn(sub, px, torch, dev, rank, world, local, dist, emit=False)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        if rec is not None:
+            rec = {k: rec[k] for k in FORM_KEYS if k in rec}
+            rec["wall_s"] = time.perf_counter() - t0
+            forms[name] = rec
+    return forms
 
 
 if __name__ == "__main__":

@@ -383,10 +383,13 @@ int xcf_index_refine(xcf_ctx *ctx, const xcf_library *lib, const float *patterns
 
 /* End to end from host memory: search and refine P patterns held in host
  * memory (pinned for full speed), streaming them through the device in chunks
- * of `chunk` patterns with copies overlapped on a second stream, and writing
- * host outputs.  pcs (host, [P, 3]) may be NULL.  Outputs: best, peak, shift
- * as xcf_index; quats, rpeak, iters as xcf_refine (seeds = library
- * orientations of best).  Synchronous. */
+ * of `chunk` patterns (<= 0: about four chunks of at least 2,048 patterns;
+ * at most 16,384): two device slots, the next chunk's patterns copied in on a
+ * copy stream while the current chunk is indexed and refined on a compute
+ * stream, and each chunk's outputs copied back behind it.  pcs (host, [P, 3])
+ * may be NULL.  Outputs: best, peak, shift as xcf_index with pcs; quats,
+ * rpeak, iters as xcf_refine (seeds = library orientations of best, the
+ * context's max_iter / tol_deg).  Synchronous. */
 int xcf_index_refine_host(xcf_ctx *ctx, const xcf_library *lib, const float *patterns,
                           int32_t P, const double *pcs, int32_t chunk, int32_t *best, float *peak,
                           float *shift, double *quats, float *rpeak, int32_t *iters);

@@ -830,54 +830,98 @@ int xcf_index_refine_host(xcf_ctx *ctx, const xcf_library *lib, const float *pat
     if (P == 0) return XCF_OK;
     if (!patterns || !best || !peak || !shift || !quats || !rpeak || !iters || P < 0)
         return fail(ctx, XCF_ERR_ARG, "xcf_index_refine_host: bad argument");
-    if (chunk <= 0 || chunk > kChunk) chunk = kChunk;
+    if (chunk <= 0) {   // about four chunks (at least 2,048 patterns each), so that copies overlap compute
+        chunk = (P + 3) / 4;
+        if (chunk < 2048) chunk = 2048;
+    }
+    if (chunk > kChunk) chunk = kChunk;
+    if (chunk > P) chunk = P;
     cudaSetDevice(ctx->device);
     const size_t img = (size_t)lib->geom.width * lib->geom.height;
-    cudaStream_t st = nullptr;
-    XCF_CHECK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream");
-    // device layout of one chunk: patterns | pcs | outputs
+    // two device slots of one chunk each: patterns | pcs | outputs; chunk i uses slot i & 1.
+    // The copy stream moves chunk i + 1 in while the compute stream works on chunk i.
     float *dpat;
-    double *dpcs = nullptr, *dq, *dseeds;
-    int *dbest, *diters;
-    float *dpeak, *dshift, *drpeak;
-    const size_t out_bytes = (size_t)chunk * (4 + 4 + 8 + 32 + 4 + 4) + 256;
+    double *dpcs = nullptr, *dseeds;
+    const size_t out_bytes = ((size_t)chunk * (4 + 4 + 8 + 32 + 4 + 4) + 255) & ~(size_t)255;
     char *dout;
-    if ((rc = scratch_t(ctx, S_IO_PAT, img * chunk, &dpat)) ||
-        (pcs && (rc = scratch_t(ctx, S_IO_PCS, (size_t)chunk * 3, &dpcs))) ||
-        (rc = scratch_t(ctx, S_IO_OUT, out_bytes, &dout)) ||
-        (rc = scratch_t(ctx, S_SEEDS, (size_t)chunk * 4, &dseeds))) {
-        cudaStreamDestroy(st);
+    if ((rc = scratch_t(ctx, S_IO_PAT, 2 * img * chunk, &dpat)) ||
+        (pcs && (rc = scratch_t(ctx, S_IO_PCS, (size_t)2 * chunk * 3, &dpcs))) ||
+        (rc = scratch_t(ctx, S_IO_OUT, 2 * out_bytes, &dout)) ||
+        (rc = scratch_t(ctx, S_SEEDS, (size_t)chunk * 4, &dseeds)))
         return rc;
-    }
-    dq = reinterpret_cast<double *>(dout);
-    dbest = reinterpret_cast<int *>(dq + 4 * (size_t)chunk);
-    diters = dbest + chunk;
-    dpeak = reinterpret_cast<float *>(diters + chunk);
-    dshift = dpeak + chunk;
-    drpeak = dshift + 2 * (size_t)chunk;
+    cudaStream_t cs = nullptr, xs = nullptr;   // compute, copies
+    cudaEvent_t ev[8] = {};                    // per slot: in_ready, in_free, out_ready, out_free
     int status = XCF_OK;
-    for (int p0 = 0; p0 < P && status == XCF_OK; p0 += chunk) {
-        const int np = P - p0 < chunk ? P - p0 : chunk;
-        cudaError_t e = cudaMemcpyAsync(dpat, patterns + img * p0, sizeof(float) * img * np, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess && pcs)
-            e = cudaMemcpyAsync(dpcs, pcs + 3 * (size_t)p0, sizeof(double) * 3 * np, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) { status = cuda_fail(ctx, e, "H2D"); break; }
-        if ((status = index_chunk(ctx, lib, dpat, np, dbest, dpeak, dshift, nullptr, st, nullptr, dpcs))) break;
-        e = launch_gather_seeds(lib->quats, dbest, np, dseeds, st);
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&xs, cudaStreamNonBlocking);
+    for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) status = cuda_fail(ctx, e, "xcf_index_refine_host: streams");
+    auto slot_out = [&](int sl, double **q, int **b, int **it, float **pk, float **sh, float **rp) {
+        char *o = dout + sl * out_bytes;
+        *q = reinterpret_cast<double *>(o);
+        *b = reinterpret_cast<int *>(*q + 4 * (size_t)chunk);
+        *it = *b + chunk;
+        *pk = reinterpret_cast<float *>(*it + chunk);
+        *sh = *pk + chunk;
+        *rp = *sh + 2 * (size_t)chunk;
+    };
+    auto h2d = [&](int c) -> cudaError_t {   // chunk c in, on the copy stream
+        const int sl = c & 1, p0 = c * chunk, np = P - p0 < chunk ? P - p0 : chunk;
+        cudaError_t r = c >= 2 ? cudaStreamWaitEvent(xs, ev[4 * sl + 1], 0) : cudaSuccess;   // slot read by c - 2
+        if (r == cudaSuccess)
+            r = cudaMemcpyAsync(dpat + img * chunk * sl, patterns + img * p0, sizeof(float) * img * np,
+                                cudaMemcpyHostToDevice, xs);
+        if (r == cudaSuccess && pcs)
+            r = cudaMemcpyAsync(dpcs + (size_t)3 * chunk * sl, pcs + 3 * (size_t)p0, sizeof(double) * 3 * np,
+                                cudaMemcpyHostToDevice, xs);
+        if (r == cudaSuccess) r = cudaEventRecord(ev[4 * sl], xs);
+        return r;
+    };
+    const int nchunks = (P + chunk - 1) / chunk;
+    if (status == XCF_OK && (e = h2d(0)) != cudaSuccess) status = cuda_fail(ctx, e, "H2D");
+    for (int c = 0; c < nchunks && status == XCF_OK; ++c) {
+        const int sl = c & 1, p0 = c * chunk, np = P - p0 < chunk ? P - p0 : chunk;
+        if (c + 1 < nchunks && (e = h2d(c + 1)) != cudaSuccess) { status = cuda_fail(ctx, e, "H2D"); break; }
+        double *dq;
+        int *dbest, *diters;
+        float *dpeak, *dshift, *drpeak;
+        slot_out(sl, &dq, &dbest, &diters, &dpeak, &dshift, &drpeak);
+        const float *pat = dpat + img * chunk * sl;
+        const double *pc = pcs ? dpcs + (size_t)3 * chunk * sl : nullptr;
+        e = cudaStreamWaitEvent(cs, ev[4 * sl], 0);                      // chunk c is in
+        if (e == cudaSuccess && c >= 2) e = cudaStreamWaitEvent(cs, ev[4 * sl + 3], 0);   // outputs of c - 2 read
+        if (e != cudaSuccess) { status = cuda_fail(ctx, e, "wait"); break; }
+        if ((status = index_chunk(ctx, lib, pat, np, dbest, dpeak, dshift, nullptr, cs, nullptr, pc))) break;
+        e = launch_gather_seeds(lib->quats, dbest, np, dseeds, cs);
         if (e != cudaSuccess) { status = cuda_fail(ctx, e, "seeds"); break; }
         ctx->launches[XCF_STAGE_OTHER] += 1;
-        if ((status = refine_chunk(ctx, lib, dpat, np, dseeds, dpcs, dq, drpeak, diters, st))) break;
-        e = cudaMemcpyAsync(best + p0, dbest, sizeof(int) * np, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(peak + p0, dpeak, sizeof(float) * np, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(shift + 2 * (size_t)p0, dshift, sizeof(float) * 2 * np, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(quats + 4 * (size_t)p0, dq, sizeof(double) * 4 * np, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(rpeak + p0, drpeak, sizeof(float) * np, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(iters + p0, diters, sizeof(int) * np, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) status = cuda_fail(ctx, e, "xcf_index_refine_host");
+        if ((status = refine_chunk(ctx, lib, pat, np, dseeds, pc, dq, drpeak, diters, cs))) break;
+        e = cudaEventRecord(ev[4 * sl + 1], cs);                         // slot's inputs no longer read
+        if (e == cudaSuccess) e = cudaEventRecord(ev[4 * sl + 2], cs);   // outputs ready
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(xs, ev[4 * sl + 2], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(best + p0, dbest, sizeof(int) * np, cudaMemcpyDeviceToHost, xs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(peak + p0, dpeak, sizeof(float) * np, cudaMemcpyDeviceToHost, xs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(shift + 2 * (size_t)p0, dshift, sizeof(float) * 2 * np, cudaMemcpyDeviceToHost, xs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(quats + 4 * (size_t)p0, dq, sizeof(double) * 4 * np, cudaMemcpyDeviceToHost, xs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rpeak + p0, drpeak, sizeof(float) * np, cudaMemcpyDeviceToHost, xs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(iters + p0, diters, sizeof(int) * np, cudaMemcpyDeviceToHost, xs);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[4 * sl + 3], xs);   // outputs read
+        if (e != cudaSuccess) status = cuda_fail(ctx, e, "D2H");
     }
-    cudaStreamSynchronize(st);
-    cudaStreamDestroy(st);
+    if (cs) {
+        e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess && status == XCF_OK) status = cuda_fail(ctx, e, "xcf_index_refine_host");
+    }
+    if (xs) {
+        e = cudaStreamSynchronize(xs);
+        if (e != cudaSuccess && status == XCF_OK) status = cuda_fail(ctx, e, "xcf_index_refine_host");
+    }
+    for (auto &x : ev)
+        if (x) cudaEventDestroy(x);
+    if (xs) cudaStreamDestroy(xs);
+    if (cs) cudaStreamDestroy(cs);
     return status;
 }
 

@@ -4,30 +4,35 @@
 // exp(+2 pi i k.s / N)), Fig. 1 B-C (best template by peak height), Fig. 5 /
 // Discussion (one inverse FFT per pattern-template pair dominates the cost).
 //
-// One CTA (256 threads, one per SM) keeps one pattern's half spectrum in
+// One CTA (512 threads, one per SM) keeps one pattern's half spectrum in
 // shared memory and streams the library's half spectra from L2/HBM, two
 // templates per inverse FFT: Z = X1 + i X2 with X_j = conj(S_tj) S_p extended
 // to the full spectrum by Hermitian symmetry, so that Re(IFFT Z) and
 // Im(IFFT Z) are the two real correlation surfaces.  The 128 x 128 inverse FFT
-// runs in three register rounds separated by two shared-memory transposes:
-//   round 1: thread (q, l) owns stored column q and rows u = l + 4m: two
-//            32-point FFTs over m (of X1 and X2), twiddle W128^(l k2); the
+// runs in three register rounds separated by two shared-memory transposes
+// (rows y = k2 + 16 k1 of the column transform, columns x = k3 + 4 k4 of the
+// row transform):
+//   round 1: thread (q, l) owns stored column q and rows u = l + 8m: two
+//            16-point FFTs over m (of X1 and X2), twiddle W128^(l k2); the
 //            conjugate-symmetric partner column 128 - q is written from the
-//            same registers (conj(A1) + i conj(A2) at sub-sequence 4 - l);
-//   round 2: thread (k2, g): radix-4 over l completes the column transform
-//            for rows k2 + 32 k1, then 16-point FFTs over the columns
-//            g + 8 i and twiddle W128^(g k3);
-//   round 3: thread (r, h): 8-point FFTs over g give row r, columns
-//            k3 + 16 k4, of both surfaces; the max of each is reduced.
+//            same registers (conj(A1) + i conj(A2) at sub-sequence 8 - l);
+//   round 2: thread (k2, g): radix-8 over l completes the column transform
+//            for rows k2 + 16 k1, then radix-4 over the columns g + 32 i and
+//            twiddle W128^(g k3);
+//   round 3: thread (y, k3): a 32-point FFT over g gives row y, columns
+//            k3 + 4 k4, of both surfaces; the max of each is reduced.
+// Each thread holds 32 complex values per round (at most 128 registers), so
+// sixteen warps share an SM and hide one another's shared-memory latency.
 // No surface is written to global memory; only the per-pattern best key (and
 // optionally every per-pair peak) leave the kernel.
 //
 // Library spectra are read in a packed "search layout" (pack_search_layout):
-// for each template, columns 0..63 as [l][m/2][q][m&1] (64 KB, so that the 32
-// rows a round-1 thread needs are 16 conflict-free 16-byte shared loads), then
-// column 64.  The next pair is copied from L2 with cp.async while round 3
-// computes: round 3 first pulls its values into registers, after which the
-// transpose buffer (128 KB) holds exactly columns 0..63 of two templates.
+// for each template, columns 0..63 as [l][m/2][q][m&1] with u = l + 8m (64 KB,
+// so that the 16 rows a round-1 thread needs are 8 conflict-free 16-byte
+// shared loads), then column 64.  The next pair is copied from L2 with
+// cp.async while round 3 computes: round 3 first pulls its values into
+// registers, after which the transpose buffer (128 KB) holds exactly columns
+// 0..63 of two templates.
 #include "common.cuh"
 #include "kernels.cuh"
 

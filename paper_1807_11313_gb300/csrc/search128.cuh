@@ -9,34 +9,33 @@ namespace s128 {
 constexpr int N = 128;
 constexpr int HW = 65;          // stored columns of a half spectrum
 constexpr int SPEC = N * HW;    // complex values per half spectrum
-constexpr int NT = 256;
+constexpr int NT = 512;
+constexpr int NW = NT / 32;
 constexpr int COL64 = 8192;     // offset of column 64 in the packed layout
 
 // shared layout (float2 units)
 constexpr int OFF_SP = 0;                  // pattern, packed layout, 8320
 constexpr int OFF_BUF = SPEC;              // transpose buffer, 16384
-constexpr int OFF_TW1 = OFF_BUF + N * N;   // W128^(l k2) at [l][k2]
-constexpr int OFF_TW2 = OFF_TW1 + 128;     // W128^(g k3) at [k3][g]
+constexpr int OFF_TW1 = OFF_BUF + N * N;   // W128^(l k2) at [l][k2], l < 8, k2 < 16
+constexpr int OFF_TW2 = OFF_TW1 + 128;     // W128^(g k3) at [k3][g], k3 < 4, g < 32
 constexpr int OFF_C64 = OFF_TW2 + 128;     // next pair's column 64: [2][128]
-constexpr int OFF_RED = OFF_C64 + 256;     // [2][8 warps] (max re, max im)
-constexpr int SMEM_F2 = OFF_RED + 16;
+constexpr int OFF_RED = OFF_C64 + 256;     // [2][16 warps] (max re, max im)
+constexpr int SMEM_F2 = OFF_RED + 2 * NW;
 constexpr size_t SMEM_BYTES = sizeof(float2) * SMEM_F2;
 
-// packed position of (row u, stored column q < 64)
+// packed position of (row u, stored column q < 64): [u & 7][(u >> 3) / 2][q][(u >> 3) & 1]
 __host__ __device__ __forceinline__ int pk(int u, int q) {
-    const int l = u & 3, m = u >> 2;
-    return (((l * 16 + (m >> 1)) * 64 + q) << 1) + (m & 1);
+    const int l = u & 7, m = u >> 3;
+    return (((l * 8 + (m >> 1)) * 64 + q) << 1) + (m & 1);
 }
 
-// round-1 output A[l][k2][v]; v swizzled by k2 so that round 2's reads of
-// four k2 rows land in distinct bank halves
-__device__ __forceinline__ int idxA(int l, int k2, int v) {
-    return ((l * 32 + k2) << 7) + (v ^ ((k2 & 3) << 3));
-}
-// round-2 output B[r][k3][g]; k3 and g swizzled by r so that round 2's 8-byte
-// stores and round 3's 16-byte loads (pairs of g) are conflict-free
-__device__ __forceinline__ int idxB(int r, int k3, int g) {
-    return (r << 7) + ((k3 ^ (r & 1)) << 3) + (g ^ (((r >> 1) & 3) << 1));
+// round-1 output A[l][k2][v] (a warp stores 32 consecutive v of one (l, k2) and
+// round 2 reads 32 consecutive v of one (l, k2): no swizzle needed)
+__device__ __forceinline__ int idxA(int l, int k2, int v) { return ((l * 16 + k2) << 7) + v; }
+// round-2 output B[row = 4 y + k3][g]: 16-byte pairs of g swizzled by row & 7 so
+// that round 3's 16-byte loads (one row per thread) spread over every bank
+__device__ __forceinline__ int idxB(int row, int g) {
+    return (row << 5) + ((((g >> 1) ^ (row & 7)) << 1) | (g & 1));
 }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -45,6 +44,13 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// exp(+2 pi i e / 128) from the compile-time table (e in [0, 128))
+__device__ __forceinline__ float2 w128(int e) {
+    const int r = e & 63;
+    const float2 w = make_float2(kTwTable<N>.re[r], kTwTable<N>.im[r]);
+    return e & 64 ? make_float2(-w.x, -w.y) : w;
+}
 
 // One work item of the search: pattern p against template pairs [pb, pe)
 // (pairs (2i, 2i + 1); T odd pairs the last template with itself).  Runs on
@@ -64,15 +70,13 @@ __device__ __forceinline__ void search_body(const float2 *__restrict__ Spk, int 
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    // round-1 identity: warp -> sub-sequence l, lane -> stored column q
-    const int l1 = warp & 3;
-    const int q = ((warp >> 2) << 5) + lane;
-    // round-2 identity
-    const int k2r = (warp << 2) + (lane >> 3);
-    const int g2 = lane & 7;
-    // round-3 identity
-    const int r3 = (warp << 4) + (lane & 15);
-    const int h3 = lane >> 4;
+    // round-1 identity: warp -> sub-sequence l (rows u = l + 8 m), lane -> stored column q
+    const int l1 = warp & 7;
+    const int q = ((warp >> 3) << 5) + lane;
+    // round-2 identity: warp -> k2, lane -> column residue g (columns g + 32 i)
+    const int k2r = warp;
+    const int g2 = lane;
+    // round-3 identity: one row (y, k3) of B per thread
 
     // stage a template pair into shared memory with asynchronous copies: the
     // packed columns 0..63 of both templates (2 x 64 KB) fill the transpose
@@ -83,7 +87,7 @@ __device__ __forceinline__ void search_body(const float2 *__restrict__ Spk, int 
         const float4 *s2 = reinterpret_cast<const float4 *>(Spk + (size_t)t2 * SPEC);
         float4 *d = reinterpret_cast<float4 *>(buf);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
+        for (int k = 0; k < 8; ++k) {
             cp_async16(d + k * NT + tid, s1 + k * NT + tid);
             cp_async16(d + 4096 + k * NT + tid, s2 + k * NT + tid);
         }
@@ -101,13 +105,10 @@ __device__ __forceinline__ void search_body(const float2 *__restrict__ Spk, int 
             sp[v < 64 ? pk(u, v) : COL64 + u] = src[i];
         }
         if (tid < 128) {
-            double s, c;
-            int l = tid >> 5, k2 = tid & 31;
-            sincospi(2.0 * (k2 * l) / N, &s, &c);
-            tw1[tid] = make_float2((float)c, (float)s);
-            int k3 = tid >> 3, g = tid & 7;
-            sincospi(2.0 * (k3 * g) / N, &s, &c);
-            tw2[tid] = make_float2((float)c, (float)s);
+            tw1[tid] = w128((tid >> 4) * (tid & 15));          // [l][k2]
+        } else if (tid < 256) {
+            const int k3 = (tid - 128) >> 5, g = tid & 31;
+            tw2[tid - 128] = w128(g * k3);                      // [k3][g]
         }
     }
     stage(pb);
@@ -120,10 +121,10 @@ __device__ __forceinline__ void search_body(const float2 *__restrict__ Spk, int 
         __syncthreads();   // sp / tables / column 64 ready; previous round 3 done with buf
         // reduce the previous pair's per-warp maxima
         if (pi > pb && tid == 0) {
-            const float2 *rr = red + ((pi - 1) & 1) * 8;
+            const float2 *rr = red + ((pi - 1) & 1) * NW;
             float m1 = rr[0].x, m2 = rr[0].y;
 #pragma unroll
-            for (int w = 1; w < 8; ++w) { m1 = fmaxf(m1, rr[w].x); m2 = fmaxf(m2, rr[w].y); }
+            for (int w = 1; w < NW; ++w) { m1 = fmaxf(m1, rr[w].x); m2 = fmaxf(m2, rr[w].y); }
             const int u1 = 2 * (pi - 1), u2 = min(u1 + 1, T - 1);
             if (m1 > best_v) { best_v = m1; best_t = u1; }
             if (u2 != u1 && m2 > best_v) { best_v = m2; best_t = u2; }
@@ -133,31 +134,26 @@ __device__ __forceinline__ void search_body(const float2 *__restrict__ Spk, int 
             }
         }
 
-        // ---------------- round 1: column sub-FFTs ----------------
-        float2 a[32], b[32];
+        // ---------------- round 1: 16-point column sub-FFTs ----------------
+        float2 a[16], b[16];
         {
-            const float4 *sp4 = reinterpret_cast<const float4 *>(sp) + (l1 * 16) * 64 + q;
-            const float4 *tp4 = reinterpret_cast<const float4 *>(buf) + (l1 * 16) * 64 + q;
+            const float4 *sp4 = reinterpret_cast<const float4 *>(sp) + (l1 * 8) * 64 + q;
+            const float4 *tp4 = reinterpret_cast<const float4 *>(buf) + (l1 * 8) * 64 + q;
 #pragma unroll
-            for (int mp = 0; mp < 16; ++mp) {
+            for (int mp = 0; mp < 8; ++mp) {
                 const float4 s4 = sp4[mp * 64];
                 const float4 t1 = tp4[mp * 64], t2 = tp4[4096 + mp * 64];
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int m = 2 * mp + e;
-                    const float2 s = e ? make_float2(s4.z, s4.w) : make_float2(s4.x, s4.y);
-                    const float2 v1 = e ? make_float2(t1.z, t1.w) : make_float2(t1.x, t1.y);
-                    const float2 v2 = e ? make_float2(t2.z, t2.w) : make_float2(t2.x, t2.y);
-                    a[m] = c_mulcj(v1, s);
-                    b[m] = c_mulcj(v2, s);
-                }
+                a[2 * mp] = c_mulcj(make_float2(t1.x, t1.y), make_float2(s4.x, s4.y));
+                a[2 * mp + 1] = c_mulcj(make_float2(t1.z, t1.w), make_float2(s4.z, s4.w));
+                b[2 * mp] = c_mulcj(make_float2(t2.x, t2.y), make_float2(s4.x, s4.y));
+                b[2 * mp + 1] = c_mulcj(make_float2(t2.z, t2.w), make_float2(s4.z, s4.w));
             }
             if (q == 0) {
                 // columns 0 and 64 are self-conjugate: pack Z = X1 + i X2 directly
                 // (column 0 from the products above, column 64 from c64)
 #pragma unroll
-                for (int m = 0; m < 32; ++m) {
-                    const int u = l1 + 4 * m;
+                for (int m = 0; m < 16; ++m) {
+                    const int u = l1 + 8 * m;
                     const float2 s64 = sp[COL64 + u];
                     const float2 y1 = c_mulcj(c64[u], s64), y2 = c_mulcj(c64[128 + u], s64);
                     a[m] = make_float2(a[m].x - b[m].y, a[m].y + b[m].x);
@@ -166,23 +162,23 @@ __device__ __forceinline__ void search_body(const float2 *__restrict__ Spk, int 
             }
         }
         __syncthreads();   // every thread has read the staged templates: buf is free
-        fft_reg_dif<32, +1>(a);
-        fft_reg_dif<32, +1>(b);
+        fft_reg_dif<16, +1>(a);
+        fft_reg_dif<16, +1>(b);
         {
             // second store: the conjugate-symmetric partner column (q > 0), or
             // column 64 (q = 0, whose b holds the column-64 transform)
             const bool q0 = q == 0;
-            const int l_2 = q0 ? l1 : (4 - l1) & 3;
+            const int l_2 = q0 ? l1 : (8 - l1) & 7;
             const int v_2 = q0 ? 64 : 128 - q;
-            const float4 *tw = reinterpret_cast<const float4 *>(tw1 + l1 * 32);
-            StaticFor<0, 16>::run([&](auto kk) {
+            const float4 *tw = reinterpret_cast<const float4 *>(tw1 + l1 * 16);
+            StaticFor<0, 8>::run([&](auto kk) {
                 constexpr int k2a = 2 * decltype(kk)::value;
                 const float4 w2 = tw[k2a >> 1];
                 StaticFor<0, 2>::run([&](auto ee) {
                     constexpr int k2 = k2a + decltype(ee)::value;
-                    constexpr int P = cx_bitrev(k2, 5);
+                    constexpr int P = cx_bitrev(k2, 4);
                     const float2 w = decltype(ee)::value ? make_float2(w2.z, w2.w) : make_float2(w2.x, w2.y);
-                    const float2 fa = c_mul(a[P], w), fb = c_mul(b[P], w);
+                    const float2 fa = k2 ? c_mul(a[P], w) : a[P], fb = k2 ? c_mul(b[P], w) : b[P];
                     const float2 d1 = make_float2(fa.x - fb.y, fa.y + fb.x);   // F1 + i F2
                     const float2 d2 = make_float2(fa.x + fb.y, fb.x - fa.y);   // conj(F1) + i conj(F2)
                     buf[idxA(l1, k2, q)] = q0 ? fa : d1;
@@ -192,78 +188,71 @@ __device__ __forceinline__ void search_body(const float2 *__restrict__ Spk, int 
         }
         __syncthreads();
 
-        // ---------------- round 2: finish columns, start rows ----------------
-        float2 c[4][16];
+        // ------- round 2: radix 8 over l finishes the columns, radix 4 starts the rows -------
+        float2 c[8][4];
 #pragma unroll
-        for (int l = 0; l < 4; ++l)
+        for (int l = 0; l < 8; ++l)
 #pragma unroll
-            for (int i = 0; i < 16; ++i) c[l][i] = buf[idxA(l, k2r, g2 + 8 * i)];
+            for (int i = 0; i < 4; ++i) c[l][i] = buf[idxA(l, k2r, g2 + 32 * i)];
         __syncthreads();
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const float2 x0 = c_add(c[0][i], c[2][i]), x1 = c_sub(c[0][i], c[2][i]);
-            const float2 x2 = c_add(c[1][i], c[3][i]), x3 = c_mul_pi(c_sub(c[1][i], c[3][i]));
-            c[0][i] = c_add(x0, x2);   // k1 = 0
-            c[2][i] = c_sub(x0, x2);   // k1 = 2
-            c[1][i] = c_add(x1, x3);   // k1 = 1
-            c[3][i] = c_sub(x1, x3);   // k1 = 3
-        }
         {
-            float2 w[16];
+            const float2 w1 = tw2[32 + g2], w2 = tw2[64 + g2], w3 = tw2[96 + g2];
 #pragma unroll
-            for (int k3 = 0; k3 < 16; ++k3) w[k3] = tw2[k3 * 8 + g2];
+            for (int i = 0; i < 4; ++i) {
+                float2 t[8];
 #pragma unroll
-            for (int k1 = 0; k1 < 4; ++k1) {
-                fft_reg_dif<16, +1>(c[k1]);
-                const int r = k2r + 32 * k1;
-                StaticFor<0, 16>::run([&](auto pp) {
-                    constexpr int P = decltype(pp)::value;
-                    constexpr int k3 = cx_bitrev(P, 4);
-                    buf[idxB(r, k3, g2)] = c_mul(c[k1][P], w[k3]);
-                });
+                for (int l = 0; l < 8; ++l) t[l] = c[l][i];
+                fft_reg_dif<8, +1>(t);   // t[P] = C[k1 = bitrev3(P)]
+#pragma unroll
+                for (int P = 0; P < 8; ++P) c[P][i] = t[P];
             }
+            StaticFor<0, 8>::run([&](auto pp) {
+                constexpr int P = decltype(pp)::value;
+                constexpr int k1 = cx_bitrev(P, 3);
+                const int row = (k2r + 16 * k1) << 2;
+                const float2 e0 = c[P][0], e1 = c[P][1], e2 = c[P][2], e3 = c[P][3];
+                const float2 s02 = c_add(e0, e2), d02 = c_sub(e0, e2);
+                const float2 s13 = c_add(e1, e3), d13 = c_mul_pi(c_sub(e1, e3));
+                buf[idxB(row, g2)] = c_add(s02, s13);                          // k3 = 0
+                buf[idxB(row + 1, g2)] = c_mul(c_add(d02, d13), w1);           // k3 = 1
+                buf[idxB(row + 2, g2)] = c_mul(c_sub(s02, s13), w2);           // k3 = 2
+                buf[idxB(row + 3, g2)] = c_mul(c_sub(d02, d13), w3);           // k3 = 3
+            });
         }
         __syncthreads();
 
-        // ------- round 3: finish rows, max; the next pair streams into buf meanwhile -------
-        float2 d[8][8];
+        // ------- round 3: 32-point row FFTs, max; the next pair streams into buf meanwhile -------
+        float2 d[32];
         {
-            const int rbase = r3 << 7, fsw = ((r3 >> 1) & 3) << 1;
+            const float4 *rowp = reinterpret_cast<const float4 *>(buf) + (tid << 4);
+            const int sw = tid & 7;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int k3 = 8 * h3 + j;
-                const float4 *row = reinterpret_cast<const float4 *>(buf + rbase + ((k3 ^ (r3 & 1)) << 3));
-#pragma unroll
-                for (int pr = 0; pr < 4; ++pr) {
-                    const float4 v = row[pr ^ (fsw >> 1)];   // logical g pair pr at physical pair pr ^ fsw/2
-                    d[j][2 * pr] = make_float2(v.x, v.y);
-                    d[j][2 * pr + 1] = make_float2(v.z, v.w);
-                }
+            for (int j = 0; j < 16; ++j) {
+                const float4 v = rowp[j ^ sw];
+                d[2 * j] = make_float2(v.x, v.y);
+                d[2 * j + 1] = make_float2(v.z, v.w);
             }
         }
         __syncthreads();   // every thread holds its row values: buf is free
         if (pi + 1 < pe) stage(pi + 1);
-        float m1 = -INFINITY, m2 = -INFINITY;
+        fft_reg_dif<32, +1>(d);
+        float m1 = d[0].x, m2 = d[0].y;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            fft_reg_dif<8, +1>(d[j]);
-#pragma unroll
-            for (int g = 0; g < 8; ++g) { m1 = fmaxf(m1, d[j][g].x); m2 = fmaxf(m2, d[j][g].y); }
-        }
+        for (int j = 1; j < 32; ++j) { m1 = fmaxf(m1, d[j].x); m2 = fmaxf(m2, d[j].y); }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
             m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
             m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
         }
-        if (lane == 0) red[(pi & 1) * 8 + warp] = make_float2(m1, m2);
+        if (lane == 0) red[(pi & 1) * NW + warp] = make_float2(m1, m2);
     }
     __syncthreads();
     if (tid == 0) {
         const int pi = pe;
-        const float2 *rr = red + ((pi - 1) & 1) * 8;
+        const float2 *rr = red + ((pi - 1) & 1) * NW;
         float m1 = rr[0].x, m2 = rr[0].y;
 #pragma unroll
-        for (int w = 1; w < 8; ++w) { m1 = fmaxf(m1, rr[w].x); m2 = fmaxf(m2, rr[w].y); }
+        for (int w = 1; w < NW; ++w) { m1 = fmaxf(m1, rr[w].x); m2 = fmaxf(m2, rr[w].y); }
         const int u1 = 2 * (pi - 1), u2 = min(u1 + 1, T - 1);
         if (m1 > best_v) { best_v = m1; best_t = u1; }
         if (u2 != u1 && m2 > best_v) { best_v = m2; best_t = u2; }

@@ -380,9 +380,9 @@ def config_precision_256(seed: int = 0, P: int = 50000, step_deg: float = 3.14) 
 
 # detector (width, height), FZ grid step (deg), patterns per map for the batched form:
 # detectors {96, 128, 160, 200, 256}^2 (cropped to 64, 128, 128, 128, 256),
-# libraries ~1,000-20,000 orientations, 2,000-8,000 patterns per map
+# libraries ~1,000-20,000 orientations, 2,000-40,000 patterns per map
 BATCHED_MAPS = (
-    ((96, 96), 8.5, 2000),
+    ((96, 96), 8.5, 40000),
     ((128, 128), 5.35, 4000),
     ((160, 160), 6.75, 3000),
     ((200, 200), 8.5, 4000),
