@@ -783,13 +783,21 @@ def run_batched(args, px, torch, dev, rank, world, local, dist, emit=True):
         d["achieved_tflops"] = d["tflop"] / (d["ms"] / 1e3)
         d["frac"] = d["achieved_tflops"] / fp32_peak
     achieved = flops / (search_ms_call / 1e3) / 1e12
-    kernels = {16: "k_search_generic", 32: "k_search_generic", 64: "k_search_generic", 96: "k_search_generic",
-               128: "k_search_maps", 160: "k_search_generic", 256: "k_search_c256"}
+    kernels = {16: "k_search_maps", 32: "k_search_maps", 64: "k_search_maps", 96: "k_search_maps",
+               128: "k_search_maps", 160: "k_search_maps", 256: "k_search_c256"}
+    body_names = {0: "warp lines (R x 32)", 1: "three rounds (16x8 | 4x32)", 2: "radix-2 in shared memory"}
+    tuning = {}
+    for (lib, _), n in zip(batch, ns):
+        t = px.xcf_maps_get_tuning(ctx, n, lib.T)
+        if t is not None:
+            tuning[f"{n}px_T{lib.T}"] = {"body": body_names.get(t[0], t[0]), "patterns_per_cta": t[1],
+                                         "pairs_per_item": t[2], "pairs_total": (lib.T + 1) // 2}
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": None,
                 "kernel": "search stage of one call: " + " + ".join(sorted({kernels[n] for n in ns})),
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
                 "search_ms_per_call": search_ms_call,
+                "autotuned": tuning,
                 "by_side_per_map_calls": by_side,
                 "stage_ms_per_step_uncaptured": {k: v[0] / 2 for k, v in prof2.items()}}
     e2e = None

@@ -352,16 +352,34 @@ int xcf_nearest_disorientation(xcf_ctx *ctx, const double *qa, int32_t na, const
 
 /* Several maps in one search (paper, Fig. 1 B-C, for every map of a batch;
  * the maps may have different detectors, pattern centres and libraries --
- * each map's detector is cropped to its 2^n square, e.g. 96 -> 64,
- * 160 / 200 -> 128 px).  Patterns are pre-processed per map, then all maps
- * are searched in ONE persistent launch that takes (map, pattern, template
- * range) work items from a queue; the work granularity per detector side and
- * library size is chosen by timing candidates on the first call (cached in
- * the context).  With XCF_MAPS_GRAPH the whole sequence is captured in a CUDA
- * graph the first time a batch configuration (pointers and sizes) is seen and
- * replayed afterwards: the patterns may change between calls, the pointers may
- * not.  Outputs per map as xcf_index.  Asynchronous with respect to `stream`
- * except for the first call of a configuration. */
+ * each map's detector is cropped to its square by the library's crop rule,
+ * e.g. 96 -> 64, 160 / 200 -> 128 px, or 96 and 160 kept whole with the
+ * native rule).  Patterns are pre-processed per map, then every map up to
+ * 160 x 160 is searched in ONE persistent launch (one 512-thread CTA per SM)
+ * that takes (map, pattern, template range) work items of all sides from one
+ * queue; 256 x 256 maps need four-CTA clusters and run the cluster search
+ * kernel in the same stream.  For each (detector side, library size) the
+ * search body and the work granularity are chosen by timing candidates on the
+ * first call (cached in the context; see xcf_maps_get_tuning): the body is one
+ * of the line-transform decompositions the queue has for that side,
+ *   XCF_BODY_REG     rows and columns as warp-line transforms in registers,
+ *                    N = R x 32 points (64, 96, 128, 160): R points per lane,
+ *                    five 32-point lane stages by shuffles;
+ *   XCF_BODY_ROUNDS  N = 128 only: three register rounds (16-point column
+ *                    FFTs; radix 8 + radix 4; 32-point row FFTs) with two
+ *                    shared-memory transposes (the kernel of xcf_index);
+ *   XCF_BODY_SMEM    N = 16, 32, 64: the surface in shared memory, radix-2
+ *                    line transforms;
+ * the number of patterns a CTA searches side by side (1, 2 or 4 groups of
+ * warps, each with its share of the shared memory, where the body fits), and
+ * the granularity, the number of template pairs per work item (the whole
+ * library, a quarter or a sixteenth).  With XCF_MAPS_GRAPH the whole
+ * sequence is captured in a CUDA graph the first time a batch configuration
+ * (pointers and sizes) is seen and replayed afterwards: the patterns may
+ * change between calls, the pointers may not.  Outputs per map as xcf_index
+ * (the same best template up to ties between bodies: different transform
+ * orders round differently).  Asynchronous with respect to `stream` except
+ * for the first call of a configuration. */
 typedef struct {
     const xcf_library *lib;   /* the map's library (its detector geometry)        */
     const float *patterns;    /* [P, H, W] float32 on the library's detector      */
@@ -372,6 +390,23 @@ typedef struct {
 } xcf_map_desc;
 #define XCF_MAPS_GRAPH 1
 int xcf_index_maps(xcf_ctx *ctx, const xcf_map_desc *maps, int32_t n_maps, int32_t flags, void *stream);
+
+#define XCF_BODY_REG 0
+#define XCF_BODY_ROUNDS 1
+#define XCF_BODY_SMEM 2
+/* The multi-map tuning of (side N, library size T) on ctx: the search body
+ * (XCF_BODY_*), the groups per CTA (1, 2 or 4 patterns side by side, each on
+ * 512 / groups threads and that share of the shared memory) and the template
+ * pairs per work item.  Host only.  get: XCF_ERR_ARG if that (N, T) has not
+ * been tuned yet.  set: fixes the choice (pairs clamped to the library's pair
+ * count) for later xcf_index_maps calls, instead of timing candidates, and
+ * drops the context's captured graph; XCF_ERR_ARG if the body does not serve
+ * side N, the groups are not 1, 2 or 4 or do not fit the body's shared
+ * memory (XCF_BODY_ROUNDS: 1; XCF_BODY_REG at 128 and 160: 1; at 96: 1 or 2),
+ * or T, pairs <= 0. */
+int xcf_maps_get_tuning(const xcf_ctx *ctx, int32_t N, int32_t T, int32_t *body, int32_t *groups,
+                        int32_t *pairs);
+int xcf_maps_set_tuning(xcf_ctx *ctx, int32_t N, int32_t T, int32_t body, int32_t groups, int32_t pairs);
 
 /* Search then refine in one call (device memory): xcf_index with pcs, seeds =
  * the library orientations of the best templates (identity for degenerate

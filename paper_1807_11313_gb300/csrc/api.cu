@@ -1809,48 +1809,79 @@ MapLayout maps_layout(const xcf_map_desc *maps, int n) {
 
 long long tune_key(int N, int T) { return ((long long)N << 32) | (unsigned)T; }
 
-int tuned_pairs(xcf_ctx *ctx, int N, int T) {
+const xcf_ctx::Tuning *tuned(const xcf_ctx *ctx, int N, int T) {
     for (auto &kv : ctx->tune)
-        if (kv.first == tune_key(N, T)) return kv.second;
-    return 0;
+        if (kv.key == tune_key(N, T)) return &kv;
+    return nullptr;
 }
 
-// work items, most expensive (largest detector) first so that the tail of
-// the persistent launch is made of short items
-// sides served by the persistent queue.  The queue kernel is shaped for the
-// 128 x 128 body (one CTA of 255 registers and 200 KB per SM); measured on
-// the batched workload, smaller sides ran 1.4-1.6x slower in that shape than
-// in their own kernels (six CTAs per SM) and 256 x 256 needs a cluster, so
-// those maps get their own launches in the same stream (and graph).
-bool queued_side(int N) { return N == 128; }
+// sides served by the persistent queue: every side up to 160 x 160 (512-thread
+// CTAs, one per SM, with shared memory for the largest body); 256 x 256 needs
+// a four-CTA cluster, so those maps run the cluster kernel in the same stream
+// (and graph)
+bool queued_side(int N) { return N != 256; }
 
-std::vector<WorkItem> maps_items(xcf_ctx *ctx, const xcf_map_desc *maps, int n, int p_limit = -1,
-                                 int only_map = -1, int pairs = 0) {
+// the body and grouping a side runs before (or without) tuning: the body of
+// its per-map kernel on whole CTAs
+int default_body(int N) { return N == 128 ? kBodyRounds : N < 64 ? kBodySmem : kBodyReg; }
+// whether G groups per CTA fit body b of side N (each group gets 1/G of the shared memory)
+bool groups_fit(int N, int b, int G) {
+    if (G != 1 && G != 2 && G != 4) return false;
+    if (b == kBodyRounds) return G == 1;
+    return maps_item_smem(N, b) <= ((maps_smem_bytes() / G) & ~(size_t)15);
+}
+int log2_groups(int G) { return G == 4 ? 2 : G == 2 ? 1 : 0; }
+
+// one choice of the tuner (or of xcf_maps_set_tuning) for one map
+struct Choice { int body, groups, pairs; };
+Choice choice_of(const xcf_ctx *ctx, const xcf_library *lib) {
+    const xcf_ctx::Tuning *t = tuned(ctx, lib->N, lib->T);
+    if (t) return {t->body, t->groups, t->pairs};
+    return {default_body(lib->N), 1, (lib->T + 1) / 2};
+}
+
+// the queue's items, ordered by phase (whole CTAs, two groups, four groups);
+// within a phase the most expensive (largest detector) first, so that the
+// tail of each phase is made of short items
+struct ItemList {
+    std::vector<WorkItem> v;
+    int offs[4] = {0, 0, 0, 0};
+};
+// p_limit >= 0: at most that many patterns per map; only_map >= 0: that map
+// alone, with the choice `force` if force.body >= 0
+ItemList maps_items(xcf_ctx *ctx, const xcf_map_desc *maps, int n, int p_limit = -1, int only_map = -1,
+                    Choice force = {-1, 1, 0}) {
     std::vector<int> order(n);
     for (int m = 0; m < n; ++m) order[m] = m;
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return maps[a].lib->N > maps[b].lib->N; });
-    std::vector<WorkItem> items;
+    std::vector<WorkItem> ph[3];
     for (int m : order) {
         if ((only_map >= 0 && m != only_map) || !queued_side(maps[m].lib->N)) continue;
         const int T = maps[m].lib->T, npairs = (T + 1) / 2;
-        int c = pairs > 0 ? pairs : tuned_pairs(ctx, maps[m].lib->N, T);
-        if (c <= 0) c = npairs;
+        const Choice c = force.body >= 0 ? force : choice_of(ctx, maps[m].lib);
+        const int pairs = c.pairs > 0 && c.pairs < npairs ? c.pairs : npairs;
         const int P = p_limit >= 0 && p_limit < maps[m].P ? p_limit : maps[m].P;
+        std::vector<WorkItem> &out = ph[log2_groups(c.groups)];
         for (int p = 0; p < P; ++p)
-            for (int pb = 0; pb < npairs; pb += c) items.push_back({m, p, pb, pb + c < npairs ? pb + c : npairs});
+            for (int pb = 0; pb < npairs; pb += pairs) out.push_back({m, p, pb, pb + pairs < npairs ? pb + pairs : npairs});
     }
-    return items;
+    ItemList L;
+    for (int k = 0; k < 3; ++k) {
+        L.offs[k] = (int)L.v.size();
+        L.v.insert(L.v.end(), ph[k].begin(), ph[k].end());
+    }
+    L.offs[3] = (int)L.v.size();
+    return L;
 }
 
 struct MapsDev {
     MapDev *maps;
     WorkItem *items;
-    int *counter;
+    int *counters;   // one per phase
     float2 *spec;
     int *degen;
     unsigned long long *keys;
-    float2 *work;
     int grid;
 };
 
@@ -1864,27 +1895,30 @@ int maps_scratch(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout 
         return rc;
     d->maps = static_cast<MapDev *>(mp);
     d->items = reinterpret_cast<WorkItem *>(static_cast<char *>(mp) + ((sizeof(MapDev) * n + 255) & ~(size_t)255));
-    d->counter = reinterpret_cast<int *>(static_cast<char *>(mp) + table);
+    d->counters = reinterpret_cast<int *>(static_cast<char *>(mp) + table);
     if (ctx->opt.upsample >= 2) {   // the peak step's argmax scratch, sized before any capture
         int maxp = 1, *am;
         for (int m = 0; m < n; ++m) maxp = maps[m].P > maxp ? maps[m].P : maxp;
         if ((rc = scratch_t(ctx, S_ARGMAX, maxp, &am))) return rc;
     }
     d->grid = ctx->num_sms;
-    d->work = nullptr;   // the queue serves 128 x 128 maps only: no global work arrays
     return XCF_OK;
 }
 
+// force.body >= 0: that body for map only_map (the tuner's trials)
 int maps_table_upload(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout &L, const MapsDev &d,
-                      const std::vector<WorkItem> &items, cudaStream_t st) {
+                      const ItemList &items, cudaStream_t st, int only_map = -1, Choice force = {-1, 1, 0}) {
     std::vector<MapDev> h(n);
     for (int m = 0; m < n; ++m) {
         const xcf_library *lib = maps[m].lib;
-        h[m] = {lib->N, lib->T, search_spectra(lib), d.spec + L.spec[m], d.degen + L.idx[m], d.keys + L.idx[m]};
+        const int body = force.body >= 0 && m == only_map ? force.body : choice_of(ctx, lib).body;
+        h[m] = {lib->N, lib->T, body, lib->spectra, lib->spectra_pk, d.spec + L.spec[m], d.degen + L.idx[m],
+                d.keys + L.idx[m]};
     }
     XCF_CHECK(cudaMemcpyAsync(d.maps, h.data(), sizeof(MapDev) * n, cudaMemcpyHostToDevice, st), "map table");
-    if (!items.empty())
-        XCF_CHECK(cudaMemcpyAsync(d.items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, st),
+    if (!items.v.empty())
+        XCF_CHECK(cudaMemcpyAsync(d.items, items.v.data(), sizeof(WorkItem) * items.v.size(), cudaMemcpyHostToDevice,
+                                  st),
                   "work items");
     XCF_CHECK(cudaStreamSynchronize(st), "map table");
     return XCF_OK;
@@ -1905,13 +1939,13 @@ int maps_prep(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout &L,
 
 // the capturable part: search of all maps in one launch, then each map's peak
 int maps_search_finish(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout &L, const MapsDev &d,
-                       int n_items, cudaStream_t st) {
+                       const ItemList &items, cudaStream_t st) {
     XCF_CHECK(cudaMemsetAsync(d.keys, 0, sizeof(unsigned long long) * L.idx_total, st), "clear keys");
-    XCF_CHECK(cudaMemsetAsync(d.counter, 0, sizeof(int), st), "clear queue");
-    if (n_items > 0)
-        XCF_LAUNCH(XCF_STAGE_SEARCH, st, launch_search_maps(d.maps, d.items, n_items, d.counter, d.work, d.grid, st),
+    XCF_CHECK(cudaMemsetAsync(d.counters, 0, 3 * sizeof(int), st), "clear queue");
+    if (!items.v.empty())
+        XCF_LAUNCH(XCF_STAGE_SEARCH, st, launch_search_maps(d.maps, d.items, items.offs, d.counters, d.grid, st),
                    "multi-map search");
-    for (int m = 0; m < n; ++m) {   // the other sides: their own kernels
+    for (int m = 0; m < n; ++m) {   // 256 x 256: the cluster kernel
         const xcf_library *lib = maps[m].lib;
         if (queued_side(lib->N)) continue;
         XCF_LAUNCH(XCF_STAGE_SEARCH, st,
@@ -1931,11 +1965,19 @@ int maps_search_finish(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapL
     return XCF_OK;
 }
 
-// time candidate work granularities on the first patterns of each untuned
-// (side, library size) and keep the fastest (patterns already pre-processed).
-// The sample spans several waves of the persistent grid: finer items balance
-// a short tail but break the library-order L2 reuse of a full-length sweep,
-// and one wave alone overstates the first and hides the second.
+// Time candidate (search body, groups per CTA, work granularity) choices on
+// the first patterns of each untuned (side, library size) and keep the
+// fastest (patterns already pre-processed).  Bodies: the line-transform
+// decompositions the queue has for the side (128: three register rounds with
+// shared-memory transposes, or warp lines of 4 x 32; 64: warp lines of
+// 2 x 32, or radix-2 lines with the surface in shared memory).  Groups: 1, 2
+// or 4 patterns side by side per CTA (each group on 512 / G threads and 1/G of
+// the shared memory) where the body fits.  Granularity: template pairs per
+// item.  Two stages: body and groups at a quarter of the library per item,
+// then the granularity for the best of those.  The sample spans several waves
+// of the persistent grid: finer items balance a short tail but break the
+// library-order L2 reuse of a full-length sweep, and one wave alone
+// overstates the first and hides the second.
 constexpr int kTuneWaves = 8;
 int maps_autotune(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout &L, const MapsDev &d,
                   cudaStream_t st) {
@@ -1943,50 +1985,76 @@ int maps_autotune(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout
     XCF_CHECK(cudaEventCreate(&e0), "event");
     XCF_CHECK(cudaEventCreate(&e1), "event");
     int status = XCF_OK;
+    const int sample = kTuneWaves * ctx->num_sms * 2;
+    auto trial = [&](int m, Choice c, float *per) -> int {
+        ItemList it = maps_items(ctx, maps, n, sample, m, c);
+        int rc = maps_table_upload(ctx, maps, n, L, d, it, st, m, c);
+        if (rc) return rc;
+        cudaMemsetAsync(d.keys, 0, sizeof(unsigned long long) * L.idx_total, st);
+        cudaMemsetAsync(d.counters, 0, 3 * sizeof(int), st);
+        cudaEventRecord(e0, st);
+        cudaError_t e = launch_search_maps(d.maps, d.items, it.offs, d.counters, d.grid, st);
+        cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const int pats = sample < maps[m].P ? sample : maps[m].P;
+        *per = ms / (pats > 0 ? pats : 1);
+        return XCF_OK;
+    };
     for (int m = 0; m < n && status == XCF_OK; ++m) {
-        const int N = maps[m].lib->N, T = maps[m].lib->T, npairs = (T + 1) / 2;
-        if (!queued_side(N) || tuned_pairs(ctx, N, T) > 0) continue;
-        const int cands[3] = {npairs, npairs / 4 > 8 ? npairs / 4 : 8, npairs / 16 > 8 ? npairs / 16 : 8};
-        int best_c = npairs;
-        float best_t = 1e30f;
-        for (int ci = 0; ci < 3 && status == XCF_OK; ++ci) {
-            if (ci > 0 && cands[ci] >= cands[ci - 1]) continue;
-            std::vector<WorkItem> it = maps_items(ctx, maps, n, kTuneWaves * ctx->num_sms, m, cands[ci]);
-            if ((status = maps_table_upload(ctx, maps, n, L, d, it, st))) break;
-            cudaMemsetAsync(d.keys, 0, sizeof(unsigned long long) * L.idx_total, st);
-            cudaMemsetAsync(d.counter, 0, sizeof(int), st);
-            cudaEventRecord(e0, st);
-            cudaError_t e = launch_search_maps(d.maps, d.items, (int)it.size(), d.counter, d.work, d.grid, st);
-            cudaEventRecord(e1, st);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            if (e != cudaSuccess) { status = cuda_fail(ctx, e, "autotune"); break; }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            const int pats = kTuneWaves * ctx->num_sms < maps[m].P ? kTuneWaves * ctx->num_sms : maps[m].P;
-            const float per = ms / (pats > 0 ? pats : 1);
-            if (per < best_t) { best_t = per; best_c = cands[ci]; }
+        const xcf_library *lib = maps[m].lib;
+        const int N = lib->N, T = lib->T, npairs = (T + 1) / 2;
+        if (!queued_side(N) || tuned(ctx, N, T)) continue;
+        const int quarter = npairs / 4 > 8 ? npairs / 4 : (npairs < 8 ? npairs : 8);
+        Choice best{default_body(N), 1, quarter};
+        float best_t = 1e30f, per = 0.f;
+        for (int body = 0; body < 3 && status == XCF_OK; ++body) {
+            if (!body_serves(N, body) || (body == kBodyRounds && !lib->spectra_pk)) continue;
+            for (int G = 1; G <= 4 && status == XCF_OK; G *= 2) {
+                if (!groups_fit(N, body, G)) continue;
+                if ((status = trial(m, {body, G, quarter}, &per))) break;
+                if (per < best_t) { best_t = per; best = {body, G, quarter}; }
+            }
         }
-        ctx->tune.push_back({tune_key(N, T), best_c});
+        const int cands[2] = {npairs, npairs / 16 > 8 ? npairs / 16 : 8};
+        for (int ci = 0; ci < 2 && status == XCF_OK; ++ci) {
+            if (cands[ci] == quarter || cands[ci] > npairs) continue;
+            Choice c = best;
+            c.pairs = cands[ci];
+            if ((status = trial(m, c, &per))) break;
+            if (per < best_t) { best_t = per; best = c; }
+        }
+        if (status == XCF_OK) ctx->tune.push_back({tune_key(N, T), best.body, best.groups, best.pairs});
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return status;
 }
 
-// launch shape of the queued items: persistent CTAs over the atomic queue
-// (grid = SMs) or one CTA per item (grid = 0).  Timed on the first waves of
-// the real item list and cached per batch configuration.
+// launch shape of the queued items: persistent CTAs over the atomic queues
+// (grid = SMs) or one CTA per 1, 2 or 4 items (grid = 0).  Timed on the first
+// waves of the real item list and cached per batch configuration.
 int maps_shape(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout &L, const MapsDev &d,
-               const std::vector<WorkItem> &items, const std::vector<char> &key, cudaStream_t st, int *grid) {
+               const ItemList &items, const std::vector<char> &key, cudaStream_t st, int *grid) {
     for (auto &kv : ctx->shape_cache)
         if (kv.first == key) {
             *grid = kv.second;
             return XCF_OK;
         }
     *grid = d.grid;
-    const size_t ns = std::min(items.size(), (size_t)kTuneWaves * ctx->num_sms);
-    if (ns > 0) {
-        std::vector<WorkItem> sample(items.begin(), items.begin() + ns);
+    if (!items.v.empty()) {
+        // a sample of each phase in proportion, kTuneWaves waves in all
+        ItemList sample;
+        const size_t want = (size_t)kTuneWaves * ctx->num_sms, total = items.v.size();
+        for (int k = 0; k < 3; ++k) {
+            sample.offs[k] = (int)sample.v.size();
+            const size_t cnt = (size_t)(items.offs[k + 1] - items.offs[k]);
+            const size_t take = total <= want ? cnt : (cnt * want + total - 1) / total;
+            sample.v.insert(sample.v.end(), items.v.begin() + items.offs[k], items.v.begin() + items.offs[k] + take);
+        }
+        sample.offs[3] = (int)sample.v.size();
         int rc = maps_table_upload(ctx, maps, n, L, d, sample, st);
         if (rc) return rc;
         cudaEvent_t e0, e1;
@@ -1996,9 +2064,9 @@ int maps_shape(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout &L
         const int shapes[2] = {d.grid, 0};
         for (int g : shapes) {
             cudaMemsetAsync(d.keys, 0, sizeof(unsigned long long) * L.idx_total, st);
-            cudaMemsetAsync(d.counter, 0, sizeof(int), st);
+            cudaMemsetAsync(d.counters, 0, 3 * sizeof(int), st);
             cudaEventRecord(e0, st);
-            cudaError_t e = launch_search_maps(d.maps, d.items, (int)ns, d.counter, d.work, g, st);
+            cudaError_t e = launch_search_maps(d.maps, d.items, sample.offs, d.counters, g, st);
             cudaEventRecord(e1, st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             if (e != cudaSuccess) {
@@ -2021,6 +2089,38 @@ int maps_shape(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout &L
 }
 
 }  // namespace
+
+int xcf_maps_get_tuning(const xcf_ctx *ctx, int32_t N, int32_t T, int32_t *body, int32_t *groups,
+                        int32_t *pairs) {
+    if (!ctx || !body || !groups || !pairs) return XCF_ERR_ARG;
+    const xcf_ctx::Tuning *t = tuned(ctx, N, T);
+    if (!t) return XCF_ERR_ARG;
+    *body = t->body;
+    *groups = t->groups;
+    *pairs = t->pairs;
+    return XCF_OK;
+}
+
+int xcf_maps_set_tuning(xcf_ctx *ctx, int32_t N, int32_t T, int32_t body, int32_t groups, int32_t pairs) {
+    if (!ctx) return XCF_ERR_ARG;
+    if (!queued_side(N) || !body_serves(N, body) || !groups_fit(N, body, groups) || T <= 0 || pairs <= 0)
+        return fail(ctx, XCF_ERR_ARG,
+                    "xcf_maps_set_tuning: body not served for this side, groups not 1 / 2 / 4 or not fitting, or "
+                    "T / pairs <= 0");
+    const int npairs = (T + 1) / 2;
+    if (pairs > npairs) pairs = npairs;
+    for (auto it = ctx->tune.begin(); it != ctx->tune.end(); ++it)
+        if (it->key == tune_key(N, T)) {
+            ctx->tune.erase(it);
+            break;
+        }
+    ctx->tune.push_back({tune_key(N, T), body, groups, pairs});
+    // captured graphs and launch shapes were made with the previous items
+    cudaSetDevice(ctx->device);
+    drop_graph(ctx);
+    ctx->shape_cache.clear();
+    return XCF_OK;
+}
 
 int xcf_index_maps(xcf_ctx *ctx, const xcf_map_desc *maps, int32_t n_maps, int32_t flags, void *stream) {
     if (!ctx) return XCF_ERR_ARG;
@@ -2059,19 +2159,20 @@ int xcf_index_maps(xcf_ctx *ctx, const xcf_map_desc *maps, int32_t n_maps, int32
     }
 
     // first call of this configuration: scratch, pre-processing, autotuning, work items
-    std::vector<WorkItem> items = maps_items(ctx, maps, n_maps);
-    size_t max_items = items.size();
+    ItemList items = maps_items(ctx, maps, n_maps);
+    size_t max_items = items.v.size();
     for (int m = 0; m < n_maps; ++m)   // the largest trial list of the autotuner
-        max_items = std::max(max_items, maps_items(ctx, maps, n_maps, kTuneWaves * ctx->num_sms, m, 8).size());
+        max_items = std::max(max_items, maps_items(ctx, maps, n_maps, 2 * kTuneWaves * ctx->num_sms, m,
+                                                   {kBodyReg, 1, 8}).v.size());
     if ((rc = maps_scratch(ctx, maps, n_maps, L, max_items, &d))) return rc;
     if ((rc = maps_prep(ctx, maps, n_maps, L, d, caller))) return rc;
     if ((rc = maps_autotune(ctx, maps, n_maps, L, d, caller))) return rc;
     items = maps_items(ctx, maps, n_maps);   // the tuned granularity may need a larger table
-    if (items.size() > max_items && (rc = maps_scratch(ctx, maps, n_maps, L, items.size(), &d))) return rc;
+    if (items.v.size() > max_items && (rc = maps_scratch(ctx, maps, n_maps, L, items.v.size(), &d))) return rc;
     if ((rc = maps_shape(ctx, maps, n_maps, L, d, items, key, caller, &d.grid))) return rc;
     if ((rc = maps_table_upload(ctx, maps, n_maps, L, d, items, caller))) return rc;
 
-    if (!graph) return maps_search_finish(ctx, maps, n_maps, L, d, (int)items.size(), caller);
+    if (!graph) return maps_search_finish(ctx, maps, n_maps, L, d, items, caller);
 
     // capture prep + search + peaks on the context's own stream, then replay
     if (!ctx->gstream) XCF_CHECK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking), "stream");
@@ -2085,7 +2186,7 @@ int xcf_index_maps(xcf_ctx *ctx, const xcf_map_desc *maps, int32_t n_maps, int32
     for (int i = 0; i < XCF_NUM_STAGES; ++i) before[i] = ctx->launches[i];
     XCF_CHECK(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal), "begin capture");
     rc = maps_prep(ctx, maps, n_maps, L, d, ctx->gstream);
-    if (rc == XCF_OK) rc = maps_search_finish(ctx, maps, n_maps, L, d, (int)items.size(), ctx->gstream);
+    if (rc == XCF_OK) rc = maps_search_finish(ctx, maps, n_maps, L, d, items, ctx->gstream);
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(ctx->gstream, &g);
     ctx->timing = timing;

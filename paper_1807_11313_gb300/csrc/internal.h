@@ -77,9 +77,10 @@ struct xcf_ctx {
     double ms[XCF_NUM_STAGES] = {};
     struct Rec { int stage; cudaEvent_t a, b; };
     std::vector<Rec> recs;
-    // multi-map search: autotuned template pairs per work item, keyed by (N, T),
-    // and the chosen launch shape per batch configuration
-    std::vector<std::pair<long long, int>> tune;
+    // multi-map search: autotuned search body and template pairs per work item,
+    // keyed by (N, T), and the chosen launch shape per batch configuration
+    struct Tuning { long long key; int body; int groups; int pairs; };
+    std::vector<Tuning> tune;
     std::vector<std::pair<std::vector<char>, int>> shape_cache;
     // multi-map search: captured graph of the last batch configuration
     std::vector<char> graph_key;

@@ -168,6 +168,15 @@ __device__ __forceinline__ void rows_phase_sp(float2 *Zc, const float2 *__restri
     }
 }
 
+// L2 prefetch of one quarter (this CTA's share) of a template's half spectrum:
+// the four CTAs of a cluster together bring the whole spectrum into L2 ahead
+// of the row phase that reads it
+constexpr uint32_t kSpecBytes = (uint32_t)(N * HW * sizeof(float2));   // 264,192 B, a multiple of 64
+__device__ __forceinline__ void prefetch_quarter(const float2 *spec, int c) {
+    const char *base = reinterpret_cast<const char *>(spec) + (size_t)c * (kSpecBytes / NC);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base), "r"(kSpecBytes / NC) : "memory");
+}
+
 __device__ __forceinline__ float warp_max(float v) {
     for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
@@ -211,6 +220,34 @@ k_search_c256(const float2 *__restrict__ St, int T, const float2 *__restrict__ S
     }
     const uint32_t red_local = (uint32_t)__cvta_generic_to_shared(red);
 
+    // template indices of pair pi of item `it` (negative candidate slots are skipped)
+    auto pair_templates = [&](int it, int pi, int &t1, int &t2) {
+        const int p = it / nchunks;
+        const int j1 = 2 * pi, j2 = min(j1 + 1, n - 1);
+        t1 = cand ? cand[(size_t)p * kc + j1] : j1;
+        t2 = cand ? cand[(size_t)p * kc + j2] : j2;
+    };
+    // prefetch the template pair that follows (item, pi) into L2: the next pair
+    // of the item, else the first pair of this cluster's next item
+    auto prefetch_next = [&](int it, int pi, int pe) {
+        if (tid != 0) return;
+        int nit = it, npi = pi + 1;
+        if (npi >= pe) {
+            nit = it + ncl;
+            if (nit >= n_items || degen[nit / nchunks]) return;
+            npi = (nit - (nit / nchunks) * nchunks) * ppc;
+            if (npi >= npairs) return;
+        }
+        int t1, t2;
+        pair_templates(nit, npi, t1, t2);
+        if (t1 >= 0) prefetch_quarter(St + (size_t)t1 * N * HW, c);
+        if (t2 >= 0 && t2 != t1) prefetch_quarter(St + (size_t)t2 * N * HW, c);
+    };
+    if (cid < n_items && !degen[cid / nchunks]) {   // the first pair of the first item
+        const int pb0 = (cid - (cid / nchunks) * nchunks) * ppc;
+        if (pb0 < npairs) prefetch_next(cid, pb0 - 1, pb0 + 1);
+    }
+
     for (int item = cid; item < n_items; item += ncl) {
         const int p = item / nchunks, ch = item - p * nchunks;
         const int pb = ch * ppc, pe = min(npairs, pb + ppc);
@@ -227,8 +264,9 @@ k_search_c256(const float2 *__restrict__ St, int T, const float2 *__restrict__ S
         int best_t = -1;
         for (int pi = pb; pi < pe; ++pi) {
             const int j1 = 2 * pi, j2 = min(j1 + 1, n - 1);
-            const int t1 = cand ? cand[(size_t)p * kc + j1] : j1;
-            const int t2 = cand ? cand[(size_t)p * kc + j2] : j2;
+            int t1, t2;
+            pair_templates(item, pi, t1, t2);
+            prefetch_next(item, pi, pe);
             const float2 *s1 = St + (size_t)max(t1, 0) * N * HW, *s2 = St + (size_t)max(t2, 0) * N * HW;
             rows_phase_sp(Zc, s1, s2, Psm, tw, scr, c, g, t, pending);
             cluster_barrier();

@@ -560,7 +560,7 @@ template <int N>
 cudaError_t search_n(const float2 *St, int T, const float2 *Sp, const int *degen, int P,
                      unsigned long long *keys, float *peaks_all, int num_sms, cudaStream_t st,
                      const int *cand = nullptr, int kc = 0) {
-    size_t sm = smem_bytes_generic<N>();
+    size_t sm = gen::smem_bytes<N>();
     cudaError_t e = set_smem(k_search_generic<N>, sm);
     if (e != cudaSuccess) return e;
     const int npairs = ((cand ? kc : T) + 1) / 2;

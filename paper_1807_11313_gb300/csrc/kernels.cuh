@@ -58,19 +58,42 @@ cudaError_t launch_topk_rows(const float *S, int P, int T, int k, int *cand, flo
 cudaError_t launch_to_bf16(const float *x, size_t n, void *y, cudaStream_t st);
 
 // multi-map search: one persistent launch over a queue of work items
+// search bodies of the multi-map queue (values of XCF_BODY_* in the header)
+constexpr int kBodyReg = 0;      // register warp-line transforms (N = R x 32: 64, 96, 128, 160)
+constexpr int kBodyRounds = 1;   // N = 128: three register rounds with two shared-memory transposes
+constexpr int kBodySmem = 2;     // surface in shared memory, radix-2 line transforms (2^k sides up to 64)
 struct MapDev {
-    int N, T;                      // detector side, library size
-    const float2 *St;              // library spectra as the side's search body reads them
+    int N, T, body;                // detector side, library size, search body (items of the map run on
+                                   // groups of 512 / G threads, G from the map's phase of the queue)
+    const float2 *St;              // library half spectra [T][N][N/2+1]
+    const float2 *Stp;             // N = 128: the same in the packed layout of the three-round body
     const float2 *Sp;              // the map's pattern spectra
     const int *degen;              // the map's degeneracy flags
     unsigned long long *keys;      // the map's best keys
 };
+// whether the queue serves side N with body b
+__host__ __device__ inline bool body_serves(int N, int b) {
+    if (b == kBodyReg) return N == 64 || N == 96 || N == 128 || N == 160;
+    if (b == kBodyRounds) return N == 128;
+    if (b == kBodySmem) return N == 16 || N == 32 || N == 64;
+    return false;
+}
 struct WorkItem {
     int map, p, pb, pe;            // pattern p of map `map` against template pairs [pb, pe)
 };
 size_t maps_smem_bytes();
-// grid > 0: persistent CTAs over an atomic queue (counter); grid <= 0: one CTA per item
-cudaError_t launch_search_maps(const MapDev *maps, const WorkItem *items, int n_items, int *counter, float2 *work,
+constexpr int kMapsThreads = 512;   // threads of a queue CTA
+// shared memory one item of side N with body b needs (the queue gives each of
+// the G groups of a CTA maps_smem_bytes() / G, rounded down to 16 bytes)
+inline size_t maps_item_smem(int N, int b) {
+    return b == kBodyRounds ? (size_t)8 * (128 * 65 + 128 * 128 + 128 + 128 + 256 + 32 + 128)
+                            : (size_t)8 * ((size_t)N * (N + 1) + N + 34);
+}
+// Items are ordered by phase: [offs[0], offs[1]) run on whole CTAs, [offs[1],
+// offs[2]) on two groups of 256 threads per CTA, [offs[2], offs[3]) on four
+// groups of 128.  grid > 0: persistent CTAs, each phase's items taken from its
+// own atomic counter (counters[0..2]); grid <= 0: one CTA per 1, 2 or 4 items.
+cudaError_t launch_search_maps(const MapDev *maps, const WorkItem *items, const int offs[4], int *counters,
                                int grid, cudaStream_t st);
 
 // N = 128: library half spectra -> the search kernel's packed layout

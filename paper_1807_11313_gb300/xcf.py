@@ -96,6 +96,8 @@ _SIGS = {
     "xcf_index_noalloc": ([_P, _P, _P, _I32, _P, _P, _P, _P], C.c_int),
     "xcf_noalloc_max_patterns": ([_I32], C.c_int),
     "xcf_index_maps": ([_P, _P, _I32, _I32, _P], C.c_int),
+    "xcf_maps_get_tuning": ([_P, _I32, _I32, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32)], C.c_int),
+    "xcf_maps_set_tuning": ([_P, _I32, _I32, _I32, _I32, _I32], C.c_int),
     "xcf_net_num_params": ([_I32], C.c_int64),
     "xcf_net_create": ([_P, _I32, _P, C.POINTER(_P)], C.c_int),
     "xcf_net_free": ([_P], C.c_int),
@@ -573,6 +575,20 @@ def xcf_rescore(ctx: Context, lib: Library, patterns, cand):
 XCF_MAPS_GRAPH = 1
 
 
+XCF_BODY_REG, XCF_BODY_ROUNDS, XCF_BODY_SMEM = 0, 1, 2
+
+
+def xcf_maps_get_tuning(ctx: Context, N: int, T: int):
+    """-> (body, groups, pairs) chosen for side N and library size T, or None if not tuned yet."""
+    b, g, p = _I32(), _I32(), _I32()
+    rc = load().xcf_maps_get_tuning(ctx.handle, int(N), int(T), C.byref(b), C.byref(g), C.byref(p))
+    return (b.value, g.value, p.value) if rc == XCF_OK else None
+
+
+def xcf_maps_set_tuning(ctx: Context, N: int, T: int, body: int, pairs: int, groups: int = 1):
+    _check(load().xcf_maps_set_tuning(ctx.handle, int(N), int(T), int(body), int(groups), int(pairs)), ctx.handle)
+
+
 def xcf_index_maps(ctx: Context, maps, outs=None, graph: bool = False):
     """Index several maps (each a (Library, patterns [P, H, W]) pair, detectors
     of any supported size) with one persistent search launch.  With graph=True
@@ -588,6 +604,7 @@ def xcf_index_maps(ctx: Context, maps, outs=None, graph: bool = False):
                          torch.empty((P, 2), dtype=torch.float32, device=d)))
     desc = (xcf_map_desc * max(n, 1))()
     for i, ((lib, pats), (best, peak, shift)) in enumerate(zip(maps, outs)):
+        _sizes(lib, pats.shape[0], patterns=pats, best=best, peak=peak, shift=shift)
         desc[i] = xcf_map_desc(lib.handle, _ptr(pats, torch.float32, "patterns"), pats.shape[0],
                                _ptr(best, torch.int32, "best"), _ptr(peak, torch.float32, "peak"),
                                _ptr(shift, torch.float32, "shift"))

@@ -8,8 +8,9 @@ tolerance), and the FP32 rescore over the candidate list (the returned best
 must be the oracle's argmax); everywhere, the refined orientations meet the
 accuracy bar.
 
-Batched form (eight maps, detectors 96 .. 256): the graph-captured multi-map
-search equals the per-map search bit for bit."""
+Batched form (eight maps, detectors 96 .. 256, 2,000-40,000 patterns per
+map): the graph-captured multi-map search (autotuned body and granularity per
+side) equals the per-map search up to ties between the bodies' roundings."""
 import numpy as np
 import pytest
 import torch
@@ -133,13 +134,22 @@ def test_batched_fullsize_equals_per_map(px):
         lib = px.xcf_build_library(ctx, master, d(m["lib_q"]), g)
         clean = px.xcf_project(ctx, master, d(m["truth_q"]), g, pcs=d(m["pcs"]))
         batch.append((lib, _noisy(torch, clean, d(m["pcs"]), d(m["peak"]), gen).contiguous()))
-    outs = px.xcf_index_maps(ctx, batch, graph=True)
+    outs = px.xcf_index_maps(ctx, batch, graph=True)               # tunes body and granularity, captures
     outs = px.xcf_index_maps(ctx, batch, outs=outs, graph=True)   # a replay
     for (lib, pats), o in zip(batch, outs):
         ref = px.xcf_index(ctx, lib, pats)
         torch.cuda.synchronize()
-        for a, b in zip(o, ref):
-            assert torch.equal(a, b)
+        # the tuned body may round differently from the per-map kernel: the best
+        # template is the same or ties with it (per-pair peaks within 2e-5 relative)
+        diff = torch.nonzero(o[0] != ref[0]).flatten()
+        assert diff.numel() <= max(2, pats.shape[0] // 1000), diff.numel()
+        if diff.numel():
+            allp = px.xcf_correlate_all(ctx, lib, pats[diff].contiguous())
+            rows = torch.arange(diff.numel(), device="cuda")
+            a, b = allp[rows, o[0][diff].long()], allp[rows, ref[0][diff].long()]
+            assert torch.all((a - b).abs() <= 2e-5 * b.abs())
+        same = o[0] == ref[0]
+        assert torch.equal(o[1][same], ref[1][same]) and torch.equal(o[2][same], ref[2][same])
     for lib, _ in batch:
         lib.close()
     ctx.close()
