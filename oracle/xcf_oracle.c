@@ -164,17 +164,17 @@ int orc_crop(int W, int H, int cap, double pcx, double pcy, double pcz,
 }
 
 /* The crop with native sides (native != 0): the largest side of
- * {16, 32, 64, 96, 128, 160, 256} that fits, so that 96- and 160-pixel
- * detectors are used whole (the paper crops to 2^n only because its FFT and
- * filters are easier there, footnote 1 of the FFT section). */
+ * {16, 32, 64, 96, 128, 160, 200, 256} that fits, so that 96-, 160- and
+ * 200-pixel detectors are used whole (the paper crops to 2^n only because its
+ * FFT and filters are easier there, footnote 1 of the FFT section). */
 int orc_crop_ex(int W, int H, int cap, int native, double pcx, double pcy, double pcz,
                 int *n_out, int *off_x, int *off_y, double pc_out[3]) {
-    static const int sides[7] = {16, 32, 64, 96, 128, 160, 256};
+    static const int sides[8] = {16, 32, 64, 96, 128, 160, 200, 256};
     int m = W < H ? W : H;
     int n = 1;
     if (native) {
         n = 0;
-        for (int i = 0; i < 7; ++i)
+        for (int i = 0; i < 8; ++i)
             if (sides[i] <= m && sides[i] <= cap) n = sides[i];
     } else {
         while (n * 2 <= m && n * 2 <= cap) n *= 2;

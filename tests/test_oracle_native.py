@@ -1,5 +1,5 @@
-"""Pins of the oracle on native (non power of two) detector sides, 96 and
-160 px: the transforms against numpy's FFT (a library routine), the native
+"""Pins of the oracle on native (non power of two) detector sides, 96, 160
+and 200 px: the transforms against numpy's FFT (a library routine), the native
 crop rule, the correlation invariants (self peak, exact integer rolls,
 brute-force spatial correlation), library matching and refinement."""
 import numpy as np
@@ -11,7 +11,7 @@ import synth
 PC0 = (0.5, 0.5, 0.6)
 
 
-@pytest.mark.parametrize("n", [96, 160])
+@pytest.mark.parametrize("n", [96, 160, 200])
 def test_transform_is_numpys_fft(n):
     rng = np.random.default_rng(n)
     x = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
@@ -20,16 +20,19 @@ def test_transform_is_numpys_fft(n):
 
 
 def test_native_crop_sides():
-    # the largest side of {16, 32, 64, 96, 128, 160, 256} that fits; PC kept on the same pixel
+    # the largest side of {16, 32, 64, 96, 128, 160, 200, 256} that fits; PC kept on the same pixel
     assert orc.crop(96, 96, PC0, native=True)[:3] == (96, 0, 0)
     assert orc.crop(160, 160, PC0, native=True)[:3] == (160, 0, 0)
+    assert orc.crop(200, 200, PC0, native=True)[:3] == (200, 0, 0)
+    assert orc.crop(240, 210, PC0, native=True)[:3] == (200, 20, 5)
+    assert orc.crop(300, 256, PC0, native=True)[:3] == (256, 22, 0)
     n, ox, oy, pc = orc.crop(200, 180, (0.4, 0.45, 0.6), native=True)
     assert (n, ox, oy) == (160, 20, 10)
     np.testing.assert_allclose(pc, [(0.4 * 200 - 20) / 160, (0.45 * 180 - 10) / 160, 0.6 * 200 / 160])
     assert orc.crop(96, 96, PC0)[0] == 64 and orc.crop(200, 200, PC0)[0] == 128   # the 2^k rule is unchanged
 
 
-@pytest.mark.parametrize("n", [96, 160])
+@pytest.mark.parametrize("n", [96, 160, 200])
 def test_self_peak_and_integer_rolls(n):
     master = synth.master_pattern("bcc", 512)
     img = orc.project_many(master, synth.random_quaternions(1, 3), PC0, n)[0]
@@ -68,3 +71,18 @@ def test_library_match_and_refinement_at_96():
     pts = orc.project_many(master, truth, PC0, n).astype(np.float32)
     q, _, it = orc.refine_many(master, pts, lib[:2], PC0, max_it=6)
     assert orc.disorientation(q, truth).max() < 0.02
+
+
+def test_library_match_at_200():
+    """A pattern simulated at a library orientation returns that template with
+    peak 1 on the native 200 px side (lines of 200 = 8 x 25 points as direct
+    DFTs)."""
+    master = synth.master_pattern("bcc", 512)
+    n = 200
+    lib = synth.random_quaternions(6, 17)
+    St, _, _ = orc.prep_many(orc.project_many(master, lib, PC0, n))
+    Sp, _, deg = orc.prep_many(orc.project_many(master, lib[[4, 1]], PC0, n))
+    best, pk, sh, _ = orc.index(St, Sp, deg)
+    assert best.tolist() == [4, 1]
+    np.testing.assert_allclose(pk, 1.0, atol=1e-12)
+    np.testing.assert_allclose(sh, 0.0, atol=1e-9)
