@@ -79,8 +79,9 @@ typedef struct {
                             whole image as one window                               */
     int32_t native_sizes; /* crop rule: 0 = the largest 2^k square (default, the
                              paper's practice); 1 = the largest of 16, 32, 64, 96,
-                             128, 160, 256 px, so that 96 and 160 px detectors are
-                             used whole (mixed-radix 3 x 32 and 5 x 32 transforms);
+                             128, 160, 200, 256 px, so that 96, 160 and 200 px
+                             detectors are used whole (mixed-radix 3 x 32 and
+                             5 x 32 transforms; 8 x 5 x 5 at 200);
                              a library keeps the rule of the context that built it.
                              The NDP calls and the proposal network need 2^k sides */
 } xcf_options;
@@ -112,7 +113,7 @@ int xcf_crop(const xcf_geometry *g, int32_t *n, int32_t *off_x, int32_t *off_y,
 
 /* The same with the crop rule chosen: native = 0 is xcf_crop's 2^k rule, 1 the
  * native rule of xcf_options.native_sizes (the largest of 16, 32, 64, 96, 128,
- * 160, 256 px that fits).  A caller sizing xcf_prep's outputs on a context
+ * 160, 200, 256 px that fits).  A caller sizing xcf_prep's outputs on a context
  * with native_sizes = 1 takes n from here.  XCF_ERR_ARG if native is not 0/1. */
 int xcf_crop_ex(const xcf_geometry *g, int32_t native, int32_t *n, int32_t *off_x,
                 int32_t *off_y, double pc_out[3]);
@@ -357,8 +358,9 @@ int xcf_nearest_disorientation(xcf_ctx *ctx, const double *qa, int32_t na, const
  * native rule).  Patterns are pre-processed per map, then every map up to
  * 160 x 160 is searched in ONE persistent launch (one 512-thread CTA per SM)
  * that takes (map, pattern, template range) work items of all sides from one
- * queue; 256 x 256 maps need four-CTA clusters and run the cluster search
- * kernel in the same stream.  For each (detector side, library size) the
+ * queue; 256 x 256 maps (four-CTA clusters) and native 200 x 200 maps (one
+ * template per pass through the real-output transform) run their own search
+ * kernels in the same stream.  For each (detector side, library size) the
  * search body and the work granularity are chosen by timing candidates on the
  * first call (cached in the context; see xcf_maps_get_tuning): the body is one
  * of the line-transform decompositions the queue has for that side,

@@ -111,9 +111,9 @@ int crop_of(const xcf_geometry *g, int cap, Crop *c, bool native = false) {
     int m = g->width < g->height ? g->width : g->height;
     int n = 1;
     if (native) {
-        static const int sides[7] = {16, 32, 64, 96, 128, 160, 256};
+        static const int sides[8] = {16, 32, 64, 96, 128, 160, 200, 256};
         n = 0;
-        for (int i = 0; i < 7; ++i)
+        for (int i = 0; i < 8; ++i)
             if (sides[i] <= m && sides[i] <= cap) n = sides[i];
     } else {
         while (n * 2 <= m && n * 2 <= cap) n *= 2;
@@ -233,19 +233,21 @@ PrepArgs prep_args_square(const Crop &c, const Resolved &r) {
 }
 
 bool supported_n(int n) {
-    return n == 16 || n == 32 || n == 64 || n == 96 || n == 128 || n == 160 || n == 256;
+    return n == 16 || n == 32 || n == 64 || n == 96 || n == 128 || n == 160 || n == 200 || n == 256;
 }
 
 // pre-processing, search and peak: shared-memory kernels up to N = 160, the
 // four-CTA cluster kernels for N = 256
 cudaError_t run_prep(xcf_ctx * /*ctx*/, const float *img, int P, const PrepArgs &a, float2 *spec, float *spatial,
                      int *degen, const int *active, cudaStream_t st) {
+    if (a.N == 200) return launch_prep_n200(img, P, a, spec, spatial, degen, active, st);
     if (a.N != 256) return launch_prep(img, P, a, spec, spatial, degen, active, st);
     return launch_prep_c256(img, P, a, spec, spatial, degen, active, st);
 }
 
 cudaError_t run_search(xcf_ctx * /*ctx*/, int n, const float2 *St, int T, const float2 *Sp, const int *degen, int P,
                        unsigned long long *keys, float *peaks_all, int num_sms, cudaStream_t st) {
+    if (n == 200) return launch_search_n200(St, T, Sp, degen, P, keys, peaks_all, num_sms, st, nullptr, 0);
     if (n != 256) return launch_search(n, St, T, Sp, degen, P, keys, peaks_all, num_sms, st);
     return launch_search_c256(St, T, Sp, degen, P, keys, peaks_all, nullptr, 0, st);
 }
@@ -256,8 +258,9 @@ cudaError_t run_pair_peak(xcf_ctx *ctx, int n, const float2 *St, const int *tidx
     const int U = ctx->opt.upsample;
     int *argmax = nullptr;
     if (U >= 2 && P > 0 && scratch_t(ctx, S_ARGMAX, P, &argmax)) return cudaErrorMemoryAllocation;
-    cudaError_t e = n != 256 ? launch_pair_peak(n, St, tidx, Sp, degen, active, P, peak, shift, st, argmax)
-                             : launch_pair_peak_c256(St, tidx, Sp, degen, active, P, peak, shift, st, argmax);
+    cudaError_t e = n == 200   ? launch_pair_peak_n200(St, tidx, Sp, degen, active, P, peak, shift, argmax, st)
+                    : n != 256 ? launch_pair_peak(n, St, tidx, Sp, degen, active, P, peak, shift, st, argmax)
+                               : launch_pair_peak_c256(St, tidx, Sp, degen, active, P, peak, shift, st, argmax);
     if (e != cudaSuccess || U < 2) return e;
     return launch_upsample_peak(n, St, tidx, Sp, degen, active, P, U, argmax, peak, shift, st);
 }
@@ -1819,7 +1822,7 @@ const xcf_ctx::Tuning *tuned(const xcf_ctx *ctx, int N, int T) {
 // CTAs, one per SM, with shared memory for the largest body); 256 x 256 needs
 // a four-CTA cluster, so those maps run the cluster kernel in the same stream
 // (and graph)
-bool queued_side(int N) { return N != 256; }
+bool queued_side(int N) { return N != 256 && N != 200; }
 
 // the body and grouping a side runs before (or without) tuning: the body of
 // its per-map kernel on whole CTAs

@@ -600,6 +600,7 @@ cudaError_t launch_prep(const float *img, int P, const PrepArgs &a, float2 *spec
         case 128: return prep_n<128>(img, P, a, spec, spatial, degen, active, st);
         case 96: return prep_cplx_n<96>(img, P, a, spec, spatial, degen, active, st);
         case 160: return prep_cplx_n<160>(img, P, a, spec, spatial, degen, active, st);
+        case 200: return launch_prep_n200(img, P, a, spec, spatial, degen, active, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -614,6 +615,7 @@ cudaError_t launch_search(int N, const float2 *St, int T, const float2 *Sp, cons
         case 128: return launch_search128(St, T, Sp, degen, P, keys, peaks_all, num_sms, st);
         case 96: return search_n<96>(St, T, Sp, degen, P, keys, peaks_all, num_sms, st);
         case 160: return search_n<160>(St, T, Sp, degen, P, keys, peaks_all, num_sms, st);
+        case 200: return launch_search_n200(St, T, Sp, degen, P, keys, peaks_all, num_sms, st, nullptr, 0);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -635,6 +637,7 @@ cudaError_t launch_search_list(int N, const float2 *St, const int *cand, int kc,
         case 128: return search_n<128>(St, 0, Sp, degen, P, keys, peaks, num_sms, st, cand, kc);
         case 96: return search_n<96>(St, 0, Sp, degen, P, keys, peaks, num_sms, st, cand, kc);
         case 160: return search_n<160>(St, 0, Sp, degen, P, keys, peaks, num_sms, st, cand, kc);
+        case 200: return launch_search_n200(St, 0, Sp, degen, P, keys, peaks, num_sms, st, cand, kc);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -650,6 +653,7 @@ cudaError_t launch_pair_peak(int N, const float2 *St, const int *tidx, const flo
         case 128: return pair_peak_n<128>(St, tidx, Sp, degen, active, P, peak, shift, argmax, st);
         case 96: return pair_peak_n<96>(St, tidx, Sp, degen, active, P, peak, shift, argmax, st);
         case 160: return pair_peak_n<160>(St, tidx, Sp, degen, active, P, peak, shift, argmax, st);
+        case 200: return launch_pair_peak_n200(St, tidx, Sp, degen, active, P, peak, shift, argmax, st);
         default: return cudaErrorInvalidValue;
     }
 }

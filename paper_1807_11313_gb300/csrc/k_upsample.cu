@@ -134,6 +134,7 @@ cudaError_t launch_upsample_peak(int N, const float2 *St, const int *tidx, const
         case 128: return upsample_n<128>(St, tidx, Sp, degen, active, P, U, argmax, peak, shift, st);
         case 96: return upsample_n<96>(St, tidx, Sp, degen, active, P, U, argmax, peak, shift, st);
         case 160: return upsample_n<160>(St, tidx, Sp, degen, active, P, U, argmax, peak, shift, st);
+        case 200: return upsample_n<200>(St, tidx, Sp, degen, active, P, U, argmax, peak, shift, st);
         case 256: return upsample_n<256>(St, tidx, Sp, degen, active, P, U, argmax, peak, shift, st);
         default: return cudaErrorInvalidValue;
     }

@@ -215,3 +215,14 @@ cudaError_t launch_fallback_seeds(const int *fb, const int *best, const double *
 // FP32 FMA rate probe (k_peak.cu): flops of one launch of the given shape
 cudaError_t launch_fma_rate(int blocks, int threads, int iters, float *sink, cudaStream_t st);
 double fma_rate_flops(int blocks, int threads, int iters);
+
+// the native 200 x 200 side (k_n200.cu): pre-processing, the all-pairs search
+// (cand != null: each pattern's candidate list of kc library indices) and the
+// single-surface peak, with the arguments of the launchers above
+cudaError_t launch_prep_n200(const float *img, int P, const PrepArgs &a, float2 *spec, float *spatial, int *degen,
+                             const int *active, cudaStream_t st);
+cudaError_t launch_search_n200(const float2 *St, int T, const float2 *Sp, const int *degen, int P,
+                               unsigned long long *keys, float *peaks_all, int num_sms, cudaStream_t st,
+                               const int *cand, int kc);
+cudaError_t launch_pair_peak_n200(const float2 *St, const int *tidx, const float2 *Sp, const int *degen,
+                                  const int *active, int P, float *peak, float *shift, int *argmax, cudaStream_t st);

@@ -65,7 +65,8 @@ def test_native_crop_rule_matches_oracle(orc):
     pattern centre as the oracle's; the 2^k rule stays the default."""
     from paper_1807_11313_gb300 import xcf
     for W, H, pc in ((96, 96, (0.5, 0.5, 0.6)), (200, 180, (0.4, 0.45, 0.6)), (170, 300, (0.52, 0.3, 0.7)),
-                     (100, 98, (0.5, 0.5, 0.6)), (1200, 1000, (0.5, 0.5, 0.6))):
+                     (100, 98, (0.5, 0.5, 0.6)), (1200, 1000, (0.5, 0.5, 0.6)), (200, 200, (0.5, 0.5, 0.6)),
+                     (240, 210, (0.45, 0.5, 0.62))):
         g = xcf.geometry(W, H, pc)
         n, ox, oy, pcc = xcf.xcf_crop(g, native=True)
         on, oox, ooy, opc = orc.crop(W, H, pc, native=True)
@@ -73,6 +74,7 @@ def test_native_crop_rule_matches_oracle(orc):
         np.testing.assert_allclose(pcc, opc, rtol=1e-15)
         assert xcf.xcf_crop(g)[:3] == orc.crop(W, H, pc)[:3]
     assert xcf.xcf_crop(xcf.geometry(96, 96), native=True)[0] == 96
+    assert xcf.xcf_crop(xcf.geometry(200, 200), native=True)[0] == 200
     assert xcf.xcf_crop(xcf.geometry(96, 96))[0] == 64
     assert xcf.load().xcf_crop_ex(ctypes.byref(xcf.geometry(96, 96)), 2, None, None, None, None) == xcf.XCF_ERR_ARG
 

@@ -1,8 +1,11 @@
-"""Native 96 x 96 and 160 x 160 detectors (option native_sizes: mixed-radix
-3 x 32 and 5 x 32 line transforms, two images per pre-processing CTA) against
+"""Native 96 x 96, 160 x 160 and 200 x 200 detectors (option native_sizes:
+mixed-radix 3 x 32 and 5 x 32 register line transforms with two images per
+pre-processing CTA at 96 and 160; at 200 one template per pass through the
+real-output transform, 8 x 5 x 5 and 4 x 5 x 5 Stockham line passes) against
 the oracle, whose lines of those lengths are direct DFTs: pre-processing
 (spectra, spatial images, degeneracy, cropping), all-pairs correlation peaks,
-library search, the up-sampled peak and the refinement."""
+library search, candidate-list rescore, the up-sampled peak and the
+refinement."""
 import numpy as np
 import pytest
 import torch
@@ -39,7 +42,7 @@ def host(t):
     return t.cpu().numpy()
 
 
-@pytest.mark.parametrize("n", [96, 160])
+@pytest.mark.parametrize("n", [96, 160, 200])
 def test_native_prep_matches_oracle(px, nctx, orc, n):
     rng = np.random.default_rng(n)
     imgs = (rng.standard_normal((5, n, n)) * 3 + 7).astype(np.float32)   # odd count: a lone last image
@@ -63,6 +66,16 @@ def test_native_crop_of_a_rectangular_detector(px, nctx, orc):
     assert spec.shape[1] == 160
     S, _, _ = orc.prep_many(imgs[:, oy:oy + n, ox:ox + n])
     np.testing.assert_allclose(host(spec), S[:, :, : n // 2 + 1], rtol=0, atol=2e-6)
+    # a 240 x 210 detector keeps a 200 px square
+    W, H = 240, 210
+    imgs = rng.standard_normal((2, H, W)).astype(np.float32)
+    g = px.geometry(W, H, (0.5, 0.48, 0.6))
+    n, ox, oy, _ = orc.crop(W, H, (0.5, 0.48, 0.6), native=True)
+    assert (n, ox, oy) == (200, 20, 5) and px.xcf_crop(g, native=True)[:3] == (200, 20, 5)
+    spec, spat, _ = px.xcf_prep(nctx, dev(imgs), g, want_spatial=True)
+    S, y, _ = orc.prep_many(imgs[:, oy:oy + n, ox:ox + n], want_spatial=True)
+    np.testing.assert_allclose(host(spec), S[:, :, : n // 2 + 1], rtol=0, atol=2e-6)
+    np.testing.assert_allclose(host(spat), y, rtol=0, atol=2e-6)
 
 
 def _patterns(orc, master, lib_q, idx, n, seed, pc=PC0, peak=300.0, perturb_deg=2.0):
@@ -71,7 +84,7 @@ def _patterns(orc, master, lib_q, idx, n, seed, pc=PC0, peak=300.0, perturb_deg=
     return synth.add_noise(clean, np.broadcast_to(np.asarray(pc), (len(idx), 3)), peak, seed + 1), q
 
 
-@pytest.mark.parametrize("n,T,P", [(96, 23, 5), (160, 9, 3)])
+@pytest.mark.parametrize("n,T,P", [(96, 23, 5), (160, 9, 3), (200, 7, 3)])
 def test_native_search_matches_oracle(px, nctx, orc, n, T, P):
     master = synth.master_pattern("bcc", 512)
     lq = synth.random_quaternions(T, 60 + n)
@@ -92,11 +105,20 @@ def test_native_search_matches_oracle(px, nctx, orc, n, T, P):
     np.testing.assert_allclose(peak[same], opk[same], rtol=1e-4, atol=1e-6)
     np.testing.assert_allclose(shift[same], osh[same], atol=2e-3)
     assert best[-1] == -1 and peak[-1] == 0.0
+    # the candidate-list search (the rescore) over every template in a shuffled order finds the same best
+    cand = np.stack([np.random.default_rng(p).permutation(T) for p in range(P + 1)]).astype(np.int32)
+    cand[0, -1] = -1                                   # an empty slot is skipped
+    rb, rpk, rsh = (host(t) for t in px.xcf_rescore(nctx, lib, dev(pimgs), dev(cand)))
+    for p in range(P):
+        allowed = [t for t in cand[p] if t >= 0]
+        ob_p = max(allowed, key=lambda t: (allp[p, t], -t))
+        assert rb[p] == ob_p or abs(allp[p, rb[p]] - allp[p, ob_p]) <= 2e-5 * abs(allp[p, ob_p])
     lib.close()
 
 
-def test_native_upsampled_peak_matches_oracle(px, orc):
-    n, U = 96, 5
+@pytest.mark.parametrize("n", [96, 200])
+def test_native_upsampled_peak_matches_oracle(px, orc, n):
+    U = 5
     ctx = px.Context(native_sizes=1, upsample=U)
     master = synth.master_pattern("bcc", 512)
     lq = synth.random_quaternions(6, 81)
@@ -114,7 +136,7 @@ def test_native_upsampled_peak_matches_oracle(px, orc):
     ctx.close()
 
 
-@pytest.mark.parametrize("n,P", [(96, 6), (160, 3)])
+@pytest.mark.parametrize("n,P", [(96, 6), (160, 3), (200, 3)])
 def test_native_refine_matches_oracle(px, orc, n, P):
     master = synth.master_pattern("bcc", 1024)
     seeds = synth.random_quaternions(P, 90 + n)
@@ -139,8 +161,9 @@ def test_native_refine_matches_oracle(px, orc, n, P):
 
 
 def test_native_maps_batch_matches_oracle(px, orc):
-    """One xcf_index_maps call over native 96 / 160 maps, a 2^k map and a 200 px
-    detector (native rule: 160) against the oracle's search of each map."""
+    """One xcf_index_maps call over native 96 / 160 maps, a 2^k map and a
+    native 200 px map (the cluster-free 200 kernel in the same stream) against
+    the oracle's search of each map."""
     master = synth.master_pattern("bcc", 512)
     c = px.Context(native_sizes=1)
     batch, oracle_in = [], []
@@ -157,7 +180,7 @@ def test_native_maps_batch_matches_oracle(px, orc):
         lib = px.xcf_build_library_images(c, dev(tfull), dev(lq), px.geometry(W, W, PC0))
         batch.append((lib, dev(pfull)))
         oracle_in.append((timgs, pimgs))
-    assert [lib.N for lib, _ in batch] == [96, 160, 128, 160]
+    assert [lib.N for lib, _ in batch] == [96, 160, 128, 200]
     outs = px.xcf_index_maps(c, batch)
     for (best, peak, shift), (timgs, pimgs), (lib, _) in zip(outs, oracle_in, batch):
         best, peak, shift = host(best), host(peak), host(shift)
