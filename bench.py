@@ -784,7 +784,7 @@ def run_batched(args, px, torch, dev, rank, world, local, dist, emit=True):
         d["frac"] = d["achieved_tflops"] / fp32_peak
     achieved = flops / (search_ms_call / 1e3) / 1e12
     kernels = {16: "k_search_maps", 32: "k_search_maps", 64: "k_search_maps", 96: "k_search_maps",
-               128: "k_search_maps", 160: "k_search_maps", 256: "k_search_c256"}
+               128: "k_search_maps", 160: "k_search_maps", 200: "k_search_n200", 256: "k_search_c256"}
     body_names = {0: "warp lines (R x 32)", 1: "three rounds (16x8 | 4x32)", 2: "radix-2 in shared memory"}
     tuning = {}
     for (lib, _), n in zip(batch, ns):
