@@ -168,20 +168,41 @@ __device__ __forceinline__ void build_pair_spectrum(float2 *buf, const float2 *_
 // Z = X1 + i X2 at the N/32 points c = lane + 32 j of row r (build_pair_spectrum
 // for one row, into registers).  The two halves of the row differ only in the
 // stored row they read and in signs, so both are loaded through one index.
+// Split in two so that a row's loads can be issued a row ahead: pair_row_load
+// fetches the spectra, pair_row_make combines them.
 template <int N>
-__device__ __forceinline__ void pair_row(float2 (&v)[N / 32], int r, int lane, const float2 *__restrict__ t1,
-                                         const float2 *__restrict__ t2, const float2 *__restrict__ sp) {
+struct PairRowRaw {
+    float2 a[N / 32], b[N / 32], s[N / 32];
+};
+template <int N>
+__device__ __forceinline__ void pair_row_load(PairRowRaw<N> &w, int r, int lane, const float2 *__restrict__ t1,
+                                              const float2 *__restrict__ t2, const float2 *__restrict__ sp) {
     constexpr int HW = N / 2 + 1;
     const int rr = r == 0 ? 0 : N - r;
 #pragma unroll
     for (int j = 0; j < N / 32; ++j) {
         const int c = lane + 32 * j;
-        const bool lo = c <= N / 2;
-        const int k = lo ? r * HW + c : rr * HW + (N - c);
-        const float2 s = sp[k];
-        const float2 x1 = c_mulcj(t1[k], s), x2 = c_mulcj(t2[k], s);
-        v[j] = lo ? make_float2(x1.x - x2.y, x1.y + x2.x) : make_float2(x1.x + x2.y, x2.x - x1.y);
+        const int k = c <= N / 2 ? r * HW + c : rr * HW + (N - c);
+        w.s[j] = sp[k];
+        w.a[j] = t1[k];
+        w.b[j] = t2[k];
     }
+}
+template <int N>
+__device__ __forceinline__ void pair_row_make(float2 (&v)[N / 32], const PairRowRaw<N> &w, int lane) {
+#pragma unroll
+    for (int j = 0; j < N / 32; ++j) {
+        const int c = lane + 32 * j;
+        const float2 x1 = c_mulcj(w.a[j], w.s[j]), x2 = c_mulcj(w.b[j], w.s[j]);
+        v[j] = c <= N / 2 ? make_float2(x1.x - x2.y, x1.y + x2.x) : make_float2(x1.x + x2.y, x2.x - x1.y);
+    }
+}
+template <int N>
+__device__ __forceinline__ void pair_row(float2 (&v)[N / 32], int r, int lane, const float2 *__restrict__ t1,
+                                         const float2 *__restrict__ t2, const float2 *__restrict__ sp) {
+    PairRowRaw<N> w;
+    pair_row_load<N>(w, r, lane, t1, t2, sp);
+    pair_row_make<N>(v, w, lane);
 }
 
 // search_body for N = R x 32 >= 64: per template pair, each warp builds its
@@ -190,7 +211,9 @@ __device__ __forceinline__ void pair_row(float2 (&v)[N / 32], int r, int lane, c
 // columns, transforms them and keeps the running maxima of the real and
 // imaginary parts in registers (the surface is never written back); after a
 // second barrier thread 0 combines the warps' maxima.
-template <int N>
+// PF: fetch the next row's spectra a row ahead (R x 6 more registers per
+// thread: for CTAs of at most 512 threads, whose register budget has room)
+template <int N, bool PF = true>
 __device__ void search_body_reg(const float2 *__restrict__ St, int T, const float2 *__restrict__ Sp, int p, int pb,
                                 int pe, unsigned long long *__restrict__ keys, float *__restrict__ peaks_all,
                                 const int *__restrict__ cand, int kc, const Grp &g) {
@@ -212,13 +235,28 @@ __device__ void search_body_reg(const float2 *__restrict__ St, int T, const floa
         const int t1 = cand ? cand[(size_t)p * kc + j1] : j1;
         const int t2 = cand ? cand[(size_t)p * kc + j2] : j2;
         const float2 *s1 = St + (size_t)max(t1, 0) * N * HW, *s2 = St + (size_t)max(t2, 0) * N * HW;
-        // rows (the previous pair's column reads ended at its second barrier)
-        for (int r = w; r < N; r += nw) {
-            float2 v[R];
-            pair_row<N>(v, r, lane, s1, s2, sp);
-            warp_fft_core<N>(v, tw, lane);
+        // rows (the previous pair's column reads ended at its second barrier); the
+        // spectra of the warp's next row are fetched before this row is transformed,
+        // so their L2 latency overlaps the transform
+        if constexpr (PF) {
+            PairRowRaw<N> raw;
+            if (w < N) pair_row_load<N>(raw, w, lane, s1, s2, sp);
+            for (int r = w; r < N; r += nw) {
+                float2 v[R];
+                pair_row_make<N>(v, raw, lane);
+                if (r + nw < N) pair_row_load<N>(raw, r + nw, lane, s1, s2, sp);
+                warp_fft_core<N>(v, tw, lane);
 #pragma unroll
-            for (int j = 0; j < R; ++j) buf[r * LD + warp_fft_out<N>(lane, j)] = v[j];
+                for (int j = 0; j < R; ++j) buf[r * LD + warp_fft_out<N>(lane, j)] = v[j];
+            }
+        } else {
+            for (int r = w; r < N; r += nw) {
+                float2 v[R];
+                pair_row<N>(v, r, lane, s1, s2, sp);
+                warp_fft_core<N>(v, tw, lane);
+#pragma unroll
+                for (int j = 0; j < R; ++j) buf[r * LD + warp_fft_out<N>(lane, j)] = v[j];
+            }
         }
         g.sync();
         // columns: maxima only
@@ -260,11 +298,11 @@ __device__ void search_body_reg(const float2 *__restrict__ St, int T, const floa
     }
     if (g.t == 0 && best_t >= 0) atomicMax(keys + p, pack_key(best_v, best_t));
 }
-template <int N>
+template <int N, bool PF = true>
 __device__ void search_body_reg(const float2 *__restrict__ St, int T, const float2 *__restrict__ Sp, int p, int pb,
                                 int pe, unsigned long long *__restrict__ keys, float *__restrict__ peaks_all,
                                 const int *__restrict__ cand, int kc) {
-    search_body_reg<N>(St, T, Sp, p, pb, pe, keys, peaks_all, cand, kc, cta_group());
+    search_body_reg<N, PF>(St, T, Sp, p, pb, pe, keys, peaks_all, cand, kc, cta_group());
 }
 
 // search body with the whole surface in shared memory: per template pair the
@@ -324,12 +362,12 @@ __device__ void search_body_smem(const float2 *__restrict__ St, int T, const flo
 // templates, or the pattern's candidate list); smem_bytes<N>() of dynamic
 // shared memory; folds the item's best into keys[p].  N >= 64 takes
 // search_body_reg, smaller sides search_body_smem.
-template <int N>
+template <int N, bool PF = true>
 __device__ void search_body(const float2 *__restrict__ St, int T, const float2 *__restrict__ Sp, int p, int pb,
                             int pe, unsigned long long *__restrict__ keys, float *__restrict__ peaks_all,
                             const int *__restrict__ cand, int kc) {
     if constexpr (N >= 64)
-        search_body_reg<N>(St, T, Sp, p, pb, pe, keys, peaks_all, cand, kc);
+        search_body_reg<N, PF>(St, T, Sp, p, pb, pe, keys, peaks_all, cand, kc);
     else
         search_body_smem<N>(St, T, Sp, p, pb, pe, keys, peaks_all, cand, kc);
 }

@@ -45,7 +45,7 @@ constexpr int prep_threads() { return N >= 128 ? 512 : kThreads; }
 template <int N>
 constexpr int peak_threads() { return N >= 128 ? 1024 : kThreads; }
 template <int N>
-constexpr int search_threads() { return N >= 128 ? 1024 : kThreads; }
+__host__ __device__ constexpr int search_threads() { return N >= 128 ? 1024 : kThreads; }
 
 template <int N, int PT = prep_threads<N>()>
 __global__ void __launch_bounds__(PT) k_prep_real(const float *__restrict__ img, PrepArgs a,
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(search_threads<N>()) k_search_generic(const fl
     if (degen[p]) return;
     const int npairs = ((cand ? kc : T) + 1) / 2;
     const int pb = blockIdx.x * pairs_per_cta, pe = min(npairs, pb + pairs_per_cta);
-    search_body<N>(St, T, Sp, p, pb, pe, keys, peaks_all, cand, kc);
+    search_body<N, (search_threads<N>() <= 512)>(St, T, Sp, p, pb, pe, keys, peaks_all, cand, kc);
 }
 
 __device__ __forceinline__ float parabola(float cm, float c0, float cp) {
