@@ -71,16 +71,24 @@ __global__ void __launch_bounds__(GT) k_gemm(int M, int N, int K, int kper, LA l
         }
 }
 
-template <class LA, class LB, class EP>
-cudaError_t gemm(int M, int N, int K, int splits, LA la, LB lb, EP ep, cudaStream_t st) {
-    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+// the reduction length per split (a multiple of BK) for about `splits` splits of K
+int split_kper(int K, int splits) {
     const int kchunks = (K + BK - 1) / BK;
     splits = max(1, min(splits, kchunks));
-    const int kper = ((kchunks + splits - 1) / splits) * BK;
-    splits = (K + kper - 1) / kper;
+    return ((kchunks + splits - 1) / splits) * BK;
+}
+
+template <class LA, class LB, class EP>
+cudaError_t gemm_kper(int M, int N, int K, int kper, LA la, LB lb, EP ep, cudaStream_t st) {
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    const int splits = (K + kper - 1) / kper;
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
     k_gemm<<<grid, GT, 0, st>>>(M, N, K, kper, la, lb, ep);
     return cudaGetLastError();
+}
+template <class LA, class LB, class EP>
+cudaError_t gemm(int M, int N, int K, int splits, LA la, LB lb, EP ep, cudaStream_t st) {
+    return gemm_kper(M, N, K, split_kper(K, splits), la, lb, ep, st);
 }
 
 // reduction splits so that a weight-gradient launch has about two CTAs per SM
@@ -225,11 +233,23 @@ struct EpStore {   // y[n][m] = acc
     int M;
     __device__ void operator()(int m, int n, float v) const { y[(long)n * M + m] = v; }
 };
-struct EpAtomic {   // grad[m][n] += acc
-    float *g;
-    int N;
-    __device__ void operator()(int m, int n, float v) const { atomicAdd(g + (long)m * N + n, v); }
+struct EpPartial {   // part[split][m][n] = acc (split = blockIdx.z; summed in split order afterwards)
+    float *part;
+    int M, N;
+    __device__ void operator()(int m, int n, float v) const {
+        part[((long)blockIdx.z * M + m) * N + n] = v;
+    }
 };
+
+// out[i] = sum over z of part[z][i], z in increasing order (fixed order: the
+// same inputs give the same sums on every run)
+__global__ void k_sum_partials(const float *__restrict__ part, int splits, long n, float *__restrict__ out) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        float s = part[i];
+        for (int z = 1; z < splits; ++z) s += part[(long)z * n + i];
+        out[i] = s;
+    }
+}
 
 // ------------------------------------------------------ small kernels
 // per-pattern (scale, shift) of the standardisation of the crop: (x - mean) / std
@@ -393,8 +413,9 @@ __global__ void k_cnn_pool_back(const float *__restrict__ gpool, const float *__
     g[i] = a[i] > 0.f ? gpool[i / Q] / Q : 0.f;
 }
 
-// bias gradient: db[c] += sum over b < B, p < Q of g[b][c][p]
-__global__ void k_cnn_bias_grad(const float *__restrict__ g, int B, int C, int Q, float *__restrict__ db) {
+// bias gradient, per block row y: dbp[y][c] = sum over its share of b < B, p < Q
+// of g[b][c][p] (fixed order); the rows are summed in order afterwards
+__global__ void k_cnn_bias_grad(const float *__restrict__ g, int B, int C, int Q, float *__restrict__ dbp) {
     const int c = blockIdx.x;
     float s = 0.f;
     for (long i = (long)blockIdx.y * blockDim.x + threadIdx.x; i < (long)B * Q; i += (long)gridDim.y * blockDim.x) {
@@ -408,7 +429,7 @@ __global__ void k_cnn_bias_grad(const float *__restrict__ g, int B, int C, int Q
     if (threadIdx.x == 0) {
         float t = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += r[w];
-        atomicAdd(db + c, t);
+        dbp[(long)blockIdx.y * C + c] = t;
     }
 }
 
@@ -652,8 +673,13 @@ size_t cnn_act_floats(int B, int k) {
     return n + (size_t)B * (kCh[5] + kHidden + 6 * k) + 2 * (size_t)B;   // pool, h1, out, affine
 }
 
+// split partials of one weight gradient, and per-block bias partials
+constexpr size_t kPartFloats = (size_t)1 << 22;
+constexpr int kBiasRows = 64;
+constexpr size_t kBiasPartFloats = (size_t)kBiasRows * 512;
+
 size_t cnn_grad_floats(int B, int k) {
-    return 2 * (size_t)B * kCh[1] * 64 * 64 + (size_t)B * (kCh[5] + kHidden + 6 * k);
+    return 2 * (size_t)B * kCh[1] * 64 * 64 + (size_t)B * (kCh[5] + kHidden + 6 * k) + kPartFloats + kBiasPartFloats;
 }
 
 namespace {
@@ -810,26 +836,44 @@ cudaError_t launch_cnn_backward(const float *params, int k, const CnnInput &in, 
     const size_t big = (size_t)B * kCh[1] * 64 * 64;
     float *gbufs[2] = {gbuf, gbuf + big};
     float *gout = gbuf + 2 * big, *gh1 = gout + (size_t)B * 6 * k, *gpool = gh1 + (size_t)B * kHidden;
+    float *part = gpool + (size_t)B * kCh[5], *bpart = part + kPartFloats;
     int n_launch = 0;
+    // weight gradient out[M][N] = A^T B over the batch, reduced over K in splits
+    // whose partials are summed in a fixed order (no atomics: reproducible)
+    auto weight_grad = [&](int M, int N, int K, auto la, auto lb, float *out) -> cudaError_t {
+        int splits = grad_splits(M, N, K, num_sms);
+        while (splits > 1 && (size_t)splits * M * N > kPartFloats) splits = (splits + 1) / 2;
+        const int kper = split_kper(K, splits);
+        splits = (K + kper - 1) / kper;
+        cudaError_t e = gemm_kper(M, N, K, kper, la, lb, EpPartial{part, M, N}, st);
+        if (e != cudaSuccess) return e;
+        const long n = (long)M * N;
+        k_sum_partials<<<(unsigned)min((n + 255) / 256, 4096L), 256, 0, st>>>(part, splits, n, out);
+        n_launch += 2;
+        return cudaGetLastError();
+    };
+    auto bias_grad = [&](const float *g, int C, int Q, int rows, float *db) -> cudaError_t {
+        rows = max(1, min(rows, kBiasRows));
+        k_cnn_bias_grad<<<dim3(C, rows), 256, 0, st>>>(g, B, C, Q, bpart);
+        k_sum_partials<<<(unsigned)((C + 255) / 256), 256, 0, st>>>(bpart, rows, C, db);
+        n_launch += 2;
+        return cudaGetLastError();
+    };
     CNN_TRY(cudaMemsetAsync(grad, 0, sizeof(float) * cnn_num_params(k), st));
     k_cnn_head_loss<<<(B + 127) / 128, 128, 0, st>>>(A.out, B, k, qgt, gout, loss_sum, winners);
     CNN_TRY(cudaGetLastError());
     // fc2: dW2 = gout^T h1, db2, gh1 = (W2^T gout) where h1 > 0
     const int M2 = 6 * k;
-    CNN_TRY(gemm(M2, kHidden, B, grad_splits(M2, kHidden, B, num_sms), LoadRowsT{gout, M2},
-                 LoadRowsB{A.h1, kHidden}, EpAtomic{grad + L.f2w, kHidden}, st));
-    k_cnn_bias_grad<<<dim3(M2, 1), 256, 0, st>>>(gout, B, M2, 1, grad + L.f2b);
-    CNN_TRY(cudaGetLastError());
+    CNN_TRY(weight_grad(M2, kHidden, B, LoadRowsT{gout, M2}, LoadRowsB{A.h1, kHidden}, grad + L.f2w));
+    CNN_TRY(bias_grad(gout, M2, 1, 1, grad + L.f2b));
     CNN_TRY(gemm(kHidden, B, M2, 1, LoadWT{params + L.f2w, kHidden}, LoadRows{gout, M2},
                  EpMasked{gh1, A.h1, kHidden}, st));
     // fc1: dW1 = gh1^T pool, db1, gpool = W1^T gh1
-    CNN_TRY(gemm(kHidden, kCh[5], B, grad_splits(kHidden, kCh[5], B, num_sms), LoadRowsT{gh1, kHidden},
-                 LoadRowsB{A.pool, kCh[5]}, EpAtomic{grad + L.f1w, kCh[5]}, st));
-    k_cnn_bias_grad<<<dim3(kHidden, 1), 256, 0, st>>>(gh1, B, kHidden, 1, grad + L.f1b);
-    CNN_TRY(cudaGetLastError());
+    CNN_TRY(weight_grad(kHidden, kCh[5], B, LoadRowsT{gh1, kHidden}, LoadRowsB{A.pool, kCh[5]}, grad + L.f1w));
+    CNN_TRY(bias_grad(gh1, kHidden, 1, 1, grad + L.f1b));
     CNN_TRY(gemm(kCh[5], B, kHidden, 1, LoadWT{params + L.f1w, kCh[5]}, LoadRows{gh1, kHidden},
                  EpStore{gpool, kCh[5]}, st));
-    n_launch += 7;
+    n_launch += 3;
     // mean pool, then the conv layers from the last to the first
     int so = 4, cur = 0;
     {
@@ -843,12 +887,9 @@ cudaError_t launch_cnn_backward(const float *params, int k, const CnnInput &in, 
         const float *g = gbufs[cur];
         Src src = l == 0 ? Src{in.x, 1, 128, in.img_stride, in.row_stride, in.ox, in.oy, A.affine}
                          : Src{A.a[l - 1], ci, si, (long)ci * si * si, si, 0, 0, nullptr};
-        CNN_TRY(gemm(co, ci * 9, B * so * so, grad_splits(co, ci * 9, B * so * so, num_sms),
-                     LoadGradT{g, co, so * so}, LoadIm2colT{src, so}, EpAtomic{grad + L.cw[l], ci * 9}, st));
-        const int ych = max(1, min(64, 2 * num_sms / co));
-        k_cnn_bias_grad<<<dim3(co, ych), 256, 0, st>>>(g, B, co, so * so, grad + L.cb[l]);
-        CNN_TRY(cudaGetLastError());
-        n_launch += 2;
+        CNN_TRY(weight_grad(co, ci * 9, B * so * so, LoadGradT{g, co, so * so}, LoadIm2colT{src, so},
+                            grad + L.cw[l]));
+        CNN_TRY(bias_grad(g, co, so * so, 2 * num_sms / co, grad + L.cb[l]));
         if (l > 0) {   // gradient into the previous layer's output, through its ReLU
             CNN_TRY(gemm(ci, B * si * si, co * 9, 1, LoadWconvT{params + L.cw[l], ci}, LoadGradScatter{g, co, so},
                          EpMaskedImg{gbufs[cur ^ 1], A.a[l - 1], ci, si * si}, st));

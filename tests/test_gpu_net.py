@@ -151,6 +151,26 @@ def test_adam_step_matches_oracle(px, ctx, orc):
     net.close()
 
 
+def test_training_is_reproducible(px, ctx):
+    """The gradients are summed in a fixed order (split partials and bias
+    partials reduced in index order, no atomics), so the same initial
+    parameters and batches give bit-identical parameters after several Adam
+    steps, on a batch large enough for the weight gradients to be split."""
+    p = synth.cnn_init_params(K, 12)
+    batches = [(_images(64, 20 + i), _quats(64, 30 + i)) for i in range(3)]
+    runs = []
+    for _ in range(2):
+        net = px.xcf_net_create(ctx, K, dev(p))
+        for x, q in batches:
+            px.xcf_net_loss_grad(ctx, net, dev(x), dev(q))
+            px.xcf_net_adam(ctx, net, lr=1e-3)
+        torch.cuda.synchronize()
+        runs.append(net.params().cpu().clone())
+        net.close()
+    assert torch.equal(runs[0], runs[1])
+    assert not torch.equal(runs[0], torch.from_numpy(p))
+
+
 def test_proposals_match_oracle(px, ctx, orc):
     p = synth.cnn_init_params(K, 7)
     x = _images(4, 8)
