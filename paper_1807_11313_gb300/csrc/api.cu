@@ -610,8 +610,8 @@ int build_from_master(xcf_ctx *ctx, const float *master, int32_t M, const double
         ctx->launches[XCF_STAGE_PROJECT] += 1;
         ctx->launches[XCF_STAGE_PREP] += 1;
     }
-    if (spectra && e == cudaSuccess && c.n == 128) {
-        e = cudaMalloc(&lib->spectra_pk, sizeof(float2) * H * T);
+    if (spectra && e == cudaSuccess && has_search_layout(c.n)) {
+        e = cudaMalloc(&lib->spectra_pk, sizeof(float2) * search_layout_f2(c.n) * T);
         if (e == cudaSuccess) e = launch_pack_search_layout(lib->spectra, T, c.n, lib->spectra_pk, st);
         ctx->launches[XCF_STAGE_OTHER] += 1;
     }
@@ -669,8 +669,8 @@ int build_from_images(xcf_ctx *ctx, const float *images, const double *quats, in
             e = run_prep(ctx, images, T, prep_args(g, c, r), lib->spectra, nullptr, degen, nullptr, st);
         ctx->launches[XCF_STAGE_PREP] += 1;
     }
-    if (spectra && e == cudaSuccess && c.n == 128) {
-        e = cudaMalloc(&lib->spectra_pk, sizeof(float2) * H * T);
+    if (spectra && e == cudaSuccess && has_search_layout(c.n)) {
+        e = cudaMalloc(&lib->spectra_pk, sizeof(float2) * search_layout_f2(c.n) * T);
         if (e == cudaSuccess) e = launch_pack_search_layout(lib->spectra, T, c.n, lib->spectra_pk, st);
         ctx->launches[XCF_STAGE_OTHER] += 1;
     }
@@ -1202,7 +1202,7 @@ int xcf_rescore(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, int
                        "rescore");
         } else {
             XCF_LAUNCH(XCF_STAGE_SEARCH, st,
-                       launch_search_c256(lib->spectra, 0, sp, degen, np, keys, nullptr, cp, k, st), "rescore");
+                       launch_search_c256(search_spectra(lib), 0, sp, degen, np, keys, nullptr, cp, k, st), "rescore");
         }
         XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_keys_to_best(keys, np, best + p0, st), "keys_to_best");
         XCF_LAUNCH(XCF_STAGE_PEAK, st,
@@ -1266,7 +1266,7 @@ int xcf_index_precision(xcf_ctx *ctx, const xcf_library *lib, const float *patte
                        "rescore");
         } else {
             XCF_LAUNCH(XCF_STAGE_SEARCH, st,
-                       launch_search_c256(lib->spectra, 0, spec, degen, np, keys, nullptr, cand, k, st), "rescore");
+                       launch_search_c256(search_spectra(lib), 0, spec, degen, np, keys, nullptr, cand, k, st), "rescore");
         }
         XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_keys_to_best(keys, np, best + p0, st), "keys_to_best");
         XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_gather_seeds(lib->quats, best + p0, np, seeds, st), "seeds");

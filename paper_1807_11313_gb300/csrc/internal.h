@@ -105,13 +105,19 @@ struct xcf_library {
     int ox = 0, oy = 0;
     double pc[3] = {0, 0, 0};
     float2 *spectra = nullptr;
-    float2 *spectra_pk = nullptr;   // N = 128 only: the search kernel's packed layout
+    float2 *spectra_pk = nullptr;   // N = 128 and 256: the search kernel's layout (always made with spectra)
     void *bf16 = nullptr;           // screen: unit-norm filtered images [T][N*N] in BF16
     float *ndp32 = nullptr;         // NDP: contrast-normalised images / N [T][N*N] in FP32 ...
     void *ndp16 = nullptr;          // ... and in BF16 (inside the same allocation)
     double *quats = nullptr;
     float *master = nullptr;
 };
+
+// sides whose search kernel reads the templates in a layout of its own, and
+// that layout's float2 per template
+size_t c256_search_layout_f2();   // k_c256.cu
+inline bool has_search_layout(int n) { return n == 128 || n == 256; }
+inline size_t search_layout_f2(int n) { return n == 256 ? c256_search_layout_f2() : (size_t)n * (n / 2 + 1); }
 
 // spectra as the all-pairs search kernel of the library's size reads them
 inline const float2 *search_spectra(const xcf_library *lib) {

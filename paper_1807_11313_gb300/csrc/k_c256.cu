@@ -30,8 +30,6 @@ constexpr int N = 256, HW = N / 2 + 1, NC = 4, NT = 256;
 constexpr int ROWS = N / NC;                      // rows (and columns) per CTA
 constexpr size_t ZC_F2 = (size_t)ROWS * N;        // 128 KB of row-transformed data
 constexpr size_t SCR_F2 = (NT / 16) * 256;        // one 16 x 16 transpose buffer per group
-constexpr size_t PSM_F2 = (size_t)ROWS * HW;                      // the pattern's rows of this CTA
-constexpr size_t SMEM_BYTES = (ZC_F2 + SCR_F2 + PSM_F2) * sizeof(float2) + 64 * sizeof(float);
 
 __device__ __forceinline__ uint32_t cluster_rank() {
     uint32_t r;
@@ -40,9 +38,6 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 }
 __device__ __forceinline__ void cluster_barrier() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void cluster_arrive() {
-    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void cluster_wait() {
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -56,6 +51,19 @@ __device__ __forceinline__ float2 ld_cluster(uint32_t addr) {
     float2 v;
     asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
     return v;
+}
+__device__ __forceinline__ float4 ld_cluster4(uint32_t addr) {   // 16-byte aligned
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+// arrive without release: for a barrier that orders reads already consumed
+// before it against writes after it
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
 }
 __device__ __forceinline__ float ld_cluster_f(uint32_t addr) {
     float v;
@@ -130,44 +138,6 @@ __device__ __forceinline__ void rows_phase(float2 *Zc, const float2 *__restrict_
     }
 }
 
-// the search's row phase: as rows_phase with the pattern's rows in shared
-// memory (Psm[slot][129], the CTA's 64 rows) and the templates from global
-// memory; when `pending`, the previous pair's column-phase barrier is
-// completed just before the first store into Zc (its wait overlaps the first
-// row's loads and transform)
-__device__ __forceinline__ void rows_phase_sp(float2 *Zc, const float2 *__restrict__ s1,
-                                              const float2 *__restrict__ s2, const float2 *Psm,
-                                              const float2 (&tw)[16], float2 *scr, int c, int g, int t,
-                                              bool &pending) {
-#pragma unroll 1
-    for (int r = 0; r < 4; ++r) {
-        const int j = g + 16 * (r >> 1), b = 32 * c + j;
-        const int u0 = b, u1 = b == 0 ? 128 : N - b;
-        const int u = (r & 1) ? u1 : u0;
-        const int pu = (N - u) & (N - 1);
-        const int su = 2 * j + (r & 1), spu = b == 0 ? su : (su ^ 1);   // slots of u and of -u
-        float2 a[16];
-#pragma unroll
-        for (int n1 = 0; n1 < 16; ++n1) {
-            const int v = 16 * n1 + t;
-            const bool direct = v <= 128;
-            const int col = direct ? v : N - v;
-            const int k = (direct ? u : pu) * HW + col;   // Hermitian half: X(u, v) = conj(X(-u, 256 - v))
-            const float2 ps = Psm[(direct ? su : spu) * HW + col];
-            const float2 x1 = c_mulcj(__ldg(s1 + k), ps), x2 = c_mulcj(__ldg(s2 + k), ps);
-            a[n1] = direct ? make_float2(x1.x - x2.y, x1.y + x2.x) : make_float2(x1.x + x2.y, -x1.y + x2.x);
-        }
-        line_ifft(a, tw, scr, t);
-        if (r == 0 && pending) {   // every CTA is done reading this CTA's Zc
-            cluster_wait();
-            pending = false;
-        }
-        const int slot = 2 * j + (r & 1);
-#pragma unroll
-        for (int q = 0; q < 16; ++q) Zc[zc_index(slot, t + 16 * cx_bitrev(q, 4))] = a[q];
-    }
-}
-
 // L2 prefetch of one quarter (this CTA's share) of a template's half spectrum:
 // the four CTAs of a cluster together bring the whole spectrum into L2 ahead
 // of the row phase that reads it
@@ -182,17 +152,177 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
+// ------------------------------------------------- search on 512-thread CTAs
+// The same cluster search with 32 groups of 16 threads per CTA (sixteen warps
+// per SM to hide the latency of the row loads and the cluster gathers).
+//
+// Rows are owned by residue class: CTA c holds every row u with u mod 16 in
+// R_c (R_0 = {0, 8, 1, 15}, R_1 = {2, 14, 3, 13}, R_2 = {4, 12, 5, 11},
+// R_3 = {6, 10, 7, 9}; each set is closed under negation mod 16), row
+// u = r + 16 b at slot 16 i + b for r the i-th member of R_c.  A column
+// transform's lane l gathers the rows l + 16 n1, all from one owner, at one
+// base address plus constant offsets.  Rows sit at column x ^ 4 i, which keeps
+// the two half-warps' gathers of columns x and x + 2 free of bank conflicts.
+//
+// A group builds a row u together with its conjugate row -u: lane l holds u
+// at columns v = l + 16 m and -u at v = 16 - l + 16 m (m < 16, mod 256).  The
+// lane loads the stored half spectra at (u, l + 16 m) and (-u, 16 - l + 16 m)
+// for m < 8 (all within v <= 128), and each value gives an element of both
+// rows: Z(u, v) = W p directly, and Z(-u, -v) = V conj(p) through the
+// Hermitian symmetry X_j(-u, -v) = conj X_j(u, v) of the two real surfaces,
+// where W = conj(s1) + i conj(s2) and V = s1 + i s2.  Lane 0's second row is
+// held at columns 16 + 16 m (its last register is column 0), which the
+// twiddle e^{+2 pi i 16 k1 / 256} of the first 16-point pass accounts for.
+// CTA 0's rows 0 and 128 are each their own conjugate: one group builds the
+// two of them with two more loads of half rows.
+namespace cw {
+
+constexpr int NT = 512, NG = NT / 16;
+constexpr size_t ZC_F2 = (size_t)ROWS * N;         // 128 KB of row-transformed data
+constexpr size_t SCR_F2 = (size_t)NG * 256;        // one 16 x 16 transpose buffer per group
+constexpr size_t TW_F2 = 512;                      // [k1][l]: e^{+2 pi i l k1 / 256}, then e^{+2 pi i (16 - l) k1 / 256}
+constexpr size_t SMEM_BYTES = (ZC_F2 + SCR_F2 + TW_F2) * sizeof(float2) + 64 * sizeof(float);
+
+// search layout of a template's half spectrum: row u, piece (j < 4, group
+// lam < 17) holds columns lam + 16 (2 j) and lam + 16 (2 j + 1) (group 16:
+// columns 16 .. 128).  A lane's eight columns d + 16 m (d = l, or 16 - l for
+// the conjugate row) are its group's four 16-byte pieces, and the 16 lanes
+// of a group read 256 contiguous bytes per piece.
+constexpr int PK_ROW = 4 * 17 * 2;              // float2 per row (1,088 bytes)
+constexpr size_t PK_F2 = (size_t)N * PK_ROW;    // float2 per template
+constexpr uint32_t kPackBytes = (uint32_t)(PK_F2 * sizeof(float2));
+static_assert(kPackBytes % (16 * NC) == 0, "a quarter of a packed template is a whole number of 16-byte units");
+
+// member i of R_c at 4 c + i, and its inverse (residue r -> 4 owner + i), as nibbles
+constexpr int kClass[16] = {0, 8, 1, 15, 2, 14, 3, 13, 4, 12, 5, 11, 6, 10, 7, 9};
+constexpr unsigned long long home_pack() {
+    unsigned long long h = 0;
+    for (int k = 0; k < 16; ++k) h |= (unsigned long long)k << (4 * kClass[k]);
+    return h;
+}
+constexpr unsigned long long kHome = home_pack();
+constexpr bool classes_closed() {   // every R_c closed under negation mod 16
+    for (int k = 0; k < 16; ++k) {
+        const int neg = (16 - kClass[k]) & 15;
+        if ((int)((kHome >> (4 * neg)) & 15) >> 2 != k >> 2) return false;
+    }
+    return true;
+}
+static_assert(classes_closed(), "row classes of a CTA must be closed under negation");
+
+__device__ __forceinline__ int slot_of(int u) {
+    const int h = (int)((kHome >> (4 * (u & 15))) & 15);
+    return 16 * (h & 3) + (u >> 4);
+}
+__device__ __forceinline__ int zc_at(int slot, int x) { return slot * N + (x ^ (4 * (slot >> 4))); }
+
+// the two rows group g of CTA c builds (ub = -ua except for CTA 0's last group)
+__device__ __forceinline__ void unit_rows(int c, int g, int &ua, int &ub) {
+    if (c > 0) {
+        ua = (g < 16 ? 2 * c : 2 * c + 1) + 16 * (g & 15);
+    } else if (g < 16) {
+        ua = 1 + 16 * g;
+    } else if (g < 24) {
+        ua = 8 + 16 * (g - 16);
+    } else if (g < 31) {
+        ua = 16 * (g - 23);
+    } else {
+        ua = 0;
+    }
+    ub = ua == 0 ? N / 2 : N - ua;
+}
+
+__device__ __forceinline__ void prefetch_packed(const float2 *spec, int c) {   // this CTA's quarter into L2
+    const char *base = reinterpret_cast<const char *>(spec) + (size_t)c * (kPackBytes / NC);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base), "r"(kPackBytes / NC) : "memory");
+}
+
+// lane loads of one row at columns d + 16 m (m < 8), templates in the search
+// layout, pattern in the plain one: x[m] = (conj s1 + i conj s2) p when
+// DIRECT, y[15 - m] = (s1 + i s2) conj p
+template <bool DIRECT>
+__device__ __forceinline__ void build_half(const float2 *__restrict__ k1, const float2 *__restrict__ k2,
+                                           const float2 *__restrict__ sp, int row, int d, float2 (&x)[16],
+                                           float2 (&y)[16]) {
+    const float4 *q1 = reinterpret_cast<const float4 *>(k1 + (size_t)row * PK_ROW) + d;
+    const float4 *q2 = reinterpret_cast<const float4 *>(k2 + (size_t)row * PK_ROW) + d;
+    const float2 *pp = sp + row * HW + d;
+    auto emit = [&](int m, float ax, float ay, float bx, float by, float2 p) {
+        if (DIRECT) x[m] = c_mul(make_float2(ax + by, bx - ay), p);
+        y[15 - m] = c_mulcj(p, make_float2(ax - by, ay + bx));
+    };
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float4 A = __ldg(q1 + 17 * j), B = __ldg(q2 + 17 * j);
+        const float2 p0 = __ldg(pp + 32 * j), p1 = __ldg(pp + 32 * j + 16);
+        emit(2 * j, A.x, A.y, B.x, B.y, p0);
+        emit(2 * j + 1, A.z, A.w, B.z, B.w, p1);
+    }
+}
+
+// the search layout of T half spectra (one-off, when the library is built)
+__global__ void k_pack_c256(const float2 *__restrict__ src, int T, float2 *__restrict__ dst) {
+    const size_t total = (size_t)T * PK_F2;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t t = i / PK_F2;
+        const int k = (int)(i - t * PK_F2), u = k / PK_ROW, r = k - u * PK_ROW;
+        const int pc = r >> 1, j = pc / 17, lam = pc - 17 * j;
+        dst[i] = src[t * (size_t)(N * HW) + (size_t)u * HW + lam + 16 * (2 * j + (r & 1))];
+    }
+}
+
+// decimation-in-frequency stages [S0, S1) of a 16-point transform in registers
+template <int S0, int S1, int SIGN>
+__device__ __forceinline__ void dif16(float2 (&x)[16]) {
+    StaticFor<S0, S1>::run([&](auto stage) {
+        constexpr int span = 16 >> (decltype(stage)::value + 1);
+        StaticFor<0, 16 / (2 * span)>::run([&](auto blk) {
+            StaticFor<0, span>::run([&](auto k) {
+                constexpr int kk = decltype(k)::value;
+                constexpr int i0 = decltype(blk)::value * 2 * span + kk;
+                constexpr int i1 = i0 + span;
+                const float2 a = x[i0], b = x[i1];
+                x[i0] = c_add(a, b);
+                x[i1] = tw_mul<kk, 2 * span, SIGN>(c_sub(a, b));
+            });
+        });
+    });
+}
+
+// first half of a 256-point inverse DFT on a 16-thread group: lane l holds
+// x[n2 + 16 n1] in a[n1 - e] (e = 0, or 1 for a line started at column 16);
+// the 16-point pass over n1, the twiddle w(k1) = e^{+2 pi i (n2 + 16 e) k1 / 256}
+// and the transpose, after which a[n2'] = A[k1 = l][n2'] for the second pass
+template <class TW>
+__device__ __forceinline__ void ifft256_pass1(float2 (&a)[16], TW w, int n2, float2 *scr, int l) {
+    dif16<0, 4, +1>(a);
+    StaticFor<0, 16>::run([&](auto pp) {
+        constexpr int p = decltype(pp)::value;
+        constexpr int k1 = cx_bitrev(p, 4);
+        scr[n2 * 16 + (k1 ^ n2)] = k1 == 0 ? a[p] : c_mul(a[p], w(k1));
+    });
+    const unsigned gm = 0xffffu << (threadIdx.x & 16);
+    __syncwarp(gm);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) a[q] = scr[q * 16 + (l ^ q)];
+    __syncwarp(gm);
+}
+
+
+}  // namespace cw
+
 // pattern p, template pairs [pb, pe) (slot indices into cand when cand != null)
-__global__ void __launch_bounds__(NT, 1)
-k_search_c256(const float2 *__restrict__ St, int T, const float2 *__restrict__ Sp, const int *__restrict__ degen,
-              int nchunks, int ppc, int n_items, unsigned long long *__restrict__ keys, float *__restrict__ peaks_all,
-              const int *__restrict__ cand, int kc) {
+__global__ void __launch_bounds__(cw::NT, 1)
+k_search_c256w(const float2 *__restrict__ St, int T, const float2 *__restrict__ Sp, const int *__restrict__ degen,
+               int nchunks, int ppc, int n_items, unsigned long long *__restrict__ keys, float *__restrict__ peaks_all,
+               const int *__restrict__ cand, int kc) {
+    using namespace cw;
     extern __shared__ float4 smem_raw[];
     float2 *Zc = reinterpret_cast<float2 *>(smem_raw);
-    float2 *scr_all = Zc + ZC_F2;
-    float2 *Psm = scr_all + SCR_F2;
-    float *red = reinterpret_cast<float *>(Psm + PSM_F2);   // [0..15] warp maxima, [32..33] CTA maxima
-    const int tid = threadIdx.x, t = tid & 15, g = tid >> 4, warp = tid >> 5, lane = tid & 31;
+    float2 *scr_all = Zc + cw::ZC_F2;
+    float2 *twa = scr_all + cw::SCR_F2, *twb = twa + 256;
+    float *red = reinterpret_cast<float *>(twa + TW_F2);   // [0..15] warp maxima, [32..33] CTA maxima
+    const int tid = threadIdx.x, l = tid & 15, g = tid >> 4, warp = tid >> 5, lane = tid & 31;
     const int c = (int)cluster_rank();
     const int cid = blockIdx.x / NC, ncl = gridDim.x / NC;
     float2 *scr = scr_all + g * 256;
@@ -200,35 +330,33 @@ k_search_c256(const float2 *__restrict__ St, int T, const float2 *__restrict__ S
     bool pending = false;   // a column-phase barrier arrived on but not yet waited for
     const int npairs = (n + 1) / 2;
 
-    float2 tw[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
+    for (int i = tid; i < 512; i += cw::NT) {   // twa[k1][l], twb[k1][l]
+        const int ll = i & 15, k1 = (i >> 4) & 15;
         double s, co;
-        sincospi(2.0 * t * k / N, &s, &co);
-        tw[k] = make_float2((float)co, (float)s);
+        sincospi(2.0 * (i < 256 ? ll : 16 - ll) * k1 / N, &s, &co);
+        twa[i] = make_float2((float)co, (float)s);
     }
-    // column phase: cluster address of row u = 16 n1 + t in its owner's buffer
+    // row phase: this group's two rows, their slots; lane l's second row starts at column sg
+    int ua, ub;
+    unit_rows(c, g, ua, ub);
+    const bool singles = ua == 0;   // rows 0 and 128, each its own conjugate
+    const int sa = slot_of(ua), sb = slot_of(ub), sg = 16 - l, ng = sg & 15;
+    // column phase: lane l's rows l + 16 n1 at owner o, slots 16 i + n1; columns 64 c + 2 g + q
+    const int hm = (int)((kHome >> (4 * l)) & 15), io = hm & 3;
     const uint32_t zc_local = (uint32_t)__cvta_generic_to_shared(Zc);
-    uint32_t rbase[16];
-    int rsw[16];
-#pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) {
-        int owner, slot;
-        row_home(16 * n1 + t, owner, slot);
-        rbase[n1] = map_to_rank(zc_local, owner) + (uint32_t)(slot * N * sizeof(float2));
-        rsw[n1] = (slot >> 1) & 15;
-    }
+    const uint32_t cbase = map_to_rank(zc_local, (uint32_t)(hm >> 2)) +
+                           (uint32_t)((16 * io * N + ((ROWS * c + 2 * g) ^ (4 * io))) * sizeof(float2));
     const uint32_t red_local = (uint32_t)__cvta_generic_to_shared(red);
+    __syncthreads();   // twa, twb
 
-    // template indices of pair pi of item `it` (negative candidate slots are skipped)
     auto pair_templates = [&](int it, int pi, int &t1, int &t2) {
         const int p = it / nchunks;
         const int j1 = 2 * pi, j2 = min(j1 + 1, n - 1);
         t1 = cand ? cand[(size_t)p * kc + j1] : j1;
         t2 = cand ? cand[(size_t)p * kc + j2] : j2;
     };
-    // prefetch the template pair that follows (item, pi) into L2: the next pair
-    // of the item, else the first pair of this cluster's next item
+    // L2 prefetch of the template pair that follows (item, pi): the next pair of
+    // the item, else the first pair (and the pattern) of this cluster's next item
     auto prefetch_next = [&](int it, int pi, int pe) {
         if (tid != 0) return;
         int nit = it, npi = pi + 1;
@@ -237,29 +365,26 @@ k_search_c256(const float2 *__restrict__ St, int T, const float2 *__restrict__ S
             if (nit >= n_items || degen[nit / nchunks]) return;
             npi = (nit - (nit / nchunks) * nchunks) * ppc;
             if (npi >= npairs) return;
+            prefetch_quarter(Sp + (size_t)(nit / nchunks) * N * HW, c);
         }
         int t1, t2;
         pair_templates(nit, npi, t1, t2);
-        if (t1 >= 0) prefetch_quarter(St + (size_t)t1 * N * HW, c);
-        if (t2 >= 0 && t2 != t1) prefetch_quarter(St + (size_t)t2 * N * HW, c);
+        if (t1 >= 0) prefetch_packed(St + (size_t)t1 * PK_F2, c);
+        if (t2 >= 0 && t2 != t1) prefetch_packed(St + (size_t)t2 * PK_F2, c);
     };
     if (cid < n_items && !degen[cid / nchunks]) {   // the first pair of the first item
         const int pb0 = (cid - (cid / nchunks) * nchunks) * ppc;
-        if (pb0 < npairs) prefetch_next(cid, pb0 - 1, pb0 + 1);
+        if (pb0 < npairs) {
+            if (tid == 0) prefetch_quarter(Sp + (size_t)(cid / nchunks) * N * HW, c);
+            prefetch_next(cid, pb0 - 1, pb0 + 1);
+        }
     }
 
     for (int item = cid; item < n_items; item += ncl) {
         const int p = item / nchunks, ch = item - p * nchunks;
         const int pb = ch * ppc, pe = min(npairs, pb + ppc);
-        if (degen[p]) continue;                       // uniform over the cluster
+        if (degen[p]) continue;   // uniform over the cluster
         const float2 *sp = Sp + (size_t)p * N * HW;
-        __syncthreads();                               // this CTA's reads of the previous pattern are done
-        for (int i = tid; i < ROWS * HW; i += NT) {    // the pattern's rows of this CTA, by slot
-            const int slot = i / HW, col = i - slot * HW, j = slot >> 1, b = 32 * c + j;
-            const int u = (slot & 1) ? (b == 0 ? 128 : N - b) : b;
-            Psm[i] = __ldg(sp + (size_t)u * HW + col);
-        }
-        __syncthreads();
         float best_v = -INFINITY;
         int best_t = -1;
         for (int pi = pb; pi < pe; ++pi) {
@@ -267,24 +392,54 @@ k_search_c256(const float2 *__restrict__ St, int T, const float2 *__restrict__ S
             int t1, t2;
             pair_templates(item, pi, t1, t2);
             prefetch_next(item, pi, pe);
-            const float2 *s1 = St + (size_t)max(t1, 0) * N * HW, *s2 = St + (size_t)max(t2, 0) * N * HW;
-            rows_phase_sp(Zc, s1, s2, Psm, tw, scr, c, g, t, pending);
-            cluster_barrier();
-            // ---- columns x = 64 c + 4 g + q: gather over the cluster, transform, maxima
-            float m1 = -INFINITY, m2 = -INFINITY;
-#pragma unroll 1
-            for (int q = 0; q < 4; ++q) {
-                const int x = ROWS * c + 4 * g + q;
-                float2 a[16];
-#pragma unroll
-                for (int n1 = 0; n1 < 16; ++n1)
-                    a[n1] = ld_cluster(rbase[n1] + (uint32_t)((x ^ rsw[n1]) * sizeof(float2)));
-                line_ifft(a, tw, scr, t);
-#pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    m1 = fmaxf(m1, a[k].x);
-                    m2 = fmaxf(m2, a[k].y);
+            const float2 *s1 = St + (size_t)max(t1, 0) * PK_F2, *s2 = St + (size_t)max(t2, 0) * PK_F2;
+            // ---- rows ua and ub of Z = X1 + i X2, transformed along v
+            {
+                float2 a[16], b[16];
+                build_half<true>(s1, s2, sp, ua, l, a, b);
+                build_half<true>(s1, s2, sp, ub, sg, b, a);
+                if (singles) {   // the conjugate halves come from the rows themselves
+                    build_half<false>(s1, s2, sp, ub, l, b, b);
+                    build_half<false>(s1, s2, sp, ua, sg, a, a);
                 }
+                ifft256_pass1(a, [&](int k1) { return twa[k1 * 16 + l]; }, l, scr, l);
+                dif16<0, 4, +1>(a);
+                if (pending) {   // every CTA is done reading this CTA's Zc
+                    cluster_wait();
+                    pending = false;
+                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q) Zc[zc_at(sa, l + 16 * cx_bitrev(q, 4))] = a[q];
+                ifft256_pass1(b, [&](int k1) { return twb[k1 * 16 + l]; }, ng, scr, l);
+                dif16<0, 4, +1>(b);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) Zc[zc_at(sb, l + 16 * cx_bitrev(q, 4))] = b[q];
+            }
+            cluster_barrier();
+            // ---- columns 64 c + 2 g + q (q < 2, adjacent in every row): gather over
+            // the cluster, 16 bytes per row, transform, maxima
+            float m1 = -INFINITY, m2 = -INFINITY;
+            {
+                float2 a[16], b[16];
+                StaticFor<0, 16>::run([&](auto nn) {
+                    constexpr int n1 = decltype(nn)::value;
+                    const float4 v = ld_cluster4(cbase + (uint32_t)(n1 * N * sizeof(float2)));
+                    a[n1] = make_float2(v.x, v.y);
+                    b[n1] = make_float2(v.z, v.w);
+                });
+                auto column_max = [&](float2(&x)[16]) {
+                    ifft256_pass1(x, [&](int k1) { return twa[k1 * 16 + l]; }, l, scr, l);
+                    dif16<0, 3, +1>(x);
+                    // the last stage (span 1, no twiddle) folded into the maxima:
+                    // max(a + b, a - b) = a + |b| per real component
+#pragma unroll
+                    for (int k = 0; k < 16; k += 2) {
+                        m1 = fmaxf(m1, x[k].x + fabsf(x[k + 1].x));
+                        m2 = fmaxf(m2, x[k].y + fabsf(x[k + 1].y));
+                    }
+                };
+                column_max(a);
+                column_max(b);
             }
             m1 = warp_max(m1);
             m2 = warp_max(m2);
@@ -295,7 +450,7 @@ k_search_c256(const float2 *__restrict__ St, int T, const float2 *__restrict__ S
             __syncthreads();
             if (tid == 0) {
                 float a1 = red[0], a2 = red[16];
-                for (int w = 1; w < NT / 32; ++w) {
+                for (int w = 1; w < cw::NT / 32; ++w) {
                     a1 = fmaxf(a1, red[w]);
                     a2 = fmaxf(a2, red[16 + w]);
                 }
@@ -309,9 +464,9 @@ k_search_c256(const float2 *__restrict__ St, int T, const float2 *__restrict__ S
             if (t1 >= 0 && (m1 > best_v || (m1 == best_v && t1 < best_t))) { best_v = m1; best_t = t1; }
             if (j2 != j1 && t2 >= 0 && (m2 > best_v || (m2 == best_v && t2 < best_t))) { best_v = m2; best_t = t2; }
             if (peaks_all) {
-                cluster_barrier();                    // every column read done; red[32..33] of all CTAs final
+                cluster_barrier();   // every column read done; red[32..33] of all CTAs final
             } else {
-                cluster_arrive();                     // completed before the next pair's first Zc store
+                cluster_arrive_relaxed();   // completed before the next pair's first Zc store
                 pending = true;
             }
             if (peaks_all && c == 0 && tid == 0) {   // the surfaces' maxima over the four CTAs
@@ -738,13 +893,12 @@ k_prep_c256(const float *__restrict__ img, int P, PrepArgs a, float2 *__restrict
     cluster_barrier();
 }
 
-int max_active_clusters() {
-    static int cached = -1;
-    if (cached >= 0) return cached;
+template <class K>
+int max_active_clusters(K kernel, int nt, size_t smem) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(NC * 64);
-    cfg.blockDim = dim3(NT);
-    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.blockDim = dim3(nt);
+    cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = NC;
@@ -753,27 +907,37 @@ int max_active_clusters() {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_search_c256, &cfg) != cudaSuccess || n <= 0) {
+    if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess || n <= 0) {
         cudaGetLastError();
         n = 32;
     }
-    cached = n;
     return n;
 }
 
 }  // namespace
 
-size_t c256_smem_bytes() { return SMEM_BYTES; }
+size_t c256_search_layout_f2() { return cw::PK_F2; }
+
+cudaError_t launch_pack_c256(const float2 *spectra, int T, float2 *packed, cudaStream_t st) {
+    if (T <= 0) return cudaSuccess;
+    const size_t total = (size_t)T * cw::PK_F2;
+    const int blocks = (int)((total + 255) / 256 < 65536 ? (total + 255) / 256 : 65536);
+    cw::k_pack_c256<<<blocks, 256, 0, st>>>(spectra, T, packed);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_search_c256(const float2 *St, int T, const float2 *Sp, const int *degen, int P,
                                unsigned long long *keys, float *peaks_all, const int *cand, int kc,
                                cudaStream_t st) {
     const int n = cand ? kc : T;
     if (P <= 0 || n <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_search_c256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    auto *kernel = k_search_c256w;
+    const int nt = cw::NT;
+    const size_t smem = cw::SMEM_BYTES;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int npairs = (n + 1) / 2;
-    const int ncl_max = max_active_clusters();
+    static const int ncl_max = max_active_clusters(kernel, nt, smem);
     // chunks of pairs so that there are at least ~4 items per resident cluster
     const long want = 4L * ncl_max;
     int nchunks = (int)((want + P - 1) / P);
@@ -785,8 +949,8 @@ cudaError_t launch_search_c256(const float2 *St, int T, const float2 *Sp, const 
     const int ncl = (int)(n_items < ncl_max ? n_items : ncl_max);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(NC * ncl);
-    cfg.blockDim = dim3(NT);
-    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.blockDim = dim3(nt);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -795,8 +959,7 @@ cudaError_t launch_search_c256(const float2 *St, int T, const float2 *Sp, const 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_search_c256, St, T, Sp, degen, nchunks, ppc, (int)n_items, keys, peaks_all,
-                              cand, kc);
+    return cudaLaunchKernelEx(&cfg, kernel, St, T, Sp, degen, nchunks, ppc, (int)n_items, keys, peaks_all, cand, kc);
 }
 
 cudaError_t launch_prep_c256(const float *img, int P, const PrepArgs &a, float2 *spec, float *spatial, int *degen,

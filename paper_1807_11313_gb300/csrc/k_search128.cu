@@ -68,6 +68,7 @@ __global__ void k_pack_search_layout(const float2 *__restrict__ src, int T, floa
 }  // namespace
 
 cudaError_t launch_pack_search_layout(const float2 *spectra, int T, int N_, float2 *packed, cudaStream_t st) {
+    if (N_ == 256) return launch_pack_c256(spectra, T, packed, st);
     if (N_ != N) return cudaErrorInvalidValue;
     if (T <= 0) return cudaSuccess;
     const size_t total = (size_t)T * SPEC;

@@ -32,11 +32,15 @@ cudaError_t launch_search(int N, const float2 *St, int T, const float2 *Sp, cons
                           unsigned long long *keys, float *peaks_all, int num_sms, cudaStream_t st);
 
 // N = 256 search on clusters of four CTAs (the 256 x 256 array in distributed
-// shared memory); with cand: each pattern's candidate list cand [P][kc]
+// shared memory); St: the templates in the search layout (launch_pack_c256),
+// Sp: the patterns' half spectra; with cand: each pattern's candidate list
+// cand [P][kc]
 cudaError_t launch_search_c256(const float2 *St, int T, const float2 *Sp, const int *degen, int P,
                                unsigned long long *keys, float *peaks_all, const int *cand, int kc,
                                cudaStream_t st);
-size_t c256_smem_bytes();
+// the N = 256 search layout: float2 per template, and the packing of T half spectra
+size_t c256_search_layout_f2();
+cudaError_t launch_pack_c256(const float2 *spectra, int T, float2 *packed, cudaStream_t st);
 // N = 256 single-surface peak on clusters of four CTAs (two patterns per pass)
 cudaError_t launch_pair_peak_c256(const float2 *St, const int *tidx, const float2 *Sp, const int *degen,
                                   const int *active, int P, float *peak, float *shift, cudaStream_t st,
