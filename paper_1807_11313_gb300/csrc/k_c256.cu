@@ -147,6 +147,10 @@ __device__ __forceinline__ void prefetch_quarter(const float2 *spec, int c) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base), "r"(kSpecBytes / NC) : "memory");
 }
 
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+    for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
 __device__ __forceinline__ float warp_max(float v) {
     for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
@@ -385,8 +389,7 @@ k_search_c256w(const float2 *__restrict__ St, int T, const float2 *__restrict__ 
         const int pb = ch * ppc, pe = min(npairs, pb + ppc);
         if (degen[p]) continue;   // uniform over the cluster
         const float2 *sp = Sp + (size_t)p * N * HW;
-        float best_v = -INFINITY;
-        int best_t = -1;
+        unsigned long long kbest = 0;
         for (int pi = pb; pi < pe; ++pi) {
             const int j1 = 2 * pi, j2 = min(j1 + 1, n - 1);
             int t1, t2;
@@ -441,6 +444,16 @@ k_search_c256w(const float2 *__restrict__ St, int T, const float2 *__restrict__ 
                 column_max(a);
                 column_max(b);
             }
+            // the pattern's key is the maximum over pairs, lanes, warps and CTAs
+            // of (value, lowest template): kept per lane, reduced once per item
+            if (t1 >= 0) kbest = max(kbest, pack_key(m1, t1));
+            if (j2 != j1 && t2 >= 0) kbest = max(kbest, pack_key(m2, t2));
+            if (!peaks_all) {
+                cluster_arrive_relaxed();   // completed before the next pair's first Zc store
+                pending = true;
+                continue;
+            }
+            // every surface's maximum over the cluster (correlate-all mode)
             m1 = warp_max(m1);
             m2 = warp_max(m2);
             if (lane == 0) {
@@ -457,20 +470,9 @@ k_search_c256w(const float2 *__restrict__ St, int T, const float2 *__restrict__ 
                 red[32] = a1;
                 red[33] = a2;
             }
-            __syncthreads();
-            m1 = red[32];
-            m2 = red[33];
-            // per-CTA partial maxima: the key of the pattern is the max over CTAs
-            if (t1 >= 0 && (m1 > best_v || (m1 == best_v && t1 < best_t))) { best_v = m1; best_t = t1; }
-            if (j2 != j1 && t2 >= 0 && (m2 > best_v || (m2 == best_v && t2 < best_t))) { best_v = m2; best_t = t2; }
-            if (peaks_all) {
-                cluster_barrier();   // every column read done; red[32..33] of all CTAs final
-            } else {
-                cluster_arrive_relaxed();   // completed before the next pair's first Zc store
-                pending = true;
-            }
-            if (peaks_all && c == 0 && tid == 0) {   // the surfaces' maxima over the four CTAs
-                float a1 = m1, a2 = m2;
+            cluster_barrier();   // every column read done; red[32..33] of all CTAs final
+            if (c == 0 && tid == 0) {
+                float a1 = red[32], a2 = red[33];
                 for (int o = 1; o < NC; ++o) {
                     const uint32_t ra = map_to_rank(red_local, o);
                     a1 = fmaxf(a1, ld_cluster_f(ra + 32 * sizeof(float)));
@@ -479,8 +481,11 @@ k_search_c256w(const float2 *__restrict__ St, int T, const float2 *__restrict__ 
                 peaks_all[(size_t)p * n + j1] = t1 >= 0 ? a1 : -INFINITY;
                 if (j2 != j1) peaks_all[(size_t)p * n + j2] = t2 >= 0 ? a2 : -INFINITY;
             }
+            // red[32..33] are written again only after the next pair's row-phase
+            // barrier, which CTA 0 reaches after these reads
         }
-        if (tid == 0 && best_t >= 0) atomicMax(keys + p, pack_key(best_v, best_t));
+        kbest = warp_max_u64(kbest);
+        if (lane == 0 && kbest) atomicMax(keys + p, kbest);
     }
     if (pending) cluster_wait();
     cluster_barrier();   // no CTA leaves while another may still read its shared memory
