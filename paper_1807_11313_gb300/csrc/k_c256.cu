@@ -669,7 +669,16 @@ k_pair_peak_c256(const float2 *__restrict__ St, const int *__restrict__ tidx, co
 // columns in place, then rows two at a time (conjugate-symmetric extension).
 constexpr size_t RC_F2 = (size_t)ROWS * HW;                        // row spectra [64][129]
 constexpr size_t ST_F2 = (size_t)N * 32;                          // column staging [256][32]
-constexpr size_t PREP_SMEM = (RC_F2 + ST_F2 + N + SCR_F2) * sizeof(float2) + 16 * sizeof(double);
+constexpr size_t IN_F = (size_t)ROWS * N;                          // input rows [64][256] of the next image
+constexpr size_t PREP_SMEM = (RC_F2 + ST_F2 + N + SCR_F2) * sizeof(float2) + 16 * sizeof(double) + IN_F * sizeof(float);
+static_assert(PREP_SMEM <= 232448, "pre-processing shared memory above the per-CTA limit");
+
+__device__ __forceinline__ void cp_async_4(uint32_t s, const float *g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(uint32_t s, const float *g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(g) : "memory");
+}
 
 __device__ __forceinline__ double ld_cluster_d(uint32_t addr) {
     double v;
@@ -701,11 +710,11 @@ k_prep_c256(const float *__restrict__ img, int P, PrepArgs a, float2 *__restrict
             int *__restrict__ degen, const int *__restrict__ active) {
     extern __shared__ float4 smem_raw[];
     float2 *Rc = reinterpret_cast<float2 *>(smem_raw);
-    float2 *Stage = Rc + RC_F2;                       // also the input rows [64][256] floats
-    float *Xr = reinterpret_cast<float *>(Stage);
+    float2 *Stage = Rc + RC_F2;
     float2 *Col128 = Stage + ST_F2;
     float2 *scr_all = Col128 + N;
     double *red = reinterpret_cast<double *>(scr_all + SCR_F2);   // [0..7] block partials, [8..10] cluster slots
+    float *Xr = reinterpret_cast<float *>(red + 16);              // this CTA's 64 input rows [64][256]
     const int tid = threadIdx.x, t = tid & 15, g = tid >> 4;
     const int c = (int)cluster_rank();
     const int cid = blockIdx.x / NC, ncl = gridDim.x / NC;
@@ -729,20 +738,41 @@ k_prep_c256(const float *__restrict__ img, int P, PrepArgs a, float2 *__restrict
         rrow[n1] = map_to_rank(rc_local, y >> 6) + (uint32_t)((y & 63) * HW * sizeof(float2));
     }
     const float inv_nn = 1.f / N;
+    // this CTA's 64 crop rows of an image into Xr, asynchronously (16-byte
+    // copies when the crop's rows start on 16-byte boundaries)
+    const bool v16 = ((reinterpret_cast<uintptr_t>(img) | ((uintptr_t)a.W * 4) | ((uintptr_t)a.ox * 4)) & 15) == 0;
+    const uint32_t xr_local = (uint32_t)__cvta_generic_to_shared(Xr);
+    auto load_rows = [&](int q) {
+        const float *src = img + (size_t)q * a.W * a.H + (size_t)(a.oy + ROWS * c) * a.W + a.ox;
+        if (v16) {
+            for (int i = tid; i < ROWS * N / 4; i += NT)
+                cp_async_16(xr_local + (uint32_t)(16 * i), src + (size_t)(i >> 6) * a.W + 4 * (i & 63));
+        } else {
+            for (int i = tid; i < ROWS * N; i += NT)
+                cp_async_4(xr_local + (uint32_t)(4 * i), src + (size_t)(i >> 8) * a.W + (i & (N - 1)));
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    auto next_active = [&](int q) {   // uniform over the cluster
+        while (q < P && active && !active[q]) q += ncl;
+        return q;
+    };
+    int p = next_active(cid), pn = P;
+    if (p < P) load_rows(p);
 
-    for (int p = cid; p < P; p += ncl) {
-        if (active && !active[p]) continue;            // uniform over the cluster
+    for (; p < P; p = pn) {
+        pn = next_active(p + ncl);
         const float *src = img + (size_t)p * a.W * a.H;
         float2 *out = spec + (size_t)p * N * HW;
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();   // Xr holds image p
         // ---- statistics of the crop: one pass of FP32 sums of (x - x0), x0 the crop's
         // first pixel (the same in every CTA; a constant crop has exactly zero variance),
         // combined in FP64, one cluster barrier for both
         const float x0 = __ldg(src + (size_t)a.oy * a.W + a.ox);
         float sf = 0.f, sf2 = 0.f;
         for (int i = tid; i < ROWS * N; i += NT) {
-            const int r = i >> 8, x = i & (N - 1);
-            const float v = __ldg(src + (size_t)(a.oy + ROWS * c + r) * a.W + a.ox + x);
-            Xr[i] = v;
+            const float v = Xr[i];
             const float d = v - x0;
             sf += d;
             sf2 = fmaf(d, d, sf2);
@@ -789,6 +819,7 @@ k_prep_c256(const float *__restrict__ img, int P, PrepArgs a, float2 *__restrict
             }
         }
         cluster_barrier();   // R complete (every CTA takes the same branch: mean and sd are cluster-wide)
+        if (pn < P) load_rows(pn);   // every warp of this CTA is done with Xr
         float e = 0.f;
         if (!bad) {
             // ---- columns: gather, transform, filter; keep in Stage / Col128
@@ -832,10 +863,7 @@ k_prep_c256(const float *__restrict__ img, int P, PrepArgs a, float2 *__restrict
         }
         if (c == NC - 1)
             for (int u = tid; u < N; u += NT) out[(size_t)u * HW + 128] = make_float2(Col128[u].x * sc, Col128[u].y * sc);
-        if (!spatial) {
-            __syncthreads();   // Stage is the next image's input buffer
-            continue;
-        }
+        if (!spatial) continue;   // Stage is written again after the next image's row barrier
         __syncthreads();
         // ---- spatial image: columns back in place, then rows two at a time
         {
