@@ -177,8 +177,9 @@ __device__ __forceinline__ float warp_max(float v) {
 // where W = conj(s1) + i conj(s2) and V = s1 + i s2.  Lane 0's second row is
 // held at columns 16 + 16 m (its last register is column 0), which the
 // twiddle e^{+2 pi i 16 k1 / 256} of the first 16-point pass accounts for.
-// CTA 0's rows 0 and 128 are each their own conjugate: one group builds the
-// two of them with two more loads of half rows.
+// CTA 0's rows 0 and 128 are each their own conjugate: one group builds row 0
+// as the pair (0, 0), transforms and stores it, then row 128 as the pair
+// (128, 128) in the same registers.
 namespace cw {
 
 constexpr int NT = 512, NG = NT / 16;
@@ -343,7 +344,7 @@ k_search_c256w(const float2 *__restrict__ St, int T, const float2 *__restrict__ 
     // row phase: this group's two rows, their slots; lane l's second row starts at column sg
     int ua, ub;
     unit_rows(c, g, ua, ub);
-    const bool singles = ua == 0;   // rows 0 and 128, each its own conjugate
+    const bool singles = ua == 0;   // rows 0 and 128 (ub), each its own conjugate
     const int sa = slot_of(ua), sb = slot_of(ub), sg = 16 - l, ng = sg & 15;
     // column phase: lane l's rows l + 16 n1 at owner o, slots 16 i + n1; columns 64 c + 2 g + q
     const int hm = (int)((kHome >> (4 * l)) & 15), io = hm & 3;
@@ -400,11 +401,7 @@ k_search_c256w(const float2 *__restrict__ St, int T, const float2 *__restrict__ 
             {
                 float2 a[16], b[16];
                 build_half<true>(s1, s2, sp, ua, l, a, b);
-                build_half<true>(s1, s2, sp, ub, sg, b, a);
-                if (singles) {   // the conjugate halves come from the rows themselves
-                    build_half<false>(s1, s2, sp, ub, l, b, b);
-                    build_half<false>(s1, s2, sp, ua, sg, a, a);
-                }
+                build_half<true>(s1, s2, sp, singles ? ua : ub, sg, b, a);   // singles: row 0 as the pair (0, 0)
                 ifft256_pass1(a, [&](int k1) { return twa[k1 * 16 + l]; }, l, scr, l);
                 dif16<0, 4, +1>(a);
                 if (pending) {   // every CTA is done reading this CTA's Zc
@@ -413,7 +410,12 @@ k_search_c256w(const float2 *__restrict__ St, int T, const float2 *__restrict__ 
                 }
 #pragma unroll
                 for (int q = 0; q < 16; ++q) Zc[zc_at(sa, l + 16 * cx_bitrev(q, 4))] = a[q];
-                ifft256_pass1(b, [&](int k1) { return twb[k1 * 16 + l]; }, ng, scr, l);
+                if (singles) {   // row 128 as the pair (128, 128), held at columns l + 16 m
+                    build_half<true>(s1, s2, sp, ub, l, b, a);
+                    build_half<true>(s1, s2, sp, ub, sg, a, b);
+                }
+                const float2 *twr = singles ? twa : twb;
+                ifft256_pass1(b, [&](int k1) { return twr[k1 * 16 + l]; }, singles ? l : ng, scr, l);
                 dif16<0, 4, +1>(b);
 #pragma unroll
                 for (int q = 0; q < 16; ++q) Zc[zc_at(sb, l + 16 * cx_bitrev(q, 4))] = b[q];
