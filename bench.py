@@ -375,7 +375,7 @@ def run_precision(args, px, torch, dev, rank, world, local, dist, emit=True):
     r_ach = P * k * flops_per_pair(n) / (r_ms / 1e3) / 1e12
     stages = {kk: v[0] / args.steps for kk, v in prof.items()}
     roofline = {"bound": "alu", "achieved": r_ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": r_ach / fp32_peak,
-                "traffic": None, "kernel": "k_search_c256 (rescore of the top-k candidates)",
+                "traffic": None, "kernel": "k_search_c256w (rescore of the top-k candidates)",
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
                 "stage_share": r_ms / max(sum(stages.values()), 1e-9),
                 "stage_ms_per_step": stages, "secondary": {"screen": screen_roof}}
@@ -784,7 +784,7 @@ def run_batched(args, px, torch, dev, rank, world, local, dist, emit=True):
         d["frac"] = d["achieved_tflops"] / fp32_peak
     achieved = flops / (search_ms_call / 1e3) / 1e12
     kernels = {16: "k_search_maps", 32: "k_search_maps", 64: "k_search_maps", 96: "k_search_maps",
-               128: "k_search_maps", 160: "k_search_maps", 200: "k_search_n200", 256: "k_search_c256"}
+               128: "k_search_maps", 160: "k_search_maps", 200: "k_search_n200", 256: "k_search_c256w"}
     body_names = {0: "warp lines (R x 32)", 1: "three rounds (16x8 | 4x32)", 2: "radix-2 in shared memory"}
     tuning = {}
     for (lib, _), n in zip(batch, ns):
