@@ -785,7 +785,8 @@ def run_batched(args, px, torch, dev, rank, world, local, dist, emit=True):
     achieved = flops / (search_ms_call / 1e3) / 1e12
     kernels = {16: "k_search_maps", 32: "k_search_maps", 64: "k_search_maps", 96: "k_search_maps",
                128: "k_search_maps", 160: "k_search_maps", 200: "k_search_n200", 256: "k_search_c256w"}
-    body_names = {0: "warp lines (R x 32)", 1: "three rounds (16x8 | 4x32)", 2: "radix-2 in shared memory"}
+    body_names = {0: "warp lines (R x 32)", 1: "three rounds (16x8 | 4x32)", 2: "radix-2 in shared memory",
+                  3: "eight-lane groups (8 x 8)"}
     tuning = {}
     for (lib, _), n in zip(batch, ns):
         t = px.xcf_maps_get_tuning(ctx, n, lib.T)

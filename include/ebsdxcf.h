@@ -372,6 +372,10 @@ int xcf_nearest_disorientation(xcf_ctx *ctx, const double *qa, int32_t na, const
  *                    shared-memory transposes (the kernel of xcf_index);
  *   XCF_BODY_SMEM    N = 16, 32, 64: the surface in shared memory, radix-2
  *                    line transforms;
+ *   XCF_BODY_OCT     N = 64 only: eight-lane groups, a 64-point line as an
+ *                    8-point FFT in registers, a twiddle, a shared-memory
+ *                    transpose and a second 8-point FFT (the kernel of
+ *                    xcf_index at N = 64);
  * the number of patterns a CTA searches side by side (1, 2 or 4 groups of
  * warps, each with its share of the shared memory, where the body fits), and
  * the granularity, the number of template pairs per work item (the whole
@@ -396,6 +400,7 @@ int xcf_index_maps(xcf_ctx *ctx, const xcf_map_desc *maps, int32_t n_maps, int32
 #define XCF_BODY_REG 0
 #define XCF_BODY_ROUNDS 1
 #define XCF_BODY_SMEM 2
+#define XCF_BODY_OCT 3
 /* The multi-map tuning of (side N, library size T) on ctx: the search body
  * (XCF_BODY_*), the groups per CTA (1, 2 or 4 patterns side by side, each on
  * 512 / groups threads and that share of the shared memory) and the template
@@ -404,7 +409,8 @@ int xcf_index_maps(xcf_ctx *ctx, const xcf_map_desc *maps, int32_t n_maps, int32
  * count) for later xcf_index_maps calls, instead of timing candidates, and
  * drops the context's captured graph; XCF_ERR_ARG if the body does not serve
  * side N, the groups are not 1, 2 or 4 or do not fit the body's shared
- * memory (XCF_BODY_ROUNDS: 1; XCF_BODY_REG at 128 and 160: 1; at 96: 1 or 2),
+ * memory (XCF_BODY_ROUNDS: 1; XCF_BODY_REG at 128 and 160: 1; at 96: 1 or 2;
+ * XCF_BODY_OCT: 1, 2 or 4),
  * or T, pairs <= 0. */
 int xcf_maps_get_tuning(const xcf_ctx *ctx, int32_t N, int32_t T, int32_t *body, int32_t *groups,
                         int32_t *pairs);

@@ -16,5 +16,5 @@ from .xcf import (  # noqa: F401
     xcf_propose, xcf_index_learned, xcf_index_precision, xcf_set_scratch_limit, xcf_scratch_bytes,
     XCF_LIB_NDP, XCF_LIB_NO_SPECTRA, xcf_index_ndp, xcf_rotation_scan, XCF_SO3_DEDUP, xcf_so3_grid,
     xcf_nearest_disorientation, xcf_fp32_fma_rate, xcf_maps_get_tuning, xcf_maps_set_tuning, XCF_BODY_REG,
-    XCF_BODY_ROUNDS, XCF_BODY_SMEM,
+    XCF_BODY_ROUNDS, XCF_BODY_SMEM, XCF_BODY_OCT,
 )

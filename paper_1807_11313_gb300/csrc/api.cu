@@ -1826,12 +1826,12 @@ bool queued_side(int N) { return N != 256 && N != 200; }
 
 // the body and grouping a side runs before (or without) tuning: the body of
 // its per-map kernel on whole CTAs
-int default_body(int N) { return N == 128 ? kBodyRounds : N < 64 ? kBodySmem : kBodyReg; }
+int default_body(int N) { return N == 128 ? kBodyRounds : N == 64 ? kBodyOct : N < 64 ? kBodySmem : kBodyReg; }
 // whether G groups per CTA fit body b of side N (each group gets 1/G of the shared memory)
 bool groups_fit(int N, int b, int G) {
     if (G != 1 && G != 2 && G != 4) return false;
     if (b == kBodyRounds) return G == 1;
-    return maps_item_smem(N, b) <= ((maps_smem_bytes() / G) & ~(size_t)15);
+    return maps_item_smem(N, b, kMapsThreads / G) <= ((maps_smem_bytes() / G) & ~(size_t)15);
 }
 int log2_groups(int G) { return G == 4 ? 2 : G == 2 ? 1 : 0; }
 
@@ -2013,7 +2013,7 @@ int maps_autotune(xcf_ctx *ctx, const xcf_map_desc *maps, int n, const MapLayout
         const int quarter = npairs / 4 > 8 ? npairs / 4 : (npairs < 8 ? npairs : 8);
         Choice best{default_body(N), 1, quarter};
         float best_t = 1e30f, per = 0.f;
-        for (int body = 0; body < 3 && status == XCF_OK; ++body) {
+        for (int body = 0; body < kNumBodies && status == XCF_OK; ++body) {
             if (!body_serves(N, body) || (body == kBodyRounds && !lib->spectra_pk)) continue;
             for (int G = 1; G <= 4 && status == XCF_OK; G *= 2) {
                 if (!groups_fit(N, body, G)) continue;

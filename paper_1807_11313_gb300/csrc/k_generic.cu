@@ -11,6 +11,7 @@
 #include "common.cuh"
 #include "generic.cuh"
 #include "kernels.cuh"
+#include "oct64.cuh"
 
 namespace {
 
@@ -416,6 +417,22 @@ __global__ void __launch_bounds__(search_threads<N>()) k_search_generic(const fl
     search_body<N, (search_threads<N>() <= 512)>(St, T, Sp, p, pb, pe, keys, peaks_all, cand, kc);
 }
 
+// N = 64: the eight-lane-group body (8 x 8 line transforms) on 128-thread
+// CTAs, several resident per SM
+constexpr int kOctThreads = 128;
+__global__ void __launch_bounds__(kOctThreads) k_search_oct64(const float2 *__restrict__ St, int T,
+                                                             const float2 *__restrict__ Sp,
+                                                             const int *__restrict__ degen, int pairs_per_cta,
+                                                             unsigned long long *__restrict__ keys,
+                                                             float *__restrict__ peaks_all,
+                                                             const int *__restrict__ cand, int kc) {
+    const int p = blockIdx.y;
+    if (degen[p]) return;
+    const int npairs = ((cand ? kc : T) + 1) / 2;
+    const int pb = blockIdx.x * pairs_per_cta, pe = min(npairs, pb + pairs_per_cta);
+    o64::search_body(St, T, Sp, p, pb, pe, keys, peaks_all, cand, kc, gen::cta_group());
+}
+
 __device__ __forceinline__ float parabola(float cm, float c0, float cp) {
     float den = cm - 2.f * c0 + cp;
     if (!(den < 0.f)) return 0.f;
@@ -560,10 +577,22 @@ template <int N>
 cudaError_t search_n(const float2 *St, int T, const float2 *Sp, const int *degen, int P,
                      unsigned long long *keys, float *peaks_all, int num_sms, cudaStream_t st,
                      const int *cand = nullptr, int kc = 0) {
+    const int npairs = ((cand ? kc : T) + 1) / 2;
+    if constexpr (N == 64) {   // 128-thread CTAs: enough to fill every SM four deep a few times over
+        const size_t sm = o64::smem_bytes(kOctThreads);
+        cudaError_t e = set_smem(k_search_oct64, sm);
+        if (e != cudaSuccess) return e;
+        const long want = (long)num_sms * 32;
+        int chunks = (int)((want + P - 1) / P);
+        chunks = max(1, min(chunks, (npairs + 3) / 4));
+        int ppc = (npairs + chunks - 1) / chunks;
+        chunks = (npairs + ppc - 1) / ppc;
+        k_search_oct64<<<dim3(chunks, P), kOctThreads, sm, st>>>(St, T, Sp, degen, ppc, keys, peaks_all, cand, kc);
+        return cudaGetLastError();
+    }
     size_t sm = gen::smem_bytes<N>();
     cudaError_t e = set_smem(k_search_generic<N>, sm);
     if (e != cudaSuccess) return e;
-    const int npairs = ((cand ? kc : T) + 1) / 2;
     // enough CTAs to fill the GPU a few times over, at least 4 pairs each
     long want = (long)num_sms * 8;
     int chunks = (int)((want + P - 1) / P);

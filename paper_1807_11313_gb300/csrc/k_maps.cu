@@ -15,7 +15,9 @@
 //                transforms in registers (R points per lane, 32-point lane
 //                stages by shuffles);
 //   kBodySmem    N = 2^k <= 64, the surface in shared memory with radix-2
-//                line transforms.
+//                line transforms;
+//   kBodyOct     N = 64, eight-lane groups: 8-point transforms in registers
+//                joined by shared-memory transposes (oct64.cuh).
 // The maps may have different libraries, pattern centres and detectors.  A
 // CTA never waits for another: the queue only hands out indices.  The
 // alternative launch shape (one CTA per item, grid = items) is one of the
@@ -25,6 +27,7 @@
 #include "kernels.cuh"
 #include "generic.cuh"
 #include "search128.cuh"
+#include "oct64.cuh"
 
 namespace {
 
@@ -34,6 +37,7 @@ static_assert(kMapThreads == kMapsThreads, "the queue CTA runs the three-round 1
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
 constexpr size_t kMapsSmem = cmax(cmax(s128::SMEM_BYTES, gen::smem_bytes<160>()),
                                   cmax(gen::smem_bytes<128>(), gen::smem_bytes<96>()));
+static_assert(o64::smem_bytes(kMapThreads) <= kMapsSmem, "the 8 x 8 body fits a whole queue CTA");
 
 __device__ __forceinline__ void run_item(const MapDev &m, const WorkItem &w, const gen::Grp &g) {
     switch (m.N) {
@@ -42,6 +46,8 @@ __device__ __forceinline__ void run_item(const MapDev &m, const WorkItem &w, con
         case 64:
             if (m.body == kBodySmem)
                 gen::search_body_smem<64>(m.St, m.T, m.Sp, w.p, w.pb, w.pe, m.keys, nullptr, nullptr, 0, g);
+            else if (m.body == kBodyOct)
+                o64::search_body(m.St, m.T, m.Sp, w.p, w.pb, w.pe, m.keys, nullptr, nullptr, 0, g);
             else
                 gen::search_body_reg<64>(m.St, m.T, m.Sp, w.p, w.pb, w.pe, m.keys, nullptr, nullptr, 0, g);
             break;

@@ -66,6 +66,8 @@ cudaError_t launch_to_bf16(const float *x, size_t n, void *y, cudaStream_t st);
 constexpr int kBodyReg = 0;      // register warp-line transforms (N = R x 32: 64, 96, 128, 160)
 constexpr int kBodyRounds = 1;   // N = 128: three register rounds with two shared-memory transposes
 constexpr int kBodySmem = 2;     // surface in shared memory, radix-2 line transforms (2^k sides up to 64)
+constexpr int kBodyOct = 3;      // N = 64: eight-lane groups, 8 x 8 line transforms with shared-memory transposes
+constexpr int kNumBodies = 4;
 struct MapDev {
     int N, T, body;                // detector side, library size, search body (items of the map run on
                                    // groups of 512 / G threads, G from the map's phase of the queue)
@@ -80,6 +82,7 @@ __host__ __device__ inline bool body_serves(int N, int b) {
     if (b == kBodyReg) return N == 64 || N == 96 || N == 128 || N == 160;
     if (b == kBodyRounds) return N == 128;
     if (b == kBodySmem) return N == 16 || N == 32 || N == 64;
+    if (b == kBodyOct) return N == 64;
     return false;
 }
 struct WorkItem {
@@ -87,11 +90,13 @@ struct WorkItem {
 };
 size_t maps_smem_bytes();
 constexpr int kMapsThreads = 512;   // threads of a queue CTA
-// shared memory one item of side N with body b needs (the queue gives each of
-// the G groups of a CTA maps_smem_bytes() / G, rounded down to 16 bytes)
-inline size_t maps_item_smem(int N, int b) {
-    return b == kBodyRounds ? (size_t)8 * (128 * 65 + 128 * 128 + 128 + 128 + 256 + 32 + 128)
-                            : (size_t)8 * ((size_t)N * (N + 1) + N + 34);
+// shared memory one item of side N with body b needs on nt threads (the queue
+// gives each of the G groups of a CTA maps_smem_bytes() / G, rounded down to
+// 16 bytes, and 512 / G threads)
+inline size_t maps_item_smem(int N, int b, int nt = kMapsThreads) {
+    if (b == kBodyRounds) return (size_t)8 * (128 * 65 + 128 * 128 + 128 + 128 + 256 + 32 + 128);
+    if (b == kBodyOct) return (size_t)8 * (64 * 64 + (size_t)(nt / 8) * 72 + 16);
+    return (size_t)8 * ((size_t)N * (N + 1) + N + 34);
 }
 // Items are ordered by phase: [offs[0], offs[1]) run on whole CTAs, [offs[1],
 // offs[2]) on two groups of 256 threads per CTA, [offs[2], offs[3]) on four

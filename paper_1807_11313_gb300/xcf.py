@@ -575,7 +575,7 @@ def xcf_rescore(ctx: Context, lib: Library, patterns, cand):
 XCF_MAPS_GRAPH = 1
 
 
-XCF_BODY_REG, XCF_BODY_ROUNDS, XCF_BODY_SMEM = 0, 1, 2
+XCF_BODY_REG, XCF_BODY_ROUNDS, XCF_BODY_SMEM, XCF_BODY_OCT = 0, 1, 2, 3
 
 
 def xcf_maps_get_tuning(ctx: Context, N: int, T: int):

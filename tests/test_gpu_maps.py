@@ -74,7 +74,8 @@ def _pin_per_map_bodies(px, ctx, ms):
     for _, lib, _ in ms:
         if lib.N == 256:
             continue
-        body = px.XCF_BODY_ROUNDS if lib.N == 128 else px.XCF_BODY_SMEM if lib.N < 64 else px.XCF_BODY_REG
+        body = (px.XCF_BODY_ROUNDS if lib.N == 128 else px.XCF_BODY_OCT if lib.N == 64 else
+                px.XCF_BODY_SMEM if lib.N < 64 else px.XCF_BODY_REG)
         px.xcf_maps_set_tuning(ctx, lib.N, lib.T, body, max(1, (lib.T + 1) // 8))
 
 
@@ -117,11 +118,12 @@ def test_maps_smallest_against_oracle(px, maps, master, orc):
 
 
 @pytest.mark.parametrize("which,body,groups", [(0, 2, 1), (0, 2, 4), (1, 0, 1), (1, 0, 2), (1, 0, 4), (1, 2, 1),
-                                               (1, 2, 4), (2, 0, 1), (2, 1, 1), (3, 1, 1)])
+                                               (1, 2, 4), (1, 3, 1), (1, 3, 2), (1, 3, 4), (2, 0, 1), (2, 1, 1),
+                                               (3, 1, 1)])
 def test_maps_every_body_against_oracle(px, maps, master, orc, which, body, groups):
     """Each search body the queue has for a side (32: radix-2 in shared
-    memory; 64: warp lines or radix-2 in shared memory; 128: warp lines or
-    three register rounds), on whole CTAs or on 2 / 4 groups of warps per CTA
+    memory; 64: warp lines, radix-2 in shared memory or 8 x 8 transforms on
+    eight-lane groups; 128: warp lines or three register rounds), on whole CTAs or on 2 / 4 groups of warps per CTA
     where it fits, at two granularities, against the oracle at the stated
     bounds."""
     ctx, ms = maps
@@ -142,7 +144,7 @@ def test_maps_autotuner_choice(px, maps):
     _, ms = maps
     ctx = px.Context()
     outs = px.xcf_index_maps(ctx, [(lib, pats) for _, lib, pats in ms])
-    serves = {16: {2}, 32: {2}, 64: {0, 2}, 96: {0}, 128: {0, 1}, 160: {0}}
+    serves = {16: {2}, 32: {2}, 64: {0, 2, 3}, 96: {0}, 128: {0, 1}, 160: {0}}
     for (g, lib, pats), o in zip(ms, outs):
         ref = _per_map(px, ctx, lib, pats)
         if lib.N == 256:
@@ -201,7 +203,7 @@ def test_maps_graph_replay_follows_new_data(px, maps):
 def test_maps_tuning_rejects_what_does_not_fit(px):
     c = px.Context()
     for N, body, groups in ((128, 1, 2), (128, 0, 2), (160, 0, 2), (96, 0, 4), (256, 0, 1), (96, 1, 1), (160, 2, 1),
-                            (64, 0, 3)):
+                            (64, 0, 3), (96, 3, 1), (128, 3, 1), (32, 3, 1), (64, 4, 1)):
         with pytest.raises(px.XcfError):
             px.xcf_maps_set_tuning(c, N, 100, body, 10, groups)
     assert px.xcf_maps_get_tuning(c, 96, 100) is None
