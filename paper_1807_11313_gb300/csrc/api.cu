@@ -252,6 +252,29 @@ cudaError_t run_search(xcf_ctx * /*ctx*/, int n, const float2 *St, int T, const 
     return launch_search_c256(St, T, Sp, degen, P, keys, peaks_all, nullptr, 0, st);
 }
 
+// templates projected at (quats, pcs) and pre-processed: in one kernel where
+// the side has one (the images never reach memory), else the projection into
+// img followed by the pre-processing
+bool fused_project_prep(int n) { return n == 16 || n == 32 || n == 64 || n == 128; }
+int project_prep(xcf_ctx *ctx, const float *master, int M, const double *quats, const double *pcs,
+                 const int *active, int P, const ProjArgs &pj, const PrepArgs &ps, float2 *spec, float *spatial,
+                 int *degen, float *img, cudaStream_t st) {
+    if (fused_project_prep(ps.N)) {
+        ProjSrc src;
+        src.master = master;
+        src.M = M;
+        src.quats = quats;
+        src.pcs = pcs;
+        src.a = pj;
+        XCF_LAUNCH(XCF_STAGE_PREP, st, launch_prep_projected(src, P, ps, spec, spatial, degen, active, st),
+                   "project + prep templates");
+        return XCF_OK;
+    }
+    XCF_LAUNCH(XCF_STAGE_PROJECT, st, launch_project(master, M, quats, pcs, active, P, pj, img, st), "project");
+    XCF_LAUNCH(XCF_STAGE_PREP, st, run_prep(ctx, img, P, ps, spec, spatial, degen, active, st), "prep templates");
+    return XCF_OK;
+}
+
 // integer peak and 3-point fit, then (with the up-sampling option) the up-sampled peak
 cudaError_t run_pair_peak(xcf_ctx *ctx, int n, const float2 *St, const int *tidx, const float2 *Sp,
                           const int *degen, const int *active, int P, float *peak, float *shift, cudaStream_t st) {
@@ -363,17 +386,15 @@ int refine_chunk(xcf_ctx *ctx, const xcf_library *lib, const float *patterns, in
     XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_init_refine(degen, select, P, active, iters, peak, st), "init");
     for (int it = 0; it < max_iter; ++it) {
         // X / Y: shift of the template at the current orientation
-        XCF_LAUNCH(XCF_STAGE_PROJECT, st, launch_project(lib->master, lib->M, quats, pcs, active, P, pj, img, st),
-                   "project");
-        XCF_LAUNCH(XCF_STAGE_PREP, st, run_prep(ctx,img, P, ps, stt, nullptr, nullptr, active, st), "prep templates");
+        if ((rc = project_prep(ctx, lib->master, lib->M, quats, pcs, active, P, pj, ps, stt, nullptr, nullptr, img, st)))
+            return rc;
         XCF_LAUNCH(XCF_STAGE_PEAK, st, run_pair_peak(ctx,n, stt, nullptr, sp, degen, active, P, peak, shift, st),
                    "xy peak");
         XCF_LAUNCH(XCF_STAGE_UPDATE, st,
                    launch_update_xy(quats, shift, pcs, g->pcz, g->width, alpha, active, P, q1, st), "xy update");
         // Z: angular shift of the log-polar images
-        XCF_LAUNCH(XCF_STAGE_PROJECT, st, launch_project(lib->master, lib->M, q1, pcs, active, P, pj, img, st),
-                   "project");
-        XCF_LAUNCH(XCF_STAGE_PREP, st, run_prep(ctx,img, P, ps, stt, yt, nullptr, active, st), "prep templates");
+        if ((rc = project_prep(ctx, lib->master, lib->M, q1, pcs, active, P, pj, ps, stt, yt, nullptr, img, st)))
+            return rc;
         XCF_LAUNCH(XCF_STAGE_LOGPOLAR, st,
                    launch_logpolar(yt, active, P, n, r.nr, r.neta, (float)r.rmin, (float)r.rmax, lpt, st),
                    "logpolar templates");
@@ -605,9 +626,18 @@ int build_from_master(xcf_ctx *ctx, const float *master, int32_t M, const double
             xcf_library_free(lib);
             return rc;
         }
-        e = launch_project(lib->master, M, lib->quats + 4 * (size_t)t0, nullptr, nullptr, nt, pj, img, st);
-        if (e == cudaSuccess) e = run_prep(ctx,img, nt, ps, lib->spectra + H * t0, nullptr, degen, nullptr, st);
-        ctx->launches[XCF_STAGE_PROJECT] += 1;
+        if (fused_project_prep(c.n)) {   // projected and pre-processed in one kernel
+            ProjSrc src;
+            src.master = lib->master;
+            src.M = M;
+            src.quats = lib->quats + 4 * (size_t)t0;
+            src.a = pj;
+            e = launch_prep_projected(src, nt, ps, lib->spectra + H * t0, nullptr, degen, nullptr, st);
+        } else {
+            e = launch_project(lib->master, M, lib->quats + 4 * (size_t)t0, nullptr, nullptr, nt, pj, img, st);
+            if (e == cudaSuccess) e = run_prep(ctx, img, nt, ps, lib->spectra + H * t0, nullptr, degen, nullptr, st);
+            ctx->launches[XCF_STAGE_PROJECT] += 1;
+        }
         ctx->launches[XCF_STAGE_PREP] += 1;
     }
     if (spectra && e == cudaSuccess && has_search_layout(c.n)) {
@@ -1761,10 +1791,9 @@ int xcf_index_learned(xcf_ctx *ctx, xcf_net *net, const xcf_library *lib, const 
         XCF_LAUNCH(XCF_STAGE_PREP, st, run_prep(ctx, pat, np, pa, sp, nullptr, degen, nullptr, st), "prep patterns");
         for (int h = 0; h < k; ++h) {
             XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_take_head(prop, np, k, h, qh, st), "take head");
-            XCF_LAUNCH(XCF_STAGE_PROJECT, st, launch_project(lib->master, lib->M, qh, pc, nullptr, np, pj, img_t, st),
-                       "project proposals");
-            XCF_LAUNCH(XCF_STAGE_PREP, st, run_prep(ctx, img_t, np, ps, stt, nullptr, nullptr, nullptr, st),
-                       "prep proposals");
+            if ((rc = project_prep(ctx, lib->master, lib->M, qh, pc, nullptr, np, pj, ps, stt, nullptr, nullptr, img_t,
+                                   st)))
+                return rc;
             XCF_LAUNCH(XCF_STAGE_PEAK, st, run_pair_peak(ctx, n, stt, nullptr, sp, degen, nullptr, np, peak_h, shift, st),
                        "proposal peaks");
             XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_keep_best(peak_h, qh, np, h, best_peak, q, nullptr, st), "keep best");

@@ -12,6 +12,7 @@
 #include "generic.cuh"
 #include "kernels.cuh"
 #include "oct64.cuh"
+#include "project.cuh"
 
 namespace {
 
@@ -48,10 +49,13 @@ constexpr int peak_threads() { return N >= 128 ? 1024 : kThreads; }
 template <int N>
 __host__ __device__ constexpr int search_threads() { return N >= 128 ? 1024 : kThreads; }
 
-template <int N, int PT = prep_threads<N>()>
+// PROJ: the image is projected from the master pattern (ps) while it is
+// loaded, instead of read from img
+template <int N, int PT = prep_threads<N>(), bool PROJ = false>
 __global__ void __launch_bounds__(PT) k_prep_real(const float *__restrict__ img, PrepArgs a,
                                                         float2 *__restrict__ spec, float *__restrict__ spatial,
-                                                        int *__restrict__ degen, const int *__restrict__ active) {
+                                                        int *__restrict__ degen, const int *__restrict__ active,
+                                                        ProjSrc ps) {
     constexpr int H = N / 2, LD = N + 1, HW = N / 2 + 1;
     if (active && !active[blockIdx.x]) return;
     extern __shared__ float4 smem_raw[];
@@ -73,11 +77,22 @@ __global__ void __launch_bounds__(PT) k_prep_real(const float *__restrict__ img,
     // ---- load (rows 2pr, 2pr+1 into the real and imaginary parts of buf row pr) and statistics:
     // one pass of FP32 sums of (x - x0), x0 the crop's first pixel (a constant crop has exactly
     // zero variance; the shift keeps the per-thread sums well conditioned), combined in FP64
-    const float x0 = __ldg(src + (size_t)a.oy * a.W + a.ox);
+    __shared__ proj::Frame fr;
+    if constexpr (PROJ) {
+        if (tid == 0) proj::frame(ps.quats + 4 * (size_t)p, ps.pcs ? ps.pcs + 3 * (size_t)p : nullptr, ps.a, fr);
+        __syncthreads();
+    }
+    auto pixel = [&](int r, int c) -> float {   // image pixel (a.oy + r, a.ox + c)
+        if constexpr (PROJ)
+            return proj::pixel(fr, ps.master, ps.M, ps.a, a.oy + r, a.ox + c);
+        else
+            return src[(size_t)(a.oy + r) * a.W + a.ox + c];
+    };
+    const float x0 = pixel(0, 0);
     float s1 = 0.f, s2 = 0.f;
     for (int idx = tid; idx < N * N; idx += PT) {
         const int r = idx / N, c = idx % N;
-        const float v = src[(size_t)(a.oy + r) * a.W + a.ox + c];
+        const float v = pixel(r, c);
         reinterpret_cast<float *>(buf + (r >> 1) * LD + c)[r & 1] = v;
         const float d = v - x0;
         s1 += d;
@@ -559,7 +574,18 @@ cudaError_t prep_n(const float *img, int P, const PrepArgs &a, float2 *spec, flo
     const size_t sm = smem_prep_real<N>();
     cudaError_t e = set_smem(k_prep_real<N>, sm);
     if (e != cudaSuccess) return e;
-    k_prep_real<N><<<P, prep_threads<N>(), sm, st>>>(img, a, spec, spatial, degen, active);
+    k_prep_real<N><<<P, prep_threads<N>(), sm, st>>>(img, a, spec, spatial, degen, active, ProjSrc{});
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t prep_projected_n(const ProjSrc &src, int P, const PrepArgs &a, float2 *spec, float *spatial, int *degen,
+                             const int *active, cudaStream_t st) {
+    const size_t sm = smem_prep_real<N>();
+    auto *k = k_prep_real<N, prep_threads<N>(), true>;
+    cudaError_t e = set_smem(k, sm);
+    if (e != cudaSuccess) return e;
+    k<<<P, prep_threads<N>(), sm, st>>>(nullptr, a, spec, spatial, degen, active, src);
     return cudaGetLastError();
 }
 
@@ -631,6 +657,22 @@ cudaError_t launch_prep(const float *img, int P, const PrepArgs &a, float2 *spec
         case 160: return prep_cplx_n<160>(img, P, a, spec, spatial, degen, active, st);
         case 200: return launch_prep_n200(img, P, a, spec, spatial, degen, active, st);
         default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_prep_projected(const ProjSrc &src, int P, const PrepArgs &a, float2 *spec, float *spatial,
+                                  int *degen, const int *active, cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    if (src.a.nx != a.W || src.a.ny != a.H) return cudaErrorInvalidValue;
+    ProjSrc s = src;   // the rotation's cosine and sine once, on the host (as launch_project)
+    s.a.ca = cos(src.a.alpha);
+    s.a.sa = sin(src.a.alpha);
+    switch (a.N) {
+        case 16: return prep_projected_n<16>(s, P, a, spec, spatial, degen, active, st);
+        case 32: return prep_projected_n<32>(s, P, a, spec, spatial, degen, active, st);
+        case 64: return prep_projected_n<64>(s, P, a, spec, spatial, degen, active, st);
+        case 128: return prep_projected_n<128>(s, P, a, spec, spatial, degen, active, st);
+        default: return cudaErrorNotSupported;
     }
 }
 

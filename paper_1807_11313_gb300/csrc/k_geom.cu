@@ -9,6 +9,7 @@
 #include "common.cuh"
 #include "line_fft.cuh"
 #include "kernels.cuh"
+#include "project.cuh"
 
 namespace {
 
@@ -41,67 +42,6 @@ __device__ __forceinline__ Q rotate_in_detector(const Q &q, const Q &R, double a
     return qcanon(qmul(qmul(qmul(q, qs), qconj(R)), qconj(qs)));
 }
 
-// ------------------------------------------------------ Lambert lookup
-// Keys' cubic convolution weight, a = -1/2
-__device__ __forceinline__ float keys_weight(float t) {
-    t = fabsf(t);
-    if (t <= 1.f) return (1.5f * t - 2.5f) * t * t + 1.f;
-    if (t < 2.f) return ((-0.5f * t + 2.5f) * t - 4.f) * t + 2.f;
-    return 0.f;
-}
-
-// Rosca equal-area square of a hemisphere, then bilinear (interp 0) or
-// bicubic (interp 1, Keys) interpolation of the M x M grid of cell centres,
-// clamped at the edges.
-__device__ __forceinline__ float master_lookup(const float *__restrict__ master, int M, float x, float y,
-                                               float z, int interp = 0) {
-    const float az = fabsf(z);
-    const float s2 = x * x + y * y;
-    float X = 0.f, Y = 0.f;
-    if (s2 > 0.f) {
-        const float qv = sqrtf(2.f * s2 / (1.f + az));   // sqrt(2 (1 - |z|)), cancellation-free
-        const float sp = 0.88622692545275801365f;         // sqrt(pi) / 2
-        const float ts = 1.12837916709551257390f;         // 2 / sqrt(pi)
-        if (fabsf(y) <= fabsf(x)) {
-            const float sg = x >= 0.f ? 1.f : -1.f;
-            X = sg * qv * sp;
-            Y = sg * qv * ts * atanf(y / x);
-        } else {
-            const float sg = y >= 0.f ? 1.f : -1.f;
-            X = sg * qv * ts * atanf(x / y);
-            Y = sg * qv * sp;
-        }
-    }
-    const float invL = 0.79788456080286535588f;           // 1 / sqrt(pi / 2)
-    float fx = (X * invL + 1.f) * (0.5f * M) - 0.5f;
-    float fy = (Y * invL + 1.f) * (0.5f * M) - 0.5f;
-    fx = fminf(fmaxf(fx, 0.f), (float)(M - 1));
-    fy = fminf(fmaxf(fy, 0.f), (float)(M - 1));
-    if (interp == 1) {
-        const float *g = master + (z >= 0.f ? 0 : (size_t)M * M);
-        const int i0 = (int)floorf(fx), j0 = (int)floorf(fy);
-        float s = 0.f;
-#pragma unroll
-        for (int dj = -1; dj <= 2; ++dj) {
-            const int j = min(max(j0 + dj, 0), M - 1);
-            const float wy = keys_weight(fy - (float)(j0 + dj));
-            float row = 0.f;
-#pragma unroll
-            for (int di = -1; di <= 2; ++di) {
-                const int i = min(max(i0 + di, 0), M - 1);
-                row = fmaf(keys_weight(fx - (float)(i0 + di)), __ldg(g + (size_t)j * M + i), row);
-            }
-            s = fmaf(wy, row, s);
-        }
-        return s;
-    }
-    int i0 = min((int)floorf(fx), M - 2), j0 = min((int)floorf(fy), M - 2);
-    const float tx = fx - i0, ty = fy - j0;
-    const float *g = master + (z >= 0.f ? 0 : (size_t)M * M) + (size_t)j0 * M + i0;
-    const float a = __ldg(g), b = __ldg(g + 1), c = __ldg(g + M), d = __ldg(g + M + 1);
-    return (1.f - ty) * ((1.f - tx) * a + tx * b) + ty * ((1.f - tx) * c + tx * d);
-}
-
 // ---------------------------------------------------------- projection
 __global__ void __launch_bounds__(256) k_project(const float *__restrict__ master, int M,
                                                  const double *__restrict__ quats,
@@ -110,46 +50,14 @@ __global__ void __launch_bounds__(256) k_project(const float *__restrict__ maste
                                                  float *__restrict__ out) {
     const int p = blockIdx.y;
     if (active && !active[p]) return;
-    __shared__ float G[9];
-    __shared__ float pc[3];
-    if (threadIdx.x == 0) {
-        // the frame in FP32 (G is stored in FP32 anyway; FP64 here stalled the block on
-        // GB300's narrow FP64 pipe)
-        const double *qq = quats + 4 * (size_t)p;
-        float w = (float)qq[0], x = (float)qq[1], y = (float)qq[2], z = (float)qq[3];
-        const float inv = rsqrtf(w * w + x * x + y * y + z * z);
-        w *= inv; x *= inv; y *= inv; z *= inv;
-        float R[9];
-        R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
-        R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
-        R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
-        const float sa = (float)a.sa, ca = (float)a.ca;
-        // G = R(q) Rx(alpha): detector direction -> crystal direction
-        for (int i = 0; i < 3; ++i) {
-            G[3 * i + 0] = R[3 * i + 0];
-            G[3 * i + 1] = R[3 * i + 1] * ca + R[3 * i + 2] * sa;
-            G[3 * i + 2] = -R[3 * i + 1] * sa + R[3 * i + 2] * ca;
-        }
-        double px = a.pcx, py = a.pcy, pz = a.pcz;
-        if (pcs) { px = pcs[3 * (size_t)p]; py = pcs[3 * (size_t)p + 1]; pz = pcs[3 * (size_t)p + 2]; }
-        pc[0] = (float)px * (float)a.W;
-        pc[1] = (float)py * (float)a.H;
-        pc[2] = (float)pz * (float)a.W;
-    }
+    __shared__ proj::Frame fr;
+    if (threadIdx.x == 0) proj::frame(quats + 4 * (size_t)p, pcs ? pcs + 3 * (size_t)p : nullptr, a, fr);
     __syncthreads();
     const int npx = a.nx * a.ny;
     float *dst = out + (size_t)p * npx;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < npx; idx += gridDim.x * blockDim.x) {
         const int i = idx / a.nx, j = idx % a.nx;
-        float dx = (float)(a.ox + j) + 0.5f - pc[0];
-        float dy = pc[1] - ((float)(a.oy + i) + 0.5f);
-        float dz = pc[2];
-        const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-        dx *= inv; dy *= inv; dz *= inv;
-        const float cx = G[0] * dx + G[1] * dy + G[2] * dz;
-        const float cy = G[3] * dx + G[4] * dy + G[5] * dz;
-        const float cz = G[6] * dx + G[7] * dy + G[8] * dz;
-        dst[idx] = master_lookup(master, M, cx, cy, cz, a.interp);
+        dst[idx] = proj::pixel(fr, master, M, a, i, j);
     }
 }
 

@@ -26,6 +26,21 @@ struct ProjArgs {
 // `active` (nullable): images whose flag is 0 are skipped entirely
 cudaError_t launch_prep(const float *img, int P, const PrepArgs &a, float2 *spec, float *spatial,
                         int *degen, const int *active, cudaStream_t st);
+// images made by projecting the master pattern instead of read from memory:
+// image p is the projection of region `a` (nx x ny = the image's W x H) at
+// orientation quats[p] and pattern centre pcs[p] (or a's default)
+struct ProjSrc {
+    const float *master = nullptr;
+    int M = 0;
+    const double *quats = nullptr;   // [P][4]
+    const double *pcs = nullptr;     // [P][3] or null
+    ProjArgs a;
+};
+// pre-processing of projected images (launch_project then launch_prep, in one
+// kernel and without the images in memory): sides 16, 32, 64 and 128;
+// cudaErrorNotSupported for the others
+cudaError_t launch_prep_projected(const ProjSrc &src, int P, const PrepArgs &a, float2 *spec, float *spatial,
+                                  int *degen, const int *active, cudaStream_t st);
 
 // all-pairs search: per-pattern best key (atomicMax) and optional per-pair peaks [P, T]
 cudaError_t launch_search(int N, const float2 *St, int T, const float2 *Sp, const int *degen, int P,
