@@ -123,7 +123,7 @@ __device__ __forceinline__ float parabola(float cm, float c0, float cp) {
 constexpr int kEtaThreads = 256, kEtaWarps = kEtaThreads / 32, kMaxLpWindows = 16;
 
 template <int NETA>
-__global__ void __launch_bounds__(kEtaThreads) k_eta_update(const float *__restrict__ lpT,
+__global__ void __launch_bounds__(kEtaThreads, NETA >= 512 ? 2 : 3) k_eta_update(const float *__restrict__ lpT,
                                                             const float *__restrict__ lpP, int nr, int windows,
                                                             const double *__restrict__ q0s,
                                                             const double *__restrict__ q1s,
@@ -144,6 +144,10 @@ __global__ void __launch_bounds__(kEtaThreads) k_eta_update(const float *__restr
     const float *ga = lpT + (size_t)p * nr * NETA, *gb = lpP + (size_t)p * nr * NETA;
     linefft::make_tw<NETA>(tw, -1);
     linefft::make_tw<NETA>(twi, +1);
+    __syncthreads();   // the twiddle tables
+    constexpr bool kRegLine = NETA >= 64;   // register warp transforms (NETA = R x 32)
+    WarpFftTw<kRegLine ? NETA : 64> wf;
+    if constexpr (kRegLine) wf.load(tw, lane);
     float2 *z = line[w];
     // radial window b holds radii [b nr / W, (b + 1) nr / W); each is correlated along eta on its own
     for (int b = 0; b < windows; ++b) {
@@ -157,10 +161,24 @@ __global__ void __launch_bounds__(kEtaThreads) k_eta_update(const float *__restr
 #pragma unroll
         for (int j = 0; j < KPL; ++j) acc[j] = make_float2(0.f, 0.f);
         for (int m = m0 + w; m < m1; m += kEtaWarps) {
-            for (int l = lane; l < NETA; l += 32)
-                z[l] = make_float2(ga[(size_t)m * NETA + l] - ma, gb[(size_t)m * NETA + l] - mb);
-            __syncwarp();
-            linefft::warp_fft_line<NETA>(z, 1, tw);   // forward: Z[k] = sum_l z[l] e^{-2 pi i k l / NETA}
+            // forward: Z[k] = sum_l z[l] e^{-2 pi i k l / NETA}
+            if constexpr (kRegLine) {   // in registers (NETA / 32 points per lane), spectrum to z
+                float2 v[NETA / 32];
+#pragma unroll
+                for (int j = 0; j < NETA / 32; ++j) {
+                    const size_t i = (size_t)m * NETA + lane + 32 * j;
+                    v[j] = make_float2(ga[i] - ma, gb[i] - mb);
+                }
+                warp_fft_core<NETA>(v, wf, lane);
+#pragma unroll
+                for (int j = 0; j < NETA / 32; ++j) z[warp_fft_out<NETA>(lane, j)] = v[j];
+                __syncwarp();
+            } else {
+                for (int l = lane; l < NETA; l += 32)
+                    z[l] = make_float2(ga[(size_t)m * NETA + l] - ma, gb[(size_t)m * NETA + l] - mb);
+                __syncwarp();
+                linefft::warp_fft_line<NETA>(z, 1, tw);
+            }
 #pragma unroll
             for (int j = 0; j < KPL; ++j) {
                 const int k = lane + 32 * j;
@@ -191,15 +209,33 @@ __global__ void __launch_bounds__(kEtaThreads) k_eta_update(const float *__restr
                 if (k > 0 && k < NETA / 2) zc[NETA - k] = make_float2((float)cr, (float)-ci);
             }
             __syncwarp();
-            linefft::warp_fft_line<NETA>(zc, 1, twi);
-            for (int d = lane; d < NETA; d += 32) cfin[d] = zc[d].x;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int best = 0;
-            for (int D = 1; D < NETA; ++D) if (cfin[D] > cfin[best]) best = D;
-            const float off = parabola(cfin[(best + NETA - 1) % NETA], cfin[best], cfin[(best + 1) % NETA]);
-            wshift[b] = (double)(best < NETA / 2 ? best : best - NETA) + off;
+            if constexpr (kRegLine) {
+                WarpFftTw<NETA> wi;
+                wi.load(twi, lane);
+                float2 v[NETA / 32];
+#pragma unroll
+                for (int j = 0; j < NETA / 32; ++j) v[j] = zc[lane + 32 * j];
+                warp_fft_core<NETA>(v, wi, lane);
+#pragma unroll
+                for (int j = 0; j < NETA / 32; ++j) cfin[warp_fft_out<NETA>(lane, j)] = v[j].x;
+            } else {
+                linefft::warp_fft_line<NETA>(zc, 1, twi);
+                for (int d = lane; d < NETA; d += 32) cfin[d] = zc[d].x;
+            }
+            __syncwarp();
+            // argmax over the shifts (the lowest shift among equal maxima), then the parabola
+            int best = lane;
+            for (int D = lane + 32; D < NETA; D += 32)
+                if (cfin[D] > cfin[best]) best = D;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+                if (cfin[ob] > cfin[best] || (cfin[ob] == cfin[best] && ob < best)) best = ob;
+            }
+            if (lane == 0) {
+                const float off = parabola(cfin[(best + NETA - 1) % NETA], cfin[best], cfin[(best + 1) % NETA]);
+                wshift[b] = (double)(best < NETA / 2 ? best : best - NETA) + off;
+            }
         }
         __syncthreads();   // line, zc and cfin are reused by the next window
     }
