@@ -62,26 +62,29 @@ __global__ void __launch_bounds__(256) k_project(const float *__restrict__ maste
 }
 
 // ------------------------------------------------------------ log-polar
+// each thread samples one (radius m, angle l) position of kLpPats images: the
+// position (one expf, one sincospif) is computed once for all of them
+constexpr int kLpPats = 8;
 __global__ void __launch_bounds__(256) k_logpolar(const float *__restrict__ spatial,
-                                                  const int *__restrict__ active, int N, int nr,
-                                                  int neta, float rmin, float rmax,
-                                                  float *__restrict__ out) {
-    const int p = blockIdx.y;
-    if (active && !active[p]) return;
-    const float *img = spatial + (size_t)p * N * N;
+                                                  const int *__restrict__ active, int P, int N, int nr,
+                                                  int neta, float rmin, float rmax, float *__restrict__ out) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nr * neta) return;
     const float c = 0.5f * N - 0.5f;
     const float lr = logf(rmax / rmin);
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nr * neta; idx += gridDim.x * blockDim.x) {
-        const int m = idx / neta, l = idx % neta;
-        const float r = rmin * expf(lr * (nr > 1 ? (float)m / (nr - 1) : 0.f));
-        float sn, cs;
-        sincospif(2.f * l / neta, &sn, &cs);
-        const float fx = c + r * cs, fy = c - r * sn;
-        int x0 = (int)floorf(fx), y0 = (int)floorf(fy);
-        x0 = min(max(x0, 0), N - 2);
-        y0 = min(max(y0, 0), N - 2);
-        const float tx = fx - x0, ty = fy - y0;
-        const float *g = img + y0 * N + x0;
+    const int m = idx / neta, l = idx % neta;
+    const float r = rmin * expf(lr * (nr > 1 ? (float)m / (nr - 1) : 0.f));
+    float sn, cs;
+    sincospif(2.f * l / neta, &sn, &cs);
+    const float fx = c + r * cs, fy = c - r * sn;
+    int x0 = (int)floorf(fx), y0 = (int)floorf(fy);
+    x0 = min(max(x0, 0), N - 2);
+    y0 = min(max(y0, 0), N - 2);
+    const float tx = fx - x0, ty = fy - y0;
+    const int p1 = min(P, (int)(blockIdx.y + 1) * kLpPats);
+    for (int p = blockIdx.y * kLpPats; p < p1; ++p) {
+        if (active && !active[p]) continue;
+        const float *g = spatial + (size_t)p * N * N + y0 * N + x0;
         out[(size_t)p * nr * neta + idx] =
             (1.f - ty) * ((1.f - tx) * g[0] + tx * g[1]) + ty * ((1.f - tx) * g[N] + tx * g[N + 1]);
     }
@@ -387,10 +390,11 @@ cudaError_t launch_project(const float *master, int M, const double *quats, cons
 cudaError_t launch_logpolar(const float *spatial, const int *active, int P, int N, int nr, int neta,
                             float rmin, float rmax, float *out, cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
-    for (int p0 = 0; p0 < P; p0 += 65535) {          // grid.y limit
-        const int np = P - p0 < 65535 ? P - p0 : 65535;
-        dim3 grid((nr * neta + 255) / 256, np);
-        k_logpolar<<<grid, 256, 0, st>>>(spatial + (size_t)N * N * p0, active ? active + p0 : nullptr, N, nr,
+    constexpr int kChunk = 65535 * kLpPats;          // grid.y limit
+    for (int p0 = 0; p0 < P; p0 += kChunk) {
+        const int np = P - p0 < kChunk ? P - p0 : kChunk;
+        dim3 grid((nr * neta + 255) / 256, (np + kLpPats - 1) / kLpPats);
+        k_logpolar<<<grid, 256, 0, st>>>(spatial + (size_t)N * N * p0, active ? active + p0 : nullptr, np, N, nr,
                                          neta, rmin, rmax, out + (size_t)nr * neta * p0);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
