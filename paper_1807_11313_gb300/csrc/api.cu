@@ -1775,15 +1775,15 @@ int xcf_index_learned(xcf_ctx *ctx, xcf_net *net, const xcf_library *lib, const 
         const float *pat = patterns + img * p0;
         const double *pc = pcs ? pcs + 3 * (size_t)p0 : nullptr;
         double *q = quats + 4 * (size_t)p0;
-        double *prop, *qh, *seeds;
+        double *prop, *qh;
         float2 *sp, *stt;
         float *img_t, *peak_h, *shift, *best_peak;
-        int *degen, *best, *count;
+        int *degen, *count;
         if ((rc = scratch_t(ctx, S_PROP, (size_t)np * k * 4, &prop)) || (rc = scratch_t(ctx, S_QH, (size_t)np * 4, &qh)) ||
             (rc = scratch_t(ctx, S_SPEC_P, (size_t)np * H, &sp)) || (rc = scratch_t(ctx, S_SPEC_T, (size_t)np * H, &stt)) ||
             (rc = scratch_t(ctx, S_IMG, (size_t)np * n * n, &img_t)) || (rc = scratch_t(ctx, S_PEAK, np, &peak_h)) ||
             (rc = scratch_t(ctx, S_SHIFT, (size_t)np * 2, &shift)) || (rc = scratch_t(ctx, S_BESTPEAK, np, &best_peak)) ||
-            (rc = scratch_t(ctx, S_DEGEN, np, &degen)) || (rc = scratch_t(ctx, S_FBCOUNT, 1, &count)))
+            (rc = scratch_t(ctx, S_DEGEN, np, &degen)) || (rc = scratch_t(ctx, S_FBCOUNT, 2, &count)))
             return rc;
         // 1. proposals
         if ((rc = propose_all(ctx, net, offset_input(in, p0), np, prop, st))) return rc;
@@ -1802,19 +1802,43 @@ int xcf_index_learned(xcf_ctx *ctx, xcf_net *net, const xcf_library *lib, const 
         if ((rc = refine_chunk(ctx, lib, pat, np, q, pc, q, peak + p0, iters + p0, st))) return rc;
         // 4. fallback where the refined peak stays below tau
         if ((rc = scratch_t(ctx, S_DEGEN, np, &degen))) return rc;   // the refinement's pattern flags
-        XCF_CHECK(cudaMemsetAsync(count, 0, sizeof(int), st), "count");
+        int *fidx, *flag_c;
+        if ((rc = scratch_t(ctx, S_FB_IDX, (size_t)np + 1, &fidx)) ||
+            (rc = scratch_t(ctx, S_FB_FLAG, (size_t)np + 1, &flag_c)))
+            return rc;
+        XCF_CHECK(cudaMemsetAsync(count, 0, 2 * sizeof(int), st), "count");
         XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_fallback_flags(peak + p0, degen, np, tau, fallback + p0, count, st),
                    "fallback flags");
-        int n_fb = 0;
-        XCF_CHECK(cudaMemcpyAsync(&n_fb, count, sizeof(int), cudaMemcpyDeviceToHost, st), "count");
+        XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_fallback_list(fallback + p0, np, fidx, flag_c, count + 1, st),
+                   "fallback list");
+        int counts[2] = {0, 0};
+        XCF_CHECK(cudaMemcpyAsync(counts, count, 2 * sizeof(int), cudaMemcpyDeviceToHost, st), "count");
         XCF_CHECK(cudaStreamSynchronize(st), "count");
-        if (n_fb == 0) continue;
-        if ((rc = scratch_t(ctx, S_BEST, np, &best)) || (rc = scratch_t(ctx, S_SEEDS, (size_t)np * 4, &seeds)))
+        if (counts[0] == 0) continue;
+        // the flagged patterns gathered (by pattern pairs) into a batch of their
+        // own: the full search then spreads the library over the SMs for them
+        // alone, and the refinement runs on them alone
+        const int nc = 2 * counts[1];
+        int *best_c, *it_c;
+        float *pat_c, *pk_c;
+        double *pc_c = nullptr, *q_c;
+        if ((rc = scratch_t(ctx, S_FB_PAT, (size_t)nc * img, &pat_c)) || (rc = scratch_t(ctx, S_FB_BEST, nc, &best_c)) ||
+            (rc = scratch_t(ctx, S_FB_IT, nc, &it_c)) || (rc = scratch_t(ctx, S_FB_PEAK, (size_t)nc * 4, &pk_c)) ||
+            (rc = scratch_t(ctx, S_FB_Q, (size_t)nc * 8, &q_c)) ||
+            (pc && (rc = scratch_t(ctx, S_FB_PC, (size_t)nc * 3, &pc_c))))
             return rc;
-        if ((rc = index_chunk(ctx, lib, pat, np, best, best_peak, shift, nullptr, st, fallback + p0))) return rc;
-        XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_fallback_seeds(fallback + p0, best, lib->quats, q, np, seeds, st),
+        double *seeds_c = q_c + 4 * (size_t)nc;
+        XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_gather_rows(pat, img, fidx, nc, pat_c, st), "gather patterns");
+        if (pc) XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_gather_rows(pc, 3, fidx, nc, pc_c, st), "gather pcs");
+        if ((rc = index_chunk(ctx, lib, pat_c, nc, best_c, pk_c + nc, pk_c + 2 * (size_t)nc, nullptr, st, flag_c)))
+            return rc;
+        XCF_LAUNCH(XCF_STAGE_OTHER, st,
+                   launch_fallback_seeds_list(fidx, flag_c, best_c, lib->quats, q, nc, seeds_c, st),
                    "fallback seeds");
-        if ((rc = refine_chunk(ctx, lib, pat, np, seeds, pc, q, peak + p0, iters + p0, st, fallback + p0))) return rc;
+        if ((rc = refine_chunk(ctx, lib, pat_c, nc, seeds_c, pc_c, q_c, pk_c, it_c, st, flag_c))) return rc;
+        XCF_LAUNCH(XCF_STAGE_OTHER, st,
+                   launch_fallback_scatter(fidx, flag_c, nc, q_c, pk_c, it_c, q, peak + p0, iters + p0, st),
+                   "fallback results");
     }
     return XCF_OK;
 }

@@ -42,7 +42,15 @@ enum Slot {
     S_QH,           // one proposal per pattern [P, 4]
     S_BESTPEAK,     // best proposal peak [P]
     S_MASK,         // search mask of the fallback pass
-    S_FBCOUNT,      // number of fallback patterns (device int)
+    S_FBCOUNT,      // fallback patterns and fallback pattern pairs (two device ints)
+    S_FB_IDX,       // fallback pass: the batch's pattern indices (by pairs)
+    S_FB_FLAG,      // fallback pass: which of them are flagged
+    S_FB_PAT,       // fallback pass: their images
+    S_FB_PC,        // fallback pass: their pattern centres
+    S_FB_BEST,      // fallback pass: their best templates
+    S_FB_PEAK,      // fallback pass: refined peak, best peak, shift (x, y) per pattern
+    S_FB_Q,         // fallback pass: refined orientations, then seeds
+    S_FB_IT,        // fallback pass: iteration counts
     S_CAND,         // screen candidates of a chunk [P, k]
     S_CANDSC,       // their screen scores
     S_ARGMAX,       // integer peak positions for the up-sampled peak

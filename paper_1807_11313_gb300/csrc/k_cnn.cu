@@ -649,6 +649,72 @@ __global__ void k_fallback_seeds(const int *__restrict__ fb, const int *__restri
     for (int i = 0; i < 4; ++i) seeds[4 * p + i] = use ? lib_q[4L * best[p] + i] : cur[4 * p + i];
 }
 
+// the fallback batch by pattern pairs (one block of 1024 threads): every
+// pair (2j, 2j + 1) with a flagged member, in order, at (2i, 2i + 1), so that
+// each pattern keeps the partner it shares a complex inverse transform with
+// in the pair-peak kernels; flag_c marks the flagged members (a last pair
+// without a second pattern repeats the first, unflagged); pairs[0] = count
+__global__ void __launch_bounds__(1024) k_fallback_list(const int *__restrict__ fb, int P, int *__restrict__ idx,
+                                                        int *__restrict__ flag_c, int *__restrict__ pairs) {
+    __shared__ int sums[1024];
+    const int U = (P + 1) / 2;
+    const int t = threadIdx.x, per = (U + 1023) / 1024, b = t * per, e = min(U, b + per);
+    auto flagged = [&](int j) { return fb[2 * j] != 0 || (2 * j + 1 < P && fb[2 * j + 1] != 0); };
+    int c = 0;
+    for (int j = b; j < e; ++j) c += flagged(j) ? 1 : 0;
+    sums[t] = c;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {   // inclusive scan of the counts
+        const int v = t >= o ? sums[t - o] : 0;
+        __syncthreads();
+        sums[t] += v;
+        __syncthreads();
+    }
+    int pos = sums[t] - c;
+    for (int j = b; j < e; ++j) {
+        if (!flagged(j)) continue;
+        const bool two = 2 * j + 1 < P;
+        idx[2 * pos] = 2 * j;
+        flag_c[2 * pos] = fb[2 * j] != 0;
+        idx[2 * pos + 1] = two ? 2 * j + 1 : 2 * j;
+        flag_c[2 * pos + 1] = two && fb[2 * j + 1] != 0;
+        ++pos;
+    }
+    if (t == 1023) pairs[0] = sums[1023];
+}
+// row i of dst = row idx[i] of src (rows of len elements)
+template <class T>
+__global__ void k_gather_rows(const T *__restrict__ src, size_t len, const int *__restrict__ idx, int n,
+                              T *__restrict__ dst) {
+    const size_t total = (size_t)n * len;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = i / len;
+        dst[i] = src[(size_t)idx[r] * len + (i - r * len)];
+    }
+}
+// seeds of the listed patterns: for flagged ones the library orientation of
+// the best template, else (and where there is none) the current orientation
+__global__ void k_fallback_seeds_list(const int *__restrict__ idx, const int *__restrict__ flag_c,
+                                      const int *__restrict__ best, const double *__restrict__ lib_q,
+                                      const double *__restrict__ cur, int n, double *__restrict__ seeds) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *src = flag_c[i] && best[i] >= 0 ? lib_q + 4L * best[i] : cur + 4L * idx[i];
+    for (int k = 0; k < 4; ++k) seeds[4 * i + k] = src[k];
+}
+// the flagged patterns' results back to their own slots
+__global__ void k_fallback_scatter(const int *__restrict__ idx, const int *__restrict__ flag_c, int n,
+                                   const double *__restrict__ q_c, const float *__restrict__ peak_c,
+                                   const int *__restrict__ it_c, double *__restrict__ q, float *__restrict__ peak,
+                                   int *__restrict__ iters) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !flag_c[i]) return;
+    const int p = idx[i];
+    for (int k = 0; k < 4; ++k) q[4L * p + k] = q_c[4 * i + k];
+    peak[p] = peak_c[i];
+    iters[p] = it_c[i];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- host side
@@ -938,6 +1004,41 @@ cudaError_t launch_fallback_flags(const float *peak, const int *degen, int P, fl
 cudaError_t launch_fallback_mask(const int *degen, const int *fb, int P, int *mask, cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
     k_fallback_mask<<<(P + 255) / 256, 256, 0, st>>>(degen, fb, P, mask);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fallback_list(const int *fb, int P, int *idx, int *flag_c, int *pairs, cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    k_fallback_list<<<1, 1024, 0, st>>>(fb, P, idx, flag_c, pairs);
+    return cudaGetLastError();
+}
+
+template <class T>
+static cudaError_t gather_rows(const T *src, size_t len, const int *idx, int n, T *dst, cudaStream_t st) {
+    if (n <= 0 || len == 0) return cudaSuccess;
+    const size_t total = (size_t)n * len;
+    const int blocks = (int)((total + 255) / 256 < 65536 ? (total + 255) / 256 : 65536);
+    k_gather_rows<T><<<blocks, 256, 0, st>>>(src, len, idx, n, dst);
+    return cudaGetLastError();
+}
+cudaError_t launch_gather_rows(const float *src, size_t len, const int *idx, int n, float *dst, cudaStream_t st) {
+    return gather_rows(src, len, idx, n, dst, st);
+}
+cudaError_t launch_gather_rows(const double *src, size_t len, const int *idx, int n, double *dst, cudaStream_t st) {
+    return gather_rows(src, len, idx, n, dst, st);
+}
+
+cudaError_t launch_fallback_seeds_list(const int *idx, const int *flag_c, const int *best, const double *lib_q,
+                                       const double *cur, int n, double *seeds, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_fallback_seeds_list<<<(n + 255) / 256, 256, 0, st>>>(idx, flag_c, best, lib_q, cur, n, seeds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fallback_scatter(const int *idx, const int *flag_c, int n, const double *q_c, const float *peak_c,
+                                    const int *it_c, double *q, float *peak, int *iters, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_fallback_scatter<<<(n + 255) / 256, 256, 0, st>>>(idx, flag_c, n, q_c, peak_c, it_c, q, peak, iters);
     return cudaGetLastError();
 }
 

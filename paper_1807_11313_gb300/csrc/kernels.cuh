@@ -233,6 +233,18 @@ cudaError_t launch_keep_best(const float *peak_h, const double *q_h, int P, int 
 cudaError_t launch_fallback_flags(const float *peak, const int *degen, int P, float tau, int *fb, int *count,
                                   cudaStream_t st);
 cudaError_t launch_fallback_mask(const int *degen, const int *fb, int P, int *mask, cudaStream_t st);
+// the fallback pass on the flagged patterns, gathered by pattern pairs (each
+// keeps its pair-peak partner): the ordered pair list (P <= 2 x 1024 x 1024;
+// idx and flag_c of 2 x pairs entries, pairs[0] = count), row gathers, seeds
+// (library orientation of the best template for flagged patterns, else the
+// current one) and the flagged patterns' results scattered back
+cudaError_t launch_fallback_list(const int *fb, int P, int *idx, int *flag_c, int *pairs, cudaStream_t st);
+cudaError_t launch_gather_rows(const float *src, size_t len, const int *idx, int n, float *dst, cudaStream_t st);
+cudaError_t launch_gather_rows(const double *src, size_t len, const int *idx, int n, double *dst, cudaStream_t st);
+cudaError_t launch_fallback_seeds_list(const int *idx, const int *flag_c, const int *best, const double *lib_q,
+                                       const double *cur, int n, double *seeds, cudaStream_t st);
+cudaError_t launch_fallback_scatter(const int *idx, const int *flag_c, int n, const double *q_c, const float *peak_c,
+                                    const int *it_c, double *q, float *peak, int *iters, cudaStream_t st);
 cudaError_t launch_fallback_seeds(const int *fb, const int *best, const double *lib_q, const double *cur, int P,
                                   double *seeds, cudaStream_t st);
 
