@@ -67,7 +67,17 @@ __global__ void __launch_bounds__(PT) k_prep_real(const float *__restrict__ img,
     float2 *c0 = twHi + N / 4;                             // S[u][0],   u < N
     float2 *cH = c0 + N;                                   // S[u][N/2], u < N
     __shared__ double red[33];
+    // per-index tables: the Hann window, and the band-pass as a product of
+    // per-frequency factors (e(f) = expm1(-f^2 / 2 s_h^2), b(f) = exp(-f^2 / 2 s_l^2):
+    // 1 - exp(-(x_u + x_v)) = -(e_u + e_v + e_u e_v), free of cancellation near DC)
+    __shared__ float win[N], fe[N / 2 + 1], fb[N / 2 + 1];
     const int p = blockIdx.x, tid = threadIdx.x;
+    for (int i = tid; i < N; i += PT) win[i] = a.window ? 0.5f * (1.f - cospif(2.f * i / N)) : 1.f;
+    for (int i = tid; i <= N / 2; i += PT) {
+        const float f2 = (float)(i * i);
+        fe[i] = expm1f(-f2 * a.inv2shp);
+        fb[i] = expf(-f2 * a.inv2slp);
+    }
     const float *src = img + (size_t)p * a.W * a.H;
     float2 *out = spec + (size_t)p * N * HW;
     make_twiddles<N>(twN, -1);
@@ -107,9 +117,7 @@ __global__ void __launch_bounds__(PT) k_prep_real(const float *__restrict__ img,
         const float m = (float)mean, inv = (float)(1.0 / sd);
         for (int idx = tid; idx < H * N; idx += PT) {
             const int pr = idx / N, c = idx % N;
-            const float wc = (a.window ? 0.5f * (1.f - cospif(2.f * c / N)) : 1.f) * inv;
-            const float w0 = a.window ? 0.5f * (1.f - cospif(2.f * (2 * pr) / N)) : 1.f;
-            const float w1 = a.window ? 0.5f * (1.f - cospif(2.f * (2 * pr + 1) / N)) : 1.f;
+            const float wc = win[c] * inv, w0 = win[2 * pr], w1 = win[2 * pr + 1];
             const float2 z = buf[pr * LD + c];
             buf[pr * LD + c] = make_float2((z.x - m) * wc * w0, (z.y - m) * wc * w1);
         }
@@ -179,9 +187,9 @@ __global__ void __launch_bounds__(PT) k_prep_real(const float *__restrict__ img,
         for (int it = tid; it < N * HW; it += PT) {
             const int u = it / HW, v = it % HW;
             float2 *x = v == 0 ? c0 + u : (v == N / 2 ? cH + u : buf + (u & (H - 1)) * LD + (u >= H ? N / 2 : 0) + v);
-            const float fu = (float)(u < N / 2 ? u : u - N), fv = (float)(v < N / 2 ? v : v - N);
-            const float rho2 = fu * fu + fv * fv;
-            const float h = -expm1f(-rho2 * a.inv2shp) * expf(-rho2 * a.inv2slp);
+            const int iu = u <= N / 2 ? u : N - u;   // |f_u|; |f_v| = v (v <= N/2)
+            const float eu = fe[iu], ev = fe[v];
+            const float h = -(eu + ev + eu * ev) * (fb[iu] * fb[v]);
             const float2 X = make_float2(x->x * h, x->y * h);
             *x = X;
             e = fmaf(v == 0 || v == N / 2 ? 1.f : 2.f, X.x * X.x + X.y * X.y, e);
