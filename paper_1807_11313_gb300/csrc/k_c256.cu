@@ -706,6 +706,15 @@ __device__ __forceinline__ double cluster_sum(double part, double *slot, uint32_
     return s;
 }
 __device__ __forceinline__ int st_index(int u, int vl) { return u * 32 + (vl ^ (u & 31)); }
+// cos and sin of 2 pi n / 16
+__device__ constexpr float kW16c[16] = {Tw<0, 16, 1>::re,  Tw<1, 16, 1>::re,  Tw<2, 16, 1>::re,  Tw<3, 16, 1>::re,
+                                        Tw<4, 16, 1>::re,  Tw<5, 16, 1>::re,  Tw<6, 16, 1>::re,  Tw<7, 16, 1>::re,
+                                        Tw<8, 16, 1>::re,  Tw<9, 16, 1>::re,  Tw<10, 16, 1>::re, Tw<11, 16, 1>::re,
+                                        Tw<12, 16, 1>::re, Tw<13, 16, 1>::re, Tw<14, 16, 1>::re, Tw<15, 16, 1>::re};
+__device__ constexpr float kW16s[16] = {Tw<0, 16, 1>::im,  Tw<1, 16, 1>::im,  Tw<2, 16, 1>::im,  Tw<3, 16, 1>::im,
+                                        Tw<4, 16, 1>::im,  Tw<5, 16, 1>::im,  Tw<6, 16, 1>::im,  Tw<7, 16, 1>::im,
+                                        Tw<8, 16, 1>::im,  Tw<9, 16, 1>::im,  Tw<10, 16, 1>::im, Tw<11, 16, 1>::im,
+                                        Tw<12, 16, 1>::im, Tw<13, 16, 1>::im, Tw<14, 16, 1>::im, Tw<15, 16, 1>::im};
 
 __global__ void __launch_bounds__(NT, 1)
 k_prep_c256(const float *__restrict__ img, int P, PrepArgs a, float2 *__restrict__ spec, float *__restrict__ spatial,
@@ -802,7 +811,9 @@ k_prep_c256(const float *__restrict__ img, int P, PrepArgs a, float2 *__restrict
 #pragma unroll
                 for (int n1 = 0; n1 < 16; ++n1) {
                     const int x = 16 * n1 + t;
-                    const float wx = (a.window ? 0.5f * (1.f - cospif(2.f * x / N)) : 1.f) * inv;
+                    // cos(2 pi x / 256) = Re(W16^n1 e^{2 pi i t / 256}), the latter in tw[1]
+                    const float cx = kW16c[n1] * tw[1].x - kW16s[n1] * tw[1].y;
+                    const float wx = (a.window ? 0.5f * (1.f - cx) : 1.f) * inv;
                     z[n1] = make_float2((Xr[ra * N + x] - m) * wx * wa, (Xr[rb * N + x] - m) * wx * wb);
                 }
                 line_fft<-1>(z, tw, scr, t);
@@ -826,6 +837,17 @@ k_prep_c256(const float *__restrict__ img, int P, PrepArgs a, float2 *__restrict
         if (!bad) {
             // ---- columns: gather, transform, filter; keep in Stage / Col128
             const int nq = (c == NC - 1 && g == 0) ? 3 : 2;
+            // the band-pass as per-frequency factors, e = expm1(-f^2 / 2 s_h^2),
+            // b = exp(-f^2 / 2 s_l^2): h = -(e_u + e_v + e_u e_v) b_u b_v; the
+            // lane's 16 row factors once per image
+            float eu[16], bu[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int u = t + 16 * cx_bitrev(k, 4);
+                const float fu = (float)(u < N / 2 ? u : u - N), f2 = fu * fu;
+                eu[k] = expm1f(-f2 * a.inv2shp);
+                bu[k] = expf(-f2 * a.inv2slp);
+            }
 #pragma unroll 1
             for (int q = 0; q < nq; ++q) {
                 const int v = q < 2 ? 32 * c + 2 * g + q : 128;
@@ -833,14 +855,13 @@ k_prep_c256(const float *__restrict__ img, int P, PrepArgs a, float2 *__restrict
 #pragma unroll
                 for (int n1 = 0; n1 < 16; ++n1) z[n1] = ld_cluster(rrow[n1] + (uint32_t)(v * sizeof(float2)));
                 line_fft<-1>(z, tw, scr, t);
-                const float fv = (float)(v < N / 2 ? v : v - N);
+                const float fv = (float)(v < N / 2 ? v : v - N), fv2 = fv * fv;
+                const float ev = expm1f(-fv2 * a.inv2shp), bv = expf(-fv2 * a.inv2slp);
                 const float wv = (v == 0 || v == N / 2) ? 1.f : 2.f;
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const int u = t + 16 * cx_bitrev(k, 4);
-                    const float fu = (float)(u < N / 2 ? u : u - N);
-                    const float rho2 = fu * fu + fv * fv;
-                    const float h = -expm1f(-rho2 * a.inv2shp) * expf(-rho2 * a.inv2slp);
+                    const float h = -(eu[k] + ev + eu[k] * ev) * (bu[k] * bv);
                     const float2 X = make_float2(z[k].x * h, z[k].y * h);
                     e = fmaf(wv, X.x * X.x + X.y * X.y, e);
                     if (q < 2) Stage[st_index(u, v - 32 * c)] = X;
