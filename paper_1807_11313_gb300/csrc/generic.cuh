@@ -147,21 +147,14 @@ __device__ __forceinline__ void build_pair_spectrum(float2 *buf, const float2 *_
                                                     const float2 *__restrict__ t2,
                                                     const float2 *__restrict__ sp, int t0, int nt) {
     constexpr int LD = N + 1, HW = N / 2 + 1;
-    for (int idx = t0; idx < N * N; idx += nt) {
-        int r = idx / N, c = idx % N;
-        float2 Z;
-        if (c <= N / 2) {
-            int k = r * HW + c;
-            float2 s = sp[k];
-            float2 x1 = c_mulcj(t1[k], s), x2 = c_mulcj(t2[k], s);
-            Z = make_float2(x1.x - x2.y, x1.y + x2.x);
-        } else {
-            int k = ((N - r) % N) * HW + (N - c);
-            float2 s = sp[k];
-            float2 x1 = c_mulcj(t1[k], s), x2 = c_mulcj(t2[k], s);
-            Z = make_float2(x1.x + x2.y, -x1.y + x2.x);
-        }
-        buf[r * LD + c] = Z;
+    // each stored value (u, v <= N/2) gives Z(u, v) = X1 + i X2 and, for
+    // 0 < v < N/2, Z(-u, -v) = conj X1 + i conj X2
+    for (int k = t0; k < N * HW; k += nt) {
+        const int u = k / HW, v = k - u * HW;
+        const float2 s = sp[k];
+        const float2 x1 = c_mulcj(t1[k], s), x2 = c_mulcj(t2[k], s);
+        buf[u * LD + v] = make_float2(x1.x - x2.y, x1.y + x2.x);
+        if (v > 0 && v < N / 2) buf[(u == 0 ? 0 : N - u) * LD + (N - v)] = make_float2(x1.x + x2.y, -x1.y + x2.x);
     }
 }
 

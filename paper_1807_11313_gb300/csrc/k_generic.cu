@@ -510,14 +510,15 @@ __global__ void __launch_bounds__(QT) k_pair_peak(const float2 *__restrict__ St,
     const float2 *qa = Sp + (size_t)(mode[0] == 2 ? pp[0] : 0) * N * HW;
     const float2 *qb = Sp + (size_t)(mode[1] == 2 ? pp[1] : 0) * N * HW;
     const float fa = mode[0] == 2 ? 1.f : 0.f, fb = mode[1] == 2 ? 1.f : 0.f;
-    for (int idx = tid; idx < N * N; idx += QT) {
-        const int r = idx / N, c = idx % N;
-        const bool direct = c <= N / 2;
-        const int k = direct ? r * HW + c : ((N - r) % N) * HW + (N - c);   // conj(X(-u, -v)) above N/2
+    // each stored value (u, v <= N/2) gives Z(u, v) = X1 + i X2 and, for 0 < v < N/2,
+    // Z(-u, -v) = conj X1 + i conj X2 (Hermitian symmetry of both surfaces)
+    for (int k = tid; k < N * HW; k += QT) {
+        const int u = k / HW, v = k - u * HW;
         float2 x1 = c_mulcj(ta[k], qa[k]), x2 = c_mulcj(tb[k], qb[k]);
         x1 = make_float2(x1.x * fa, x1.y * fa);
         x2 = make_float2(x2.x * fb, x2.y * fb);
-        buf[r * LD + c] = direct ? make_float2(x1.x - x2.y, x1.y + x2.x) : make_float2(x1.x + x2.y, -x1.y + x2.x);
+        buf[u * LD + v] = make_float2(x1.x - x2.y, x1.y + x2.x);
+        if (v > 0 && v < N / 2) buf[(u == 0 ? 0 : N - u) * LD + (N - v)] = make_float2(x1.x + x2.y, -x1.y + x2.x);
     }
     __syncthreads();
     fft2_smem<N>(buf, twi);
