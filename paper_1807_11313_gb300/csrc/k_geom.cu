@@ -121,7 +121,7 @@ __device__ __forceinline__ float parabola(float cm, float c0, float cp) {
 // each warp transforms radii m = warp, warp + 8, ... as one complex line
 // z = a_m + i b_m, splits A_m and B_m by Hermitian symmetry and accumulates
 // C[k] = sum_m conj(A_m[k]) B_m[k] (k <= neta/2) in registers; the warps'
-// sums are added in float64 and one inverse transform of the Hermitian C
+// eight sums are added and one inverse transform of the Hermitian C
 // gives c(D) for every shift.  neta log neta work per radius instead of neta^2.
 constexpr int kEtaThreads = 256, kEtaWarps = kEtaThreads / 32, kMaxLpWindows = 16;
 
@@ -206,10 +206,10 @@ __global__ void __launch_bounds__(kEtaThreads, NETA >= 512 ? 2 : 3) k_eta_update
         // The correlation's scale does not move its argmax or parabolic offset, so it is not normalised.
         if (w == 0) {
             for (int k = lane; k < H; k += 32) {
-                double cr = 0, ci = 0;
+                float cr = 0.f, ci = 0.f;   // eight FP32 partials (FP64 here kept GB300's narrow FP64 pipe busy)
                 for (int v = 0; v < kEtaWarps; ++v) { cr += line[v][k].x; ci += line[v][k].y; }
-                zc[k] = make_float2((float)cr, (float)ci);
-                if (k > 0 && k < NETA / 2) zc[NETA - k] = make_float2((float)cr, (float)-ci);
+                zc[k] = make_float2(cr, ci);
+                if (k > 0 && k < NETA / 2) zc[NETA - k] = make_float2(cr, -ci);
             }
             __syncwarp();
             if constexpr (kRegLine) {
