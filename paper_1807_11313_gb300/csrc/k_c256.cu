@@ -71,6 +71,16 @@ __device__ __forceinline__ float ld_cluster_f(uint32_t addr) {
     return v;
 }
 
+// cos and sin of 2 pi n / 16
+__device__ constexpr float kW16c[16] = {Tw<0, 16, 1>::re,  Tw<1, 16, 1>::re,  Tw<2, 16, 1>::re,  Tw<3, 16, 1>::re,
+                                        Tw<4, 16, 1>::re,  Tw<5, 16, 1>::re,  Tw<6, 16, 1>::re,  Tw<7, 16, 1>::re,
+                                        Tw<8, 16, 1>::re,  Tw<9, 16, 1>::re,  Tw<10, 16, 1>::re, Tw<11, 16, 1>::re,
+                                        Tw<12, 16, 1>::re, Tw<13, 16, 1>::re, Tw<14, 16, 1>::re, Tw<15, 16, 1>::re};
+__device__ constexpr float kW16s[16] = {Tw<0, 16, 1>::im,  Tw<1, 16, 1>::im,  Tw<2, 16, 1>::im,  Tw<3, 16, 1>::im,
+                                        Tw<4, 16, 1>::im,  Tw<5, 16, 1>::im,  Tw<6, 16, 1>::im,  Tw<7, 16, 1>::im,
+                                        Tw<8, 16, 1>::im,  Tw<9, 16, 1>::im,  Tw<10, 16, 1>::im, Tw<11, 16, 1>::im,
+                                        Tw<12, 16, 1>::im, Tw<13, 16, 1>::im, Tw<14, 16, 1>::im, Tw<15, 16, 1>::im};
+
 // home of row u: owner CTA and slot.  Row classes {u, 256 - u}; class b (the
 // smaller member, classes 0 and 128 merged into one pair {0, 128}) goes to
 // CTA b / 32, slot 2 (b mod 32) for the member below 128, +1 for the other.
@@ -185,7 +195,7 @@ namespace cw {
 constexpr int NT = 512, NG = NT / 16;
 constexpr size_t ZC_F2 = (size_t)ROWS * N;         // 128 KB of row-transformed data
 constexpr size_t SCR_F2 = (size_t)NG * 256;        // one 16 x 16 transpose buffer per group
-constexpr size_t TW_F2 = 512;                      // [k1][l]: e^{+2 pi i l k1 / 256}, then e^{+2 pi i (16 - l) k1 / 256}
+constexpr size_t TW_F2 = 256;                      // [k1][l]: e^{+2 pi i l k1 / 256}
 constexpr size_t SMEM_BYTES = (ZC_F2 + SCR_F2 + TW_F2) * sizeof(float2) + 64 * sizeof(float);
 
 // search layout of a template's half spectrum: row u, piece (j < 4, group
@@ -325,7 +335,7 @@ k_search_c256w(const float2 *__restrict__ St, int T, const float2 *__restrict__ 
     extern __shared__ float4 smem_raw[];
     float2 *Zc = reinterpret_cast<float2 *>(smem_raw);
     float2 *scr_all = Zc + cw::ZC_F2;
-    float2 *twa = scr_all + cw::SCR_F2, *twb = twa + 256;
+    float2 *twa = scr_all + cw::SCR_F2;
     float *red = reinterpret_cast<float *>(twa + TW_F2);   // [0..15] warp maxima, [32..33] CTA maxima
     const int tid = threadIdx.x, l = tid & 15, g = tid >> 4, warp = tid >> 5, lane = tid & 31;
     const int c = (int)cluster_rank();
@@ -335,10 +345,10 @@ k_search_c256w(const float2 *__restrict__ St, int T, const float2 *__restrict__ 
     bool pending = false;   // a column-phase barrier arrived on but not yet waited for
     const int npairs = (n + 1) / 2;
 
-    for (int i = tid; i < 512; i += cw::NT) {   // twa[k1][l], twb[k1][l]
-        const int ll = i & 15, k1 = (i >> 4) & 15;
+    for (int i = tid; i < 256; i += cw::NT) {   // twa[k1][l]
+        const int ll = i & 15, k1 = i >> 4;
         double s, co;
-        sincospi(2.0 * (i < 256 ? ll : 16 - ll) * k1 / N, &s, &co);
+        sincospi(2.0 * ll * k1 / N, &s, &co);
         twa[i] = make_float2((float)co, (float)s);
     }
     // row phase: this group's two rows, their slots; lane l's second row starts at column sg
@@ -352,7 +362,7 @@ k_search_c256w(const float2 *__restrict__ St, int T, const float2 *__restrict__ 
     const uint32_t cbase = map_to_rank(zc_local, (uint32_t)(hm >> 2)) +
                            (uint32_t)((16 * io * N + ((ROWS * c + 2 * g) ^ (4 * io))) * sizeof(float2));
     const uint32_t red_local = (uint32_t)__cvta_generic_to_shared(red);
-    __syncthreads();   // twa, twb
+    __syncthreads();   // twa
 
     auto pair_templates = [&](int it, int pi, int &t1, int &t2) {
         const int p = it / nchunks;
@@ -414,8 +424,16 @@ k_search_c256w(const float2 *__restrict__ St, int T, const float2 *__restrict__ 
                     build_half<true>(s1, s2, sp, ub, l, b, a);
                     build_half<true>(s1, s2, sp, ub, sg, a, b);
                 }
-                const float2 *twr = singles ? twa : twb;
-                ifft256_pass1(b, [&](int k1) { return twr[k1 * 16 + l]; }, singles ? l : ng, scr, l);
+                // the second row's twiddle e^{+2 pi i (16 - l) k1 / 256} = W16^k1 conj(e^{+2 pi i l k1 / 256})
+                // (the singles' row 128 sits at columns l + 16 m: the plain twiddle)
+                ifft256_pass1(
+                    b,
+                    [&](int k1) {
+                        const float2 w = twa[k1 * 16 + l];
+                        const float2 c = singles ? make_float2(1.f, 0.f) : make_float2(kW16c[k1], kW16s[k1]);
+                        return c_mul(c, make_float2(w.x, singles ? w.y : -w.y));
+                    },
+                    singles ? l : ng, scr, l);
                 dif16<0, 4, +1>(b);
 #pragma unroll
                 for (int q = 0; q < 16; ++q) Zc[zc_at(sb, l + 16 * cx_bitrev(q, 4))] = b[q];
@@ -706,15 +724,7 @@ __device__ __forceinline__ double cluster_sum(double part, double *slot, uint32_
     return s;
 }
 __device__ __forceinline__ int st_index(int u, int vl) { return u * 32 + (vl ^ (u & 31)); }
-// cos and sin of 2 pi n / 16
-__device__ constexpr float kW16c[16] = {Tw<0, 16, 1>::re,  Tw<1, 16, 1>::re,  Tw<2, 16, 1>::re,  Tw<3, 16, 1>::re,
-                                        Tw<4, 16, 1>::re,  Tw<5, 16, 1>::re,  Tw<6, 16, 1>::re,  Tw<7, 16, 1>::re,
-                                        Tw<8, 16, 1>::re,  Tw<9, 16, 1>::re,  Tw<10, 16, 1>::re, Tw<11, 16, 1>::re,
-                                        Tw<12, 16, 1>::re, Tw<13, 16, 1>::re, Tw<14, 16, 1>::re, Tw<15, 16, 1>::re};
-__device__ constexpr float kW16s[16] = {Tw<0, 16, 1>::im,  Tw<1, 16, 1>::im,  Tw<2, 16, 1>::im,  Tw<3, 16, 1>::im,
-                                        Tw<4, 16, 1>::im,  Tw<5, 16, 1>::im,  Tw<6, 16, 1>::im,  Tw<7, 16, 1>::im,
-                                        Tw<8, 16, 1>::im,  Tw<9, 16, 1>::im,  Tw<10, 16, 1>::im, Tw<11, 16, 1>::im,
-                                        Tw<12, 16, 1>::im, Tw<13, 16, 1>::im, Tw<14, 16, 1>::im, Tw<15, 16, 1>::im};
+
 
 __global__ void __launch_bounds__(NT, 1)
 k_prep_c256(const float *__restrict__ img, int P, PrepArgs a, float2 *__restrict__ spec, float *__restrict__ spatial,
