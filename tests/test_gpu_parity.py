@@ -214,6 +214,23 @@ def test_build_library_matches_oracle_spectra(px, ctx, orc):
     lib.close()
 
 
+@pytest.mark.parametrize("n,W,H", [(64, 64, 64), (128, 150, 140), (256, 256, 256)])
+def test_library_projection_inside_prep_equals_two_kernels(px, ctx, n, W, H):
+    """The library build projects its templates inside the pre-processing
+    kernel (sides up to 128) or with the projection kernel first (256): the
+    spectra are bit-identical to xcf_project followed by xcf_prep, including
+    on a detector larger than its crop."""
+    master = synth.master_pattern("bcc", 512)
+    lq = synth.random_quaternions(5, 9)
+    g = px.geometry(W, H, PC0)
+    assert px.xcf_crop(g)[0] == n
+    lib = px.xcf_build_library(ctx, dev(master), dev(lq), g)
+    imgs = px.xcf_project(ctx, dev(master), dev(lq), g)
+    spec, _, degen = px.xcf_prep(ctx, imgs, g)
+    assert torch.equal(lib.spectra(), spec) and int(degen.sum()) == 0
+    lib.close()
+
+
 def test_index_chunks_and_empty(px, orc):
     """More patterns than one device pass holds (ragged tail), and P = 0."""
     c = px.Context()
