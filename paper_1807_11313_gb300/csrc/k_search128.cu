@@ -83,10 +83,21 @@ cudaError_t launch_search128(const float2 *Spk, int T, const float2 *Sp, const i
                                          (int)SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int npairs = (T + 1) / 2;
-    // split the library across CTAs only when there are too few patterns to
-    // fill the GPU; each split CTA still covers at least 8 pairs
-    int chunks = (num_sms + P - 1) / P;
-    chunks = max(1, min(chunks, (npairs + 7) / 8));
+    // one CTA per SM at a time: split the library into at most max(4, SMs / P)
+    // parts of at least 8 pairs each, taking the part count c that minimises
+    // waves(P c) x pairs per part (the split does not change the results: the
+    // key is an exact maximum, the lowest template winning ties)
+    const int cap = max(1, min(max(4, (num_sms + P - 1) / P), (npairs + 7) / 8));
+    int chunks = 1;
+    long best_cost = -1;
+    for (int c = 1; c <= cap; ++c) {
+        const long waves = ((long)P * c + num_sms - 1) / num_sms;
+        const long cost = waves * ((npairs + c - 1) / c);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            chunks = c;
+        }
+    }
     int ppc = (npairs + chunks - 1) / chunks;
     chunks = (npairs + ppc - 1) / ppc;
     dim3 grid(chunks, P);
