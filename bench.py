@@ -1018,7 +1018,7 @@ def run_learned(args, px, torch, dev, rank, world, local, dist, emit=True):
         net_peak, bound, kern, basis = fp32_peak, "alu", "proposal network forward (k_gemm, FP32)", "FP32 ALU"
     else:
         net_peak = (pk or {}).get("bf16_tflops_sustained") or 1700.0
-        bound, kern = "tensor", "proposal network forward (convolution 1 k_gemm FP32; 2-5 im2col + k_screen_tc BF16)"
+        bound, kern = "tensor", "proposal network forward (convolution 1 direct FP32 -> BF16; 2-5 k_conv_tc implicit GEMM, tcgen05 BF16)"
         basis = "measured sustained cuBLAS BF16 (MEASURED_PEAKS.json)" if pk else "fallback"
     roofline = {"bound": bound, "achieved": net_flops / (net_ms / 1e3) / 1e12 if net_ms else None, "peak": net_peak,
                 "unit": "TFLOP/s", "kernel": kern, "peak_basis": basis, "traffic": None,

@@ -1568,7 +1568,7 @@ int net_forward_chunk(xcf_ctx *ctx, xcf_net *net, const CnnInput &in, int B, cud
         int *err;
         if ((rc = scratch(ctx, S_NET_BF16, cnn_bf16_work_bytes(B), &work)) || (rc = scratch_t(ctx, S_ERR, 1, &err)))
             return rc;
-        XCF_LAUNCH(XCF_STAGE_NET, st, launch_cnn_forward_bf16(net->params, net->k, in, B, net->act, work, err, &nl, st),
+        XCF_LAUNCH(XCF_STAGE_NET, st, launch_cnn_forward_bf16(net->params, net->k, in, B, net->act, work, err, ctx->num_sms, &nl, st),
                    "net forward (bf16)");
     } else {
         XCF_LAUNCH(XCF_STAGE_NET, st, launch_cnn_forward(net->params, net->k, in, B, net->act, &nl, st),

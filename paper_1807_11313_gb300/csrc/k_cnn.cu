@@ -298,51 +298,21 @@ __global__ void k_cnn_pool(const float *__restrict__ a, int BC, int Q, float *__
     pool[i] = s / Q;
 }
 
-// ---- BF16 inference form: convolutions 2..5 as tensor-core products of a
-// BF16 im2col matrix [rows = B So^2][Kp] and the layer's BF16 weights
-// [Co][Kp] (K = 9 Ci padded with zeros to Kp, a multiple of 64), FP32
-// accumulation into [rows][Co] (NHWC activations), then bias and ReLU.  The
-// first convolution (K = 9) stays an FP32 product and writes NHWC too.
-
-// im2col rows of NHWC input [B][S][S][Ci] (Ci a power of two, >= 8) in the
-// order k = (ky * 3 + kx) Ci + ci: each thread moves 8 consecutive channels
-// of one input pixel (two float4 loads, one 16-byte store of 8 BF16); zeros
-// for k >= 9 Ci.  Eight output positions per CTA.
-constexpr int kIm2colRows = 8;
-__global__ void __launch_bounds__(256) k_cnn_im2col_bf16(const float *__restrict__ x, int Ci, int S, int Kp,
-                                                         long rows, __nv_bfloat16 *__restrict__ out) {
-    const int So = S / 2, lg = __ffs(So) - 1, lc = __ffs(Ci) - 1, K = 9 * Ci, K8 = Kp / 8;
-    for (int rr = 0; rr < kIm2colRows; ++rr) {
-        const long row = (long)blockIdx.x * kIm2colRows + rr;
-        if (row >= rows) return;
-        const int b = (int)(row >> (2 * lg)), p = (int)(row & (So * So - 1)), oy = p >> lg, ox = p & (So - 1);
-        for (int k8 = threadIdx.x; k8 < K8; k8 += blockDim.x) {
-            const int k = 8 * k8;
-            float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
-            if (k < K) {
-                const int r = k >> lc, ci = k & (Ci - 1), ky = r / 3, kx = r - 3 * ky;
-                const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
-                if (iy >= 0 && iy < S && ix >= 0 && ix < S) {
-                    const float4 *src = reinterpret_cast<const float4 *>(x + (((long)b * S + iy) * S + ix) * Ci + ci);
-                    lo = src[0];
-                    hi = src[1];
-                }
-            }
-            __nv_bfloat162 h[4] = {__floats2bfloat162_rn(lo.x, lo.y), __floats2bfloat162_rn(lo.z, lo.w),
-                                   __floats2bfloat162_rn(hi.x, hi.y), __floats2bfloat162_rn(hi.z, hi.w)};
-            *reinterpret_cast<uint4 *>(out + row * Kp + k) = *reinterpret_cast<const uint4 *>(h);
-        }
-    }
-}
+// ---- BF16 inference form: the first convolution (K = 9) stays an FP32
+// product and writes BF16 NHWC activations; convolutions 2..5 run as implicit
+// GEMMs on the tensor cores (k_conv.cu) on BF16 NHWC activations and BF16
+// weights [Co][Kp] (K = 9 Ci in the order (ky * 3 + kx) Ci + ci, padded with
+// zeros to Kp, a multiple of 64), bias and ReLU in their epilogue.
 
 // the first convolution (one input channel, 32 outputs) directly: one thread
 // per output position, the standardised 3 x 3 input window against all 32
 // filters (weights and biases in shared memory), bias, ReLU, NHWC output
+// rounded to BF16 (the second convolution's operand)
 __global__ void __launch_bounds__(256) k_cnn_conv1_nhwc(const float *__restrict__ x, long img_stride,
                                                         long row_stride, int ox0, int oy0,
                                                         const float2 *__restrict__ affine,
                                                         const float *__restrict__ w, const float *__restrict__ bias,
-                                                        int B, float *__restrict__ y) {
+                                                        int B, __nv_bfloat16 *__restrict__ y) {
     constexpr int S = 128, So = 64, Co = 32;
     __shared__ float ws[Co * 9], bs[Co];
     for (int i = threadIdx.x; i < Co * 9; i += blockDim.x) ws[i] = w[i];
@@ -359,19 +329,25 @@ __global__ void __launch_bounds__(256) k_cnn_conv1_nhwc(const float *__restrict_
         const int iy = 2 * oy - 1 + r / 3, ix = 2 * ox - 1 + r % 3;
         v[r] = (iy >= 0 && iy < S && ix >= 0 && ix < S) ? fmaf(img[(long)iy * row_stride + ix], a.x, a.y) : 0.f;
     }
-    float4 *dst = reinterpret_cast<float4 *>(y + n * Co);
+    uint4 *dst = reinterpret_cast<uint4 *>(y + n * Co);
 #pragma unroll
-    for (int c4 = 0; c4 < Co / 4; ++c4) {
-        float o[4];
+    for (int c8 = 0; c8 < Co / 8; ++c8) {
+        uint32_t h[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int c = 4 * c4 + j;
-            float acc = bs[c];
+            float o[2];
 #pragma unroll
-            for (int r = 0; r < 9; ++r) acc = fmaf(ws[c * 9 + r], v[r], acc);
-            o[j] = fmaxf(acc, 0.f);
+            for (int u = 0; u < 2; ++u) {
+                const int c = 8 * c8 + 2 * j + u;
+                float acc = bs[c];
+#pragma unroll
+                for (int r = 0; r < 9; ++r) acc = fmaf(ws[c * 9 + r], v[r], acc);
+                o[u] = fmaxf(acc, 0.f);
+            }
+            const __nv_bfloat162 t = __floats2bfloat162_rn(o[0], o[1]);
+            h[j] = *reinterpret_cast<const uint32_t *>(&t);
         }
-        dst[c4] = make_float4(o[0], o[1], o[2], o[3]);
+        dst[c8] = make_uint4(h[0], h[1], h[2], h[3]);
     }
 }
 
@@ -387,12 +363,6 @@ __global__ void k_cnn_weights_bf16(const float *__restrict__ w, int Co, int Ci, 
         v = w[((long)co * Ci + ci) * 9 + r];
     }
     out[i] = __float2bfloat16_rn(v);
-}
-
-// y[row][c] = relu(y[row][c] + bias[c]), C a power of two
-__global__ void k_cnn_bias_relu_rows(float *__restrict__ y, const float *__restrict__ bias, long n, int C) {
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        y[i] = fmaxf(y[i] + bias[i & (C - 1)], 0.f);
 }
 
 // mean over the Q positions of NHWC activations [B][Q][C]: pool[b][c]
@@ -831,55 +801,33 @@ size_t bf16_weight_elems() {
 }
 }  // namespace
 
-size_t cnn_bf16_work_bytes(int B) {
-    size_t im = 0;
-    int s = 64;
-    for (int l = 1; l < 5; ++l) {
-        const size_t rows = (size_t)B * (s / 2) * (s / 2);
-        im = std::max(im, rows * kBf16Kp[l]);
-        s /= 2;
-    }
-    return 2 * (im + bf16_weight_elems()) + 256;
-}
+size_t cnn_bf16_work_bytes(int) { return 2 * bf16_weight_elems() + 256; }
 
 cudaError_t launch_cnn_forward_bf16(const float *params, int k, const CnnInput &in, int B, float *act, void *work,
-                                    int *err, int *launches, cudaStream_t st) {
+                                    int *err, int num_sms, int *launches, cudaStream_t st) {
     if (B <= 0) return cudaSuccess;
     const Layout L(k);
-    Acts A(act, B, k);
-    __nv_bfloat16 *wb = static_cast<__nv_bfloat16 *>(work);
-    __nv_bfloat16 *im = wb + ((bf16_weight_elems() + 127) & ~(size_t)127);   // 256-byte aligned
+    Acts A(act, B, k);   // a[0..3] hold BF16 NHWC activations, a[4] FP32 NHWC
+    __nv_bfloat16 *wl = static_cast<__nv_bfloat16 *>(work);
     k_cnn_stats<<<B, 256, 0, st>>>(in.x, in.img_stride, in.row_stride, in.ox, in.oy, 128, A.affine);
     CNN_TRY(cudaGetLastError());
     int n_launch = 1;
-    // first convolution (K = 9) directly in FP32; every activation NHWC
     {
         const long np = (long)B * 64 * 64;
-        k_cnn_conv1_nhwc<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(in.x, in.img_stride, in.row_stride, in.ox,
-                                                                      in.oy, A.affine, params + L.cw[0],
-                                                                      params + L.cb[0], B, A.a[0]);
+        k_cnn_conv1_nhwc<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(
+            in.x, in.img_stride, in.row_stride, in.ox, in.oy, A.affine, params + L.cw[0], params + L.cb[0], B,
+            reinterpret_cast<__nv_bfloat16 *>(A.a[0]));
         CNN_TRY(cudaGetLastError());
         ++n_launch;
     }
-    __nv_bfloat16 *wl = wb;
-    int s = 64;
     for (int l = 1; l < 5; ++l) {
-        const int so = s / 2, Kp = kBf16Kp[l], Co = kCh[l + 1];
-        const long rows = (long)B * so * so;
+        const int Kp = kBf16Kp[l], Co = kCh[l + 1];
         const long nw = (long)Co * Kp;
         k_cnn_weights_bf16<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(params + L.cw[l], Co, kCh[l], Kp, wl);
         CNN_TRY(cudaGetLastError());
-        k_cnn_im2col_bf16<<<(unsigned)((rows + kIm2colRows - 1) / kIm2colRows), 256, 0, st>>>(A.a[l - 1], kCh[l], s,
-                                                                                            Kp, rows, im);
-        CNN_TRY(cudaGetLastError());
-        CNN_TRY(launch_screen_tc(im, (int)rows, wl, Co, Kp, A.a[l], err, st));
-        const long n = rows * Co;
-        k_cnn_bias_relu_rows<<<(unsigned)std::min<long>((n + 255) / 256, 65535), 256, 0, st>>>(A.a[l],
-                                                                                            params + L.cb[l], n, Co);
-        CNN_TRY(cudaGetLastError());
-        n_launch += 4;
+        CNN_TRY(launch_conv_tc(l, A.a[l - 1], B, wl, params + L.cb[l], A.a[l], err, num_sms, st));
+        n_launch += 2;
         wl += nw;
-        s = so;
     }
     k_cnn_pool_nhwc<<<(B * kCh[5] + 255) / 256, 256, 0, st>>>(A.a[4], B, kCh[5], 16, A.pool);
     CNN_TRY(cudaGetLastError());

@@ -216,7 +216,15 @@ const float *cnn_output(float *act, int B, int k);   // [B][6k] inside the activ
 // bytes (256-byte aligned); err: the tensor-core pipeline's status word
 size_t cnn_bf16_work_bytes(int B);
 cudaError_t launch_cnn_forward_bf16(const float *params, int k, const CnnInput &in, int B, float *act, void *work,
-                                    int *err, int *launches, cudaStream_t st);
+                                    int *err, int num_sms, int *launches, cudaStream_t st);
+// convolution `layer` (1..4 = the network's second to fifth) as an implicit
+// GEMM on the tensor cores: x NHWC BF16 [B][S][S][Ci], w BF16 [Co][Kp] in the
+// order (ky * 3 + kx) Ci + ci (zero beyond 9 Ci), y NHWC [B][S/2][S/2][Co] =
+// relu(conv + bias), BF16 for layers 1..3 and FP32 for layer 4; (Ci, Co, S) =
+// (32, 64, 64), (64, 64, 32), (64, 128, 16), (128, 128, 8); err set to 1 when
+// a pipeline wait expired; x, w, y 16-byte aligned
+cudaError_t launch_conv_tc(int layer, const void *x, int B, const void *w, const float *bias, void *y, int *err,
+                           int num_sms, cudaStream_t st);
 cudaError_t launch_cnn_forward(const float *params, int k, const CnnInput &in, int B, float *act, int *launches,
                                cudaStream_t st);
 // after launch_cnn_forward on the same act: loss_sum += sum of per-pattern

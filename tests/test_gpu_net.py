@@ -101,6 +101,24 @@ def test_bf16_forward_matches_oracle_bf16_form(px, ctx, orc):
     net.close()
 
 
+def test_bf16_forward_many_tiles_sampled(px, ctx, orc):
+    """The BF16 form on 1,100 patterns: two network passes (1,024 + 76), tens
+    of tiles per CTA in every tensor-core convolution (so both accumulator
+    buffers and every ring stage wrap many times), ragged last tiles; sampled
+    rows against the oracle's BF16 form at the same 2e-3 of the output scale."""
+    p = synth.cnn_init_params(K, 6)
+    x = _images(1100, 7)
+    net = px.xcf_net_create(ctx, K, dev(p))
+    net.set_bf16(True)
+    out = px.xcf_net_forward(ctx, net, dev(x)).cpu().numpy()
+    idx = np.array([0, 1, 2, 127, 128, 511, 700, 1022, 1023, 1024, 1025, 1062, 1098, 1099])
+    ref = orc.cnn_forward_bf16(p, x[idx], K)
+    scale = np.abs(ref).max()
+    assert np.abs(out[idx] - ref).max() <= 2e-3 * scale, np.abs(out[idx] - ref).max() / scale
+    assert np.isfinite(out).all()
+    net.close()
+
+
 def test_forward_reads_the_centred_crop(px, ctx, orc):
     W, H, pc = 160, 140, (0.5, 0.5, 0.6)
     p = synth.cnn_init_params(K, 4)
