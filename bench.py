@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--form-steps", type=int, default=3, help="timed steps of each sub-record form")
     ap.add_argument("--cpu-sample", type=int, default=0, help="patterns in the CPU sample (0: auto)")
     ap.add_argument("--form", default="plain",
-                    choices=["plain", "precision", "batched", "learned", "ndp", "fwhm", "so3"],
+                    choices=["plain", "precision", "batched", "learned", "ndp", "fwhm", "so3", "net"],
                     help="plain: full FP32 XCF search + refinement of the 128^2 map; precision: BF16 "
                          "tensor-core screen top-32 + FP32 rescore + refinement at 256^2; batched: eight maps "
                          "with different detectors in one persistent graph-captured search; learned: CNN proposals "
@@ -83,8 +83,10 @@ def parse():
                          "(Eq. 1) over the 2.5 deg library on the tensor cores + FP32 rescore + refinement of the "
                          "same 128^2 map; fwhm: the peak-width experiments of Figs. 3-4 (rotation scans about the "
                          "detector axes, NDP and FFT, against screen size and PC error); so3: the SO(3) sampling "
-                         "study of Fig. 2 (library generation and nearest-neighbour disorientations)")
-    ap.add_argument("--patterns", type=int, default=0, help="precision form: patterns per GPU (0: 50,000)")
+                         "study of Fig. 2 (library generation and nearest-neighbour disorientations); net: the proposal "
+                         "network's forward alone on 128^2 images (--patterns, default 100,000)")
+    ap.add_argument("--patterns", type=int, default=0,
+                    help="precision form: patterns per GPU (0: 50,000); net form: images per GPU (0: 100,000)")
     ap.add_argument("--scale", type=float, default=1.0, help="batched form: scale of every map's pattern count")
     ap.add_argument("--native", action="store_true",
                     help="batched form: native crop rule (96 and 160 px detectors used whole, 200 -> 160)")
@@ -587,6 +589,70 @@ def run_fwhm(args, px, torch, dev, rank, world, local, dist):
                 "stage_ms_per_step": {kk: v[0] / args.steps for kk, v in prof.items()},
                 "roofline": None, "e2e": None, "cpu_baseline": None}
         print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+# --------------------------------------------------------------- net form
+def run_net(args, px, torch, dev, rank, world, local, dist):
+    """The proposal network's forward pass alone (the learned form's stage
+    `net`): standardisation, five convolutions, pool, two fc layers on
+    synthetic 128 x 128 images with seeded random weights.  One step = the
+    forward of every image; BF16 tensor-core convolutions 2-5 unless --net-fp32."""
+    n = args.patterns or 100000
+    g = torch.Generator(device=dev).manual_seed(11 + rank)
+    imgs = torch.rand((n, 128, 128), generator=g, device=dev, dtype=torch.float32)
+    ctx = px.Context()
+    net = px.xcf_net_create(ctx, 8, torch.from_numpy(synth.cnn_init_params(8, 3)).to(dev))
+    net.set_bf16(not args.net_fp32)
+    for _ in range(args.warmup):
+        out = px.xcf_net_forward(ctx, net, imgs)
+    px.xcf_profile_read(ctx, reset=True)
+    px.xcf_profile_enable(ctx, True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks_start(local)
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        out = px.xcf_net_forward(ctx, net, imgs)
+    ev1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clocks_stop(clk)
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
+    px.xcf_profile_enable(ctx, False)
+    prof = px.xcf_profile_read(ctx, reset=True)
+    pk = peaks_file()
+    if args.net_fp32:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        sm_max = (pk or {}).get("sm_max_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
+        peak, bound, basis = sms * 128 * 2 * sm_max * 1e6 / 1e12, "alu", "152 SMs x 128 FP32 lanes x 2 x clock"
+        kern = "proposal network forward (k_gemm, FP32)"
+    else:
+        peak, bound = (pk or {}).get("bf16_tflops_sustained") or 1700.0, "tensor"
+        basis = "measured sustained cuBLAS BF16 (MEASURED_PEAKS.json)" if pk else "fallback"
+        kern = "proposal network forward (convolution 1 direct FP32 -> BF16; 2-5 k_conv_tc implicit GEMM, tcgen05 BF16)"
+    achieved = CNN_FORWARD_FLOPS * n * args.steps / (elapsed_ms / 1e3) / 1e12
+    if rank == 0:
+        line = {"metric": "proposal network forward images/s", "value": whole_job_rate(n, args.steps, world, elapsed_ms),
+                "unit": "images/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if args.net_fp32 else "bf16 convolutions 2-5 + f32",
+                "data": "synthetic",
+                "config": {"workload": f"net128_k8_B{n}", "form": "net", "images_per_gpu": n,
+                           "parallelism": f"replicas x{world}",
+                           "l2": f"inputs larger than L2 ({n * 128 * 128 * 4 / 1e6:.0f} MB images; L2 129 MB)"},
+                "checksum": float(out.double().abs().sum()),
+                "gpu_launches": int(sum(v[1] for v in prof.values())), "clocks": clocks,
+                "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "traffic": None, "kernel": kern, "peak_basis": basis},
+                "stage_ms_per_step": {kk: v[0] / args.steps for kk, v in prof.items()},
+                "e2e": None, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+    net.close()
     ctx.close()
 
 
@@ -1130,9 +1196,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    if args.form in ("precision", "batched", "learned", "ndp", "fwhm", "so3"):
+    if args.form in ("precision", "batched", "learned", "ndp", "fwhm", "so3", "net"):
         fn = {"precision": run_precision, "batched": run_batched, "learned": run_learned, "ndp": run_ndp,
-              "fwhm": run_fwhm, "so3": run_so3}[args.form]
+              "fwhm": run_fwhm, "so3": run_so3, "net": run_net}[args.form]
         fn(args, px, torch, dev, rank, world, local, dist)
         if dist:
             dist.destroy_process_group()

@@ -88,25 +88,36 @@ __global__ void __launch_bounds__(PT) k_prep_real(const float *__restrict__ img,
     // one pass of FP32 sums of (x - x0), x0 the crop's first pixel (a constant crop has exactly
     // zero variance; the shift keeps the per-thread sums well conditioned), combined in FP64
     __shared__ proj::Frame fr;
+    proj::Frame f{};   // in registers: the loops below store to shared memory, which could alias fr
     if constexpr (PROJ) {
         if (tid == 0) proj::frame(ps.quats + 4 * (size_t)p, ps.pcs ? ps.pcs + 3 * (size_t)p : nullptr, ps.a, fr);
         __syncthreads();
+        f = fr;
     }
     auto pixel = [&](int r, int c) -> float {   // image pixel (a.oy + r, a.ox + c)
         if constexpr (PROJ)
-            return proj::pixel(fr, ps.master, ps.M, ps.a, a.oy + r, a.ox + c);
+            return proj::pixel(f, ps.master, ps.M, ps.a, a.oy + r, a.ox + c);
         else
             return src[(size_t)(a.oy + r) * a.W + a.ox + c];
     };
     const float x0 = pixel(0, 0);
     float s1 = 0.f, s2 = 0.f;
-    for (int idx = tid; idx < N * N; idx += PT) {
-        const int r = idx / N, c = idx % N;
-        const float v = pixel(r, c);
+    auto take = [&](int r, int c, float v) {
         reinterpret_cast<float *>(buf + (r >> 1) * LD + c)[r & 1] = v;
         const float d = v - x0;
         s1 += d;
         s2 = fmaf(d, d, s2);
+    };
+    if constexpr (PROJ && PT % N == 0) {
+        // every pixel of this thread lies in column tid mod N: its column part once
+        const int c = tid % N;
+        const proj::Col col = proj::column(f, ps.a, a.ox + c);
+        for (int r = tid / N; r < N; r += PT / N) take(r, c, proj::pixel(f, col, ps.master, ps.M, ps.a, a.oy + r));
+    } else {
+        for (int idx = tid; idx < N * N; idx += PT) {
+            const int r = idx / N, c = idx % N;
+            take(r, c, pixel(r, c));
+        }
     }
     const double m1 = block_sum_f(s1, red) / (N * N), m2 = block_sum_f(s2, red) / (N * N);
     const double mean = x0 + m1, var = m2 - m1 * m1;

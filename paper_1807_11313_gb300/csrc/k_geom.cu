@@ -53,11 +53,12 @@ __global__ void __launch_bounds__(256) k_project(const float *__restrict__ maste
     __shared__ proj::Frame fr;
     if (threadIdx.x == 0) proj::frame(quats + 4 * (size_t)p, pcs ? pcs + 3 * (size_t)p : nullptr, a, fr);
     __syncthreads();
+    const proj::Frame f = fr;   // in registers: the loop's stores could alias shared memory
     const int npx = a.nx * a.ny;
     float *dst = out + (size_t)p * npx;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < npx; idx += gridDim.x * blockDim.x) {
         const int i = idx / a.nx, j = idx % a.nx;
-        dst[idx] = proj::pixel(fr, master, M, a, i, j);
+        dst[idx] = proj::pixel(f, master, M, a, i, j);
     }
 }
 

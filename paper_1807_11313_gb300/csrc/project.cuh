@@ -31,15 +31,15 @@ __device__ __forceinline__ float master_lookup(const float *__restrict__ master,
         const float qv = sqrtf(2.f * s2 / (1.f + az));   // sqrt(2 (1 - |z|)), cancellation-free
         const float sp = 0.88622692545275801365f;         // sqrt(pi) / 2
         const float ts = 1.12837916709551257390f;         // 2 / sqrt(pi)
-        if (fabsf(y) <= fabsf(x)) {
-            const float sg = x >= 0.f ? 1.f : -1.f;
-            X = sg * qv * sp;
-            Y = sg * qv * ts * atanf(y / x);
-        } else {
-            const float sg = y >= 0.f ? 1.f : -1.f;
-            X = sg * qv * ts * atanf(x / y);
-            Y = sg * qv * sp;
-        }
+        // the square's sector: |y| <= |x| maps to (sg qv sp, sg qv ts atan(y / x)),
+        // else to (sg qv ts atan(x / y), sg qv sp), sg the sign of the larger
+        // component; both cases as one division and one arctangent (no divergence)
+        const bool xmaj = fabsf(y) <= fabsf(x);
+        const float num = xmaj ? y : x, den = xmaj ? x : y;
+        const float sg = den >= 0.f ? 1.f : -1.f;
+        const float u = sg * qv * sp, t = sg * qv * ts * atanf(num / den);
+        X = xmaj ? u : t;
+        Y = xmaj ? t : u;
     }
     const float invL = 0.79788456080286535588f;           // 1 / sqrt(pi / 2)
     float fx = (X * invL + 1.f) * (0.5f * M) - 0.5f;
@@ -99,19 +99,32 @@ __device__ __forceinline__ void frame(const double *__restrict__ q4, const doubl
     f.pc[1] = (float)py * (float)a.H;
     f.pc[2] = (float)pz * (float)a.W;
 }
-// the template's value at pixel (i, j) of the output region (detector pixel
-// (oy + i, ox + j), centre of the pixel)
+// the part of a pixel's detector direction that depends on its column j alone
+// (detector column ox + j): the x offset from the pattern centre and the
+// rotated contributions of the x and z components, G[:, 0] dx + G[:, 2] dz
+struct Col {
+    float dx, bx, by, bz;
+};
+__device__ __forceinline__ Col column(const Frame &f, const ProjArgs &a, int j) {
+    const float dx = (float)(a.ox + j) + 0.5f - f.pc[0], dz = f.pc[2];
+    return Col{dx, fmaf(f.G[0], dx, f.G[2] * dz), fmaf(f.G[3], dx, f.G[5] * dz), fmaf(f.G[6], dx, f.G[8] * dz)};
+}
+// the template's value at pixel (i, c) of the output region (detector pixel
+// (oy + i, ox + j) for the column c = column(f, a, j), centre of the pixel):
+// the crystal direction G d / |d| (G is a rotation, so the direction is
+// rotated first and normalised after) looked up in the master pattern
+__device__ __forceinline__ float pixel(const Frame &f, const Col &c, const float *__restrict__ master, int M,
+                                       const ProjArgs &a, int i) {
+    const float dy = f.pc[1] - ((float)(a.oy + i) + 0.5f), dz = f.pc[2];
+    const float inv = rsqrtf(fmaf(dy, dy, fmaf(c.dx, c.dx, dz * dz)));
+    const float cx = fmaf(f.G[1], dy, c.bx) * inv;
+    const float cy = fmaf(f.G[4], dy, c.by) * inv;
+    const float cz = fmaf(f.G[7], dy, c.bz) * inv;
+    return master_lookup(master, M, cx, cy, cz, a.interp);
+}
 __device__ __forceinline__ float pixel(const Frame &f, const float *__restrict__ master, int M, const ProjArgs &a,
                                        int i, int j) {
-    float dx = (float)(a.ox + j) + 0.5f - f.pc[0];
-    float dy = f.pc[1] - ((float)(a.oy + i) + 0.5f);
-    float dz = f.pc[2];
-    const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-    dx *= inv; dy *= inv; dz *= inv;
-    const float cx = f.G[0] * dx + f.G[1] * dy + f.G[2] * dz;
-    const float cy = f.G[3] * dx + f.G[4] * dy + f.G[5] * dz;
-    const float cz = f.G[6] * dx + f.G[7] * dy + f.G[8] * dz;
-    return master_lookup(master, M, cx, cy, cz, a.interp);
+    return pixel(f, column(f, a, j), master, M, a, i);
 }
 
 }  // namespace proj
