@@ -1777,18 +1777,20 @@ int xcf_index_learned(xcf_ctx *ctx, xcf_net *net, const xcf_library *lib, const 
         double *q = quats + 4 * (size_t)p0;
         double *prop, *qh;
         float2 *sp, *stt;
-        float *img_t, *peak_h, *shift, *best_peak;
+        float *img_t, *peak_h, *shift, *best_peak, *yp;
         int *degen, *count;
         if ((rc = scratch_t(ctx, S_PROP, (size_t)np * k * 4, &prop)) || (rc = scratch_t(ctx, S_QH, (size_t)np * 4, &qh)) ||
             (rc = scratch_t(ctx, S_SPEC_P, (size_t)np * H, &sp)) || (rc = scratch_t(ctx, S_SPEC_T, (size_t)np * H, &stt)) ||
+            (rc = scratch_t(ctx, S_SPATIAL_P, (size_t)np * n * n, &yp)) ||
             (rc = scratch_t(ctx, S_IMG, (size_t)np * n * n, &img_t)) || (rc = scratch_t(ctx, S_PEAK, np, &peak_h)) ||
             (rc = scratch_t(ctx, S_SHIFT, (size_t)np * 2, &shift)) || (rc = scratch_t(ctx, S_BESTPEAK, np, &best_peak)) ||
             (rc = scratch_t(ctx, S_DEGEN, np, &degen)) || (rc = scratch_t(ctx, S_FBCOUNT, 2, &count)))
             return rc;
         // 1. proposals
         if ((rc = propose_all(ctx, net, offset_input(in, p0), np, prop, st))) return rc;
-        // 2. correlation score of every proposal, the best kept as the seed
-        XCF_LAUNCH(XCF_STAGE_PREP, st, run_prep(ctx, pat, np, pa, sp, nullptr, degen, nullptr, st), "prep patterns");
+        // 2. correlation score of every proposal, the best kept as the seed (the
+        // patterns' spectra, filtered images and flags stay for the refinement)
+        XCF_LAUNCH(XCF_STAGE_PREP, st, run_prep(ctx, pat, np, pa, sp, yp, degen, nullptr, st), "prep patterns");
         for (int h = 0; h < k; ++h) {
             XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_take_head(prop, np, k, h, qh, st), "take head");
             if ((rc = project_prep(ctx, lib->master, lib->M, qh, pc, nullptr, np, pj, ps, stt, nullptr, nullptr, img_t,
@@ -1798,8 +1800,8 @@ int xcf_index_learned(xcf_ctx *ctx, xcf_net *net, const xcf_library *lib, const 
                        "proposal peaks");
             XCF_LAUNCH(XCF_STAGE_OTHER, st, launch_keep_best(peak_h, qh, np, h, best_peak, q, nullptr, st), "keep best");
         }
-        // 3. refinement of the best proposal
-        if ((rc = refine_chunk(ctx, lib, pat, np, q, pc, q, peak + p0, iters + p0, st))) return rc;
+        // 3. refinement of the best proposal, on the patterns pre-processed above
+        if ((rc = refine_chunk(ctx, lib, pat, np, q, pc, q, peak + p0, iters + p0, st, nullptr, true))) return rc;
         // 4. fallback where the refined peak stays below tau
         if ((rc = scratch_t(ctx, S_DEGEN, np, &degen))) return rc;   // the refinement's pattern flags
         int *fidx, *flag_c;

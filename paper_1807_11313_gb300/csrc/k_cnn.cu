@@ -314,8 +314,9 @@ __global__ void __launch_bounds__(256) k_cnn_conv1_nhwc(const float *__restrict_
                                                         const float *__restrict__ w, const float *__restrict__ bias,
                                                         int B, __nv_bfloat16 *__restrict__ y) {
     constexpr int S = 128, So = 64, Co = 32;
-    __shared__ float ws[Co * 9], bs[Co];
-    for (int i = threadIdx.x; i < Co * 9; i += blockDim.x) ws[i] = w[i];
+    __shared__ __align__(16) float ws[9 * Co];   // [tap][channel]: four channels per 16-byte broadcast load
+    __shared__ float bs[Co];
+    for (int i = threadIdx.x; i < Co * 9; i += blockDim.x) ws[(i % 9) * Co + i / 9] = w[i];
     if (threadIdx.x < Co) bs[threadIdx.x] = bias[threadIdx.x];
     __syncthreads();
     const long n = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -329,29 +330,37 @@ __global__ void __launch_bounds__(256) k_cnn_conv1_nhwc(const float *__restrict_
         const int iy = 2 * oy - 1 + r / 3, ix = 2 * ox - 1 + r % 3;
         v[r] = (iy >= 0 && iy < S && ix >= 0 && ix < S) ? fmaf(img[(long)iy * row_stride + ix], a.x, a.y) : 0.f;
     }
+    // per channel: bias, then the taps in order 0..8 (one FMA each)
+    float acc[Co];
+#pragma unroll
+    for (int c = 0; c < Co; ++c) acc[c] = bs[c];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        const float4 *w4 = reinterpret_cast<const float4 *>(ws + r * Co);
+#pragma unroll
+        for (int c4 = 0; c4 < Co / 4; ++c4) {
+            const float4 q = w4[c4];
+            acc[4 * c4 + 0] = fmaf(q.x, v[r], acc[4 * c4 + 0]);
+            acc[4 * c4 + 1] = fmaf(q.y, v[r], acc[4 * c4 + 1]);
+            acc[4 * c4 + 2] = fmaf(q.z, v[r], acc[4 * c4 + 2]);
+            acc[4 * c4 + 3] = fmaf(q.w, v[r], acc[4 * c4 + 3]);
+        }
+    }
     uint4 *dst = reinterpret_cast<uint4 *>(y + n * Co);
 #pragma unroll
     for (int c8 = 0; c8 < Co / 8; ++c8) {
         uint32_t h[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            float o[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int c = 8 * c8 + 2 * j + u;
-                float acc = bs[c];
-#pragma unroll
-                for (int r = 0; r < 9; ++r) acc = fmaf(ws[c * 9 + r], v[r], acc);
-                o[u] = fmaxf(acc, 0.f);
-            }
-            const __nv_bfloat162 t = __floats2bfloat162_rn(o[0], o[1]);
+            const int c = 8 * c8 + 2 * j;
+            const __nv_bfloat162 t = __floats2bfloat162_rn(fmaxf(acc[c], 0.f), fmaxf(acc[c + 1], 0.f));
             h[j] = *reinterpret_cast<const uint32_t *>(&t);
         }
         dst[c8] = make_uint4(h[0], h[1], h[2], h[3]);
     }
 }
 
-// weights [Co][Ci][9] FP32 -> [Co][Kp] BF16 in the im2col order (r Ci + ci), zero padded
+// weights [Co][Ci][9] FP32 -> [Co][Kp] BF16 in the order k = r Ci + ci (r = ky * 3 + kx), zero padded
 __global__ void k_cnn_weights_bf16(const float *__restrict__ w, int Co, int Ci, int Kp,
                                    __nv_bfloat16 *__restrict__ out) {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
