@@ -63,16 +63,15 @@ __global__ void __launch_bounds__(256) k_project(const float *__restrict__ maste
 }
 
 // ------------------------------------------------------------ log-polar
-// each thread samples one (radius m, angle l) position of kLpPats images: the
-// position (one expf, one sincospif) is computed once for all of them
-constexpr int kLpPats = 8;
-__global__ void __launch_bounds__(256) k_logpolar(const float *__restrict__ spatial,
-                                                  const int *__restrict__ active, int P, int N, int nr,
-                                                  int neta, float rmin, float rmax, float *__restrict__ out) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nr * neta) return;
+// sample idx = m neta + l sits at radius rmin (rmax / rmin)^(m / (nr - 1)) and
+// angle 2 pi l / neta about the image centre; o = y0 N + x0 is its bilinear
+// corner and (tx, ty) its weights (lr = log(rmax / rmin))
+struct LpPos {
+    int o;
+    float tx, ty;
+};
+__device__ __forceinline__ LpPos lp_pos(int idx, int N, int nr, int neta, float rmin, float lr) {
     const float c = 0.5f * N - 0.5f;
-    const float lr = logf(rmax / rmin);
     const int m = idx / neta, l = idx % neta;
     const float r = rmin * expf(lr * (nr > 1 ? (float)m / (nr - 1) : 0.f));
     float sn, cs;
@@ -81,13 +80,48 @@ __global__ void __launch_bounds__(256) k_logpolar(const float *__restrict__ spat
     int x0 = (int)floorf(fx), y0 = (int)floorf(fy);
     x0 = min(max(x0, 0), N - 2);
     y0 = min(max(y0, 0), N - 2);
-    const float tx = fx - x0, ty = fy - y0;
+    return LpPos{y0 * N + x0, fx - x0, fy - y0};
+}
+__device__ __forceinline__ float lp_bilinear(const float *g, int N, const LpPos &q) {
+    return (1.f - q.ty) * ((1.f - q.tx) * g[0] + q.tx * g[1]) + q.ty * ((1.f - q.tx) * g[N] + q.tx * g[N + 1]);
+}
+
+// sides above the shared-memory limit: each thread samples one position of
+// kLpPats images (the position, one expf and one sincospif, computed once for
+// all of them) straight from global memory
+constexpr int kLpPats = 8;
+__global__ void __launch_bounds__(256) k_logpolar(const float *__restrict__ spatial,
+                                                  const int *__restrict__ active, int P, int N, int nr,
+                                                  int neta, float rmin, float rmax, float *__restrict__ out) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nr * neta) return;
+    const LpPos q = lp_pos(idx, N, nr, neta, rmin, logf(rmax / rmin));
     const int p1 = min(P, (int)(blockIdx.y + 1) * kLpPats);
     for (int p = blockIdx.y * kLpPats; p < p1; ++p) {
         if (active && !active[p]) continue;
-        const float *g = spatial + (size_t)p * N * N + y0 * N + x0;
-        out[(size_t)p * nr * neta + idx] =
-            (1.f - ty) * ((1.f - tx) * g[0] + tx * g[1]) + ty * ((1.f - tx) * g[N] + tx * g[N + 1]);
+        out[(size_t)p * nr * neta + idx] = lp_bilinear(spatial + (size_t)p * N * N + q.o, N, q);
+    }
+}
+
+// sides up to kLpSmemSide: one image per CTA, read from HBM once with
+// coalesced 16-byte loads into shared memory and sampled there (the samples'
+// scattered bilinear reads then cost shared-memory wavefronts, not sectors)
+constexpr int kLpSmemSide = 160;
+__global__ void __launch_bounds__(256) k_logpolar_img(const float *__restrict__ spatial,
+                                                      const int *__restrict__ active, int N, int nr, int neta,
+                                                      float rmin, float rmax, float *__restrict__ out) {
+    extern __shared__ float4 lp_img4[];
+    const int p = blockIdx.x;
+    if (active && !active[p]) return;
+    const float4 *src = reinterpret_cast<const float4 *>(spatial + (size_t)p * N * N);
+    for (int i = threadIdx.x; i < N * N / 4; i += blockDim.x) lp_img4[i] = src[i];
+    __syncthreads();
+    const float *img = reinterpret_cast<const float *>(lp_img4);
+    const float lr = logf(rmax / rmin);
+    float *dst = out + (size_t)p * nr * neta;
+    for (int idx = threadIdx.x; idx < nr * neta; idx += blockDim.x) {
+        const LpPos q = lp_pos(idx, N, nr, neta, rmin, lr);
+        dst[idx] = lp_bilinear(img + q.o, N, q);
     }
 }
 
@@ -391,6 +425,14 @@ cudaError_t launch_project(const float *master, int M, const double *quats, cons
 cudaError_t launch_logpolar(const float *spatial, const int *active, int P, int N, int nr, int neta,
                             float rmin, float rmax, float *out, cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
+    if (N <= kLpSmemSide && N % 2 == 0 && !(reinterpret_cast<uintptr_t>(spatial) & 15)) {
+        const int sm = (int)(sizeof(float) * N * N);
+        cudaError_t e = cudaFuncSetAttribute(k_logpolar_img, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(sizeof(float) * kLpSmemSide * kLpSmemSide));
+        if (e != cudaSuccess) return e;
+        k_logpolar_img<<<P, 256, sm, st>>>(spatial, active, N, nr, neta, rmin, rmax, out);
+        return cudaGetLastError();
+    }
     constexpr int kChunk = 65535 * kLpPats;          // grid.y limit
     for (int p0 = 0; p0 < P; p0 += kChunk) {
         const int np = P - p0 < kChunk ? P - p0 : kChunk;
