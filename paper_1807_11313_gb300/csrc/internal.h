@@ -64,7 +64,7 @@ enum Slot {
     S_NN_KEYS,      // nearest neighbour: packed best keys
     S_NN_ANG,       // nearest neighbour: angles (generator's duplicate pass)
     S_NN_IDX,       // nearest neighbour: indices (generator's duplicate pass)
-    S_NET_BF16,     // proposal network, BF16 inference: weights and im2col matrix
+    S_NET_BF16,     // proposal network, BF16 inference: the convolutions' BF16 weights [Co][Kp]
     S_PROBE,        // FMA rate probe: its sink word
     S_COUNT
 };
